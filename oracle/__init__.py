@@ -1,0 +1,231 @@
+"""CPU oracle for the BLINK dirty-imaging hot path (arXiv 2505.15204).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+are the only callers.  The product library never imports this package and shares no code with it.
+
+The arithmetic lives in ``blink_oracle.c`` (plain loops, int64 correlation, FP64 geometry, gridding and
+FFT); this module compiles it with gcc on first use and wraps it with numpy arrays.  See the C file's
+header for the equation each function follows.
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against closed forms, invariants, a
+brute-force direct DFT, an independent library FFT and the paper's data-volume table.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "blink_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+POL_I = 0
+POL_XX = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, -ffp-contract=off, OpenMP)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            lib.oracle_n_baselines.restype = C.c_int64
+            lib.oracle_n_baselines.argtypes = [C.c_int]
+            lib.oracle_correlate.restype = None
+            lib.oracle_correlate.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+            lib.oracle_correlate_one.restype = None
+            lib.oracle_correlate_one.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
+            lib.oracle_output_freqs.restype = None
+            lib.oracle_output_freqs.argtypes = [P, C.c_int, C.c_int, P]
+            lib.oracle_uvw.restype = None
+            lib.oracle_uvw.argtypes = [P, C.c_int, C.c_double, P]
+            lib.oracle_default_cell.restype = C.c_double
+            lib.oracle_default_cell.argtypes = [P, C.c_int, P, C.c_double, C.c_int]
+            lib.oracle_cells.restype = None
+            lib.oracle_cells.argtypes = [P, C.c_int64, C.c_double, C.c_int, P, P, P]
+            lib.oracle_grid.restype = C.c_double
+            lib.oracle_grid.argtypes = [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, P, P, C.c_int, P]
+            lib.oracle_ifft2.restype = C.c_int
+            lib.oracle_ifft2.argtypes = [P, C.c_int]
+            lib.oracle_idft2.restype = None
+            lib.oracle_idft2.argtypes = [P, C.c_int, P]
+            lib.oracle_image.restype = C.c_double
+            lib.oracle_image.argtypes = [P, C.c_int, C.c_double, P]
+            lib.oracle_pipeline.restype = C.c_int
+            lib.oracle_pipeline.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
+                                            C.c_int, C.c_double, C.c_int, C.c_int, P, C.c_int64, C.c_int,
+                                            P, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _flags(flags, n_tiles):
+    if flags is None:
+        return None
+    f = np.ascontiguousarray(flags, dtype=np.uint8)
+    assert f.shape == (n_tiles,)
+    return f
+
+
+def n_baselines(n_tiles: int) -> int:
+    return int(_load().oracle_n_baselines(n_tiles))
+
+
+def correlate(volt: np.ndarray, ns: int, c: int, flags=None) -> np.ndarray:
+    """Raw integer correlation products S, int64 [T][F][B][4][2] (Eq. 2; lower triangle, XX XY YX YY).
+
+    ``volt`` is uint8 [S][F_fine][n_tiles][2]; T = S // ns, F = F_fine // c.
+    """
+    volt = np.ascontiguousarray(volt, dtype=np.uint8)
+    s, nf, nt, two = volt.shape
+    assert two == 2
+    T, F, B = s // ns, nf // c, n_baselines(nt)
+    out = np.zeros((T, F, B, 4, 2), dtype=np.int64)
+    fl = _flags(flags, nt)
+    _load().oracle_correlate(_p(volt), nf, nt, nf, c, ns, s, _p(fl), _p(out))
+    return out
+
+
+def correlate_one(volt: np.ndarray, ns: int, c: int, tau: int, f: int, flags=None, fine0: int = 0,
+                  n_fine: int | None = None) -> np.ndarray:
+    """S for one integration and one output channel of the set starting at fine channel ``fine0``."""
+    volt = np.ascontiguousarray(volt, dtype=np.uint8)
+    s, nf, nt, _ = volt.shape
+    B = n_baselines(nt)
+    out = np.zeros((B, 4, 2), dtype=np.int64)
+    fl = _flags(flags, nt)
+    _load().oracle_correlate_one(volt.ctypes.data + fine0 * nt * 2, nf, nt, ns, c, tau, f, _p(fl), _p(out))
+    return out
+
+
+def visibilities(S: np.ndarray, K: int) -> np.ndarray:
+    """V = S / K as complex64, each component one IEEE float32 division of float32(S) by float32(K)."""
+    q = S.astype(np.float32) / np.float32(K)
+    return q[..., 0] + 1j * q[..., 1]
+
+
+def output_freqs(fine: np.ndarray, c: int) -> np.ndarray:
+    fine = np.ascontiguousarray(fine, dtype=np.float64)
+    out = np.zeros(len(fine) // c, dtype=np.float64)
+    _load().oracle_output_freqs(_p(fine), len(fine), c, _p(out))
+    return out
+
+
+def uvw(enu: np.ndarray, nu: float) -> np.ndarray:
+    enu = np.ascontiguousarray(enu, dtype=np.float64)
+    out = np.zeros((n_baselines(enu.shape[0]), 3), dtype=np.float64)
+    _load().oracle_uvw(_p(enu), enu.shape[0], float(nu), _p(out))
+    return out
+
+
+def default_cell(enu: np.ndarray, nu_max: float, n_pix: int, flags=None) -> float:
+    enu = np.ascontiguousarray(enu, dtype=np.float64)
+    fl = _flags(flags, enu.shape[0])
+    return float(_load().oracle_default_cell(_p(enu), enu.shape[0], _p(fl), float(nu_max), n_pix))
+
+
+def cells(uvw_: np.ndarray, du: float, n_pix: int):
+    uvw_ = np.ascontiguousarray(uvw_, dtype=np.float64)
+    B = uvw_.shape[0]
+    iu = np.zeros(B, np.int32)
+    iv = np.zeros(B, np.int32)
+    keep = np.zeros(B, np.uint8)
+    _load().oracle_cells(_p(uvw_), B, float(du), n_pix, _p(iu), _p(iv), _p(keep))
+    return iu, iv, keep
+
+
+def grid(S_img: np.ndarray, n_tiles: int, K: int, iu, iv, keep, n_pix: int, pol: int = POL_I,
+         autos: bool = True, flags=None):
+    """Full complex128 grid [N][N] (row v, column u, DC at [0][0]) and W, the sum of weights."""
+    S_img = np.ascontiguousarray(S_img, dtype=np.int64)
+    G = np.zeros((n_pix, n_pix, 2), dtype=np.float64)
+    fl = _flags(flags, n_tiles)
+    iu = np.ascontiguousarray(iu, np.int32)
+    iv = np.ascontiguousarray(iv, np.int32)
+    keep = np.ascontiguousarray(keep, np.uint8)
+    W = _load().oracle_grid(_p(S_img), n_tiles, _p(fl), K, pol, int(bool(autos)), _p(iu), _p(iv), _p(keep),
+                            n_pix, _p(G))
+    return G[..., 0] + 1j * G[..., 1], float(W)
+
+
+def ifft2(G: np.ndarray) -> np.ndarray:
+    """Unnormalised inverse 2D transform by the oracle's own radix-2 FFT (power-of-two sides)."""
+    n = G.shape[0]
+    a = np.ascontiguousarray(np.stack([G.real, G.imag], axis=-1), dtype=np.float64)
+    if _load().oracle_ifft2(_p(a), n):
+        raise ValueError("side must be a power of two")
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def idft2(G: np.ndarray) -> np.ndarray:
+    """The same transform as a direct O(n^4) sum."""
+    n = G.shape[0]
+    g = np.ascontiguousarray(np.stack([G.real, G.imag], axis=-1), dtype=np.float64)
+    a = np.zeros_like(g)
+    _load().oracle_idft2(_p(g), n, _p(a))
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def image(a: np.ndarray, W: float):
+    """Shifted real image / W and max |Im| / W."""
+    n = a.shape[0]
+    aa = np.ascontiguousarray(np.stack([a.real, a.imag], axis=-1), dtype=np.float64)
+    img = np.zeros((n, n), dtype=np.float64)
+    mx = _load().oracle_image(_p(aa), n, float(W), _p(img))
+    return img, float(mx)
+
+
+def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int, c: int, n_pix: int,
+             ids=None, flags=None, fine0: int = 0, n_fine: int | None = None, cell_lambda: float = 0.0,
+             pol: int = POL_I, autos: bool = True, n_threads: int = 1, want_grids: bool = False):
+    """Dirty images for the listed image ids (id = tau * F + f) of one set.
+
+    Returns dict(images [n][N][N] float64, W [n], max_im [n], grids [n][N][N] complex128 or None).
+    """
+    volt = np.ascontiguousarray(volt, dtype=np.uint8)
+    s, nf_total, nt, _ = volt.shape
+    if n_fine is None:
+        n_fine = nf_total - fine0
+    F = n_fine // c
+    T = s // ns
+    if ids is None:
+        ids = np.arange(T * F, dtype=np.int64)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    n = len(ids)
+    enu = np.ascontiguousarray(enu, dtype=np.float64)
+    ff = np.ascontiguousarray(fine_freqs[fine0:fine0 + n_fine], dtype=np.float64)
+    fl = _flags(flags, nt)
+    imgs = np.zeros((n, n_pix, n_pix), dtype=np.float64)
+    W = np.zeros(n, dtype=np.float64)
+    mx = np.zeros(n, dtype=np.float64)
+    grids = np.zeros((n, n_pix, n_pix, 2), dtype=np.float64) if want_grids else None
+    rc = _load().oracle_pipeline(volt.ctypes.data + fine0 * nt * 2, nf_total, nt, n_fine, c, ns, _p(enu), _p(ff),
+                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), _p(ids), n, n_threads,
+                                 _p(grids), _p(imgs), _p(W), _p(mx))
+    if rc:
+        raise ValueError("oracle_pipeline: bad arguments")
+    return {"images": imgs, "W": W, "max_im": mx,
+            "grids": None if grids is None else grids[..., 0] + 1j * grids[..., 1]}

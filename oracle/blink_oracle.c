@@ -1,0 +1,320 @@
+/*
+ * CPU oracle for the BLINK dirty-imaging hot path (arXiv 2505.15204).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load this library.  It shares no code, header or constant with the CUDA library.
+ *
+ * It is a plain, slow statement of what the method computes, one function per step, in exact integer
+ * arithmetic for the correlation and in FP64 for everything else:
+ *
+ *   correlate   Eq. 2 and Sec. 5.2.2: S_ij^pq = sum_{t, ch} x_i^p conj(x_j^q) over the N_s samples of an
+ *               integration and the c fine channels of an output channel; lower triangle i >= j.
+ *   uvw         Sec. 5.2.3-5.2.4: (u, v, w) = (r_i - r_j) * nu / c for every baseline and channel.
+ *   cells       Sec. 5.2.4 (gridding "based on the (u, v) coordinates", nearest cell, no kernel).
+ *   grid        Sec. 5.2.4: natural weighting, every visibility and its Hermitian mirror weight 1.
+ *   fft2        Eq. 4 / Sec. 5.2.4: unnormalised inverse 2D transform, own radix-2 FFT; direct DFT
+ *               for small sides.
+ *   image       Sec. 5.2.4: real part / sum of weights, shifted so the phase centre is the middle pixel.
+ *
+ * Readings where the paper is silent (stated in the design notes): Stokes I = (S_XX + S_YY) / (2K);
+ * uv cell default = u_max / (N/2 - 1); cell = floor(u / du + 1/2); autos gridded at (0, 0); grid DC at
+ * [0][0], row = v, column = u; image row = y (m), column = x (l), pixel (N/2, N/2) = phase centre.
+ *
+ * Compiled with -ffp-contract=off so each FP64 operation rounds once, in the order written.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_C_LIGHT 299792458.0
+#define ORC_TWO_PI 6.283185307179586476925286766559
+
+enum { ORC_POL_I = 0, ORC_POL_XX = 1 };
+
+/* ---- packed 4-bit complex sample: re = low nibble, im = high nibble, two's complement ---- */
+static int orc_lo(uint8_t b) { int v = b & 0xF; return v >= 8 ? v - 16 : v; }
+static int orc_hi(uint8_t b) { int v = (b >> 4) & 0xF; return v >= 8 ? v - 16 : v; }
+
+int64_t oracle_n_baselines(int n_tiles) { return (int64_t)n_tiles * (n_tiles + 1) / 2; }
+
+/*
+ * Correlation of one integration `tau` and one output channel `f` (Eq. 2; Sec. 5.2.2: lower triangle per
+ * integration and channel).  `volt` points at sample 0 of the set's first fine channel; consecutive
+ * samples are `fine_stride * n_tiles * 2` bytes apart and consecutive fine channels `n_tiles * 2`.
+ * S is int64 [B][4][2] (re, im) with b = i(i+1)/2 + j and polarisation index 2p + q (XX, XY, YX, YY).
+ * Pairs with a flagged tile stay 0.
+ */
+void oracle_correlate_one(const uint8_t* volt, int64_t fine_stride, int n_tiles, int ns, int c, int tau, int f,
+                          const uint8_t* flags, int64_t* S)
+{
+    int64_t B = oracle_n_baselines(n_tiles);
+    memset(S, 0, (size_t)B * 8 * sizeof(int64_t));
+    int64_t sample_stride = fine_stride * n_tiles * 2;
+    for (int t = tau * ns; t < (tau + 1) * ns; t++) {
+        for (int ch = f * c; ch < (f + 1) * c; ch++) {
+            const uint8_t* x = volt + (int64_t)t * sample_stride + (int64_t)ch * n_tiles * 2;
+            for (int i = 0; i < n_tiles; i++) {
+                for (int j = 0; j <= i; j++) {
+                    if (flags && (flags[i] || flags[j])) continue;
+                    int64_t b = (int64_t)i * (i + 1) / 2 + j;
+                    for (int p = 0; p < 2; p++) {
+                        for (int q = 0; q < 2; q++) {
+                            int64_t ar = orc_lo(x[2 * i + p]), ai = orc_hi(x[2 * i + p]);
+                            int64_t br = orc_lo(x[2 * j + q]), bi = orc_hi(x[2 * j + q]);
+                            /* (ar + i ai) * conj(br + i bi) */
+                            S[(b * 4 + 2 * p + q) * 2 + 0] += ar * br + ai * bi;
+                            S[(b * 4 + 2 * p + q) * 2 + 1] += ai * br - ar * bi;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* All integrations and output channels: S int64 [T][F][B][4][2], T = n_samples / ns, F = n_fine / c. */
+void oracle_correlate(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n_fine, int c, int ns,
+                      int n_samples, const uint8_t* flags, int64_t* S)
+{
+    int T = n_samples / ns, F = n_fine / c;
+    int64_t per = oracle_n_baselines(n_tiles) * 8;
+    for (int tau = 0; tau < T; tau++)
+        for (int f = 0; f < F; f++)
+            oracle_correlate_one(volt, fine_stride, n_tiles, ns, c, tau, f, flags, S + ((int64_t)tau * F + f) * per);
+}
+
+/* Output-channel centre frequency = mean of its c fine-channel centres (summed in order, then / c). */
+void oracle_output_freqs(const double* fine, int n_fine, int c, double* out)
+{
+    for (int f = 0; f < n_fine / c; f++) {
+        double s = 0.0;
+        for (int k = 0; k < c; k++) s += fine[f * c + k];
+        out[f] = s / (double)c;
+    }
+}
+
+/* Baseline coordinates in wavelengths (Sec. 5.2.3-5.2.4): b = r_i - r_j (E, N, U metres),
+ * (u, v, w) = b * (nu / c).  uvw is [B][3]. */
+void oracle_uvw(const double* enu, int n_tiles, double nu, double* uvw)
+{
+    double inv_lambda = nu / ORC_C_LIGHT;
+    for (int i = 0; i < n_tiles; i++)
+        for (int j = 0; j <= i; j++) {
+            int64_t b = (int64_t)i * (i + 1) / 2 + j;
+            for (int d = 0; d < 3; d++) uvw[b * 3 + d] = (enu[i * 3 + d] - enu[j * 3 + d]) * inv_lambda;
+        }
+}
+
+/* Default uv cell (wavelengths): the longest unflagged projected baseline at the highest frequency lands
+ * in the outermost usable cell, du = u_max / (N/2 - 1); u_max = max |(b_E, b_N)| * (nu_max / c).
+ * Degenerate arrays (no unflagged baseline of non-zero length) get du = 1. */
+double oracle_default_cell(const double* enu, int n_tiles, const uint8_t* flags, double nu_max, int n_pix)
+{
+    double dmax = 0.0;
+    for (int i = 0; i < n_tiles; i++)
+        for (int j = 0; j < i; j++) {
+            if (flags && (flags[i] || flags[j])) continue;
+            double be = enu[i * 3 + 0] - enu[j * 3 + 0];
+            double bn = enu[i * 3 + 1] - enu[j * 3 + 1];
+            double d = sqrt(be * be + bn * bn);
+            if (d > dmax) dmax = d;
+        }
+    double umax = dmax * (nu_max / ORC_C_LIGHT);
+    if (!(umax > 0.0)) return 1.0;
+    return umax / (double)(n_pix / 2 - 1);
+}
+
+/* Nearest grid cell: iu = floor(u / du + 1/2), iv = floor(v / du + 1/2); kept iff |iu|, |iv| < N/2. */
+void oracle_cells(const double* uvw, int64_t n_baselines, double du, int n_pix, int32_t* iu, int32_t* iv,
+                  uint8_t* keep)
+{
+    int h = n_pix / 2;
+    for (int64_t b = 0; b < n_baselines; b++) {
+        double x = floor(uvw[b * 3 + 0] / du + 0.5);
+        double y = floor(uvw[b * 3 + 1] / du + 0.5);
+        int ok = fabs(x) < (double)h && fabs(y) < (double)h;
+        iu[b] = ok ? (int32_t)x : 0;
+        iv[b] = ok ? (int32_t)y : 0;
+        keep[b] = (uint8_t)ok;
+    }
+}
+
+/*
+ * Gridding of one image (Sec. 5.2.4): natural weighting, nearest cell, no convolution kernel.
+ * Visibility of baseline (i, j): Stokes I = (S_XX + S_YY) / (2K), or XX = S_XX / K.
+ * Cross baselines (i > j, kept): G[v][u] += I and G[-v][-u] += conj(I), weight 2.
+ * Autocorrelations (i == j, when `autos`): G[0][0] += I, weight 1.
+ * G is complex double [N][N] (re, im interleaved), row = v, column = u, indices modulo N.
+ * Returns W, the sum of weights.
+ */
+double oracle_grid(const int64_t* S, int n_tiles, const uint8_t* flags, int K, int pol, int autos,
+                   const int32_t* iu, const int32_t* iv, const uint8_t* keep, int n_pix, double* G)
+{
+    int n = n_pix;
+    memset(G, 0, (size_t)n * n * 2 * sizeof(double));
+    double W = 0.0;
+    for (int i = 0; i < n_tiles; i++) {
+        for (int j = 0; j <= i; j++) {
+            if (flags && (flags[i] || flags[j])) continue;
+            int64_t b = (int64_t)i * (i + 1) / 2 + j;
+            const int64_t* s = S + b * 8;
+            double re, im;
+            if (pol == ORC_POL_I) {
+                re = (double)(s[0] + s[6]) / (2.0 * (double)K);
+                im = (double)(s[1] + s[7]) / (2.0 * (double)K);
+            } else {
+                re = (double)s[0] / (double)K;
+                im = (double)s[1] / (double)K;
+            }
+            if (i == j) {
+                if (!autos) continue;
+                G[0] += re;
+                G[1] += im;
+                W += 1.0;
+                continue;
+            }
+            if (!keep[b]) continue;
+            int u = ((iu[b] % n) + n) % n, v = ((iv[b] % n) + n) % n;
+            int um = ((-iu[b] % n) + n) % n, vm = ((-iv[b] % n) + n) % n;
+            G[((int64_t)v * n + u) * 2 + 0] += re;
+            G[((int64_t)v * n + u) * 2 + 1] += im;
+            G[((int64_t)vm * n + um) * 2 + 0] += re;
+            G[((int64_t)vm * n + um) * 2 + 1] -= im;
+            W += 2.0;
+        }
+    }
+    return W;
+}
+
+/* In-place unnormalised inverse DFT of n (a power of two) complex values spaced `stride` complex elements
+ * apart: X[k] <- sum_m X[m] exp(+2 pi i k m / n).  Iterative radix-2 Cooley-Tukey: bit-reversal
+ * permutation, then log2(n) butterfly stages; twiddles from libm cos/sin. */
+static void orc_ifft_1d(double* x, int n, int64_t stride)
+{
+    for (int i = 1, j = 0; i < n; i++) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) {
+            double* a = x + (int64_t)i * stride * 2;
+            double* b = x + (int64_t)j * stride * 2;
+            double tr = a[0], ti = a[1];
+            a[0] = b[0]; a[1] = b[1];
+            b[0] = tr; b[1] = ti;
+        }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        int half = len >> 1;
+        for (int k = 0; k < half; k++) {
+            double ang = ORC_TWO_PI * (double)k / (double)len;
+            double wr = cos(ang), wi = sin(ang);
+            for (int i = 0; i < n; i += len) {
+                double* a = x + (int64_t)(i + k) * stride * 2;
+                double* b = x + (int64_t)(i + k + half) * stride * 2;
+                double tr = b[0] * wr - b[1] * wi;
+                double ti = b[0] * wi + b[1] * wr;
+                b[0] = a[0] - tr; b[1] = a[1] - ti;
+                a[0] = a[0] + tr; a[1] = a[1] + ti;
+            }
+        }
+    }
+}
+
+/* Unnormalised inverse 2D transform in place (Eq. 4): a[y][x] = sum_{v,u} G[v][u] exp(+2 pi i (u x + v y) / n).
+ * Rows (u -> x) first, then columns (v -> y).  n must be a power of two; returns 0, or -1 otherwise. */
+int oracle_ifft2(double* a, int n)
+{
+    if (n <= 0 || (n & (n - 1))) return -1;
+    for (int r = 0; r < n; r++) orc_ifft_1d(a + (int64_t)r * n * 2, n, 1);
+    for (int col = 0; col < n; col++) orc_ifft_1d(a + (int64_t)col * 2, n, n);
+    return 0;
+}
+
+/* The same transform as a direct sum (any n; O(n^4), for small sides).  The phase index (u x + v y) is
+ * reduced modulo n in integers before the angle is formed. */
+void oracle_idft2(const double* G, int n, double* a)
+{
+    for (int y = 0; y < n; y++)
+        for (int x = 0; x < n; x++) {
+            double sr = 0.0, si = 0.0;
+            for (int v = 0; v < n; v++)
+                for (int u = 0; u < n; u++) {
+                    int64_t k = ((int64_t)u * x + (int64_t)v * y) % n;
+                    double ang = ORC_TWO_PI * (double)k / (double)n;
+                    double c = cos(ang), s = sin(ang);
+                    double gr = G[((int64_t)v * n + u) * 2], gi = G[((int64_t)v * n + u) * 2 + 1];
+                    sr += gr * c - gi * s;
+                    si += gr * s + gi * c;
+                }
+            a[((int64_t)y * n + x) * 2] = sr;
+            a[((int64_t)y * n + x) * 2 + 1] = si;
+        }
+}
+
+/* Dirty image (Sec. 5.2.4): img[y][x] = Re a[(y + N/2) mod N][(x + N/2) mod N] / W, which puts the phase
+ * centre (l = m = 0) at pixel (N/2, N/2).  Returns max |Im a| / W, which is zero up to rounding for a
+ * Hermitian grid. */
+double oracle_image(const double* a, int n, double W, double* img)
+{
+    int h = n / 2;
+    double mx = 0.0;
+    for (int y = 0; y < n; y++)
+        for (int x = 0; x < n; x++) {
+            const double* s = a + ((int64_t)((y + h) % n) * n + (x + h) % n) * 2;
+            img[(int64_t)y * n + x] = s[0] / W;
+            double m = fabs(s[1]) / W;
+            if (m > mx) mx = m;
+        }
+    return mx;
+}
+
+/*
+ * The whole path for a list of images of one set (one flag vector, one image side): for each image id
+ * (= tau * F + f) correlate, compute uvw and cells at the output channel's frequency, grid, transform and
+ * form the image.  cell_lambda <= 0 selects the default cell over the set's highest output frequency.
+ * Optional outputs (NULL to skip): grids [n_ids][N][N][2], images [n_ids][N][N], W [n_ids],
+ * max|Im|/W [n_ids].  Images are independent, so they are spread over `n_threads` OpenMP threads.
+ * Returns 0, or -1 on bad arguments.
+ */
+int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n_fine, int c, int ns,
+                    const double* enu, const double* fine_freq, const uint8_t* flags,
+                    int n_pix, double cell_lambda, int pol, int autos,
+                    const int64_t* ids, int64_t n_ids, int n_threads,
+                    double* grids, double* imgs, double* W_out, double* maxim_out)
+{
+    if (n_pix <= 2 || (n_pix & (n_pix - 1)) || c <= 0 || ns <= 0 || n_fine % c) return -1;
+    int F = n_fine / c;
+    double* fout = (double*)malloc(sizeof(double) * F);
+    oracle_output_freqs(fine_freq, n_fine, c, fout);
+    double numax = fout[0];
+    for (int f = 1; f < F; f++) if (fout[f] > numax) numax = fout[f];
+    double du = cell_lambda > 0.0 ? cell_lambda : oracle_default_cell(enu, n_tiles, flags, numax, n_pix);
+    int64_t B = oracle_n_baselines(n_tiles);
+    int K = ns * c;
+    int bad = 0;
+#pragma omp parallel for num_threads(n_threads) schedule(dynamic, 1)
+    for (int64_t q = 0; q < n_ids; q++) {
+        int tau = (int)(ids[q] / F), f = (int)(ids[q] % F);
+        int64_t* S = (int64_t*)malloc(sizeof(int64_t) * B * 8);
+        double* uvw = (double*)malloc(sizeof(double) * B * 3);
+        int32_t* iu = (int32_t*)malloc(sizeof(int32_t) * B);
+        int32_t* iv = (int32_t*)malloc(sizeof(int32_t) * B);
+        uint8_t* keep = (uint8_t*)malloc(B);
+        double* G = (double*)malloc(sizeof(double) * 2 * n_pix * n_pix);
+        double* im = (double*)malloc(sizeof(double) * n_pix * n_pix);
+        oracle_correlate_one(volt, fine_stride, n_tiles, ns, c, tau, f, flags, S);
+        oracle_uvw(enu, n_tiles, fout[f], uvw);
+        oracle_cells(uvw, B, du, n_pix, iu, iv, keep);
+        double W = oracle_grid(S, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
+        if (grids) memcpy(grids + q * 2 * n_pix * n_pix, G, sizeof(double) * 2 * n_pix * n_pix);
+        if (oracle_ifft2(G, n_pix)) bad = 1;
+        double mx = oracle_image(G, n_pix, W > 0.0 ? W : 1.0, im);
+        if (imgs) memcpy(imgs + q * n_pix * n_pix, im, sizeof(double) * n_pix * n_pix);
+        if (W_out) W_out[q] = W;
+        if (maxim_out) maxim_out[q] = mx;
+        free(S); free(uvw); free(iu); free(iv); free(keep); free(G); free(im);
+    }
+    free(fout);
+    return bad ? -1 : 0;
+}

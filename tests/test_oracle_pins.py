@@ -1,0 +1,378 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each test fixes one oracle function with a closed form, an invariant, a brute-force sum, an independent
+library routine or a number printed in the paper, chosen so that a plausible slip (a dropped term, a
+wrong sign or conjugate, a swapped index or polarisation, a wrong shift or normalisation) fails a test.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import blinksynth as bs
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+C_LIGHT = 299_792_458.0
+
+
+def _bidx(i, j):
+    return i * (i + 1) // 2 + j
+
+
+# ----------------------------------------------------------------------------------------------
+# correlation (Eq. 2; Sec. 5.2.2)
+# ----------------------------------------------------------------------------------------------
+
+def test_correlate_constant_voltages_closed_form():
+    # every sample of every input = a + ib  =>  S_ij^pq = K (a^2 + b^2), imaginary part 0
+    a, b, ns, c, nt = 3, -2, 5, 2, 6
+    v = bs.constant_voltages(ns * 2, c * 3, nt, a, b)
+    S = oracle.correlate(v, ns, c)
+    K = ns * c
+    assert S.shape == (2, 3, nt * (nt + 1) // 2, 4, 2)
+    assert np.all(S[..., 0] == K * (a * a + b * b))
+    assert np.all(S[..., 1] == 0)
+
+
+def test_correlate_phase_pattern_conjugates_second_tile():
+    # x_i^p = 2 * i^(k_ip) with distinct powers per tile and polarisation:
+    # S_ij^pq = K * 4 * i^(k_ip - k_jq) exactly.  A conjugate on the wrong factor flips the sign of Im;
+    # swapping XY and YX or i and j changes which power appears.
+    nt, ns = 5, 3
+    rng = np.random.default_rng(7)
+    k = rng.integers(0, 4, size=(nt, 2))
+    x = 2 * (1j ** k)
+    v = np.broadcast_to(bs.pack_complex(x), (ns, 1, nt, 2)).copy()
+    S = oracle.correlate(v, ns, 1)[0, 0]
+    for i in range(nt):
+        for j in range(i + 1):
+            for p in range(2):
+                for q in range(2):
+                    want = ns * 4 * (1j ** ((k[i, p] - k[j, q]) % 4))
+                    got = S[_bidx(i, j), 2 * p + q]
+                    assert got[0] == round(want.real) and got[1] == round(want.imag), (i, j, p, q)
+
+
+def test_correlate_single_product_lands_in_its_slot():
+    # one non-zero sample on tile 4 pol X and tile 1 pol Y: only S_41^XY = x conj(y) is non-zero
+    nt = 6
+    v = np.zeros((1, 1, nt, 2), np.uint8)
+    v[0, 0, 4, 0] = bs.pack_complex(np.array(3 - 1j))
+    v[0, 0, 1, 1] = bs.pack_complex(np.array(-2 + 5j))
+    S = oracle.correlate(v, 1, 1)[0, 0]
+    want = (3 - 1j) * np.conj(-2 + 5j)
+    nz = np.argwhere(np.any(S != 0, axis=-1))
+    # autos of the two tiles and the cross product
+    slots = {tuple(r) for r in nz}
+    assert (_bidx(4, 1), 1) in slots                     # XY of baseline (4, 1)
+    got = S[_bidx(4, 1), 1]
+    assert got[0] == want.real and got[1] == want.imag
+    assert slots == {(_bidx(4, 1), 1), (_bidx(4, 4), 0), (_bidx(1, 1), 3)}
+
+
+def test_correlate_autos_real_nonnegative_and_hermitian_pol_pairs():
+    w = bs.build_workload("tiny")
+    S = oracle.correlate(w["volt"], 10, 1)[0, 0]
+    nt = w["enu"].shape[0]
+    for i in range(nt):
+        b = _bidx(i, i)
+        assert S[b, 0, 1] == 0 and S[b, 3, 1] == 0           # XX, YY autos real
+        assert S[b, 0, 0] >= 0 and S[b, 3, 0] >= 0
+        assert S[b, 1, 0] == S[b, 2, 0] and S[b, 1, 1] == -S[b, 2, 1]   # XY = conj(YX)
+
+
+def test_correlate_blocks_add_up():
+    # an integration of N_s samples over c channels is the sum of its single-sample, single-channel products
+    w = bs.build_workload("coarse", n_samples=20)
+    v = w["volt"][:, :8]
+    S = oracle.correlate(v, 10, 4)
+    S1 = oracle.correlate(v, 1, 1)
+    for tau in range(2):
+        for f in range(2):
+            want = S1[tau * 10:(tau + 1) * 10, f * 4:(f + 1) * 4].sum(axis=(0, 1))
+            assert np.array_equal(S[tau, f], want)
+
+
+def test_correlate_flags_zero_their_baselines_only():
+    w = bs.build_workload("tiny")
+    flags = np.zeros(128, np.uint8)
+    flags[[3, 77]] = 1
+    S = oracle.correlate(w["volt"], 10, 1)[0, 0]
+    Sf = oracle.correlate(w["volt"], 10, 1, flags=flags)[0, 0]
+    for i in (0, 3, 50, 77, 127):
+        for j in range(i + 1):
+            b = _bidx(i, j)
+            if flags[i] or flags[j]:
+                assert not Sf[b].any()
+            else:
+                assert np.array_equal(Sf[b], S[b])
+
+
+def test_correlate_noise_power_statistics():
+    # E[S_ii^XX / K] = E|x|^2 for the quantised noise; with sigma = 2 per component the quantised
+    # variance per component is sigma^2 + 1/12 to within a few percent (Sheppard's correction).
+    sky = bs.Sky(lmn=np.zeros((0, 3)), power=np.zeros(0))
+    enu = bs.tile_positions(16, 100.0, 1)
+    v = bs.voltages(enu, np.array([150e6]), 4000, sky, seed=5)
+    S = oracle.correlate(v, 4000, 1)[0, 0]
+    autos = np.array([S[_bidx(i, i), 0, 0] for i in range(16)]) / 4000.0
+    assert abs(autos.mean() - 2 * (4 + 1 / 12)) < 0.1
+    cross = np.array([S[_bidx(i, j), 0] for i in range(16) for j in range(i)]) / 4000.0
+    assert np.abs(cross).max() < 6 * 8 / math.sqrt(4000)
+
+
+def test_visibility_is_one_float32_division():
+    S = np.array([[7, -3], [1, 1], [2 ** 20 + 1, -(2 ** 19)]], np.int64)
+    V = oracle.visibilities(S, 30)
+    assert V.dtype == np.complex64
+    assert np.float32(V[0].real) == np.float32(7) / np.float32(30)
+    assert np.float32(V[2].imag) == np.float32(-(2 ** 19)) / np.float32(30)
+
+
+# ----------------------------------------------------------------------------------------------
+# geometry (Sec. 5.2.3-5.2.4)
+# ----------------------------------------------------------------------------------------------
+
+def test_uvw_hand_computed():
+    enu = np.array([[0.0, 0.0, 0.0], [100.0, -50.0, 3.0], [10.0, 20.0, 0.0]])
+    nu = C_LIGHT            # wavelength 1 m => (u, v, w) = baseline in metres
+    u = oracle.uvw(enu, nu)
+    assert np.allclose(u[_bidx(1, 0)], [100.0, -50.0, 3.0], rtol=0, atol=1e-12)
+    assert np.allclose(u[_bidx(2, 1)], [-90.0, 70.0, -3.0], rtol=0, atol=1e-12)
+    assert np.all(u[[_bidx(i, i) for i in range(3)]] == 0.0)
+    u2 = oracle.uvw(enu, 2 * nu)
+    assert np.allclose(u2, 2 * u, rtol=0, atol=1e-12)
+
+
+def test_output_freqs_mean_of_fine_centres():
+    fine = bs.fine_frequencies([121])
+    out = oracle.output_freqs(fine, 4)
+    # group g of 4 covers fine channels 4g..4g+3, centre = f_cc - 640 kHz + (4g + 2) * 10 kHz
+    g = np.arange(32)
+    assert np.allclose(out, 121 * 1.28e6 - 640e3 + (4 * g + 2) * 10e3, rtol=0, atol=1e-6)
+
+
+def test_default_cell_puts_longest_baseline_in_outer_cell():
+    w = bs.build_workload("tiny")
+    enu, nu = w["enu"], 154.88e6
+    for n in (64, 256, 512):
+        du = oracle.default_cell(enu, nu, n)
+        iu, iv, keep = oracle.cells(oracle.uvw(enu, nu), du, n)
+        assert keep.all()
+        r = np.hypot(iu, iv)
+        assert max(np.abs(iu).max(), np.abs(iv).max()) <= n // 2 - 1
+        assert r.max() >= n // 2 - 2
+        # the longest baseline's |(u, v)| is exactly u_max = du * (N/2 - 1) up to rounding
+        uv = oracle.uvw(enu, nu)
+        assert math.isclose(np.hypot(uv[:, 0], uv[:, 1]).max(), du * (n // 2 - 1), rel_tol=1e-12)
+
+
+def test_cells_round_half_up_and_drop_outside():
+    uvw = np.array([[2.5, -2.5, 0], [127.4, 0, 0], [127.6, 0, 0], [-127.6, 3.49, 0], [0.49, -0.51, 0]])
+    iu, iv, keep = oracle.cells(uvw, 1.0, 256)
+    assert list(keep) == [1, 1, 0, 0, 1]
+    assert (iu[0], iv[0]) == (3, -2)
+    assert iu[1] == 127
+    assert (iu[4], iv[4]) == (0, -1)
+
+
+# ----------------------------------------------------------------------------------------------
+# gridding (Sec. 5.2.4)
+# ----------------------------------------------------------------------------------------------
+
+def _tiny_grid(n=64, pol=oracle.POL_I, autos=True, flags=None):
+    w = bs.build_workload("tiny")
+    S = oracle.correlate(w["volt"], 10, 1, flags=flags)[0, 0]
+    nu = 154.88e6
+    du = oracle.default_cell(w["enu"], nu, n, flags=flags)
+    iu, iv, keep = oracle.cells(oracle.uvw(w["enu"], nu), du, n)
+    G, W = oracle.grid(S, 128, 10, iu, iv, keep, n, pol=pol, autos=autos, flags=flags)
+    return S, G, W, (iu, iv, keep)
+
+
+def test_grid_is_hermitian():
+    _, G, _, _ = _tiny_grid()
+    n = G.shape[0]
+    idx = (-np.arange(n)) % n
+    assert np.array_equal(G[np.ix_(idx, idx)], np.conj(G))
+
+
+def test_grid_sum_and_weights():
+    S, G, W, (iu, iv, keep) = _tiny_grid()
+    nt, K = 128, 10
+    assert keep.all()
+    assert W == nt * nt                          # N_a(N_a - 1) cross + N_a autos, weight 1 each
+    I = (S[:, 0] + S[:, 3]) / (2.0 * K)          # Stokes I per baseline (re, im)
+    autos = np.array([_bidx(i, i) for i in range(nt)])
+    cross = np.setdiff1d(np.arange(len(S)), autos)
+    want = 2 * I[cross, 0].sum() + I[autos, 0].sum()
+    assert math.isclose(G.sum().real, want, rel_tol=1e-12)
+    assert abs(G.sum().imag) < 1e-9 * abs(want)
+    # without autos, W = N_a (N_a - 1) and the DC cell loses exactly the autos' sum
+    _, G2, W2, _ = _tiny_grid(autos=False)
+    assert W2 == nt * (nt - 1)
+    assert math.isclose(G[0, 0].real - G2[0, 0].real, I[autos, 0].sum(), rel_tol=1e-12)
+
+
+def test_grid_places_visibility_and_mirror_at_its_cell():
+    nt, n = 3, 16
+    S = np.zeros((6, 4, 2), np.int64)
+    S[_bidx(2, 0), 0] = [20, 6]      # XX
+    S[_bidx(2, 0), 3] = [4, 2]       # YY
+    iu = np.array([0, 0, 0, 3, 0, 0], np.int32)
+    iv = np.array([0, 0, 0, -5, 0, 0], np.int32)
+    keep = np.ones(6, np.uint8)
+    G, W = oracle.grid(S, nt, 2, iu, iv, keep, n, autos=False)
+    I = ((20 + 4) + 1j * (6 + 2)) / 4.0
+    assert G[(-5) % n, 3] == I
+    assert G[5, (-3) % n] == np.conj(I)
+    Gx, _ = oracle.grid(S, nt, 2, iu, iv, keep, n, pol=oracle.POL_XX, autos=False)
+    assert Gx[(-5) % n, 3] == (20 + 6j) / 2.0
+
+
+def test_grid_flags_change_weight_sum():
+    flags = np.zeros(128, np.uint8)
+    flags[:10] = 1
+    _, _, W, _ = _tiny_grid(flags=flags)
+    assert W == 118 * 118
+
+
+# ----------------------------------------------------------------------------------------------
+# transform and image (Eq. 4; Sec. 5.2.4)
+# ----------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [4, 8, 16])
+def test_fft_matches_direct_dft(n):
+    rng = np.random.default_rng(n)
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    a = oracle.ifft2(G)
+    d = oracle.idft2(G)
+    assert np.abs(a - d).max() <= 1e-12 * np.abs(d).max()
+
+
+def test_fft_matches_numpy_library():
+    rng = np.random.default_rng(3)
+    n = 128
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    a = oracle.ifft2(G)
+    ref = np.fft.ifft2(G) * n * n
+    assert np.abs(a - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_fft_parseval():
+    rng = np.random.default_rng(4)
+    n = 64
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    a = oracle.ifft2(G)
+    assert math.isclose((np.abs(a) ** 2).sum(), n * n * (np.abs(G) ** 2).sum(), rel_tol=1e-12)
+
+
+def test_fft_delta_and_single_cell_closed_forms():
+    n = 32
+    G = np.zeros((n, n), complex)
+    G[0, 0] = 2.5 - 1j
+    assert np.allclose(oracle.ifft2(G), 2.5 - 1j, rtol=0, atol=1e-13)
+    # a cell and its mirror: a[y][x] = 2 cos(2 pi (u0 x + v0 y) / n)
+    u0, v0 = 3, 5
+    G = np.zeros((n, n), complex)
+    G[v0, u0] = 1
+    G[-v0 % n, -u0 % n] = 1
+    y, x = np.mgrid[0:n, 0:n]
+    want = 2 * np.cos(2 * np.pi * (u0 * x + v0 * y) / n)
+    assert np.abs(oracle.ifft2(G) - want).max() < 1e-12
+
+
+def test_fft_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        oracle.ifft2(np.zeros((12, 12), complex))
+
+
+def test_image_shift_puts_phase_centre_in_middle_pixel():
+    n = 16
+    a = np.zeros((n, n), complex)
+    a[0, 0] = 8.0
+    a[0, 1] = 4.0                 # l > 0 neighbour -> x = N/2 + 1
+    a[n - 1, 0] = 2.0             # m < 0 neighbour -> y = N/2 - 1
+    img, mx = oracle.image(a, 2.0)
+    assert img[n // 2, n // 2] == 4.0
+    assert img[n // 2, n // 2 + 1] == 2.0
+    assert img[n // 2 - 1, n // 2] == 1.0
+    assert mx == 0.0
+
+
+# ----------------------------------------------------------------------------------------------
+# end to end
+# ----------------------------------------------------------------------------------------------
+
+def test_point_source_at_phase_centre_gives_flux_in_centre_pixel():
+    # identical voltages at every tile = a noiseless source at the phase centre: every visibility is
+    # |x|^2, so the centre pixel is exactly that flux and it is the image maximum
+    w = bs.build_workload("tiny")
+    v = bs.constant_voltages(10, 1, 128, 2, 1)
+    out = oracle.pipeline(v, w["enu"], w["freqs"], 10, 1, 64)
+    img = out["images"][0]
+    assert math.isclose(img[32, 32], 5.0, rel_tol=1e-12)
+    assert img.max() == img[32, 32]
+    assert out["max_im"][0] < 1e-12
+
+
+def test_off_centre_source_peaks_at_its_direction():
+    # A strong noiseless source at direction (l, m) drawn by the generator (sign convention of Eq. 3):
+    # the dirty image peaks at pixel (N/2 + l N du, N/2 + m N du), not at its mirror.
+    enu = bs.tile_positions(64, 1500.0, 11)
+    nu = 154.88e6
+    n = 128
+    du = oracle.default_cell(enu, nu, n)
+    fov = 1.0 / du                      # image spans l in [-fov/2, fov/2)
+    lm = np.array([0.23 * fov, -0.17 * fov])
+    sky = bs.Sky(lmn=np.array([[lm[0], lm[1], math.sqrt(1 - lm @ lm)]]), power=np.array([20.0]))
+    v = bs.voltages(enu, np.array([nu]), 40, sky, seed=9, sigma=0.0)
+    out = oracle.pipeline(v, enu, np.array([nu]), 40, 1, n)
+    img = out["images"][0]
+    y, x = np.unravel_index(np.argmax(img), img.shape)
+    assert abs(x - (n / 2 + lm[0] * n * du)) <= 1.0
+    assert abs(y - (n / 2 + lm[1] * n * du)) <= 1.0
+
+
+def test_noise_level_of_pure_noise_image():
+    # One polarisation: sigma_img = P_n / sqrt(2 N_cross K); Stokes I averages two independent
+    # polarisations, so its noise is smaller by sqrt(2).  P_n is the quantised noise power per sample.
+    enu = bs.tile_positions(64, 1500.0, 12)
+    sky = bs.Sky(lmn=np.zeros((0, 3)), power=np.zeros(0))
+    v = bs.voltages(enu, np.array([150e6]), 40, sky, seed=13)
+    p_n = 2 * (4 + 1 / 12)
+    xx = p_n / math.sqrt(2 * 64 * 63 / 2 * 40)
+    for pol, want in ((oracle.POL_XX, xx), (oracle.POL_I, xx / math.sqrt(2))):
+        out = oracle.pipeline(v, enu, np.array([150e6]), 40, 1, 128, autos=False, pol=pol)
+        img = out["images"][0]
+        assert 0.85 * want < img.std() < 1.15 * want, pol
+    assert math.isclose(bs.image_noise(2.0, 64, 40), 8 / math.sqrt(2 * 2016 * 40) / math.sqrt(2))
+
+
+def test_layout_sizes_match_paper_data_volume_table():
+    # Table "Data volumes" (Sec. 7): visibilities and images per second of data for the two test cases,
+    # reproduced by this layout (lower triangle with autos, 4 polarisations, complex64; float32 images).
+    with open(os.path.join(GOLDEN, "paper_data_volumes.json")) as f:
+        gold = json.load(f)
+    for case in gold["cases"]:
+        nt = case["n_tiles"]
+        B = nt * (nt + 1) // 2
+        vis = case["n_integrations"] * case["n_channels"] * B * 4 * 8
+        img = case["n_integrations"] * case["n_channels"] * case["n_pix"] ** 2 * 4 // case["images_averaged"]
+        assert abs(vis / 2 ** 20 - case["visibilities_MiB"]) / case["visibilities_MiB"] < 0.01, case["name"]
+        assert abs(img / 2 ** 20 - case["images_MiB"]) / case["images_MiB"] < 0.01, case["name"]
+
+
+def test_pipeline_matches_stepwise_functions():
+    w = bs.build_workload("tiny")
+    out = oracle.pipeline(w["volt"], w["enu"], w["freqs"], 10, 1, 64, want_grids=True)
+    S = oracle.correlate(w["volt"], 10, 1)[0, 0]
+    du = oracle.default_cell(w["enu"], 154.88e6, 64)
+    iu, iv, keep = oracle.cells(oracle.uvw(w["enu"], 154.88e6), du, 64)
+    G, W = oracle.grid(S, 128, 10, iu, iv, keep, 64)
+    assert np.array_equal(out["grids"][0], G)
+    img, _ = oracle.image(oracle.ifft2(G), W)
+    assert np.array_equal(out["images"][0], img)
