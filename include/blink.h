@@ -1,0 +1,187 @@
+/*
+ * blink.h - C ABI of the GB300 (sm_103a) dirty-imaging library: BLINK's data-parallel hot path
+ * (arXiv 2505.15204): 4-bit tile voltages -> correlation -> uv gridding -> batched 2D inverse FFT ->
+ * dirty images, on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers prefixed d_ are device memory owned by the caller (for example PyTorch tensors); pointers
+ *   prefixed h_ and the pointers inside the descriptor structs are host memory owned by the caller and
+ *   read only during the call.  The library keeps no pointer to caller memory after returning.
+ * - Calls are asynchronous and ordered on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *   default stream).  Argument errors are reported synchronously through the return value, and nothing
+ *   is launched.  Device-side errors (a failed index guard, a bounded wait that ran out) are recorded
+ *   in a per-context status word and reported by blink_sync().
+ * - No call aborts or throws across the ABI.  blink_last_error() returns the calling thread's last
+ *   error message.
+ * - The library allocates device memory only inside the context: per-configuration plans (cell maps,
+ *   gather lists) on first use, and workspace that grows to the largest request seen.  A repeated call
+ *   with the same configuration allocates nothing.
+ *
+ * Data layouts
+ * ------------
+ * voltages  uint8 [n_samples][fine_stride][n_tiles][2]: one byte per complex sample and polarisation
+ *           (last axis X, Y), re = low nibble, im = high nibble, both two's-complement in [-8, 7].
+ *           The channels of one call are n_fine consecutive channels of that axis; d_volt points at
+ *           the first of them in sample 0.
+ * baselines b = i(i+1)/2 + j for tiles i >= j (autocorrelations included); B = n_tiles(n_tiles+1)/2.
+ * images    id = tau * F + f for integration tau (T = n_samples / samples_per_int) and output channel
+ *           f (F = n_fine / chan_avg).
+ * vis       float [T][F][B][4][2]: complex64 per polarisation product XX, XY, YX, YY, V = S / K with
+ *           S the integer sum of x_i^p conj(x_j^q) and K = samples_per_int * chan_avg.
+ * grid      float [n_images][N][N/2 + 1][2]: the u >= 0 half of the Hermitian uv grid, row = v
+ *           (index mod N), column = u, DC at [0][0]; the u < 0 half is G(-u,-v) = conj G(u,v).
+ * image     float [n_images][N][N]: row y (direction cosine m), column x (l); pixel (N/2, N/2) is the
+ *           phase centre; l = (x - N/2) / (N du), m = (y - N/2) / (N du).
+ */
+#ifndef BLINK_H
+#define BLINK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BLINK_OK = 0,
+    BLINK_ERR_INVALID_ARG = 1,   /* a pointer, size or layout violates the rules of the call */
+    BLINK_ERR_UNSUPPORTED = 2,   /* valid request outside what this build implements (e.g. image side) */
+    BLINK_ERR_OOM = 3,           /* device allocation for a plan or workspace failed */
+    BLINK_ERR_CUDA = 4,          /* a CUDA runtime call failed; the message names it */
+    BLINK_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out (reported by blink_sync) */
+    BLINK_ERR_DEVICE = 6         /* a device-side index or size guard failed (reported by blink_sync) */
+} blink_status;
+
+enum { BLINK_POL_I = 0, BLINK_POL_XX = 1 };            /* imaged polarisation */
+enum { BLINK_CORR_FP32 = 0, BLINK_CORR_FP8 = 1 };      /* correlation arithmetic */
+enum { BLINK_PREC_FP32 = 0, BLINK_PREC_BF16 = 1 };     /* grid / FFT intermediate storage */
+enum { BLINK_MODE_BATCHED = 0, BLINK_MODE_PLAIN = 1 }; /* pipeline form */
+
+typedef struct blink_context blink_context;
+
+/* The array (Sec. 5.2.3-5.2.4: tile positions are the metadata the imager uses for (u, v, w)). */
+typedef struct {
+    int32_t n_tiles;            /* 1..512 */
+    const double* enu_m;        /* host [n_tiles][3]: East, North, Up in metres */
+    const uint8_t* flags;       /* host [n_tiles], non-zero = flagged (excluded); NULL = none flagged */
+} blink_array;
+
+/* The observation (Sec. 5.2.1-5.2.2 and the -t / -c options of the pipeline's command line). */
+typedef struct {
+    int32_t n_fine;             /* fine channels processed by the call */
+    int32_t fine_stride;        /* fine channels per sample in the voltage buffer; 0 means n_fine */
+    const double* fine_freq_hz; /* host [n_fine]: centre frequency of each processed fine channel */
+    int32_t chan_avg;           /* c: consecutive fine channels averaged into one output channel (-c) */
+    int32_t samples_per_int;    /* N_s: voltage samples per integration (-t / sample time) */
+    int32_t n_samples;          /* samples in the buffer; a multiple of samples_per_int */
+} blink_obs;
+
+/* Imaging parameters (Sec. 5.2.4 and the -n option). */
+typedef struct {
+    int32_t n_pix;              /* N: image and grid side, a power of two in [64, 2048] */
+    double cell_lambda;         /* uv cell du in wavelengths; <= 0 selects u_max / (N/2 - 1) */
+    int32_t pol;                /* BLINK_POL_I: (XX + YY) / 2; BLINK_POL_XX: XX only */
+    int32_t include_autos;      /* non-zero: autocorrelations gridded at (0, 0) with weight 1 */
+    int32_t precision;          /* BLINK_PREC_FP32, or BLINK_PREC_BF16 (bf16 grid/intermediate storage) */
+} blink_imaging;
+
+/* ---- context ---------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (which becomes current on the calling thread). */
+blink_status blink_create(int32_t device, blink_context** out);
+/* Free everything the context allocated.  Waits for its work to finish first.  NULL is a no-op. */
+void blink_destroy(blink_context* ctx);
+/* Message of the calling thread's last failed call ("" if none).  Valid until the next call. */
+const char* blink_last_error(void);
+const char* blink_status_name(blink_status status);
+/* Wait for `stream`, then report (and clear) the context's device-side status word. */
+blink_status blink_sync(blink_context* ctx, void* stream);
+/* B = n_tiles (n_tiles + 1) / 2. */
+int64_t blink_n_baselines(int32_t n_tiles);
+
+/* ---- the hot path, one stage per call ---------------------------------------------------------- */
+
+/*
+ * Baseline geometry (Sec. 5.2.3, geometric correction "implemented in the imaging library", and the
+ * (u, v, w) computation of Sec. 5.2.4), in FP64 on the GPU: for every output channel f (centre = mean of
+ * its chan_avg fine-channel centres) and baseline b, (u, v, w) = (r_i - r_j) * (nu_f / c) and the
+ * nearest uv cell (iu, iv) = floor((u, v) / du + 1/2).
+ *   d_cells  int32 [F][B]: (iu & 0xFFFF) | (iv << 16) for a gridded baseline, or 0x80008000 when the
+ *            baseline is flagged or falls outside |iu|, |iv| < N/2.
+ *   d_uvw    double [F][B][3] or NULL.
+ *   h_du     host double or NULL: receives the cell size used.
+ */
+blink_status blink_cells(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                         const blink_imaging* imaging, int32_t* d_cells, double* d_uvw, double* h_du,
+                         void* stream);
+
+/*
+ * Correlation (Eq. 2; Sec. 5.2.2): for every integration and output channel, the lower-triangular
+ * matrix of V_ij^pq = (1/K) sum x_i^p conj(x_j^q) over the N_s samples and c fine channels, as float
+ * [T][F][B][4][2].  Products of 4-bit integers are summed exactly (integers below 2^24), then divided
+ * by K once in IEEE FP32.  Flagged tiles' baselines are written as 0.
+ *   arith  BLINK_CORR_FP32: CUDA-core FP32; BLINK_CORR_FP8: tcgen05 tensor cores, e4m3 operands,
+ *          FP32 accumulation.  Both give identical bits.
+ */
+blink_status blink_correlate(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                             int32_t arith, const uint8_t* d_volt, float* d_vis, void* stream);
+
+/*
+ * Gridding (Sec. 5.2.4): natural weighting, nearest cell, no convolution kernel.  Images
+ * [first_image, first_image + n_images) of the visibility layout above are gridded; d_vis points at
+ * image first_image.  Each cross baseline adds I at its cell and conj(I) at the mirror cell, each
+ * autocorrelation adds I at (0, 0) (when include_autos), with I = (V_XX + V_YY) / 2 or V_XX.
+ *   d_grid    float [n_images][N][N/2 + 1][2] (half plane; the Nyquist column u = N/2 is written 0).
+ *   d_weight  float [n_images] or NULL: W, the sum of weights (2 per gridded cross baseline, 1 per auto).
+ * The sum over a cell is taken in a fixed order, so results are bitwise reproducible.
+ */
+blink_status blink_grid(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                        const blink_imaging* imaging, const float* d_vis, int32_t first_image,
+                        int32_t n_images, float* d_grid, float* d_weight, void* stream);
+
+/*
+ * Imaging (Eq. 4; Sec. 5.2.4): for each grid, the unnormalised inverse 2D transform
+ * a[y][x] = sum G[v][u] exp(+2 pi i (u x + v y) / N) of the Hermitian grid, divided by W and shifted so
+ * the phase centre is pixel (N/2, N/2).  The grid is real-valued in image space, so only Re a is formed
+ * (a complex-to-real transform of the half plane).
+ *   d_grid    float [n_images][N][N/2 + 1][2] as written by blink_grid.
+ *   d_weight  float [n_images]: W per image (entries <= 0 are treated as 1).
+ *   d_img     float [n_images][N][N].
+ */
+blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const float* d_grid,
+                         int32_t n_images, const float* d_weight, float* d_img, void* stream);
+
+/*
+ * The whole path (Sec. 5, Fig. "BLINK FRB search pipeline", imaging half): correlation -> gridding ->
+ * inverse FFT -> shifted, normalised dirty images for every integration and output channel of the call,
+ * d_img float [T * F][N][N] in image-id order.  Only the products the imaged polarisation needs are
+ * formed (XX and YY for Stokes I).
+ *   arith     correlation arithmetic as in blink_correlate.
+ *   mode      BLINK_MODE_BATCHED: images in waves through batched kernels (the fast form);
+ *             BLINK_MODE_PLAIN: one launch set per image with atomic gridding (the reference GPU form).
+ *   d_weight  float [T * F] or NULL: W per image.
+ * Images equal blink_image(blink_grid(blink_correlate(...))) up to FP32 rounding.
+ */
+blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                            const blink_imaging* imaging, int32_t arith, int32_t mode,
+                            const uint8_t* d_volt, float* d_img, float* d_weight, void* stream);
+
+/*
+ * blink_pipeline on host buffers: copies h_volt to device workspace, runs the batched path and copies
+ * the images back to h_img, all ordered on `stream`.  Page-locked host buffers make the copies
+ * asynchronous; the call returns after enqueueing (blink_sync waits).  `images_per_pass` (>= 1, 0 = all)
+ * bounds the device image buffer: the images come back in passes of at most that many.
+ *   h_volt  host uint8 as the voltage layout (fine_stride channels per sample).
+ *   h_img   host float [T * F][N][N].
+ */
+blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                 const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt,
+                                 float* h_img, int32_t images_per_pass, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLINK_H */

@@ -1,0 +1,229 @@
+"""Thin Python binding of the C ABI in ``include/blink.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device buffers are passed as torch CUDA
+tensors (or raw integer device pointers); descriptor structs are built from numpy arrays that this
+module keeps alive for the duration of the call.  A non-OK status raises :class:`BlinkError`.
+
+There is no fallback: if the compiled library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libblink.so")
+
+BLINK_OK = 0
+BLINK_ERR_INVALID_ARG = 1
+BLINK_ERR_UNSUPPORTED = 2
+BLINK_ERR_OOM = 3
+BLINK_ERR_CUDA = 4
+BLINK_ERR_TIMEOUT = 5
+BLINK_ERR_DEVICE = 6
+
+BLINK_POL_I = 0
+BLINK_POL_XX = 1
+BLINK_CORR_FP32 = 0
+BLINK_CORR_FP8 = 1
+BLINK_PREC_FP32 = 0
+BLINK_PREC_BF16 = 1
+BLINK_MODE_BATCHED = 0
+BLINK_MODE_PLAIN = 1
+
+# every entry point declared in include/blink.h
+ENTRY_POINTS = (
+    "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
+    "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
+)
+
+
+class BlinkError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class blink_array(C.Structure):
+    _fields_ = [("n_tiles", C.c_int32), ("enu_m", C.c_void_p), ("flags", C.c_void_p)]
+
+
+class blink_obs(C.Structure):
+    _fields_ = [("n_fine", C.c_int32), ("fine_stride", C.c_int32), ("fine_freq_hz", C.c_void_p),
+                ("chan_avg", C.c_int32), ("samples_per_int", C.c_int32), ("n_samples", C.c_int32)]
+
+
+class blink_imaging(C.Structure):
+    _fields_ = [("n_pix", C.c_int32), ("cell_lambda", C.c_double), ("pol", C.c_int32),
+                ("include_autos", C.c_int32), ("precision", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, S = C.c_void_p, C.c_int32, C.c_int64, C.c_int
+    sig = {
+        "blink_create": (S, [I32, C.POINTER(C.c_void_p)]),
+        "blink_destroy": (None, [P]),
+        "blink_last_error": (C.c_char_p, []),
+        "blink_status_name": (C.c_char_p, [S]),
+        "blink_sync": (S, [P, P]),
+        "blink_n_baselines": (I64, [I32]),
+        "blink_cells": (S, [P, P, P, P, P, P, P, P]),
+        "blink_correlate": (S, [P, P, P, I32, P, P, P]),
+        "blink_grid": (S, [P, P, P, P, P, I32, I32, P, P, P]),
+        "blink_image": (S, [P, P, P, I32, P, P, P]),
+        "blink_pipeline": (S, [P, P, P, P, I32, I32, P, P, P, P]),
+        "blink_pipeline_host": (S, [P, P, P, P, I32, P, P, I32, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor, numpy array or integer (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status: int, where: str):
+    if status != BLINK_OK:
+        raise BlinkError(status, where, _lib.blink_last_error().decode())
+
+
+# ---- descriptors ------------------------------------------------------------------------------------
+
+@dataclass
+class Array:
+    enu_m: np.ndarray
+    flags: np.ndarray | None = None
+
+    def c(self):
+        self._enu = np.ascontiguousarray(self.enu_m, dtype=np.float64)
+        self._flags = None if self.flags is None else np.ascontiguousarray(self.flags, dtype=np.uint8)
+        return blink_array(self._enu.shape[0], self._enu.ctypes.data,
+                           None if self._flags is None else self._flags.ctypes.data)
+
+
+@dataclass
+class Obs:
+    fine_freq_hz: np.ndarray
+    chan_avg: int
+    samples_per_int: int
+    n_samples: int
+    fine_stride: int = 0
+
+    def c(self):
+        self._f = np.ascontiguousarray(self.fine_freq_hz, dtype=np.float64)
+        return blink_obs(len(self._f), self.fine_stride, self._f.ctypes.data, self.chan_avg, self.samples_per_int,
+                         self.n_samples)
+
+
+@dataclass
+class Imaging:
+    n_pix: int
+    cell_lambda: float = 0.0
+    pol: int = BLINK_POL_I
+    include_autos: int = 1
+    precision: int = BLINK_PREC_FP32
+
+    def c(self):
+        return blink_imaging(self.n_pix, self.cell_lambda, self.pol, self.include_autos, self.precision)
+
+
+def _ref(x):
+    return None if x is None else C.byref(x)
+
+
+# ---- entry points -----------------------------------------------------------------------------------
+
+def blink_create(device: int = 0) -> int:
+    out = C.c_void_p()
+    _check(_lib.blink_create(device, C.byref(out)), "blink_create")
+    return out.value
+
+
+def blink_destroy(ctx) -> None:
+    _lib.blink_destroy(ctx)
+
+
+def blink_last_error() -> str:
+    return _lib.blink_last_error().decode()
+
+
+def blink_status_name(status: int) -> str:
+    return _lib.blink_status_name(status).decode()
+
+
+def blink_sync(ctx, stream=None) -> None:
+    _check(_lib.blink_sync(ctx, _stream(stream)), "blink_sync")
+
+
+def blink_n_baselines(n_tiles: int) -> int:
+    return int(_lib.blink_n_baselines(n_tiles))
+
+
+def blink_cells(ctx, array: Array, obs: Obs, imaging: Imaging, d_cells, d_uvw=None, stream=None) -> float:
+    du = C.c_double(0.0)
+    a, o, i = array.c(), obs.c(), imaging.c()
+    _check(_lib.blink_cells(ctx, C.byref(a), C.byref(o), C.byref(i), _ptr(d_cells), _ptr(d_uvw), C.byref(du),
+                            _stream(stream)), "blink_cells")
+    return du.value
+
+
+def blink_correlate(ctx, array: Array, obs: Obs, arith: int, d_volt, d_vis, stream=None) -> None:
+    a, o = array.c(), obs.c()
+    _check(_lib.blink_correlate(ctx, C.byref(a), C.byref(o), arith, _ptr(d_volt), _ptr(d_vis), _stream(stream)),
+           "blink_correlate")
+
+
+def blink_grid(ctx, array: Array, obs: Obs, imaging: Imaging, d_vis, first_image: int, n_images: int, d_grid,
+               d_weight=None, stream=None) -> None:
+    a, o, i = array.c(), obs.c(), imaging.c()
+    _check(_lib.blink_grid(ctx, C.byref(a), C.byref(o), C.byref(i), _ptr(d_vis), first_image, n_images,
+                           _ptr(d_grid), _ptr(d_weight), _stream(stream)), "blink_grid")
+
+
+def blink_image(ctx, imaging: Imaging, d_grid, n_images: int, d_weight, d_img, stream=None) -> None:
+    i = imaging.c()
+    _check(_lib.blink_image(ctx, C.byref(i), _ptr(d_grid), n_images, _ptr(d_weight), _ptr(d_img), _stream(stream)),
+           "blink_image")
+
+
+def blink_pipeline(ctx, array: Array, obs: Obs, imaging: Imaging, arith: int, mode: int, d_volt, d_img,
+                   d_weight=None, stream=None) -> None:
+    a, o, i = array.c(), obs.c(), imaging.c()
+    _check(_lib.blink_pipeline(ctx, C.byref(a), C.byref(o), C.byref(i), arith, mode, _ptr(d_volt), _ptr(d_img),
+                               _ptr(d_weight), _stream(stream)), "blink_pipeline")
+
+
+def blink_pipeline_host(ctx, array: Array, obs: Obs, imaging: Imaging, arith: int, h_volt, h_img,
+                        images_per_pass: int = 0, stream=None) -> None:
+    a, o, i = array.c(), obs.c(), imaging.c()
+    _check(_lib.blink_pipeline_host(ctx, C.byref(a), C.byref(o), C.byref(i), arith, _ptr(h_volt), _ptr(h_img),
+                                    images_per_pass, _stream(stream)), "blink_pipeline_host")

@@ -1,0 +1,697 @@
+// C ABI entry points, argument validation, plans and workspace.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "blink_internal.cuh"
+
+namespace blink {
+
+int col_block_width(int N);
+
+static thread_local std::string g_err;
+
+blink_status set_error(blink_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+blink_status cuda_error(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? BLINK_ERR_OOM : BLINK_ERR_CUDA;
+}
+
+namespace {
+
+constexpr double kSpeedOfLight = 299792458.0;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+struct Hasher {
+    uint64_t h = 1469598103934665603ull;
+    void bytes(const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; i++) {
+            h ^= c[i];
+            h *= 1099511628211ull;
+        }
+    }
+    template <typename T> void val(T v) { bytes(&v, sizeof(v)); }
+};
+
+blink_status check_array(const blink_array* a) {
+    if (!a) return set_error(BLINK_ERR_INVALID_ARG, "array descriptor is NULL");
+    if (a->n_tiles < 1 || a->n_tiles > 512) return set_error(BLINK_ERR_INVALID_ARG, "n_tiles must be in [1, 512]");
+    if (!a->enu_m) return set_error(BLINK_ERR_INVALID_ARG, "array.enu_m is NULL");
+    for (int i = 0; i < 3 * a->n_tiles; i++)
+        if (!std::isfinite(a->enu_m[i])) return set_error(BLINK_ERR_INVALID_ARG, "array.enu_m has a non-finite value");
+    return BLINK_OK;
+}
+
+blink_status check_obs(const blink_obs* o, bool need_freq) {
+    if (!o) return set_error(BLINK_ERR_INVALID_ARG, "obs descriptor is NULL");
+    if (o->n_fine < 1) return set_error(BLINK_ERR_INVALID_ARG, "obs.n_fine must be >= 1");
+    if (o->fine_stride != 0 && o->fine_stride < o->n_fine)
+        return set_error(BLINK_ERR_INVALID_ARG, "obs.fine_stride must be 0 or >= n_fine");
+    if (o->chan_avg < 1 || o->n_fine % o->chan_avg)
+        return set_error(BLINK_ERR_INVALID_ARG, "obs.chan_avg must be >= 1 and divide n_fine");
+    if (o->samples_per_int < 1) return set_error(BLINK_ERR_INVALID_ARG, "obs.samples_per_int must be >= 1");
+    if (o->n_samples < 0 || o->n_samples % o->samples_per_int)
+        return set_error(BLINK_ERR_INVALID_ARG, "obs.n_samples must be a non-negative multiple of samples_per_int");
+    if ((int64_t)o->samples_per_int * o->chan_avg > 131072)
+        return set_error(BLINK_ERR_UNSUPPORTED, "samples_per_int * chan_avg above 131072 (sums could leave the exact "
+                                                "FP32 integer range)");
+    if (need_freq) {
+        if (!o->fine_freq_hz) return set_error(BLINK_ERR_INVALID_ARG, "obs.fine_freq_hz is NULL");
+        for (int i = 0; i < o->n_fine; i++)
+            if (!(o->fine_freq_hz[i] > 0.0) || !std::isfinite(o->fine_freq_hz[i]))
+                return set_error(BLINK_ERR_INVALID_ARG, "obs.fine_freq_hz must be positive and finite");
+    }
+    return BLINK_OK;
+}
+
+blink_status check_imaging(const blink_imaging* im) {
+    if (!im) return set_error(BLINK_ERR_INVALID_ARG, "imaging descriptor is NULL");
+    const int n = im->n_pix;
+    if (n < 64 || n > 2048 || (n & (n - 1)))
+        return set_error(BLINK_ERR_UNSUPPORTED, "imaging.n_pix must be a power of two in [64, 2048]");
+    if (im->pol != BLINK_POL_I && im->pol != BLINK_POL_XX)
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.pol must be BLINK_POL_I or BLINK_POL_XX");
+    if (im->precision != BLINK_PREC_FP32 && im->precision != BLINK_PREC_BF16)
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.precision must be BLINK_PREC_FP32 or BLINK_PREC_BF16");
+    if (!std::isfinite(im->cell_lambda)) return set_error(BLINK_ERR_INVALID_ARG, "imaging.cell_lambda is not finite");
+    return BLINK_OK;
+}
+
+blink_status make_current(blink_context* ctx) {
+    if (!ctx) return set_error(BLINK_ERR_INVALID_ARG, "context is NULL");
+    int cur = -1;
+    BLINK_CUDA(cudaGetDevice(&cur));
+    if (cur != ctx->device) BLINK_CUDA(cudaSetDevice(ctx->device));
+    return BLINK_OK;
+}
+
+template <typename T>
+blink_status dmalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(plan)");
+    return BLINK_OK;
+}
+
+void free_plan(Plan* p) {
+    if (!p) return;
+    cudaFree(p->d_bl);
+    cudaFree(p->d_flags);
+    cudaFree(p->d_enu);
+    cudaFree(p->d_freq);
+    cudaFree(p->d_cells);
+    cudaFree(p->d_cell_off);
+    cudaFree(p->d_cell_key);
+    cudaFree(p->d_cell_beg);
+    cudaFree(p->d_contrib);
+    cudaFree(p->d_W);
+    cudaFree(p->d_tw);
+    delete p;
+}
+
+// Output-channel centre = mean of its fine-channel centres, summed in order (host FP64, no contraction).
+std::vector<double> output_freqs(const blink_obs* o) {
+    const int F = o->n_fine / o->chan_avg;
+    std::vector<double> out(F);
+    for (int f = 0; f < F; f++) {
+        double s = 0.0;
+        for (int k = 0; k < o->chan_avg; k++) s += o->fine_freq_hz[f * o->chan_avg + k];
+        out[f] = s / (double)o->chan_avg;
+    }
+    return out;
+}
+
+// Default uv cell: u_max / (N/2 - 1), u_max = longest unflagged projected baseline * nu_max / c.
+double default_cell(const blink_array* a, double nu_max, int n_pix) {
+    double dmax = 0.0;
+    for (int i = 0; i < a->n_tiles; i++)
+        for (int j = 0; j < i; j++) {
+            if (a->flags && (a->flags[i] || a->flags[j])) continue;
+            const double be = a->enu_m[i * 3 + 0] - a->enu_m[j * 3 + 0];
+            const double bn = a->enu_m[i * 3 + 1] - a->enu_m[j * 3 + 1];
+            const double d = std::sqrt(be * be + bn * bn);
+            if (d > dmax) dmax = d;
+        }
+    const double umax = dmax * (nu_max / kSpeedOfLight);
+    if (!(umax > 0.0)) return 1.0;
+    return umax / (double)(n_pix / 2 - 1);
+}
+
+// Cell-sorted gather list of the u >= 0 half plane for every output channel (see grid_fft.cu).
+blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std::vector<short2>& bl,
+                          const blink_array* a) {
+    const int N = p->N, cw = p->cw, half = N / 2;
+    const int64_t B = p->B;
+    const int64_t nkeys = (int64_t)half * N;                 // (cb, v, du) key space
+    std::vector<int> count(nkeys + 1);
+    std::vector<int> cell_off((size_t)p->F * (p->n_cb + 1));
+    std::vector<uint32_t> cell_key;
+    std::vector<int> cell_beg;
+    std::vector<uint32_t> contrib;
+    std::vector<uint32_t> ekey, eval;
+    cell_key.reserve((size_t)p->F * B);
+    cell_beg.reserve((size_t)p->F * B + 1);
+    contrib.reserve((size_t)p->F * (B + B / 16));
+    p->W.assign(p->F, 0.f);
+    int64_t dropped = 0;
+    for (int f = 0; f < p->F; f++) {
+        ekey.clear();
+        eval.clear();
+        int64_t w = 0;
+        auto key_of = [&](int u, int v) -> uint32_t {
+            const int cb = u / cw;
+            return (uint32_t)((int64_t)cb * N * cw + (int64_t)v * cw + (u - cb * cw));
+        };
+        for (int64_t b = 0; b < B; b++) {
+            const uint32_t c = cells[(size_t)f * B + b];
+            const int i = bl[b].x, j = bl[b].y;
+            if (i == j) {
+                if (c == CELL_NONE || !p->autos) continue;
+                ekey.push_back(key_of(0, 0));
+                eval.push_back((uint32_t)(b << 1));
+                w += 1;
+                continue;
+            }
+            if (c == CELL_NONE) {
+                if (!(a->flags && (a->flags[i] || a->flags[j]))) dropped++;
+                continue;
+            }
+            const int iu = (int16_t)(c & 0xFFFF), iv = (int16_t)(c >> 16);
+            const int vpos = ((iv % N) + N) % N, vneg = ((-iv % N) + N) % N;
+            if (iu > 0) {
+                ekey.push_back(key_of(iu, vpos));
+                eval.push_back((uint32_t)(b << 1));
+            } else if (iu < 0) {
+                ekey.push_back(key_of(-iu, vneg));
+                eval.push_back((uint32_t)((b << 1) | 1));
+            } else {
+                ekey.push_back(key_of(0, vpos));
+                eval.push_back((uint32_t)(b << 1));
+                ekey.push_back(key_of(0, vneg));
+                eval.push_back((uint32_t)((b << 1) | 1));
+            }
+            w += 2;
+        }
+        p->W[f] = (float)w;
+        // stable counting sort by key (contributions of a cell stay in baseline order)
+        std::fill(count.begin(), count.end(), 0);
+        for (uint32_t k : ekey) count[k + 1]++;
+        for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
+        std::vector<uint32_t> sorted_val(eval.size());
+        {
+            std::vector<int> cur(count.begin(), count.end() - 1);
+            for (size_t e = 0; e < ekey.size(); e++) sorted_val[cur[ekey[e]]++] = eval[e];
+        }
+        int cb_prev = -1;
+        const int64_t contrib_base = (int64_t)contrib.size();
+        for (int64_t k = 0; k < nkeys; k++) {
+            const int cb = (int)(k / ((int64_t)N * cw));
+            while (cb_prev < cb) cell_off[(size_t)f * (p->n_cb + 1) + (++cb_prev)] = (int)cell_key.size();
+            const int n = count[k + 1] - count[k];
+            if (!n) continue;
+            const int rem = (int)(k - (int64_t)cb * N * cw);
+            const int v = rem / cw, u = cb * cw + rem % cw;
+            cell_key.push_back(((uint32_t)v << 16) | (uint32_t)u);
+            cell_beg.push_back((int)(contrib_base + count[k]));
+        }
+        while (cb_prev < p->n_cb) cell_off[(size_t)f * (p->n_cb + 1) + (++cb_prev)] = (int)cell_key.size();
+        contrib.insert(contrib.end(), sorted_val.begin(), sorted_val.end());
+        if ((int64_t)contrib.size() > INT32_MAX / 2 || (int64_t)cell_key.size() > INT32_MAX / 2)
+            return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
+    }
+    cell_beg.push_back((int)contrib.size());
+    p->n_cells = (int64_t)cell_key.size();
+    p->n_contrib = (int64_t)contrib.size();
+    p->n_dropped = dropped;
+    BLINK_TRY(dmalloc(&p->d_cell_off, cell_off.size()));
+    BLINK_TRY(dmalloc(&p->d_cell_key, cell_key.size()));
+    BLINK_TRY(dmalloc(&p->d_cell_beg, cell_beg.size()));
+    BLINK_TRY(dmalloc(&p->d_contrib, contrib.size()));
+    BLINK_CUDA(cudaMemcpy(p->d_cell_off, cell_off.data(), cell_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!cell_key.empty())
+        BLINK_CUDA(cudaMemcpy(p->d_cell_key, cell_key.data(), cell_key.size() * 4, cudaMemcpyHostToDevice));
+    BLINK_CUDA(cudaMemcpy(p->d_cell_beg, cell_beg.data(), cell_beg.size() * 4, cudaMemcpyHostToDevice));
+    if (!contrib.empty())
+        BLINK_CUDA(cudaMemcpy(p->d_contrib, contrib.data(), contrib.size() * 4, cudaMemcpyHostToDevice));
+    return BLINK_OK;
+}
+
+}  // namespace
+
+blink_status workspace(blink_context* ctx, int slot, size_t bytes, void** out) {
+    Workspace& w = ctx->ws[slot];
+    if (w.bytes < bytes) {
+        if (w.ptr) {
+            BLINK_CUDA(cudaDeviceSynchronize());
+            cudaFree(w.ptr);
+            w.ptr = nullptr;
+            w.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&w.ptr, bytes);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(workspace)");
+        w.bytes = bytes;
+    }
+    *out = w.ptr;
+    return BLINK_OK;
+}
+
+// exp(+2 pi i k / N), k < N, rounded from FP64; one table per image side, made on first use.
+blink_status twiddles(blink_context* ctx, int N, float2** out) {
+    int lg = 0;
+    while ((1 << lg) < N) lg++;
+    if (lg >= 16 || (1 << lg) != N) return set_error(BLINK_ERR_UNSUPPORTED, "twiddle table side");
+    if (!ctx->tw[lg]) {
+        std::vector<float2> tw(N);
+        for (int k = 0; k < N; k++) {
+            const double ang = kTwoPi * (double)k / (double)N;
+            tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+        float2* d = nullptr;
+        BLINK_CUDA(cudaMalloc(&d, sizeof(float2) * N));
+        cudaError_t e = cudaMemcpy(d, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_error(e, "cudaMemcpy(twiddles)");
+        }
+        ctx->tw[lg] = d;
+    }
+    *out = ctx->tw[lg];
+    return BLINK_OK;
+}
+
+// Plans are keyed by every input they depend on.  Imaging-free plans (im == NULL) serve correlation.
+blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs* o, const blink_imaging* im,
+                      bool need_gather, cudaStream_t st, Plan** out) {
+    Hasher h;
+    h.val(a->n_tiles);
+    h.val(a->flags != nullptr);
+    if (a->flags) h.bytes(a->flags, a->n_tiles);
+    h.val(im != nullptr);
+    if (im) {
+        h.bytes(a->enu_m, sizeof(double) * 3 * a->n_tiles);
+        h.val(o->n_fine);
+        h.val(o->chan_avg);
+        h.bytes(o->fine_freq_hz, sizeof(double) * o->n_fine);
+        h.val(im->n_pix);
+        h.val(im->cell_lambda);
+        h.val(im->pol);
+        h.val(im->include_autos != 0);
+        h.val(need_gather);
+    } else {
+        h.val(o->n_fine / o->chan_avg);
+        h.val(o->chan_avg);
+    }
+    for (size_t k = 0; k < ctx->plans.size(); k++) {
+        Plan* p = ctx->plans[k];
+        if (p->key == h.h) {
+            ctx->plans.erase(ctx->plans.begin() + k);
+            ctx->plans.push_back(p);
+            *out = p;
+            return BLINK_OK;
+        }
+    }
+    if (ctx->plans.size() >= 8) {
+        BLINK_CUDA(cudaDeviceSynchronize());
+        free_plan(ctx->plans.front());
+        ctx->plans.erase(ctx->plans.begin());
+    }
+    Plan* p = new Plan();
+    p->key = h.h;
+    p->n_tiles = a->n_tiles;
+    p->n_fine = o->n_fine;
+    p->chan_avg = o->chan_avg;
+    p->F = o->n_fine / o->chan_avg;
+    p->B = blink_n_baselines(a->n_tiles);
+    std::vector<short2> bl(p->B);
+    for (int i = 0, b = 0; i < a->n_tiles; i++)
+        for (int j = 0; j <= i; j++, b++) bl[b] = make_short2((short)i, (short)j);
+    std::vector<uint8_t> flags(a->n_tiles, 0);
+    if (a->flags)
+        for (int i = 0; i < a->n_tiles; i++) flags[i] = a->flags[i] ? 1 : 0;
+    blink_status s = BLINK_OK;
+    auto fail = [&](blink_status e) {
+        free_plan(p);
+        return e;
+    };
+    if ((s = dmalloc(&p->d_bl, p->B)) != BLINK_OK) return fail(s);
+    if ((s = dmalloc(&p->d_flags, a->n_tiles)) != BLINK_OK) return fail(s);
+    cudaError_t e = cudaMemcpy(p->d_bl, bl.data(), bl.size() * sizeof(short2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(plan)"));
+    if (im) {
+        p->N = im->n_pix;
+        p->pol = im->pol;
+        p->autos = im->include_autos ? 1 : 0;
+        p->cw = col_block_width(p->N);
+        p->n_cb = (p->N / 2) / p->cw;
+        p->out_freq = output_freqs(o);
+        double numax = p->out_freq[0];
+        for (double f : p->out_freq) numax = std::max(numax, f);
+        p->du = im->cell_lambda > 0.0 ? im->cell_lambda : default_cell(a, numax, p->N);
+        if ((s = dmalloc(&p->d_enu, 3 * a->n_tiles)) != BLINK_OK) return fail(s);
+        if ((s = dmalloc(&p->d_freq, p->F)) != BLINK_OK) return fail(s);
+        if ((s = dmalloc(&p->d_cells, (size_t)p->F * p->B)) != BLINK_OK) return fail(s);
+        if ((s = dmalloc(&p->d_W, p->F)) != BLINK_OK) return fail(s);
+        if ((s = dmalloc(&p->d_tw, p->N)) != BLINK_OK) return fail(s);
+        std::vector<float2> tw(p->N);
+        for (int k = 0; k < p->N; k++) {
+            const double ang = kTwoPi * (double)k / (double)p->N;
+            tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+        e = cudaMemcpy(p->d_enu, a->enu_m, sizeof(double) * 3 * a->n_tiles, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_freq, p->out_freq.data(), sizeof(double) * p->F, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw.data(), sizeof(float2) * p->N, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(plan)"));
+        launch_cells(*p, st);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(cuda_error(e, "geometry kernel"));
+        if (need_gather) {
+            std::vector<uint32_t> cells((size_t)p->F * p->B);
+            e = cudaMemcpy(cells.data(), p->d_cells, cells.size() * 4, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(cells)"));
+            if ((s = build_gather(p, cells, bl, a)) != BLINK_OK) return fail(s);
+            e = cudaMemcpy(p->d_W, p->W.data(), sizeof(float) * p->F, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(W)"));
+        }
+    }
+    ctx->plans.push_back(p);
+    *out = p;
+    return BLINK_OK;
+}
+
+namespace {
+
+__global__ void k_fill_weights(float* out, const float* W, int F, int first, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = W[(first + i) % F];
+}
+
+int64_t sample_stride_bytes(const blink_obs* o, int n_tiles) {
+    const int stride = o->fine_stride ? o->fine_stride : o->n_fine;
+    return (int64_t)stride * n_tiles * 2;
+}
+
+// Batched path for images [id0, id1): waves of images through correlation (the imaged products only),
+// gather-gridding fused with the column FFT, and the row FFT.
+blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
+                         const uint8_t* d_volt, int64_t sstride, int id0, int id1, float* d_img, cudaStream_t st) {
+    const int N = p.N;
+    const int ldh = N / 2;
+    const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
+    const size_t per_img = (size_t)N * ldh * el;
+    int wave = (int)std::max<size_t>(1, ((size_t)64 << 20) / per_img);
+    wave = std::min(wave, std::max(1, id1 - id0));
+    void* vis = nullptr;
+    void* H = nullptr;
+    BLINK_TRY(workspace(ctx, 0, (size_t)wave * p.B * sizeof(float2), &vis));
+    BLINK_TRY(workspace(ctx, 1, (size_t)wave * per_img, &H));
+    const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
+    for (int w0 = id0; w0 < id1; w0 += wave) {
+        const int nw = std::min(wave, id1 - w0);
+        if (arith == BLINK_CORR_FP8)
+            BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B, ctx->d_status,
+                                      ctx->n_sm, st));
+        else
+            BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B, ctx->d_status,
+                                       st));
+        BLINK_TRY(launch_colpass_gather(p, prec, static_cast<float2*>(vis), p.B, w0, nw, H, ldh, ctx->d_status, st));
+        BLINK_TRY(launch_rowpass(N, prec, p.d_tw, H, ldh, 0, p.d_W, w0, p.F, nw, d_img + (int64_t)(w0 - id0) * N * N,
+                                 st));
+    }
+    return BLINK_OK;
+}
+
+}  // namespace
+
+}  // namespace blink
+
+using namespace blink;
+
+extern "C" {
+
+const char* blink_last_error(void) { return g_err.c_str(); }
+
+const char* blink_status_name(blink_status s) {
+    switch (s) {
+        case BLINK_OK: return "BLINK_OK";
+        case BLINK_ERR_INVALID_ARG: return "BLINK_ERR_INVALID_ARG";
+        case BLINK_ERR_UNSUPPORTED: return "BLINK_ERR_UNSUPPORTED";
+        case BLINK_ERR_OOM: return "BLINK_ERR_OOM";
+        case BLINK_ERR_CUDA: return "BLINK_ERR_CUDA";
+        case BLINK_ERR_TIMEOUT: return "BLINK_ERR_TIMEOUT";
+        case BLINK_ERR_DEVICE: return "BLINK_ERR_DEVICE";
+    }
+    return "BLINK_UNKNOWN";
+}
+
+int64_t blink_n_baselines(int32_t n_tiles) { return n_tiles < 0 ? 0 : (int64_t)n_tiles * (n_tiles + 1) / 2; }
+
+blink_status blink_create(int32_t device, blink_context** out) {
+    if (!out) return set_error(BLINK_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    BLINK_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return set_error(BLINK_ERR_INVALID_ARG, "no such CUDA device");
+    BLINK_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    BLINK_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10)
+        return set_error(BLINK_ERR_UNSUPPORTED, "this library is built for sm_103a (Blackwell) devices");
+    blink_context* ctx = new blink_context();
+    ctx->device = device;
+    ctx->n_sm = prop.multiProcessorCount;
+    cudaError_t e = cudaMalloc(&ctx->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_error(e, "cudaMalloc(status)");
+    }
+    *out = ctx;
+    return BLINK_OK;
+}
+
+void blink_destroy(blink_context* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    for (Plan* p : ctx->plans) free_plan(p);
+    for (auto& w : ctx->ws) cudaFree(w.ptr);
+    for (float2* t : ctx->tw) cudaFree(t);
+    cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+blink_status blink_sync(blink_context* ctx, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BLINK_CUDA(cudaStreamSynchronize(st));
+    int status = 0;
+    BLINK_CUDA(cudaMemcpy(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        BLINK_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        if (status & DEV_ERR_TIMEOUT) return set_error(BLINK_ERR_TIMEOUT, "a bounded device-side wait ran out");
+        return set_error(BLINK_ERR_DEVICE, "a device-side index guard failed");
+    }
+    return BLINK_OK;
+}
+
+blink_status blink_cells(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                         const blink_imaging* imaging, int32_t* d_cells, double* d_uvw, double* h_du, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, true));
+    BLINK_TRY(check_imaging(imaging));
+    if (!d_cells) return set_error(BLINK_ERR_INVALID_ARG, "d_cells is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan* p = nullptr;
+    BLINK_TRY(get_plan(ctx, array, obs, imaging, false, st, &p));
+    Plan q = *p;                   // same geometry inputs, caller's output buffers
+    q.d_cells = reinterpret_cast<uint32_t*>(d_cells);
+    q.d_uvw = d_uvw;
+    launch_cells(q, st);
+    BLINK_CUDA(cudaGetLastError());
+    if (h_du) *h_du = p->du;
+    return BLINK_OK;
+}
+
+blink_status blink_correlate(blink_context* ctx, const blink_array* array, const blink_obs* obs, int32_t arith,
+                             const uint8_t* d_volt, float* d_vis, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, false));
+    if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
+        return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
+    if (!d_volt || !d_vis) return set_error(BLINK_ERR_INVALID_ARG, "d_volt or d_vis is NULL");
+    if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_vis & 15))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_vis 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan* p = nullptr;
+    BLINK_TRY(get_plan(ctx, array, obs, nullptr, false, st, &p));
+    const int T = obs->n_samples / obs->samples_per_int;
+    const int n_items = T * p->F;
+    if (n_items == 0) return BLINK_OK;
+    const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
+    if (arith == BLINK_CORR_FP8)
+        return launch_corr_fp8(CORR_OUT_VIS4, d_volt, ss, *p, obs->samples_per_int, 0, n_items, d_vis, p->B * 8,
+                               ctx->d_status, ctx->n_sm, st);
+    return launch_corr_fp32(CORR_OUT_VIS4, d_volt, ss, *p, obs->samples_per_int, 0, n_items, d_vis, p->B * 8,
+                            ctx->d_status, st);
+}
+
+blink_status blink_grid(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                        const blink_imaging* imaging, const float* d_vis, int32_t first_image, int32_t n_images,
+                        float* d_grid, float* d_weight, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, true));
+    BLINK_TRY(check_imaging(imaging));
+    if (!d_vis || !d_grid) return set_error(BLINK_ERR_INVALID_ARG, "d_vis or d_grid is NULL");
+    if (first_image < 0 || n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "negative image range");
+    if (((uintptr_t)d_vis & 7) || ((uintptr_t)d_grid & 7))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_vis and d_grid must be 8-byte aligned");
+    const int64_t total = (int64_t)(obs->n_samples / obs->samples_per_int) * (obs->n_fine / obs->chan_avg);
+    if ((int64_t)first_image + n_images > total)
+        return set_error(BLINK_ERR_INVALID_ARG, "image range beyond the observation's T * F images");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan* p = nullptr;
+    BLINK_TRY(get_plan(ctx, array, obs, imaging, true, st, &p));
+    if (n_images == 0) return BLINK_OK;
+    BLINK_TRY(launch_grid_gather(*p, d_vis, first_image, n_images, d_grid, ctx->d_status, st));
+    if (d_weight) {
+        k_fill_weights<<<(n_images + 255) / 256, 256, 0, st>>>(d_weight, p->d_W, p->F, first_image, n_images);
+        BLINK_CUDA(cudaGetLastError());
+    }
+    return BLINK_OK;
+}
+
+blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const float* d_grid, int32_t n_images,
+                         const float* d_weight, float* d_img, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    BLINK_TRY(check_imaging(imaging));
+    if (!d_grid || !d_weight || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_grid, d_weight or d_img is NULL");
+    if (n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "n_images < 0");
+    if (((uintptr_t)d_grid & 7) || ((uintptr_t)d_img & 7))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_grid and d_img must be 8-byte aligned");
+    if (n_images == 0) return BLINK_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int N = imaging->n_pix, prec = imaging->precision;
+    const int cw = col_block_width(N);
+    const int ldh = N / 2 + cw;                 // room for the Nyquist column u = N/2
+    float2* tw = nullptr;
+    BLINK_TRY(twiddles(ctx, N, &tw));
+    const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
+    const size_t per_img = (size_t)N * ldh * el;
+    const int wave = (int)std::min<size_t>((size_t)n_images, std::max<size_t>(1, ((size_t)64 << 20) / per_img));
+    void* H = nullptr;
+    BLINK_TRY(workspace(ctx, 1, (size_t)wave * per_img, &H));
+    for (int w0 = 0; w0 < n_images; w0 += wave) {
+        const int nw = std::min(wave, n_images - w0);
+        BLINK_TRY(launch_colpass_grid(N, prec, tw,
+                                      reinterpret_cast<const float2*>(d_grid) + (int64_t)w0 * N * (N / 2 + 1), nw, H,
+                                      ldh, st));
+        BLINK_TRY(launch_rowpass(N, prec, tw, H, ldh, 1, d_weight, w0, n_images, nw,
+                                 d_img + (int64_t)w0 * N * N, st));
+    }
+    return BLINK_OK;
+}
+
+blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                            const blink_imaging* imaging, int32_t arith, int32_t mode, const uint8_t* d_volt,
+                            float* d_img, float* d_weight, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, true));
+    BLINK_TRY(check_imaging(imaging));
+    if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
+        return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
+    if (mode != BLINK_MODE_BATCHED && mode != BLINK_MODE_PLAIN)
+        return set_error(BLINK_ERR_INVALID_ARG, "mode must be BLINK_MODE_BATCHED or BLINK_MODE_PLAIN");
+    if (!d_volt || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_volt or d_img is NULL");
+    if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_img & 7))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_img 8-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan* p = nullptr;
+    BLINK_TRY(get_plan(ctx, array, obs, imaging, true, st, &p));
+    const int T = obs->n_samples / obs->samples_per_int;
+    const int n_img = T * p->F;
+    if (n_img == 0) return BLINK_OK;
+    const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
+    const int N = p->N;
+    if (mode == BLINK_MODE_BATCHED) {
+        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, d_volt, ss, 0, n_img, d_img, st));
+    } else {
+        const int cw = p->cw, ldh = N / 2 + cw;
+        const size_t el = imaging->precision == BLINK_PREC_BF16 ? 4 : 8;
+        void *vis = nullptr, *H = nullptr, *grid = nullptr;
+        BLINK_TRY(workspace(ctx, 0, (size_t)p->B * sizeof(float2), &vis));
+        BLINK_TRY(workspace(ctx, 1, (size_t)N * ldh * el, &H));
+        BLINK_TRY(workspace(ctx, 2, (size_t)N * (N / 2 + 1) * sizeof(float2), &grid));
+        const int kind = p->pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
+        for (int id = 0; id < n_img; id++) {
+            if (arith == BLINK_CORR_FP8)
+                BLINK_TRY(launch_corr_fp8(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B, ctx->d_status,
+                                          ctx->n_sm, st));
+            else
+                BLINK_TRY(launch_corr_fp32(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B,
+                                           ctx->d_status, st));
+            BLINK_CUDA(cudaMemsetAsync(grid, 0, (size_t)N * (N / 2 + 1) * sizeof(float2), st));
+            BLINK_TRY(launch_grid_atomic(*p, static_cast<float2*>(vis), id, static_cast<float2*>(grid), st));
+            BLINK_TRY(launch_colpass_grid(N, imaging->precision, p->d_tw, static_cast<float2*>(grid), 1, H, ldh, st));
+            BLINK_TRY(launch_rowpass(N, imaging->precision, p->d_tw, H, ldh, 0, p->d_W, id, p->F, 1,
+                                     d_img + (int64_t)id * N * N, st));
+        }
+    }
+    if (d_weight) {
+        k_fill_weights<<<(n_img + 255) / 256, 256, 0, st>>>(d_weight, p->d_W, p->F, 0, n_img);
+        BLINK_CUDA(cudaGetLastError());
+    }
+    return BLINK_OK;
+}
+
+blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                 const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt, float* h_img,
+                                 int32_t images_per_pass, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, true));
+    BLINK_TRY(check_imaging(imaging));
+    if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
+        return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
+    if (!h_volt || !h_img) return set_error(BLINK_ERR_INVALID_ARG, "h_volt or h_img is NULL");
+    if (images_per_pass < 0) return set_error(BLINK_ERR_INVALID_ARG, "images_per_pass < 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Plan* p = nullptr;
+    BLINK_TRY(get_plan(ctx, array, obs, imaging, true, st, &p));
+    const int T = obs->n_samples / obs->samples_per_int;
+    const int n_img = T * p->F;
+    if (n_img == 0) return BLINK_OK;
+    const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
+    const size_t vbytes = (size_t)obs->n_samples * ss;
+    const int per = images_per_pass > 0 ? std::min(images_per_pass, n_img) : n_img;
+    const int N = p->N;
+    void* dv = nullptr;
+    void* di = nullptr;
+    BLINK_TRY(workspace(ctx, 2, vbytes, &dv));
+    BLINK_TRY(workspace(ctx, 3, (size_t)per * N * N * sizeof(float), &di));
+    BLINK_CUDA(cudaMemcpyAsync(dv, h_volt, vbytes, cudaMemcpyHostToDevice, st));
+    for (int i0 = 0; i0 < n_img; i0 += per) {
+        const int n = std::min(per, n_img - i0);
+        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, static_cast<uint8_t*>(dv), ss, i0, i0 + n,
+                              static_cast<float*>(di), st));
+        BLINK_CUDA(cudaMemcpyAsync(h_img + (int64_t)i0 * N * N, di, (size_t)n * N * N * sizeof(float),
+                                   cudaMemcpyDeviceToHost, st));
+    }
+    return BLINK_OK;
+}
+
+}  // extern "C"

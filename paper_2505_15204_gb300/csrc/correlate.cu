@@ -1,0 +1,139 @@
+// Correlation on CUDA cores (Eq. 2; Sec. 5.2.2), the plain FP32 form.
+//
+// One CTA per (integration x output channel, block of baselines).  The CTA stages K-chunks of the
+// item's voltages in shared memory, unpacked to float4 (X re, X im, Y re, Y im) per tile, and each
+// thread accumulates the four polarisation products of BPT baselines.  All values are integers below
+// 2^24, so the FP32 sums are exact and independent of the summation order.
+#include "blink_internal.cuh"
+
+namespace blink {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBpt = 2;                               // baselines per thread
+constexpr int kStageFloat4 = 3072;                    // 48 KiB of staged samples
+
+__device__ __forceinline__ float nib_lo(unsigned b) { return (float)((int)(b << 28) >> 28); }
+__device__ __forceinline__ float nib_hi(unsigned b) { return (float)((int)(b << 24) >> 28); }
+
+template <int OUT>
+__global__ void __launch_bounds__(kThreads)
+k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles, int ns, int c, int F,
+            int first_item, const short2* __restrict__ bl, int64_t B, const uint8_t* __restrict__ flags,
+            void* __restrict__ out, int64_t out_item_stride, int kc) {
+    extern __shared__ float4 xs[];                    // [kc][n_tiles]
+    const int item = first_item + blockIdx.y;
+    const int tau = item / F, f = item - (item / F) * F;
+    const int K = ns * c;
+    const int tid = threadIdx.x;
+
+    int bi[kBpt], bj[kBpt];
+    bool act[kBpt];
+    float acc[kBpt][8];
+#pragma unroll
+    for (int m = 0; m < kBpt; m++) {
+        const int64_t b = (int64_t)blockIdx.x * kThreads * kBpt + m * kThreads + tid;
+        act[m] = b < B;
+        bi[m] = 0;
+        bj[m] = 0;
+        if (act[m]) {
+            const short2 ij = bl[b];
+            bi[m] = ij.x;
+            bj[m] = ij.y;
+            act[m] = !flags[ij.x] && !flags[ij.y];
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[m][q] = 0.f;
+    }
+
+    for (int k0 = 0; k0 < K; k0 += kc) {
+        const int kn = min(kc, K - k0);
+        for (int e = tid; e < kn * n_tiles; e += kThreads) {
+            const int kk = e / n_tiles, a = e - (e / n_tiles) * n_tiles;
+            const int k = k0 + kk;
+            const int s = tau * ns + k / c, ch = f * c + k % c;
+            const unsigned two = *reinterpret_cast<const uint16_t*>(volt + s * sample_stride +
+                                                                    ((int64_t)ch * n_tiles + a) * 2);
+            xs[kk * n_tiles + a] = make_float4(nib_lo(two & 0xFF), nib_hi(two & 0xFF), nib_lo(two >> 8),
+                                               nib_hi(two >> 8));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < kBpt; m++) {
+            if (!act[m]) continue;
+            const float4* pi = xs + bi[m];
+            const float4* pj = xs + bj[m];
+            for (int kk = 0; kk < kn; kk++) {
+                const float4 a = pi[kk * n_tiles], b = pj[kk * n_tiles];
+                // (ar + i ai) conj(br + i bi) = (ar br + ai bi) + i (ai br - ar bi)
+                acc[m][0] += a.x * b.x + a.y * b.y;           // XX
+                acc[m][1] += a.y * b.x - a.x * b.y;
+                acc[m][6] += a.z * b.z + a.w * b.w;           // YY
+                acc[m][7] += a.w * b.z - a.z * b.w;
+                if (OUT == CORR_OUT_VIS4) {
+                    acc[m][2] += a.x * b.z + a.y * b.w;       // XY
+                    acc[m][3] += a.y * b.z - a.x * b.w;
+                    acc[m][4] += a.z * b.x + a.w * b.y;       // YX
+                    acc[m][5] += a.w * b.x - a.z * b.y;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    const float fk = (float)K;
+#pragma unroll
+    for (int m = 0; m < kBpt; m++) {
+        const int64_t b = (int64_t)blockIdx.x * kThreads * kBpt + m * kThreads + tid;
+        if (b >= B) continue;
+        if (OUT == CORR_OUT_VIS4) {
+            float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + (int64_t)blockIdx.y * out_item_stride +
+                                                  b * 8);
+            float r[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) r[q] = __fdiv_rn(acc[m][q], fk);
+            o[0] = make_float4(r[0], r[1], r[2], r[3]);
+            o[1] = make_float4(r[4], r[5], r[6], r[7]);
+        } else {
+            float2* o = static_cast<float2*>(out) + (int64_t)blockIdx.y * out_item_stride + b;
+            if (OUT == CORR_OUT_STOKES_I)
+                *o = make_float2(__fdiv_rn(acc[m][0] + acc[m][6], 2.f * fk), __fdiv_rn(acc[m][1] + acc[m][7], 2.f * fk));
+            else
+                *o = make_float2(__fdiv_rn(acc[m][0], fk), __fdiv_rn(acc[m][1], fk));
+        }
+    }
+}
+
+}  // namespace
+
+blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
+                              int first_item, int n_items, void* out, int64_t out_item_stride, int*,
+                              cudaStream_t st) {
+    const int kc = std::max(1, std::min(ns * p.chan_avg, kStageFloat4 / p.n_tiles));
+    const size_t smem = (size_t)kc * p.n_tiles * sizeof(float4);
+    const unsigned gx = (unsigned)((p.B + kThreads * kBpt - 1) / (kThreads * kBpt));
+    for (int i0 = 0; i0 < n_items; i0 += 65535) {
+        const int n = std::min(65535, n_items - i0);
+        dim3 grid(gx, n);
+        char* o = static_cast<char*>(out) + (int64_t)i0 * out_item_stride *
+                                                (out_kind == CORR_OUT_VIS4 ? sizeof(float) : sizeof(float2));
+        switch (out_kind) {
+            case CORR_OUT_VIS4:
+                k_corr_fp32<CORR_OUT_VIS4><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
+                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc);
+                break;
+            case CORR_OUT_STOKES_I:
+                k_corr_fp32<CORR_OUT_STOKES_I><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
+                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc);
+                break;
+            default:
+                k_corr_fp32<CORR_OUT_XX><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
+                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc);
+        }
+    }
+    BLINK_CUDA(cudaGetLastError());
+    return BLINK_OK;
+}
+
+}  // namespace blink

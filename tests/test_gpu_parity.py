@@ -1,0 +1,329 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Correlation and cell maps must match bit for bit; grids and images within the FP32 tolerances below
+(images: relative RMS <= 1e-4 against the FP64 oracle, the precision gate of the method's mixed-precision
+form).  Sizes span several tiles and waves and include ragged ends.
+"""
+import numpy as np
+import pytest
+
+import blinksynth as bs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+IMG_RTOL = 1e-4          # relative RMS, FP32 imaging against the FP64 oracle
+GRID_RTOL = 2e-6         # max |diff| / max |G|, FP32 gridding sums of FP32 visibilities
+
+
+def rel_rms(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2505_15204_gb300 import blink
+    return blink
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.blink_create(0)
+    yield c
+    B.blink_destroy(c)
+
+
+def _case(name, n_samples=None, fine=None, flags=False):
+    w = bs.build_workload(name, n_samples=n_samples)
+    volt, freqs = w["volt"], w["freqs"]
+    if fine is not None:
+        volt = np.ascontiguousarray(volt[:, :fine])
+        freqs = freqs[:fine]
+    fl = None
+    if flags:
+        fl = bs.tile_flags(w["enu"].shape[0], 0.15, w["workload"].seed, 99)
+        fl[3] = 1
+    return w, volt, freqs, fl
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ---------------------------------------------------------------------------------------------------
+# correlation
+# ---------------------------------------------------------------------------------------------------
+
+CORR_CASES = [
+    ("tiny", None, None, 1, False),
+    ("precision", None, None, 1, False),
+    ("coarse", 30, 8, 4, False),        # 3 integrations x 2 output channels of 4 fine channels
+    ("uneven", 20, 6, 2, True),         # flagged tiles
+]
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp32", "fp8"])
+@pytest.mark.parametrize("case", CORR_CASES, ids=[c[0] for c in CORR_CASES])
+def test_correlate_bit_exact(B, ctx, case, arith):
+    name, ns_total, fine, c, flags = case
+    w, volt, freqs, fl = _case(name, ns_total, fine, flags)
+    S = oracle.correlate(volt, 10, c, flags=fl)
+    want = oracle.visibilities(S, 10 * c)
+    T, F = S.shape[:2]
+    out = torch.full(S.shape, float("nan"), dtype=torch.float32, device="cuda")
+    B.blink_correlate(ctx, B.Array(w["enu"], fl), B.Obs(freqs, c, 10, volt.shape[0]), arith, dev(volt), out)
+    B.blink_sync(ctx)
+    got = out.cpu().numpy()
+    assert np.array_equal(got[..., 0], want.real.astype(np.float32))
+    assert np.array_equal(got[..., 1], want.imag.astype(np.float32))
+
+
+def test_correlate_sub_band_with_fine_stride(B, ctx):
+    # channels 4..11 of a 16-channel buffer: d_volt offset + fine_stride
+    w, volt, freqs, _ = _case("coarse", 20, 16)
+    S = oracle.correlate(np.ascontiguousarray(volt[:, 4:12]), 10, 2)
+    want = oracle.visibilities(S, 20)
+    d = dev(volt)
+    out = torch.empty(S.shape, dtype=torch.float32, device="cuda")
+    off = 4 * 128 * 2
+    B.blink_correlate(ctx, B.Array(w["enu"]), B.Obs(freqs[4:12], 2, 10, 20, fine_stride=16), 0,
+                      d.data_ptr() + off, out)
+    B.blink_sync(ctx)
+    got = out.cpu().numpy()
+    assert np.array_equal(got[..., 0], want.real.astype(np.float32))
+
+
+# ---------------------------------------------------------------------------------------------------
+# geometry
+# ---------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,n_pix,fine,c,flags", [("tiny", 256, None, 1, False), ("precision", 512, None, 1, False),
+                                                     ("coarse", 512, 128, 4, False), ("uneven", 1024, 8, 1, True)])
+def test_cells_and_uvw_bit_exact(B, ctx, name, n_pix, fine, c, flags):
+    w, volt, freqs, fl = _case(name, 10, fine, flags)
+    arr = B.Array(w["enu"], fl)
+    F = len(freqs) // c
+    nb = B.blink_n_baselines(w["enu"].shape[0])
+    cells = torch.empty((F, nb), dtype=torch.int32, device="cuda")
+    uvw = torch.empty((F, nb, 3), dtype=torch.float64, device="cuda")
+    du = B.blink_cells(ctx, arr, B.Obs(freqs, c, 10, 10), B.Imaging(n_pix), cells, uvw)
+    B.blink_sync(ctx)
+    fout = oracle.output_freqs(freqs, c)
+    du_ref = oracle.default_cell(w["enu"], fout.max(), n_pix, flags=fl)
+    assert du == du_ref
+    got_c = cells.cpu().numpy().view(np.uint32)
+    got_uvw = uvw.cpu().numpy()
+    for f in range(F):
+        uv = oracle.uvw(w["enu"], fout[f])
+        assert np.array_equal(got_uvw[f], uv)
+        iu, iv, keep = oracle.cells(uv, du_ref, n_pix)
+        if fl is not None:
+            ij = np.array([(i, j) for i in range(len(fl)) for j in range(i + 1)])
+            keep = keep & (fl[ij[:, 0]] == 0) & (fl[ij[:, 1]] == 0)
+        want = np.where(keep.astype(bool), (iu.astype(np.uint32) & 0xFFFF) | (iv.astype(np.uint32) << 16),
+                        np.uint32(0x80008000))
+        assert np.array_equal(got_c[f], want)
+
+
+# ---------------------------------------------------------------------------------------------------
+# gridding and imaging stages
+# ---------------------------------------------------------------------------------------------------
+
+def _half(G):
+    n = G.shape[0]
+    return G[:, : n // 2 + 1]
+
+
+@pytest.mark.parametrize("pol", [0, 1], ids=["stokesI", "xx"])
+def test_grid_matches_oracle(B, ctx, pol):
+    w, volt, freqs, fl = _case("uneven", 20, 2, True)
+    n_pix = 256
+    arr, obs = B.Array(w["enu"], fl), B.Obs(freqs, 1, 10, 20)
+    im = B.Imaging(n_pix, pol=pol)
+    S = oracle.correlate(volt, 10, 1, flags=fl)
+    vis = torch.empty(S.shape, dtype=torch.float32, device="cuda")
+    B.blink_correlate(ctx, arr, obs, 0, dev(volt), vis)
+    n_img = S.shape[0] * S.shape[1]
+    grid = torch.empty((n_img, n_pix, n_pix // 2 + 1, 2), dtype=torch.float32, device="cuda")
+    wts = torch.empty(n_img, dtype=torch.float32, device="cuda")
+    B.blink_grid(ctx, arr, obs, im, vis, 0, n_img, grid, wts)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n_pix, flags=fl, pol=pol, want_grids=True)
+    g = grid.cpu().numpy()
+    g = g[..., 0] + 1j * g[..., 1]
+    for q in range(n_img):
+        h = _half(ref["grids"][q])
+        assert np.abs(g[q] - h).max() <= GRID_RTOL * np.abs(h).max(), q
+        assert wts[q].item() == ref["W"][q]
+
+
+def test_image_stage_on_oracle_grid(B, ctx):
+    w, volt, freqs, _ = _case("precision")
+    for n_pix in (64, 256, 512, 1024, 2048):
+        ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n_pix, want_grids=True)
+        h = _half(ref["grids"][0])
+        g = np.stack([h.real, h.imag], axis=-1).astype(np.float32)[None]
+        img = torch.empty((1, n_pix, n_pix), dtype=torch.float32, device="cuda")
+        wt = torch.tensor([ref["W"][0]], dtype=torch.float32, device="cuda")
+        B.blink_image(ctx, B.Imaging(n_pix), dev(g), 1, wt, img)
+        B.blink_sync(ctx)
+        err = rel_rms(img[0].cpu().numpy(), ref["images"][0])
+        assert err <= 1e-5, (n_pix, err)
+
+
+def test_image_stage_nyquist_column(B, ctx):
+    # a grid whose only non-zero entries sit in the Nyquist column u = N/2 (allowed by the ABI layout)
+    n = 64
+    G = np.zeros((n, n), complex)
+    G[5, n // 2] = 1 + 2j
+    G[-5 % n, n // 2] = 1 - 2j
+    a = np.fft.ifft2(G) * n * n
+    want = np.roll(a.real, (n // 2, n // 2), axis=(0, 1))
+    g = np.stack([G[:, : n // 2 + 1].real, G[:, : n // 2 + 1].imag], -1).astype(np.float32)[None]
+    img = torch.empty((1, n, n), dtype=torch.float32, device="cuda")
+    B.blink_image(ctx, B.Imaging(n), dev(g), 1, torch.ones(1, device="cuda"), img)
+    B.blink_sync(ctx)
+    assert np.abs(img[0].cpu().numpy() - want).max() < 1e-5
+
+
+# ---------------------------------------------------------------------------------------------------
+# the whole path
+# ---------------------------------------------------------------------------------------------------
+
+PIPE_CASES = [
+    # name, n_samples, fine, chan_avg, n_pix, pol, autos, flags
+    ("tiny", None, None, 1, 256, 0, 1, False),
+    ("precision", None, None, 1, 256, 0, 1, False),
+    ("precision", None, None, 1, 512, 0, 1, False),
+    ("precision", None, None, 1, 1024, 0, 1, False),
+    ("uneven", 20, 3, 1, 64, 1, 0, True),
+    ("coarse", 20, 8, 4, 128, 0, 1, False),
+    ("tiny", None, None, 1, 2048, 0, 1, False),
+]
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp32", "fp8"])
+@pytest.mark.parametrize("mode", [0, 1], ids=["batched", "plain"])
+@pytest.mark.parametrize("case", PIPE_CASES, ids=[f"{c[0]}-{c[4]}-{c[2]}" for c in PIPE_CASES])
+def test_pipeline_matches_oracle(B, ctx, case, mode, arith):
+    name, ns_total, fine, c, n_pix, pol, autos, flags = case
+    w, volt, freqs, fl = _case(name, ns_total, fine, flags)
+    T = volt.shape[0] // 10
+    F = len(freqs) // c
+    img = torch.empty((T * F, n_pix, n_pix), dtype=torch.float32, device="cuda")
+    wts = torch.empty(T * F, dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"], fl), B.Obs(freqs, c, 10, volt.shape[0]),
+                     B.Imaging(n_pix, pol=pol, include_autos=autos), arith, mode, dev(volt), img, wts)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, c, n_pix, flags=fl, pol=pol, autos=bool(autos), n_threads=8)
+    got = img.cpu().numpy()
+    for q in range(T * F):
+        err = rel_rms(got[q], ref["images"][q])
+        assert err <= IMG_RTOL, (q, err)
+        assert wts[q].item() == ref["W"][q]
+
+
+def test_pipeline_many_waves_sampled(B, ctx):
+    # 4 integrations x 128 channels = 512 images of 512^2: several waves; the oracle checks a sample
+    w, volt, freqs, _ = _case("coarse", 40)
+    n_pix = 512
+    n = 4 * 128
+    img = torch.empty((n, n_pix, n_pix), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 40), B.Imaging(n_pix), 0, 0, dev(volt), img)
+    B.blink_sync(ctx)
+    ids = np.array([0, 63, 64, 127, 255, 300, 511])
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n_pix, ids=ids, n_threads=8)
+    for k, q in enumerate(ids):
+        assert rel_rms(img[q].cpu().numpy(), ref["images"][k]) <= IMG_RTOL, q
+
+
+def test_pipeline_is_bitwise_reproducible(B, ctx):
+    w, volt, freqs, _ = _case("coarse", 20, 16)
+    outs = []
+    for _ in range(2):
+        img = torch.empty((32, 256, 256), dtype=torch.float32, device="cuda")
+        B.blink_pipeline(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 20), B.Imaging(256), 0, 0, dev(volt), img)
+        B.blink_sync(ctx)
+        outs.append(img.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_bf16_storage_error_is_reported(B, ctx):
+    w, volt, freqs, _ = _case("precision")
+    errs = {}
+    for n_pix in (256, 512):
+        img = torch.empty((1, n_pix, n_pix), dtype=torch.float32, device="cuda")
+        B.blink_pipeline(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 10), B.Imaging(n_pix, precision=1), 0, 0,
+                         dev(volt), img)
+        B.blink_sync(ctx)
+        ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n_pix)["images"][0]
+        got = img[0].cpu().numpy()
+        errs[n_pix] = (rel_rms(got, ref), float(np.abs(got - ref).max()))
+    print("bf16 storage: rel RMS / max abs per side", errs)
+    assert all(e[0] < 2e-2 for e in errs.values())
+
+
+def test_pipeline_host_buffers_equal_device_path(B, ctx):
+    w, volt, freqs, _ = _case("coarse", 20, 8)
+    arr, obs, im = B.Array(w["enu"]), B.Obs(freqs, 1, 10, 20), B.Imaging(256)
+    d = torch.empty((16, 256, 256), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, arr, obs, im, 0, 0, dev(volt), d)
+    h_volt = torch.from_numpy(volt).pin_memory()
+    h_img = torch.empty((16, 256, 256), dtype=torch.float32).pin_memory()
+    B.blink_pipeline_host(ctx, arr, obs, im, 0, h_volt, h_img, images_per_pass=5)
+    B.blink_sync(ctx)
+    assert np.array_equal(h_img.numpy(), d.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------------------------------
+# edge cases and argument errors
+# ---------------------------------------------------------------------------------------------------
+
+def test_zero_samples_is_a_no_op(B, ctx):
+    w, volt, freqs, _ = _case("tiny")
+    out = torch.zeros(4, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 0), B.Imaging(256), 0, 0, dev(volt), out)
+    B.blink_correlate(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 0), 0, dev(volt), out)
+    B.blink_sync(ctx)
+    assert not out.any()
+
+
+def test_single_tile_and_all_flagged(B, ctx):
+    # one tile: only its autocorrelation; all tiles flagged: an all-zero image with W = 0 treated as 1
+    enu = np.zeros((1, 3))
+    v = bs.constant_voltages(10, 1, 1, 2, -1)
+    img = torch.empty((1, 64, 64), device="cuda")
+    B.blink_pipeline(ctx, B.Array(enu), B.Obs(np.array([150e6]), 1, 10, 10), B.Imaging(64), 0, 0, dev(v), img)
+    B.blink_sync(ctx)
+    assert np.allclose(img[0].cpu().numpy(), 5.0)
+    w, volt, freqs, _ = _case("tiny")
+    fl = np.ones(128, np.uint8)
+    img = torch.full((1, 256, 256), 7.0, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"], fl), B.Obs(freqs, 1, 10, 10), B.Imaging(256), 0, 0, dev(volt), img)
+    B.blink_sync(ctx)
+    assert not img.any()
+
+
+@pytest.mark.parametrize("bad", ["n_pix", "chan_avg", "n_samples", "null"])
+def test_invalid_arguments_are_rejected_before_launch(B, ctx, bad):
+    w, volt, freqs, _ = _case("tiny")
+    arr, obs, im = B.Array(w["enu"]), B.Obs(freqs, 1, 10, 10), B.Imaging(256)
+    img = torch.zeros((1, 256, 256), device="cuda")
+    d = dev(volt)
+    if bad == "n_pix":
+        im = B.Imaging(300)
+    elif bad == "chan_avg":
+        obs = B.Obs(freqs, 2, 10, 10)
+    elif bad == "n_samples":
+        obs = B.Obs(freqs, 1, 10, 15)
+    else:
+        d = None
+    with pytest.raises(B.BlinkError) as e:
+        B.blink_pipeline(ctx, arr, obs, im, 0, 0, d, img)
+    assert e.value.status in (B.BLINK_ERR_INVALID_ARG, B.BLINK_ERR_UNSUPPORTED)
+    B.blink_sync(ctx)
+    assert not img.any()
