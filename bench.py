@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the dirty-imaging hot path: dirty images/s on the full-band streaming workload.
+
+Workload (one step): one 50 ms chunk of the full-band observation - 144 tiles, 2 polarisations,
+24 coarse x 128 fine channels at 10 kHz averaged by 4 into 768 channels of 40 kHz, 500 voltage samples
+of 100 us integrated to 1 ms (K = 40) - imaged into 50 x 768 = 38,400 Stokes-I dirty images of 512^2.
+The step is the whole path: correlation (FP8 tensor cores by default), gridding, 2D inverse FFT.
+
+`value`: images/s with voltages resident in HBM.  `e2e`: the same metric through the host-buffer entry
+point (pinned voltages in, images back to pinned host memory, both copies timed) on a 5 ms sub-chunk.
+Inputs (442 MB of voltages) and outputs (40 GB of images) are far larger than L2, so no flush is needed.
+
+Multi-GPU (torchrun): every rank images its own chunk (chunk 4 + rank), with no collective on the data
+path; the timing is the max over ranks and `value` counts all ranks' images (weak scaling).
+
+`--impl reference` times the CPU oracle (the only other implementation of the method here) on a
+bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "dirty images/s (512² px, 144 tiles) mixed-prec vs FP32 at ≤1e-4 rel RMS"
+WORKLOAD = "fullband"
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--arith", choices=["fp8", "fp32"], default="fp8")
+    ap.add_argument("--mode", choices=["batched", "plain"], default="batched")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--samples", type=int, default=0, help="voltage samples per step (default: the 50 ms chunk)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str):
+        self.dev = dev_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.dev, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                pw.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------------------------------
+# roofline of the dominant kernel
+# ---------------------------------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def stage_bytes(stage: int, n_tiles: int, n_pix: int, K: int) -> float:
+    """Algorithmic bytes per image of each pipeline stage (what the step must move, not what it moves)."""
+    B = n_tiles * (n_tiles + 1) // 2
+    half = n_pix * (n_pix // 2)                       # complex entries of the u >= 0 half plane (no Nyquist)
+    if stage == 0:                                    # voltages in, Stokes-I visibilities out
+        return K * 2 * n_tiles + 8 * B
+    if stage == 1:                                    # visibilities in, column-transformed half plane out
+        return 8 * B + 8 * half
+    return 8 * half + 4 * n_pix * n_pix               # half plane in, image out
+
+
+STAGE_NAMES = ["correlate", "grid+column FFT", "row c2r FFT"]
+STAGE_KERNELS = ["k_corr_tc", "k_colpass_gather", "k_rowpass"]
+STAGE_SOURCES = ["correlate_tc.cu", "grid_fft.cu", "grid_fft.cu"]
+
+
+def source_hash(name: str) -> str:
+    with open(os.path.join(ROOT, "paper_2505_15204_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_for(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if its source is unchanged."""
+    p = os.path.join(PROFILES, "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_sha256_16") != source_hash(source):
+        return None
+    return e.get("dram_bytes_per_launch_fullsize")
+
+
+# ---------------------------------------------------------------------------------------------------
+# the reference arm: the CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------------------------------
+
+def oracle_sample_ids(n_total: int, n: int) -> np.ndarray:
+    return np.unique(np.linspace(0, n_total - 1, n).round().astype(np.int64))
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import blinksynth as bs
+    import oracle
+    w = bs.WORKLOADS[WORKLOAD]
+    cores = os.cpu_count() or 1
+    ns = args.samples or w.samples_per_chunk
+    inp = bs.build_workload(WORKLOAD, chunk=4, workers=min(16, cores), n_samples=ns)
+    n_total = (ns // w.samples_per_int) * w.n_out_chan
+    n_per = max(2, cores)
+    ids = oracle_sample_ids(n_total, n_per * (args.steps + args.warmup))
+    times = []
+    for s in range(args.warmup + args.steps):
+        sel = ids[s::args.warmup + args.steps][:n_per]
+        t = time.perf_counter()
+        oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], w.samples_per_int, w.chan_avg, w.n_pix[0], ids=sel,
+                        n_threads=cores)
+        dt = time.perf_counter() - t
+        if s >= args.warmup:
+            times.append((len(sel), dt))
+    n = sum(a for a, _ in times)
+    tt = sum(b for _, b in times)
+    v = n / tt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tt / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 50 ms chunk, 144 tiles, 768 x 40 kHz, 50 x 1 ms, 512^2 Stokes I",
+                   "images_per_step": n_per, "sample": "evenly spaced image ids of the chunk"},
+        "cpu_baseline": {"value": v, "unit": "images/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n_per} images per step, ids evenly spaced over the {n_total}-image chunk"},
+        "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import blinksynth as bs
+    w = bs.WORKLOADS[WORKLOAD]
+    cores = os.cpu_count() or 1
+    ns = args.samples or w.samples_per_chunk
+    chunk = (4 + rank) % w.n_chunks
+    t_gen = time.perf_counter()
+    inp = bs.build_workload(WORKLOAD, chunk=chunk, workers=max(1, min(16, cores // max(1, world))), n_samples=ns)
+    t_gen = time.perf_counter() - t_gen
+
+    import torch
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    from paper_2505_15204_gb300 import blink as B
+
+    n_tiles, n_pix, K = w.n_tiles, w.n_pix[0], w.k
+    T = ns // w.samples_per_int
+    n_img = T * w.n_out_chan
+    arith = B.BLINK_CORR_FP8 if args.arith == "fp8" else B.BLINK_CORR_FP32
+    mode = B.BLINK_MODE_BATCHED if args.mode == "batched" else B.BLINK_MODE_PLAIN
+    ctx = B.blink_create(local)
+    arr, obs, im = B.Array(inp["enu"]), B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns), B.Imaging(n_pix)
+    stream = torch.cuda.current_stream()
+    volt = torch.from_numpy(inp["volt"]).cuda()
+    img = torch.empty((n_img, n_pix, n_pix), dtype=torch.float32, device="cuda")
+    wts = torch.empty(n_img, dtype=torch.float32, device="cuda")
+
+    t_plan = time.perf_counter()
+    B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, wts, stream)
+    B.blink_sync(ctx, stream)
+    t_plan = time.perf_counter() - t_plan
+    for _ in range(args.warmup):
+        B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, None, stream)
+    B.blink_sync(ctx, stream)
+
+    props = torch.cuda.get_device_properties(local)
+    dev_id = str(getattr(props, "uuid", local))
+    if dev_id and not dev_id.startswith("GPU-") and len(dev_id) == 36:
+        dev_id = "GPU-" + dev_id
+    sampler = ClockSampler(dev_id)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    B.blink_read_profile(ctx, stream, reset=True)
+    B.blink_set_profiling(ctx, True)
+    sampler.start()
+    time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    B.blink_set_profiling(ctx, False)
+    B.blink_sync(ctx, stream)
+    stage_ms, stage_n = B.blink_read_profile(ctx, stream, reset=True)
+    ms_total = e0.elapsed_time(e1)
+    ms_step = ms_total / args.steps
+    if pg:
+        t = torch.tensor([ms_step], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n_img / (ms_step / 1e3)
+
+    # roofline of the dominant stage (live CUDA-event times of its launches in the timed region)
+    dom = int(np.argmax(stage_ms)) if mode == B.BLINK_MODE_BATCHED else 1
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if stage_n[dom]:
+        bytes_total = stage_bytes(dom, n_tiles, n_pix, K) * n_img * args.steps
+        per_launch = bytes_total / stage_n[dom]
+        avg_s = stage_ms[dom] / 1e3 / stage_n[dom]
+        ach = per_launch / avg_s / 1e9
+        kern = STAGE_KERNELS[dom] if (dom or arith == B.BLINK_CORR_FP8) else "k_corr_fp32"
+        src = STAGE_SOURCES[dom] if (dom or arith == B.BLINK_CORR_FP8) else "correlate.cu"
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": traffic_for(kern, src), "kernel": kern, "stage": STAGE_NAMES[dom],
+                "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3, "peak_kind": f"{peak_kind} hbm_gbs"}
+    stages = {STAGE_NAMES[s]: {"ms_per_step": stage_ms[s] / args.steps, "launches_per_step": stage_n[s] / args.steps,
+                               "GBps": (stage_bytes(s, n_tiles, n_pix, K) * n_img * args.steps / (stage_ms[s] / 1e3) / 1e9)
+                               if stage_ms[s] else None}
+              for s in range(B.BLINK_N_STAGES)}
+
+    # full-size parity on sampled images, and the oracle's own throughput on them (rank 0, one GPU)
+    parity = None
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        n_s = max(4, 4 * cores)
+        ids = oracle_sample_ids(n_img, n_s)
+        t = time.perf_counter()
+        ref = oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], w.samples_per_int, w.chan_avg, n_pix, ids=ids,
+                              n_threads=cores)
+        dt = time.perf_counter() - t
+        got = img[torch.from_numpy(ids).cuda()].cpu().numpy()
+        errs = [float(np.linalg.norm(got[k] - ref["images"][k]) / np.linalg.norm(ref["images"][k]))
+                for k in range(len(ids))]
+        parity = {"images_checked": len(ids), "max_rel_rms": max(errs), "gate": 1e-4, "pass": max(errs) <= 1e-4,
+                  "max_abs": float(max(np.abs(got[k] - ref["images"][k]).max() for k in range(len(ids))))}
+        if world == 1:
+            cpu = {"value": len(ids) / dt, "unit": "images/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{len(ids)} images, ids evenly spaced over the {n_img}-image chunk"}
+
+    # end to end through the host-buffer entry point (pinned voltages in, pinned images out)
+    e2e = None
+    if not args.no_e2e:
+        ns_e = 5 * w.samples_per_int
+        n_e = (ns_e // w.samples_per_int) * w.n_out_chan
+        obs_e = B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns_e)
+        h_volt = torch.from_numpy(np.ascontiguousarray(inp["volt"][:ns_e])).pin_memory()
+        h_img = torch.empty((n_e, n_pix, n_pix), dtype=torch.float32).pin_memory()
+        B.blink_pipeline_host(ctx, arr, obs_e, im, arith, h_volt, h_img, 0, stream)
+        B.blink_sync(ctx, stream)
+        reps = max(3, min(args.steps, 10))
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            B.blink_pipeline_host(ctx, arr, obs_e, im, arith, h_volt, h_img, 0, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / reps
+        if pg:
+            t = torch.tensor([ms_e], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms_e = float(t.item())
+        e2e = {"value": world * n_e / (ms_e / 1e3), "unit": "images/s", "h2d_bytes_per_step": int(h_volt.numel()),
+               "d2h_bytes_per_step": int(h_img.numel() * 4), "images_per_step": n_e,
+               "workload": "5 ms sub-chunk (5 integrations x 768 channels) of the same chunk"}
+
+    launches = int(sum(stage_n))
+    line = {
+        "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e4m3->f32 correlation, f32 grid/FFT" if arith == B.BLINK_CORR_FP8 else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 50 ms chunk, 144 tiles x 2 pol, 768 x 40 kHz (10 kHz averaged by 4), "
+                               f"50 x 1 ms (K = 40), 512^2 Stokes-I images",
+                   "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
+                   "mode": args.mode, "l2": "inputs 442 MB and outputs 40 GB per step exceed L2; no flush",
+                   "generate_s": round(t_gen, 2), "plan_s": round(t_plan, 3)},
+        "roofline": roof, "stages": stages, "clocks": clocks, "gpu_launches": launches,
+        "cpu_baseline": cpu, "parity": parity, "e2e": e2e,
+        "vis_per_s": value * (n_tiles * (n_tiles + 1) // 2) * 2,
+        "vis_note": "visibilities formed per second: XX and YY products of every baseline incl. autos per image",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    B.blink_destroy(ctx)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

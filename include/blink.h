@@ -180,6 +180,26 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
                                  const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt,
                                  float* h_img, int32_t images_per_pass, void* stream);
 
+/* ---- measurement -------------------------------------------------------------------------------- */
+
+/* Pipeline stages, for per-stage GPU time. */
+enum {
+    BLINK_STAGE_CORRELATE = 0,   /* correlation kernels */
+    BLINK_STAGE_GRID_FFT = 1,    /* gridding + first (column) FFT pass */
+    BLINK_STAGE_ROW_FFT = 2,     /* second (row, complex-to-real) FFT pass + 1/W */
+    BLINK_N_STAGES = 3
+};
+
+/*
+ * Per-stage timing of blink_pipeline (not part of the method; for measurement).  While enabled, every
+ * kernel launch of the batched pipeline is bracketed by a pair of CUDA events recorded on the launch's
+ * stream.  blink_read_profile waits for `stream`, then adds each stage's summed event time (ms) and
+ * launch count to ms[BLINK_N_STAGES] and launches[BLINK_N_STAGES] (host arrays, overwritten), and
+ * forgets the recorded events when `reset` is non-zero.
+ */
+blink_status blink_set_profiling(blink_context* ctx, int32_t enable);
+blink_status blink_read_profile(blink_context* ctx, void* stream, double* ms, int64_t* launches, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,7 +38,12 @@ BLINK_MODE_PLAIN = 1
 ENTRY_POINTS = (
     "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
+    "blink_set_profiling", "blink_read_profile",
 )
+BLINK_STAGE_CORRELATE = 0
+BLINK_STAGE_GRID_FFT = 1
+BLINK_STAGE_ROW_FFT = 2
+BLINK_N_STAGES = 3
 
 
 class BlinkError(RuntimeError):
@@ -79,6 +84,8 @@ def _load():
         "blink_image": (S, [P, P, P, I32, P, P, P]),
         "blink_pipeline": (S, [P, P, P, P, I32, I32, P, P, P, P]),
         "blink_pipeline_host": (S, [P, P, P, P, I32, P, P, I32, P]),
+        "blink_set_profiling": (S, [P, I32]),
+        "blink_read_profile": (S, [P, P, P, P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,3 +234,15 @@ def blink_pipeline_host(ctx, array: Array, obs: Obs, imaging: Imaging, arith: in
     a, o, i = array.c(), obs.c(), imaging.c()
     _check(_lib.blink_pipeline_host(ctx, C.byref(a), C.byref(o), C.byref(i), arith, _ptr(h_volt), _ptr(h_img),
                                     images_per_pass, _stream(stream)), "blink_pipeline_host")
+
+
+def blink_set_profiling(ctx, enable: bool) -> None:
+    _check(_lib.blink_set_profiling(ctx, int(bool(enable))), "blink_set_profiling")
+
+
+def blink_read_profile(ctx, stream=None, reset: bool = True):
+    """Per-stage (ms, launches) summed over the recorded pipeline launches, as two lists."""
+    ms = (C.c_double * BLINK_N_STAGES)()
+    n = (C.c_int64 * BLINK_N_STAGES)()
+    _check(_lib.blink_read_profile(ctx, _stream(stream), ms, n, int(bool(reset))), "blink_read_profile")
+    return list(ms), list(n)

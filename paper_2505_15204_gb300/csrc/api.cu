@@ -288,6 +288,33 @@ blink_status twiddles(blink_context* ctx, int N, float2** out) {
     return BLINK_OK;
 }
 
+static cudaEvent_t take_event(blink_context* ctx) {
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+StageTimer::StageTimer(blink_context* c, int s, cudaStream_t stream) : ctx(c), stage(s), st(stream) {
+    if (!ctx->profiling) return;
+    cudaEvent_t a = take_event(ctx);
+    b = take_event(ctx);
+    if (!a || !b) {
+        b = nullptr;
+        return;
+    }
+    cudaEventRecord(a, st);
+    ctx->recs.push_back({stage, a, b});
+}
+
+StageTimer::~StageTimer() {
+    if (b) cudaEventRecord(b, st);
+}
+
 // Plans are keyed by every input they depend on.  Imaging-free plans (im == NULL) serve correlation.
 blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs* o, const blink_imaging* im,
                       bool need_gather, cudaStream_t st, Plan** out) {
@@ -418,15 +445,25 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
     const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
     for (int w0 = id0; w0 < id1; w0 += wave) {
         const int nw = std::min(wave, id1 - w0);
-        if (arith == BLINK_CORR_FP8)
-            BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B, ctx->d_status,
-                                      ctx->n_sm, st));
-        else
-            BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B, ctx->d_status,
-                                       st));
-        BLINK_TRY(launch_colpass_gather(p, prec, static_cast<float2*>(vis), p.B, w0, nw, H, ldh, ctx->d_status, st));
-        BLINK_TRY(launch_rowpass(N, prec, p.d_tw, H, ldh, 0, p.d_W, w0, p.F, nw, d_img + (int64_t)(w0 - id0) * N * N,
-                                 st));
+        {
+            StageTimer t(ctx, BLINK_STAGE_CORRELATE, st);
+            if (arith == BLINK_CORR_FP8)
+                BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B,
+                                          ctx->d_status, ctx->n_sm, st));
+            else
+                BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B,
+                                           ctx->d_status, st));
+        }
+        {
+            StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
+            BLINK_TRY(launch_colpass_gather(p, prec, static_cast<float2*>(vis), p.B, w0, nw, H, ldh, ctx->d_status,
+                                            st));
+        }
+        {
+            StageTimer t(ctx, BLINK_STAGE_ROW_FFT, st);
+            BLINK_TRY(launch_rowpass(N, prec, p.d_tw, H, ldh, 0, p.d_W, w0, p.F, nw,
+                                     d_img + (int64_t)(w0 - id0) * N * N, st));
+        }
     }
     return BLINK_OK;
 }
@@ -487,6 +524,11 @@ void blink_destroy(blink_context* ctx) {
     for (Plan* p : ctx->plans) free_plan(p);
     for (auto& w : ctx->ws) cudaFree(w.ptr);
     for (float2* t : ctx->tw) cudaFree(t);
+    for (auto& r : ctx->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     cudaFree(ctx->d_status);
     delete ctx;
 }
@@ -501,6 +543,39 @@ blink_status blink_sync(blink_context* ctx, void* stream) {
         BLINK_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
         if (status & DEV_ERR_TIMEOUT) return set_error(BLINK_ERR_TIMEOUT, "a bounded device-side wait ran out");
         return set_error(BLINK_ERR_DEVICE, "a device-side index guard failed");
+    }
+    return BLINK_OK;
+}
+
+blink_status blink_set_profiling(blink_context* ctx, int32_t enable) {
+    if (!ctx) return set_error(BLINK_ERR_INVALID_ARG, "context is NULL");
+    ctx->profiling = enable != 0;
+    return BLINK_OK;
+}
+
+blink_status blink_read_profile(blink_context* ctx, void* stream, double* ms, int64_t* launches, int32_t reset) {
+    BLINK_TRY(make_current(ctx));
+    if (!ms || !launches) return set_error(BLINK_ERR_INVALID_ARG, "ms or launches is NULL");
+    BLINK_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    for (int s = 0; s < BLINK_N_STAGES; s++) {
+        ms[s] = 0.0;
+        launches[s] = 0;
+    }
+    for (auto& r : ctx->recs) {
+        float t = 0.f;
+        BLINK_CUDA(cudaEventSynchronize(r.b));
+        BLINK_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        if (r.stage >= 0 && r.stage < BLINK_N_STAGES) {
+            ms[r.stage] += t;
+            launches[r.stage] += 1;
+        }
+    }
+    if (reset) {
+        for (auto& r : ctx->recs) {
+            ctx->pool.push_back(r.a);
+            ctx->pool.push_back(r.b);
+        }
+        ctx->recs.clear();
     }
     return BLINK_OK;
 }

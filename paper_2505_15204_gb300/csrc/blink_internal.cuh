@@ -76,7 +76,11 @@ struct blink_context {
     std::vector<blink::Plan*> plans;       // most recent last
     blink::Workspace ws[4];
     float2* tw[16] = {};                   // twiddle tables by log2(side)
-    cudaEvent_t ev = nullptr;
+    // per-stage profiling (blink_set_profiling): recorded (stage, start, stop) event pairs and a free pool
+    bool profiling = false;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
 };
 
 namespace blink {
@@ -85,6 +89,16 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
                       bool need_gather, cudaStream_t st, Plan** out);
 blink_status workspace(blink_context* ctx, int slot, size_t bytes, void** out);
 blink_status twiddles(blink_context* ctx, int N, float2** out);
+
+// Brackets one stage launch with profiling events when profiling is on.
+struct StageTimer {
+    blink_context* ctx;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t b = nullptr;
+    StageTimer(blink_context* c, int s, cudaStream_t stream);
+    ~StageTimer();
+};
 
 // ---- kernel launchers (defined next to their kernels) --------------------------------------------
 void launch_cells(const Plan& p, cudaStream_t st);

@@ -1,11 +1,413 @@
-// Correlation on the tcgen05 tensor cores (placeholder until the FP8 kernel lands).
+// Correlation on the tcgen05 tensor cores (Eq. 2; Sec. 5.2.2) with FP8 e4m3 operands and FP32
+// accumulation in tensor memory.
+//
+// Every 4-bit component is an integer in [-8, 7] (and its negation in [-7, 8]), all exact in e4m3, and
+// each product and partial sum is an integer below 2^24, so the tensor-core result equals the integer
+// correlation bit for bit.
+//
+// The complex product is realified.  With x_u in C^K for a unit u (a tile, or a tile and polarisation),
+//   P_u = [Re x_u, Im x_u],   Q_u = [Im x_u, -Re x_u]     (length 2K bytes each)
+//   Re S_uv = P_u . P_v,       Im S_uv = Q_u . P_v,        S_uv = sum_k x_u[k] conj(x_v[k]).
+// Units are grouped in blocks of 64.  The A operand of block m is the 128 rows [P of its 64 units;
+// Q of its 64 units]; the B operand of block n is the 64 P rows of block n.  One M=128, N=64 MMA chain
+// over K gives Re S (TMEM lanes 0-63) and Im S (lanes 64-127) for the 64 x 64 units of the block pair.
+// Only block pairs n <= m are computed (the lower triangle).  For Stokes I the two polarisations are
+// concatenated along K (units = tiles, K' = 2K), which sums S_XX + S_YY inside the MMA.
+//
+// Per CTA (persistent, one per SM): TMA loads an item's raw voltage block (double buffered), all
+// threads unpack nibbles to e4m3 operand tiles in shared memory (K-major, no swizzle, 8x16-byte core
+// matrices), one thread issues the MMAs and commits them to an mbarrier, and four warps read the
+// accumulators back from TMEM (each warp its 32 lanes), stage them in shared memory and write the
+// visibilities.  Every wait is bounded; on expiry the CTA records BLINK_ERR_TIMEOUT, waits (bounded) for
+// its own copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "blink_internal.cuh"
 
 namespace blink {
 
-blink_status launch_corr_fp8(int, const uint8_t*, int64_t, const Plan&, int, int, int, void*, int64_t, int*, int,
-                             cudaStream_t) {
-    return set_error(BLINK_ERR_UNSUPPORTED, "FP8 tensor-core correlation is not built yet");
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kUnitsPerBlk = 64;
+constexpr int kTmemCols = 512;
+constexpr int kPairsPerRound = kTmemCols / 64;
+constexpr int kStageLd = 65;                     // padded row of the epilogue staging tiles (floats)
+constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
+
+struct TcParams {
+    int mode;                // CORR_OUT_*
+    int n_tiles, ns, c, F, K;
+    int units, n_blk, Kr, Kp;
+    int n_pairs, n_rounds;
+    int first_item, n_items;
+    int raw_bytes;
+    uint32_t off_raw0, off_raw1, off_re, off_im, off_lut, off_bar, off_tmem;
+    const uint8_t* flags;
+    void* out;
+    int64_t out_item_stride;
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity` to complete; false if the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitBudget) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle.  lbo = byte distance of core matrices adjacent
+// along K, sbo = byte distance of 8-row groups; bits 46-47 hold the descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major, dense.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// byte offset of (row, kbyte) inside a 128-row operand tile of Kp bytes per row
+__device__ __forceinline__ int op_off(int row, int kb, int Kp) {
+    return (row >> 3) * (Kp * 8) + (kb >> 4) * 128 + (row & 7) * 16 + (kb & 15);
+}
+
+__device__ __forceinline__ void pair_of(int q, int& mb, int& jb) {
+    mb = 0;
+    while ((mb + 1) * (mb + 2) / 2 <= q) mb++;
+    jb = q - mb * (mb + 1) / 2;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* ops = smem;                                   // n_blk tiles of 128 x Kp bytes
+    float* st_re = reinterpret_cast<float*>(smem + P.off_re);
+    float* st_im = reinterpret_cast<float*>(smem + P.off_im);
+    uint8_t* lut = smem + P.off_lut;                       // [0,16): e4m3 of nibble, [16,32): of -nibble
+    const uint32_t bar_tma0 = smem_u32(smem + P.off_bar), bar_tma1 = bar_tma0 + 8, bar_mma = bar_tma0 + 16;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + P.off_tmem);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (smem_u32(smem) & 1023) {                          // descriptors and TMA need an aligned base
+        if (tid == 0) atomicOr(P.status, DEV_ERR_INDEX);
+        return;
+    }
+
+    if (tid == 0) {
+        mbar_init(bar_tma0, 1);
+        mbar_init(bar_tma1, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 32) {
+        // e4m3 of v (v in [-8, 8]): 0, 1, 2, 3, 4, 5, 6, 7 and 8, with the sign bit 0x80 for negatives
+        const uint8_t pos[9] = {0x00, 0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E, 0x50};
+        const int n = tid & 15;
+        const int v = (n >= 8 ? n - 16 : n) * (tid < 16 ? 1 : -1);
+        lut[tid] = v >= 0 ? pos[v] : (uint8_t)(0x80 | pos[-v]);
+    }
+    {
+        uint4* z = reinterpret_cast<uint4*>(ops);
+        const int n16 = P.n_blk * 128 * P.Kp / 16;
+        for (int e = tid; e < n16; e += kThreads) z[e] = make_uint4(0, 0, 0, 0);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const uint32_t ops_s = smem_u32(ops);
+    const uint32_t raw_s[2] = {smem_u32(smem + P.off_raw0), smem_u32(smem + P.off_raw1)};
+    const uint32_t bar_tma[2] = {bar_tma0, bar_tma1};
+    uint32_t tma_par[2] = {0, 0}, mma_par = 0;
+    bool pending[2] = {false, false};
+    bool abort = false;
+    const int total = P.first_item + P.n_items;
+    const uint32_t sbo = (uint32_t)P.Kp * 8, tile_bytes = 128u * P.Kp;
+    const uint32_t idesc = idesc_e4m3(128, 64);
+    const float div = (float)(P.mode == CORR_OUT_STOKES_I ? 2 * P.K : P.K);
+    const int per_k = 2 * P.n_tiles;
+
+    auto issue = [&](int item, int b) {
+        const int tau = item / P.F, f = item - (item / P.F) * P.F;
+        mbar_expect_tx(bar_tma[b], (uint32_t)P.raw_bytes);
+        tma_load_3d(raw_s[b], &tmap, bar_tma[b], 0, f * P.c, tau * P.ns);
+    };
+
+    int it = P.first_item + blockIdx.x;
+    if (tid == 0 && it < total) issue(it, 0);
+    pending[0] = it < total;
+    for (int buf = 0; it < total; it += gridDim.x, buf ^= 1) {
+        const int nxt = it + gridDim.x;
+        if (nxt < total) {
+            if (tid == 0) issue(nxt, buf ^ 1);
+            pending[buf ^ 1] = true;
+        }
+        const bool ok = mbar_wait(bar_tma[buf], tma_par[buf]);
+        tma_par[buf] ^= 1;
+        pending[buf] = !ok;
+        if (__syncthreads_or(!ok)) {
+            abort = true;
+            break;
+        }
+        // ---- unpack nibbles to e4m3 operand rows -------------------------------------------------------
+        const uint8_t* raw = smem + (buf ? P.off_raw1 : P.off_raw0);
+        const int n_el = P.K * per_k;
+        for (int e = tid; e < n_el; e += kThreads) {
+            const int k = e / per_k, rem = e - (e / per_k) * per_k;
+            const int a = rem >> 1, p = rem & 1;
+            int unit, kp, kh;
+            if (P.mode == CORR_OUT_STOKES_I) {
+                unit = a; kp = p * P.K + k; kh = 2 * P.K;
+            } else if (P.mode == CORR_OUT_VIS4) {
+                unit = 2 * a + p; kp = k; kh = P.K;
+            } else {
+                if (p) continue;
+                unit = a; kp = k; kh = P.K;
+            }
+            const uint32_t byte = raw[e];
+            const uint8_t re8 = lut[byte & 15], im8 = lut[byte >> 4], nre8 = lut[16 + (byte & 15)];
+            uint8_t* tile = ops + (unit >> 6) * tile_bytes;
+            const int r = unit & 63;
+            tile[op_off(r, kp, P.Kp)] = re8;
+            tile[op_off(r, kp + kh, P.Kp)] = im8;
+            tile[op_off(r + 64, kp, P.Kp)] = im8;
+            tile[op_off(r + 64, kp + kh, P.Kp)] = nre8;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // ---- MMA rounds of up to 8 block pairs, each followed by its epilogue ---------------------------
+        for (int r = 0; r < P.n_rounds && !abort; r++) {
+            const int q0 = r * kPairsPerRound, q1 = min(P.n_pairs, q0 + kPairsPerRound);
+            if (tid == 0) {
+                tc_fence_after();
+                for (int q = q0; q < q1; q++) {
+                    int mb, jb;
+                    pair_of(q, mb, jb);
+                    const uint32_t d = tmem + (uint32_t)(q - q0) * 64;
+                    const uint32_t a0 = ops_s + mb * tile_bytes, b0 = ops_s + jb * tile_bytes;
+                    for (int s = 0; s < P.Kp / 32; s++)
+                        mma_e4m3(d, smem_desc(a0 + s * 256, 128, sbo), smem_desc(b0 + s * 256, 128, sbo), idesc,
+                                 s > 0);
+                }
+                mma_commit(bar_mma);
+            }
+            const bool okm = mbar_wait(bar_mma, mma_par);
+            mma_par ^= 1;
+            if (__syncthreads_or(!okm)) {
+                abort = true;
+                break;
+            }
+            tc_fence_after();
+            const int local = it - P.first_item;
+            for (int q = q0; q < q1; q++) {
+                int mb, jb;
+                pair_of(q, mb, jb);
+                const int row = warp * 32 + lane;
+                float* st = row < 64 ? st_re + row * kStageLd : st_im + (row - 64) * kStageLd;
+                uint32_t v[32];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q - q0) * 64 + h * 32, v);
+#pragma unroll
+                    for (int cc = 0; cc < 32; cc++) st[h * 32 + cc] = __uint_as_float(v[cc]);
+                }
+                __syncthreads();
+                for (int e = tid; e < 64 * 64; e += kThreads) {
+                    const int il = e >> 6, jl = e & 63;
+                    const int ui = mb * 64 + il, uj = jb * 64 + jl;
+                    float re = st_re[il * kStageLd + jl], im = st_im[il * kStageLd + jl];
+                    if (P.mode == CORR_OUT_VIS4) {
+                        if (ui >= P.units) continue;
+                        const int ai = ui >> 1, aj = uj >> 1;
+                        if (aj > ai) continue;
+                        if (P.flags[ai] || P.flags[aj]) re = im = 0.f;
+                        const int64_t b = (int64_t)ai * (ai + 1) / 2 + aj;
+                        float* o = static_cast<float*>(P.out) + (int64_t)local * P.out_item_stride +
+                                   (b * 4 + 2 * (ui & 1) + (uj & 1)) * 2;
+                        *reinterpret_cast<float2*>(o) = make_float2(__fdiv_rn(re, div), __fdiv_rn(im, div));
+                    } else {
+                        if (ui >= P.n_tiles || uj > ui) continue;
+                        if (P.flags[ui] || P.flags[uj]) re = im = 0.f;
+                        const int64_t b = (int64_t)ui * (ui + 1) / 2 + uj;
+                        static_cast<float2*>(P.out)[(int64_t)local * P.out_item_stride + b] =
+                            make_float2(__fdiv_rn(re, div), __fdiv_rn(im, div));
+                    }
+                }
+                __syncthreads();
+            }
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (abort) break;
+    }
+    if (abort) {
+        if (tid == 0) {
+            atomicOr(P.status, DEV_ERR_TIMEOUT);
+            for (int b = 0; b < 2; b++)
+                if (pending[b]) mbar_wait(bar_tma[b], tma_par[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
+                             int first_item, int n_items, void* out, int64_t out_item_stride, int* d_status, int n_sm,
+                             cudaStream_t st) {
+    if (n_items <= 0) return BLINK_OK;
+    const int nt = p.n_tiles, c = p.chan_avg, K = ns * c;
+    if (nt % 8 || ns > 256 || c > 256 || ((uintptr_t)d_volt & 15) || (sample_stride % 16))
+        return set_error(BLINK_ERR_UNSUPPORTED,
+                         "FP8 tensor-core correlation needs n_tiles % 8 == 0, samples_per_int <= 256, chan_avg <= 256 "
+                         "and a 16-byte aligned voltage block");
+    TcParams P{};
+    P.mode = out_kind;
+    P.n_tiles = nt;
+    P.ns = ns;
+    P.c = c;
+    P.F = p.F;
+    P.K = K;
+    P.units = out_kind == CORR_OUT_VIS4 ? 2 * nt : nt;
+    P.n_blk = (P.units + kUnitsPerBlk - 1) / kUnitsPerBlk;
+    P.Kr = out_kind == CORR_OUT_STOKES_I ? 4 * K : 2 * K;
+    P.Kp = (P.Kr + 31) / 32 * 32;
+    P.n_pairs = P.n_blk * (P.n_blk + 1) / 2;
+    P.n_rounds = (P.n_pairs + kPairsPerRound - 1) / kPairsPerRound;
+    P.first_item = first_item;
+    P.n_items = n_items;
+    P.raw_bytes = ns * c * nt * 2;
+    uint32_t off = align_up((uint32_t)P.n_blk * 128u * P.Kp, 1024);
+    P.off_raw0 = off;
+    off = align_up(off + P.raw_bytes, 128);
+    P.off_raw1 = off;
+    off = align_up(off + P.raw_bytes, 128);
+    P.off_re = off;
+    off += 64 * kStageLd * 4;
+    P.off_im = off;
+    off = align_up(off + 64 * kStageLd * 4, 16);
+    P.off_lut = off;
+    off += 32;
+    P.off_bar = off;
+    off += 24;
+    P.off_tmem = off;
+    off += 8;
+    const size_t smem = std::max<size_t>(off, 120 * 1024);   // one CTA per SM: it owns all 512 TMEM columns
+    if (smem > 227 * 1024 || (uint32_t)P.Kp * 8 >= (1u << 18))
+        return set_error(BLINK_ERR_UNSUPPORTED, "FP8 tensor-core correlation: operands of this K do not fit shared memory");
+    P.flags = p.d_flags;
+    P.out = out;
+    P.out_item_stride = out_item_stride;
+    P.status = d_status;
+
+    auto encode = encode_fn();
+    if (!encode) return set_error(BLINK_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int last_tau = (first_item + n_items - 1) / p.F;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)(nt / 2), (cuuint64_t)p.n_fine, (cuuint64_t)(last_tau + 1) * ns};
+    const cuuint64_t strides[2] = {(cuuint64_t)nt * 2, (cuuint64_t)sample_stride};
+    const cuuint32_t box[3] = {(cuuint32_t)(nt / 2), (cuuint32_t)c, (cuuint32_t)ns};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint8_t*>(d_volt), dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(BLINK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the voltage block");
+    BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = std::min(n_items, n_sm);
+    k_corr_tc<<<grid, kThreads, smem, st>>>(map, P);
+    BLINK_CUDA(cudaGetLastError());
+    return BLINK_OK;
 }
 
 }  // namespace blink
