@@ -180,6 +180,27 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
                                  const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt,
                                  float* h_img, int32_t images_per_pass, void* stream);
 
+/*
+ * blink_image without any device allocation (the paper has no counterpart; this is a library service).
+ * Callers that cannot allocate device memory while they image - a real-time instrument pipeline that
+ * reserves all device memory when an observation starts, or an application whose device memory belongs
+ * to another allocator - can use this entry point: it needs no context and calls no cudaMalloc, cudaFree
+ * or allocating library routine.  Arguments, layouts and results are those of blink_image; it runs on
+ * the calling thread's current CUDA device.
+ *   Scratch: a fixed 16 MiB array in the library's static device memory (held by every GPU that loads
+ *   the library until the process exits) holds the twiddle table and the column-pass result of as many
+ *   images as fit; larger batches are processed in passes.  One image must fit: sides up to 1024 with
+ *   BLINK_PREC_FP32 storage and up to 2048 with BLINK_PREC_BF16; a larger side returns
+ *   BLINK_ERR_UNSUPPORTED before anything is launched.  Every call rewrites the parts of the scratch it
+ *   reads, so nothing needs clearing between calls.
+ *   Set-up: the first call on a device looks up the scratch's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ *   All calls share the one scratch array: calls whose work overlaps on the GPU (different streams,
+ *   or different host threads) race and corrupt each other's images.  Order them on one stream.
+ */
+blink_status blink_image_noalloc(const blink_imaging* imaging, const float* d_grid, int32_t n_images,
+                                 const float* d_weight, float* d_img, void* stream);
+
 /* ---- measurement -------------------------------------------------------------------------------- */
 
 /* Pipeline stages, for per-stage GPU time. */

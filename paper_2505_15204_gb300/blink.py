@@ -38,7 +38,7 @@ BLINK_MODE_PLAIN = 1
 ENTRY_POINTS = (
     "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
-    "blink_set_profiling", "blink_read_profile",
+    "blink_set_profiling", "blink_read_profile", "blink_image_noalloc",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
@@ -86,6 +86,7 @@ def _load():
         "blink_pipeline_host": (S, [P, P, P, P, I32, P, P, I32, P]),
         "blink_set_profiling": (S, [P, I32]),
         "blink_read_profile": (S, [P, P, P, P, I32]),
+        "blink_image_noalloc": (S, [P, P, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -246,3 +247,10 @@ def blink_read_profile(ctx, stream=None, reset: bool = True):
     n = (C.c_int64 * BLINK_N_STAGES)()
     _check(_lib.blink_read_profile(ctx, _stream(stream), ms, n, int(bool(reset))), "blink_read_profile")
     return list(ms), list(n)
+
+
+def blink_image_noalloc(imaging: Imaging, d_grid, n_images: int, d_weight, d_img, stream=None) -> None:
+    """blink_image without a context and without device allocation (static scratch, current device)."""
+    i = imaging.c()
+    _check(_lib.blink_image_noalloc(C.byref(i), _ptr(d_grid), n_images, _ptr(d_weight), _ptr(d_img),
+                                    _stream(stream)), "blink_image_noalloc")
