@@ -123,14 +123,14 @@ def stage_bytes(stage: int, n_tiles: int, n_pix: int, K: int) -> float:
     half = n_pix * (n_pix // 2)                       # complex entries of the u >= 0 half plane (no Nyquist)
     if stage == 0:                                    # voltages in, Stokes-I visibilities out
         return K * 2 * n_tiles + 8 * B
-    if stage == 1:                                    # visibilities in, column-transformed half plane out
-        return 8 * B + 8 * half
+    if stage == 1:                                    # visibilities in, images out (intermediate on chip / L2)
+        return 8 * B + 4 * n_pix * n_pix
     return 8 * half + 4 * n_pix * n_pix               # half plane in, image out
 
 
-STAGE_NAMES = ["correlate", "grid+column FFT", "row c2r FFT"]
-STAGE_KERNELS = ["k_corr_tc", "k_colpass_gather", "k_rowpass"]
-STAGE_SOURCES = ["correlate_tc.cu", "grid_fft.cu", "grid_fft.cu"]
+STAGE_NAMES = ["correlate", "grid + 2D FFT", "row c2r FFT"]
+STAGE_KERNELS = ["k_corr_tc", "k_fft_persistent", "k_rowpass"]
+STAGE_SOURCES = ["correlate_tc.cu", "fft_persistent.cu", "grid_fft.cu"]
 
 
 def source_hash(name: str) -> str:

@@ -206,8 +206,8 @@ blink_status blink_image_noalloc(const blink_imaging* imaging, const float* d_gr
 /* Pipeline stages, for per-stage GPU time. */
 enum {
     BLINK_STAGE_CORRELATE = 0,   /* correlation kernels */
-    BLINK_STAGE_GRID_FFT = 1,    /* gridding + first (column) FFT pass */
-    BLINK_STAGE_ROW_FFT = 2,     /* second (row, complex-to-real) FFT pass + 1/W */
+    BLINK_STAGE_GRID_FFT = 1,    /* gridding + the 2D inverse FFT (the batched form's persistent kernel) */
+    BLINK_STAGE_ROW_FFT = 2,     /* a separate row (complex-to-real) FFT pass, where one runs */
     BLINK_N_STAGES = 3
 };
 

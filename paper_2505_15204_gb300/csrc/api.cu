@@ -27,7 +27,6 @@ blink_status cuda_error(cudaError_t e, const char* what) {
 namespace {
 
 constexpr double kSpeedOfLight = 299792458.0;
-constexpr double kTwoPi = 6.283185307179586476925286766559;
 
 struct Hasher {
     uint64_t h = 1469598103934665603ull;
@@ -109,11 +108,10 @@ void free_plan(Plan* p) {
     cudaFree(p->d_enu);
     cudaFree(p->d_freq);
     cudaFree(p->d_cells);
-    cudaFree(p->d_cell_off);
-    cudaFree(p->d_cell_key);
-    cudaFree(p->d_cell_beg);
-    cudaFree(p->d_contrib);
+    cudaFree(p->d_ent_off);
+    cudaFree(p->d_ent);
     cudaFree(p->d_W);
+    cudaFree(p->d_Wk);
     cudaFree(p->d_tw);
     delete p;
 }
@@ -146,31 +144,29 @@ double default_cell(const blink_array* a, double nu_max, int n_pix) {
     return umax / (double)(n_pix / 2 - 1);
 }
 
-// Cell-sorted gather list of the u >= 0 half plane for every output channel (see grid_fft.cu).
+// Cell-sorted gather list of the u >= 0 half plane for every output channel (see grid_fft.cu): one entry
+// per visibility (and per mirror) that lands in the half plane, ordered by (column block, cell, baseline).
 blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std::vector<short2>& bl,
                           const blink_array* a) {
     const int N = p->N, cw = p->cw, half = N / 2;
     const int64_t B = p->B;
-    const int64_t nkeys = (int64_t)half * N;                 // (cb, v, du) key space
+    const int64_t nkeys = (int64_t)half * N;                 // (column block, v, u within block)
+    const int64_t block_keys = (int64_t)N * cw;
     std::vector<int> count(nkeys + 1);
-    std::vector<int> cell_off((size_t)p->F * (p->n_cb + 1));
-    std::vector<uint32_t> cell_key;
-    std::vector<int> cell_beg;
-    std::vector<uint32_t> contrib;
-    std::vector<uint32_t> ekey, eval;
-    cell_key.reserve((size_t)p->F * B);
-    cell_beg.reserve((size_t)p->F * B + 1);
-    contrib.reserve((size_t)p->F * (B + B / 16));
+    std::vector<int> ent_off((size_t)p->F * (p->n_cb + 1));
+    std::vector<uint2> ent;
+    std::vector<uint32_t> ekey, eval, sorted;
+    ent.reserve((size_t)p->F * (B + B / 16));
     p->W.assign(p->F, 0.f);
     int64_t dropped = 0;
+    auto key_of = [&](int u, int v) -> uint32_t {
+        const int cb = u / cw;
+        return (uint32_t)(cb * block_keys + (int64_t)v * cw + (u - cb * cw));
+    };
     for (int f = 0; f < p->F; f++) {
         ekey.clear();
         eval.clear();
         int64_t w = 0;
-        auto key_of = [&](int u, int v) -> uint32_t {
-            const int cb = u / cw;
-            return (uint32_t)((int64_t)cb * N * cw + (int64_t)v * cw + (u - cb * cw));
-        };
         for (int64_t b = 0; b < B; b++) {
             const uint32_t c = cells[(size_t)f * B + b];
             const int i = bl[b].x, j = bl[b].y;
@@ -202,46 +198,36 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
             w += 2;
         }
         p->W[f] = (float)w;
-        // stable counting sort by key (contributions of a cell stay in baseline order)
+        // stable counting sort by key: the entries of a cell stay in baseline order
         std::fill(count.begin(), count.end(), 0);
         for (uint32_t k : ekey) count[k + 1]++;
         for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
-        std::vector<uint32_t> sorted_val(eval.size());
+        sorted.assign(ekey.size(), 0);
+        std::vector<uint32_t> skey(ekey.size());
         {
             std::vector<int> cur(count.begin(), count.end() - 1);
-            for (size_t e = 0; e < ekey.size(); e++) sorted_val[cur[ekey[e]]++] = eval[e];
+            for (size_t e = 0; e < ekey.size(); e++) {
+                const int at = cur[ekey[e]]++;
+                sorted[at] = eval[e];
+                skey[at] = ekey[e];
+            }
         }
-        int cb_prev = -1;
-        const int64_t contrib_base = (int64_t)contrib.size();
-        for (int64_t k = 0; k < nkeys; k++) {
-            const int cb = (int)(k / ((int64_t)N * cw));
-            while (cb_prev < cb) cell_off[(size_t)f * (p->n_cb + 1) + (++cb_prev)] = (int)cell_key.size();
-            const int n = count[k + 1] - count[k];
-            if (!n) continue;
-            const int rem = (int)(k - (int64_t)cb * N * cw);
-            const int v = rem / cw, u = cb * cw + rem % cw;
-            cell_key.push_back(((uint32_t)v << 16) | (uint32_t)u);
-            cell_beg.push_back((int)(contrib_base + count[k]));
+        const int64_t base = (int64_t)ent.size();
+        for (int cb = 0; cb <= p->n_cb; cb++)
+            ent_off[(size_t)f * (p->n_cb + 1) + cb] = (int)(base + count[std::min<int64_t>((int64_t)cb * block_keys, nkeys)]);
+        for (size_t e = 0; e < sorted.size(); e++) {
+            const uint32_t local = (uint32_t)(skey[e] % block_keys);
+            ent.push_back(make_uint2(local | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
         }
-        while (cb_prev < p->n_cb) cell_off[(size_t)f * (p->n_cb + 1) + (++cb_prev)] = (int)cell_key.size();
-        contrib.insert(contrib.end(), sorted_val.begin(), sorted_val.end());
-        if ((int64_t)contrib.size() > INT32_MAX / 2 || (int64_t)cell_key.size() > INT32_MAX / 2)
-            return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
+        if ((int64_t)ent.size() > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
     }
-    cell_beg.push_back((int)contrib.size());
-    p->n_cells = (int64_t)cell_key.size();
-    p->n_contrib = (int64_t)contrib.size();
+    p->n_contrib = (int64_t)ent.size();
+    p->n_cells = p->n_contrib;
     p->n_dropped = dropped;
-    BLINK_TRY(dmalloc(&p->d_cell_off, cell_off.size()));
-    BLINK_TRY(dmalloc(&p->d_cell_key, cell_key.size()));
-    BLINK_TRY(dmalloc(&p->d_cell_beg, cell_beg.size()));
-    BLINK_TRY(dmalloc(&p->d_contrib, contrib.size()));
-    BLINK_CUDA(cudaMemcpy(p->d_cell_off, cell_off.data(), cell_off.size() * sizeof(int), cudaMemcpyHostToDevice));
-    if (!cell_key.empty())
-        BLINK_CUDA(cudaMemcpy(p->d_cell_key, cell_key.data(), cell_key.size() * 4, cudaMemcpyHostToDevice));
-    BLINK_CUDA(cudaMemcpy(p->d_cell_beg, cell_beg.data(), cell_beg.size() * 4, cudaMemcpyHostToDevice));
-    if (!contrib.empty())
-        BLINK_CUDA(cudaMemcpy(p->d_contrib, contrib.data(), contrib.size() * 4, cudaMemcpyHostToDevice));
+    BLINK_TRY(dmalloc(&p->d_ent_off, ent_off.size()));
+    BLINK_TRY(dmalloc(&p->d_ent, ent.size()));
+    BLINK_CUDA(cudaMemcpy(p->d_ent_off, ent_off.data(), ent_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!ent.empty()) BLINK_CUDA(cudaMemcpy(p->d_ent, ent.data(), ent.size() * sizeof(uint2), cudaMemcpyHostToDevice));
     return BLINK_OK;
 }
 
@@ -264,23 +250,19 @@ blink_status workspace(blink_context* ctx, int slot, size_t bytes, void** out) {
     return BLINK_OK;
 }
 
-// exp(+2 pi i k / N), k < N, rounded from FP64; one table per image side, made on first use.
+// The twiddle set of side N (see tws_total), made on the device on first use and kept in the context.
 blink_status twiddles(blink_context* ctx, int N, float2** out) {
     int lg = 0;
     while ((1 << lg) < N) lg++;
     if (lg >= 16 || (1 << lg) != N) return set_error(BLINK_ERR_UNSUPPORTED, "twiddle table side");
     if (!ctx->tw[lg]) {
-        std::vector<float2> tw(N);
-        for (int k = 0; k < N; k++) {
-            const double ang = kTwoPi * (double)k / (double)N;
-            tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-        }
         float2* d = nullptr;
-        BLINK_CUDA(cudaMalloc(&d, sizeof(float2) * N));
-        cudaError_t e = cudaMemcpy(d, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
+        BLINK_CUDA(cudaMalloc(&d, sizeof(float2) * tws_total(N)));
+        blink_status s = make_twiddles(d, N, 0);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (s != BLINK_OK || e != cudaSuccess) {
             cudaFree(d);
-            return cuda_error(e, "cudaMemcpy(twiddles)");
+            return s != BLINK_OK ? s : cuda_error(e, "twiddle kernel");
         }
         ctx->tw[lg] = d;
     }
@@ -327,6 +309,7 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         h.bytes(a->enu_m, sizeof(double) * 3 * a->n_tiles);
         h.val(o->n_fine);
         h.val(o->chan_avg);
+        h.val(o->samples_per_int);
         h.bytes(o->fine_freq_hz, sizeof(double) * o->n_fine);
         h.val(im->n_pix);
         h.val(im->cell_lambda);
@@ -388,16 +371,12 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         if ((s = dmalloc(&p->d_freq, p->F)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_cells, (size_t)p->F * p->B)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_W, p->F)) != BLINK_OK) return fail(s);
-        if ((s = dmalloc(&p->d_tw, p->N)) != BLINK_OK) return fail(s);
-        std::vector<float2> tw(p->N);
-        for (int k = 0; k < p->N; k++) {
-            const double ang = kTwoPi * (double)k / (double)p->N;
-            tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-        }
+        if ((s = dmalloc(&p->d_Wk, p->F)) != BLINK_OK) return fail(s);
+        if ((s = dmalloc(&p->d_tw, tws_total(p->N))) != BLINK_OK) return fail(s);
         e = cudaMemcpy(p->d_enu, a->enu_m, sizeof(double) * 3 * a->n_tiles, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->d_freq, p->out_freq.data(), sizeof(double) * p->F, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(p->d_tw, tw.data(), sizeof(float2) * p->N, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(plan)"));
+        if ((s = make_twiddles(p->d_tw, p->N, st)) != BLINK_OK) return fail(s);
         launch_cells(*p, st);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -407,7 +386,12 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
             e = cudaMemcpy(cells.data(), p->d_cells, cells.size() * 4, cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(cells)"));
             if ((s = build_gather(p, cells, bl, a)) != BLINK_OK) return fail(s);
+            // the imaging path grids raw correlation sums: scale by 1 / (W * 2K) (Stokes I) or 1 / (W * K)
+            const double div = (p->pol == BLINK_POL_I ? 2.0 : 1.0) * o->samples_per_int * o->chan_avg;
+            std::vector<float> wk(p->F);
+            for (int f = 0; f < p->F; f++) wk[f] = (float)(p->W[f] * div);
             e = cudaMemcpy(p->d_W, p->W.data(), sizeof(float) * p->F, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(p->d_Wk, wk.data(), sizeof(float) * p->F, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(W)"));
         }
     }
@@ -428,41 +412,42 @@ int64_t sample_stride_bytes(const blink_obs* o, int n_tiles) {
     return (int64_t)stride * n_tiles * 2;
 }
 
-// Batched path for images [id0, id1): waves of images through correlation (the imaged products only),
-// gather-gridding fused with the column FFT, and the row FFT.
+// Batched path for the integrations [tau0, tau1) (images [tau0 F, tau1 F)), written to d_img starting at
+// image tau0 F: one correlator launch over as many integrations as the visibility workspace holds, then
+// one persistent launch that grids and transforms all of their images (fft_persistent.cu).
+constexpr size_t kVisCapBytes = (size_t)4 << 30;
+
 blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
-                         const uint8_t* d_volt, int64_t sstride, int id0, int id1, float* d_img, cudaStream_t st) {
-    const int N = p.N;
-    const int ldh = N / 2;
+                         const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st) {
+    const int N = p.N, F = p.F;
     const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
-    const size_t per_img = (size_t)N * ldh * el;
-    int wave = (int)std::max<size_t>(1, ((size_t)64 << 20) / per_img);
-    wave = std::min(wave, std::max(1, id1 - id0));
+    const int T = tau1 - tau0;
+    if (T <= 0) return BLINK_OK;
+    const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)p.B * 8 * F))));
     void* vis = nullptr;
     void* H = nullptr;
-    BLINK_TRY(workspace(ctx, 0, (size_t)wave * p.B * sizeof(float2), &vis));
-    BLINK_TRY(workspace(ctx, 1, (size_t)wave * per_img, &H));
+    void* cnt = nullptr;
+    BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));
+    BLINK_TRY(workspace(ctx, 1, (size_t)fft_ring_images() * N * (N / 2) * el, &H));
+    BLINK_TRY(workspace(ctx, 4, sizeof(int) * (2 + 2 * (size_t)t_chunk * F), &cnt));
     const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
-    for (int w0 = id0; w0 < id1; w0 += wave) {
-        const int nw = std::min(wave, id1 - w0);
+    const int out_first = tau0 * F;
+    for (int ta = tau0; ta < tau1; ta += t_chunk) {
+        const int tb = std::min(tau1, ta + t_chunk);
+        const int first = ta * F, n_items = (tb - ta) * F;
         {
             StageTimer t(ctx, BLINK_STAGE_CORRELATE, st);
             if (arith == BLINK_CORR_FP8)
-                BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B,
+                BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
                                           ctx->d_status, ctx->n_sm, st));
             else
-                BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, w0, nw, vis, p.B,
+                BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
                                            ctx->d_status, st));
         }
         {
             StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
-            BLINK_TRY(launch_colpass_gather(p, prec, static_cast<float2*>(vis), p.B, w0, nw, H, ldh, ctx->d_status,
-                                            st));
-        }
-        {
-            StageTimer t(ctx, BLINK_STAGE_ROW_FFT, st);
-            BLINK_TRY(launch_rowpass(N, prec, p.d_tw, H, ldh, 0, p.d_W, w0, p.F, nw,
-                                     d_img + (int64_t)(w0 - id0) * N * N, st));
+            BLINK_TRY(launch_fft_persistent(p, prec, static_cast<float2*>(vis), p.B, first, ta, tb - ta, H,
+                                            static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm, st));
         }
     }
     return BLINK_OK;
@@ -674,8 +659,7 @@ blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const
         BLINK_TRY(launch_colpass_grid(N, prec, tw,
                                       reinterpret_cast<const float2*>(d_grid) + (int64_t)w0 * N * (N / 2 + 1), nw, H,
                                       ldh, st));
-        BLINK_TRY(launch_rowpass(N, prec, tw, H, ldh, 1, d_weight, w0, n_images, nw,
-                                 d_img + (int64_t)w0 * N * N, st));
+        BLINK_TRY(launch_rowpass(N, prec, tw, H, ldh, 1, d_weight, n_images, WaveMap{1, 0, w0, nw}, nw, 0, d_img, st));
     }
     return BLINK_OK;
 }
@@ -703,7 +687,7 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
     const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
     const int N = p->N;
     if (mode == BLINK_MODE_BATCHED) {
-        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, d_volt, ss, 0, n_img, d_img, st));
+        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, d_volt, ss, 0, T, d_img, st));
     } else {
         const int cw = p->cw, ldh = N / 2 + cw;
         const size_t el = imaging->precision == BLINK_PREC_BF16 ? 4 : 8;
@@ -722,8 +706,8 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
             BLINK_CUDA(cudaMemsetAsync(grid, 0, (size_t)N * (N / 2 + 1) * sizeof(float2), st));
             BLINK_TRY(launch_grid_atomic(*p, static_cast<float2*>(vis), id, static_cast<float2*>(grid), st));
             BLINK_TRY(launch_colpass_grid(N, imaging->precision, p->d_tw, static_cast<float2*>(grid), 1, H, ldh, st));
-            BLINK_TRY(launch_rowpass(N, imaging->precision, p->d_tw, H, ldh, 0, p->d_W, id, p->F, 1,
-                                     d_img + (int64_t)id * N * N, st));
+            BLINK_TRY(launch_rowpass(N, imaging->precision, p->d_tw, H, ldh, 0, p->d_Wk, p->F,
+                                     WaveMap{p->F, id % p->F, id / p->F, 1}, 1, 0, d_img, st));
         }
     }
     if (d_weight) {
@@ -752,18 +736,20 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
     if (n_img == 0) return BLINK_OK;
     const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
     const size_t vbytes = (size_t)obs->n_samples * ss;
-    const int per = images_per_pass > 0 ? std::min(images_per_pass, n_img) : n_img;
+    // passes of whole integrations (F images each), at least one integration per pass
+    const int t_per = images_per_pass > 0 ? std::max(1, std::min(T, images_per_pass / p->F)) : T;
     const int N = p->N;
     void* dv = nullptr;
     void* di = nullptr;
     BLINK_TRY(workspace(ctx, 2, vbytes, &dv));
-    BLINK_TRY(workspace(ctx, 3, (size_t)per * N * N * sizeof(float), &di));
+    BLINK_TRY(workspace(ctx, 3, (size_t)t_per * p->F * N * N * sizeof(float), &di));
     BLINK_CUDA(cudaMemcpyAsync(dv, h_volt, vbytes, cudaMemcpyHostToDevice, st));
-    for (int i0 = 0; i0 < n_img; i0 += per) {
-        const int n = std::min(per, n_img - i0);
-        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, static_cast<uint8_t*>(dv), ss, i0, i0 + n,
+    for (int t0 = 0; t0 < T; t0 += t_per) {
+        const int t1 = std::min(T, t0 + t_per);
+        const size_t n = (size_t)(t1 - t0) * p->F;
+        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, static_cast<uint8_t*>(dv), ss, t0, t1,
                               static_cast<float*>(di), st));
-        BLINK_CUDA(cudaMemcpyAsync(h_img + (int64_t)i0 * N * N, di, (size_t)n * N * N * sizeof(float),
+        BLINK_CUDA(cudaMemcpyAsync(h_img + (int64_t)t0 * p->F * N * N, di, n * N * N * sizeof(float),
                                    cudaMemcpyDeviceToHost, st));
     }
     return BLINK_OK;

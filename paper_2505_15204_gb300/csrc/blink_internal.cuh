@@ -53,12 +53,12 @@ struct Plan {
     double* d_enu = nullptr;               // [n_tiles][3]
     double* d_freq = nullptr;              // [F]
     uint32_t* d_cells = nullptr;           // [F][B]
-    int* d_cell_off = nullptr;             // [F][n_cb + 1] -> index into cell arrays
-    uint32_t* d_cell_key = nullptr;        // [n_cells] (v << 16) | u
-    int* d_cell_beg = nullptr;             // [n_cells + 1] -> index into contrib
-    uint32_t* d_contrib = nullptr;         // [n_contrib] (b << 1) | conj
-    float* d_W = nullptr;                  // [F]
-    float2* d_tw = nullptr;                // [N] exp(+2 pi i k / N)
+    int* d_ent_off = nullptr;              // [F][n_cb + 1] -> index into the gather entries
+    uint2* d_ent = nullptr;                // [n_contrib] {local cell (v * cw + u - cb * cw) | conj << 31, b},
+                                           // sorted by (column block, cell, baseline)
+    float* d_W = nullptr;                  // [F] W, the sum of weights
+    float* d_Wk = nullptr;                 // [F] W times the divisor of the correlator's raw sums (2K or K)
+    float2* d_tw = nullptr;                // twiddle set of side N (tws_total(N) entries)
     double* d_uvw = nullptr;               // [F][B][3] (kept for blink_cells)
 };
 
@@ -74,7 +74,7 @@ struct blink_context {
     int n_sm = 0;
     int* d_status = nullptr;
     std::vector<blink::Plan*> plans;       // most recent last
-    blink::Workspace ws[4];
+    blink::Workspace ws[6];
     float2* tw[16] = {};                   // twiddle tables by log2(side)
     // per-stage profiling (blink_set_profiling): recorded (stage, start, stop) event pairs and a free pool
     bool profiling = false;
@@ -112,19 +112,30 @@ blink_status launch_grid_gather(const Plan& p, const float* d_vis4, int first_im
                                 int* d_status, cudaStream_t st);
 blink_status launch_grid_atomic(const Plan& p, const float2* d_visI, int image, float2* d_grid_full,
                                 cudaStream_t st);
-blink_status launch_colpass_gather(const Plan& p, int prec, const float2* d_visI, int64_t vis_stride,
-                                   int first_image, int n_images, void* d_H, int ldh, int* d_status,
-                                   cudaStream_t st);
+// A wave of images as a block of (channel, integration) pairs: wave-local image i is the image id
+// (tau0 + i % nt) * F + f0 + i / nt.  Contiguous ids are the case F = 1, f0 = 0.
+struct WaveMap {
+    int F, f0, tau0, nt;
+    __host__ __device__ int id(int i) const { return (tau0 + i % nt) * F + f0 + i / nt; }
+};
+
+// Gridding + both FFT passes of images [tau0, tau0 + n_tau) x all channels in one persistent launch;
+// d_H holds fft_ring_images() column-pass results, d_counters 2 + 2 * F * n_tau ints.
+int fft_ring_images();
+blink_status launch_fft_persistent(const Plan& p, int prec, const float2* d_vis, int64_t vis_stride, int vis_first,
+                                   int tau0, int n_tau, void* d_H, int* d_counters, float* d_img, int out_first,
+                                   int* d_status, int n_sm, cudaStream_t st);
 blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const float2* d_grid, int n_images,
                                  void* d_H, int ldh, cudaStream_t st);
 blink_status launch_rowpass(int N, int prec, const float2* d_tw, const void* d_H, int ldh, int has_nyq,
-                            const float* d_w, int w_offset, int w_mod, int n_images, float* d_img,
+                            const float* d_w, int w_mod, WaveMap wm, int n_images, int out_first, float* d_img,
                             cudaStream_t st);
 
-// output kinds of the correlators
+// output kinds of the correlators: VIS4 = the ABI visibilities V = S / K; STOKES_I and XX = the raw
+// integer sums S_XX + S_YY and S_XX (as floats) that the imaging path grids, divided later with 1/W
 enum { CORR_OUT_VIS4 = 0, CORR_OUT_STOKES_I = 1, CORR_OUT_XX = 2 };
 
-constexpr int COL_CW = 16;                 // u columns per column-pass CTA
+constexpr int COL_CW = 8;                  // u columns per column-pass CTA (one warp per column)
 
 // ------------------------------------------------------------------------------------------------
 // device helpers
@@ -188,10 +199,41 @@ template <> __device__ __forceinline__ void idft<8>(float2* v) {
 
 // One pass of a batched, in-place Stockham autosort inverse FFT in shared memory.
 // BATCH transforms of N points; point p of transform `lane` lives at s[p * PS + lane * LS].
-// NS is the product of the radices of the earlier passes.  tw[k * TWS] = exp(+2 pi i k / N).
-// Every butterfly reads its R inputs into registers, the block synchronises, then all write.
-template <int N, int R, int NS, int BATCH, int NTHR, int PS, int LS, int TWS, typename T>
-__device__ __forceinline__ void fft_pass(T* s, const float2* __restrict__ tw, int tid) {
+// NS is the product of the radices of the earlier passes; tw is the transform's per-pass twiddle table.
+// Every butterfly reads its R inputs into registers, the block synchronises, then all write: to shared
+// memory, or - for the last pass - through `out(lane, position, value)` (OUT = true).
+// LM selects the thread mapping: lane-major (consecutive threads take consecutive transforms, for
+// column layouts with LS = 1) or position-major (consecutive threads take consecutive butterflies of one
+// transform, for row layouts with PS = 1).
+// ---- twiddle tables ---------------------------------------------------------------------------------
+// Radix of the pass of an N-point transform that follows passes whose radices multiply to NS: radix 8
+// while at least 8 points remain, then the remaining factor (2 or 4).
+__host__ __device__ constexpr int radix_at(int N, int NS) { return ((N / NS) % 8 == 0) ? 8 : N / NS; }
+// Offset of the pass starting at NS in the per-pass table of an N-point transform: the pass's twiddles
+// exp(+2 pi i k r / (NS R)) sit at [(r - 1) * NS + k] for r in [1, R) and k in [0, NS), so that threads
+// with consecutive k read consecutive entries.
+__host__ __device__ constexpr int tw_off(int N, int NS) {
+    int off = 0;
+    for (int ns = 1; ns < NS; ns *= radix_at(N, ns)) off += (radix_at(N, ns) - 1) * ns;
+    return off;
+}
+__host__ __device__ constexpr int tw_size(int N) { return tw_off(N, N); }
+// Twiddle set of an image side N, in one array: [0, N/2] exp(+2 pi i k / N) (complex-to-real pre-twiddle),
+// then the per-pass table of the N-point column transform, then that of the N/2-point row transform.
+__host__ __device__ constexpr int tws_pre(int) { return 0; }
+__host__ __device__ constexpr int tws_col(int N) { return (N / 2 + 1 + 7) / 8 * 8; }
+__host__ __device__ constexpr int tws_row(int N) { return tws_col(N) + (tw_size(N) + 7) / 8 * 8; }
+__host__ __device__ constexpr int tws_total(int N) { return tws_row(N) + (tw_size(N / 2) + 7) / 8 * 8; }
+// Fill the twiddle set of side N (one kernel launch, FP64 sincospi rounded to FP32).
+blink_status make_twiddles(float2* d_out, int N, cudaStream_t st);
+
+// Padded position of point p in a transform stored with one spare slot after every 16 points: it keeps the
+// stride-R writes of the Stockham passes of a single transform free of shared-memory bank conflicts.
+__device__ __forceinline__ int padx(int p) { return p + (p >> 4); }
+
+template <int N, int R, int NS, int BATCH, int NTHR, int PS, int LS, bool LM, bool OUT, bool WARP, typename T,
+          typename Out, bool PAD = false>
+__device__ __forceinline__ void fft_pass(T* s, const float2* tw, int tid, Out& out) {
     constexpr int NB = N / R;
     constexpr int TOT = NB * BATCH;
     constexpr int PER = (TOT + NTHR - 1) / NTHR;
@@ -200,44 +242,99 @@ __device__ __forceinline__ void fft_pass(T* s, const float2* __restrict__ tw, in
     for (int m = 0; m < PER; m++) {
         const int bf = tid + m * NTHR;
         if (TOT % NTHR == 0 || bf < TOT) {
-            const int lane = bf % BATCH, j = bf / BATCH;
+            const int lane = LM ? bf % BATCH : bf / NB, j = LM ? bf / BATCH : bf % NB;
 #pragma unroll
-            for (int r = 0; r < R; r++) v[m][r] = ld_c(s + (j + r * NB) * PS + lane * LS);
+            for (int r = 0; r < R; r++) {
+                const int q = j + r * NB;
+                v[m][r] = ld_c(s + (PAD ? padx(q) : q) * PS + lane * LS);
+            }
             if (NS > 1) {
                 const int k = j % NS;
 #pragma unroll
-                for (int r = 1; r < R; r++) v[m][r] = cmul(v[m][r], __ldg(tw + (k * r * (N / (NS * R))) * TWS));
+                for (int r = 1; r < R; r++) v[m][r] = cmul(v[m][r], tw[tw_off(N, NS) + (r - 1) * NS + k]);
             }
             idft<R>(v[m]);
         }
     }
-    __syncthreads();
+    if (!OUT) {
+        if (WARP) __syncwarp(); else __syncthreads();
+    }
 #pragma unroll
     for (int m = 0; m < PER; m++) {
         const int bf = tid + m * NTHR;
         if (TOT % NTHR == 0 || bf < TOT) {
-            const int lane = bf % BATCH, j = bf / BATCH;
+            const int lane = LM ? bf % BATCH : bf / NB, j = LM ? bf / BATCH : bf % NB;
             const int d = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-            for (int r = 0; r < R; r++) st_c(s + (d + r * NS) * PS + lane * LS, v[m][r]);
+            for (int r = 0; r < R; r++) {
+                if (OUT)
+                    out(lane, d + r * NS, v[m][r]);
+                else
+                    st_c(s + (PAD ? padx(d + r * NS) : d + r * NS) * PS + lane * LS, v[m][r]);
+            }
         }
     }
-    __syncthreads();
-}
-
-// The full transform: radix-8 passes, then one pass of the remaining factor (2 or 4).
-template <int N, int NS, int BATCH, int NTHR, int PS, int LS, int TWS, typename T>
-__device__ __forceinline__ void fft_run(T* s, const float2* __restrict__ tw, int tid) {
-    if constexpr (NS < N) {
-        constexpr int REM = N / NS;
-        constexpr int R = (REM % 8 == 0) ? 8 : REM;
-        fft_pass<N, R, NS, BATCH, NTHR, PS, LS, TWS, T>(s, tw, tid);
-        fft_run<N, NS * R, BATCH, NTHR, PS, LS, TWS, T>(s, tw, tid);
+    if (!OUT) {
+        if (WARP) __syncwarp(); else __syncthreads();
     }
 }
+
+// The full transform: radix-8 passes, then one pass of the remaining factor (2 or 4).  With OUT = true
+// the last pass hands its results to `out` instead of writing shared memory.  WARP = true: the threads
+// of one warp (tid = lane, NTHR = 32) own the transforms and synchronise with __syncwarp only.
+template <int N, int NS, int BATCH, int NTHR, int PS, int LS, bool LM, bool OUT, bool WARP, typename T, typename Out,
+          bool PAD = false>
+__device__ __forceinline__ void fft_run(T* s, const float2* tw, int tid, Out& out) {
+    if constexpr (NS < N) {
+        constexpr int R = radix_at(N, NS);
+        constexpr bool LAST = NS * R == N;
+        fft_pass<N, R, NS, BATCH, NTHR, PS, LS, LM, OUT && LAST, WARP, T, Out, PAD>(s, tw, tid, out);
+        fft_run<N, NS * R, BATCH, NTHR, PS, LS, LM, OUT, WARP, T, Out, PAD>(s, tw, tid, out);
+    }
+}
+
+struct NoOut {
+    __device__ void operator()(int, int, float2) const {}
+};
 
 __device__ __forceinline__ void dev_fail(int* status, int code) {
     if (status) atomicOr(status, code);
 }
+
+// Column tile of a column-pass CTA: column c at s[c * col_ld(N)], point v at padx(v); the extra 2 slots
+// keep the row-wise store phase free of bank conflicts.
+template <int N> __host__ __device__ constexpr int col_ld() { return N + N / 16 + 2; }
+
+// Sum the gather entries [beg, end) of one column block into the tile s[v * cw + du]; `val(b)` is the
+// complex visibility of baseline b.  The first entry of each cell sums the whole cell in list order.
+template <typename T, typename Val, typename Idx>
+__device__ __forceinline__ void gather_block(const uint2* __restrict__ ent, int beg, int end, int n_cells, int tid,
+                                             int nthr, T* s, Val val, Idx idx, bool sign_shift, int cw, int u0,
+                                             int* status) {
+    for (int i = beg + tid; i < end; i += nthr) {
+        const uint2 e = ent[i];
+        const uint32_t cell = e.x & 0x7FFFFFFFu;
+        if (i > beg && (ent[i - 1].x & 0x7FFFFFFFu) == cell) continue;
+        if ((int)cell >= n_cells) {
+            dev_fail(status, DEV_ERR_INDEX);
+            continue;
+        }
+        float2 acc = make_float2(0.f, 0.f);
+        uint2 ej = e;
+        for (int j = i;;) {
+            float2 x = val(ej.y);
+            if (ej.x >> 31) x.y = -x.y;
+            acc = cadd(acc, x);
+            if (++j >= end) break;
+            ej = ent[j];
+            if ((ej.x & 0x7FFFFFFFu) != cell) break;
+        }
+        const int v = (int)cell / cw, c = (int)cell % cw;
+        if (sign_shift && ((u0 + c + v) & 1)) acc = make_float2(-acc.x, -acc.y);   // (-1)^(u+v): shift by N/2
+        st_c(s + idx(v, c), acc);
+    }
+}
+
+
 
 }  // namespace blink

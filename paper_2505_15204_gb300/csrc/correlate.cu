@@ -96,11 +96,12 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
             o[0] = make_float4(r[0], r[1], r[2], r[3]);
             o[1] = make_float4(r[4], r[5], r[6], r[7]);
         } else {
+            // imaging kinds: the exact integer sums; the 1/K (or 1/2K) is applied together with 1/W
             float2* o = static_cast<float2*>(out) + (int64_t)blockIdx.y * out_item_stride + b;
             if (OUT == CORR_OUT_STOKES_I)
-                *o = make_float2(__fdiv_rn(acc[m][0] + acc[m][6], 2.f * fk), __fdiv_rn(acc[m][1] + acc[m][7], 2.f * fk));
+                *o = make_float2(acc[m][0] + acc[m][6], acc[m][1] + acc[m][7]);
             else
-                *o = make_float2(__fdiv_rn(acc[m][0], fk), __fdiv_rn(acc[m][1], fk));
+                *o = make_float2(acc[m][0], acc[m][1]);
         }
     }
 }

@@ -42,11 +42,12 @@ constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second
 struct TcParams {
     int mode;                // CORR_OUT_*
     int n_tiles, ns, c, F, K;
+    int Kq;                  // K rounded up to a multiple of 4 (one 32-bit word of e4m3 values)
     int units, n_blk, Kr, Kp;
     int n_pairs, n_rounds;
     int first_item, n_items;
     int raw_bytes;
-    uint32_t off_raw0, off_raw1, off_re, off_im, off_lut, off_bar, off_tmem;
+    uint32_t off_raw0, off_raw1, off_re, off_im, off_lut, off_flags, off_bar, off_tmem;
     const uint8_t* flags;
     void* out;
     int64_t out_item_stride;
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
     uint8_t* ops = smem;                                   // n_blk tiles of 128 x Kp bytes
     float* st_re = reinterpret_cast<float*>(smem + P.off_re);
     float* st_im = reinterpret_cast<float*>(smem + P.off_im);
-    uint8_t* lut = smem + P.off_lut;                       // [0,16): e4m3 of nibble, [16,32): of -nibble
+    uint32_t* lut = reinterpret_cast<uint32_t*>(smem + P.off_lut);   // raw byte -> e4m3 (re, im, im, -re)
+    uint8_t* sflags = smem + P.off_flags;
     const uint32_t bar_tma0 = smem_u32(smem + P.off_bar), bar_tma1 = bar_tma0 + 8, bar_mma = bar_tma0 + 16;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + P.off_tmem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -164,12 +166,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < 32) {
-        // e4m3 of v (v in [-8, 8]): 0, 1, 2, 3, 4, 5, 6, 7 and 8, with the sign bit 0x80 for negatives
-        const uint8_t pos[9] = {0x00, 0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E, 0x50};
-        const int n = tid & 15;
-        const int v = (n >= 8 ? n - 16 : n) * (tid < 16 ? 1 : -1);
-        lut[tid] = v >= 0 ? pos[v] : (uint8_t)(0x80 | pos[-v]);
+    {
+        // e4m3 of v in [-8, 8]: 0, 1, 2, ..., 8 encoded, the sign bit 0x80 for negatives
+        const uint32_t pos[9] = {0x00, 0x38, 0x40, 0x44, 0x48, 0x4A, 0x4C, 0x4E, 0x50};
+        auto e4m3 = [&](int v) -> uint32_t { return v >= 0 ? pos[v] : (0x80u | pos[-v]); };
+        for (int b = tid; b < 256; b += kThreads) {
+            const int re = (b & 15) >= 8 ? (b & 15) - 16 : (b & 15);
+            const int im = (b >> 4) >= 8 ? (b >> 4) - 16 : (b >> 4);
+            lut[b] = e4m3(re) | (e4m3(im) << 8) | (e4m3(im) << 16) | (e4m3(-re) << 24);
+        }
+        for (int a = tid; a < P.n_tiles; a += kThreads) sflags[a] = P.flags[a] ? 1 : 0;
     }
     {
         uint4* z = reinterpret_cast<uint4*>(ops);
@@ -221,29 +227,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             abort = true;
             break;
         }
-        // ---- unpack nibbles to e4m3 operand rows -------------------------------------------------------
+        // ---- unpack nibbles to e4m3 operand rows, four consecutive k per 32-bit store -----------------
+        // A task is (k group g, tile a, polarisation p): its four raw bytes give, through the LUT, the words
+        // P_re, P_im (= Q_im) and Q_-re of four consecutive K positions of one unit row.
         const uint8_t* raw = smem + (buf ? P.off_raw1 : P.off_raw0);
-        const int n_el = P.K * per_k;
-        for (int e = tid; e < n_el; e += kThreads) {
-            const int k = e / per_k, rem = e - (e / per_k) * per_k;
-            const int a = rem >> 1, p = rem & 1;
-            int unit, kp, kh;
-            if (P.mode == CORR_OUT_STOKES_I) {
-                unit = a; kp = p * P.K + k; kh = 2 * P.K;
-            } else if (P.mode == CORR_OUT_VIS4) {
-                unit = 2 * a + p; kp = k; kh = P.K;
-            } else {
-                if (p) continue;
-                unit = a; kp = k; kh = P.K;
+        const int n_groups = P.Kq >> 2;
+        for (int g = 0; g < n_groups; g++) {
+            const int k0 = 4 * g;
+            for (int r = tid; r < per_k; r += kThreads) {
+                const int a = r >> 1, p = r & 1;
+                int unit, kp, kh;
+                if (P.mode == CORR_OUT_STOKES_I) {
+                    unit = a; kp = p * P.Kq + k0; kh = 2 * P.Kq;
+                } else if (P.mode == CORR_OUT_VIS4) {
+                    unit = 2 * a + p; kp = k0; kh = P.Kq;
+                } else {
+                    if (p) continue;
+                    unit = a; kp = k0; kh = P.Kq;
+                }
+                uint32_t w[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) w[i] = (k0 + i < P.K) ? lut[raw[(k0 + i) * per_k + r]] : 0u;
+                const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], 0x0040), __byte_perm(w[2], w[3], 0x0040), 0x5410);
+                const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], 0x0051), __byte_perm(w[2], w[3], 0x0051), 0x5410);
+                const uint32_t nre = __byte_perm(__byte_perm(w[0], w[1], 0x0073), __byte_perm(w[2], w[3], 0x0073), 0x5410);
+                uint8_t* tile = ops + (unit >> 6) * tile_bytes;
+                const int row = unit & 63;
+                *reinterpret_cast<uint32_t*>(tile + op_off(row, kp, P.Kp)) = re;
+                *reinterpret_cast<uint32_t*>(tile + op_off(row, kp + kh, P.Kp)) = im;
+                *reinterpret_cast<uint32_t*>(tile + op_off(row + 64, kp, P.Kp)) = im;
+                *reinterpret_cast<uint32_t*>(tile + op_off(row + 64, kp + kh, P.Kp)) = nre;
             }
-            const uint32_t byte = raw[e];
-            const uint8_t re8 = lut[byte & 15], im8 = lut[byte >> 4], nre8 = lut[16 + (byte & 15)];
-            uint8_t* tile = ops + (unit >> 6) * tile_bytes;
-            const int r = unit & 63;
-            tile[op_off(r, kp, P.Kp)] = re8;
-            tile[op_off(r, kp + kh, P.Kp)] = im8;
-            tile[op_off(r + 64, kp, P.Kp)] = im8;
-            tile[op_off(r + 64, kp + kh, P.Kp)] = nre8;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -292,17 +306,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                         if (ui >= P.units) continue;
                         const int ai = ui >> 1, aj = uj >> 1;
                         if (aj > ai) continue;
-                        if (P.flags[ai] || P.flags[aj]) re = im = 0.f;
+                        if (sflags[ai] | sflags[aj]) re = im = 0.f;
                         const int64_t b = (int64_t)ai * (ai + 1) / 2 + aj;
                         float* o = static_cast<float*>(P.out) + (int64_t)local * P.out_item_stride +
                                    (b * 4 + 2 * (ui & 1) + (uj & 1)) * 2;
                         *reinterpret_cast<float2*>(o) = make_float2(__fdiv_rn(re, div), __fdiv_rn(im, div));
                     } else {
+                        // imaging kinds: the exact integer sums; the 1/K (or 1/2K) is applied with 1/W
                         if (ui >= P.n_tiles || uj > ui) continue;
-                        if (P.flags[ui] || P.flags[uj]) re = im = 0.f;
+                        if (sflags[ui] | sflags[uj]) re = im = 0.f;
                         const int64_t b = (int64_t)ui * (ui + 1) / 2 + uj;
-                        static_cast<float2*>(P.out)[(int64_t)local * P.out_item_stride + b] =
-                            make_float2(__fdiv_rn(re, div), __fdiv_rn(im, div));
+                        static_cast<float2*>(P.out)[(int64_t)local * P.out_item_stride + b] = make_float2(re, im);
                     }
                 }
                 __syncthreads();
@@ -361,7 +375,8 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     P.K = K;
     P.units = out_kind == CORR_OUT_VIS4 ? 2 * nt : nt;
     P.n_blk = (P.units + kUnitsPerBlk - 1) / kUnitsPerBlk;
-    P.Kr = out_kind == CORR_OUT_STOKES_I ? 4 * K : 2 * K;
+    P.Kq = (K + 3) / 4 * 4;
+    P.Kr = out_kind == CORR_OUT_STOKES_I ? 4 * P.Kq : 2 * P.Kq;
     P.Kp = (P.Kr + 31) / 32 * 32;
     P.n_pairs = P.n_blk * (P.n_blk + 1) / 2;
     P.n_rounds = (P.n_pairs + kPairsPerRound - 1) / kPairsPerRound;
@@ -378,7 +393,9 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     P.off_im = off;
     off = align_up(off + 64 * kStageLd * 4, 16);
     P.off_lut = off;
-    off += 32;
+    off += 256 * 4;
+    P.off_flags = off;
+    off = align_up(off + nt, 16);
     P.off_bar = off;
     off += 24;
     P.off_tmem = off;

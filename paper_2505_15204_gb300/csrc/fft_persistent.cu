@@ -1,0 +1,254 @@
+// Gridding and the batched 2D inverse FFT of a whole correlated chunk in one persistent launch.
+//
+// The work is two kinds of task per image (Sec. 5.2.4, Eq. 4):
+//   column task (image k, column block cb): gather-grid the block's 8 u-columns in shared memory and
+//       transform each along v (one warp per column), then write the block to the image's slot of a
+//       small ring of intermediates (kept in L2);
+//   row task (image k, row block rb): once all column tasks of image k are done, transform 8 rows
+//       along u (complex to real, one warp per row), scale by 1 / (W * 2K) and write the image rows.
+// CTAs take task tickets in order from a global counter.  The ticket stream is cut into segments of
+// (column tasks of image s) + (row tasks of image s - lag), so an image's row tasks come `lag` segments
+// after its column tasks.  Dependencies are per-image counters: a row task waits for the image's column
+// tasks, and a column task that reuses a ring slot waits for the previous occupant's row tasks.  A task
+// only ever waits on tasks with smaller tickets, which resident CTAs already hold, so the waits always
+// end; they are nevertheless bounded, and on expiry the launch records BLINK_ERR_TIMEOUT and every CTA
+// stops taking tickets.
+#include <algorithm>
+
+#include "blink_internal.cuh"
+
+namespace blink {
+
+namespace {
+
+constexpr int kPT = 256;                         // threads: 8 warps
+constexpr int kRB = 8;                           // rows per row task (one per warp)
+constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
+
+struct FftParams {
+    const float2* vis;       // correlation sums of the chunk's images, [item][B]
+    int64_t vis_stride;
+    int vis_first;           // image id of vis row 0
+    int F, tau0, n_tau;      // images: channel-major order k -> (f = k / n_tau, tau = tau0 + k % n_tau)
+    int n_img;
+    int n_cb, n_rb;          // column tasks and row tasks per image
+    const int* ent_off;      // [F][n_cb + 1]
+    const uint2* ent;        // gather entries
+    const float2* tw;        // twiddle set of side N
+    void* H;                 // ring of column-pass results, [ring][N][ldh]
+    int ldh, ring, lag;
+    const float* wk;         // [F] W * 2K (or W * K)
+    float* img_out;
+    int out_first;           // image id of img_out's first image
+    int* tickets;            // counters, zeroed before the launch: [0] ticket, [1] abort,
+    int* col_done;           //   [n_img] column tasks finished per image
+    int* row_done;           //   [n_img] row tasks finished per image
+    int* status;
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float2 ldcg_c(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ldcg_c(const __nv_bfloat162* p) {
+    const unsigned u = __ldcg(reinterpret_cast<const unsigned*>(p));
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
+}
+
+// Thread 0 waits (bounded) until *cnt reaches `target`; the verdict is shared with the whole CTA.
+__device__ bool wait_count(const FftParams& P, const int* cnt, int target, int* s_flag) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire(cnt) < target) {
+            if (clock64() - t0 > kWaitBudget || ld_acquire(P.tickets + 1)) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (!ok) {
+            atomicOr(P.status, DEV_ERR_TIMEOUT);
+            atomicExch(P.tickets + 1, 1);
+        }
+        *s_flag = ok;
+    }
+    __syncthreads();
+    const bool ok = *s_flag != 0;
+    __syncthreads();
+    return ok;
+}
+
+template <int N, typename T>
+__device__ void column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
+                            int* s_flag) {
+    constexpr int CW = COL_CW, LD = col_ld<N>();
+    const int tid = threadIdx.x;
+    const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
+    const int slot = k % P.ring;
+    if (k >= P.ring && !wait_count(P, P.row_done + (k - P.ring), P.n_rb, s_flag)) return;
+    T* s = reinterpret_cast<T*>(work);
+    for (int e = tid; e < CW * LD; e += kPT) st_c(s + e, make_float2(0.f, 0.f));
+    __syncthreads();
+    const float2* V = P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
+    auto val = [&](uint32_t b) { return __ldg(V + b); };
+    auto idx = [&](int v, int c) { return c * LD + padx(v); };
+    gather_block(P.ent, P.ent_off[f * (P.n_cb + 1) + cb], P.ent_off[f * (P.n_cb + 1) + cb + 1], N * CW, tid, kPT, s,
+                 val, idx, true, CW, cb * CW, P.status);
+    __syncthreads();
+    NoOut none;
+    fft_run<N, 1, 1, 32, 1, 0, true, false, true, T, NoOut, true>(s + (tid >> 5) * LD, s_twc, tid & 31, none);
+    __syncthreads();
+    T* out = static_cast<T*>(P.H) + (int64_t)slot * N * P.ldh + cb * CW;
+    for (int e = tid; e < N * CW; e += kPT) {
+        const int y = e / CW, c = e % CW;
+        out[(int64_t)y * P.ldh + c] = s[c * LD + padx(y)];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(P.col_done + k, 1);
+}
+
+template <int N, typename T>
+__device__ void row_task(const FftParams& P, int k, int rb, const float2* s_pre, const float2* s_twr,
+                         unsigned char* work, int* s_flag) {
+    constexpr int M = N / 2, LS = M + M / 16 + 2;
+    const int tid = threadIdx.x, r = tid >> 5, lane = tid & 31;
+    const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
+    const int slot = k % P.ring;
+    if (!wait_count(P, P.col_done + k, P.n_cb, s_flag)) return;
+    const int y = rb * kRB + r;
+    const T* row = static_cast<const T*>(P.H) + ((int64_t)slot * N + y) * P.ldh;
+    float2* dst = reinterpret_cast<float2*>(work) + r * LS;
+    for (int q = lane; q <= M / 2; q += 32) {
+        const float2 zk = ldcg_c(row + q);
+        const float2 zm = (q == 0) ? make_float2(0.f, 0.f) : ldcg_c(row + (M - q));
+        dst[padx(q)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), s_pre[q])));
+        if (q > 0 && q < M - q)
+            dst[padx(M - q)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), s_pre[M - q])));
+    }
+    __syncwarp();
+    const float w = P.wk[f];
+    const float inv = 1.0f / (w > 0.f ? w : 1.f);
+    float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
+    auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
+    fft_run<M, 1, 1, 32, 1, 0, false, true, true, float2, decltype(store), true>(dst, s_twr, lane, store);
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        atomicAdd(P.row_done + k, 1);
+    }
+}
+
+__host__ __device__ constexpr int even(int x) { return (x + 1) / 2 * 2; }
+
+template <int N, typename T> constexpr size_t fft_smem() {
+    constexpr int M = N / 2;
+    constexpr size_t tw = (size_t)(even(tw_size(N)) + even(M + 1) + even(tw_size(M))) * sizeof(float2);
+    constexpr size_t col = (size_t)COL_CW * col_ld<N>() * sizeof(T);
+    constexpr size_t row = (size_t)kRB * (M + M / 16 + 2) * sizeof(float2);
+    return tw + (col > row ? col : row);
+}
+
+// Four CTAs per SM for sides up to 512 (measured faster than three, despite a few register spills).
+template <int N, typename T>
+__global__ void __launch_bounds__(kPT, (N <= 512 ? 4 : 1)) k_fft_persistent(const FftParams P) {
+    constexpr int M = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* s_twc = reinterpret_cast<float2*>(smem_raw);
+    float2* s_pre = s_twc + even(tw_size(N));
+    float2* s_twr = s_pre + even(M + 1);
+    unsigned char* work = reinterpret_cast<unsigned char*>(s_twr + even(tw_size(M)));
+    __shared__ int s_ticket, s_flag;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < tw_size(N); e += kPT) s_twc[e] = P.tw[tws_col(N) + e];
+    for (int e = tid; e <= M; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
+    for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
+    const int seg = P.n_cb + P.n_rb;
+    const int total = (P.n_img + P.lag) * seg;
+    for (;;) {
+        if (tid == 0) {
+            int t = atomicAdd(P.tickets, 1);
+            if (ld_acquire(P.tickets + 1)) t = total;
+            s_ticket = t;
+        }
+        __syncthreads();
+        const int t = s_ticket;
+        __syncthreads();
+        if (t >= total) break;
+        const int sg = t / seg, r = t - sg * seg;
+        if (r < P.n_cb) {
+            if (sg < P.n_img) column_task<N, T>(P, sg, r, s_twc, work, &s_flag);
+        } else {
+            const int k = sg - P.lag;
+            if (k >= 0 && k < P.n_img) row_task<N, T>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
+        }
+    }
+}
+
+template <int N, typename T>
+blink_status launch_n(FftParams P, int n_sm, cudaStream_t st) {
+    auto kern = k_fft_persistent<N, T>;
+    const size_t smem = fft_smem<N, T>();
+    if (smem > 48 * 1024) BLINK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int per_sm = 0;
+    BLINK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem));
+    if (per_sm < 1) return set_error(BLINK_ERR_UNSUPPORTED, "persistent FFT kernel does not fit on an SM");
+    P.n_cb = N / 2 / COL_CW;
+    P.n_rb = N / kRB;
+    kern<<<n_sm * per_sm, kPT, smem, st>>>(P);
+    BLINK_CUDA(cudaGetLastError());
+    return BLINK_OK;
+}
+
+}  // namespace
+
+// Ring of column-pass results and the lag (in images) between an image's column and row tasks.  Task
+// durations vary a lot, so the row tasks trail by many images to rarely wait; the ring is a little larger
+// than the lag so that reusing a slot rarely waits either (80 images of 512^2 in FP32 = 84 MB, in L2).
+constexpr int kRing = 80, kLag = 64;
+int fft_ring_images() { return kRing; }
+
+blink_status launch_fft_persistent(const Plan& p, int prec, const float2* d_vis, int64_t vis_stride, int vis_first,
+                                   int tau0, int n_tau, void* d_H, int* d_counters, float* d_img, int out_first,
+                                   int* d_status, int n_sm, cudaStream_t st) {
+    FftParams P{};
+    P.vis = d_vis;
+    P.vis_stride = vis_stride;
+    P.vis_first = vis_first;
+    P.F = p.F;
+    P.tau0 = tau0;
+    P.n_tau = n_tau;
+    P.n_img = p.F * n_tau;
+    P.ent_off = p.d_ent_off;
+    P.ent = p.d_ent;
+    P.tw = p.d_tw;
+    P.H = d_H;
+    P.ldh = p.N / 2;
+    P.ring = kRing;
+    P.lag = kLag;
+    P.wk = p.d_Wk;
+    P.img_out = d_img;
+    P.out_first = out_first;
+    P.tickets = d_counters;
+    P.col_done = d_counters + 2;
+    P.row_done = d_counters + 2 + P.n_img;
+    P.status = d_status;
+    BLINK_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int) * (2 + 2 * (size_t)P.n_img), st));
+    const bool bf = prec == BLINK_PREC_BF16;
+    switch (p.N) {
+        case 64: return bf ? launch_n<64, __nv_bfloat162>(P, n_sm, st) : launch_n<64, float2>(P, n_sm, st);
+        case 128: return bf ? launch_n<128, __nv_bfloat162>(P, n_sm, st) : launch_n<128, float2>(P, n_sm, st);
+        case 256: return bf ? launch_n<256, __nv_bfloat162>(P, n_sm, st) : launch_n<256, float2>(P, n_sm, st);
+        case 512: return bf ? launch_n<512, __nv_bfloat162>(P, n_sm, st) : launch_n<512, float2>(P, n_sm, st);
+        case 1024: return bf ? launch_n<1024, __nv_bfloat162>(P, n_sm, st) : launch_n<1024, float2>(P, n_sm, st);
+        case 2048: return bf ? launch_n<2048, __nv_bfloat162>(P, n_sm, st) : launch_n<2048, float2>(P, n_sm, st);
+    }
+    return set_error(BLINK_ERR_UNSUPPORTED, "image side must be a power of two in [64, 2048]");
+}
+
+}  // namespace blink

@@ -9,8 +9,10 @@
 // grid (a shift by N/2 in both image axes), so the passes need no index remapping.
 //
 // Gridding never uses atomics in the batched form: a precomputed, cell-sorted gather list (one entry per
-// visibility and mirror that lands in the half plane) lets one thread own each non-empty cell and sum
-// its contributions in a fixed order, in shared memory, right before the column FFT of that tile.
+// visibility and mirror that lands in the half plane) lets the thread holding the first entry of each
+// cell sum that cell's contributions in a fixed order, in shared memory, right before the column FFT of
+// that tile.  Each warp then transforms one column (or, in the row pass, one row) on its own, so the
+// FFT passes synchronise with __syncwarp only.
 #include <algorithm>
 
 #include "blink_internal.cuh"
@@ -26,8 +28,7 @@ constexpr int kGridThreads = 256;
 
 __global__ void __launch_bounds__(kGridThreads)
 k_grid_gather(const float* __restrict__ vis4, int64_t B, int F, int first_image, int pol, int N, int cw,
-              int n_cb, const int* __restrict__ cell_off, const uint32_t* __restrict__ cell_key,
-              const int* __restrict__ cell_beg, const uint32_t* __restrict__ contrib, float2* __restrict__ grid,
+              int n_cb, const int* __restrict__ ent_off, const uint2* __restrict__ ent, float2* __restrict__ grid,
               int* status) {
     extern __shared__ float2 sg[];                       // [N][cw]
     const int img = blockIdx.y, cb = blockIdx.x, tid = threadIdx.x;
@@ -36,26 +37,14 @@ k_grid_gather(const float* __restrict__ vis4, int64_t B, int F, int first_image,
     for (int e = tid; e < N * cw; e += kGridThreads) sg[e] = make_float2(0.f, 0.f);
     __syncthreads();
     if (cb < n_cb) {
-        const int beg = cell_off[f * (n_cb + 1) + cb], end = cell_off[f * (n_cb + 1) + cb + 1];
         const float* V = vis4 + (int64_t)img * B * 8;
-        for (int c = beg + tid; c < end; c += kGridThreads) {
-            const uint32_t key = cell_key[c];
-            const int v = key >> 16, u = key & 0xFFFF;
-            if (v >= N || u < u0 || u >= u0 + cw) {
-                dev_fail(status, DEV_ERR_INDEX);
-                continue;
-            }
-            float2 acc = make_float2(0.f, 0.f);
-            for (int k = cell_beg[c]; k < cell_beg[c + 1]; k++) {
-                const uint32_t w = contrib[k];
-                const float* p = V + (int64_t)(w >> 1) * 8;
-                float2 val = (pol == BLINK_POL_I) ? make_float2(0.5f * (p[0] + p[6]), 0.5f * (p[1] + p[7]))
-                                                  : make_float2(p[0], p[1]);
-                if (w & 1) val.y = -val.y;
-                acc = cadd(acc, val);
-            }
-            sg[v * cw + (u - u0)] = acc;
-        }
+        auto val = [&](uint32_t b) {
+            const float* q = V + (int64_t)b * 8;
+            return (pol == BLINK_POL_I) ? make_float2(0.5f * (q[0] + q[6]), 0.5f * (q[1] + q[7])) : make_float2(q[0], q[1]);
+        };
+        auto idx = [&](int v, int c) { return v * cw + c; };
+        gather_block(ent, ent_off[f * (n_cb + 1) + cb], ent_off[f * (n_cb + 1) + cb + 1], N * cw, tid, kGridThreads, sg,
+                     val, idx, false, cw, u0, status);
     }
     __syncthreads();
     const int ncols = min(cw, half + 1 - u0);
@@ -102,61 +91,19 @@ __global__ void k_grid_atomic(const float2* __restrict__ vis, int64_t B, const u
 }
 
 // ---------------------------------------------------------------------------------------------------
-// column pass, fused with gather gridding (pipeline): one CTA per (image, block of CW u-columns)
-// ---------------------------------------------------------------------------------------------------
-template <int N, int CW, int NTHR, typename T>
-__global__ void __launch_bounds__(NTHR)
-k_colpass_gather(const float2* __restrict__ vis, int64_t vis_stride, int F, int first_image, int n_cb,
-                 const int* __restrict__ cell_off, const uint32_t* __restrict__ cell_key,
-                 const int* __restrict__ cell_beg, const uint32_t* __restrict__ contrib,
-                 const float2* __restrict__ tw, T* __restrict__ H, int ldh, int* status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* s = reinterpret_cast<T*>(smem_raw);                 // [N][CW]
-    const int img = blockIdx.y, cb = blockIdx.x, tid = threadIdx.x;
-    const int f = (first_image + img) % F;
-    const int u0 = cb * CW;
-    for (int e = tid; e < N * CW; e += NTHR) st_c(s + e, make_float2(0.f, 0.f));
-    __syncthreads();
-    {
-        const int beg = cell_off[f * (n_cb + 1) + cb], end = cell_off[f * (n_cb + 1) + cb + 1];
-        const float2* V = vis + (int64_t)img * vis_stride;
-        for (int c = beg + tid; c < end; c += NTHR) {
-            const uint32_t key = cell_key[c];
-            const int v = key >> 16, u = key & 0xFFFF;
-            if (v >= N || u < u0 || u >= u0 + CW) {
-                dev_fail(status, DEV_ERR_INDEX);
-                continue;
-            }
-            float2 acc = make_float2(0.f, 0.f);
-            const int k1 = cell_beg[c + 1];
-            for (int k = cell_beg[c]; k < k1; k++) {
-                const uint32_t w = __ldg(contrib + k);
-                float2 val = __ldg(V + (w >> 1));
-                if (w & 1) val.y = -val.y;
-                acc = cadd(acc, val);
-            }
-            if ((u + v) & 1) acc = make_float2(-acc.x, -acc.y);   // (-1)^(u+v): image shift by N/2
-            st_c(s + v * CW + (u - u0), acc);
-        }
-    }
-    __syncthreads();
-    fft_run<N, 1, CW, NTHR, CW, 1, 1, T>(s, tw, tid);
-    T* out = H + (int64_t)img * N * ldh + u0;
-    for (int e = tid; e < N * CW; e += NTHR) {
-        const int y = e / CW, cc = e % CW;
-        out[(int64_t)y * ldh + cc] = s[e];
-    }
-}
-
 // column pass reading a stored half-plane grid (blink_image and the plain form)
 template <int N, int CW, int NTHR, typename T>
-__global__ void __launch_bounds__(NTHR)
+__global__ void __launch_bounds__(NTHR, (N <= 256 ? 4 : (N <= 512 ? 3 : 1)))
 k_colpass_grid(const float2* __restrict__ grid, const float2* __restrict__ tw, T* __restrict__ H, int ldh) {
+    static_assert(NTHR == 32 * CW, "one warp per column");
+    constexpr int LD = col_ld<N>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* s = reinterpret_cast<T*>(smem_raw);                 // [N][CW]
+    float2* stw = reinterpret_cast<float2*>(smem_raw);                 // column-transform twiddle table
+    T* s = reinterpret_cast<T*>(smem_raw + (tw_size(N) + 1) / 2 * 2 * sizeof(float2));   // [CW][LD]
     const int img = blockIdx.y, cb = blockIdx.x, tid = threadIdx.x;
     const int u0 = cb * CW, half = N / 2;
     const float2* G = grid + (int64_t)img * N * (half + 1);
+    for (int e = tid; e < tw_size(N); e += NTHR) stw[e] = tw[tws_col(N) + e];
     for (int e = tid; e < N * CW; e += NTHR) {
         const int v = e / CW, cc = e % CW, u = u0 + cc;
         float2 val = make_float2(0.f, 0.f);
@@ -164,14 +111,16 @@ k_colpass_grid(const float2* __restrict__ grid, const float2* __restrict__ tw, T
             val = G[(int64_t)v * (half + 1) + u];
             if ((u + v) & 1) val = make_float2(-val.x, -val.y);
         }
-        st_c(s + e, val);
+        st_c(s + cc * LD + padx(v), val);
     }
     __syncthreads();
-    fft_run<N, 1, CW, NTHR, CW, 1, 1, T>(s, tw, tid);
+    NoOut none;
+    fft_run<N, 1, 1, 32, 1, 0, true, false, true, T, NoOut, true>(s + (tid >> 5) * LD, stw, tid & 31, none);
+    __syncthreads();
     T* out = H + (int64_t)img * N * ldh + u0;
     for (int e = tid; e < N * CW; e += NTHR) {
-        const int y = e / CW, cc = e % CW;
-        out[(int64_t)y * ldh + cc] = s[e];
+        const int y = e / CW, c = e % CW;
+        out[(int64_t)y * ldh + c] = s[c * LD + padx(y)];
     }
 }
 
@@ -184,74 +133,53 @@ k_colpass_grid(const float2* __restrict__ grid, const float2* __restrict__ tw, T
 // ---------------------------------------------------------------------------------------------------
 template <int N, int RB, int NTHR, typename T>
 __global__ void __launch_bounds__(NTHR)
-k_rowpass(const T* __restrict__ H, int ldh, int has_nyq, const float* __restrict__ wts, int w_offset, int w_mod,
-          const float2* __restrict__ tw, float* __restrict__ img_out) {
+k_rowpass(const T* __restrict__ H, int ldh, int has_nyq, const float* __restrict__ wts, int w_mod, WaveMap wm,
+          int out_first, const float2* __restrict__ tw, float* __restrict__ img_out) {
+    static_assert(NTHR == 32 * RB, "one warp per row");
     constexpr int M = N / 2;
-    constexpr int LS = M + 1;
+    constexpr int LS = M + M / 16 + 2;          // padded row (padx) with room for the Nyquist slot
+    __shared__ float2 spre[M + 1];              // exp(+2 pi i k / N), k in [0, M]
+    __shared__ float2 stw[tw_size(M)];          // row-transform twiddle table
     __shared__ float2 s[RB * LS];
     const int img = blockIdx.y, y0 = blockIdx.x * RB, tid = threadIdx.x;
-    const T* src = H + ((int64_t)img * N + y0) * ldh;
-    for (int e = tid; e < RB * M; e += NTHR) {
-        const int r = e / M, k = e % M;
-        s[r * LS + k] = ld_c(src + (int64_t)r * ldh + k);
-    }
-    for (int r = tid; r < RB; r += NTHR) s[r * LS + M] = has_nyq ? ld_c(src + (int64_t)r * ldh + M) : make_float2(0.f, 0.f);
+    const int r = tid >> 5, lane = tid & 31;
+    for (int e = tid; e <= M; e += NTHR) spre[e] = tw[tws_pre(N) + e];
+    for (int e = tid; e < tw_size(M); e += NTHR) stw[e] = tw[tws_row(N) + e];
     __syncthreads();
-    constexpr int PAIRS = M / 2 + 1;
-    for (int e = tid; e < RB * PAIRS; e += NTHR) {
-        const int r = e / PAIRS, k = e % PAIRS;
-        float2* row = s + r * LS;
-        const float2 zk = row[k], zm = row[M - k];
-        const float2 yk = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), __ldg(tw + k))));
-        if (k > 0 && k < M - k) {
-            const float2 ym = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), __ldg(tw + (M - k)))));
-            row[M - k] = ym;
-        }
-        row[k] = yk;
+    // this warp's row: load the half spectrum and form the M-point input of the complex-to-real transform
+    const T* row = H + ((int64_t)img * N + y0 + r) * ldh;
+    float2* dst = s + r * LS;
+    for (int k = lane; k <= M / 2; k += 32) {
+        const float2 zk = ld_c(row + k);
+        const float2 zm = (k == 0) ? (has_nyq ? ld_c(row + M) : make_float2(0.f, 0.f)) : ld_c(row + (M - k));
+        dst[padx(k)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), spre[k])));
+        if (k > 0 && k < M - k)
+            dst[padx(M - k)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), spre[M - k])));
     }
-    __syncthreads();
-    fft_run<M, 1, RB, NTHR, 1, LS, 2, float2>(s, tw, tid);
-    float w = wts[(w_offset + img) % w_mod];
+    __syncwarp();
+    const int id = wm.id(img);
+    float w = wts[id % w_mod];
     const float inv = 1.0f / (w > 0.f ? w : 1.f);
-    float2* out = reinterpret_cast<float2*>(img_out + ((int64_t)img * N + y0) * N);
-    for (int e = tid; e < RB * M; e += NTHR) {
-        const int r = e / M, m = e % M;
-        const float2 y = s[r * LS + m];
-        out[(int64_t)r * M + m] = make_float2(y.x * inv, y.y * inv);
-    }
+    float2* out = reinterpret_cast<float2*>(img_out + ((int64_t)(id - out_first) * N + y0 + r) * N);
+    auto store = [&](int, int m, float2 y) { out[m] = make_float2(y.x * inv, y.y * inv); };
+    fft_run<M, 1, 1, 32, 1, 0, false, true, true, float2, decltype(store), true>(dst, stw, lane, store);
 }
 
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
-constexpr int col_threads(int N) { return N >= 512 ? 512 : 256; }
-constexpr int col_cw(int N) { return N >= 2048 ? 8 : COL_CW; }
-constexpr int row_rb(int N) { return N >= 2048 ? 4 : (N >= 1024 ? 8 : 16); }
-
-template <int N, typename T>
-blink_status colpass_gather_n(const Plan& p, const float2* vis, int64_t vis_stride, int first_image, int n_images,
-                              void* H, int ldh, int* status, cudaStream_t st) {
-    constexpr int CW = col_cw(N), NT = col_threads(N);
-    auto kern = k_colpass_gather<N, CW, NT, T>;
-    const size_t smem = (size_t)N * CW * sizeof(T);
-    set_smem(kern, smem);
-    for (int i0 = 0; i0 < n_images; i0 += 65535) {
-        const int n = std::min(65535, n_images - i0);
-        kern<<<dim3(p.n_cb, n), NT, smem, st>>>(vis + (int64_t)i0 * vis_stride, vis_stride, p.F, first_image + i0,
-                                                p.n_cb, p.d_cell_off, p.d_cell_key, p.d_cell_beg, p.d_contrib,
-                                                p.d_tw, static_cast<T*>(H) + (int64_t)i0 * N * ldh, ldh, status);
-    }
-    BLINK_CUDA(cudaGetLastError());
-    return BLINK_OK;
-}
+constexpr int col_threads(int) { return 32 * COL_CW; }
+constexpr int col_cw(int N) { return COL_CW; }
+constexpr int row_rb(int N) { return N >= 2048 ? 2 : 8; }
 
 template <int N, typename T>
 blink_status colpass_grid_n(const float2* tw, const float2* grid, int n_images, void* H, int ldh, cudaStream_t st) {
     constexpr int CW = col_cw(N), NT = col_threads(N);
     auto kern = k_colpass_grid<N, CW, NT, T>;
-    const size_t smem = (size_t)N * CW * sizeof(T);
+    const size_t smem = (size_t)col_ld<N>() * CW * sizeof(T) + (tw_size(N) + 1) / 2 * 2 * sizeof(float2);
     set_smem(kern, smem);
     const int nb = (N / 2 + 1 + CW - 1) / CW;
     for (int i0 = 0; i0 < n_images; i0 += 65535) {
@@ -264,15 +192,13 @@ blink_status colpass_grid_n(const float2* tw, const float2* grid, int n_images, 
 }
 
 template <int N, typename T>
-blink_status rowpass_n(const float2* tw, const void* H, int ldh, int has_nyq, const float* w, int w_offset, int w_mod,
-                       int n_images, float* img, cudaStream_t st) {
+blink_status rowpass_n(const float2* tw, const void* H, int ldh, int has_nyq, const float* w, int w_mod, WaveMap wm,
+                       int n_images, int out_first, float* img, cudaStream_t st) {
     constexpr int RB = row_rb(N);
-    for (int i0 = 0; i0 < n_images; i0 += 65535) {
-        const int n = std::min(65535, n_images - i0);
-        k_rowpass<N, RB, 256, T><<<dim3(N / RB, n), 256, 0, st>>>(
-            static_cast<const T*>(H) + (int64_t)i0 * N * ldh, ldh, has_nyq, w, w_offset + i0, w_mod, tw,
-            img + (int64_t)i0 * N * N);
-    }
+    set_smem(k_rowpass<N, RB, 32 * RB, T>, 0);
+    if (n_images > 65535) return set_error(BLINK_ERR_UNSUPPORTED, "wave of more than 65535 images");
+    k_rowpass<N, RB, 32 * RB, T><<<dim3(N / RB, n_images), 32 * RB, 0, st>>>(static_cast<const T*>(H), ldh, has_nyq, w,
+                                                                             w_mod, wm, out_first, tw, img);
     BLINK_CUDA(cudaGetLastError());
     return BLINK_OK;
 }
@@ -290,7 +216,47 @@ blink_status rowpass_n(const float2* tw, const void* H, int ldh, int has_nyq, co
 
 }  // namespace
 
-int col_block_width(int N) { return N >= 2048 ? 8 : COL_CW; }
+int col_block_width(int) { return COL_CW; }
+
+namespace {
+__device__ float2 unit_root(int k, int n) {     // exp(+2 pi i k / n), FP64 sincospi rounded to FP32
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)n, &sn, &cs);
+    return make_float2((float)cs, (float)sn);
+}
+
+__device__ float2 pass_twiddle(int N, int e) {  // entry e of the per-pass table of an N-point transform
+    for (int ns = 1; ns < N; ns *= radix_at(N, ns)) {
+        const int R = radix_at(N, ns), sz = (R - 1) * ns;
+        if (e < sz) {
+            const int r = e / ns + 1, k = e % ns;
+            return unit_root(k * r, ns * R);
+        }
+        e -= sz;
+    }
+    return make_float2(1.f, 0.f);
+}
+
+__global__ void k_make_twiddles(float2* out, int N) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= tws_total(N)) return;
+    float2 v = make_float2(0.f, 0.f);
+    if (e < tws_col(N)) {
+        if (e <= N / 2) v = unit_root(e, N);
+    } else if (e < tws_row(N)) {
+        if (e - tws_col(N) < tw_size(N)) v = pass_twiddle(N, e - tws_col(N));
+    } else if (e - tws_row(N) < tw_size(N / 2)) {
+        v = pass_twiddle(N / 2, e - tws_row(N));
+    }
+    out[e] = v;
+}
+}  // namespace
+
+blink_status make_twiddles(float2* d_out, int N, cudaStream_t st) {
+    k_make_twiddles<<<(tws_total(N) + 255) / 256, 256, 0, st>>>(d_out, N);
+    BLINK_CUDA(cudaGetLastError());
+    return BLINK_OK;
+}
 
 blink_status launch_grid_gather(const Plan& p, const float* d_vis4, int first_image, int n_images, float* d_grid,
                                 int* d_status, cudaStream_t st) {
@@ -300,9 +266,8 @@ blink_status launch_grid_gather(const Plan& p, const float* d_vis4, int first_im
     for (int i0 = 0; i0 < n_images; i0 += 65535) {
         const int n = std::min(65535, n_images - i0);
         k_grid_gather<<<dim3(nb, n), kGridThreads, smem, st>>>(
-            d_vis4 + (int64_t)i0 * p.B * 8, p.B, p.F, first_image + i0, p.pol, p.N, p.cw, p.n_cb, p.d_cell_off,
-            p.d_cell_key, p.d_cell_beg, p.d_contrib,
-            reinterpret_cast<float2*>(d_grid) + (int64_t)i0 * p.N * (p.N / 2 + 1), d_status);
+            d_vis4 + (int64_t)i0 * p.B * 8, p.B, p.F, first_image + i0, p.pol, p.N, p.cw, p.n_cb, p.d_ent_off,
+            p.d_ent, reinterpret_cast<float2*>(d_grid) + (int64_t)i0 * p.N * (p.N / 2 + 1), d_status);
     }
     BLINK_CUDA(cudaGetLastError());
     return BLINK_OK;
@@ -318,17 +283,6 @@ blink_status launch_grid_atomic(const Plan& p, const float2* d_visI, int image, 
     return BLINK_OK;
 }
 
-blink_status launch_colpass_gather(const Plan& p, int prec, const float2* d_visI, int64_t vis_stride,
-                                   int first_image, int n_images, void* d_H, int ldh, int* d_status,
-                                   cudaStream_t st) {
-    if (prec == BLINK_PREC_BF16) {
-        BLINK_DISPATCH_N(p.N, return (colpass_gather_n<NN, __nv_bfloat162>(p, d_visI, vis_stride, first_image,
-                                                                            n_images, d_H, ldh, d_status, st)));
-    }
-    BLINK_DISPATCH_N(p.N, return (colpass_gather_n<NN, float2>(p, d_visI, vis_stride, first_image, n_images, d_H,
-                                                                ldh, d_status, st)));
-}
-
 blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const float2* d_grid, int n_images,
                                  void* d_H, int ldh, cudaStream_t st) {
     if (prec == BLINK_PREC_BF16) {
@@ -338,13 +292,13 @@ blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const floa
 }
 
 blink_status launch_rowpass(int N, int prec, const float2* d_tw, const void* d_H, int ldh, int has_nyq,
-                            const float* d_w, int w_offset, int w_mod, int n_images, float* d_img,
+                            const float* d_w, int w_mod, WaveMap wm, int n_images, int out_first, float* d_img,
                             cudaStream_t st) {
     if (prec == BLINK_PREC_BF16) {
-        BLINK_DISPATCH_N(N, return (rowpass_n<NN, __nv_bfloat162>(d_tw, d_H, ldh, has_nyq, d_w, w_offset, w_mod,
-                                                                   n_images, d_img, st)));
+        BLINK_DISPATCH_N(N, return (rowpass_n<NN, __nv_bfloat162>(d_tw, d_H, ldh, has_nyq, d_w, w_mod, wm, n_images,
+                                                                   out_first, d_img, st)));
     }
-    BLINK_DISPATCH_N(N, return (rowpass_n<NN, float2>(d_tw, d_H, ldh, has_nyq, d_w, w_offset, w_mod, n_images,
+    BLINK_DISPATCH_N(N, return (rowpass_n<NN, float2>(d_tw, d_H, ldh, has_nyq, d_w, w_mod, wm, n_images, out_first,
                                                        d_img, st)));
 }
 

@@ -22,7 +22,7 @@ namespace {
 // result of as many images as fit.  It lives in the module's static device memory, so every GPU that
 // loads the library holds these 16 MiB until the process exits.
 constexpr size_t kScratchBytes = (size_t)16 << 20;
-constexpr size_t kTwiddleBytes = 2048 * sizeof(float2);       // room for the largest supported side
+constexpr size_t kTwiddleBytes = (size_t)tws_total(2048) * sizeof(float2);   // room for the largest side
 __device__ __align__(256) unsigned char g_image_scratch[kScratchBytes];
 
 // Device address of g_image_scratch per device.  In host code the array's name stands for a host-side
@@ -45,15 +45,6 @@ blink_status scratch_for_current_device(void** out) {
     }
     *out = g_scratch_addr[dev];
     return BLINK_OK;
-}
-
-// exp(+2 pi i k / N) for k < N, evaluated in FP64 with sincospi and rounded to FP32.
-__global__ void k_twiddle_table(float2* tw, int N) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    double s, c;
-    sincospi(2.0 * (double)k / (double)N, &s, &c);
-    tw[k] = make_float2((float)c, (float)s);
 }
 
 }  // namespace
@@ -88,13 +79,12 @@ extern "C" blink_status blink_image_noalloc(const blink_imaging* imaging, const 
     float2* tw = static_cast<float2*>(scratch);
     void* H = static_cast<unsigned char*>(scratch) + kTwiddleBytes;
     const int wave = (int)std::min<size_t>((size_t)n_images, room / per_img);
-    k_twiddle_table<<<(N + 255) / 256, 256, 0, st>>>(tw, N);
-    BLINK_CUDA(cudaGetLastError());
+    BLINK_TRY(make_twiddles(tw, N, st));
     for (int w0 = 0; w0 < n_images; w0 += wave) {
         const int nw = std::min(wave, n_images - w0);
         BLINK_TRY(launch_colpass_grid(N, prec, tw, reinterpret_cast<const float2*>(d_grid) + (int64_t)w0 * N * (N / 2 + 1),
                                       nw, H, ldh, st));
-        BLINK_TRY(launch_rowpass(N, prec, tw, H, ldh, 1, d_weight, w0, n_images, nw, d_img + (int64_t)w0 * N * N, st));
+        BLINK_TRY(launch_rowpass(N, prec, tw, H, ldh, 1, d_weight, n_images, WaveMap{1, 0, w0, nw}, nw, 0, d_img, st));
     }
     return BLINK_OK;
 }
