@@ -10,8 +10,9 @@ The step is the whole path: correlation (FP8 tensor cores by default), gridding,
 point (pinned voltages in, images back to pinned host memory, both copies timed) on a 5 ms sub-chunk.
 Inputs (442 MB of voltages) and outputs (40 GB of images) are far larger than L2, so no flush is needed.
 
-Multi-GPU (torchrun): every rank images its own chunk (chunk 4 + rank), with no collective on the data
-path; the timing is the max over ranks and `value` counts all ranks' images (weak scaling).
+Multi-GPU (torchrun): every rank images its own chunk (chunks are dealt round-robin from chunk 4), with
+no collective on the data path; the timing is the max over ranks and `value` counts all ranks' images
+(weak scaling).
 
 `--impl reference` times the CPU oracle (the only other implementation of the method here) on a
 bounded sample of the same workload, on the host cores.
@@ -206,7 +207,8 @@ def run_ours(args, world, rank, local):
     w = bs.WORKLOADS[WORKLOAD]
     cores = os.cpu_count() or 1
     ns = args.samples or w.samples_per_chunk
-    chunk = (4 + rank) % w.n_chunks
+    from paper_2505_15204_gb300.shard import chunks_for_rank, job_rate, max_over_ranks
+    chunk = chunks_for_rank(w.n_chunks, rank, world, first=4)[0]
     t_gen = time.perf_counter()
     inp = bs.build_workload(WORKLOAD, chunk=chunk, workers=max(1, min(16, cores // max(1, world))), n_samples=ns)
     t_gen = time.perf_counter() - t_gen
@@ -265,12 +267,8 @@ def run_ours(args, world, rank, local):
     B.blink_sync(ctx, stream)
     stage_ms, stage_n = B.blink_read_profile(ctx, stream, reset=True)
     ms_total = e0.elapsed_time(e1)
-    ms_step = ms_total / args.steps
-    if pg:
-        t = torch.tensor([ms_step], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * n_img / (ms_step / 1e3)
+    ms_step = max_over_ranks(ms_total / args.steps, pg, "cuda")
+    value = job_rate(n_img, world, ms_step / 1e3)
 
     # roofline of the dominant stage (live CUDA-event times of its launches in the timed region)
     dom = int(np.argmax(stage_ms)) if mode == B.BLINK_MODE_BATCHED else 1
@@ -330,12 +328,8 @@ def run_ours(args, world, rank, local):
             B.blink_pipeline_host(ctx, arr, obs_e, im, arith, h_volt, h_img, 0, stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_e = e0.elapsed_time(e1) / reps
-        if pg:
-            t = torch.tensor([ms_e], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms_e = float(t.item())
-        e2e = {"value": world * n_e / (ms_e / 1e3), "unit": "images/s", "h2d_bytes_per_step": int(h_volt.numel()),
+        ms_e = max_over_ranks(e0.elapsed_time(e1) / reps, pg, "cuda")
+        e2e = {"value": job_rate(n_e, world, ms_e / 1e3), "unit": "images/s", "h2d_bytes_per_step": int(h_volt.numel()),
                "d2h_bytes_per_step": int(h_img.numel() * 4), "images_per_step": n_e,
                "workload": "5 ms sub-chunk (5 integrations x 768 channels) of the same chunk"}
 

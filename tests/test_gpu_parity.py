@@ -327,3 +327,29 @@ def test_invalid_arguments_are_rejected_before_launch(B, ctx, bad):
     assert e.value.status in (B.BLINK_ERR_INVALID_ARG, B.BLINK_ERR_UNSUPPORTED)
     B.blink_sync(ctx)
     assert not img.any()
+
+
+def test_correlate_fp8_longer_integration_bit_exact(B, ctx):
+    # K = 20 samples x 4 channels = 80: larger integer sums through the tensor-core accumulator
+    w, volt, freqs, _ = _case("coarse", 40, 16)
+    S = oracle.correlate(volt, 20, 4)
+    want = oracle.visibilities(S, 80)
+    out = torch.empty(S.shape, dtype=torch.float32, device="cuda")
+    B.blink_correlate(ctx, B.Array(w["enu"]), B.Obs(freqs, 4, 20, 40), 1, dev(volt), out)
+    B.blink_sync(ctx)
+    got = out.cpu().numpy()
+    assert np.array_equal(got[..., 0], want.real.astype(np.float32))
+    assert np.array_equal(got[..., 1], want.imag.astype(np.float32))
+
+
+def test_correlate_fp8_rejects_tile_count_not_multiple_of_8(B, ctx):
+    enu = bs.tile_positions(12, 500.0, 3)
+    v = bs.constant_voltages(10, 1, 12, 1, 1)
+    out = torch.zeros((1, 1, 78, 4, 2), device="cuda")
+    with pytest.raises(B.BlinkError) as e:
+        B.blink_correlate(ctx, B.Array(enu), B.Obs(np.array([150e6]), 1, 10, 10), 1, dev(v), out)
+    assert e.value.status == B.BLINK_ERR_UNSUPPORTED
+    # the CUDA-core form handles it
+    B.blink_correlate(ctx, B.Array(enu), B.Obs(np.array([150e6]), 1, 10, 10), 0, dev(v), out)
+    B.blink_sync(ctx)
+    assert np.all(out.cpu().numpy()[..., 0] == 2.0)
