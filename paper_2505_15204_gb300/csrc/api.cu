@@ -144,25 +144,22 @@ double default_cell(const blink_array* a, double nu_max, int n_pix) {
     return umax / (double)(n_pix / 2 - 1);
 }
 
-// Cell-sorted gather list of the u >= 0 half plane for every output channel (see grid_fft.cu): one entry
-// per visibility (and per mirror) that lands in the half plane, ordered by (column block, cell, baseline).
+// Cell-sorted gather list of the u >= 0 half plane for every output channel: one entry per visibility (and
+// per mirror) that lands in the half plane, ordered by (u, v, baseline), with the offsets of every column
+// u so that a column, or a block of consecutive columns, is one contiguous range.
 blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std::vector<short2>& bl,
                           const blink_array* a) {
-    const int N = p->N, cw = p->cw, half = N / 2;
+    const int N = p->N, half = N / 2;
     const int64_t B = p->B;
-    const int64_t nkeys = (int64_t)half * N;                 // (column block, v, u within block)
-    const int64_t block_keys = (int64_t)N * cw;
+    const int64_t nkeys = (int64_t)half * N;                 // key = u * N + v
     std::vector<int> count(nkeys + 1);
-    std::vector<int> ent_off((size_t)p->F * (p->n_cb + 1));
+    std::vector<int> ent_off((size_t)p->F * (half + 1));
     std::vector<uint2> ent;
-    std::vector<uint32_t> ekey, eval, sorted;
+    std::vector<uint32_t> ekey, eval, sorted, skey;
     ent.reserve((size_t)p->F * (B + B / 16));
     p->W.assign(p->F, 0.f);
     int64_t dropped = 0;
-    auto key_of = [&](int u, int v) -> uint32_t {
-        const int cb = u / cw;
-        return (uint32_t)(cb * block_keys + (int64_t)v * cw + (u - cb * cw));
-    };
+    auto key_of = [&](int u, int v) -> uint32_t { return (uint32_t)((int64_t)u * N + v); };
     for (int f = 0; f < p->F; f++) {
         ekey.clear();
         eval.clear();
@@ -203,7 +200,7 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
         for (uint32_t k : ekey) count[k + 1]++;
         for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
         sorted.assign(ekey.size(), 0);
-        std::vector<uint32_t> skey(ekey.size());
+        skey.assign(ekey.size(), 0);
         {
             std::vector<int> cur(count.begin(), count.end() - 1);
             for (size_t e = 0; e < ekey.size(); e++) {
@@ -213,11 +210,11 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
             }
         }
         const int64_t base = (int64_t)ent.size();
-        for (int cb = 0; cb <= p->n_cb; cb++)
-            ent_off[(size_t)f * (p->n_cb + 1) + cb] = (int)(base + count[std::min<int64_t>((int64_t)cb * block_keys, nkeys)]);
+        for (int u = 0; u <= half; u++)
+            ent_off[(size_t)f * (half + 1) + u] = (int)(base + count[std::min<int64_t>((int64_t)u * N, nkeys)]);
         for (size_t e = 0; e < sorted.size(); e++) {
-            const uint32_t local = (uint32_t)(skey[e] % block_keys);
-            ent.push_back(make_uint2(local | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
+            const uint32_t u = skey[e] / N, v = skey[e] % N;
+            ent.push_back(make_uint2(u | (v << 11) | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
         }
         if ((int64_t)ent.size() > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
     }

@@ -53,9 +53,8 @@ struct Plan {
     double* d_enu = nullptr;               // [n_tiles][3]
     double* d_freq = nullptr;              // [F]
     uint32_t* d_cells = nullptr;           // [F][B]
-    int* d_ent_off = nullptr;              // [F][n_cb + 1] -> index into the gather entries
-    uint2* d_ent = nullptr;                // [n_contrib] {local cell (v * cw + u - cb * cw) | conj << 31, b},
-                                           // sorted by (column block, cell, baseline)
+    int* d_ent_off = nullptr;              // [F][N/2 + 1]: first gather entry of each column u
+    uint2* d_ent = nullptr;                // [n_contrib] {u | v << 11 | conj << 31, b}, sorted by (u, v, b)
     float* d_W = nullptr;                  // [F] W, the sum of weights
     float* d_Wk = nullptr;                 // [F] W times the divisor of the correlator's raw sums (2K or K)
     float2* d_tw = nullptr;                // twiddle set of side N (tws_total(N) entries)
@@ -305,36 +304,49 @@ __device__ __forceinline__ void dev_fail(int* status, int code) {
 // keep the row-wise store phase free of bank conflicts.
 template <int N> __host__ __device__ constexpr int col_ld() { return N + N / 16 + 2; }
 
-// Sum the gather entries [beg, end) of one column block into the tile s[v * cw + du]; `val(b)` is the
-// complex visibility of baseline b.  The first entry of each cell sums the whole cell in list order.
+// Gather entries: x = u | v << 11 | conj << 31 (cell (u, v) of the half plane), y = baseline.
+__device__ __forceinline__ int ent_u(uint32_t x) { return (int)(x & 0x7FFu); }
+__device__ __forceinline__ int ent_v(uint32_t x) { return (int)((x >> 11) & 0xFFFFFu); }
+__device__ __forceinline__ uint32_t ent_cell(uint32_t x) { return x & 0x7FFFFFFFu; }
+
+// Grid one column with one warp: sum its gather entries [beg, end) (sorted by v, then baseline) into the
+// column's cells s[idx(v)], which the caller has zeroed.  The warp takes the entries 32 at a time, one per
+// lane, and sums runs of equal cells with a segmented scan over the lanes (keys are sorted, so lanes with
+// equal keys are contiguous); the last lane of each run adds the run's sum to its cell.  A cell with many
+// contributions (the autocorrelations at (0, 0)) therefore costs a few chunks, not a serial chain, and
+// the order of additions is fixed, so results are reproducible.  `val(b)` is baseline b's visibility;
+// with `shift` every cell is multiplied by (-1)^(u+v) (the image shift by N/2).
 template <typename T, typename Val, typename Idx>
-__device__ __forceinline__ void gather_block(const uint2* __restrict__ ent, int beg, int end, int n_cells, int tid,
-                                             int nthr, T* s, Val val, Idx idx, bool sign_shift, int cw, int u0,
-                                             int* status) {
-    for (int i = beg + tid; i < end; i += nthr) {
-        const uint2 e = ent[i];
-        const uint32_t cell = e.x & 0x7FFFFFFFu;
-        if (i > beg && (ent[i - 1].x & 0x7FFFFFFFu) == cell) continue;
-        if ((int)cell >= n_cells) {
-            dev_fail(status, DEV_ERR_INDEX);
-            continue;
+__device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
+                                                   Val val, Idx idx, bool shift) {
+    for (int base = beg; base < end; base += 32) {
+        const int i = base + lane;
+        uint32_t key = 0xFFFFFFFFu;
+        float2 x = make_float2(0.f, 0.f);
+        if (i < end) {
+            const uint2 e = ent[i];
+            key = ent_cell(e.x);
+            x = val(e.y);
+            if (e.x >> 31) x.y = -x.y;
         }
-        float2 acc = make_float2(0.f, 0.f);
-        uint2 ej = e;
-        for (int j = i;;) {
-            float2 x = val(ej.y);
-            if (ej.x >> 31) x.y = -x.y;
-            acc = cadd(acc, x);
-            if (++j >= end) break;
-            ej = ent[j];
-            if ((ej.x & 0x7FFFFFFFu) != cell) break;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t k2 = __shfl_up_sync(0xFFFFFFFFu, key, d);
+            const float xr = __shfl_up_sync(0xFFFFFFFFu, x.x, d), xi = __shfl_up_sync(0xFFFFFFFFu, x.y, d);
+            if (lane >= d && k2 == key) {
+                x.x += xr;
+                x.y += xi;
+            }
         }
-        const int v = (int)cell / cw, c = (int)cell % cw;
-        if (sign_shift && ((u0 + c + v) & 1)) acc = make_float2(-acc.x, -acc.y);   // (-1)^(u+v): shift by N/2
-        st_c(s + idx(v, c), acc);
+        const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, key, 1);
+        if (i < end && (lane == 31 || i + 1 >= end || knext != key)) {
+            const int u = ent_u(key), v = ent_v(key);
+            if (shift && ((u + v) & 1)) x = make_float2(-x.x, -x.y);
+            T* p = s + idx(u, v);
+            st_c(p, cadd(ld_c(p), x));
+        }
+        __syncwarp();
     }
 }
-
-
 
 }  // namespace blink

@@ -32,7 +32,7 @@ struct FftParams {
     int F, tau0, n_tau;      // images: channel-major order k -> (f = k / n_tau, tau = tau0 + k % n_tau)
     int n_img;
     int n_cb, n_rb;          // column tasks and row tasks per image
-    const int* ent_off;      // [F][n_cb + 1]
+    const int* ent_off;      // [F][N/2 + 1]
     const uint2* ent;        // gather entries
     const float2* tw;        // twiddle set of side N
     void* H;                 // ring of column-pass results, [ring][N][ldh]
@@ -95,9 +95,10 @@ __device__ void column_task(const FftParams& P, int k, int cb, const float2* s_t
     __syncthreads();
     const float2* V = P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
     auto val = [&](uint32_t b) { return __ldg(V + b); };
-    auto idx = [&](int v, int c) { return c * LD + padx(v); };
-    gather_block(P.ent, P.ent_off[f * (P.n_cb + 1) + cb], P.ent_off[f * (P.n_cb + 1) + cb + 1], N * CW, tid, kPT, s,
-                 val, idx, true, CW, cb * CW, P.status);
+    const int u = cb * CW + (tid >> 5);                 // one warp per column
+    auto idx = [&](int, int v) { return (tid >> 5) * LD + padx(v); };
+    const int* off = P.ent_off + f * (N / 2 + 1);
+    warp_gather_column(P.ent, off[u], off[u + 1], tid & 31, s, val, idx, true);
     __syncthreads();
     NoOut none;
     fft_run<N, 1, 1, 32, 1, 0, true, false, true, T, NoOut, true>(s + (tid >> 5) * LD, s_twc, tid & 31, none);
@@ -207,10 +208,11 @@ blink_status launch_n(FftParams P, int n_sm, cudaStream_t st) {
 
 }  // namespace
 
-// Ring of column-pass results and the lag (in images) between an image's column and row tasks.  Task
-// durations vary a lot, so the row tasks trail by many images to rarely wait; the ring is a little larger
-// than the lag so that reusing a slot rarely waits either (80 images of 512^2 in FP32 = 84 MB, in L2).
-constexpr int kRing = 80, kLag = 64;
+// Ring of column-pass results and the lag (in images) between an image's column and row tasks: the row
+// tasks trail by enough images that they rarely wait, and the ring is a little larger than the lag so that
+// reusing a slot rarely waits either, while staying small enough to live in L2 (24 images of 512^2 in
+// FP32 = 25 MB).  Measured on the full-band chunk: ring/lag 24/16 beats 20/8, 48/24, 40/32 and 80/64.
+constexpr int kRing = 24, kLag = 16;
 int fft_ring_images() { return kRing; }
 
 blink_status launch_fft_persistent(const Plan& p, int prec, const float2* d_vis, int64_t vis_stride, int vis_first,

@@ -42,9 +42,10 @@ k_grid_gather(const float* __restrict__ vis4, int64_t B, int F, int first_image,
             const float* q = V + (int64_t)b * 8;
             return (pol == BLINK_POL_I) ? make_float2(0.5f * (q[0] + q[6]), 0.5f * (q[1] + q[7])) : make_float2(q[0], q[1]);
         };
-        auto idx = [&](int v, int c) { return v * cw + c; };
-        gather_block(ent, ent_off[f * (n_cb + 1) + cb], ent_off[f * (n_cb + 1) + cb + 1], N * cw, tid, kGridThreads, sg,
-                     val, idx, false, cw, u0, status);
+        auto idx = [&](int u, int v) { return v * cw + (u - u0); };
+        const int* off = ent_off + f * (half + 1);
+        for (int u = u0 + (tid >> 5); u < min(u0 + cw, half); u += kGridThreads / 32)   // one warp per column
+            warp_gather_column(ent, off[u], off[u + 1], tid & 31, sg, val, idx, false);
     }
     __syncthreads();
     const int ncols = min(cw, half + 1 - u0);
