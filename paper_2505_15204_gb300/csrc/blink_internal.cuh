@@ -296,6 +296,84 @@ struct NoOut {
     __device__ void operator()(int, int, float2) const {}
 };
 
+// ---- one transform per warp, padded positions (padx), with the index arithmetic hoisted ---------------
+// A position p = A(lane) + C, where C is a compile-time constant and (A mod 16) + (C mod 16) < 16, has
+// padx(p) = padx(A) + C + C / 16: each lane computes padx(A) once per pass and every element address is
+// that plus a constant.  The passes below only use such decompositions; sides whose radix-8 passes would
+// not fit them (fewer than 16 butterflies per pass) fall back to the generic fft_pass.
+template <int C> __device__ __forceinline__ constexpr int padc() { return C + C / 16; }
+
+template <int N, int R, int NS, bool OUT, typename T, typename Out>
+__device__ __forceinline__ void wfft_pass(T* s, const float2* tw, int lane, Out& out) {
+    constexpr int NB = N / R;
+    constexpr int PER = NB / 32;                    // butterflies per lane
+    static_assert(NB % 32 == 0, "warp transform needs at least 32 butterflies per pass");
+    static_assert(NS == 1 || NS == 8 || NS % 32 == 0, "unsupported pass layout");
+    float2 v[PER][R];
+    const int rbase = padx(lane);                   // reads: j + r * NB, j = lane + 32 m, NB % 32 == 0
+#pragma unroll
+    for (int m = 0; m < PER; m++) {
+#pragma unroll
+        for (int r = 0; r < R; r++) v[m][r] = ld_c(s + rbase + (32 * m + r * NB) * 17 / 16);
+        if (NS > 1) {
+            // k = j % NS
+            const int k = (NS % 32 == 0) ? (lane + (32 * m) % NS) : (lane & (NS - 1));
+#pragma unroll
+            for (int r = 1; r < R; r++) v[m][r] = cmul(v[m][r], tw[tw_off(N, NS) + (r - 1) * NS + k]);
+        }
+        idft<R>(v[m]);
+    }
+    if (!OUT) __syncwarp();
+    // writes: d + r * NS with d = (j / NS) * NS * R + j % NS
+    int wbase;
+    if (NS == 1) {
+        wbase = R * lane + ((R * lane) >> 4);       // d = R j = R lane + 32 m R
+    } else if (NS == 8) {
+        wbase = 68 * (lane >> 3) + (lane & 7);      // d = 64 (lane >> 3) + (lane & 7) + 256 m
+    } else {
+        wbase = padx(lane);                         // d = lane + const (NS % 32 == 0)
+    }
+#pragma unroll
+    for (int m = 0; m < PER; m++) {
+        const int j0 = 32 * m;                      // the lane-independent part of j
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            if (OUT) {
+                const int j = lane + j0;
+                out(0, (j / NS) * NS * R + (j % NS) + r * NS, v[m][r]);
+            } else {
+                int c;
+                if (NS == 1) c = 32 * m * R + r;
+                else if (NS == 8) c = 256 * m + 8 * r;
+                else c = (j0 / NS) * NS * R + (j0 % NS) + r * NS;
+                st_c(s + wbase + c + c / 16, v[m][r]);
+            }
+        }
+    }
+    if (!OUT) __syncwarp();
+}
+
+// Whole transform by one warp on a padded array; OUT: the last pass hands results to `out`.
+template <int N, int NS, bool OUT, typename T, typename Out>
+__device__ __forceinline__ void wfft_run(T* s, const float2* tw, int lane, Out& out) {
+    if constexpr (NS < N) {
+        constexpr int R = radix_at(N, NS);
+        constexpr bool LAST = NS * R == N;
+        wfft_pass<N, R, NS, OUT && LAST, T, Out>(s, tw, lane, out);
+        wfft_run<N, NS * R, OUT, T, Out>(s, tw, lane, out);
+    }
+}
+
+// Warp transform of a padded array: the hoisted form when every pass has at least 32 butterflies (sides of
+// 256 and more), the generic one otherwise.
+template <int N, bool OUT, typename T, typename Out>
+__device__ __forceinline__ void warp_fft(T* s, const float2* tw, int lane, Out& out) {
+    if constexpr (N >= 256)
+        wfft_run<N, 1, OUT, T, Out>(s, tw, lane, out);
+    else
+        fft_run<N, 1, 1, 32, 1, 0, OUT ? false : true, OUT, true, T, Out, true>(s, tw, lane, out);
+}
+
 __device__ __forceinline__ void dev_fail(int* status, int code) {
     if (status) atomicOr(status, code);
 }

@@ -101,7 +101,7 @@ __device__ void column_task(const FftParams& P, int k, int cb, const float2* s_t
     warp_gather_column(P.ent, off[u], off[u + 1], tid & 31, s, val, idx, true);
     __syncthreads();
     NoOut none;
-    fft_run<N, 1, 1, 32, 1, 0, true, false, true, T, NoOut, true>(s + (tid >> 5) * LD, s_twc, tid & 31, none);
+    warp_fft<N, false, T, NoOut>(s + (tid >> 5) * LD, s_twc, tid & 31, none);
     __syncthreads();
     T* out = static_cast<T*>(P.H) + (int64_t)slot * N * P.ldh + cb * CW;
     for (int e = tid; e < N * CW; e += kPT) {
@@ -136,7 +136,7 @@ __device__ void row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     const float inv = 1.0f / (w > 0.f ? w : 1.f);
     float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
     auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
-    fft_run<M, 1, 1, 32, 1, 0, false, true, true, float2, decltype(store), true>(dst, s_twr, lane, store);
+    warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
     __syncthreads();
     if (tid == 0) {
         __threadfence();
