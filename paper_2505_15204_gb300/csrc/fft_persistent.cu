@@ -52,19 +52,27 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ float2 ldcg_c(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ float2 ldcg_c(const __nv_bfloat162* p) {
     const unsigned u = __ldcg(reinterpret_cast<const unsigned*>(p));
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u));
 }
 
-// Thread 0 waits (bounded) until *cnt reaches `target`; the verdict is shared with the whole CTA.
+// Thread 0 waits (bounded) until *cnt reaches `target` (no wait and no load when cnt is NULL); the
+// verdict is shared with the whole CTA through one barrier (s_flag is not written again before the task's
+// closing barrier).
 __device__ bool wait_count(const FftParams& P, const int* cnt, int target, int* s_flag) {
     if (threadIdx.x == 0) {
         int ok = 1;
         const long long t0 = clock64();
-        while (ld_acquire(cnt) < target) {
-            if (clock64() - t0 > kWaitBudget || ld_acquire(P.tickets + 1)) {
+        while (cnt && ld_acquire(cnt) < target) {
+            if (clock64() - t0 > kWaitBudget || ld_relaxed(P.tickets + 1)) {
                 ok = 0;
                 break;
             }
@@ -77,9 +85,7 @@ __device__ bool wait_count(const FftParams& P, const int* cnt, int target, int* 
         *s_flag = ok;
     }
     __syncthreads();
-    const bool ok = *s_flag != 0;
-    __syncthreads();
-    return ok;
+    return *s_flag != 0;
 }
 
 template <int N, typename T>
@@ -89,20 +95,22 @@ __device__ void column_task(const FftParams& P, int k, int cb, const float2* s_t
     const int tid = threadIdx.x;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
-    if (k >= P.ring && !wait_count(P, P.row_done + (k - P.ring), P.n_rb, s_flag)) return;
+    const int warp = tid >> 5, lane = tid & 31;
     T* s = reinterpret_cast<T*>(work);
-    for (int e = tid; e < CW * LD; e += kPT) st_c(s + e, make_float2(0.f, 0.f));
-    __syncthreads();
+    T* col = s + warp * LD;                              // this warp's column
+    for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
+    __syncwarp();
     const float2* V = P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
-    auto val = [&](uint32_t b) { return __ldg(V + b); };
-    const int u = cb * CW + (tid >> 5);                 // one warp per column
-    auto idx = [&](int, int v) { return (tid >> 5) * LD + padx(v); };
+    auto val = [&](uint32_t b) { return __ldcs(V + b); };          // read once: do not keep in L2
+    const int u = cb * CW + warp;
+    auto idx = [&](int, int v) { return warp * LD + padx(v); };
     const int* off = P.ent_off + f * (N / 2 + 1);
-    warp_gather_column(P.ent, off[u], off[u + 1], tid & 31, s, val, idx, true);
-    __syncthreads();
+    warp_gather_column(P.ent, off[u], off[u + 1], lane, s, val, idx, true);
+    __syncwarp();
     NoOut none;
-    warp_fft<N, false, T, NoOut>(s + (tid >> 5) * LD, s_twc, tid & 31, none);
-    __syncthreads();
+    warp_fft<N, false, T, NoOut>(col, s_twc, lane, none);
+    // all columns transformed (the wait's barrier), and the ring slot free of its previous image
+    if (!wait_count(P, k >= P.ring ? P.row_done + (k - P.ring) : nullptr, P.n_rb, s_flag)) return;
     T* out = static_cast<T*>(P.H) + (int64_t)slot * N * P.ldh + cb * CW;
     for (int e = tid; e < N * CW; e += kPT) {
         const int y = e / CW, c = e % CW;
@@ -171,14 +179,14 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 4 : 1)) k_fft_persistent(cons
     const int seg = P.n_cb + P.n_rb;
     const int total = (P.n_img + P.lag) * seg;
     for (;;) {
+        // every task ends with a barrier, so s_ticket is free to rewrite here
         if (tid == 0) {
             int t = atomicAdd(P.tickets, 1);
-            if (ld_acquire(P.tickets + 1)) t = total;
+            if (ld_relaxed(P.tickets + 1)) t = total;
             s_ticket = t;
         }
         __syncthreads();
         const int t = s_ticket;
-        __syncthreads();
         if (t >= total) break;
         const int sg = t / seg, r = t - sg * seg;
         if (r < P.n_cb) {
@@ -187,6 +195,7 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 4 : 1)) k_fft_persistent(cons
             const int k = sg - P.lag;
             if (k >= 0 && k < P.n_img) row_task<N, T>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
         }
+        __syncthreads();
     }
 }
 
