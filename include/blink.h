@@ -168,6 +168,26 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
                             const blink_imaging* imaging, int32_t arith, int32_t mode,
                             const uint8_t* d_volt, float* d_img, float* d_weight, void* stream);
 
+/* One set of channels imaged with its own flags and image parameters (blink_pipeline_sets). */
+typedef struct {
+    int32_t fine0;              /* first fine channel of the set: index into the call's channel axis */
+    int32_t n_fine;             /* fine channels in the set (a multiple of obs.chan_avg) */
+    const uint8_t* flags;       /* host [n_tiles] flags of this set, or NULL (array.flags is ignored) */
+    blink_imaging imaging;      /* image side, cell, polarisation, autos, precision of this set */
+} blink_set;
+
+/*
+ * The whole path for several sets of channels at once (the batched form of Sec. 5.2.4's parallel gridding
+ * of many channels and intervals, with uneven baseline counts and image sizes): each set has its own
+ * flagged tiles and image side.  obs describes the whole buffer (n_fine channels, fine_freq_hz for all of
+ * them); set s covers channels [fine0, fine0 + n_fine).  Images of set s are written in the order of
+ * blink_pipeline (id = tau * F_s + f) at float offset sum_{s' < s} T * F_s' * N_s'^2 of d_img.
+ *   img_capacity  floats available at d_img; too small -> BLINK_ERR_INVALID_ARG before any launch.
+ */
+blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                 const blink_set* sets, int32_t n_sets, int32_t arith, const uint8_t* d_volt,
+                                 float* d_img, size_t img_capacity, void* stream);
+
 /*
  * blink_pipeline on host buffers: copies h_volt to device workspace, runs the batched path and copies
  * the images back to h_img, all ordered on `stream`.  Page-locked host buffers make the copies

@@ -38,7 +38,7 @@ BLINK_MODE_PLAIN = 1
 ENTRY_POINTS = (
     "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
-    "blink_set_profiling", "blink_read_profile", "blink_image_noalloc",
+    "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
@@ -66,6 +66,10 @@ class blink_imaging(C.Structure):
                 ("include_autos", C.c_int32), ("precision", C.c_int32)]
 
 
+class blink_set(C.Structure):
+    _fields_ = [("fine0", C.c_int32), ("n_fine", C.c_int32), ("flags", C.c_void_p), ("imaging", blink_imaging)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
@@ -87,6 +91,7 @@ def _load():
         "blink_set_profiling": (S, [P, I32]),
         "blink_read_profile": (S, [P, P, P, P, I32]),
         "blink_image_noalloc": (S, [P, P, I32, P, P, P]),
+        "blink_pipeline_sets": (S, [P, P, P, P, I32, I32, P, P, C.c_size_t, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -254,3 +259,23 @@ def blink_image_noalloc(imaging: Imaging, d_grid, n_images: int, d_weight, d_img
     i = imaging.c()
     _check(_lib.blink_image_noalloc(C.byref(i), _ptr(d_grid), n_images, _ptr(d_weight), _ptr(d_img),
                                     _stream(stream)), "blink_image_noalloc")
+
+
+@dataclass
+class Set:
+    fine0: int
+    n_fine: int
+    imaging: Imaging
+    flags: np.ndarray | None = None
+
+
+def blink_pipeline_sets(ctx, array: Array, obs: Obs, sets, arith: int, d_volt, d_img, img_capacity: int,
+                        stream=None) -> None:
+    """Several channel sets, each with its own flags and image parameters; images packed per set."""
+    a, o = array.c(), obs.c()
+    keep = [None if s.flags is None else np.ascontiguousarray(s.flags, dtype=np.uint8) for s in sets]
+    arr = (blink_set * len(sets))()
+    for q, (s, fl) in enumerate(zip(sets, keep)):
+        arr[q] = blink_set(s.fine0, s.n_fine, None if fl is None else fl.ctypes.data, s.imaging.c())
+    _check(_lib.blink_pipeline_sets(ctx, C.byref(a), C.byref(o), arr, len(sets), arith, _ptr(d_volt), _ptr(d_img),
+                                    img_capacity, _stream(stream)), "blink_pipeline_sets")

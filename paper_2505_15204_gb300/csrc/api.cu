@@ -714,6 +714,51 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
     return BLINK_OK;
 }
 
+blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                 const blink_set* sets, int32_t n_sets, int32_t arith, const uint8_t* d_volt,
+                                 float* d_img, size_t img_capacity, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, true));
+    if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
+        return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
+    if (!sets || n_sets < 1) return set_error(BLINK_ERR_INVALID_ARG, "no sets");
+    if (!d_volt || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_volt or d_img is NULL");
+    if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_img & 7))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_img 8-byte aligned");
+    const int T = obs->n_samples / obs->samples_per_int;
+    const int stride = obs->fine_stride ? obs->fine_stride : obs->n_fine;
+    // validate every set and the packed output size before launching anything
+    size_t need = 0;
+    for (int s = 0; s < n_sets; s++) {
+        const blink_set& st = sets[s];
+        if (st.fine0 < 0 || st.n_fine < 1 || st.fine0 + st.n_fine > obs->n_fine || st.n_fine % obs->chan_avg)
+            return set_error(BLINK_ERR_INVALID_ARG, "set channel range outside the buffer or not a multiple of chan_avg");
+        BLINK_TRY(check_imaging(&st.imaging));
+        need += (size_t)T * (st.n_fine / obs->chan_avg) * st.imaging.n_pix * st.imaging.n_pix;
+    }
+    if (need > img_capacity) return set_error(BLINK_ERR_INVALID_ARG, "img_capacity smaller than the sets' images");
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    size_t at = 0;
+    for (int s = 0; s < n_sets; s++) {
+        const blink_set& st = sets[s];
+        blink_array a = *array;
+        a.flags = st.flags;
+        blink_obs o = *obs;
+        o.n_fine = st.n_fine;
+        o.fine_stride = stride;
+        o.fine_freq_hz = obs->fine_freq_hz + st.fine0;
+        Plan* p = nullptr;
+        BLINK_TRY(get_plan(ctx, &a, &o, &st.imaging, true, strm, &p));
+        const int64_t ss = sample_stride_bytes(&o, a.n_tiles);
+        if (T > 0)
+            BLINK_TRY(run_batched(ctx, *p, &o, st.imaging.precision, arith, d_volt + (int64_t)st.fine0 * a.n_tiles * 2,
+                                  ss, 0, T, d_img + at, strm));
+        at += (size_t)T * p->F * p->N * p->N;
+    }
+    return BLINK_OK;
+}
+
 blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                                  const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt, float* h_img,
                                  int32_t images_per_pass, void* stream) {

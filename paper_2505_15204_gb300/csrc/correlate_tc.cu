@@ -420,7 +420,11 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(BLINK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the voltage block");
-    BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    static size_t smem_set = 0;                   // raise the kernel's limit once (not during a capture)
+    if (smem > smem_set) {
+        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        smem_set = 227 * 1024;
+    }
     const int grid = std::min(n_items, n_sm);
     k_corr_tc<<<grid, kThreads, smem, st>>>(map, P);
     BLINK_CUDA(cudaGetLastError());

@@ -203,10 +203,13 @@ template <int N, typename T>
 blink_status launch_n(FftParams P, int n_sm, cudaStream_t st) {
     auto kern = k_fft_persistent<N, T>;
     const size_t smem = fft_smem<N, T>();
-    if (smem > 48 * 1024) BLINK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int per_sm = 0;
-    BLINK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem));
+    static int per_sm = 0;                         // attributes and occupancy once per instantiation
+    if (!per_sm) {
+        if (smem > 48 * 1024)
+            BLINK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        BLINK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem));
+    }
     if (per_sm < 1) return set_error(BLINK_ERR_UNSUPPORTED, "persistent FFT kernel does not fit on an SM");
     P.n_cb = N / 2 / COL_CW;
     P.n_rb = N / kRB;

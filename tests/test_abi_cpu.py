@@ -52,3 +52,4 @@ def test_struct_layout_matches_header(lib_path):
     assert ctypes.sizeof(B.blink_array) == 24
     assert ctypes.sizeof(B.blink_obs) == 32
     assert ctypes.sizeof(B.blink_imaging) == 32
+    assert ctypes.sizeof(B.blink_set) == 48

@@ -353,3 +353,54 @@ def test_correlate_fp8_rejects_tile_count_not_multiple_of_8(B, ctx):
     B.blink_correlate(ctx, B.Array(enu), B.Obs(np.array([150e6]), 1, 10, 10), 0, dev(v), out)
     B.blink_sync(ctx)
     assert np.all(out.cpu().numpy()[..., 0] == 2.0)
+
+
+# ---------------------------------------------------------------------------------------------------
+# several channel sets with their own flags and image sizes; CUDA graph capture
+# ---------------------------------------------------------------------------------------------------
+
+def test_pipeline_sets_uneven_flags_and_sizes(B, ctx):
+    # the uneven workload: 4 coarse channels, each with its own flagged tiles and image side; 8 fine
+    # channels of each coarse channel and one integration keep the oracle quick
+    w = bs.build_workload("uneven", n_samples=10)
+    volt, freqs, sets_w = w["volt"], w["freqs"], w["sets"]
+    sets = [B.Set(fine0=st.fine0, n_fine=8, imaging=B.Imaging(st.n_pix), flags=st.flags) for st in sets_w]
+    assert sorted({st.n_pix for st in sets_w}) == [256, 512, 1024]
+    assert len({int(st.flags.sum()) for st in sets_w}) > 1
+    total = sum(8 * st.n_pix ** 2 for st in sets_w)
+    img = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    B.blink_pipeline_sets(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 10), sets, 1, dev(volt), img, total)
+    B.blink_sync(ctx)
+    got = img.cpu().numpy()
+    at = 0
+    for st in sets_w:
+        n = st.n_pix
+        ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n, flags=st.flags, fine0=st.fine0, n_fine=8, n_threads=8)
+        part = got[at:at + 8 * n * n].reshape(8, n, n)
+        for q in range(8):
+            assert rel_rms(part[q], ref["images"][q]) <= IMG_RTOL, (st.fine0, q)
+        at += 8 * n * n
+    with pytest.raises(B.BlinkError):
+        B.blink_pipeline_sets(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 10), sets, 1, dev(volt), img, total - 1)
+
+
+def test_pipeline_replays_in_a_cuda_graph(B, ctx):
+    w, volt, freqs, _ = _case("coarse", 20, 16)
+    arr, obs, im = B.Array(w["enu"]), B.Obs(freqs, 1, 10, 20), B.Imaging(256)
+    d = dev(volt)
+    eager = torch.empty((32, 256, 256), dtype=torch.float32, device="cuda")
+    out = torch.zeros((32, 256, 256), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        B.blink_pipeline(ctx, arr, obs, im, 1, 0, d, eager, stream=s)      # plan and workspace on first use
+        B.blink_pipeline(ctx, arr, obs, im, 1, 0, d, out, stream=s)
+    s.synchronize()
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        B.blink_pipeline(ctx, arr, obs, im, 1, 0, d, out, stream=s)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    B.blink_sync(ctx)
+    assert torch.equal(out, eager)
