@@ -425,7 +425,7 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
     void* H = nullptr;
     void* cnt = nullptr;
     BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));
-    BLINK_TRY(workspace(ctx, 1, (size_t)fft_ring_images() * N * (N / 2) * el, &H));
+    BLINK_TRY(workspace(ctx, 1, (size_t)fft_ring_images_max() * N * (N / 2) * el, &H));
     BLINK_TRY(workspace(ctx, 4, sizeof(int) * (2 + 2 * (size_t)t_chunk * F), &cnt));
     const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
     const int out_first = tau0 * F;
@@ -441,9 +441,34 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
                                            ctx->d_status, st));
         }
-        {
+        if (!p.tuned) {
+            // autotune the FFT launch shape on this first batch: time each candidate (every run writes the
+            // same images), keep the fastest for every later call of the plan
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            BLINK_CUDA(cudaEventCreate(&e0));
+            BLINK_CUDA(cudaEventCreate(&e1));
+            float best = 0.f;
+            for (const FftTune& c : fft_tune_candidates()) {
+                BLINK_CUDA(cudaEventRecord(e0, st));
+                BLINK_TRY(launch_fft_persistent(p, c, prec, static_cast<float2*>(vis), p.B, first, ta, tb - ta, H,
+                                                static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm,
+                                                st));
+                BLINK_CUDA(cudaEventRecord(e1, st));
+                BLINK_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BLINK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (!p.tuned || ms < best) {
+                    best = ms;
+                    p.tune = c;
+                    p.tuned = true;
+                }
+            }
+            p.tune_ms = best;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        } else {
             StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
-            BLINK_TRY(launch_fft_persistent(p, prec, static_cast<float2*>(vis), p.B, first, ta, tb - ta, H,
+            BLINK_TRY(launch_fft_persistent(p, p.tune, prec, static_cast<float2*>(vis), p.B, first, ta, tb - ta, H,
                                             static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm, st));
         }
     }

@@ -38,8 +38,17 @@ constexpr uint32_t CELL_NONE = 0x80008000u;   // flagged or outside the grid
 // ------------------------------------------------------------------------------------------------
 // plan: everything that depends only on (array, channels, imaging), built once and cached
 // ------------------------------------------------------------------------------------------------
+// Launch shape of the persistent FFT kernel, chosen by the autotuner on a plan's first batched call.
+struct FftTune {
+    int ring = 24, lag = 16;   // ring of column-pass results and row-task lag (images)
+    int ctas_per_sm = 0;       // resident CTAs per SM (0 = as many as fit)
+};
+
 struct Plan {
     uint64_t key = 0;
+    mutable FftTune tune;                  // autotuned FFT launch shape
+    mutable bool tuned = false;
+    mutable float tune_ms = 0.f;           // time of the chosen shape on the tuning call
     int n_tiles = 0, n_fine = 0, chan_avg = 1, F = 0, N = 0, pol = 0, autos = 1;
     int64_t B = 0;
     int cw = 16, n_cb = 0;                 // column-block width and count of the u >= 0 half plane
@@ -119,11 +128,13 @@ struct WaveMap {
 };
 
 // Gridding + both FFT passes of images [tau0, tau0 + n_tau) x all channels in one persistent launch;
-// d_H holds fft_ring_images() column-pass results, d_counters 2 + 2 * F * n_tau ints.
-int fft_ring_images();
-blink_status launch_fft_persistent(const Plan& p, int prec, const float2* d_vis, int64_t vis_stride, int vis_first,
-                                   int tau0, int n_tau, void* d_H, int* d_counters, float* d_img, int out_first,
-                                   int* d_status, int n_sm, cudaStream_t st);
+// d_H holds fft_ring_images_max() column-pass results, d_counters 2 + 2 * F * n_tau ints.
+int fft_ring_images_max();
+blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec, const float2* d_vis,
+                                   int64_t vis_stride, int vis_first, int tau0, int n_tau, void* d_H, int* d_counters,
+                                   float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st);
+// Candidate launch shapes the autotuner times.
+std::vector<FftTune> fft_tune_candidates();
 blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const float2* d_grid, int n_images,
                                  void* d_H, int ldh, cudaStream_t st);
 blink_status launch_rowpass(int N, int prec, const float2* d_tw, const void* d_H, int ldh, int has_nyq,

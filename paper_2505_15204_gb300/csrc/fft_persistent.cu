@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 4 : 1)) k_fft_persistent(cons
 }
 
 template <int N, typename T>
-blink_status launch_n(FftParams P, int n_sm, cudaStream_t st) {
+blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
     auto kern = k_fft_persistent<N, T>;
     const size_t smem = fft_smem<N, T>();
     static int per_sm = 0;                         // attributes and occupancy once per instantiation
@@ -213,7 +213,8 @@ blink_status launch_n(FftParams P, int n_sm, cudaStream_t st) {
     if (per_sm < 1) return set_error(BLINK_ERR_UNSUPPORTED, "persistent FFT kernel does not fit on an SM");
     P.n_cb = N / 2 / COL_CW;
     P.n_rb = N / kRB;
-    kern<<<n_sm * per_sm, kPT, smem, st>>>(P);
+    const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, per_sm) : per_sm;
+    kern<<<n_sm * per, kPT, smem, st>>>(P);
     BLINK_CUDA(cudaGetLastError());
     return BLINK_OK;
 }
@@ -222,14 +223,16 @@ blink_status launch_n(FftParams P, int n_sm, cudaStream_t st) {
 
 // Ring of column-pass results and the lag (in images) between an image's column and row tasks: the row
 // tasks trail by enough images that they rarely wait, and the ring is a little larger than the lag so that
-// reusing a slot rarely waits either, while staying small enough to live in L2 (24 images of 512^2 in
-// FP32 = 25 MB).  Measured on the full-band chunk: ring/lag 24/16 beats 20/8, 48/24, 40/32 and 80/64.
-constexpr int kRing = 24, kLag = 16;
-int fft_ring_images() { return kRing; }
+// reusing a slot rarely waits either, while staying small enough to live in L2.  The autotuner picks among
+// these shapes per plan (on the full-band chunk 24/16 measured best by hand as well).
+std::vector<FftTune> fft_tune_candidates() {
+    return {{24, 16, 0}, {16, 8, 0}, {32, 24, 0}, {48, 32, 0}, {24, 16, 3}, {32, 24, 3}};
+}
+int fft_ring_images_max() { return 48; }
 
-blink_status launch_fft_persistent(const Plan& p, int prec, const float2* d_vis, int64_t vis_stride, int vis_first,
-                                   int tau0, int n_tau, void* d_H, int* d_counters, float* d_img, int out_first,
-                                   int* d_status, int n_sm, cudaStream_t st) {
+blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec, const float2* d_vis,
+                                   int64_t vis_stride, int vis_first, int tau0, int n_tau, void* d_H, int* d_counters,
+                                   float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st) {
     FftParams P{};
     P.vis = d_vis;
     P.vis_stride = vis_stride;
@@ -243,8 +246,8 @@ blink_status launch_fft_persistent(const Plan& p, int prec, const float2* d_vis,
     P.tw = p.d_tw;
     P.H = d_H;
     P.ldh = p.N / 2;
-    P.ring = kRing;
-    P.lag = kLag;
+    P.ring = std::min(tune.ring, fft_ring_images_max());
+    P.lag = std::min(tune.lag, P.ring);
     P.wk = p.d_Wk;
     P.img_out = d_img;
     P.out_first = out_first;
@@ -255,12 +258,12 @@ blink_status launch_fft_persistent(const Plan& p, int prec, const float2* d_vis,
     BLINK_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int) * (2 + 2 * (size_t)P.n_img), st));
     const bool bf = prec == BLINK_PREC_BF16;
     switch (p.N) {
-        case 64: return bf ? launch_n<64, __nv_bfloat162>(P, n_sm, st) : launch_n<64, float2>(P, n_sm, st);
-        case 128: return bf ? launch_n<128, __nv_bfloat162>(P, n_sm, st) : launch_n<128, float2>(P, n_sm, st);
-        case 256: return bf ? launch_n<256, __nv_bfloat162>(P, n_sm, st) : launch_n<256, float2>(P, n_sm, st);
-        case 512: return bf ? launch_n<512, __nv_bfloat162>(P, n_sm, st) : launch_n<512, float2>(P, n_sm, st);
-        case 1024: return bf ? launch_n<1024, __nv_bfloat162>(P, n_sm, st) : launch_n<1024, float2>(P, n_sm, st);
-        case 2048: return bf ? launch_n<2048, __nv_bfloat162>(P, n_sm, st) : launch_n<2048, float2>(P, n_sm, st);
+        case 64: return bf ? launch_n<64, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<64, float2>(P, n_sm, tune.ctas_per_sm, st);
+        case 128: return bf ? launch_n<128, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<128, float2>(P, n_sm, tune.ctas_per_sm, st);
+        case 256: return bf ? launch_n<256, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<256, float2>(P, n_sm, tune.ctas_per_sm, st);
+        case 512: return bf ? launch_n<512, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<512, float2>(P, n_sm, tune.ctas_per_sm, st);
+        case 1024: return bf ? launch_n<1024, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<1024, float2>(P, n_sm, tune.ctas_per_sm, st);
+        case 2048: return bf ? launch_n<2048, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<2048, float2>(P, n_sm, tune.ctas_per_sm, st);
     }
     return set_error(BLINK_ERR_UNSUPPORTED, "image side must be a power of two in [64, 2048]");
 }
