@@ -189,10 +189,13 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
                                  float* d_img, size_t img_capacity, void* stream);
 
 /*
- * blink_pipeline on host buffers: copies h_volt to device workspace, runs the batched path and copies
- * the images back to h_img, all ordered on `stream`.  Page-locked host buffers make the copies
- * asynchronous; the call returns after enqueueing (blink_sync waits).  `images_per_pass` (>= 1, 0 = all)
- * bounds the device image buffer: the images come back in passes of at most that many.
+ * blink_pipeline on host buffers: copies h_volt to device workspace, runs the batched path and delivers
+ * the images to h_img, all ordered on `stream`.  When h_img lies in one page-locked allocation
+ * (cudaHostAlloc, cudaHostRegister) the imaging kernel writes the images straight into it over the host
+ * link, overlapping the transfer with the computation, and `images_per_pass` is ignored.  Otherwise the
+ * images are staged in device memory and copied back in passes: `images_per_pass` (>= 1, 0 = all) bounds
+ * that device image buffer.  Page-locked buffers make the call asynchronous: it returns after enqueueing
+ * (blink_sync waits).
  *   h_volt  host uint8 as the voltage layout (fine_stride channels per sample).
  *   h_img   host float [T * F][N][N].
  */

@@ -415,7 +415,8 @@ int64_t sample_stride_bytes(const blink_obs* o, int n_tiles) {
 constexpr size_t kVisCapBytes = (size_t)4 << 30;
 
 blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
-                         const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st) {
+                         const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st,
+                         bool may_tune = true) {
     const int N = p.N, F = p.F;
     const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
     const int T = tau1 - tau0;
@@ -441,7 +442,13 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
                                            ctx->d_status, st));
         }
-        if (!p.tuned) {
+        if (!p.tuned && !may_tune) {
+            // output over the host link: timings would measure the link, so run the default shape untuned
+            StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
+            BLINK_TRY(launch_fft_persistent(p, fft_tune_candidates()[0], prec, static_cast<float2*>(vis), p.B, first,
+                                            ta, tb - ta, H, static_cast<int*>(cnt), d_img, out_first, ctx->d_status,
+                                            ctx->n_sm, st));
+        } else if (!p.tuned) {
             // autotune the FFT launch shape on this first batch: time each candidate (every run writes the
             // same images), keep the fastest for every later call of the plan
             cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -473,6 +480,28 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
         }
     }
     return BLINK_OK;
+}
+
+// Device address of a host buffer of `bytes` bytes that lies in page-locked (cudaHostAlloc or
+// cudaHostRegister) memory mapped for the device, judged by its first and last byte; NULL otherwise
+// (pageable memory, or a runtime that cannot map it).
+float* device_view(float* h, size_t bytes) {
+    if (!h || !bytes) return nullptr;
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const char* last = reinterpret_cast<const char*>(h) + bytes - 1;
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if (static_cast<char*>(b.devicePointer) - static_cast<char*>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
+        return nullptr;
+    return static_cast<float*>(a.devicePointer);
 }
 
 }  // namespace
@@ -803,6 +832,15 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
     if (n_img == 0) return BLINK_OK;
     const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
     const size_t vbytes = (size_t)obs->n_samples * ss;
+    // page-locked output: the imaging kernel writes the images straight into h_img, so the transfer over the
+    // host link overlaps the computation instead of following it
+    if (float* direct = device_view(h_img, (size_t)n_img * p->N * p->N * sizeof(float))) {
+        void* dv = nullptr;
+        BLINK_TRY(workspace(ctx, 2, vbytes, &dv));
+        BLINK_CUDA(cudaMemcpyAsync(dv, h_volt, vbytes, cudaMemcpyHostToDevice, st));
+        return run_batched(ctx, *p, obs, imaging->precision, arith, static_cast<uint8_t*>(dv), ss, 0, T, direct, st,
+                           false);
+    }
     // passes of whole integrations (F images each), at least one integration per pass
     const int t_per = images_per_pass > 0 ? std::max(1, std::min(T, images_per_pass / p->F)) : T;
     const int N = p->N;

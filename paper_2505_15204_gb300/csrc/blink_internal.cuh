@@ -307,25 +307,32 @@ struct NoOut {
     __device__ void operator()(int, int, float2) const {}
 };
 
-// ---- one transform per warp, padded positions (padx), with the index arithmetic hoisted ---------------
-// A position p = A(lane) + C, where C is a compile-time constant and (A mod 16) + (C mod 16) < 16, has
-// padx(p) = padx(A) + C + C / 16: each lane computes padx(A) once per pass and every element address is
-// that plus a constant.  The passes below only use such decompositions; sides whose radix-8 passes would
-// not fit them (fewer than 16 butterflies per pass) fall back to the generic fft_pass.
-template <int C> __device__ __forceinline__ constexpr int padc() { return C + C / 16; }
+// ---- one transform per warp, padded positions, with the index arithmetic hoisted -----------------------
+// Layout of a pass's buffer: point p at padq<C>(p) = p + C * (p / 16), i.e. C spare slots after every 16
+// points (C = 1 is padx).  Every pass reads aligned runs of 16 consecutive points per half-warp, which are
+// conflict-free under any C; the writes of the pass after the first radix-8 pass (stride 8 within groups of
+// 64) are conflict-free only with C = 2, the others with C = 1, so that pass writes with C = 2 and the next
+// reads with it.  Transforms start and end in the C = 1 layout.
+// A position p = A(lane) + K, where K is a compile-time multiple of 16 or stays inside A's run of 16, has
+// padq<C>(p) = padq<C>(A) + K + C * (K / 16): each lane computes its base once per pass and every element
+// address is that plus a constant.  Sides whose radix-8 passes would not fit these decompositions (fewer
+// than 32 butterflies per pass) fall back to the generic fft_pass.
+template <int C> __device__ __forceinline__ int padq(int p) { return p + C * (p >> 4); }
+// Slots a warp transform of n points needs (room for the C = 2 layout when the hoisted form is used).
+__host__ __device__ constexpr int wfft_slots(int n) { return n >= 256 ? n + n / 8 : n + n / 16; }
 
-template <int N, int R, int NS, bool OUT, typename T, typename Out>
+template <int N, int R, int NS, int PR, int PW, bool OUT, typename T, typename Out>
 __device__ __forceinline__ void wfft_pass(T* s, const float2* tw, int lane, Out& out) {
     constexpr int NB = N / R;
     constexpr int PER = NB / 32;                    // butterflies per lane
     static_assert(NB % 32 == 0, "warp transform needs at least 32 butterflies per pass");
     static_assert(NS == 1 || NS == 8 || NS % 32 == 0, "unsupported pass layout");
     float2 v[PER][R];
-    const int rbase = padx(lane);                   // reads: j + r * NB, j = lane + 32 m, NB % 32 == 0
+    const int rbase = padq<PR>(lane);               // reads: j + r * NB, j = lane + 32 m, NB % 32 == 0
 #pragma unroll
     for (int m = 0; m < PER; m++) {
 #pragma unroll
-        for (int r = 0; r < R; r++) v[m][r] = ld_c(s + rbase + (32 * m + r * NB) * 17 / 16);
+        for (int r = 0; r < R; r++) v[m][r] = ld_c(s + rbase + (32 * m + r * NB) * (16 + PR) / 16);
         if (NS > 1) {
             // k = j % NS
             const int k = (NS % 32 == 0) ? (lane + (32 * m) % NS) : (lane & (NS - 1));
@@ -338,11 +345,11 @@ __device__ __forceinline__ void wfft_pass(T* s, const float2* tw, int lane, Out&
     // writes: d + r * NS with d = (j / NS) * NS * R + j % NS
     int wbase;
     if (NS == 1) {
-        wbase = R * lane + ((R * lane) >> 4);       // d = R j = R lane + 32 m R
+        wbase = R * lane + PW * ((R * lane) >> 4);  // d = R j = R lane + 32 m R
     } else if (NS == 8) {
-        wbase = 68 * (lane >> 3) + (lane & 7);      // d = 64 (lane >> 3) + (lane & 7) + 256 m
+        wbase = (64 + 4 * PW) * (lane >> 3) + (lane & 7);   // d = 64 (lane >> 3) + (lane & 7) + 256 m
     } else {
-        wbase = padx(lane);                         // d = lane + const (NS % 32 == 0)
+        wbase = padq<PW>(lane);                     // d = lane + const (NS % 32 == 0)
     }
 #pragma unroll
     for (int m = 0; m < PER; m++) {
@@ -357,30 +364,32 @@ __device__ __forceinline__ void wfft_pass(T* s, const float2* tw, int lane, Out&
                 if (NS == 1) c = 32 * m * R + r;
                 else if (NS == 8) c = 256 * m + 8 * r;
                 else c = (j0 / NS) * NS * R + (j0 % NS) + r * NS;
-                st_c(s + wbase + c + c / 16, v[m][r]);
+                st_c(s + wbase + c + PW * (c / 16), v[m][r]);
             }
         }
     }
     if (!OUT) __syncwarp();
 }
 
-// Whole transform by one warp on a padded array; OUT: the last pass hands results to `out`.
-template <int N, int NS, bool OUT, typename T, typename Out>
+// Whole transform by one warp on a padded array; OUT: the last pass hands results to `out`.  PR is the
+// layout the pass reads (C = 1 for the first).
+template <int N, int NS, int PR, bool OUT, typename T, typename Out>
 __device__ __forceinline__ void wfft_run(T* s, const float2* tw, int lane, Out& out) {
     if constexpr (NS < N) {
         constexpr int R = radix_at(N, NS);
         constexpr bool LAST = NS * R == N;
-        wfft_pass<N, R, NS, OUT && LAST, T, Out>(s, tw, lane, out);
-        wfft_run<N, NS * R, OUT, T, Out>(s, tw, lane, out);
+        constexpr int PW = (NS == 8 && !LAST) ? 2 : 1;
+        wfft_pass<N, R, NS, PR, PW, OUT && LAST, T, Out>(s, tw, lane, out);
+        wfft_run<N, NS * R, PW, OUT, T, Out>(s, tw, lane, out);
     }
 }
 
-// Warp transform of a padded array: the hoisted form when every pass has at least 32 butterflies (sides of
-// 256 and more), the generic one otherwise.
+// Warp transform of a padded array (padx layout in and out, wfft_slots(N) slots): the hoisted form when
+// every pass has at least 32 butterflies (sides of 256 and more), the generic one otherwise.
 template <int N, bool OUT, typename T, typename Out>
 __device__ __forceinline__ void warp_fft(T* s, const float2* tw, int lane, Out& out) {
     if constexpr (N >= 256)
-        wfft_run<N, 1, OUT, T, Out>(s, tw, lane, out);
+        wfft_run<N, 1, 1, OUT, T, Out>(s, tw, lane, out);
     else
         fft_run<N, 1, 1, 32, 1, 0, OUT ? false : true, OUT, true, T, Out, true>(s, tw, lane, out);
 }

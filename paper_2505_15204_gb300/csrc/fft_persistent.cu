@@ -88,10 +88,15 @@ __device__ bool wait_count(const FftParams& P, const int* cnt, int target, int* 
     return *s_flag != 0;
 }
 
+__host__ __device__ constexpr int even(int x) { return (x + 1) / 2 * 2; }
+// Column tile stride (in elements) and row buffer stride: room for the warp transforms' layouts, and 2 mod 16
+// slots so that the tile's row-wise store phase is free of bank conflicts.
+template <int N> __host__ __device__ constexpr int tile_ld() { return wfft_slots(N) + 2; }
+
 template <int N, typename T>
 __device__ void column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
                             int* s_flag) {
-    constexpr int CW = COL_CW, LD = col_ld<N>();
+    constexpr int CW = COL_CW, LD = tile_ld<N>();
     const int tid = threadIdx.x;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
@@ -124,7 +129,7 @@ __device__ void column_task(const FftParams& P, int k, int cb, const float2* s_t
 template <int N, typename T>
 __device__ void row_task(const FftParams& P, int k, int rb, const float2* s_pre, const float2* s_twr,
                          unsigned char* work, int* s_flag) {
-    constexpr int M = N / 2, LS = M + M / 16 + 2;
+    constexpr int M = N / 2, LS = tile_ld<M>();
     const int tid = threadIdx.x, r = tid >> 5, lane = tid & 31;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
@@ -135,9 +140,10 @@ __device__ void row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     for (int q = lane; q <= M / 2; q += 32) {
         const float2 zk = ldcg_c(row + q);
         const float2 zm = (q == 0) ? make_float2(0.f, 0.f) : ldcg_c(row + (M - q));
-        dst[padx(q)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), s_pre[q])));
+        const float2 w = s_pre[q];                    // exp(2 pi i q / N); that of M - q is -conj(w)
+        dst[padx(q)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), w)));
         if (q > 0 && q < M - q)
-            dst[padx(M - q)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), s_pre[M - q])));
+            dst[padx(M - q)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), make_float2(-w.x, w.y))));
     }
     __syncwarp();
     const float w = P.wk[f];
@@ -152,13 +158,12 @@ __device__ void row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     }
 }
 
-__host__ __device__ constexpr int even(int x) { return (x + 1) / 2 * 2; }
 
 template <int N, typename T> constexpr size_t fft_smem() {
     constexpr int M = N / 2;
-    constexpr size_t tw = (size_t)(even(tw_size(N)) + even(M + 1) + even(tw_size(M))) * sizeof(float2);
-    constexpr size_t col = (size_t)COL_CW * col_ld<N>() * sizeof(T);
-    constexpr size_t row = (size_t)kRB * (M + M / 16 + 2) * sizeof(float2);
+    constexpr size_t tw = (size_t)(even(tw_size(N)) + even(M / 2 + 1) + even(tw_size(M))) * sizeof(float2);
+    constexpr size_t col = (size_t)COL_CW * tile_ld<N>() * sizeof(T);
+    constexpr size_t row = (size_t)kRB * tile_ld<M>() * sizeof(float2);
     return tw + (col > row ? col : row);
 }
 
@@ -169,12 +174,12 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 4 : 1)) k_fft_persistent(cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* s_twc = reinterpret_cast<float2*>(smem_raw);
     float2* s_pre = s_twc + even(tw_size(N));
-    float2* s_twr = s_pre + even(M + 1);
+    float2* s_twr = s_pre + even(M / 2 + 1);
     unsigned char* work = reinterpret_cast<unsigned char*>(s_twr + even(tw_size(M)));
     __shared__ int s_ticket, s_flag;
     const int tid = threadIdx.x;
     for (int e = tid; e < tw_size(N); e += kPT) s_twc[e] = P.tw[tws_col(N) + e];
-    for (int e = tid; e <= M; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
+    for (int e = tid; e <= M / 2; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
     for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
     const int seg = P.n_cb + P.n_rb;
     const int total = (P.n_img + P.lag) * seg;

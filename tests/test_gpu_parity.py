@@ -279,6 +279,24 @@ def test_pipeline_host_buffers_equal_device_path(B, ctx):
     assert np.array_equal(h_img.numpy(), d.cpu().numpy())
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_pipeline_host_direct_and_staged_outputs(B, ctx, pinned):
+    # page-locked images are written by the imaging kernel over the host link; pageable ones are staged
+    # through device memory in passes: both equal the device path bit for bit (FP8 correlation, 512^2)
+    w, volt, freqs, _ = _case("coarse", 20, 8)
+    arr, obs, im = B.Array(w["enu"]), B.Obs(freqs, 2, 10, 20), B.Imaging(512)
+    n = 2 * (len(freqs) // 2)
+    d = torch.empty((n, 512, 512), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, arr, obs, im, 1, 0, dev(volt), d)
+    h_volt = torch.from_numpy(volt)
+    h_img = torch.full((n, 512, 512), float("nan"), dtype=torch.float32)
+    if pinned:
+        h_volt, h_img = h_volt.pin_memory(), h_img.pin_memory()
+    B.blink_pipeline_host(ctx, arr, obs, im, 1, h_volt, h_img, images_per_pass=3)
+    B.blink_sync(ctx)
+    assert np.array_equal(h_img.numpy(), d.cpu().numpy())
+
+
 # ---------------------------------------------------------------------------------------------------
 # edge cases and argument errors
 # ---------------------------------------------------------------------------------------------------
