@@ -407,26 +407,38 @@ __device__ __forceinline__ int ent_u(uint32_t x) { return (int)(x & 0x7FFu); }
 __device__ __forceinline__ int ent_v(uint32_t x) { return (int)((x >> 11) & 0xFFFFFu); }
 __device__ __forceinline__ uint32_t ent_cell(uint32_t x) { return x & 0x7FFFFFFFu; }
 
+// Gather entry i of a column whose entries end at `end`: its cell key and visibility (conjugated for an
+// entry of the mirrored half plane); key 0xFFFFFFFF and zero past the end.
+template <typename Val>
+__device__ __forceinline__ void gather_entry(const uint2* __restrict__ ent, int i, int end, Val val, uint32_t& key,
+                                             float2& x) {
+    key = 0xFFFFFFFFu;
+    x = make_float2(0.f, 0.f);
+    if (i < end) {
+        const uint2 e = ent[i];
+        key = ent_cell(e.x);
+        x = val(e.y);
+        if (e.x >> 31) x.y = -x.y;
+    }
+}
+
 // Grid one column with one warp: sum its gather entries [beg, end) (sorted by v, then baseline) into the
-// column's cells s[idx(v)], which the caller has zeroed.  The warp takes the entries 32 at a time, one per
+// column's cells s[idx(u, v)], which the caller has zeroed.  The warp takes the entries 32 at a time, one per
 // lane, and sums runs of equal cells with a segmented scan over the lanes (keys are sorted, so lanes with
 // equal keys are contiguous); the last lane of each run adds the run's sum to its cell.  A cell with many
 // contributions (the autocorrelations at (0, 0)) therefore costs a few chunks, not a serial chain, and
 // the order of additions is fixed, so results are reproducible.  `val(b)` is baseline b's visibility;
 // with `shift` every cell is multiplied by (-1)^(u+v) (the image shift by N/2).
+// (key, x) is lane's entry of the first chunk (gather_entry(ent, beg + lane, ...)), loaded by the caller so
+// that its latency overlaps the caller's own work; each later chunk is loaded while the previous is summed.
 template <typename T, typename Val, typename Idx>
 __device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
-                                                   Val val, Idx idx, bool shift) {
+                                                   Val val, Idx idx, bool shift, uint32_t key, float2 x) {
     for (int base = beg; base < end; base += 32) {
         const int i = base + lane;
-        uint32_t key = 0xFFFFFFFFu;
-        float2 x = make_float2(0.f, 0.f);
-        if (i < end) {
-            const uint2 e = ent[i];
-            key = ent_cell(e.x);
-            x = val(e.y);
-            if (e.x >> 31) x.y = -x.y;
-        }
+        uint32_t nkey;
+        float2 nx;
+        gather_entry(ent, i + 32, end, val, nkey, nx);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t k2 = __shfl_up_sync(0xFFFFFFFFu, key, d);
@@ -444,7 +456,19 @@ __device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent
             st_c(p, cadd(ld_c(p), x));
         }
         __syncwarp();
+        key = nkey;
+        x = nx;
     }
+}
+
+// The same, loading the first chunk itself.
+template <typename T, typename Val, typename Idx>
+__device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
+                                                   Val val, Idx idx, bool shift) {
+    uint32_t key;
+    float2 x;
+    gather_entry(ent, beg + lane, end, val, key, x);
+    warp_gather_column(ent, beg, end, lane, s, val, idx, shift, key, x);
 }
 
 }  // namespace blink

@@ -21,8 +21,10 @@ namespace blink {
 
 namespace {
 
-constexpr int kPT = 256;                         // threads: 8 warps
-constexpr int kRB = 8;                           // rows per row task (one per warp)
+constexpr int kW = 8;                            // warps per CTA: columns per column task, rows per row task
+constexpr int kPT = 32 * kW;                     // threads
+constexpr int kCW = kW;                          // u columns per column task (one per warp)
+constexpr int kRB = kW;                          // rows per row task (one per warp)
 constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
 
 struct FftParams {
@@ -89,55 +91,64 @@ __device__ bool wait_count(const FftParams& P, const int* cnt, int target, int* 
 }
 
 __host__ __device__ constexpr int even(int x) { return (x + 1) / 2 * 2; }
-// Column tile stride (in elements) and row buffer stride: room for the warp transforms' layouts, and 2 mod 16
-// slots so that the tile's row-wise store phase is free of bank conflicts.
-template <int N> __host__ __device__ constexpr int tile_ld() { return wfft_slots(N) + 2; }
+// Column tile stride (in elements) and row buffer stride: room for the warp transforms' layouts, and
+// 16 / kCW mod 16 slots so that the tile's row-wise store phase (kCW columns x 16 / kCW rows per half-warp)
+// is free of bank conflicts.
+template <int N> __host__ __device__ constexpr int tile_ld() { return wfft_slots(N) + 16 / kCW; }
 
+// The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
 template <int N, typename T>
-__device__ void column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
+__device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
                             int* s_flag) {
-    constexpr int CW = COL_CW, LD = tile_ld<N>();
+    constexpr int CW = kCW, LD = tile_ld<N>();
     const int tid = threadIdx.x;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
     const int warp = tid >> 5, lane = tid & 31;
+    // the ring slot's previous occupant, read now so that the load overlaps the gridding and transforms
+    const int* prev = k >= P.ring ? P.row_done + (k - P.ring) : nullptr;
+    int prev_done = 0;
+    if (tid == 0 && prev) prev_done = ld_acquire(prev);
     T* s = reinterpret_cast<T*>(work);
     T* col = s + warp * LD;                              // this warp's column
-    for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
-    __syncwarp();
     const float2* V = P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
     auto val = [&](uint32_t b) { return __ldcs(V + b); };          // read once: do not keep in L2
     const int u = cb * CW + warp;
     auto idx = [&](int, int v) { return warp * LD + padx(v); };
     const int* off = P.ent_off + f * (N / 2 + 1);
-    warp_gather_column(P.ent, off[u], off[u + 1], lane, s, val, idx, true);
+    const int beg = off[u], end = off[u + 1];
+    uint32_t key;
+    float2 x;
+    gather_entry(P.ent, beg + lane, end, val, key, x);    // in flight while the column is zeroed
+    for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
+    __syncwarp();
+    warp_gather_column(P.ent, beg, end, lane, s, val, idx, true, key, x);
     __syncwarp();
     NoOut none;
     warp_fft<N, false, T, NoOut>(col, s_twc, lane, none);
     // all columns transformed (the wait's barrier), and the ring slot free of its previous image
-    if (!wait_count(P, k >= P.ring ? P.row_done + (k - P.ring) : nullptr, P.n_rb, s_flag)) return;
+    if (!wait_count(P, prev_done >= P.n_rb ? nullptr : prev, P.n_rb, s_flag)) return nullptr;
     T* out = static_cast<T*>(P.H) + (int64_t)slot * N * P.ldh + cb * CW;
     for (int e = tid; e < N * CW; e += kPT) {
         const int y = e / CW, c = e % CW;
         out[(int64_t)y * P.ldh + c] = s[c * LD + padx(y)];
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) atomicAdd(P.col_done + k, 1);
+    return P.col_done + k;
 }
 
 template <int N, typename T>
-__device__ void row_task(const FftParams& P, int k, int rb, const float2* s_pre, const float2* s_twr,
+__device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre, const float2* s_twr,
                          unsigned char* work, int* s_flag) {
     constexpr int M = N / 2, LS = tile_ld<M>();
     const int tid = threadIdx.x, r = tid >> 5, lane = tid & 31;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
-    if (!wait_count(P, P.col_done + k, P.n_cb, s_flag)) return;
+    if (!wait_count(P, P.col_done + k, P.n_cb, s_flag)) return nullptr;
     const int y = rb * kRB + r;
     const T* row = static_cast<const T*>(P.H) + ((int64_t)slot * N + y) * P.ldh;
     float2* dst = reinterpret_cast<float2*>(work) + r * LS;
-    for (int q = lane; q <= M / 2; q += 32) {
+#pragma unroll
+    for (int q = lane; q <= M / 2; q += 32) {       // unrolled: every load of the row is issued at once
         const float2 zk = ldcg_c(row + q);
         const float2 zm = (q == 0) ? make_float2(0.f, 0.f) : ldcg_c(row + (M - q));
         const float2 w = s_pre[q];                    // exp(2 pi i q / N); that of M - q is -conj(w)
@@ -151,25 +162,21 @@ __device__ void row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
     auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
     warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        atomicAdd(P.row_done + k, 1);
-    }
+    return P.row_done + k;
 }
 
 
 template <int N, typename T> constexpr size_t fft_smem() {
     constexpr int M = N / 2;
     constexpr size_t tw = (size_t)(even(tw_size(N)) + even(M / 2 + 1) + even(tw_size(M))) * sizeof(float2);
-    constexpr size_t col = (size_t)COL_CW * tile_ld<N>() * sizeof(T);
+    constexpr size_t col = (size_t)kCW * tile_ld<N>() * sizeof(T);
     constexpr size_t row = (size_t)kRB * tile_ld<M>() * sizeof(float2);
     return tw + (col > row ? col : row);
 }
 
-// Four CTAs per SM for sides up to 512 (measured faster than three, despite a few register spills).
+// 32 warps per SM for sides up to 512 (measured faster than 24, despite a few register spills).
 template <int N, typename T>
-__global__ void __launch_bounds__(kPT, (N <= 512 ? 4 : 1)) k_fft_persistent(const FftParams P) {
+__global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persistent(const FftParams P) {
     constexpr int M = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* s_twc = reinterpret_cast<float2*>(smem_raw);
@@ -183,22 +190,30 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 4 : 1)) k_fft_persistent(cons
     for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
     const int seg = P.n_cb + P.n_rb;
     const int total = (P.n_img + P.lag) * seg;
+    if (tid == 0) s_ticket = atomicAdd(P.tickets, 1);
+    __syncthreads();
     for (;;) {
-        // every task ends with a barrier, so s_ticket is free to rewrite here
-        if (tid == 0) {
-            int t = atomicAdd(P.tickets, 1);
-            if (ld_relaxed(P.tickets + 1)) t = total;
-            s_ticket = t;
-        }
-        __syncthreads();
         const int t = s_ticket;
         if (t >= total) break;
         const int sg = t / seg, r = t - sg * seg;
+        int* done = nullptr;
         if (r < P.n_cb) {
-            if (sg < P.n_img) column_task<N, T>(P, sg, r, s_twc, work, &s_flag);
+            if (sg < P.n_img) done = column_task<N, T>(P, sg, r, s_twc, work, &s_flag);
         } else {
             const int k = sg - P.lag;
-            if (k >= 0 && k < P.n_img) row_task<N, T>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
+            if (k >= 0 && k < P.n_img) done = row_task<N, T>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
+        }
+        // every thread's reads and writes of the task are done; thread 0 takes the next ticket and releases the
+        // task (the fence orders the whole CTA's accesses before the counter), its latencies overlapping
+        __syncthreads();
+        if (tid == 0) {
+            int nt = atomicAdd(P.tickets, 1);
+            const int ab = ld_relaxed(P.tickets + 1);
+            if (done) {
+                __threadfence();
+                atomicAdd(done, 1);
+            }
+            s_ticket = ab ? total : nt;
         }
         __syncthreads();
     }
@@ -216,7 +231,7 @@ blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
         BLINK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem));
     }
     if (per_sm < 1) return set_error(BLINK_ERR_UNSUPPORTED, "persistent FFT kernel does not fit on an SM");
-    P.n_cb = N / 2 / COL_CW;
+    P.n_cb = N / 2 / kCW;
     P.n_rb = N / kRB;
     const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, per_sm) : per_sm;
     kern<<<n_sm * per, kPT, smem, st>>>(P);
