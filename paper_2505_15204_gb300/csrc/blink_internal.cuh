@@ -207,6 +207,40 @@ template <> __device__ __forceinline__ void idft<8>(float2* v) {
     v[7] = csub(e3, t3);
 }
 
+template <> __device__ __forceinline__ void idft<16>(float2* v) {
+    // 4 x 4: 4-point transforms over r1 of v[4 r1 + r2], twiddles exp(2 pi i r2 q1 / 16), then 4-point
+    // transforms over r2, giving v[q1 + 4 q2]
+    const float c = 0.92387953251128675613f, s = 0.38268343236508977173f, h = 0.70710678118654752440f;
+    float2 a[4][4];
+#pragma unroll
+    for (int r2 = 0; r2 < 4; r2++) {
+        a[r2][0] = v[r2];
+        a[r2][1] = v[4 + r2];
+        a[r2][2] = v[8 + r2];
+        a[r2][3] = v[12 + r2];
+        idft<4>(a[r2]);
+    }
+    auto rot = [](float2 x, float cr, float ci) { return make_float2(x.x * cr - x.y * ci, x.x * ci + x.y * cr); };
+    a[1][1] = rot(a[1][1], c, s);                                               // w^1
+    a[1][2] = make_float2((a[1][2].x - a[1][2].y) * h, (a[1][2].x + a[1][2].y) * h);   // w^2
+    a[1][3] = rot(a[1][3], s, c);                                               // w^3
+    a[2][1] = make_float2((a[2][1].x - a[2][1].y) * h, (a[2][1].x + a[2][1].y) * h);   // w^2
+    a[2][2] = cmul_i(a[2][2]);                                                  // w^4
+    a[2][3] = make_float2((-a[2][3].x - a[2][3].y) * h, (a[2][3].x - a[2][3].y) * h);  // w^6
+    a[3][1] = rot(a[3][1], s, c);                                               // w^3
+    a[3][2] = make_float2((-a[3][2].x - a[3][2].y) * h, (a[3][2].x - a[3][2].y) * h);  // w^6
+    a[3][3] = rot(a[3][3], -c, -s);                                             // w^9
+#pragma unroll
+    for (int q1 = 0; q1 < 4; q1++) {
+        float2 t[4] = {a[0][q1], a[1][q1], a[2][q1], a[3][q1]};
+        idft<4>(t);
+        v[q1] = t[0];
+        v[q1 + 4] = t[1];
+        v[q1 + 8] = t[2];
+        v[q1 + 12] = t[3];
+    }
+}
+
 // One pass of a batched, in-place Stockham autosort inverse FFT in shared memory.
 // BATCH transforms of N points; point p of transform `lane` lives at s[p * PS + lane * LS].
 // NS is the product of the radices of the earlier passes; tw is the transform's per-pass twiddle table.

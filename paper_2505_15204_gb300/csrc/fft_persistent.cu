@@ -4,8 +4,8 @@
 //   column task (image k, column block cb): gather-grid the block's 8 u-columns in shared memory and
 //       transform each along v (one warp per column), then write the block to the image's slot of a
 //       small ring of intermediates (kept in L2);
-//   row task (image k, row block rb): once all column tasks of image k are done, transform 8 rows
-//       along u (complex to real, one warp per row), scale by 1 / (W * 2K) and write the image rows.
+//   row task (image k, row block rb): once all column tasks of image k are done, transform 16 rows
+//       along u (complex to real, two per warp), scale by 1 / (W * 2K) and write the image rows.
 // CTAs take task tickets in order from a global counter.  The ticket stream is cut into segments of
 // (column tasks of image s) + (row tasks of image s - lag), so an image's row tasks come `lag` segments
 // after its column tasks.  Dependencies are per-image counters: a row task waits for the image's column
@@ -24,7 +24,8 @@ namespace {
 constexpr int kW = 8;                            // warps per CTA: columns per column task, rows per row task
 constexpr int kPT = 32 * kW;                     // threads
 constexpr int kCW = kW;                          // u columns per column task (one per warp)
-constexpr int kRB = kW;                          // rows per row task (one per warp)
+constexpr int kRPW = 2;                          // rows per warp in a row task
+constexpr int kRB = kW * kRPW;                   // rows per row task
 constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
 
 struct FftParams {
@@ -96,6 +97,32 @@ __host__ __device__ constexpr int even(int x) { return (x + 1) / 2 * 2; }
 // is free of bank conflicts.
 template <int N> __host__ __device__ constexpr int tile_ld() { return wfft_slots(N) + 16 / kCW; }
 
+// Two 256-point inverse transforms by one warp in two radix-16 Stockham passes: rows at s and s + stride
+// (padx layout), half-warp h transforms row h and lane j = lane % 16 takes butterfly j of each pass.  tw16
+// holds exp(2 pi i j r / 256) at [(r - 1) * 16 + j].  Results go to out(h, position, value).
+template <typename Out>
+__device__ __forceinline__ void warp_fft256x2(float2* s, int stride, const float2* tw16, int lane, Out& out) {
+    const int h = lane >> 4, j = lane & 15;
+    float2* b = s + h * stride;
+    float2 v[16];
+    // pass 1: inputs j + 16 r (padded: j + 17 r), outputs 16 j + r (padded: 17 j + r); both conflict-free
+#pragma unroll
+    for (int r = 0; r < 16; r++) v[r] = b[j + 17 * r];
+    idft<16>(v);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; r++) b[17 * j + r] = v[r];
+    __syncwarp();
+    // pass 2: inputs j + 16 r, twiddles of k = j, outputs j + 16 r (natural order)
+#pragma unroll
+    for (int r = 0; r < 16; r++) v[r] = b[j + 17 * r];
+#pragma unroll
+    for (int r = 1; r < 16; r++) v[r] = cmul(v[r], tw16[(r - 1) * 16 + j]);
+    idft<16>(v);
+#pragma unroll
+    for (int r = 0; r < 16; r++) out(h, j + 16 * r, v[r]);
+}
+
 // The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
 template <int N, typename T>
 __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
@@ -144,24 +171,39 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
     if (!wait_count(P, P.col_done + k, P.n_cb, s_flag)) return nullptr;
-    const int y = rb * kRB + r;
-    const T* row = static_cast<const T*>(P.H) + ((int64_t)slot * N + y) * P.ldh;
-    float2* dst = reinterpret_cast<float2*>(work) + r * LS;
-#pragma unroll
-    for (int q = lane; q <= M / 2; q += 32) {       // unrolled: every load of the row is issued at once
-        const float2 zk = ldcg_c(row + q);
-        const float2 zm = (q == 0) ? make_float2(0.f, 0.f) : ldcg_c(row + (M - q));
-        const float2 w = s_pre[q];                    // exp(2 pi i q / N); that of M - q is -conj(w)
-        dst[padx(q)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), w)));
-        if (q > 0 && q < M - q)
-            dst[padx(M - q)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), make_float2(-w.x, w.y))));
-    }
-    __syncwarp();
     const float w = P.wk[f];
     const float inv = 1.0f / (w > 0.f ? w : 1.f);
-    float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
-    auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
-    warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
+#pragma unroll
+    for (int h = 0; h < kRPW; h++) {
+        const int y = rb * kRB + h * kW + r;
+        const T* row = static_cast<const T*>(P.H) + ((int64_t)slot * N + y) * P.ldh;
+        float2* dst = reinterpret_cast<float2*>(work) + (h * kW + r) * LS;
+#pragma unroll
+        for (int q = lane; q <= M / 2; q += 32) {       // unrolled: every load of the rows is issued at once
+            const float2 zk = ldcg_c(row + q);
+            const float2 zm = (q == 0) ? make_float2(0.f, 0.f) : ldcg_c(row + (M - q));
+            const float2 wq = s_pre[q];                   // exp(2 pi i q / N); that of M - q is -conj(wq)
+            dst[padx(q)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), wq)));
+            if (q > 0 && q < M - q)
+                dst[padx(M - q)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), make_float2(-wq.x, wq.y))));
+        }
+    }
+    __syncwarp();
+    if constexpr (M == 256 && kRPW == 2) {
+        // both rows at once: rows h * kW + r of the buffer, image rows y0 + h * kW
+        float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + rb * kRB + r) * N);
+        auto store = [&](int h, int m, float2 v) { out[h * kW * (N / 2) + m] = make_float2(v.x * inv, v.y * inv); };
+        warp_fft256x2(reinterpret_cast<float2*>(work) + r * LS, kW * LS, s_twr, lane, store);
+    } else {
+#pragma unroll 1
+        for (int h = 0; h < kRPW; h++) {
+            const int y = rb * kRB + h * kW + r;
+            float2* dst = reinterpret_cast<float2*>(work) + (h * kW + r) * LS;
+            float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
+            auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
+            warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
+        }
+    }
     return P.row_done + k;
 }
 
@@ -187,7 +229,18 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
     const int tid = threadIdx.x;
     for (int e = tid; e < tw_size(N); e += kPT) s_twc[e] = P.tw[tws_col(N) + e];
     for (int e = tid; e <= M / 2; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
-    for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
+    if constexpr (M == 256 && kRPW == 2) {
+        // exp(2 pi i j r / 256) = exp(2 pi i m / N) with m = 2 j r: the pre-twiddle table's entry m, or minus
+        // that of m - N / 2 (entries 0 .. N / 2 are stored)
+        static_assert(15 * 16 <= tw_size(M), "radix-16 table must fit the row table's room");
+        for (int e = tid; e < 15 * 16; e += kPT) {
+            const int m = 2 * (e & 15) * (e / 16 + 1);
+            const float2 w = P.tw[tws_pre(N) + (m <= N / 2 ? m : m - N / 2)];
+            s_twr[e] = m <= N / 2 ? w : make_float2(-w.x, -w.y);
+        }
+    } else {
+        for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
+    }
     const int seg = P.n_cb + P.n_rb;
     const int total = (P.n_img + P.lag) * seg;
     if (tid == 0) s_ticket = atomicAdd(P.tickets, 1);
