@@ -355,18 +355,27 @@ template <int C> __device__ __forceinline__ int padq(int p) { return p + C * (p 
 // Slots a warp transform of n points needs (room for the C = 2 layout when the hoisted form is used).
 __host__ __device__ constexpr int wfft_slots(int n) { return n >= 256 ? n + n / 8 : n + n / 16; }
 
-template <int N, int R, int NS, int PR, int PW, bool OUT, typename T, typename Out>
-__device__ __forceinline__ void wfft_pass(T* s, const float2* tw, int lane, Out& out) {
+// MASKED (first pass only): point p = lane + 32 t holds data only if bit t of `occ` is set, else it reads as
+// zero without a shared-memory access.
+template <int N, int R, int NS, int PR, int PW, bool OUT, bool MASKED, typename T, typename Out>
+__device__ __forceinline__ void wfft_pass(T* s, const float2* tw, int lane, Out& out, uint32_t occ) {
     constexpr int NB = N / R;
     constexpr int PER = NB / 32;                    // butterflies per lane
     static_assert(NB % 32 == 0, "warp transform needs at least 32 butterflies per pass");
     static_assert(NS == 1 || NS == 8 || NS % 32 == 0, "unsupported pass layout");
+    static_assert(!MASKED || (NS == 1 && N <= 1024), "the occupancy mask covers the first pass of up to 1024 points");
     float2 v[PER][R];
     const int rbase = padq<PR>(lane);               // reads: j + r * NB, j = lane + 32 m, NB % 32 == 0
 #pragma unroll
     for (int m = 0; m < PER; m++) {
 #pragma unroll
-        for (int r = 0; r < R; r++) v[m][r] = ld_c(s + rbase + (32 * m + r * NB) * (16 + PR) / 16);
+        for (int r = 0; r < R; r++) {
+            const int t = (32 * m + r * NB) / 32;   // the point's index over the lanes
+            if (!MASKED || ((occ >> t) & 1u))
+                v[m][r] = ld_c(s + rbase + (32 * m + r * NB) * (16 + PR) / 16);
+            else
+                v[m][r] = make_float2(0.f, 0.f);
+        }
         if (NS > 1) {
             // k = j % NS
             const int k = (NS % 32 == 0) ? (lane + (32 * m) % NS) : (lane & (NS - 1));
@@ -406,15 +415,15 @@ __device__ __forceinline__ void wfft_pass(T* s, const float2* tw, int lane, Out&
 }
 
 // Whole transform by one warp on a padded array; OUT: the last pass hands results to `out`.  PR is the
-// layout the pass reads (C = 1 for the first).
-template <int N, int NS, int PR, bool OUT, typename T, typename Out>
-__device__ __forceinline__ void wfft_run(T* s, const float2* tw, int lane, Out& out) {
+// layout the pass reads (C = 1 for the first); MASKED: the first pass reads only the points `occ` marks.
+template <int N, int NS, int PR, bool OUT, bool MASKED, typename T, typename Out>
+__device__ __forceinline__ void wfft_run(T* s, const float2* tw, int lane, Out& out, uint32_t occ) {
     if constexpr (NS < N) {
         constexpr int R = radix_at(N, NS);
         constexpr bool LAST = NS * R == N;
         constexpr int PW = (NS == 8 && !LAST) ? 2 : 1;
-        wfft_pass<N, R, NS, PR, PW, OUT && LAST, T, Out>(s, tw, lane, out);
-        wfft_run<N, NS * R, PW, OUT, T, Out>(s, tw, lane, out);
+        wfft_pass<N, R, NS, PR, PW, OUT && LAST, MASKED && NS == 1, T, Out>(s, tw, lane, out, occ);
+        wfft_run<N, NS * R, PW, OUT, false, T, Out>(s, tw, lane, out, occ);
     }
 }
 
@@ -423,9 +432,19 @@ __device__ __forceinline__ void wfft_run(T* s, const float2* tw, int lane, Out& 
 template <int N, bool OUT, typename T, typename Out>
 __device__ __forceinline__ void warp_fft(T* s, const float2* tw, int lane, Out& out) {
     if constexpr (N >= 256)
-        wfft_run<N, 1, 1, OUT, T, Out>(s, tw, lane, out);
+        wfft_run<N, 1, 1, OUT, false, T, Out>(s, tw, lane, out, 0u);
     else
         fft_run<N, 1, 1, 32, 1, 0, OUT ? false : true, OUT, true, T, Out, true>(s, tw, lane, out);
+}
+
+// The same on a column whose points p = lane + 32 t are valid only where bit t of this lane's `occ` is set
+// (the rest of the array may hold stale data).  Sides below 256 take the generic form, which needs the
+// array zeroed, so callers only use this for N >= 256.
+template <int N, typename T>
+__device__ __forceinline__ void warp_fft_masked(T* s, const float2* tw, int lane, uint32_t occ) {
+    static_assert(N >= 256, "masked warp transform needs the hoisted form");
+    NoOut none;
+    wfft_run<N, 1, 1, false, true, T, NoOut>(s, tw, lane, none, occ);
 }
 
 __device__ __forceinline__ void dev_fail(int* status, int code) {
@@ -489,6 +508,45 @@ __device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent
             T* p = s + idx(u, v);
             st_c(p, cadd(ld_c(p), x));
         }
+        __syncwarp();
+        key = nkey;
+        x = nx;
+    }
+}
+
+// The same for a column array that is not zeroed (shift always applied): each cell's first contribution is
+// stored rather than added, and bit v / 32 of occ[v % 32] records that cell v holds data (occ zeroed by the
+// caller).  Only the first run of a chunk can continue a cell of the previous chunk, which it then adds to.
+template <typename T, typename Val, typename Idx>
+__device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__ ent, int beg, int end, int lane,
+                                                       T* s, Val val, Idx idx, uint32_t key, float2 x,
+                                                       uint32_t* occ) {
+    uint32_t prev = 0xFFFFFFFFu;                    // the last cell of the previous chunk
+    for (int base = beg; base < end; base += 32) {
+        const int i = base + lane;
+        uint32_t nkey;
+        float2 nx;
+        gather_entry(ent, i + 32, end, val, nkey, nx);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t k2 = __shfl_up_sync(0xFFFFFFFFu, key, d);
+            const float xr = __shfl_up_sync(0xFFFFFFFFu, x.x, d), xi = __shfl_up_sync(0xFFFFFFFFu, x.y, d);
+            if (lane >= d && k2 == key) {
+                x.x += xr;
+                x.y += xi;
+            }
+        }
+        const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, key, 1);
+        const uint32_t klast = __shfl_sync(0xFFFFFFFFu, key, min(31, end - 1 - base));
+        if (i < end && (lane == 31 || i + 1 >= end || knext != key)) {
+            const int u = ent_u(key), v = ent_v(key);
+            if ((u + v) & 1) x = make_float2(-x.x, -x.y);
+            T* p = s + idx(u, v);
+            if (key == prev) x = cadd(ld_c(p), x);
+            st_c(p, x);
+            atomicOr(occ + (v & 31), 1u << (v >> 5));
+        }
+        prev = klast;
         __syncwarp();
         key = nkey;
         x = nx;

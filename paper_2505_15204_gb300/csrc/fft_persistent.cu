@@ -126,7 +126,7 @@ __device__ __forceinline__ void warp_fft256x2(float2* s, int stride, const float
 // The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
 template <int N, typename T>
 __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
-                            int* s_flag) {
+                            uint32_t* s_occ, int* s_flag) {
     constexpr int CW = kCW, LD = tile_ld<N>();
     const int tid = threadIdx.x;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
@@ -146,13 +146,23 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     const int beg = off[u], end = off[u + 1];
     uint32_t key;
     float2 x;
-    gather_entry(P.ent, beg + lane, end, val, key, x);    // in flight while the column is zeroed
-    for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
-    __syncwarp();
-    warp_gather_column(P.ent, beg, end, lane, s, val, idx, true, key, x);
-    __syncwarp();
-    NoOut none;
-    warp_fft<N, false, T, NoOut>(col, s_twc, lane, none);
+    gather_entry(P.ent, beg + lane, end, val, key, x);    // in flight while the column is prepared
+    if constexpr (N >= 256 && N <= 1024) {
+        // no zeroing: the gridding marks the cells it writes, and the first pass reads only those
+        uint32_t* occ = s_occ + warp * 32;
+        occ[lane] = 0u;
+        __syncwarp();
+        warp_gather_column_occ(P.ent, beg, end, lane, s, val, idx, key, x, occ);
+        __syncwarp();
+        warp_fft_masked<N, T>(col, s_twc, lane, occ[lane]);
+    } else {
+        for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
+        __syncwarp();
+        warp_gather_column(P.ent, beg, end, lane, s, val, idx, true, key, x);
+        __syncwarp();
+        NoOut none;
+        warp_fft<N, false, T, NoOut>(col, s_twc, lane, none);
+    }
     // all columns transformed (the wait's barrier), and the ring slot free of its previous image
     if (!wait_count(P, prev_done >= P.n_rb ? nullptr : prev, P.n_rb, s_flag)) return nullptr;
     T* out = static_cast<T*>(P.H) + (int64_t)slot * N * P.ldh + cb * CW;
@@ -226,6 +236,7 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
     float2* s_twr = s_pre + even(M / 2 + 1);
     unsigned char* work = reinterpret_cast<unsigned char*>(s_twr + even(tw_size(M)));
     __shared__ int s_ticket, s_flag;
+    __shared__ uint32_t s_occ[kW * 32];            // per warp: occupancy of its column, one word per lane
     const int tid = threadIdx.x;
     for (int e = tid; e < tw_size(N); e += kPT) s_twc[e] = P.tw[tws_col(N) + e];
     for (int e = tid; e <= M / 2; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
         const int sg = t / seg, r = t - sg * seg;
         int* done = nullptr;
         if (r < P.n_cb) {
-            if (sg < P.n_img) done = column_task<N, T>(P, sg, r, s_twc, work, &s_flag);
+            if (sg < P.n_img) done = column_task<N, T>(P, sg, r, s_twc, work, s_occ, &s_flag);
         } else {
             const int k = sg - P.lag;
             if (k >= 0 && k < P.n_img) done = row_task<N, T>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
