@@ -4,8 +4,9 @@
 //   column task (image k, column block cb): gather-grid the block's 8 u-columns in shared memory and
 //       transform each along v (one warp per column), then write the block to the image's slot of a
 //       small ring of intermediates (kept in L2);
-//   row task (image k, row block rb): once all column tasks of image k are done, transform 16 rows
-//       along u (complex to real, two per warp), scale by 1 / (W * 2K) and write the image rows.
+//   row task (image k, row block rb): once all column tasks of image k are done, transform 32 rows
+//       along u (complex to real, in two batches of two rows per warp), scale by 1 / (W * 2K) and write
+//       the image rows.
 // CTAs take task tickets in order from a global counter.  The ticket stream is cut into segments of
 // (column tasks of image s) + (row tasks of image s - lag), so an image's row tasks come `lag` segments
 // after its column tasks.  Dependencies are per-image counters: a row task waits for the image's column
@@ -24,8 +25,9 @@ namespace {
 constexpr int kW = 8;                            // warps per CTA: columns per column task, rows per row task
 constexpr int kPT = 32 * kW;                     // threads
 constexpr int kCW = kW;                          // u columns per column task (one per warp)
-constexpr int kRPW = 2;                          // rows per warp in a row task
-constexpr int kRB = kW * kRPW;                   // rows per row task
+constexpr int kRPW = 2;                          // rows per warp in a row batch
+constexpr int kRB = kW * kRPW;                   // rows per row batch
+constexpr int kRowBatches = 2;                   // row batches per row task
 constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
 
 struct FftParams {
@@ -183,40 +185,44 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     if (!wait_count(P, P.col_done + k, P.n_cb, s_flag)) return nullptr;
     const float w = P.wk[f];
     const float inv = 1.0f / (w > 0.f ? w : 1.f);
-#pragma unroll
-    for (int h = 0; h < kRPW; h++) {
-        const int y = rb * kRB + h * kW + r;
-        const T* row = static_cast<const T*>(P.H) + ((int64_t)slot * N + y) * P.ldh;
-        float2* dst = reinterpret_cast<float2*>(work) + (h * kW + r) * LS;
-#pragma unroll
-        for (int q = lane; q <= M / 2; q += 32) {       // unrolled: every load of the rows is issued at once
-            const float2 zk = ldcg_c(row + q);
-            const float2 zm = (q == 0) ? make_float2(0.f, 0.f) : ldcg_c(row + (M - q));
-            const float2 wq = s_pre[q];                   // exp(2 pi i q / N); that of M - q is -conj(wq)
-            dst[padx(q)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), wq)));
-            if (q > 0 && q < M - q)
-                dst[padx(M - q)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), make_float2(-wq.x, wq.y))));
-        }
-    }
-    __syncwarp();
-    if constexpr (M == 256 && kRPW == 2) {
-        // both rows at once: rows h * kW + r of the buffer, image rows y0 + h * kW
-        float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + rb * kRB + r) * N);
-        auto store = [&](int h, int m, float2 v) { out[h * kW * (N / 2) + m] = make_float2(v.x * inv, v.y * inv); };
-        warp_fft256x2(reinterpret_cast<float2*>(work) + r * LS, kW * LS, s_twr, lane, store);
-    } else {
 #pragma unroll 1
+    for (int b = 0; b < kRowBatches; b++) {
+        const int y0 = (rb * kRowBatches + b) * kRB;       // the batch's rows: y0 + h * kW + r (warp r)
+#pragma unroll
         for (int h = 0; h < kRPW; h++) {
-            const int y = rb * kRB + h * kW + r;
+            const int y = y0 + h * kW + r;
+            const T* row = static_cast<const T*>(P.H) + ((int64_t)slot * N + y) * P.ldh;
             float2* dst = reinterpret_cast<float2*>(work) + (h * kW + r) * LS;
-            float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
-            auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
-            warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
+#pragma unroll
+            for (int q = lane; q <= M / 2; q += 32) {   // unrolled: every load of the rows is issued at once
+                const float2 zk = ldcg_c(row + q);
+                const float2 zm = (q == 0) ? make_float2(0.f, 0.f) : ldcg_c(row + (M - q));
+                const float2 wq = s_pre[q];               // exp(2 pi i q / N); that of M - q is -conj(wq)
+                dst[padx(q)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), wq)));
+                if (q > 0 && q < M - q)
+                    dst[padx(M - q)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), make_float2(-wq.x, wq.y))));
+            }
         }
+        __syncwarp();
+        if constexpr (M == 256 && kRPW == 2) {
+            // both rows at once: rows h * kW + r of the buffer, image rows y0 + h * kW + r
+            float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y0 + r) * N);
+            auto store = [&](int h, int m, float2 v) { out[h * kW * (N / 2) + m] = make_float2(v.x * inv, v.y * inv); };
+            warp_fft256x2(reinterpret_cast<float2*>(work) + r * LS, kW * LS, s_twr, lane, store);
+        } else {
+#pragma unroll 1
+            for (int h = 0; h < kRPW; h++) {
+                const int y = y0 + h * kW + r;
+                float2* dst = reinterpret_cast<float2*>(work) + (h * kW + r) * LS;
+                float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
+                auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
+                warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
+            }
+        }
+        __syncwarp();                                   // the warp's rows are rewritten by the next batch
     }
     return P.row_done + k;
 }
-
 
 template <int N, typename T> constexpr size_t fft_smem() {
     constexpr int M = N / 2;
@@ -268,10 +274,11 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
             if (k >= 0 && k < P.n_img) done = row_task<N, T>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
         }
         // every thread's reads and writes of the task are done; thread 0 takes the next ticket and releases the
-        // task (the fence orders the whole CTA's accesses before the counter), its latencies overlapping
+        // task (the fence orders the whole CTA's accesses before the counter), its latencies overlapping.  (Taking
+        // the ticket earlier, during the task, measured slower.)
         __syncthreads();
         if (tid == 0) {
-            int nt = atomicAdd(P.tickets, 1);
+            const int nt = atomicAdd(P.tickets, 1);
             const int ab = ld_relaxed(P.tickets + 1);
             if (done) {
                 __threadfence();
@@ -296,7 +303,7 @@ blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
     }
     if (per_sm < 1) return set_error(BLINK_ERR_UNSUPPORTED, "persistent FFT kernel does not fit on an SM");
     P.n_cb = N / 2 / kCW;
-    P.n_rb = N / kRB;
+    P.n_rb = N / (kRB * kRowBatches);
     const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, per_sm) : per_sm;
     kern<<<n_sm * per, kPT, smem, st>>>(P);
     BLINK_CUDA(cudaGetLastError());
