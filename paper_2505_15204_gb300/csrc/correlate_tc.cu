@@ -16,9 +16,9 @@
 //
 // Per CTA (persistent, one per SM): TMA loads an item's raw voltage block (double buffered), all
 // threads unpack nibbles to e4m3 operand tiles in shared memory (K-major, no swizzle, 8x16-byte core
-// matrices), one thread issues the MMAs and commits them to an mbarrier, and four warps read the
-// accumulators back from TMEM (each warp its 32 lanes), stage them in shared memory and write the
-// visibilities.  Every wait is bounded; on expiry the CTA records BLINK_ERR_TIMEOUT, waits (bounded) for
+// matrices), one thread issues the MMAs and commits them to an mbarrier, and the 16 warps read the
+// accumulators back from TMEM (four warps per 32-lane quarter, 16 columns each), stage them in shared memory
+// (two buffers: the next block pair is staged while the previous one is written) and write the visibilities.  Every wait is bounded; on expiry the CTA records BLINK_ERR_TIMEOUT, waits (bounded) for
 // its own copies, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -32,11 +32,12 @@ namespace blink {
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 512;                   // 16 warps: four per TMEM lane quarter
 constexpr int kUnitsPerBlk = 64;
 constexpr int kTmemCols = 512;
 constexpr int kPairsPerRound = kTmemCols / 64;
 constexpr int kStageLd = 65;                     // padded row of the epilogue staging tiles (floats)
+constexpr int kStageBuf = 2 * 64 * kStageLd;     // floats between the two staging buffers (re and im tiles)
 constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
 
 struct TcParams {
@@ -45,6 +46,7 @@ struct TcParams {
     int Kq;                  // K rounded up to a multiple of 4 (one 32-bit word of e4m3 values)
     int units, n_blk, Kr, Kp;
     int n_pairs, n_rounds;
+    int two_stage;           // two epilogue staging buffers (else one)
     int first_item, n_items;
     int raw_bytes;
     uint32_t off_raw0, off_raw1, off_re, off_im, off_lut, off_flags, off_bar, off_tmem;
@@ -130,6 +132,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -285,23 +297,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             }
             tc_fence_after();
             const int local = it - P.first_item;
-            for (int q = q0; q < q1; q++) {
+            // stage block pair q into buffer sb: warp w reads TMEM lanes 32 (w % 4) + lane, columns 16 (w / 4) ..
+            auto stage = [&](int q, int sb) {
+                const int row = (warp & 3) * 32 + lane, c0 = (warp >> 2) * 16;
+                float* st = (row < 64 ? st_re + row * kStageLd : st_im + (row - 64) * kStageLd) + sb * kStageBuf;
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q - q0) * 64 + c0, v);
+#pragma unroll
+                for (int cc = 0; cc < 16; cc++) st[c0 + cc] = __uint_as_float(v[cc]);
+            };
+            // write block pair q from buffer sb
+            auto write = [&](int q, int sb) {
                 int mb, jb;
                 pair_of(q, mb, jb);
-                const int row = warp * 32 + lane;
-                float* st = row < 64 ? st_re + row * kStageLd : st_im + (row - 64) * kStageLd;
-                uint32_t v[32];
-#pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(q - q0) * 64 + h * 32, v);
-#pragma unroll
-                    for (int cc = 0; cc < 32; cc++) st[h * 32 + cc] = __uint_as_float(v[cc]);
-                }
-                __syncthreads();
+                const float* sre = st_re + sb * kStageBuf;
+                const float* sim = st_im + sb * kStageBuf;
                 for (int e = tid; e < 64 * 64; e += kThreads) {
                     const int il = e >> 6, jl = e & 63;
                     const int ui = mb * 64 + il, uj = jb * 64 + jl;
-                    float re = st_re[il * kStageLd + jl], im = st_im[il * kStageLd + jl];
+                    float re = sre[il * kStageLd + jl], im = sim[il * kStageLd + jl];
                     if (P.mode == CORR_OUT_VIS4) {
                         if (ui >= P.units) continue;
                         const int ai = ui >> 1, aj = uj >> 1;
@@ -319,7 +333,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                         static_cast<float2*>(P.out)[(int64_t)local * P.out_item_stride + b] = make_float2(re, im);
                     }
                 }
+            };
+            if (P.two_stage) {
+                stage(q0, 0);
                 __syncthreads();
+                for (int q = q0; q < q1; q++) {
+                    if (q + 1 < q1) stage(q + 1, (q + 1 - q0) & 1);
+                    write(q, (q - q0) & 1);
+                    __syncthreads();
+                }
+            } else {
+                for (int q = q0; q < q1; q++) {
+                    stage(q, 0);
+                    __syncthreads();
+                    write(q, 0);
+                    __syncthreads();
+                }
             }
             tc_fence_before();
             __syncthreads();
@@ -388,10 +417,11 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     off = align_up(off + P.raw_bytes, 128);
     P.off_raw1 = off;
     off = align_up(off + P.raw_bytes, 128);
-    P.off_re = off;
-    off += 64 * kStageLd * 4;
-    P.off_im = off;
-    off = align_up(off + 64 * kStageLd * 4, 16);
+    P.off_re = off;                                // buffer b: re at off_re + b * kStageBuf, im 64 rows on
+    P.off_im = off + 64 * kStageLd * 4;
+    const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32;   // LUT, flags, barriers, TMEM slot
+    P.two_stage = off + 2 * kStageBuf * 4 + tail <= 227 * 1024;
+    off = align_up(off + (P.two_stage ? 2 : 1) * kStageBuf * 4, 16);
     P.off_lut = off;
     off += 256 * 4;
     P.off_flags = off;
