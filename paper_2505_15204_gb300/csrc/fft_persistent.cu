@@ -2,8 +2,8 @@
 //
 // The work is two kinds of task per image (Sec. 5.2.4, Eq. 4):
 //   column task (image k, column block cb): gather-grid the block's 8 u-columns in shared memory and
-//       transform each along v (one warp per column), then write the block to the image's slot of a
-//       small ring of intermediates (kept in L2);
+//       transform each along v (one warp per column; 512 points in a radix-16 and a radix-32 pass), then
+//       write the block to the image's slot of a small ring of intermediates (kept in L2);
 //   row task (image k, row block rb): once all column tasks of image k are done, transform 32 rows
 //       along u (complex to real, in two batches of two rows per warp), scale by 1 / (W * 2K) and write
 //       the image rows.
@@ -125,6 +125,50 @@ __device__ __forceinline__ void warp_fft256x2(float2* s, int stride, const float
     for (int r = 0; r < 16; r++) out(h, j + 16 * r, v[r]);
 }
 
+// exp(2 pi i q / 32) for a compile-time q in [0, 16): cos(k pi / 16) for k = 0 .. 8 gives both parts.
+__device__ __forceinline__ float2 w32(int q) {
+    constexpr float C[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                            0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                            0.19509032201612826785f, 0.0f};
+    return make_float2(q <= 8 ? C[q] : -C[16 - q], C[q <= 8 ? 8 - q : q - 8]);
+}
+
+// One 512-point inverse transform by one warp in two Stockham passes: radix 16 (butterfly j = lane, points
+// j + 32 r), then radix 32 with twiddles of k = b (butterfly b = lane % 16, points b + 16 r), each radix-32
+// butterfly split over lanes b and b + 16: lane h = lane / 16 transforms the points of r = 2 s + h with 16
+// points and one exchange of the halves combines them.  Positions are padx; the first pass reads only the
+// points `occ` marks (point lane + 32 r: bit r) and treats the others as zero.  tw32 holds exp(2 pi i k r / 512)
+// at [r * 16 + k], r < 32, k < 16.
+template <typename T>
+__device__ __forceinline__ void warp_fft512(T* s, const float2* tw32, int lane, uint32_t occ) {
+    float2 v[16];
+    const int pj = lane + (lane >> 4);              // padx(lane + 32 r) = pj + 34 r
+    // pass 1: inputs lane + 32 r, outputs 16 lane + r (padded 17 lane + r): both conflict-free
+#pragma unroll
+    for (int r = 0; r < 16; r++) v[r] = ((occ >> r) & 1u) ? ld_c(s + pj + 34 * r) : make_float2(0.f, 0.f);
+    idft<16>(v);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; r++) st_c(s + 17 * lane + r, v[r]);
+    __syncwarp();
+    // pass 2: lane (b, h) reads points b + 16 (2 s + h) = lane + 32 s and twiddles them by exp(2 pi i b r / 512)
+    const int b = lane & 15, h = lane >> 4;
+#pragma unroll
+    for (int q = 0; q < 16; q++) v[q] = cmul(ld_c(s + pj + 34 * q), tw32[32 * q + lane]);
+    idft<16>(v);                                    // E (h = 0) or O (h = 1)
+    __syncwarp();
+    // X[q + 16 h] = E[q] + (-1)^h exp(2 pi i q / 32) O[q], at position b + 16 (q + 16 h) (padded b + 17 q + 272 h)
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        const float2 mine = v[q];
+        const float2 other = make_float2(__shfl_xor_sync(0xFFFFFFFFu, mine.x, 16),
+                                         __shfl_xor_sync(0xFFFFFFFFu, mine.y, 16));
+        const float2 e = h ? other : mine, t = cmul(h ? mine : other, w32(q));
+        st_c(s + b + 17 * q + 272 * h, h ? csub(e, t) : cadd(e, t));
+    }
+    __syncwarp();
+}
+
 // The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
 template <int N, typename T>
 __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
@@ -156,7 +200,10 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
         __syncwarp();
         warp_gather_column_occ(P.ent, beg, end, lane, s, val, idx, key, x, occ);
         __syncwarp();
-        warp_fft_masked<N, T>(col, s_twc, lane, occ[lane]);
+        if constexpr (N == 512)
+            warp_fft512(col, s_twc, lane, occ[lane]);
+        else
+            warp_fft_masked<N, T>(col, s_twc, lane, occ[lane]);
     } else {
         for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
         __syncwarp();
@@ -244,7 +291,17 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
     __shared__ int s_ticket, s_flag;
     __shared__ uint32_t s_occ[kW * 32];            // per warp: occupancy of its column, one word per lane
     const int tid = threadIdx.x;
-    for (int e = tid; e < tw_size(N); e += kPT) s_twc[e] = P.tw[tws_col(N) + e];
+    if constexpr (N == 512) {
+        // exp(2 pi i k r / 512) = the pre-twiddle table's entry m = k r, or minus that of m - 256
+        static_assert(32 * 16 <= even(tw_size(N)), "radix-32 table must fit the column table's room");
+        for (int e = tid; e < 32 * 16; e += kPT) {
+            const int m = (e & 15) * (e >> 4);
+            const float2 w = P.tw[tws_pre(N) + (m <= N / 2 ? m : m - N / 2)];
+            s_twc[e] = m <= N / 2 ? w : make_float2(-w.x, -w.y);
+        }
+    } else {
+        for (int e = tid; e < tw_size(N); e += kPT) s_twc[e] = P.tw[tws_col(N) + e];
+    }
     for (int e = tid; e <= M / 2; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
     if constexpr (M == 256 && kRPW == 2) {
         // exp(2 pi i j r / 256) = exp(2 pi i m / N) with m = 2 j r: the pre-twiddle table's entry m, or minus
