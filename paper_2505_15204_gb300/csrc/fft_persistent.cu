@@ -28,12 +28,14 @@ constexpr int kCW = kW;                          // u columns per column task (o
 constexpr int kRPW = 2;                          // rows per warp in a row batch
 constexpr int kRB = kW * kRPW;                   // rows per row batch
 constexpr int kRowBatches = 2;                   // row batches per row task
+constexpr int kVisAhead = 8;                     // images ahead whose visibilities a column task prefetches
 constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
 
 struct FftParams {
     const float2* vis;       // correlation sums of the chunk's images, [item][B]
     int64_t vis_stride;
     int vis_first;           // image id of vis row 0
+    uint32_t vis_prefetch;   // bytes of one image's visibilities when they can be prefetched (16-byte multiple), else 0
     int F, tau0, n_tau;      // images: channel-major order k -> (f = k / n_tau, tau = tau0 + k % n_tau)
     int n_img;
     int n_cb, n_rb;          // column tasks and row tasks per image
@@ -61,6 +63,12 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Asynchronous copy of [p, p + bytes) from memory into L2 (a hint: nothing waits for it).  p and bytes are
+// multiples of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ float2 ldcg_c(const float2* p) { return __ldcg(p); }
@@ -182,6 +190,11 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     const int* prev = k >= P.ring ? P.row_done + (k - P.ring) : nullptr;
     int prev_done = 0;
     if (tid == 0 && prev) prev_done = ld_acquire(prev);
+    // the visibilities of the image kVisAhead images on, brought into L2 for its gridding
+    if (kVisAhead > 0 && tid == 0 && cb == 0 && k + kVisAhead < P.n_img && P.vis_prefetch) {
+        const int k2 = k + kVisAhead, f2 = k2 / P.n_tau, id2 = (P.tau0 + k2 % P.n_tau) * P.F + f2;
+        prefetch_l2(P.vis + (int64_t)(id2 - P.vis_first) * P.vis_stride, P.vis_prefetch);
+    }
     T* s = reinterpret_cast<T*>(work);
     T* col = s + warp * LD;                              // this warp's column
     const float2* V = P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
@@ -385,6 +398,12 @@ blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec,
     P.vis = d_vis;
     P.vis_stride = vis_stride;
     P.vis_first = vis_first;
+    {
+        const uint64_t bytes = (uint64_t)p.B * sizeof(float2);
+        const bool ok = bytes % 16 == 0 && (vis_stride * sizeof(float2)) % 16 == 0 &&
+                        reinterpret_cast<uintptr_t>(d_vis) % 16 == 0 && bytes < (1ull << 31);
+        P.vis_prefetch = ok ? (uint32_t)bytes : 0u;
+    }
     P.F = p.F;
     P.tau0 = tau0;
     P.n_tau = n_tau;
