@@ -267,7 +267,9 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
         if constexpr (M == 256 && kRPW == 2) {
             // both rows at once: rows h * kW + r of the buffer, image rows y0 + h * kW + r
             float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y0 + r) * N);
-            auto store = [&](int h, int m, float2 v) { out[h * kW * (N / 2) + m] = make_float2(v.x * inv, v.y * inv); };
+            auto store = [&](int h, int m, float2 v) {      // streaming: the images are not read back
+                __stcs(out + h * kW * (N / 2) + m, make_float2(v.x * inv, v.y * inv));
+            };
             warp_fft256x2(reinterpret_cast<float2*>(work) + r * LS, kW * LS, s_twr, lane, store);
         } else {
 #pragma unroll 1
@@ -275,7 +277,7 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
                 const int y = y0 + h * kW + r;
                 float2* dst = reinterpret_cast<float2*>(work) + (h * kW + r) * LS;
                 float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
-                auto store = [&](int, int m, float2 v) { out[m] = make_float2(v.x * inv, v.y * inv); };
+                auto store = [&](int, int m, float2 v) { __stcs(out + m, make_float2(v.x * inv, v.y * inv)); };
                 warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
             }
         }
@@ -385,11 +387,11 @@ blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
 // Ring of column-pass results and the lag (in images) between an image's column and row tasks: the row
 // tasks trail by enough images that they rarely wait, and the ring is a little larger than the lag so that
 // reusing a slot rarely waits either, while staying small enough to live in L2.  The autotuner picks among
-// these shapes per plan (on the full-band chunk 24/16 measured best by hand as well).
+// these shapes per plan.
 std::vector<FftTune> fft_tune_candidates() {
-    return {{24, 16, 0}, {16, 8, 0}, {32, 24, 0}, {48, 32, 0}, {24, 16, 3}, {32, 24, 3}};
+    return {{24, 16, 0}, {16, 8, 0}, {32, 24, 0}, {48, 32, 0}, {64, 48, 0}, {40, 32, 0}, {32, 24, 3}};
 }
-int fft_ring_images_max() { return 48; }
+int fft_ring_images_max() { return 64; }
 
 blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec, const float2* d_vis,
                                    int64_t vis_stride, int vis_first, int tau0, int n_tau, void* d_H, int* d_counters,
