@@ -16,6 +16,10 @@ no collective on the data path; the timing is the max over ranks and `value` cou
 
 `--impl reference` times the CPU oracle (the only other implementation of the method here) on a
 bounded sample of the same workload, on the host cores.
+
+`--workload` runs one of the other synthetic workloads instead (tiny, coarse, precision, uneven; the
+default is the full-band one above); the uneven workload, four channel sets with their own flagged tiles
+and image sides, goes through `blink_pipeline_sets`.  `--cpu-threads` sets the oracle's thread count.
 """
 from __future__ import annotations
 
@@ -52,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--samples", type=int, default=0, help="voltage samples per step (default: the 50 ms chunk)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "coarse", "precision", "uneven", "fullband"])
+    ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (default: every host core)")
     return ap.parse_args()
 
 
@@ -158,6 +164,48 @@ def traffic_for(kernel: str, source: str):
 # the reference arm: the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------------------------------
 
+def workload_label(name: str, w) -> str:
+    if name == "fullband":
+        return ("fullband: 50 ms chunk, 144 tiles x 2 pol, 768 x 40 kHz (10 kHz averaged by 4), "
+                "50 x 1 ms (K = 40), 512^2 Stokes-I images")
+    return f"{name}: {w.description}"
+
+
+def image_sets(inp, w, ns):
+    """(set, first image, images, side) of every channel set of the workload, images packed per set."""
+    T = ns // w.samples_per_int
+    out, first = [], 0
+    for st in inp["sets"]:
+        n = T * (st.n_fine // w.chan_avg)
+        out.append((st, first, n, st.n_pix))
+        first += n
+    return out
+
+
+def oracle_sets_images(oracle, inp, w, sets, picks, threads):
+    """The oracle's images for the picked (set index, local image id) pairs, in order."""
+    out = []
+    for q, (st, _, _, side) in enumerate(sets):
+        ids = np.array([i for s_, i in picks if s_ == q], dtype=np.int64)
+        if len(ids) == 0:
+            continue
+        kw = {} if len(sets) == 1 else {"flags": st.flags, "fine0": st.fine0, "n_fine": st.n_fine}
+        ref = oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], w.samples_per_int, w.chan_avg, side, ids=ids,
+                              n_threads=threads, **kw)
+        out.extend(ref["images"])
+    return out
+
+
+def pick_images(sets, n):
+    """About n (set, local id) pairs spread evenly over every set's images."""
+    total = sum(c for _, _, c, _ in sets)
+    picks = []
+    for q, (_, _, cnt, _) in enumerate(sets):
+        k = max(1, round(n * cnt / total))
+        picks += [(q, int(i)) for i in oracle_sample_ids(cnt, min(k, cnt))]
+    return picks
+
+
 def oracle_sample_ids(n_total: int, n: int) -> np.ndarray:
     return np.unique(np.linspace(0, n_total - 1, n).round().astype(np.int64))
 
@@ -167,21 +215,24 @@ def run_reference(args, world, rank):
         return 0
     import blinksynth as bs
     import oracle
-    w = bs.WORKLOADS[WORKLOAD]
-    cores = os.cpu_count() or 1
+    w = bs.WORKLOADS[args.workload]
+    cores = args.cpu_threads or os.cpu_count() or 1
     ns = args.samples or w.samples_per_chunk
-    inp = bs.build_workload(WORKLOAD, chunk=4, workers=min(16, cores), n_samples=ns)
-    n_total = (ns // w.samples_per_int) * w.n_out_chan
+    chunk = min(4, w.n_chunks - 1)
+    inp = bs.build_workload(args.workload, chunk=chunk, workers=min(16, os.cpu_count() or 1), n_samples=ns)
+    sets = image_sets(inp, w, ns)
+    n_total = sum(c for _, _, c, _ in sets)
     n_per = max(2, cores)
-    ids = oracle_sample_ids(n_total, n_per * (args.steps + args.warmup))
+    picks = pick_images(sets, n_per * (args.steps + args.warmup))
     times = []
-    for s in range(args.warmup + args.steps):
-        sel = ids[s::args.warmup + args.steps][:n_per]
+    for s_ in range(args.warmup + args.steps):
+        sel = picks[s_::args.warmup + args.steps][:n_per]
+        if not sel:
+            sel = picks[:1]
         t = time.perf_counter()
-        oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], w.samples_per_int, w.chan_avg, w.n_pix[0], ids=sel,
-                        n_threads=cores)
+        oracle_sets_images(oracle, inp, w, sets, sel, cores)
         dt = time.perf_counter() - t
-        if s >= args.warmup:
+        if s_ >= args.warmup:
             times.append((len(sel), dt))
     n = sum(a for a, _ in times)
     tt = sum(b for _, b in times)
@@ -190,8 +241,8 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "images/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tt / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 50 ms chunk, 144 tiles, 768 x 40 kHz, 50 x 1 ms, 512^2 Stokes I",
-                   "images_per_step": n_per, "sample": "evenly spaced image ids of the chunk"},
+        "config": {"workload": workload_label(args.workload, w), "images_per_step": n_per,
+                   "sample": "evenly spaced image ids of the chunk"},
         "cpu_baseline": {"value": v, "unit": "images/s", "cores": cores, "kind": "oracle",
                          "sample": f"{n_per} images per step, ids evenly spaced over the {n_total}-image chunk"},
         "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -206,13 +257,14 @@ def run_reference(args, world, rank):
 
 def run_ours(args, world, rank, local):
     import blinksynth as bs
-    w = bs.WORKLOADS[WORKLOAD]
-    cores = os.cpu_count() or 1
+    w = bs.WORKLOADS[args.workload]
+    cores = args.cpu_threads or os.cpu_count() or 1
     ns = args.samples or w.samples_per_chunk
     from paper_2505_15204_gb300.shard import chunks_for_rank, job_rate, max_over_ranks
-    chunk = chunks_for_rank(w.n_chunks, rank, world, first=4)[0]
+    chunk = chunks_for_rank(w.n_chunks, rank, world, first=min(4, w.n_chunks - 1))[0]
     t_gen = time.perf_counter()
-    inp = bs.build_workload(WORKLOAD, chunk=chunk, workers=max(1, min(16, cores // max(1, world))), n_samples=ns)
+    host = os.cpu_count() or 1
+    inp = bs.build_workload(args.workload, chunk=chunk, workers=max(1, min(16, host // max(1, world))), n_samples=ns)
     t_gen = time.perf_counter() - t_gen
 
     import torch
@@ -224,26 +276,42 @@ def run_ours(args, world, rank, local):
         pg = dist
     from paper_2505_15204_gb300 import blink as B
 
-    n_tiles, n_pix, K = w.n_tiles, w.n_pix[0], w.k
-    T = ns // w.samples_per_int
-    n_img = T * w.n_out_chan
+    n_tiles, K = w.n_tiles, w.k
+    sets = image_sets(inp, w, ns)
+    multi = len(sets) > 1
+    n_pix = sets[0][3]
+    n_img = sum(c for _, _, c, _ in sets)
+    img_floats = sum(c * side * side for _, _, c, side in sets)
     arith = B.BLINK_CORR_FP8 if args.arith == "fp8" else B.BLINK_CORR_FP32
     mode = B.BLINK_MODE_BATCHED if args.mode == "batched" else B.BLINK_MODE_PLAIN
+    if multi and mode != B.BLINK_MODE_BATCHED:
+        raise SystemExit("several channel sets run only in the batched mode")
     ctx = B.blink_create(local)
     prec = B.BLINK_PREC_BF16 if args.precision == "bf16" else B.BLINK_PREC_FP32
     arr, obs = B.Array(inp["enu"]), B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns)
     im = B.Imaging(n_pix, precision=prec)
+    bsets = [B.Set(fine0=st.fine0, n_fine=st.n_fine, imaging=B.Imaging(side, precision=prec), flags=st.flags)
+             for st, _, _, side in sets]
     stream = torch.cuda.current_stream()
     volt = torch.from_numpy(inp["volt"]).cuda()
-    img = torch.empty((n_img, n_pix, n_pix), dtype=torch.float32, device="cuda")
+    if multi:
+        img = torch.empty(img_floats, dtype=torch.float32, device="cuda")
+    else:
+        img = torch.empty((n_img, n_pix, n_pix), dtype=torch.float32, device="cuda")
     wts = torch.empty(n_img, dtype=torch.float32, device="cuda")
 
+    def step(weights=None):
+        if multi:
+            B.blink_pipeline_sets(ctx, arr, obs, bsets, arith, volt, img, img_floats, stream)
+        else:
+            B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, weights, stream)
+
     t_plan = time.perf_counter()
-    B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, wts, stream)
+    step(wts)
     B.blink_sync(ctx, stream)
     t_plan = time.perf_counter() - t_plan
     for _ in range(args.warmup):
-        B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, None, stream)
+        step()
     B.blink_sync(ctx, stream)
 
     props = torch.cuda.get_device_properties(local)
@@ -259,9 +327,24 @@ def run_ours(args, world, rank, local):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
+    L2_BYTES = 129 * 2 ** 20
+    in_bytes, out_bytes = volt.numel(), img_floats * 4
+    small = in_bytes + out_bytes < 2 * L2_BYTES
+    if small:
+        # the step's data fit L2: time each step alone and overwrite L2 with a larger buffer in between
+        flush = torch.empty(4 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms_steps = sum(a.elapsed_time(b) for a, b in ev)
     e0.record(stream)
-    for _ in range(args.steps):
-        B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, None, stream)
+    if not small:
+        for _ in range(args.steps):
+            step()
     e1.record(stream)
     torch.cuda.synchronize()
     if pg:
@@ -270,7 +353,7 @@ def run_ours(args, world, rank, local):
     B.blink_set_profiling(ctx, False)
     B.blink_sync(ctx, stream)
     stage_ms, stage_n = B.blink_read_profile(ctx, stream, reset=True)
-    ms_total = e0.elapsed_time(e1)
+    ms_total = ms_steps if small else e0.elapsed_time(e1)
     ms_step = max_over_ranks(ms_total / args.steps, pg, "cuda")
     value = job_rate(n_img, world, ms_step / 1e3)
 
@@ -278,8 +361,11 @@ def run_ours(args, world, rank, local):
     dom = int(np.argmax(stage_ms)) if mode == B.BLINK_MODE_BATCHED else 1
     peak, peak_kind = measured_peaks()
     roof = None
+    def set_bytes(stage):
+        return sum(stage_bytes(stage, n_tiles, side, K) * c for _, _, c, side in sets)
+
     if stage_n[dom]:
-        bytes_total = stage_bytes(dom, n_tiles, n_pix, K) * n_img * args.steps
+        bytes_total = set_bytes(dom) * args.steps
         per_launch = bytes_total / stage_n[dom]
         avg_s = stage_ms[dom] / 1e3 / stage_n[dom]
         ach = per_launch / avg_s / 1e9
@@ -289,7 +375,7 @@ def run_ours(args, world, rank, local):
                 "traffic": traffic_for(kern, src), "kernel": kern, "stage": STAGE_NAMES[dom],
                 "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3, "peak_kind": f"{peak_kind} hbm_gbs"}
     stages = {STAGE_NAMES[s]: {"ms_per_step": stage_ms[s] / args.steps, "launches_per_step": stage_n[s] / args.steps,
-                               "GBps": (stage_bytes(s, n_tiles, n_pix, K) * n_img * args.steps / (stage_ms[s] / 1e3) / 1e9)
+                               "GBps": (set_bytes(s) * args.steps / (stage_ms[s] / 1e3) / 1e9)
                                if stage_ms[s] else None}
               for s in range(B.BLINK_N_STAGES)}
 
@@ -299,25 +385,28 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_cpu:
         import oracle
         n_s = max(4, 4 * cores)
-        ids = oracle_sample_ids(n_img, n_s)
+        picks = pick_images(sets, n_s)
         t = time.perf_counter()
-        ref = oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], w.samples_per_int, w.chan_avg, n_pix, ids=ids,
-                              n_threads=cores)
+        refs = oracle_sets_images(oracle, inp, w, sets, picks, cores)
         dt = time.perf_counter() - t
-        got = img[torch.from_numpy(ids).cuda()].cpu().numpy()
-        errs = [float(np.linalg.norm(got[k] - ref["images"][k]) / np.linalg.norm(ref["images"][k]))
-                for k in range(len(ids))]
+        flat = img.reshape(-1)
+        got = []
+        for q, i in picks:
+            _, first, _, side = sets[q]
+            off = sum(c * sd * sd for _, _, c, sd in sets[:q]) + i * side * side
+            got.append(flat[off:off + side * side].reshape(side, side).cpu().numpy())
+        errs = [float(np.linalg.norm(g - r) / np.linalg.norm(r)) for g, r in zip(got, refs)]
         gate = 1e-4 if args.precision == "fp32" else None
         parity = {"images_checked": len(ids), "max_rel_rms": max(errs), "gate": gate,
                   "pass": (max(errs) <= 1e-4) if gate else None,
-                  "max_abs": float(max(np.abs(got[k] - ref["images"][k]).max() for k in range(len(ids))))}
+                  "max_abs": float(max(np.abs(g - r).max() for g, r in zip(got, refs)))}
         if world == 1:
-            cpu = {"value": len(ids) / dt, "unit": "images/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{len(ids)} images, ids evenly spaced over the {n_img}-image chunk"}
+            cpu = {"value": len(picks) / dt, "unit": "images/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{len(picks)} images, ids evenly spaced over the {n_img}-image chunk"}
 
     # cuFFT's batched complex-to-real transform of grids of the same shape (a timing reference only)
     cufft = None
-    if args.cufft and rank == 0:
+    if args.cufft and rank == 0 and not multi:
         nb = 768
         g = torch.randn((nb, n_pix, n_pix // 2 + 1), dtype=torch.complex64, device="cuda")
         o = torch.empty((nb, n_pix, n_pix), dtype=torch.float32, device="cuda")
@@ -337,8 +426,8 @@ def run_ours(args, world, rank, local):
 
     # end to end through the host-buffer entry point (pinned voltages in, pinned images out)
     e2e = None
-    if not args.no_e2e:
-        ns_e = 5 * w.samples_per_int
+    if not args.no_e2e and not multi:
+        ns_e = min(5 * w.samples_per_int, ns)
         n_e = (ns_e // w.samples_per_int) * w.n_out_chan
         obs_e = B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns_e)
         h_volt = torch.from_numpy(np.ascontiguousarray(inp["volt"][:ns_e])).pin_memory()
@@ -357,7 +446,7 @@ def run_ours(args, world, rank, local):
         ms_e = max_over_ranks(e0.elapsed_time(e1) / reps, pg, "cuda")
         e2e = {"value": job_rate(n_e, world, ms_e / 1e3), "unit": "images/s", "h2d_bytes_per_step": int(h_volt.numel()),
                "d2h_bytes_per_step": int(h_img.numel() * 4), "images_per_step": n_e,
-               "workload": "5 ms sub-chunk (5 integrations x 768 channels) of the same chunk"}
+               "workload": f"{ns_e // w.samples_per_int} integrations x {w.n_out_chan} channels of the same chunk"}
 
     launches = int(sum(stage_n))
     line = {
@@ -367,10 +456,13 @@ def run_ours(args, world, rank, local):
         "dtype": ("e4m3->f32 correlation" if arith == B.BLINK_CORR_FP8 else "f32 correlation")
                  + (", bf16-stored f32 grid/FFT" if args.precision == "bf16" else ", f32 grid/FFT"),
         "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: 50 ms chunk, 144 tiles x 2 pol, 768 x 40 kHz (10 kHz averaged by 4), "
-                               f"50 x 1 ms (K = 40), 512^2 Stokes-I images",
+        "config": {"workload": workload_label(args.workload, w),
                    "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
-                   "mode": args.mode, "precision": args.precision, "l2": "inputs 442 MB and outputs 40 GB per step exceed L2; no flush",
+                   "mode": args.mode, "precision": args.precision,
+                   "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
+                          "each step timed alone after a 516 MB buffer overwrite") if small else
+                         (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e9:.3g} GB per step exceed L2; "
+                          "no flush"),
                    "generate_s": round(t_gen, 2), "plan_s": round(t_plan, 3)},
         "roofline": roof, "stages": stages, "clocks": clocks, "gpu_launches": launches,
         "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "cufft_reference": cufft,
