@@ -397,7 +397,7 @@ def run_ours(args, world, rank, local):
             got.append(flat[off:off + side * side].reshape(side, side).cpu().numpy())
         errs = [float(np.linalg.norm(g - r) / np.linalg.norm(r)) for g, r in zip(got, refs)]
         gate = 1e-4 if args.precision == "fp32" else None
-        parity = {"images_checked": len(ids), "max_rel_rms": max(errs), "gate": gate,
+        parity = {"images_checked": len(picks), "max_rel_rms": max(errs), "gate": gate,
                   "pass": (max(errs) <= 1e-4) if gate else None,
                   "max_abs": float(max(np.abs(g - r).max() for g, r in zip(got, refs)))}
         if world == 1:
