@@ -2,11 +2,13 @@
 //
 // The work is two kinds of task per image (Sec. 5.2.4, Eq. 4):
 //   column task (image k, column block cb): gather-grid the block's 8 u-columns in shared memory and
-//       transform each along v (one warp per column; 512 points in a radix-16 and a radix-32 pass), then
-//       write the block to the image's slot of a small ring of intermediates (kept in L2);
+//       transform each along v (one warp per column; a side of 512 in a radix-16 and a radix-32 pass, other
+//       sides in radix-8 passes), then write the block to the image's slot of a small ring of intermediates
+//       (kept in L2);
 //   row task (image k, row block rb): once all column tasks of image k are done, transform 32 rows
-//       along u (complex to real, in two batches of two rows per warp), scale by 1 / (W * 2K) and write
-//       the image rows.
+//       along u (complex to real, in two batches of two rows per warp; 256-point rows in two radix-16
+//       passes over both rows at once), scale by 1 / (W * 2K) and write the image rows with streaming
+//       stores (they are not read back, so they should not displace the ring from L2).
 // CTAs take task tickets in order from a global counter.  The ticket stream is cut into segments of
 // (column tasks of image s) + (row tasks of image s - lag), so an image's row tasks come `lag` segments
 // after its column tasks.  Dependencies are per-image counters: a row task waits for the image's column
