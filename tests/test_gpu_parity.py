@@ -422,3 +422,28 @@ def test_pipeline_replays_in_a_cuda_graph(B, ctx):
     torch.cuda.synchronize()
     B.blink_sync(ctx)
     assert torch.equal(out, eager)
+
+
+def test_pipeline_sets_replays_in_a_cuda_graph(B, ctx):
+    # the uneven form as one graph: every set's correlation and persistent FFT launch captured together
+    w = bs.build_workload("uneven", n_samples=20)
+    volt, freqs, sets_w = w["volt"], w["freqs"], w["sets"]
+    sets = [B.Set(fine0=st.fine0, n_fine=16, imaging=B.Imaging(st.n_pix), flags=st.flags) for st in sets_w]
+    total = sum(2 * 16 * st.n_pix ** 2 for st in sets_w)
+    arr, obs, d = B.Array(w["enu"]), B.Obs(freqs, 1, 10, 20), dev(volt)
+    eager = torch.empty(total, dtype=torch.float32, device="cuda")
+    out = torch.zeros(total, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        B.blink_pipeline_sets(ctx, arr, obs, sets, 1, d, eager, total, stream=s)   # plans, tuning, workspace
+        B.blink_pipeline_sets(ctx, arr, obs, sets, 1, d, out, total, stream=s)
+    s.synchronize()
+    out.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        B.blink_pipeline_sets(ctx, arr, obs, sets, 1, d, out, total, stream=s)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    B.blink_sync(ctx)
+    assert torch.equal(out, eager)
