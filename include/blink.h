@@ -190,12 +190,16 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
 
 /*
  * blink_pipeline on host buffers: copies h_volt to device workspace, runs the batched path and delivers
- * the images to h_img, all ordered on `stream`.  When h_img lies in one page-locked allocation
- * (cudaHostAlloc, cudaHostRegister) the imaging kernel writes the images straight into it over the host
- * link, overlapping the transfer with the computation, and `images_per_pass` is ignored.  Otherwise the
- * images are staged in device memory and copied back in passes: `images_per_pass` (>= 1, 0 = all) bounds
- * that device image buffer.  Page-locked buffers make the call asynchronous: it returns after enqueueing
- * (blink_sync waits).
+ * the images to h_img, all ordered on `stream`.
+ *   images_per_pass == 0: when the device can write h_img - one page-locked allocation (cudaHostAlloc,
+ *     cudaHostRegister), or pageable memory on a device that reaches it through the host's page tables
+ *     (hardware-coherent links such as NVLink-C2C) - the imaging kernel writes the images straight into it,
+ *     overlapping the transfer with the computation; otherwise all images are staged in device memory and
+ *     copied back.
+ *   images_per_pass >= 1: the images are staged and copied back in passes of at most that many (bounding
+ *     the device image buffer).
+ * Page-locked or directly written buffers make the call asynchronous: it returns after enqueueing
+ * (blink_sync waits); a pageable buffer written directly must stay allocated until then.
  *   h_volt  host uint8 as the voltage layout (fine_stride channels per sample).
  *   h_img   host float [T * F][N][N].
  */

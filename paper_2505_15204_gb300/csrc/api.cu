@@ -482,15 +482,26 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
     return BLINK_OK;
 }
 
-// Device address of a host buffer of `bytes` bytes that lies in page-locked (cudaHostAlloc or
-// cudaHostRegister) memory mapped for the device, judged by its first and last byte; NULL otherwise
-// (pageable memory, or a runtime that cannot map it).
+// Device address of a host buffer of `bytes` bytes that the current device can write: page-locked
+// (cudaHostAlloc or cudaHostRegister) memory mapped for the device, judged by its first and last byte, or
+// pageable memory on a device that reaches it through the host's page tables (hardware-coherent host
+// links); NULL otherwise.
 float* device_view(float* h, size_t bytes) {
     if (!h || !bytes) return nullptr;
     cudaPointerAttributes a{}, b{};
     if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
+    }
+    if (a.type == cudaMemoryTypeUnregistered) {
+        int dev = 0, pageable = 0, host_tables = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return pageable && host_tables ? h : nullptr;
     }
     const char* last = reinterpret_cast<const char*>(h) + bytes - 1;
     if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
@@ -832,9 +843,10 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
     if (n_img == 0) return BLINK_OK;
     const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
     const size_t vbytes = (size_t)obs->n_samples * ss;
-    // page-locked output: the imaging kernel writes the images straight into h_img, so the transfer over the
-    // host link overlaps the computation instead of following it
-    if (float* direct = device_view(h_img, (size_t)n_img * p->N * p->N * sizeof(float))) {
+    // output the device can write: the imaging kernel writes the images straight into h_img, so the transfer
+    // over the host link overlaps the computation instead of following it
+    float* direct = images_per_pass == 0 ? device_view(h_img, (size_t)n_img * p->N * p->N * sizeof(float)) : nullptr;
+    if (direct) {
         void* dv = nullptr;
         BLINK_TRY(workspace(ctx, 2, vbytes, &dv));
         BLINK_CUDA(cudaMemcpyAsync(dv, h_volt, vbytes, cudaMemcpyHostToDevice, st));

@@ -280,9 +280,11 @@ def test_pipeline_host_buffers_equal_device_path(B, ctx):
 
 
 @pytest.mark.parametrize("pinned", [True, False])
-def test_pipeline_host_direct_and_staged_outputs(B, ctx, pinned):
-    # page-locked images are written by the imaging kernel over the host link; pageable ones are staged
-    # through device memory in passes: both equal the device path bit for bit (FP8 correlation, 512^2)
+@pytest.mark.parametrize("per_pass", [0, 3])
+def test_pipeline_host_direct_and_staged_outputs(B, ctx, pinned, per_pass):
+    # per_pass 0: images the device can write (page-locked, or pageable through the host page tables) are
+    # written by the imaging kernel over the host link; per_pass 3: staged through device memory in passes.
+    # Every form equals the device path bit for bit (FP8 correlation, 512^2)
     w, volt, freqs, _ = _case("coarse", 20, 8)
     arr, obs, im = B.Array(w["enu"]), B.Obs(freqs, 2, 10, 20), B.Imaging(512)
     n = 2 * (len(freqs) // 2)
@@ -292,7 +294,7 @@ def test_pipeline_host_direct_and_staged_outputs(B, ctx, pinned):
     h_img = torch.full((n, 512, 512), float("nan"), dtype=torch.float32)
     if pinned:
         h_volt, h_img = h_volt.pin_memory(), h_img.pin_memory()
-    B.blink_pipeline_host(ctx, arr, obs, im, 1, h_volt, h_img, images_per_pass=3)
+    B.blink_pipeline_host(ctx, arr, obs, im, 1, h_volt, h_img, images_per_pass=per_pass)
     B.blink_sync(ctx)
     assert np.array_equal(h_img.numpy(), d.cpu().numpy())
 
