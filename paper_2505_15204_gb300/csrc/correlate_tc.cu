@@ -257,9 +257,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                     if (p) continue;
                     unit = a; kp = k0; kh = P.Kq;
                 }
+                // a flagged tile's operand rows are zero, so every product involving it is exactly zero
+                const bool live = !sflags[a];
                 uint32_t w[4];
 #pragma unroll
-                for (int i = 0; i < 4; i++) w[i] = (k0 + i < P.K) ? lut[raw[(k0 + i) * per_k + r]] : 0u;
+                for (int i = 0; i < 4; i++) w[i] = (live && k0 + i < P.K) ? lut[raw[(k0 + i) * per_k + r]] : 0u;
                 const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], 0x0040), __byte_perm(w[2], w[3], 0x0040), 0x5410);
                 const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], 0x0051), __byte_perm(w[2], w[3], 0x0051), 0x5410);
                 const uint32_t nre = __byte_perm(__byte_perm(w[0], w[1], 0x0073), __byte_perm(w[2], w[3], 0x0073), 0x5410);
@@ -312,25 +314,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                 pair_of(q, mb, jb);
                 const float* sre = st_re + sb * kStageBuf;
                 const float* sim = st_im + sb * kStageBuf;
-                for (int e = tid; e < 64 * 64; e += kThreads) {
-                    const int il = e >> 6, jl = e & 63;
-                    const int ui = mb * 64 + il, uj = jb * 64 + jl;
-                    float re = sre[il * kStageLd + jl], im = sim[il * kStageLd + jl];
-                    if (P.mode == CORR_OUT_VIS4) {
+                // (flagged tiles need no test: their operand rows were zeroed in the unpack)
+                if (P.mode == CORR_OUT_VIS4) {
+                    for (int e = tid; e < 64 * 64; e += kThreads) {
+                        const int il = e >> 6, jl = e & 63;
+                        const int ui = mb * 64 + il, uj = jb * 64 + jl;
                         if (ui >= P.units) continue;
                         const int ai = ui >> 1, aj = uj >> 1;
                         if (aj > ai) continue;
-                        if (sflags[ai] | sflags[aj]) re = im = 0.f;
+                        const float re = sre[il * kStageLd + jl], im = sim[il * kStageLd + jl];
                         const int64_t b = (int64_t)ai * (ai + 1) / 2 + aj;
                         float* o = static_cast<float*>(P.out) + (int64_t)local * P.out_item_stride +
                                    (b * 4 + 2 * (ui & 1) + (uj & 1)) * 2;
                         *reinterpret_cast<float2*>(o) = make_float2(__fdiv_rn(re, div), __fdiv_rn(im, div));
-                    } else {
-                        // imaging kinds: the exact integer sums; the 1/K (or 1/2K) is applied with 1/W
+                    }
+                } else {
+                    // imaging kinds: the exact integer sums (the 1/K or 1/2K is applied with 1/W).  Each thread
+                    // keeps one column jl and steps down the rows, so consecutive lanes write consecutive
+                    // baselines of a row.
+                    constexpr int kRowStep = kThreads / 64;
+                    const int jl = tid & 63, uj = jb * 64 + jl;
+                    float2* out = static_cast<float2*>(P.out) + (int64_t)local * P.out_item_stride + uj;
+                    const float* pre = sre + jl;
+                    const float* pim = sim + jl;
+#pragma unroll 4
+                    for (int il = tid >> 6; il < 64; il += kRowStep) {
+                        const int ui = mb * 64 + il;
                         if (ui >= P.n_tiles || uj > ui) continue;
-                        if (sflags[ui] | sflags[uj]) re = im = 0.f;
-                        const int64_t b = (int64_t)ui * (ui + 1) / 2 + uj;
-                        static_cast<float2*>(P.out)[(int64_t)local * P.out_item_stride + b] = make_float2(re, im);
+                        out[(int64_t)ui * (ui + 1) / 2] = make_float2(pre[il * kStageLd], pim[il * kStageLd]);
                     }
                 }
             };
