@@ -72,8 +72,12 @@ def _load():
             lib.oracle_image.argtypes = [P, C.c_int, C.c_double, P]
             lib.oracle_pipeline.restype = C.c_int
             lib.oracle_pipeline.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
-                                            C.c_int, C.c_double, C.c_int, C.c_int, P, C.c_int64, C.c_int,
+                                            C.c_int, C.c_double, C.c_int, C.c_int, P, P, C.c_int64, C.c_int,
                                             P, P, P, P]
+            lib.oracle_apply_gains.restype = None
+            lib.oracle_apply_gains.argtypes = [P, C.c_int, P, P]
+            lib.oracle_grid_v.restype = C.c_double
+            lib.oracle_grid_v.argtypes = [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, P, P, C.c_int, P]
             _lib = lib
     return _lib
 
@@ -119,6 +123,20 @@ def correlate_one(volt: np.ndarray, ns: int, c: int, tau: int, f: int, flags=Non
     fl = _flags(flags, nt)
     _load().oracle_correlate_one(volt.ctypes.data + fine0 * nt * 2, nf, nt, ns, c, tau, f, _p(fl), _p(out))
     return out
+
+
+def apply_gains(S: np.ndarray, gains: np.ndarray) -> np.ndarray:
+    """Calibrated sums V_ij^pq = g_i^p S_ij^pq conj(g_j^q) (Sec. 5.2.3), complex128 [B][4].
+
+    ``S`` int64 [B][4][2] of one integration and channel; ``gains`` complex [n_tiles][2] (pol X, Y).
+    """
+    S = np.ascontiguousarray(S, dtype=np.int64)
+    g = np.ascontiguousarray(np.stack([np.real(gains), np.imag(gains)], axis=-1), dtype=np.float64)
+    nt = g.shape[0]
+    assert S.shape == (n_baselines(nt), 4, 2) and g.shape == (nt, 2, 2)
+    out = np.zeros((S.shape[0], 4, 2), dtype=np.float64)
+    _load().oracle_apply_gains(_p(S), nt, _p(g), _p(out))
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def visibilities(S: np.ndarray, K: int) -> np.ndarray:
@@ -200,8 +218,10 @@ def image(a: np.ndarray, W: float):
 
 def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int, c: int, n_pix: int,
              ids=None, flags=None, fine0: int = 0, n_fine: int | None = None, cell_lambda: float = 0.0,
-             pol: int = POL_I, autos: bool = True, n_threads: int = 1, want_grids: bool = False):
+             pol: int = POL_I, autos: bool = True, n_threads: int = 1, want_grids: bool = False, gains=None):
     """Dirty images for the listed image ids (id = tau * F + f) of one set.
+
+    ``gains``: complex [F][n_tiles][2] per output channel of the set, tile and polarisation, or None.
 
     Returns dict(images [n][N][N] float64, W [n], max_im [n], grids [n][N][N] complex128 or None).
     """
@@ -222,9 +242,14 @@ def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int,
     W = np.zeros(n, dtype=np.float64)
     mx = np.zeros(n, dtype=np.float64)
     grids = np.zeros((n, n_pix, n_pix, 2), dtype=np.float64) if want_grids else None
+    g = None
+    if gains is not None:
+        gains = np.asarray(gains)
+        assert gains.shape == (F, nt, 2)
+        g = np.ascontiguousarray(np.stack([np.real(gains), np.imag(gains)], axis=-1), dtype=np.float64)
     rc = _load().oracle_pipeline(volt.ctypes.data + fine0 * nt * 2, nf_total, nt, n_fine, c, ns, _p(enu), _p(ff),
-                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), _p(ids), n, n_threads,
-                                 _p(grids), _p(imgs), _p(W), _p(mx))
+                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), _p(g), _p(ids), n,
+                                 n_threads, _p(grids), _p(imgs), _p(W), _p(mx))
     if rc:
         raise ValueError("oracle_pipeline: bad arguments")
     return {"images": imgs, "W": W, "max_im": mx,

@@ -11,6 +11,8 @@
  *               integration and the c fine channels of an output channel; lower triangle i >= j.
  *   uvw         Sec. 5.2.3-5.2.4: (u, v, w) = (r_i - r_j) * nu / c for every baseline and channel.
  *   cells       Sec. 5.2.4 (gridding "based on the (u, v) coordinates", nearest cell, no kernel).
+ *   gains       Sec. 5.2.3 (calibration and cable-length corrections): per-tile, per-polarisation complex
+ *               gains g, V_ij^pq = g_i^p S_ij^pq conj(g_j^q) (a diagonal Jones matrix per tile).
  *   grid        Sec. 5.2.4: natural weighting, every visibility and its Hermitian mirror weight 1.
  *   fft2        Eq. 4 / Sec. 5.2.4: unnormalised inverse 2D transform, own radix-2 FFT; direct DFT
  *               for small sides.
@@ -82,6 +84,32 @@ void oracle_correlate(const uint8_t* volt, int64_t fine_stride, int n_tiles, int
     for (int tau = 0; tau < T; tau++)
         for (int f = 0; f < F; f++)
             oracle_correlate_one(volt, fine_stride, n_tiles, ns, c, tau, f, flags, S + ((int64_t)tau * F + f) * per);
+}
+
+/*
+ * Calibration of one integration and channel (Sec. 5.2.3, corrections applied to the visibilities): with a
+ * diagonal Jones matrix diag(g_i^X, g_i^Y) per tile, V_ij^pq = g_i^p S_ij^pq conj(g_j^q).  g is complex
+ * double [n_tiles][2 pol][2] (re, im); S int64 [B][4][2]; V complex double [B][4][2] (raw sums, not / K).
+ */
+void oracle_apply_gains(const int64_t* S, int n_tiles, const double* g, double* V)
+{
+    for (int i = 0; i < n_tiles; i++) {
+        for (int j = 0; j <= i; j++) {
+            int64_t b = (int64_t)i * (i + 1) / 2 + j;
+            for (int p = 0; p < 2; p++) {
+                for (int q = 0; q < 2; q++) {
+                    double sr = (double)S[(b * 4 + 2 * p + q) * 2 + 0], si = (double)S[(b * 4 + 2 * p + q) * 2 + 1];
+                    double gr = g[(i * 2 + p) * 2 + 0], gi = g[(i * 2 + p) * 2 + 1];
+                    double hr = g[(j * 2 + q) * 2 + 0], hi = -g[(j * 2 + q) * 2 + 1];   /* conj(g_j^q) */
+                    /* (gr + i gi)(sr + i si) */
+                    double tr = gr * sr - gi * si, ti = gr * si + gi * sr;
+                    /* (tr + i ti)(hr + i hi) */
+                    V[(b * 4 + 2 * p + q) * 2 + 0] = tr * hr - ti * hi;
+                    V[(b * 4 + 2 * p + q) * 2 + 1] = tr * hi + ti * hr;
+                }
+            }
+        }
+    }
 }
 
 /* Output-channel centre frequency = mean of its c fine-channel centres (summed in order, then / c). */
@@ -166,6 +194,47 @@ double oracle_grid(const int64_t* S, int n_tiles, const uint8_t* flags, int K, i
             } else {
                 re = (double)s[0] / (double)K;
                 im = (double)s[1] / (double)K;
+            }
+            if (i == j) {
+                if (!autos) continue;
+                G[0] += re;
+                G[1] += im;
+                W += 1.0;
+                continue;
+            }
+            if (!keep[b]) continue;
+            int u = ((iu[b] % n) + n) % n, v = ((iv[b] % n) + n) % n;
+            int um = ((-iu[b] % n) + n) % n, vm = ((-iv[b] % n) + n) % n;
+            G[((int64_t)v * n + u) * 2 + 0] += re;
+            G[((int64_t)v * n + u) * 2 + 1] += im;
+            G[((int64_t)vm * n + um) * 2 + 0] += re;
+            G[((int64_t)vm * n + um) * 2 + 1] -= im;
+            W += 2.0;
+        }
+    }
+    return W;
+}
+
+/* oracle_grid for calibrated visibilities V (complex double [B][4][2], raw sums as from oracle_apply_gains):
+ * the same cells, weights and order of additions. */
+double oracle_grid_v(const double* V, int n_tiles, const uint8_t* flags, int K, int pol, int autos,
+                     const int32_t* iu, const int32_t* iv, const uint8_t* keep, int n_pix, double* G)
+{
+    int n = n_pix;
+    memset(G, 0, (size_t)n * n * 2 * sizeof(double));
+    double W = 0.0;
+    for (int i = 0; i < n_tiles; i++) {
+        for (int j = 0; j <= i; j++) {
+            if (flags && (flags[i] || flags[j])) continue;
+            int64_t b = (int64_t)i * (i + 1) / 2 + j;
+            const double* s = V + b * 8;
+            double re, im;
+            if (pol == ORC_POL_I) {
+                re = (s[0] + s[6]) / (2.0 * (double)K);
+                im = (s[1] + s[7]) / (2.0 * (double)K);
+            } else {
+                re = s[0] / (double)K;
+                im = s[1] / (double)K;
             }
             if (i == j) {
                 if (!autos) continue;
@@ -273,13 +342,14 @@ double oracle_image(const double* a, int n, double W, double* img)
  * The whole path for a list of images of one set (one flag vector, one image side): for each image id
  * (= tau * F + f) correlate, compute uvw and cells at the output channel's frequency, grid, transform and
  * form the image.  cell_lambda <= 0 selects the default cell over the set's highest output frequency.
+ * gains (or NULL): complex double [F][n_tiles][2 pol][2], applied to the sums before gridding.
  * Optional outputs (NULL to skip): grids [n_ids][N][N][2], images [n_ids][N][N], W [n_ids],
  * max|Im|/W [n_ids].  Images are independent, so they are spread over `n_threads` OpenMP threads.
  * Returns 0, or -1 on bad arguments.
  */
 int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n_fine, int c, int ns,
                     const double* enu, const double* fine_freq, const uint8_t* flags,
-                    int n_pix, double cell_lambda, int pol, int autos,
+                    int n_pix, double cell_lambda, int pol, int autos, const double* gains,
                     const int64_t* ids, int64_t n_ids, int n_threads,
                     double* grids, double* imgs, double* W_out, double* maxim_out)
 {
@@ -306,7 +376,15 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
         oracle_correlate_one(volt, fine_stride, n_tiles, ns, c, tau, f, flags, S);
         oracle_uvw(enu, n_tiles, fout[f], uvw);
         oracle_cells(uvw, B, du, n_pix, iu, iv, keep);
-        double W = oracle_grid(S, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
+        double W;
+        if (gains) {
+            double* V = (double*)malloc(sizeof(double) * B * 8);
+            oracle_apply_gains(S, n_tiles, gains + (int64_t)f * n_tiles * 4, V);
+            W = oracle_grid_v(V, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
+            free(V);
+        } else {
+            W = oracle_grid(S, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
+        }
         if (grids) memcpy(grids + q * 2 * n_pix * n_pix, G, sizeof(double) * 2 * n_pix * n_pix);
         if (oracle_ifft2(G, n_pix)) bad = 1;
         double mx = oracle_image(G, n_pix, W > 0.0 ? W : 1.0, im);

@@ -376,3 +376,83 @@ def test_pipeline_matches_stepwise_functions():
     assert np.array_equal(out["grids"][0], G)
     img, _ = oracle.image(oracle.ifft2(G), W)
     assert np.array_equal(out["images"][0], img)
+
+
+# ----------------------------------------------------------------------------------------------
+# calibration gains (Sec. 5.2.3): V_ij^pq = g_i^p S_ij^pq conj(g_j^q)
+# ----------------------------------------------------------------------------------------------
+
+def _unpack(volt):
+    b = volt.astype(np.int64)
+    lo, hi = b & 0xF, (b >> 4) & 0xF
+    return (np.where(lo >= 8, lo - 16, lo) + 1j * np.where(hi >= 8, hi - 16, hi)).astype(np.complex128)
+
+
+def _random_gains(n_tiles, seed, shape=()):
+    rng = np.random.default_rng(seed)
+    amp = rng.uniform(0.5, 1.5, size=shape + (n_tiles, 2))
+    ph = rng.uniform(-np.pi, np.pi, size=shape + (n_tiles, 2))
+    return amp * np.exp(1j * ph)
+
+
+def test_gains_equal_brute_force_on_calibrated_voltages():
+    # gains applied to the voltages before the products, summed directly in complex FP64: another order of
+    # the same arithmetic (catches a conjugate on the wrong gain or a swapped polarisation)
+    rng = np.random.default_rng(11)
+    nt, ns = 5, 7
+    volt = rng.integers(0, 256, size=(ns, 1, nt, 2), dtype=np.uint8)
+    g = _random_gains(nt, 12)
+    x = _unpack(volt)[:, 0] * g[None]                  # [t][tile][pol]
+    S = oracle.correlate(volt, ns, 1)[0, 0]
+    V = oracle.apply_gains(S, g)
+    for i in range(nt):
+        for j in range(i + 1):
+            for p in range(2):
+                for q in range(2):
+                    ref = np.sum(x[:, i, p] * np.conj(x[:, j, q]))
+                    assert abs(V[_bidx(i, j), 2 * p + q] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+def test_unit_gains_change_nothing():
+    w = bs.build_workload("tiny")
+    S = oracle.correlate(w["volt"], 10, 1)[0, 0]
+    V = oracle.apply_gains(S, np.ones((128, 2), dtype=np.complex128))
+    assert np.array_equal(V, S[..., 0] + 1j * S[..., 1])
+    a = oracle.pipeline(w["volt"], w["enu"], w["freqs"], 10, 1, 64)
+    b = oracle.pipeline(w["volt"], w["enu"], w["freqs"], 10, 1, 64, gains=np.ones((1, 128, 2), np.complex128))
+    assert np.array_equal(a["images"], b["images"]) and np.array_equal(a["W"], b["W"])
+
+
+def test_gains_keep_autocorrelations_hermitian():
+    # S_ii^XY = conj S_ii^YX survives calibration: g^X S conj(g^Y) = conj(g^Y conj(S) conj(g^X))
+    w = bs.build_workload("tiny")
+    S = oracle.correlate(w["volt"], 10, 1)[0, 0]
+    V = oracle.apply_gains(S, _random_gains(128, 3))
+    for i in range(0, 128, 7):
+        b = _bidx(i, i)
+        assert abs(V[b, 1] - np.conj(V[b, 2])) <= 1e-9 * abs(V[b, 1]) + 1e-9
+        assert abs(V[b, 0].imag) <= 1e-9 * abs(V[b, 0]) and V[b, 0].real >= 0
+
+
+def test_gains_undo_a_per_tile_phase_corruption():
+    # identical voltages at every tile (a noiseless source at the phase centre) seen through per-tile
+    # phases exp(i phi_a): uncalibrated, the centre pixel loses flux; with gains exp(-i phi_a) the image
+    # equals the uncorrupted one (the corruption is applied exactly, by rotating the unit-modulus samples
+    # 1 + 0i by quarter turns, which the 4-bit format represents without rounding)
+    nt, ns = 8, 10
+    turns = np.arange(nt) % 4                           # phi_a = turns * pi / 2
+    rot = {0: (1, 0), 1: (0, 1), 2: (-1 & 0xF, 0), 3: (0, -1 & 0xF)}
+    volt = np.zeros((ns, 1, nt, 2), dtype=np.uint8)
+    clean = np.zeros_like(volt)
+    for a in range(nt):
+        re, im = rot[turns[a]]
+        volt[:, 0, a, :] = re | (im << 4)
+        clean[:, 0, a, :] = 1
+    enu = bs.tile_positions(nt, 200.0, 5)
+    freqs = np.array([150e6])
+    g = np.exp(-1j * turns * np.pi / 2)[None, :, None] * np.ones((1, nt, 2))
+    ref = oracle.pipeline(clean, enu, freqs, ns, 1, 32)["images"][0]
+    bad = oracle.pipeline(volt, enu, freqs, ns, 1, 32)["images"][0]
+    fixed = oracle.pipeline(volt, enu, freqs, ns, 1, 32, gains=g)["images"][0]
+    assert np.allclose(fixed, ref, rtol=0, atol=1e-12)
+    assert bad[16, 16] < 0.5 * ref[16, 16]
