@@ -66,6 +66,11 @@ typedef struct {
     int32_t n_tiles;            /* 1..512 */
     const double* enu_m;        /* host [n_tiles][3]: East, North, Up in metres */
     const uint8_t* flags;       /* host [n_tiles], non-zero = flagged (excluded); NULL = none flagged */
+    const float* gains;         /* host [F][n_tiles][2 pol][2] (re, im) or NULL: calibration (Sec. 5.2.3), a
+                                   diagonal Jones matrix per output channel and tile, applied to the products
+                                   as V_ij^pq = g_i^p S_ij^pq conj(g_j^q) inside the correlation; F = the call's
+                                   output channels (obs.n_fine / obs.chan_avg, for blink_pipeline_sets over
+                                   the call's whole channel axis).  Read during the call only. */
 } blink_array;
 
 /* The observation (Sec. 5.2.1-5.2.2 and the -t / -c options of the pipeline's command line). */

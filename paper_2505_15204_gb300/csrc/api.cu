@@ -49,6 +49,7 @@ blink_status check_array(const blink_array* a) {
     return BLINK_OK;
 }
 
+
 blink_status check_obs(const blink_obs* o, bool need_freq) {
     if (!o) return set_error(BLINK_ERR_INVALID_ARG, "obs descriptor is NULL");
     if (o->n_fine < 1) return set_error(BLINK_ERR_INVALID_ARG, "obs.n_fine must be >= 1");
@@ -247,6 +248,20 @@ blink_status workspace(blink_context* ctx, int slot, size_t bytes, void** out) {
     return BLINK_OK;
 }
 
+// The call's calibration gains (F output channels) copied to device workspace, or an empty reference.
+blink_status upload_gains(blink_context* ctx, const blink_array* a, int F, cudaStream_t st, GainRef* out) {
+    *out = GainRef{};
+    if (!a->gains || F < 1) return BLINK_OK;
+    const size_t n = (size_t)F * a->n_tiles * 4;
+    for (size_t i = 0; i < n; i++)
+        if (!std::isfinite(a->gains[i])) return set_error(BLINK_ERR_INVALID_ARG, "array.gains has a non-finite value");
+    void* d = nullptr;
+    BLINK_TRY(workspace(ctx, 6, n * sizeof(float), &d));
+    BLINK_CUDA(cudaMemcpyAsync(d, a->gains, n * sizeof(float), cudaMemcpyHostToDevice, st));
+    out->d = static_cast<const float2*>(d);
+    return BLINK_OK;
+}
+
 // The twiddle set of side N (see tws_total), made on the device on first use and kept in the context.
 blink_status twiddles(blink_context* ctx, int N, float2** out) {
     int lg = 0;
@@ -416,7 +431,7 @@ constexpr size_t kVisCapBytes = (size_t)4 << 30;
 
 blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
                          const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st,
-                         bool may_tune = true) {
+                         bool may_tune = true, GainRef gains = {}) {
     const int N = p.N, F = p.F;
     const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
     const int T = tau1 - tau0;
@@ -437,10 +452,10 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
             StageTimer t(ctx, BLINK_STAGE_CORRELATE, st);
             if (arith == BLINK_CORR_FP8)
                 BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
-                                          ctx->d_status, ctx->n_sm, st));
+                                          ctx->d_status, ctx->n_sm, st, gains));
             else
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
-                                           ctx->d_status, st));
+                                           ctx->d_status, st, gains));
         }
         if (!p.tuned && !may_tune) {
             // output over the host link: timings would measure the link, so run the default shape untuned
@@ -663,11 +678,13 @@ blink_status blink_correlate(blink_context* ctx, const blink_array* array, const
     const int n_items = T * p->F;
     if (n_items == 0) return BLINK_OK;
     const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
+    GainRef g;
+    BLINK_TRY(upload_gains(ctx, array, p->F, st, &g));
     if (arith == BLINK_CORR_FP8)
         return launch_corr_fp8(CORR_OUT_VIS4, d_volt, ss, *p, obs->samples_per_int, 0, n_items, d_vis, p->B * 8,
-                               ctx->d_status, ctx->n_sm, st);
+                               ctx->d_status, ctx->n_sm, st, g);
     return launch_corr_fp32(CORR_OUT_VIS4, d_volt, ss, *p, obs->samples_per_int, 0, n_items, d_vis, p->B * 8,
-                            ctx->d_status, st);
+                            ctx->d_status, st, g);
 }
 
 blink_status blink_grid(blink_context* ctx, const blink_array* array, const blink_obs* obs,
@@ -748,8 +765,10 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
     if (n_img == 0) return BLINK_OK;
     const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
     const int N = p->N;
+    GainRef g;
+    BLINK_TRY(upload_gains(ctx, array, p->F, st, &g));
     if (mode == BLINK_MODE_BATCHED) {
-        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, d_volt, ss, 0, T, d_img, st));
+        BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, d_volt, ss, 0, T, d_img, st, true, g));
     } else {
         const int cw = p->cw, ldh = N / 2 + cw;
         const size_t el = imaging->precision == BLINK_PREC_BF16 ? 4 : 8;
@@ -761,10 +780,10 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
         for (int id = 0; id < n_img; id++) {
             if (arith == BLINK_CORR_FP8)
                 BLINK_TRY(launch_corr_fp8(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B, ctx->d_status,
-                                          ctx->n_sm, st));
+                                          ctx->n_sm, st, g));
             else
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B,
-                                           ctx->d_status, st));
+                                           ctx->d_status, st, g));
             BLINK_CUDA(cudaMemsetAsync(grid, 0, (size_t)N * (N / 2 + 1) * sizeof(float2), st));
             BLINK_TRY(launch_grid_atomic(*p, static_cast<float2*>(vis), id, static_cast<float2*>(grid), st));
             BLINK_TRY(launch_colpass_grid(N, imaging->precision, p->d_tw, static_cast<float2*>(grid), 1, H, ldh, st));
@@ -803,7 +822,13 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
         need += (size_t)T * (st.n_fine / obs->chan_avg) * st.imaging.n_pix * st.imaging.n_pix;
     }
     if (need > img_capacity) return set_error(BLINK_ERR_INVALID_ARG, "img_capacity smaller than the sets' images");
+    if (array->gains)
+        for (int s = 0; s < n_sets; s++)
+            if (sets[s].fine0 % obs->chan_avg)
+                return set_error(BLINK_ERR_INVALID_ARG, "with gains, every set must start on an output channel");
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    GainRef g_all;
+    BLINK_TRY(upload_gains(ctx, array, obs->n_fine / obs->chan_avg, strm, &g_all));
     size_t at = 0;
     for (int s = 0; s < n_sets; s++) {
         const blink_set& st = sets[s];
@@ -816,9 +841,11 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
         Plan* p = nullptr;
         BLINK_TRY(get_plan(ctx, &a, &o, &st.imaging, true, strm, &p));
         const int64_t ss = sample_stride_bytes(&o, a.n_tiles);
+        GainRef g = g_all;
+        g.f0 = st.fine0 / obs->chan_avg;
         if (T > 0)
             BLINK_TRY(run_batched(ctx, *p, &o, st.imaging.precision, arith, d_volt + (int64_t)st.fine0 * a.n_tiles * 2,
-                                  ss, 0, T, d_img + at, strm));
+                                  ss, 0, T, d_img + at, strm, true, g));
         at += (size_t)T * p->F * p->N * p->N;
     }
     return BLINK_OK;
@@ -843,6 +870,8 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
     if (n_img == 0) return BLINK_OK;
     const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
     const size_t vbytes = (size_t)obs->n_samples * ss;
+    GainRef g;
+    BLINK_TRY(upload_gains(ctx, array, p->F, st, &g));
     // output the device can write: the imaging kernel writes the images straight into h_img, so the transfer
     // over the host link overlaps the computation instead of following it
     float* direct = images_per_pass == 0 ? device_view(h_img, (size_t)n_img * p->N * p->N * sizeof(float)) : nullptr;
@@ -851,7 +880,7 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
         BLINK_TRY(workspace(ctx, 2, vbytes, &dv));
         BLINK_CUDA(cudaMemcpyAsync(dv, h_volt, vbytes, cudaMemcpyHostToDevice, st));
         return run_batched(ctx, *p, obs, imaging->precision, arith, static_cast<uint8_t*>(dv), ss, 0, T, direct, st,
-                           false);
+                           false, g);
     }
     // passes of whole integrations (F images each), at least one integration per pass
     const int t_per = images_per_pass > 0 ? std::max(1, std::min(T, images_per_pass / p->F)) : T;
@@ -865,7 +894,7 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
         const int t1 = std::min(T, t0 + t_per);
         const size_t n = (size_t)(t1 - t0) * p->F;
         BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, static_cast<uint8_t*>(dv), ss, t0, t1,
-                              static_cast<float*>(di), st));
+                              static_cast<float*>(di), st, true, g));
         BLINK_CUDA(cudaMemcpyAsync(h_img + (int64_t)t0 * p->F * N * N, di, n * N * N * sizeof(float),
                                    cudaMemcpyDeviceToHost, st));
     }

@@ -17,11 +17,17 @@ constexpr int kStageFloat4 = 3072;                    // 48 KiB of staged sample
 __device__ __forceinline__ float nib_lo(unsigned b) { return (float)((int)(b << 28) >> 28); }
 __device__ __forceinline__ float nib_hi(unsigned b) { return (float)((int)(b << 24) >> 28); }
 
+// Gains (when given) multiply the products in the epilogue: V^pq = g_i^p S^pq conj(g_j^q).
+__device__ __forceinline__ float2 gain_prod(float2 gi, float sr, float si, float2 gjc) {
+    const float tr = gi.x * sr - gi.y * si, ti = gi.x * si + gi.y * sr;
+    return make_float2(tr * gjc.x - ti * gjc.y, tr * gjc.y + ti * gjc.x);
+}
+
 template <int OUT>
 __global__ void __launch_bounds__(kThreads)
 k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles, int ns, int c, int F,
             int first_item, const short2* __restrict__ bl, int64_t B, const uint8_t* __restrict__ flags,
-            void* __restrict__ out, int64_t out_item_stride, int kc) {
+            void* __restrict__ out, int64_t out_item_stride, int kc, const float2* __restrict__ gains, int gain_f0) {
     extern __shared__ float4 xs[];                    // [kc][n_tiles]
     const int item = first_item + blockIdx.y;
     const int tau = item / F, f = item - (item / F) * F;
@@ -83,10 +89,23 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
     }
 
     const float fk = (float)K;
+    const float2* g = gains ? gains + (int64_t)(gain_f0 + f) * n_tiles * 2 : nullptr;
 #pragma unroll
     for (int m = 0; m < kBpt; m++) {
         const int64_t b = (int64_t)blockIdx.x * kThreads * kBpt + m * kThreads + tid;
         if (b >= B) continue;
+        if (g) {
+            // calibrated products (p, q) = (X, X), (X, Y), (Y, X), (Y, Y) in acc slots 0-1, 2-3, 4-5, 6-7
+#pragma unroll
+            for (int pq = 0; pq < 4; pq++) {
+                const int p = pq >> 1, q = pq & 1;
+                if (OUT != CORR_OUT_VIS4 && p != q) continue;
+                const float2 gi = g[bi[m] * 2 + p], gj = g[bj[m] * 2 + q];
+                const float2 v = gain_prod(gi, acc[m][2 * pq], acc[m][2 * pq + 1], make_float2(gj.x, -gj.y));
+                acc[m][2 * pq] = v.x;
+                acc[m][2 * pq + 1] = v.y;
+            }
+        }
         if (OUT == CORR_OUT_VIS4) {
             float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + (int64_t)blockIdx.y * out_item_stride +
                                                   b * 8);
@@ -110,7 +129,7 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
 
 blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
                               int first_item, int n_items, void* out, int64_t out_item_stride, int*,
-                              cudaStream_t st) {
+                              cudaStream_t st, GainRef gains) {
     const int kc = std::max(1, std::min(ns * p.chan_avg, kStageFloat4 / p.n_tiles));
     const size_t smem = (size_t)kc * p.n_tiles * sizeof(float4);
     const unsigned gx = (unsigned)((p.B + kThreads * kBpt - 1) / (kThreads * kBpt));
@@ -122,15 +141,15 @@ blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sampl
         switch (out_kind) {
             case CORR_OUT_VIS4:
                 k_corr_fp32<CORR_OUT_VIS4><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
-                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc);
+                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
                 break;
             case CORR_OUT_STOKES_I:
                 k_corr_fp32<CORR_OUT_STOKES_I><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
-                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc);
+                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
                 break;
             default:
                 k_corr_fp32<CORR_OUT_XX><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
-                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc);
+                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
         }
     }
     BLINK_CUDA(cudaGetLastError());

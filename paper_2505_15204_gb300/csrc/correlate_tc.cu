@@ -35,9 +35,8 @@ namespace {
 constexpr int kThreads = 512;                   // 16 warps: four per TMEM lane quarter
 constexpr int kUnitsPerBlk = 64;
 constexpr int kTmemCols = 512;
-constexpr int kPairsPerRound = kTmemCols / 64;
 constexpr int kStageLd = 65;                     // padded row of the epilogue staging tiles (floats)
-constexpr int kStageBuf = 2 * 64 * kStageLd;     // floats between the two staging buffers (re and im tiles)
+constexpr int kPlane = 64 * kStageLd;            // floats of one staging plane (64 x 64 values, padded rows)
 constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
 
 struct TcParams {
@@ -46,7 +45,14 @@ struct TcParams {
     int Kq;                  // K rounded up to a multiple of 4 (one 32-bit word of e4m3 values)
     int units, n_blk, Kr, Kp;
     int n_pairs, n_rounds;
+    int split;               // Stokes I with gains: XX and YY from separate MMA chains (per-polarisation K halves)
+    int Kpol;                // split: bytes of one polarisation's part of an operand row (a multiple of 32)
+    int pair_cols, pairs_per_round;   // TMEM columns per block pair (64, or 128 when split) and pairs per round
+    int stage_buf;           // floats per staging buffer: 2 planes (re, im), or 4 (re, im of XX, then of YY)
     int two_stage;           // two epilogue staging buffers (else one)
+    const float2* gains;     // calibration gains [channels][n_tiles][2 pol] or NULL; item channel f uses row gain_f0 + f
+    int gain_f0;
+    uint32_t off_gain;       // shared copy of the current item's gains [n_tiles][2]
     int first_item, n_items;
     int raw_bytes;
     uint32_t off_raw0, off_raw1, off_re, off_im, off_lut, off_flags, off_bar, off_tmem;
@@ -160,8 +166,9 @@ __device__ __forceinline__ void pair_of(int q, int& mb, int& jb) {
 __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ops = smem;                                   // n_blk tiles of 128 x Kp bytes
-    float* st_re = reinterpret_cast<float*>(smem + P.off_re);
+    float* st_re = reinterpret_cast<float*>(smem + P.off_re);   // plane 0 of buffer 0; planes kPlane apart
     float* st_im = reinterpret_cast<float*>(smem + P.off_im);
+    float2* s_g = reinterpret_cast<float2*>(smem + P.off_gain);
     uint32_t* lut = reinterpret_cast<uint32_t*>(smem + P.off_lut);   // raw byte -> e4m3 (re, im, im, -re)
     uint8_t* sflags = smem + P.off_flags;
     const uint32_t bar_tma0 = smem_u32(smem + P.off_bar), bar_tma1 = bar_tma0 + 8, bar_mma = bar_tma0 + 16;
@@ -239,6 +246,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             abort = true;
             break;
         }
+        if (P.gains) {
+            // this item's gains, read by the epilogue (after the barrier that ends the unpack)
+            const int f = it - (it / P.F) * P.F;
+            const float2* g = P.gains + (int64_t)(P.gain_f0 + f) * P.n_tiles * 2;
+            for (int e = tid; e < 2 * P.n_tiles; e += kThreads) s_g[e] = g[e];
+        }
         // ---- unpack nibbles to e4m3 operand rows, four consecutive k per 32-bit store -----------------
         // A task is (k group g, tile a, polarisation p): its four raw bytes give, through the LUT, the words
         // P_re, P_im (= Q_im) and Q_-re of four consecutive K positions of one unit row.
@@ -249,8 +262,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             for (int r = tid; r < per_k; r += kThreads) {
                 const int a = r >> 1, p = r & 1;
                 int unit, kp, kh;
-                if (P.mode == CORR_OUT_STOKES_I) {
-                    unit = a; kp = p * P.Kq + k0; kh = 2 * P.Kq;
+                if (P.mode == CORR_OUT_STOKES_I && P.split) {
+                    unit = a; kp = p * P.Kpol + k0; kh = P.Kq;          // [re, im] of X, then of Y
+                } else if (P.mode == CORR_OUT_STOKES_I) {
+                    unit = a; kp = p * P.Kq + k0; kh = 2 * P.Kq;        // re X, re Y, im X, im Y
                 } else if (P.mode == CORR_OUT_VIS4) {
                     unit = 2 * a + p; kp = k0; kh = P.Kq;
                 } else {
@@ -277,17 +292,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         __syncthreads();
         // ---- MMA rounds of up to 8 block pairs, each followed by its epilogue ---------------------------
         for (int r = 0; r < P.n_rounds && !abort; r++) {
-            const int q0 = r * kPairsPerRound, q1 = min(P.n_pairs, q0 + kPairsPerRound);
+            const int q0 = r * P.pairs_per_round, q1 = min(P.n_pairs, q0 + P.pairs_per_round);
             if (tid == 0) {
                 tc_fence_after();
+                const int nk = P.Kp / 32, nh = P.split ? nk / 2 : nk;
                 for (int q = q0; q < q1; q++) {
                     int mb, jb;
                     pair_of(q, mb, jb);
-                    const uint32_t d = tmem + (uint32_t)(q - q0) * 64;
+                    const uint32_t d = tmem + (uint32_t)((q - q0) * P.pair_cols);
                     const uint32_t a0 = ops_s + mb * tile_bytes, b0 = ops_s + jb * tile_bytes;
-                    for (int s = 0; s < P.Kp / 32; s++)
-                        mma_e4m3(d, smem_desc(a0 + s * 256, 128, sbo), smem_desc(b0 + s * 256, 128, sbo), idesc,
-                                 s > 0);
+                    // one chain over all of K, or (split) the X half into columns 0-63 and the Y half into 64-127
+                    for (int s = 0; s < nk; s++)
+                        mma_e4m3(s < nh ? d : d + 64, smem_desc(a0 + s * 256, 128, sbo),
+                                 smem_desc(b0 + s * 256, 128, sbo), idesc, s % nh > 0);
                 }
                 mma_commit(bar_mma);
             }
@@ -302,18 +319,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             // stage block pair q into buffer sb: warp w reads TMEM lanes 32 (w % 4) + lane, columns 16 (w / 4) ..
             auto stage = [&](int q, int sb) {
                 const int row = (warp & 3) * 32 + lane, c0 = (warp >> 2) * 16;
-                float* st = (row < 64 ? st_re + row * kStageLd : st_im + (row - 64) * kStageLd) + sb * kStageBuf;
+                float* st = (row < 64 ? st_re + row * kStageLd : st_im + (row - 64) * kStageLd) + sb * P.stage_buf;
+                const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((q - q0) * P.pair_cols) + c0;
                 uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q - q0) * 64 + c0, v);
+                tmem_ld16(ta, v);
 #pragma unroll
                 for (int cc = 0; cc < 16; cc++) st[c0 + cc] = __uint_as_float(v[cc]);
+                if (P.split) {                                 // YY: planes 2 and 3
+                    tmem_ld16(ta + 64, v);
+#pragma unroll
+                    for (int cc = 0; cc < 16; cc++) st[2 * kPlane + c0 + cc] = __uint_as_float(v[cc]);
+                }
             };
             // write block pair q from buffer sb
             auto write = [&](int q, int sb) {
                 int mb, jb;
                 pair_of(q, mb, jb);
-                const float* sre = st_re + sb * kStageBuf;
-                const float* sim = st_im + sb * kStageBuf;
+                const float* sre = st_re + sb * P.stage_buf;
+                const float* sim = st_im + sb * P.stage_buf;
                 // (flagged tiles need no test: their operand rows were zeroed in the unpack)
                 if (P.mode == CORR_OUT_VIS4) {
                     for (int e = tid; e < 64 * 64; e += kThreads) {
@@ -322,7 +345,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                         if (ui >= P.units) continue;
                         const int ai = ui >> 1, aj = uj >> 1;
                         if (aj > ai) continue;
-                        const float re = sre[il * kStageLd + jl], im = sim[il * kStageLd + jl];
+                        float re = sre[il * kStageLd + jl], im = sim[il * kStageLd + jl];
+                        if (P.gains) {                         // g_i^p S conj(g_j^q), unit u = 2 tile + pol
+                            const float2 gi = s_g[ui], gj = s_g[uj];
+                            const float tr = gi.x * re - gi.y * im, ti = gi.x * im + gi.y * re;
+                            re = tr * gj.x + ti * gj.y;
+                            im = ti * gj.x - tr * gj.y;
+                        }
                         const int64_t b = (int64_t)ai * (ai + 1) / 2 + aj;
                         float* o = static_cast<float*>(P.out) + (int64_t)local * P.out_item_stride +
                                    (b * 4 + 2 * (ui & 1) + (uj & 1)) * 2;
@@ -337,11 +366,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                     float2* out = static_cast<float2*>(P.out) + (int64_t)local * P.out_item_stride + uj;
                     const float* pre = sre + jl;
                     const float* pim = sim + jl;
+                    if (!P.gains) {
 #pragma unroll 4
-                    for (int il = tid >> 6; il < 64; il += kRowStep) {
-                        const int ui = mb * 64 + il;
-                        if (ui >= P.n_tiles || uj > ui) continue;
-                        out[(int64_t)ui * (ui + 1) / 2] = make_float2(pre[il * kStageLd], pim[il * kStageLd]);
+                        for (int il = tid >> 6; il < 64; il += kRowStep) {
+                            const int ui = mb * 64 + il;
+                            if (ui >= P.n_tiles || uj > ui) continue;
+                            out[(int64_t)ui * (ui + 1) / 2] = make_float2(pre[il * kStageLd], pim[il * kStageLd]);
+                        }
+                    } else {
+                        // calibrated: g_i^X S_XX conj(g_j^X) (+ g_i^Y S_YY conj(g_j^Y) for Stokes I, split)
+                        const int ujc = uj < P.n_tiles ? uj : 0;
+                        const float2 hx = s_g[2 * ujc], hy = s_g[2 * ujc + 1];
+                        for (int il = tid >> 6; il < 64; il += kRowStep) {
+                            const int ui = mb * 64 + il;
+                            if (ui >= P.n_tiles || uj > ui) continue;
+                            const float2 gx = s_g[2 * ui];
+                            float sr = pre[il * kStageLd], si = pim[il * kStageLd];
+                            float tr = gx.x * sr - gx.y * si, ti = gx.x * si + gx.y * sr;
+                            float vr = tr * hx.x + ti * hx.y, vi = ti * hx.x - tr * hx.y;
+                            if (P.split) {
+                                const float2 gy = s_g[2 * ui + 1];
+                                sr = pre[2 * kPlane + il * kStageLd];
+                                si = pim[2 * kPlane + il * kStageLd];
+                                tr = gy.x * sr - gy.y * si;
+                                ti = gy.x * si + gy.y * sr;
+                                vr += tr * hy.x + ti * hy.y;
+                                vi += ti * hy.x - tr * hy.y;
+                            }
+                            out[(int64_t)ui * (ui + 1) / 2] = make_float2(vr, vi);
+                        }
                     }
                 }
             };
@@ -399,7 +452,7 @@ uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
                              int first_item, int n_items, void* out, int64_t out_item_stride, int* d_status, int n_sm,
-                             cudaStream_t st) {
+                             cudaStream_t st, GainRef gains) {
     if (n_items <= 0) return BLINK_OK;
     const int nt = p.n_tiles, c = p.chan_avg, K = ns * c;
     if (nt % 8 || ns > 256 || c > 256 || ((uintptr_t)d_volt & 15) || (sample_stride % 16))
@@ -416,10 +469,17 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     P.units = out_kind == CORR_OUT_VIS4 ? 2 * nt : nt;
     P.n_blk = (P.units + kUnitsPerBlk - 1) / kUnitsPerBlk;
     P.Kq = (K + 3) / 4 * 4;
+    P.gains = gains.d;
+    P.gain_f0 = gains.f0;
+    P.split = gains.d && out_kind == CORR_OUT_STOKES_I;
+    P.Kpol = (2 * P.Kq + 31) / 32 * 32;
     P.Kr = out_kind == CORR_OUT_STOKES_I ? 4 * P.Kq : 2 * P.Kq;
-    P.Kp = (P.Kr + 31) / 32 * 32;
+    P.Kp = P.split ? 2 * P.Kpol : (P.Kr + 31) / 32 * 32;
     P.n_pairs = P.n_blk * (P.n_blk + 1) / 2;
-    P.n_rounds = (P.n_pairs + kPairsPerRound - 1) / kPairsPerRound;
+    P.pair_cols = P.split ? 128 : 64;
+    P.pairs_per_round = kTmemCols / P.pair_cols;
+    P.n_rounds = (P.n_pairs + P.pairs_per_round - 1) / P.pairs_per_round;
+    P.stage_buf = (P.split ? 4 : 2) * kPlane;
     P.first_item = first_item;
     P.n_items = n_items;
     P.raw_bytes = ns * c * nt * 2;
@@ -428,11 +488,13 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     off = align_up(off + P.raw_bytes, 128);
     P.off_raw1 = off;
     off = align_up(off + P.raw_bytes, 128);
-    P.off_re = off;                                // buffer b: re at off_re + b * kStageBuf, im 64 rows on
-    P.off_im = off + 64 * kStageLd * 4;
-    const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32;   // LUT, flags, barriers, TMEM slot
-    P.two_stage = off + 2 * kStageBuf * 4 + tail <= 227 * 1024;
-    off = align_up(off + (P.two_stage ? 2 : 1) * kStageBuf * 4, 16);
+    P.off_re = off;                                // buffer b: planes from off_re + b * stage_buf, kPlane apart
+    P.off_im = off + kPlane * 4;
+    const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32 + (gains.d ? nt * 16 + 16 : 0);
+    P.two_stage = off + 2 * P.stage_buf * 4 + tail <= 227 * 1024;
+    off = align_up(off + (P.two_stage ? 2 : 1) * P.stage_buf * 4, 16);
+    P.off_gain = off;                              // [n_tiles][2] float2 when gains are given
+    if (gains.d) off = align_up(off + nt * 16, 16);
     P.off_lut = off;
     off += 256 * 4;
     P.off_flags = off;

@@ -449,3 +449,82 @@ def test_pipeline_sets_replays_in_a_cuda_graph(B, ctx):
     torch.cuda.synchronize()
     B.blink_sync(ctx)
     assert torch.equal(out, eager)
+
+
+# ---------------------------------------------------------------------------------------------------
+# calibration gains inside the correlation (diagonal Jones per output channel, tile and polarisation)
+# ---------------------------------------------------------------------------------------------------
+
+def _gains(F, n_tiles, seed):
+    rng = np.random.default_rng(seed)
+    g = rng.uniform(0.5, 1.5, size=(F, n_tiles, 2)) * np.exp(1j * rng.uniform(-np.pi, np.pi, size=(F, n_tiles, 2)))
+    return g.astype(np.complex64)                      # the values both sides use
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_correlate_with_gains_matches_oracle(B, ctx, arith):
+    w, volt, freqs, fl = _case("coarse", 20, 8, flags=True)
+    F, K = 4, 20                                       # 8 fine channels averaged by 2, 10 samples per integration
+    g = _gains(F, 128, 5)
+    out = torch.empty((2, F, 8256, 4, 2), dtype=torch.float32, device="cuda")
+    B.blink_correlate(ctx, B.Array(w["enu"], fl, g), B.Obs(freqs, 2, 10, 20), arith, dev(volt), out)
+    B.blink_sync(ctx)
+    got = out.cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    S = oracle.correlate(volt, 10, 2, flags=fl)
+    for tau in range(2):
+        for f in range(F):
+            ref = oracle.apply_gains(S[tau, f], g[f].astype(np.complex128)) / K
+            err = np.abs(got[tau, f] - ref).max() / np.abs(ref).max()
+            assert err <= 2e-6, (arith, tau, f, err)
+
+
+@pytest.mark.parametrize("arith,mode,pol", [(1, 0, 0), (0, 0, 0), (1, 0, 1), (1, 1, 0)])
+def test_pipeline_with_gains_matches_oracle(B, ctx, arith, mode, pol):
+    # Stokes I with gains takes the split XX / YY tensor-core chains; XX one chain; plain mode per image
+    w, volt, freqs, fl = _case("coarse", 20, 8, flags=True)
+    F, n = 8, 256
+    g = _gains(F, 128, 6)
+    img = torch.empty((2 * F, n, n), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"], fl, g), B.Obs(freqs, 1, 10, 20), B.Imaging(n, pol=pol), arith, mode,
+                     dev(volt), img)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n, flags=fl, pol=pol, gains=g.astype(np.complex128),
+                          n_threads=8)["images"]
+    got = img.cpu().numpy()
+    for q in range(2 * F):
+        assert rel_rms(got[q], ref[q]) <= IMG_RTOL, (q, rel_rms(got[q], ref[q]))
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_unit_gains_equal_no_gains_bit_for_bit(B, ctx, arith):
+    w, volt, freqs, _ = _case("coarse", 20, 8)
+    n = 256
+    a = torch.empty((16, n, n), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    obs, im = B.Obs(freqs, 1, 10, 20), B.Imaging(n)
+    B.blink_pipeline(ctx, B.Array(w["enu"]), obs, im, arith, 0, dev(volt), a)
+    B.blink_pipeline(ctx, B.Array(w["enu"], None, np.ones((8, 128, 2), np.complex64)), obs, im, arith, 0, dev(volt), b)
+    B.blink_sync(ctx)
+    assert torch.equal(a, b)
+
+
+def test_pipeline_sets_with_gains(B, ctx):
+    w = bs.build_workload("uneven", n_samples=10)
+    volt, freqs, sets_w = w["volt"], w["freqs"], w["sets"]
+    g = _gains(len(freqs), 144, 7)                     # one row per output channel of the call (chan_avg 1)
+    sets = [B.Set(fine0=st.fine0, n_fine=8, imaging=B.Imaging(st.n_pix), flags=st.flags) for st in sets_w]
+    total = sum(8 * st.n_pix ** 2 for st in sets_w)
+    img = torch.empty(total, dtype=torch.float32, device="cuda")
+    B.blink_pipeline_sets(ctx, B.Array(w["enu"], None, g), B.Obs(freqs, 1, 10, 10), sets, 1, dev(volt), img, total)
+    B.blink_sync(ctx)
+    got = img.cpu().numpy()
+    at = 0
+    for st in sets_w:
+        n = st.n_pix
+        ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n, flags=st.flags, fine0=st.fine0, n_fine=8, n_threads=8,
+                              gains=g[st.fine0:st.fine0 + 8].astype(np.complex128))
+        part = got[at:at + 8 * n * n].reshape(8, n, n)
+        for q in range(8):
+            assert rel_rms(part[q], ref["images"][q]) <= IMG_RTOL, (st.fine0, q)
+        at += 8 * n * n
