@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--samples", type=int, default=0, help="voltage samples per step (default: the 50 ms chunk)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "coarse", "precision", "uneven", "fullband"])
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (default: every host core)")
+    ap.add_argument("--gains", action="store_true",
+                    help="apply seeded per-channel, per-tile, per-polarisation calibration gains in the correlation")
     return ap.parse_args()
 
 
@@ -182,7 +184,14 @@ def image_sets(inp, w, ns):
     return out
 
 
-def oracle_sets_images(oracle, inp, w, sets, picks, threads):
+def bench_gains(n_out_chan: int, n_tiles: int) -> np.ndarray:
+    """Seeded calibration gains, complex64 [channels][tiles][2]: amplitude 0.5-1.5, any phase."""
+    rng = np.random.default_rng(2505152040)
+    amp = rng.uniform(0.5, 1.5, size=(n_out_chan, n_tiles, 2))
+    return (amp * np.exp(1j * rng.uniform(-np.pi, np.pi, size=amp.shape))).astype(np.complex64)
+
+
+def oracle_sets_images(oracle, inp, w, sets, picks, threads, gains=None):
     """The oracle's images for the picked (set index, local image id) pairs, in order."""
     out = []
     for q, (st, _, _, side) in enumerate(sets):
@@ -190,6 +199,9 @@ def oracle_sets_images(oracle, inp, w, sets, picks, threads):
         if len(ids) == 0:
             continue
         kw = {} if len(sets) == 1 else {"flags": st.flags, "fine0": st.fine0, "n_fine": st.n_fine}
+        if gains is not None:
+            f0 = st.fine0 // w.chan_avg
+            kw["gains"] = gains[f0:f0 + st.n_fine // w.chan_avg].astype(np.complex128)
         ref = oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], w.samples_per_int, w.chan_avg, side, ids=ids,
                               n_threads=threads, **kw)
         out.extend(ref["images"])
@@ -230,7 +242,8 @@ def run_reference(args, world, rank):
         if not sel:
             sel = picks[:1]
         t = time.perf_counter()
-        oracle_sets_images(oracle, inp, w, sets, sel, cores)
+        oracle_sets_images(oracle, inp, w, sets, sel, cores,
+                           bench_gains(w.n_out_chan, w.n_tiles) if args.gains else None)
         dt = time.perf_counter() - t
         if s_ >= args.warmup:
             times.append((len(sel), dt))
@@ -288,7 +301,8 @@ def run_ours(args, world, rank, local):
         raise SystemExit("several channel sets run only in the batched mode")
     ctx = B.blink_create(local)
     prec = B.BLINK_PREC_BF16 if args.precision == "bf16" else B.BLINK_PREC_FP32
-    arr, obs = B.Array(inp["enu"]), B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns)
+    gains = bench_gains(w.n_out_chan, n_tiles) if args.gains else None
+    arr, obs = B.Array(inp["enu"], None, gains), B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns)
     im = B.Imaging(n_pix, precision=prec)
     bsets = [B.Set(fine0=st.fine0, n_fine=st.n_fine, imaging=B.Imaging(side, precision=prec), flags=st.flags)
              for st, _, _, side in sets]
@@ -387,7 +401,7 @@ def run_ours(args, world, rank, local):
         n_s = max(4, 4 * cores)
         picks = pick_images(sets, n_s)
         t = time.perf_counter()
-        refs = oracle_sets_images(oracle, inp, w, sets, picks, cores)
+        refs = oracle_sets_images(oracle, inp, w, sets, picks, cores, gains)
         dt = time.perf_counter() - t
         flat = img.reshape(-1)
         got = []
@@ -458,7 +472,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": workload_label(args.workload, w),
                    "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
-                   "mode": args.mode, "precision": args.precision,
+                   "mode": args.mode, "precision": args.precision, "gains": bool(args.gains),
                    "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
                           "each step timed alone after a 516 MB buffer overwrite") if small else
                          (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e9:.3g} GB per step exceed L2; "
