@@ -163,6 +163,9 @@ __device__ __forceinline__ void pair_of(int q, int& mb, int& jb) {
     jb = q - mb * (mb + 1) / 2;
 }
 
+// GAINS: the calibrated form (gains applied in the epilogue; Stokes I through split X / Y chains).  The
+// uncalibrated kernel is a separate instantiation with none of that code.
+template <bool GAINS>
 __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ops = smem;                                   // n_blk tiles of 128 x Kp bytes
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             abort = true;
             break;
         }
-        if (P.gains) {
+        if (GAINS) {
             // this item's gains, read by the epilogue (after the barrier that ends the unpack)
             const int f = it - (it / P.F) * P.F;
             const float2* g = P.gains + (int64_t)(P.gain_f0 + f) * P.n_tiles * 2;
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             for (int r = tid; r < per_k; r += kThreads) {
                 const int a = r >> 1, p = r & 1;
                 int unit, kp, kh;
-                if (P.mode == CORR_OUT_STOKES_I && P.split) {
+                if (GAINS && P.mode == CORR_OUT_STOKES_I && P.split) {
                     unit = a; kp = p * P.Kpol + k0; kh = P.Kq;          // [re, im] of X, then of Y
                 } else if (P.mode == CORR_OUT_STOKES_I) {
                     unit = a; kp = p * P.Kq + k0; kh = 2 * P.Kq;        // re X, re Y, im X, im Y
@@ -292,19 +295,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         __syncthreads();
         // ---- MMA rounds of up to 8 block pairs, each followed by its epilogue ---------------------------
         for (int r = 0; r < P.n_rounds && !abort; r++) {
-            const int q0 = r * P.pairs_per_round, q1 = min(P.n_pairs, q0 + P.pairs_per_round);
+            const int ppr = GAINS ? P.pairs_per_round : kTmemCols / 64;
+            const int q0 = r * ppr, q1 = min(P.n_pairs, q0 + ppr);
             if (tid == 0) {
                 tc_fence_after();
-                const int nk = P.Kp / 32, nh = P.split ? nk / 2 : nk;
+                const int nk = P.Kp / 32, nh = GAINS && P.split ? nk / 2 : nk;
                 for (int q = q0; q < q1; q++) {
                     int mb, jb;
                     pair_of(q, mb, jb);
-                    const uint32_t d = tmem + (uint32_t)((q - q0) * P.pair_cols);
+                    const uint32_t d = tmem + (uint32_t)((q - q0) * (GAINS ? P.pair_cols : 64));
                     const uint32_t a0 = ops_s + mb * tile_bytes, b0 = ops_s + jb * tile_bytes;
                     // one chain over all of K, or (split) the X half into columns 0-63 and the Y half into 64-127
                     for (int s = 0; s < nk; s++)
-                        mma_e4m3(s < nh ? d : d + 64, smem_desc(a0 + s * 256, 128, sbo),
-                                 smem_desc(b0 + s * 256, 128, sbo), idesc, s % nh > 0);
+                        mma_e4m3(GAINS && s >= nh ? d + 64 : d, smem_desc(a0 + s * 256, 128, sbo),
+                                 smem_desc(b0 + s * 256, 128, sbo), idesc, GAINS ? s % nh > 0 : s > 0);
                 }
                 mma_commit(bar_mma);
             }
@@ -316,16 +320,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             }
             tc_fence_after();
             const int local = it - P.first_item;
+            const int stage_buf = GAINS ? P.stage_buf : 2 * kPlane;
             // stage block pair q into buffer sb: warp w reads TMEM lanes 32 (w % 4) + lane, columns 16 (w / 4) ..
             auto stage = [&](int q, int sb) {
                 const int row = (warp & 3) * 32 + lane, c0 = (warp >> 2) * 16;
-                float* st = (row < 64 ? st_re + row * kStageLd : st_im + (row - 64) * kStageLd) + sb * P.stage_buf;
-                const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((q - q0) * P.pair_cols) + c0;
+                float* st = (row < 64 ? st_re + row * kStageLd : st_im + (row - 64) * kStageLd) + sb * stage_buf;
+                const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                    (uint32_t)((q - q0) * (GAINS ? P.pair_cols : 64)) + c0;
                 uint32_t v[16];
                 tmem_ld16(ta, v);
 #pragma unroll
                 for (int cc = 0; cc < 16; cc++) st[c0 + cc] = __uint_as_float(v[cc]);
-                if (P.split) {                                 // YY: planes 2 and 3
+                if (GAINS && P.split) {                        // YY: planes 2 and 3
                     tmem_ld16(ta + 64, v);
 #pragma unroll
                     for (int cc = 0; cc < 16; cc++) st[2 * kPlane + c0 + cc] = __uint_as_float(v[cc]);
@@ -335,8 +341,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             auto write = [&](int q, int sb) {
                 int mb, jb;
                 pair_of(q, mb, jb);
-                const float* sre = st_re + sb * P.stage_buf;
-                const float* sim = st_im + sb * P.stage_buf;
+                const float* sre = st_re + sb * stage_buf;
+                const float* sim = st_im + sb * stage_buf;
                 // (flagged tiles need no test: their operand rows were zeroed in the unpack)
                 if (P.mode == CORR_OUT_VIS4) {
                     for (int e = tid; e < 64 * 64; e += kThreads) {
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                         const int ai = ui >> 1, aj = uj >> 1;
                         if (aj > ai) continue;
                         float re = sre[il * kStageLd + jl], im = sim[il * kStageLd + jl];
-                        if (P.gains) {                         // g_i^p S conj(g_j^q), unit u = 2 tile + pol
+                        if (GAINS) {                           // g_i^p S conj(g_j^q), unit u = 2 tile + pol
                             const float2 gi = s_g[ui], gj = s_g[uj];
                             const float tr = gi.x * re - gi.y * im, ti = gi.x * im + gi.y * re;
                             re = tr * gj.x + ti * gj.y;
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                     float2* out = static_cast<float2*>(P.out) + (int64_t)local * P.out_item_stride + uj;
                     const float* pre = sre + jl;
                     const float* pim = sim + jl;
-                    if (!P.gains) {
+                    if (!GAINS) {
 #pragma unroll 4
                         for (int il = tid >> 6; il < 64; il += kRowStep) {
                             const int ui = mb * 64 + il;
@@ -525,11 +531,15 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     if (r != CUDA_SUCCESS) return set_error(BLINK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the voltage block");
     static size_t smem_set = 0;                   // raise the kernel's limit once (not during a capture)
     if (smem > smem_set) {
-        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         smem_set = 227 * 1024;
     }
     const int grid = std::min(n_items, n_sm);
-    k_corr_tc<<<grid, kThreads, smem, st>>>(map, P);
+    if (gains.d)
+        k_corr_tc<true><<<grid, kThreads, smem, st>>>(map, P);
+    else
+        k_corr_tc<false><<<grid, kThreads, smem, st>>>(map, P);
     BLINK_CUDA(cudaGetLastError());
     return BLINK_OK;
 }
