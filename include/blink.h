@@ -126,9 +126,10 @@ blink_status blink_cells(blink_context* ctx, const blink_array* array, const bli
  * Correlation (Eq. 2; Sec. 5.2.2): for every integration and output channel, the lower-triangular
  * matrix of V_ij^pq = (1/K) sum x_i^p conj(x_j^q) over the N_s samples and c fine channels, as float
  * [T][F][B][4][2].  Products of 4-bit integers are summed exactly (integers below 2^24), then divided
- * by K once in IEEE FP32.  Flagged tiles' baselines are written as 0.
+ * by K once in IEEE FP32.  Flagged tiles' baselines are written as 0.  With array.gains the products are
+ * calibrated first, V_ij^pq = g_i^p S_ij^pq conj(g_j^q) / K (FP32 arithmetic).
  *   arith  BLINK_CORR_FP32: CUDA-core FP32; BLINK_CORR_FP8: tcgen05 tensor cores, e4m3 operands,
- *          FP32 accumulation.  Both give identical bits.
+ *          FP32 accumulation.  Without gains both give identical bits.
  */
 blink_status blink_correlate(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                              int32_t arith, const uint8_t* d_volt, float* d_vis, void* stream);
@@ -162,9 +163,10 @@ blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const
  * The whole path (Sec. 5, Fig. "BLINK FRB search pipeline", imaging half): correlation -> gridding ->
  * inverse FFT -> shifted, normalised dirty images for every integration and output channel of the call,
  * d_img float [T * F][N][N] in image-id order.  Only the products the imaged polarisation needs are
- * formed (XX and YY for Stokes I).
+ * formed (XX and YY for Stokes I), calibrated with array.gains when given.
  *   arith     correlation arithmetic as in blink_correlate.
- *   mode      BLINK_MODE_BATCHED: images in waves through batched kernels (the fast form);
+ *   mode      BLINK_MODE_BATCHED: one correlation launch and one persistent gridding + FFT launch for the
+ *             whole call (the fast form; its launch shape is autotuned on a plan's first call);
  *             BLINK_MODE_PLAIN: one launch set per image with atomic gridding (the reference GPU form).
  *   d_weight  float [T * F] or NULL: W per image.
  * Images equal blink_image(blink_grid(blink_correlate(...))) up to FP32 rounding.
