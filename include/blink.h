@@ -92,6 +92,14 @@ typedef struct {
     int32_t precision;          /* BLINK_PREC_FP32, or BLINK_PREC_BF16 (bf16 grid/intermediate storage) */
 } blink_imaging;
 
+/*
+ * Stream ordering and graph capture: every entry point only enqueues work on `stream` (NULL = the legacy
+ * default stream) and returns; blink_sync waits.  The first call for a new plan (array, channels and image
+ * parameters) builds the plan and, in the batched form, times the persistent kernel's launch shapes on the
+ * stream with a blocking event wait; make that call before any CUDA-graph capture.  Later calls with the
+ * same plan allocate nothing and never block, so they can be captured and replayed.
+ */
+
 /* ---- context ---------------------------------------------------------------------------------- */
 
 /* Create a context on CUDA device `device` (which becomes current on the calling thread). */
