@@ -97,7 +97,8 @@ typedef struct {
  * default stream) and returns; blink_sync waits.  The first call for a new plan (array, channels and image
  * parameters) builds the plan and, in the batched form, times the persistent kernel's launch shapes on the
  * stream with a blocking event wait; make that call before any CUDA-graph capture.  Later calls with the
- * same plan allocate nothing and never block, so they can be captured and replayed.
+ * same plan allocate nothing and never block, so they can be captured and replayed (calibration gains are
+ * copied from host memory on every call, so under capture they must be page-locked).
  */
 
 /* ---- context ---------------------------------------------------------------------------------- */
