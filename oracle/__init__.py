@@ -74,6 +74,8 @@ def _load():
             lib.oracle_pipeline.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
                                             C.c_int, C.c_double, C.c_int, C.c_int, P, P, C.c_int64, C.c_int,
                                             P, P, P, P]
+            lib.oracle_dedisperse.restype = C.c_int
+            lib.oracle_dedisperse.argtypes = [P, C.c_int, C.c_int, C.c_int64, P, P]
             lib.oracle_apply_gains.restype = None
             lib.oracle_apply_gains.argtypes = [P, C.c_int, P, P]
             lib.oracle_grid_v.restype = C.c_double
@@ -254,3 +256,24 @@ def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int,
         raise ValueError("oracle_pipeline: bad arguments")
     return {"images": imgs, "W": W, "max_im": mx,
             "grids": None if grids is None else grids[..., 0] + 1j * grids[..., 1]}
+
+
+def dedisperse(img: np.ndarray, delays) -> np.ndarray:
+    """Incoherent dedispersion (the FRB search after imaging): ``img`` [T][F][...] images of T integrations and
+    F channels, ``delays`` int [F] >= 0 in integrations; returns float64 [T - max(delays)][...] with
+    out[t] = mean_f img[t + d_f][f].
+    """
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    T, F = img.shape[:2]
+    P = int(np.prod(img.shape[2:])) if img.ndim > 2 else 1
+    d = np.ascontiguousarray(delays, dtype=np.int32)
+    assert d.shape == (F,)
+    To = T - int(d.max())
+    if To < 1 or d.min() < 0:
+        raise ValueError("dedisperse: delays must be >= 0 and leave at least one integration")
+    out = np.zeros((To,) + img.shape[2:], dtype=np.float64)
+    rc = _load().oracle_dedisperse(_p(img), T, F, P, _p(d), _p(out))
+    if rc != To:
+        raise ValueError("oracle_dedisperse: bad arguments")
+    return out
+

@@ -17,6 +17,8 @@
  *   fft2        Eq. 4 / Sec. 5.2.4: unnormalised inverse 2D transform, own radix-2 FFT; direct DFT
  *               for small sides.
  *   image       Sec. 5.2.4: real part / sum of weights, shifted so the phase centre is the middle pixel.
+ *   dedisperse  Sec. 2 and 7 (the FRB search that follows imaging): incoherent dedispersion of the image cube,
+ *               out[t] = (1/F) sum_f img[t + d_f][f] with per-channel delays d_f in integrations.
  *
  * Readings where the paper is silent (stated in the design notes): Stokes I = (S_XX + S_YY) / (2K);
  * uv cell default = u_max / (N/2 - 1); cell = floor(u / du + 1/2); autos gridded at (0, 0); grid DC at
@@ -396,3 +398,30 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
     free(fout);
     return bad ? -1 : 0;
 }
+
+/*
+ * Incoherent dedispersion of an image cube (the FRB search the images feed, Sec. 2, 7): img is double
+ * [T][F][P] (integration, channel, pixel), d[f] >= 0 the delay of channel f in integrations; for every
+ * t < T - max(d), out[t][p] = (1/F) sum_f img[t + d_f][f][p].  Zero delays give the band-averaged image.
+ * Returns the number of output integrations, or -1 on bad arguments.
+ */
+int oracle_dedisperse(const double* img, int T, int F, int64_t P, const int32_t* d, double* out)
+{
+    if (T < 1 || F < 1 || P < 1) return -1;
+    int dmax = 0;
+    for (int f = 0; f < F; f++) {
+        if (d[f] < 0) return -1;
+        if (d[f] > dmax) dmax = d[f];
+    }
+    int To = T - dmax;
+    if (To < 1) return -1;
+    for (int t = 0; t < To; t++) {
+        for (int64_t p = 0; p < P; p++) {
+            double acc = 0.0;
+            for (int f = 0; f < F; f++) acc += img[((int64_t)(t + d[f]) * F + f) * P + p];
+            out[(int64_t)t * P + p] = acc / (double)F;
+        }
+    }
+    return To;
+}
+

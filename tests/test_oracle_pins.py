@@ -456,3 +456,40 @@ def test_gains_undo_a_per_tile_phase_corruption():
     fixed = oracle.pipeline(volt, enu, freqs, ns, 1, 32, gains=g)["images"][0]
     assert np.allclose(fixed, ref, rtol=0, atol=1e-12)
     assert bad[16, 16] < 0.5 * ref[16, 16]
+
+
+# ----------------------------------------------------------------------------------------------
+# incoherent dedispersion of the image cube (the FRB search after imaging)
+# ----------------------------------------------------------------------------------------------
+
+def test_dedisperse_zero_delays_is_the_band_mean():
+    rng = np.random.default_rng(21)
+    img = rng.normal(size=(6, 5, 4, 3))
+    out = oracle.dedisperse(img, np.zeros(5, np.int32))
+    assert np.allclose(out, img.mean(axis=1), rtol=1e-14, atol=1e-14)
+
+
+def test_dedisperse_realigns_a_dispersed_pulse():
+    # a pulse reaching channel f at integration t0 + d_f: dedispersion with those delays stacks it at t0 with
+    # its full amplitude and nothing elsewhere; one channel's delay wrong by one loses exactly 1/F of it
+    T, F, t0 = 12, 6, 2
+    d = np.array([5, 4, 2, 1, 1, 0], dtype=np.int32)
+    img = np.zeros((T, F, 3, 3))
+    for f in range(F):
+        img[t0 + d[f], f, 1, 2] = 7.0
+    out = oracle.dedisperse(img, d)
+    assert out.shape == (T - 5, 3, 3)
+    assert out[t0, 1, 2] == 7.0 and np.count_nonzero(out) == 1
+    bad = d.copy()
+    bad[3] += 1
+    assert oracle.dedisperse(img, bad)[t0, 1, 2] == pytest.approx(7.0 * (F - 1) / F)
+
+
+def test_dedisperse_equals_direct_sum():
+    rng = np.random.default_rng(22)
+    img = rng.normal(size=(9, 4, 5))
+    d = np.array([0, 3, 1, 2], dtype=np.int32)
+    out = oracle.dedisperse(img, d)
+    for t in range(9 - 3):
+        ref = sum(img[t + d[f], f] for f in range(4)) / 4
+        assert np.allclose(out[t], ref, rtol=0, atol=1e-15)
