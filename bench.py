@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--samples", type=int, default=0, help="voltage samples per step (default: the 50 ms chunk)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "coarse", "precision", "uneven", "fullband"])
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (default: every host core)")
+    ap.add_argument("--dedisperse", action="store_true",
+                    help="also time blink_dedisperse on the step's images (a DM sweeping half the chunk)")
     ap.add_argument("--gains", action="store_true",
                     help="apply seeded per-channel, per-tile, per-polarisation calibration gains in the correlation")
     return ap.parse_args()
@@ -418,6 +420,33 @@ def run_ours(args, world, rank, local):
             cpu = {"value": len(picks) / dt, "unit": "images/s", "cores": cores, "kind": "oracle",
                    "sample": f"{len(picks)} images, ids evenly spaced over the {n_img}-image chunk"}
 
+    # incoherent dedispersion of the step's image cube: a dispersion measure whose sweep across the band
+    # fills half the chunk, delays rounded to whole integrations
+    dedisp = None
+    if args.dedisperse and rank == 0 and not multi:
+        T_int, F = ns // w.samples_per_int, n_img // (ns // w.samples_per_int)
+        t_int = w.samples_per_int * 100e-6
+        nu = inp["freqs"].reshape(F, w.chan_avg).mean(axis=1) / 1e6          # MHz
+        per_dm = 4.148808e3 * (nu.min() ** -2 - nu.max() ** -2)               # s per pc cm^-3
+        dm = (T_int // 2) * t_int / per_dm
+        delays = np.rint(4.148808e3 * dm * (nu ** -2 - nu.max() ** -2) / t_int).astype(np.int32)
+        n_out = T_int - int(delays.max())
+        dd = torch.empty((n_out, n_pix, n_pix), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            B.blink_dedisperse(ctx, img, T_int, F, n_pix, delays, dd, stream)
+        reps = 10
+        e0.record(stream)
+        for _ in range(reps):
+            B.blink_dedisperse(ctx, img, T_int, F, n_pix, delays, dd, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_d = e0.elapsed_time(e1) / reps
+        byts = n_out * (F + 1) * n_pix * n_pix * 4
+        dedisp = {"dm_pc_cm3": round(float(dm), 4), "max_delay_integrations": int(delays.max()), "outputs": n_out,
+                  "ms": ms_d, "GBps": byts / (ms_d / 1e3) / 1e9, "frac": byts / (ms_d / 1e3) / 1e9 / peak,
+                  "bytes_per_launch": byts, "kernel": "k_dedisperse"}
+        del dd
+
     # cuFFT's batched complex-to-real transform of grids of the same shape (a timing reference only)
     cufft = None
     if args.cufft and rank == 0 and not multi:
@@ -479,7 +508,7 @@ def run_ours(args, world, rank, local):
                           "no flush"),
                    "generate_s": round(t_gen, 2), "plan_s": round(t_plan, 3)},
         "roofline": roof, "stages": stages, "clocks": clocks, "gpu_launches": launches,
-        "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "cufft_reference": cufft,
+        "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "cufft_reference": cufft, "dedisperse": dedisp,
         "vis_per_s": value * (n_tiles * (n_tiles + 1) // 2) * 2,
         "vis_note": "visibilities formed per second: XX and YY products of every baseline incl. autos per image",
     }

@@ -205,6 +205,19 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
                                  float* d_img, size_t img_capacity, void* stream);
 
 /*
+ * Incoherent dedispersion of an image cube (the FRB search the images feed, Sec. 2 and 7): d_img is float
+ * [n_int][n_chan][N][N] in blink_pipeline's image order (id = integration * n_chan + channel); for every
+ * t < n_int - max(delays), d_out[t] = (1/n_chan) sum_f d_img[t + delays[f]][f].  All-zero delays give the
+ * band-averaged image of every integration.
+ *   h_delays  host int32 [n_chan], >= 0, in integrations, e.g. round(4.148808e3 s MHz^2 * DM *
+ *             (nu_f^-2 - nu_top^-2) / t_int) for a dispersion measure DM in pc cm^-3 and nu in MHz.
+ *   d_out     float [n_int - max(delays)][N][N].
+ * N is a power of two in [64, 2048]; max(delays) < n_int, else BLINK_ERR_INVALID_ARG before any launch.
+ */
+blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_int, int32_t n_chan, int32_t n_pix,
+                              const int32_t* h_delays, float* d_out, void* stream);
+
+/*
  * blink_pipeline on host buffers: copies h_volt to device workspace, runs the batched path and delivers
  * the images to h_img, all ordered on `stream`.
  *   images_per_pass == 0: when the device can write h_img - one page-locked allocation (cudaHostAlloc,

@@ -38,7 +38,7 @@ BLINK_MODE_PLAIN = 1
 ENTRY_POINTS = (
     "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
-    "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets",
+    "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets", "blink_dedisperse",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
@@ -92,6 +92,7 @@ def _load():
         "blink_read_profile": (S, [P, P, P, P, I32]),
         "blink_image_noalloc": (S, [P, P, I32, P, P, P]),
         "blink_pipeline_sets": (S, [P, P, P, P, I32, I32, P, P, C.c_size_t, P]),
+        "blink_dedisperse": (S, [P, P, I32, I32, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -246,6 +247,15 @@ def blink_pipeline_host(ctx, array: Array, obs: Obs, imaging: Imaging, arith: in
     a, o, i = array.c(), obs.c(), imaging.c()
     _check(_lib.blink_pipeline_host(ctx, C.byref(a), C.byref(o), C.byref(i), arith, _ptr(h_volt), _ptr(h_img),
                                     images_per_pass, _stream(stream)), "blink_pipeline_host")
+
+
+def blink_dedisperse(ctx, d_img, n_int: int, n_chan: int, n_pix: int, delays, d_out, stream=None) -> None:
+    """Dedispersed channel means of an image cube [n_int][n_chan][N][N] into [n_int - max(delays)][N][N]."""
+    d = np.ascontiguousarray(delays, dtype=np.int32)
+    if d.shape != (n_chan,):
+        raise ValueError("delays must have one entry per channel")
+    _check(_lib.blink_dedisperse(ctx, _ptr(d_img), n_int, n_chan, n_pix, d.ctypes.data, _ptr(d_out), _stream(stream)),
+           "blink_dedisperse")
 
 
 def blink_set_profiling(ctx, enable: bool) -> None:

@@ -851,6 +851,28 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
     return BLINK_OK;
 }
 
+blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_int, int32_t n_chan, int32_t n_pix,
+                              const int32_t* h_delays, float* d_out, void* stream) {
+    BLINK_TRY(make_current(ctx));
+    if (!d_img || !d_out || !h_delays) return set_error(BLINK_ERR_INVALID_ARG, "d_img, d_out or h_delays is NULL");
+    if (n_int < 1 || n_chan < 1) return set_error(BLINK_ERR_INVALID_ARG, "n_int and n_chan must be >= 1");
+    if (n_pix < 64 || n_pix > 2048 || (n_pix & (n_pix - 1)))
+        return set_error(BLINK_ERR_INVALID_ARG, "n_pix must be a power of two in [64, 2048]");
+    if (((uintptr_t)d_img & 15) || ((uintptr_t)d_out & 15))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_img and d_out must be 16-byte aligned");
+    int dmax = 0;
+    for (int f = 0; f < n_chan; f++) {
+        if (h_delays[f] < 0) return set_error(BLINK_ERR_INVALID_ARG, "delays must be >= 0");
+        dmax = std::max(dmax, (int)h_delays[f]);
+    }
+    if (dmax >= n_int) return set_error(BLINK_ERR_INVALID_ARG, "max(delays) must be < n_int");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* d = nullptr;
+    BLINK_TRY(workspace(ctx, 7, sizeof(int32_t) * (size_t)n_chan, &d));
+    BLINK_CUDA(cudaMemcpyAsync(d, h_delays, sizeof(int32_t) * (size_t)n_chan, cudaMemcpyHostToDevice, st));
+    return launch_dedisperse(d_img, n_int - dmax, n_chan, n_pix, static_cast<const int*>(d), d_out, st);
+}
+
 blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                                  const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt, float* h_img,
                                  int32_t images_per_pass, void* stream) {

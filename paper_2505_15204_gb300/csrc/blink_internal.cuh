@@ -82,7 +82,7 @@ struct blink_context {
     int n_sm = 0;
     int* d_status = nullptr;
     std::vector<blink::Plan*> plans;       // most recent last
-    blink::Workspace ws[7];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains
+    blink::Workspace ws[8];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays
     float2* tw[16] = {};                   // twiddle tables by log2(side)
     // per-stage profiling (blink_set_profiling): recorded (stage, start, stop) event pairs and a free pool
     bool profiling = false;
@@ -122,6 +122,8 @@ blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sampl
 blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample_stride_bytes, const Plan& p,
                              int ns, int first_item, int n_items, void* out, int64_t out_item_stride,
                              int* d_status, int n_sm, cudaStream_t st, GainRef gains = {});
+blink_status launch_dedisperse(const float* d_img, int n_out, int F, int n_pix, const int* d_delay, float* d_out,
+                               cudaStream_t st);
 blink_status launch_grid_gather(const Plan& p, const float* d_vis4, int first_image, int n_images, float* d_grid,
                                 int* d_status, cudaStream_t st);
 blink_status launch_grid_atomic(const Plan& p, const float2* d_visI, int image, float2* d_grid_full,

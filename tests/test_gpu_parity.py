@@ -528,3 +528,44 @@ def test_pipeline_sets_with_gains(B, ctx):
         for q in range(8):
             assert rel_rms(part[q], ref["images"][q]) <= IMG_RTOL, (st.fine0, q)
         at += 8 * n * n
+
+
+# ---------------------------------------------------------------------------------------------------
+# incoherent dedispersion of the image cube
+# ---------------------------------------------------------------------------------------------------
+
+def test_dedisperse_matches_oracle(B, ctx):
+    rng = np.random.default_rng(31)
+    T, F, n = 9, 13, 64                                # F not a multiple of the kernel's unroll
+    img = rng.normal(size=(T, F, n, n)).astype(np.float32)
+    d = np.array([0, 3, 1, 4, 2, 0, 1, 4, 3, 2, 0, 1, 2], dtype=np.int32)
+    out = torch.empty((T - 4, n, n), dtype=torch.float32, device="cuda")
+    B.blink_dedisperse(ctx, dev(img), T, F, n, d, out)
+    B.blink_sync(ctx)
+    ref = oracle.dedisperse(img.astype(np.float64), d)
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
+
+
+def test_dedispersed_pipeline_images_match_oracle(B, ctx):
+    # images of 4 integrations x 8 channels, then a dedispersion over their channels, against the oracle's
+    w, volt, freqs, _ = _case("coarse", 40, 8)
+    n, T, F = 128, 4, 8
+    img = torch.empty((T * F, n, n), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 40), B.Imaging(n), 1, 0, dev(volt), img)
+    d = np.array([2, 2, 1, 1, 1, 0, 0, 0], dtype=np.int32)
+    out = torch.empty((T - 2, n, n), dtype=torch.float32, device="cuda")
+    B.blink_dedisperse(ctx, img, T, F, n, d, out)
+    B.blink_sync(ctx)
+    ref_img = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n, n_threads=8)["images"].reshape(T, F, n, n)
+    ref = oracle.dedisperse(ref_img, d)
+    got = out.cpu().numpy()
+    for t in range(T - 2):
+        assert rel_rms(got[t], ref[t]) <= IMG_RTOL
+
+
+def test_dedisperse_rejects_bad_delays(B, ctx):
+    img = torch.zeros((4, 2, 64, 64), dtype=torch.float32, device="cuda")
+    out = torch.zeros((4, 64, 64), dtype=torch.float32, device="cuda")
+    for d in ([0, 4], [-1, 0]):
+        with pytest.raises(B.BlinkError):
+            B.blink_dedisperse(ctx, img, 4, 2, 64, np.array(d, np.int32), out)
