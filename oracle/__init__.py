@@ -72,8 +72,10 @@ def _load():
             lib.oracle_image.argtypes = [P, C.c_int, C.c_double, P]
             lib.oracle_pipeline.restype = C.c_int
             lib.oracle_pipeline.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
-                                            C.c_int, C.c_double, C.c_int, C.c_int, P, P, C.c_int64, C.c_int,
-                                            P, P, P, P]
+                                            C.c_int, C.c_double, C.c_int, C.c_int, P, C.c_int, P, C.c_int64,
+                                            C.c_int, P, P, P, P]
+            lib.oracle_apply_jones.restype = None
+            lib.oracle_apply_jones.argtypes = [P, C.c_int, P, P]
             lib.oracle_dedisperse.restype = C.c_int
             lib.oracle_dedisperse.argtypes = [P, C.c_int, C.c_int, C.c_int64, P, P]
             lib.oracle_apply_gains.restype = None
@@ -138,6 +140,20 @@ def apply_gains(S: np.ndarray, gains: np.ndarray) -> np.ndarray:
     assert S.shape == (n_baselines(nt), 4, 2) and g.shape == (nt, 2, 2)
     out = np.zeros((S.shape[0], 4, 2), dtype=np.float64)
     _load().oracle_apply_gains(_p(S), nt, _p(g), _p(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def apply_jones(S: np.ndarray, jones: np.ndarray) -> np.ndarray:
+    """Calibrated sums V_ij = J_i S_ij J_j^H with full 2x2 Jones matrices, complex128 [B][4].
+
+    ``jones`` complex [n_tiles][2][2] (J[p][r]).
+    """
+    S = np.ascontiguousarray(S, dtype=np.int64)
+    J = np.ascontiguousarray(np.stack([np.real(jones), np.imag(jones)], axis=-1), dtype=np.float64)
+    nt = J.shape[0]
+    assert S.shape == (n_baselines(nt), 4, 2) and J.shape == (nt, 2, 2, 2)
+    out = np.zeros((S.shape[0], 4, 2), dtype=np.float64)
+    _load().oracle_apply_jones(_p(S), nt, _p(J), _p(out))
     return out[..., 0] + 1j * out[..., 1]
 
 
@@ -223,7 +239,8 @@ def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int,
              pol: int = POL_I, autos: bool = True, n_threads: int = 1, want_grids: bool = False, gains=None):
     """Dirty images for the listed image ids (id = tau * F + f) of one set.
 
-    ``gains``: complex [F][n_tiles][2] per output channel of the set, tile and polarisation, or None.
+    ``gains``: complex [F][n_tiles][2] per output channel of the set, tile and polarisation, or complex
+    [F][n_tiles][2][2] full Jones matrices, or None.
 
     Returns dict(images [n][N][N] float64, W [n], max_im [n], grids [n][N][N] complex128 or None).
     """
@@ -244,14 +261,15 @@ def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int,
     W = np.zeros(n, dtype=np.float64)
     mx = np.zeros(n, dtype=np.float64)
     grids = np.zeros((n, n_pix, n_pix, 2), dtype=np.float64) if want_grids else None
-    g = None
+    g, full = None, 0
     if gains is not None:
         gains = np.asarray(gains)
-        assert gains.shape == (F, nt, 2)
+        full = int(gains.ndim == 4)
+        assert gains.shape == ((F, nt, 2, 2) if full else (F, nt, 2))
         g = np.ascontiguousarray(np.stack([np.real(gains), np.imag(gains)], axis=-1), dtype=np.float64)
     rc = _load().oracle_pipeline(volt.ctypes.data + fine0 * nt * 2, nf_total, nt, n_fine, c, ns, _p(enu), _p(ff),
-                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), _p(g), _p(ids), n,
-                                 n_threads, _p(grids), _p(imgs), _p(W), _p(mx))
+                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), _p(g), full, _p(ids),
+                                 n, n_threads, _p(grids), _p(imgs), _p(W), _p(mx))
     if rc:
         raise ValueError("oracle_pipeline: bad arguments")
     return {"images": imgs, "W": W, "max_im": mx,

@@ -114,6 +114,38 @@ void oracle_apply_gains(const int64_t* S, int n_tiles, const double* g, double* 
     }
 }
 
+/*
+ * Full calibration (Sec. 5.2.3) with a 2x2 Jones matrix per tile: V_ij = J_i S_ij J_j^H, i.e.
+ * V_ij^pq = sum_{r,s} J_i[p][r] S_ij^rs conj(J_j[q][s]).  J is complex double [n_tiles][2][2][2]
+ * (J[p][r] re, im); S int64 [B][4][2]; V complex double [B][4][2].  A diagonal J is oracle_apply_gains.
+ */
+void oracle_apply_jones(const int64_t* S, int n_tiles, const double* J, double* V)
+{
+    for (int i = 0; i < n_tiles; i++) {
+        for (int j = 0; j <= i; j++) {
+            int64_t b = (int64_t)i * (i + 1) / 2 + j;
+            for (int p = 0; p < 2; p++) {
+                for (int q = 0; q < 2; q++) {
+                    double vr = 0.0, vi = 0.0;
+                    for (int r = 0; r < 2; r++) {
+                        for (int s2 = 0; s2 < 2; s2++) {
+                            double sr = (double)S[(b * 4 + 2 * r + s2) * 2 + 0];
+                            double si = (double)S[(b * 4 + 2 * r + s2) * 2 + 1];
+                            double ar = J[((i * 2 + p) * 2 + r) * 2 + 0], ai = J[((i * 2 + p) * 2 + r) * 2 + 1];
+                            double cr = J[((j * 2 + q) * 2 + s2) * 2 + 0], ci = -J[((j * 2 + q) * 2 + s2) * 2 + 1];
+                            double tr = ar * sr - ai * si, ti = ar * si + ai * sr;   /* J_i[p][r] S^rs */
+                            vr += tr * cr - ti * ci;                                  /* * conj(J_j[q][s]) */
+                            vi += tr * ci + ti * cr;
+                        }
+                    }
+                    V[(b * 4 + 2 * p + q) * 2 + 0] = vr;
+                    V[(b * 4 + 2 * p + q) * 2 + 1] = vi;
+                }
+            }
+        }
+    }
+}
+
 /* Output-channel centre frequency = mean of its c fine-channel centres (summed in order, then / c). */
 void oracle_output_freqs(const double* fine, int n_fine, int c, double* out)
 {
@@ -344,14 +376,15 @@ double oracle_image(const double* a, int n, double W, double* img)
  * The whole path for a list of images of one set (one flag vector, one image side): for each image id
  * (= tau * F + f) correlate, compute uvw and cells at the output channel's frequency, grid, transform and
  * form the image.  cell_lambda <= 0 selects the default cell over the set's highest output frequency.
- * gains (or NULL): complex double [F][n_tiles][2 pol][2], applied to the sums before gridding.
+ * gains (or NULL): complex double [F][n_tiles][2 pol][2], applied to the sums before gridding; with
+ * full_jones, complex double [F][n_tiles][2][2][2] full Jones matrices instead.
  * Optional outputs (NULL to skip): grids [n_ids][N][N][2], images [n_ids][N][N], W [n_ids],
  * max|Im|/W [n_ids].  Images are independent, so they are spread over `n_threads` OpenMP threads.
  * Returns 0, or -1 on bad arguments.
  */
 int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n_fine, int c, int ns,
                     const double* enu, const double* fine_freq, const uint8_t* flags,
-                    int n_pix, double cell_lambda, int pol, int autos, const double* gains,
+                    int n_pix, double cell_lambda, int pol, int autos, const double* gains, int full_jones,
                     const int64_t* ids, int64_t n_ids, int n_threads,
                     double* grids, double* imgs, double* W_out, double* maxim_out)
 {
@@ -381,7 +414,10 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
         double W;
         if (gains) {
             double* V = (double*)malloc(sizeof(double) * B * 8);
-            oracle_apply_gains(S, n_tiles, gains + (int64_t)f * n_tiles * 4, V);
+            if (full_jones)
+                oracle_apply_jones(S, n_tiles, gains + (int64_t)f * n_tiles * 8, V);
+            else
+                oracle_apply_gains(S, n_tiles, gains + (int64_t)f * n_tiles * 4, V);
             W = oracle_grid_v(V, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
             free(V);
         } else {

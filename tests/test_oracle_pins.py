@@ -493,3 +493,36 @@ def test_dedisperse_equals_direct_sum():
     for t in range(9 - 3):
         ref = sum(img[t + d[f], f] for f in range(4)) / 4
         assert np.allclose(out[t], ref, rtol=0, atol=1e-15)
+
+
+def _random_jones(n_tiles, seed, shape=()):
+    rng = np.random.default_rng(seed)
+    return (rng.normal(size=shape + (n_tiles, 2, 2)) + 1j * rng.normal(size=shape + (n_tiles, 2, 2)))
+
+
+def test_jones_equal_brute_force_on_mixed_voltages():
+    # J applied to each tile's voltage pair before the products (x' = J x), summed directly: another order
+    rng = np.random.default_rng(13)
+    nt, ns = 4, 6
+    volt = rng.integers(0, 256, size=(ns, 1, nt, 2), dtype=np.uint8)
+    J = _random_jones(nt, 14)
+    x = np.einsum("apr,tar->tap", J, _unpack(volt)[:, 0])      # [t][tile][pol]
+    V = oracle.apply_jones(oracle.correlate(volt, ns, 1)[0, 0], J)
+    for i in range(nt):
+        for j in range(i + 1):
+            for p in range(2):
+                for q in range(2):
+                    ref = np.sum(x[:, i, p] * np.conj(x[:, j, q]))
+                    assert abs(V[_bidx(i, j), 2 * p + q] - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+def test_diagonal_jones_are_gains():
+    w = bs.build_workload("tiny")
+    S = oracle.correlate(w["volt"], 10, 1)[0, 0]
+    g = _random_gains(128, 4)
+    J = np.zeros((128, 2, 2), np.complex128)
+    J[:, 0, 0], J[:, 1, 1] = g[:, 0], g[:, 1]
+    assert np.allclose(oracle.apply_jones(S, J), oracle.apply_gains(S, g), rtol=1e-13, atol=1e-9)
+    a = oracle.pipeline(w["volt"], w["enu"], w["freqs"], 10, 1, 64, gains=g[None])
+    b = oracle.pipeline(w["volt"], w["enu"], w["freqs"], 10, 1, 64, gains=J[None])
+    assert np.allclose(a["images"], b["images"], rtol=0, atol=1e-12)
