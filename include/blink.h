@@ -71,6 +71,9 @@ typedef struct {
                                    as V_ij^pq = g_i^p S_ij^pq conj(g_j^q) inside the correlation; F = the call's
                                    output channels (obs.n_fine / obs.chan_avg, for blink_pipeline_sets over
                                    the call's whole channel axis).  Read during the call only. */
+    const float* jones;         /* host [F][n_tiles][2][2][2] (J[p][r] re, im) or NULL: full 2x2 Jones matrices
+                                   (polarisation leakage included), V_ij = J_i S_ij J_j^H; takes precedence
+                                   over gains; Stokes I and XX then need all four products. */
 } blink_array;
 
 /* The observation (Sec. 5.2.1-5.2.2 and the -t / -c options of the pipeline's command line). */

@@ -53,7 +53,8 @@ class BlinkError(RuntimeError):
 
 
 class blink_array(C.Structure):
-    _fields_ = [("n_tiles", C.c_int32), ("enu_m", C.c_void_p), ("flags", C.c_void_p), ("gains", C.c_void_p)]
+    _fields_ = [("n_tiles", C.c_int32), ("enu_m", C.c_void_p), ("flags", C.c_void_p), ("gains", C.c_void_p),
+                ("jones", C.c_void_p)]
 
 
 class blink_obs(C.Structure):
@@ -137,17 +138,23 @@ class Array:
     enu_m: np.ndarray
     flags: np.ndarray | None = None
     gains: np.ndarray | None = None      # complex [F][n_tiles][2] per output channel, tile, polarisation
+    jones: np.ndarray | None = None      # complex [F][n_tiles][2][2] full Jones matrices J[p][r]
 
     def c(self):
         self._enu = np.ascontiguousarray(self.enu_m, dtype=np.float64)
         self._flags = None if self.flags is None else np.ascontiguousarray(self.flags, dtype=np.uint8)
-        self._gains = None
-        if self.gains is not None:
-            g = np.asarray(self.gains)
-            self._gains = np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1), dtype=np.float32)
+
+        def pack(z):
+            if z is None:
+                return None
+            z = np.asarray(z)
+            return np.ascontiguousarray(np.stack([z.real, z.imag], axis=-1), dtype=np.float32)
+
+        self._gains, self._jones = pack(self.gains), pack(self.jones)
         return blink_array(self._enu.shape[0], self._enu.ctypes.data,
                            None if self._flags is None else self._flags.ctypes.data,
-                           None if self._gains is None else self._gains.ctypes.data)
+                           None if self._gains is None else self._gains.ctypes.data,
+                           None if self._jones is None else self._jones.ctypes.data)
 
 
 @dataclass

@@ -248,17 +248,21 @@ blink_status workspace(blink_context* ctx, int slot, size_t bytes, void** out) {
     return BLINK_OK;
 }
 
-// The call's calibration gains (F output channels) copied to device workspace, or an empty reference.
+// The call's calibration (F output channels) copied to device workspace: full Jones matrices when given,
+// else diagonal gains, else an empty reference.
 blink_status upload_gains(blink_context* ctx, const blink_array* a, int F, cudaStream_t st, GainRef* out) {
     *out = GainRef{};
-    if (!a->gains || F < 1) return BLINK_OK;
-    const size_t n = (size_t)F * a->n_tiles * 4;
+    const float* src = a->jones ? a->jones : a->gains;
+    if (!src || F < 1) return BLINK_OK;
+    const size_t n = (size_t)F * a->n_tiles * (a->jones ? 8 : 4);
     for (size_t i = 0; i < n; i++)
-        if (!std::isfinite(a->gains[i])) return set_error(BLINK_ERR_INVALID_ARG, "array.gains has a non-finite value");
+        if (!std::isfinite(src[i]))
+            return set_error(BLINK_ERR_INVALID_ARG, "array.gains or array.jones has a non-finite value");
     void* d = nullptr;
     BLINK_TRY(workspace(ctx, 6, n * sizeof(float), &d));
-    BLINK_CUDA(cudaMemcpyAsync(d, a->gains, n * sizeof(float), cudaMemcpyHostToDevice, st));
+    BLINK_CUDA(cudaMemcpyAsync(d, src, n * sizeof(float), cudaMemcpyHostToDevice, st));
     out->d = static_cast<const float2*>(d);
+    out->full = a->jones != nullptr;
     return BLINK_OK;
 }
 
@@ -822,7 +826,7 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
         need += (size_t)T * (st.n_fine / obs->chan_avg) * st.imaging.n_pix * st.imaging.n_pix;
     }
     if (need > img_capacity) return set_error(BLINK_ERR_INVALID_ARG, "img_capacity smaller than the sets' images");
-    if (array->gains)
+    if (array->gains || array->jones)
         for (int s = 0; s < n_sets; s++)
             if (sets[s].fine0 % obs->chan_avg)
                 return set_error(BLINK_ERR_INVALID_ARG, "with gains, every set must start on an output channel");

@@ -110,11 +110,13 @@ struct StageTimer {
 
 // ---- kernel launchers (defined next to their kernels) --------------------------------------------
 void launch_cells(const Plan& p, cudaStream_t st);
-// Calibration gains of a correlation launch: complex float [channels][n_tiles][2 pol] on the device; item
-// channel f uses row f0 + f.  d == NULL: no gains.
+// Calibration of a correlation launch: complex float [channels][n_tiles][2 pol] gains, or (full) complex
+// [channels][n_tiles][2][2] Jones matrices J[p][r], on the device; item channel f uses row f0 + f.
+// d == NULL: none.
 struct GainRef {
     const float2* d = nullptr;
     int f0 = 0;
+    bool full = false;
 };
 blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sample_stride_bytes, const Plan& p,
                               int ns, int first_item, int n_items, void* out, int64_t out_item_stride,

@@ -23,7 +23,8 @@ __device__ __forceinline__ float2 gain_prod(float2 gi, float sr, float si, float
     return make_float2(tr * gjc.x - ti * gjc.y, tr * gjc.y + ti * gjc.x);
 }
 
-template <int OUT>
+// FULL: gains are 2x2 Jones matrices, V^pq = sum_rs J_i[p][r] S^rs conj(J_j[q][s]); all four products formed.
+template <int OUT, bool FULL>
 __global__ void __launch_bounds__(kThreads)
 k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles, int ns, int c, int F,
             int first_item, const short2* __restrict__ bl, int64_t B, const uint8_t* __restrict__ flags,
@@ -77,7 +78,7 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
                 acc[m][1] += a.y * b.x - a.x * b.y;
                 acc[m][6] += a.z * b.z + a.w * b.w;           // YY
                 acc[m][7] += a.w * b.z - a.z * b.w;
-                if (OUT == CORR_OUT_VIS4) {
+                if (OUT == CORR_OUT_VIS4 || FULL) {
                     acc[m][2] += a.x * b.z + a.y * b.w;       // XY
                     acc[m][3] += a.y * b.z - a.x * b.w;
                     acc[m][4] += a.z * b.x + a.w * b.y;       // YX
@@ -89,12 +90,34 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
     }
 
     const float fk = (float)K;
-    const float2* g = gains ? gains + (int64_t)(gain_f0 + f) * n_tiles * 2 : nullptr;
+    const float2* g = gains ? gains + (int64_t)(gain_f0 + f) * n_tiles * (FULL ? 4 : 2) : nullptr;
 #pragma unroll
     for (int m = 0; m < kBpt; m++) {
         const int64_t b = (int64_t)blockIdx.x * kThreads * kBpt + m * kThreads + tid;
         if (b >= B) continue;
-        if (g) {
+        if (FULL) {
+            // V = J_i S J_j^H over the four products (slots 2 (p, q) and 2 (p, q) + 1: re, im)
+            const float2* Ji = g + bi[m] * 4;
+            const float2* Jj = g + bj[m] * 4;
+            float v[8];
+#pragma unroll
+            for (int pq = 0; pq < 4; pq++) {
+                const int p = pq >> 1, q = pq & 1;
+                float vr = 0.f, vi = 0.f;
+#pragma unroll
+                for (int rs = 0; rs < 4; rs++) {
+                    const int r = rs >> 1, s2 = rs & 1;
+                    const float2 t = gain_prod(Ji[2 * p + r], acc[m][2 * rs], acc[m][2 * rs + 1],
+                                               make_float2(Jj[2 * q + s2].x, -Jj[2 * q + s2].y));
+                    vr += t.x;
+                    vi += t.y;
+                }
+                v[2 * pq] = vr;
+                v[2 * pq + 1] = vi;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) acc[m][q] = v[q];
+        } else if (g) {
             // calibrated products (p, q) = (X, X), (X, Y), (Y, X), (Y, Y) in acc slots 0-1, 2-3, 4-5, 6-7
 #pragma unroll
             for (int pq = 0; pq < 4; pq++) {
@@ -127,6 +150,13 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
 
 }  // namespace
 
+template <int OUT, bool FULL>
+void corr_fp32(dim3 grid, size_t smem, cudaStream_t st, const uint8_t* d_volt, int64_t sample_stride, const Plan& p,
+               int ns, int first, void* o, int64_t out_item_stride, int kc, GainRef gains) {
+    k_corr_fp32<OUT, FULL><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns, p.chan_avg, p.F, first,
+                                                         p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
+}
+
 blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
                               int first_item, int n_items, void* out, int64_t out_item_stride, int*,
                               cudaStream_t st, GainRef gains) {
@@ -138,18 +168,25 @@ blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sampl
         dim3 grid(gx, n);
         char* o = static_cast<char*>(out) + (int64_t)i0 * out_item_stride *
                                                 (out_kind == CORR_OUT_VIS4 ? sizeof(float) : sizeof(float2));
+        const bool full = gains.d && gains.full;
         switch (out_kind) {
             case CORR_OUT_VIS4:
-                k_corr_fp32<CORR_OUT_VIS4><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
-                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
+                if (full) corr_fp32<CORR_OUT_VIS4, true>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
+                                                         out_item_stride, kc, gains);
+                else corr_fp32<CORR_OUT_VIS4, false>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
+                                                     out_item_stride, kc, gains);
                 break;
             case CORR_OUT_STOKES_I:
-                k_corr_fp32<CORR_OUT_STOKES_I><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
-                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
+                if (full) corr_fp32<CORR_OUT_STOKES_I, true>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0,
+                                                             o, out_item_stride, kc, gains);
+                else corr_fp32<CORR_OUT_STOKES_I, false>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0,
+                                                         o, out_item_stride, kc, gains);
                 break;
             default:
-                k_corr_fp32<CORR_OUT_XX><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns,
-                    p.chan_avg, p.F, first_item + i0, p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
+                if (full) corr_fp32<CORR_OUT_XX, true>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
+                                                       out_item_stride, kc, gains);
+                else corr_fp32<CORR_OUT_XX, false>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
+                                                   out_item_stride, kc, gains);
         }
     }
     BLINK_CUDA(cudaGetLastError());

@@ -163,10 +163,12 @@ __device__ __forceinline__ void pair_of(int q, int& mb, int& jb) {
     jb = q - mb * (mb + 1) / 2;
 }
 
-// GAINS: the calibrated form (gains applied in the epilogue; Stokes I through split X / Y chains).  The
-// uncalibrated kernel is a separate instantiation with none of that code.
-template <bool GAINS>
+// CAL: 0 uncalibrated; 1 diagonal gains applied in the epilogue (Stokes I through split X / Y chains); 2 full
+// 2x2 Jones matrices, which need all four products, so every output kind runs the four-product layout and the
+// epilogue forms J_i S J_j^H.  Each is a separate instantiation.
+template <int CAL>
 __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    constexpr bool GAINS = CAL > 0, FULL = CAL == 2;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* ops = smem;                                   // n_blk tiles of 128 x Kp bytes
     float* st_re = reinterpret_cast<float*>(smem + P.off_re);   // plane 0 of buffer 0; planes kPlane apart
@@ -252,8 +254,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         if (GAINS) {
             // this item's gains, read by the epilogue (after the barrier that ends the unpack)
             const int f = it - (it / P.F) * P.F;
-            const float2* g = P.gains + (int64_t)(P.gain_f0 + f) * P.n_tiles * 2;
-            for (int e = tid; e < 2 * P.n_tiles; e += kThreads) s_g[e] = g[e];
+            const int per = FULL ? 4 : 2;                        // float2 per tile: J[p][r], or g[p]
+            const float2* g = P.gains + (int64_t)(P.gain_f0 + f) * P.n_tiles * per;
+            for (int e = tid; e < per * P.n_tiles; e += kThreads) s_g[e] = g[e];
         }
         // ---- unpack nibbles to e4m3 operand rows, four consecutive k per 32-bit store -----------------
         // A task is (k group g, tile a, polarisation p): its four raw bytes give, through the LUT, the words
@@ -267,9 +270,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                 int unit, kp, kh;
                 if (GAINS && P.mode == CORR_OUT_STOKES_I && P.split) {
                     unit = a; kp = p * P.Kpol + k0; kh = P.Kq;          // [re, im] of X, then of Y
-                } else if (P.mode == CORR_OUT_STOKES_I) {
+                } else if (P.mode == CORR_OUT_STOKES_I && !FULL) {
                     unit = a; kp = p * P.Kq + k0; kh = 2 * P.Kq;        // re X, re Y, im X, im Y
-                } else if (P.mode == CORR_OUT_VIS4) {
+                } else if (P.mode == CORR_OUT_VIS4 || FULL) {
                     unit = 2 * a + p; kp = k0; kh = P.Kq;
                 } else {
                     if (p) continue;
@@ -343,6 +346,49 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                 pair_of(q, mb, jb);
                 const float* sre = st_re + sb * stage_buf;
                 const float* sim = st_im + sb * stage_buf;
+                if (FULL) {
+                    // tile pairs of this unit block pair (units 2 tile + pol): V = J_i S J_j^H from the four
+                    // staged products of each pair; VIS4 writes all four / K, the imaging kinds XX (+ YY)
+                    for (int e = tid; e < 32 * 32; e += kThreads) {
+                        const int il = e >> 5, jl = e & 31;
+                        const int ti = mb * 32 + il, tj = jb * 32 + jl;
+                        if (ti >= P.n_tiles || tj > ti) continue;
+                        const float2* Ji = s_g + 4 * ti;
+                        const float2* Jj = s_g + 4 * tj;
+                        float2 S[4];
+#pragma unroll
+                        for (int rs = 0; rs < 4; rs++) {
+                            const int o = (2 * il + (rs >> 1)) * kStageLd + 2 * jl + (rs & 1);
+                            S[rs] = make_float2(sre[o], sim[o]);
+                        }
+                        float2 V[4];
+#pragma unroll
+                        for (int pq = 0; pq < 4; pq++) {
+                            const int pp = pq >> 1, qq = pq & 1;
+                            float vr = 0.f, vi = 0.f;
+#pragma unroll
+                            for (int rs = 0; rs < 4; rs++) {
+                                const float2 a = Ji[2 * pp + (rs >> 1)], c = Jj[2 * qq + (rs & 1)];
+                                const float tr = a.x * S[rs].x - a.y * S[rs].y, tim = a.x * S[rs].y + a.y * S[rs].x;
+                                vr += tr * c.x + tim * c.y;
+                                vi += tim * c.x - tr * c.y;
+                            }
+                            V[pq] = make_float2(vr, vi);
+                        }
+                        const int64_t b = (int64_t)ti * (ti + 1) / 2 + tj;
+                        if (P.mode == CORR_OUT_VIS4) {
+                            float2* o = reinterpret_cast<float2*>(static_cast<float*>(P.out) +
+                                                                  (int64_t)local * P.out_item_stride) + b * 4;
+#pragma unroll
+                            for (int pq = 0; pq < 4; pq++)
+                                o[pq] = make_float2(__fdiv_rn(V[pq].x, div), __fdiv_rn(V[pq].y, div));
+                        } else {
+                            float2* o = static_cast<float2*>(P.out) + (int64_t)local * P.out_item_stride + b;
+                            *o = P.mode == CORR_OUT_STOKES_I ? make_float2(V[0].x + V[3].x, V[0].y + V[3].y) : V[0];
+                        }
+                    }
+                    return;
+                }
                 // (flagged tiles need no test: their operand rows were zeroed in the unpack)
                 if (P.mode == CORR_OUT_VIS4) {
                     for (int e = tid; e < 64 * 64; e += kThreads) {
@@ -472,14 +518,15 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     P.c = c;
     P.F = p.F;
     P.K = K;
-    P.units = out_kind == CORR_OUT_VIS4 ? 2 * nt : nt;
+    const bool four = out_kind == CORR_OUT_VIS4 || (gains.d && gains.full);   // all four products
+    P.units = four ? 2 * nt : nt;
     P.n_blk = (P.units + kUnitsPerBlk - 1) / kUnitsPerBlk;
     P.Kq = (K + 3) / 4 * 4;
     P.gains = gains.d;
     P.gain_f0 = gains.f0;
-    P.split = gains.d && out_kind == CORR_OUT_STOKES_I;
+    P.split = gains.d && !gains.full && out_kind == CORR_OUT_STOKES_I;
     P.Kpol = (2 * P.Kq + 31) / 32 * 32;
-    P.Kr = out_kind == CORR_OUT_STOKES_I ? 4 * P.Kq : 2 * P.Kq;
+    P.Kr = (out_kind == CORR_OUT_STOKES_I && !four) ? 4 * P.Kq : 2 * P.Kq;
     P.Kp = P.split ? 2 * P.Kpol : (P.Kr + 31) / 32 * 32;
     P.n_pairs = P.n_blk * (P.n_blk + 1) / 2;
     P.pair_cols = P.split ? 128 : 64;
@@ -496,11 +543,12 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     off = align_up(off + P.raw_bytes, 128);
     P.off_re = off;                                // buffer b: planes from off_re + b * stage_buf, kPlane apart
     P.off_im = off + kPlane * 4;
-    const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32 + (gains.d ? nt * 16 + 16 : 0);
+    const uint32_t gain_bytes = gains.d ? (uint32_t)nt * (gains.full ? 32 : 16) : 0;
+    const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32 + (gains.d ? gain_bytes + 16 : 0);
     P.two_stage = off + 2 * P.stage_buf * 4 + tail <= 227 * 1024;
     off = align_up(off + (P.two_stage ? 2 : 1) * P.stage_buf * 4, 16);
-    P.off_gain = off;                              // [n_tiles][2] float2 when gains are given
-    if (gains.d) off = align_up(off + nt * 16, 16);
+    P.off_gain = off;                              // [n_tiles][2] (or [n_tiles][4] Jones) float2 when given
+    if (gains.d) off = align_up(off + gain_bytes, 16);
     P.off_lut = off;
     off += 256 * 4;
     P.off_flags = off;
@@ -531,15 +579,18 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     if (r != CUDA_SUCCESS) return set_error(BLINK_ERR_CUDA, "cuTensorMapEncodeTiled failed for the voltage block");
     static size_t smem_set = 0;                   // raise the kernel's limit once (not during a capture)
     if (smem > smem_set) {
-        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        BLINK_CUDA(cudaFuncSetAttribute(k_corr_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         smem_set = 227 * 1024;
     }
     const int grid = std::min(n_items, n_sm);
-    if (gains.d)
-        k_corr_tc<true><<<grid, kThreads, smem, st>>>(map, P);
+    if (gains.d && gains.full)
+        k_corr_tc<2><<<grid, kThreads, smem, st>>>(map, P);
+    else if (gains.d)
+        k_corr_tc<1><<<grid, kThreads, smem, st>>>(map, P);
     else
-        k_corr_tc<false><<<grid, kThreads, smem, st>>>(map, P);
+        k_corr_tc<0><<<grid, kThreads, smem, st>>>(map, P);
     BLINK_CUDA(cudaGetLastError());
     return BLINK_OK;
 }

@@ -49,7 +49,7 @@ def test_host_only_calls_without_gpu(lib_path):
 
 def test_struct_layout_matches_header(lib_path):
     from paper_2505_15204_gb300 import blink as B
-    assert ctypes.sizeof(B.blink_array) == 32
+    assert ctypes.sizeof(B.blink_array) == 40
     assert ctypes.sizeof(B.blink_obs) == 32
     assert ctypes.sizeof(B.blink_imaging) == 32
     assert ctypes.sizeof(B.blink_set) == 48

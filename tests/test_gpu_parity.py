@@ -569,3 +569,60 @@ def test_dedisperse_rejects_bad_delays(B, ctx):
     for d in ([0, 4], [-1, 0]):
         with pytest.raises(B.BlinkError):
             B.blink_dedisperse(ctx, img, 4, 2, 64, np.array(d, np.int32), out)
+
+
+def _jones(F, n_tiles, seed):
+    rng = np.random.default_rng(seed)
+    J = (np.eye(2) + 0.3 * (rng.normal(size=(F, n_tiles, 2, 2)) + 1j * rng.normal(size=(F, n_tiles, 2, 2))))
+    return J.astype(np.complex64)                      # leakage of about 30 %
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_correlate_with_jones_matches_oracle(B, ctx, arith):
+    w, volt, freqs, fl = _case("coarse", 20, 8, flags=True)
+    F, K = 4, 20
+    J = _jones(F, 128, 8)
+    out = torch.empty((2, F, 8256, 4, 2), dtype=torch.float32, device="cuda")
+    B.blink_correlate(ctx, B.Array(w["enu"], fl, None, J), B.Obs(freqs, 2, 10, 20), arith, dev(volt), out)
+    B.blink_sync(ctx)
+    got = out.cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    S = oracle.correlate(volt, 10, 2, flags=fl)
+    for tau in range(2):
+        for f in range(F):
+            ref = oracle.apply_jones(S[tau, f], J[f].astype(np.complex128)) / K
+            err = np.abs(got[tau, f] - ref).max() / np.abs(ref).max()
+            assert err <= 2e-6, (arith, tau, f, err)
+
+
+@pytest.mark.parametrize("arith,pol", [(1, 0), (0, 0), (1, 1)])
+def test_pipeline_with_jones_matches_oracle(B, ctx, arith, pol):
+    w, volt, freqs, fl = _case("coarse", 20, 8, flags=True)
+    F, n = 8, 256
+    J = _jones(F, 128, 9)
+    img = torch.empty((2 * F, n, n), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"], fl, None, J), B.Obs(freqs, 1, 10, 20), B.Imaging(n, pol=pol), arith, 0,
+                     dev(volt), img)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n, flags=fl, pol=pol, gains=J.astype(np.complex128),
+                          n_threads=8)["images"]
+    got = img.cpu().numpy()
+    for q in range(2 * F):
+        assert rel_rms(got[q], ref[q]) <= IMG_RTOL, (q, rel_rms(got[q], ref[q]))
+
+
+def test_diagonal_jones_images_equal_gains_images(B, ctx):
+    # the four-product Jones kernel and the split-chain gains kernel agree to FP32 rounding
+    w, volt, freqs, _ = _case("coarse", 20, 8)
+    n = 256
+    g = _gains(8, 128, 10)
+    J = np.zeros((8, 128, 2, 2), np.complex64)
+    J[..., 0, 0], J[..., 1, 1] = g[..., 0], g[..., 1]
+    a = torch.empty((16, n, n), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    obs, im = B.Obs(freqs, 1, 10, 20), B.Imaging(n)
+    B.blink_pipeline(ctx, B.Array(w["enu"], None, g), obs, im, 1, 0, dev(volt), a)
+    B.blink_pipeline(ctx, B.Array(w["enu"], None, None, J), obs, im, 1, 0, dev(volt), b)
+    B.blink_sync(ctx)
+    for q in range(16):
+        assert rel_rms(b[q].cpu().numpy(), a[q].cpu().numpy()) <= 1e-6
