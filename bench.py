@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (default: every host core)")
     ap.add_argument("--dedisperse", action="store_true",
                     help="also time blink_dedisperse on the step's images (a DM sweeping half the chunk)")
+    ap.add_argument("--jones", action="store_true",
+                    help="apply seeded full 2x2 Jones matrices (30 %% leakage) in the correlation")
     ap.add_argument("--gains", action="store_true",
                     help="apply seeded per-channel, per-tile, per-polarisation calibration gains in the correlation")
     return ap.parse_args()
@@ -193,6 +195,13 @@ def bench_gains(n_out_chan: int, n_tiles: int) -> np.ndarray:
     return (amp * np.exp(1j * rng.uniform(-np.pi, np.pi, size=amp.shape))).astype(np.complex64)
 
 
+def bench_jones(n_out_chan: int, n_tiles: int) -> np.ndarray:
+    """Seeded Jones matrices, complex64 [channels][tiles][2][2]: identity plus about 30 % random leakage."""
+    rng = np.random.default_rng(2505152041)
+    z = rng.normal(size=(n_out_chan, n_tiles, 2, 2)) + 1j * rng.normal(size=(n_out_chan, n_tiles, 2, 2))
+    return (np.eye(2) + 0.3 * z).astype(np.complex64)
+
+
 def oracle_sets_images(oracle, inp, w, sets, picks, threads, gains=None):
     """The oracle's images for the picked (set index, local image id) pairs, in order."""
     out = []
@@ -244,8 +253,9 @@ def run_reference(args, world, rank):
         if not sel:
             sel = picks[:1]
         t = time.perf_counter()
-        oracle_sets_images(oracle, inp, w, sets, sel, cores,
-                           bench_gains(w.n_out_chan, w.n_tiles) if args.gains else None)
+        cal = (bench_jones(w.n_out_chan, w.n_tiles) if args.jones else
+               bench_gains(w.n_out_chan, w.n_tiles) if args.gains else None)
+        oracle_sets_images(oracle, inp, w, sets, sel, cores, cal)
         dt = time.perf_counter() - t
         if s_ >= args.warmup:
             times.append((len(sel), dt))
@@ -304,7 +314,9 @@ def run_ours(args, world, rank, local):
     ctx = B.blink_create(local)
     prec = B.BLINK_PREC_BF16 if args.precision == "bf16" else B.BLINK_PREC_FP32
     gains = bench_gains(w.n_out_chan, n_tiles) if args.gains else None
-    arr, obs = B.Array(inp["enu"], None, gains), B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns)
+    jones = bench_jones(w.n_out_chan, n_tiles) if args.jones else None
+    arr = B.Array(inp["enu"], None, gains, jones)
+    obs = B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns)
     im = B.Imaging(n_pix, precision=prec)
     bsets = [B.Set(fine0=st.fine0, n_fine=st.n_fine, imaging=B.Imaging(side, precision=prec), flags=st.flags)
              for st, _, _, side in sets]
@@ -403,7 +415,7 @@ def run_ours(args, world, rank, local):
         n_s = max(4, 4 * cores)
         picks = pick_images(sets, n_s)
         t = time.perf_counter()
-        refs = oracle_sets_images(oracle, inp, w, sets, picks, cores, gains)
+        refs = oracle_sets_images(oracle, inp, w, sets, picks, cores, jones if jones is not None else gains)
         dt = time.perf_counter() - t
         flat = img.reshape(-1)
         got = []
@@ -513,6 +525,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": workload_label(args.workload, w),
                    "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
                    "mode": args.mode, "precision": args.precision, "gains": bool(args.gains),
+                   "jones": bool(args.jones),
                    "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
                           "each step timed alone after a 516 MB buffer overwrite") if small else
                          (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e9:.3g} GB per step exceed L2; "
