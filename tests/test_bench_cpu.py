@@ -55,3 +55,31 @@ def test_workload_labels(bench):
     assert "38,400" not in bench.workload_label("fullband", bs.WORKLOADS["fullband"])
     assert bench.workload_label("fullband", bs.WORKLOADS["fullband"]).startswith("fullband: 50 ms chunk, 144 tiles")
     assert bench.workload_label("uneven", bs.WORKLOADS["uneven"]).startswith("uneven: 144 tiles")
+
+
+def test_calibration_generators_are_seeded_and_shaped(bench):
+    g1, g2 = bench.bench_gains(8, 16), bench.bench_gains(8, 16)
+    assert g1.shape == (8, 16, 2) and g1.dtype == np.complex64 and np.array_equal(g1, g2)
+    assert 0.5 <= np.abs(g1).min() and np.abs(g1).max() <= 1.5
+    J = bench.bench_jones(8, 16)
+    assert J.shape == (8, 16, 2, 2) and np.array_equal(J, bench.bench_jones(8, 16))
+
+
+def test_oracle_images_of_picked_sets_use_each_sets_calibration(bench):
+    # the per-set slice of a call-wide calibration array reaches the oracle: the picked images equal direct
+    # oracle calls on each set with its own channels, flags and gains
+    import oracle
+    w = bs.WORKLOADS["uneven"]
+    inp = bs.build_workload("uneven", n_samples=10)
+    small = [type(st)(fine0=st.fine0, n_fine=2, n_pix=64, flags=st.flags) for st in inp["sets"]]
+    inp = dict(inp, sets=small)
+    sets = bench.image_sets(inp, w, 10)
+    gains = bench.bench_gains(w.n_fine // w.chan_avg, w.n_tiles)
+    picks = [(0, 1), (2, 0), (3, 1)]
+    got = bench.oracle_sets_images(oracle, inp, w, sets, picks, 2, gains)
+    for (q, i), img in zip(picks, got):
+        st = small[q]
+        ref = oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], w.samples_per_int, w.chan_avg, 64,
+                              ids=np.array([i]), flags=st.flags, fine0=st.fine0, n_fine=st.n_fine,
+                              gains=gains[st.fine0:st.fine0 + st.n_fine].astype(np.complex128))["images"][0]
+        assert np.array_equal(img, ref)
