@@ -56,6 +56,21 @@ def test_correlate_phase_pattern_conjugates_second_tile():
                     assert got[0] == round(want.real) and got[1] == round(want.imag), (i, j, p, q)
 
 
+def test_correlate_unpacks_every_byte_value():
+    # one sample per channel, channel f carries byte f on tile 1 (X) against 1 + 0i on tile 0 (X):
+    # S_10^XX = x_1 conj(1) = x_1 reads back the decoded byte, S_11^XX = |x_1|^2.  The format (Sec. 5.2.1,
+    # 4-bit complex) is low nibble = real, high nibble = imaginary, each two's complement in [-8, 7].
+    v = np.zeros((1, 256, 2, 2), dtype=np.uint8)
+    v[0, :, 0, 0] = 0x01
+    v[0, :, 1, 0] = np.arange(256, dtype=np.uint8)
+    S = oracle.correlate(v, 1, 1)[0]
+    for b in range(256):
+        re_, im_ = ((b & 15) ^ 8) - 8, ((b >> 4) ^ 8) - 8
+        assert tuple(S[b, _bidx(1, 0), 0]) == (re_, im_), b
+        assert tuple(S[b, _bidx(1, 1), 0]) == (re_ * re_ + im_ * im_, 0), b
+        assert not S[b, :, 1:].any()
+
+
 def test_correlate_single_product_lands_in_its_slot():
     # one non-zero sample on tile 4 pol X and tile 1 pol Y: only S_41^XY = x conj(y) is non-zero
     nt = 6
@@ -335,6 +350,27 @@ def test_off_centre_source_peaks_at_its_direction():
     y, x = np.unravel_index(np.argmax(img), img.shape)
     assert abs(x - (n / 2 + lm[0] * n * du)) <= 1.0
     assert abs(y - (n / 2 + lm[1] * n * du)) <= 1.0
+
+
+def test_noisy_source_at_phase_centre_adds_autocorrelation_noise_share():
+    # Voltage-level source of power S at the phase centre in noise of quantised power P_n per sample: every
+    # cross visibility has mean S and every auto S + P_n, so with autos gridded (weight N_a^2) the centre
+    # pixel has mean S + P_n / N_a.  Its spread per integration is the thermal sigma_img plus the source's own
+    # power fluctuation over K samples (at most S / sqrt(K)); the mean of 16 integrations must sit within
+    # 3 of those of S + P_n / N_a.  The autos' share alone is several times that margin, so dropping the
+    # autos or the 1/2 of Stokes I fails.
+    n_a, K, T = 64, 40, 16
+    enu = bs.tile_positions(n_a, 1500.0, 14)
+    sigma_img = bs.image_noise(2.0, n_a, K)
+    S = 10 * sigma_img
+    sky = bs.Sky(lmn=np.array([[0.0, 0.0, 1.0]]), power=np.array([S]))
+    v = bs.voltages(enu, np.array([150e6]), K * T, sky, seed=15)
+    out = oracle.pipeline(v, enu, np.array([150e6]), K, 1, 64)
+    centre = out["images"][:, 32, 32]
+    p_n = 2 * (4 + 1 / 12)
+    assert centre.shape == (T,)
+    spread = math.sqrt(sigma_img ** 2 + S ** 2 / K)
+    assert abs(centre.mean() - (S + p_n / n_a)) < 3 * spread / math.sqrt(T)
 
 
 def test_noise_level_of_pure_noise_image():
