@@ -7,7 +7,10 @@
  * ---------------------------------------
  * - Pointers prefixed d_ are device memory owned by the caller (for example PyTorch tensors); pointers
  *   prefixed h_ and the pointers inside the descriptor structs are host memory owned by the caller and
- *   read only during the call.  The library keeps no pointer to caller memory after returning.
+ *   read only during the call, with two exceptions stated where they apply: page-locked calibration
+ *   tables (array.gains, array.jones) and blink_pipeline_host's page-locked or device-writable buffers
+ *   are used by work still queued on the stream.  The library keeps no other pointer to caller memory
+ *   after returning.
  * - Calls are asynchronous and ordered on `stream` (a cudaStream_t passed as void*; NULL = legacy
  *   default stream).  Argument errors are reported synchronously through the return value, and nothing
  *   is launched.  Device-side errors (a failed index guard, a bounded wait that ran out) are recorded
@@ -70,10 +73,14 @@ typedef struct {
                                    diagonal Jones matrix per output channel and tile, applied to the products
                                    as V_ij^pq = g_i^p S_ij^pq conj(g_j^q) inside the correlation; F = the call's
                                    output channels (obs.n_fine / obs.chan_avg, for blink_pipeline_sets over
-                                   the call's whole channel axis).  Read during the call only. */
+                                   the call's whole channel axis).  Copied to the device on `stream` by
+                                   an asynchronous copy: pageable memory is read before the call returns,
+                                   page-locked memory when the stream reaches the copy (keep it unchanged
+                                   until then; under graph capture every replay reads its contents anew). */
     const float* jones;         /* host [F][n_tiles][2][2][2] (J[p][r] re, im) or NULL: full 2x2 Jones matrices
                                    (polarisation leakage included), V_ij = J_i S_ij J_j^H; takes precedence
-                                   over gains; Stokes I and XX then need all four products. */
+                                   over gains; Stokes I and XX then need all four products.  Copied like
+                                   gains. */
 } blink_array;
 
 /* The observation (Sec. 5.2.1-5.2.2 and the -t / -c options of the pipeline's command line). */
@@ -100,8 +107,9 @@ typedef struct {
  * default stream) and returns; blink_sync waits.  The first call for a new plan (array, channels and image
  * parameters) builds the plan and, in the batched form, times the persistent kernel's launch shapes on the
  * stream with a blocking event wait; make that call before any CUDA-graph capture.  Later calls with the
- * same plan allocate nothing and never block, so they can be captured and replayed (calibration gains are
- * copied from host memory on every call, so under capture they must be page-locked).
+ * same plan and the same calibration kind (none, gains or Jones) allocate nothing and never block, so they
+ * can be captured and replayed (calibration gains are copied from host memory on every call, so under
+ * capture they must be page-locked).
  */
 
 /* ---- context ---------------------------------------------------------------------------------- */

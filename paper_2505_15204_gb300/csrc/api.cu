@@ -60,6 +60,8 @@ blink_status check_obs(const blink_obs* o, bool need_freq) {
     if (o->samples_per_int < 1) return set_error(BLINK_ERR_INVALID_ARG, "obs.samples_per_int must be >= 1");
     if (o->n_samples < 0 || o->n_samples % o->samples_per_int)
         return set_error(BLINK_ERR_INVALID_ARG, "obs.n_samples must be a non-negative multiple of samples_per_int");
+    if ((int64_t)(o->n_samples / o->samples_per_int) * (o->n_fine / o->chan_avg) > INT32_MAX)
+        return set_error(BLINK_ERR_UNSUPPORTED, "more than 2^31 - 1 images (integrations x output channels) in one call");
     if ((int64_t)o->samples_per_int * o->chan_avg > 131072)
         return set_error(BLINK_ERR_UNSUPPORTED, "samples_per_int * chan_avg above 131072 (sums could leave the exact "
                                                 "FP32 integer range)");
@@ -648,11 +650,11 @@ blink_status blink_read_profile(blink_context* ctx, void* stream, double* ms, in
 
 blink_status blink_cells(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                          const blink_imaging* imaging, int32_t* d_cells, double* d_uvw, double* h_du, void* stream) {
-    BLINK_TRY(make_current(ctx));
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, true));
     BLINK_TRY(check_imaging(imaging));
     if (!d_cells) return set_error(BLINK_ERR_INVALID_ARG, "d_cells is NULL");
+    BLINK_TRY(make_current(ctx));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Plan* p = nullptr;
     BLINK_TRY(get_plan(ctx, array, obs, imaging, false, st, &p));
@@ -667,7 +669,6 @@ blink_status blink_cells(blink_context* ctx, const blink_array* array, const bli
 
 blink_status blink_correlate(blink_context* ctx, const blink_array* array, const blink_obs* obs, int32_t arith,
                              const uint8_t* d_volt, float* d_vis, void* stream) {
-    BLINK_TRY(make_current(ctx));
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, false));
     if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
@@ -675,6 +676,7 @@ blink_status blink_correlate(blink_context* ctx, const blink_array* array, const
     if (!d_volt || !d_vis) return set_error(BLINK_ERR_INVALID_ARG, "d_volt or d_vis is NULL");
     if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_vis & 15))
         return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_vis 16-byte aligned");
+    BLINK_TRY(make_current(ctx));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Plan* p = nullptr;
     BLINK_TRY(get_plan(ctx, array, obs, nullptr, false, st, &p));
@@ -694,7 +696,6 @@ blink_status blink_correlate(blink_context* ctx, const blink_array* array, const
 blink_status blink_grid(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                         const blink_imaging* imaging, const float* d_vis, int32_t first_image, int32_t n_images,
                         float* d_grid, float* d_weight, void* stream) {
-    BLINK_TRY(make_current(ctx));
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, true));
     BLINK_TRY(check_imaging(imaging));
@@ -705,6 +706,7 @@ blink_status blink_grid(blink_context* ctx, const blink_array* array, const blin
     const int64_t total = (int64_t)(obs->n_samples / obs->samples_per_int) * (obs->n_fine / obs->chan_avg);
     if ((int64_t)first_image + n_images > total)
         return set_error(BLINK_ERR_INVALID_ARG, "image range beyond the observation's T * F images");
+    BLINK_TRY(make_current(ctx));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Plan* p = nullptr;
     BLINK_TRY(get_plan(ctx, array, obs, imaging, true, st, &p));
@@ -719,12 +721,12 @@ blink_status blink_grid(blink_context* ctx, const blink_array* array, const blin
 
 blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const float* d_grid, int32_t n_images,
                          const float* d_weight, float* d_img, void* stream) {
-    BLINK_TRY(make_current(ctx));
     BLINK_TRY(check_imaging(imaging));
     if (!d_grid || !d_weight || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_grid, d_weight or d_img is NULL");
     if (n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "n_images < 0");
     if (((uintptr_t)d_grid & 7) || ((uintptr_t)d_img & 7))
         return set_error(BLINK_ERR_INVALID_ARG, "d_grid and d_img must be 8-byte aligned");
+    BLINK_TRY(make_current(ctx));
     if (n_images == 0) return BLINK_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int N = imaging->n_pix, prec = imaging->precision;
@@ -750,7 +752,6 @@ blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const
 blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                             const blink_imaging* imaging, int32_t arith, int32_t mode, const uint8_t* d_volt,
                             float* d_img, float* d_weight, void* stream) {
-    BLINK_TRY(make_current(ctx));
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, true));
     BLINK_TRY(check_imaging(imaging));
@@ -761,6 +762,7 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
     if (!d_volt || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_volt or d_img is NULL");
     if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_img & 7))
         return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_img 8-byte aligned");
+    BLINK_TRY(make_current(ctx));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Plan* p = nullptr;
     BLINK_TRY(get_plan(ctx, array, obs, imaging, true, st, &p));
@@ -805,7 +807,6 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
 blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                                  const blink_set* sets, int32_t n_sets, int32_t arith, const uint8_t* d_volt,
                                  float* d_img, size_t img_capacity, void* stream) {
-    BLINK_TRY(make_current(ctx));
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, true));
     if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
@@ -830,6 +831,7 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
         for (int s = 0; s < n_sets; s++)
             if (sets[s].fine0 % obs->chan_avg)
                 return set_error(BLINK_ERR_INVALID_ARG, "with gains, every set must start on an output channel");
+    BLINK_TRY(make_current(ctx));
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     GainRef g_all;
     BLINK_TRY(upload_gains(ctx, array, obs->n_fine / obs->chan_avg, strm, &g_all));
@@ -857,7 +859,6 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
 
 blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_int, int32_t n_chan, int32_t n_pix,
                               const int32_t* h_delays, float* d_out, void* stream) {
-    BLINK_TRY(make_current(ctx));
     if (!d_img || !d_out || !h_delays) return set_error(BLINK_ERR_INVALID_ARG, "d_img, d_out or h_delays is NULL");
     if (n_int < 1 || n_chan < 1) return set_error(BLINK_ERR_INVALID_ARG, "n_int and n_chan must be >= 1");
     if (n_pix < 64 || n_pix > 2048 || (n_pix & (n_pix - 1)))
@@ -870,6 +871,7 @@ blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_
         dmax = std::max(dmax, (int)h_delays[f]);
     }
     if (dmax >= n_int) return set_error(BLINK_ERR_INVALID_ARG, "max(delays) must be < n_int");
+    BLINK_TRY(make_current(ctx));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     void* d = nullptr;
     BLINK_TRY(workspace(ctx, 7, sizeof(int32_t) * (size_t)n_chan, &d));
@@ -880,7 +882,6 @@ blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_
 blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                                  const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt, float* h_img,
                                  int32_t images_per_pass, void* stream) {
-    BLINK_TRY(make_current(ctx));
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, true));
     BLINK_TRY(check_imaging(imaging));
@@ -888,6 +889,7 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
         return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
     if (!h_volt || !h_img) return set_error(BLINK_ERR_INVALID_ARG, "h_volt or h_img is NULL");
     if (images_per_pass < 0) return set_error(BLINK_ERR_INVALID_ARG, "images_per_pass < 0");
+    BLINK_TRY(make_current(ctx));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Plan* p = nullptr;
     BLINK_TRY(get_plan(ctx, array, obs, imaging, true, st, &p));
