@@ -17,6 +17,8 @@
  *   in a per-context status word and reported by blink_sync().
  * - No call aborts or throws across the ABI.  blink_last_error() returns the calling thread's last
  *   error message.
+ * - A context is used by one host thread at a time, and its calls share its device workspace: calls on
+ *   different streams must be ordered between those streams (an event), or use separate contexts.
  * - The library allocates device memory only inside the context: per-configuration plans (cell maps,
  *   gather lists) on first use, and workspace that grows to the largest request seen.  A repeated call
  *   with the same configuration allocates nothing.

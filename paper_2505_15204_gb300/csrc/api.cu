@@ -472,9 +472,16 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
         } else if (!p.tuned) {
             // autotune the FFT launch shape on this first batch: time each candidate (every run writes the
             // same images), keep the fastest for every later call of the plan
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            BLINK_CUDA(cudaEventCreate(&e0));
-            BLINK_CUDA(cudaEventCreate(&e1));
+            struct Events {
+                cudaEvent_t e[2] = {nullptr, nullptr};
+                ~Events() {
+                    for (cudaEvent_t x : e)
+                        if (x) cudaEventDestroy(x);
+                }
+            } ev;
+            BLINK_CUDA(cudaEventCreate(&ev.e[0]));
+            BLINK_CUDA(cudaEventCreate(&ev.e[1]));
+            cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
             float best = 0.f;
             for (const FftTune& c : fft_tune_candidates()) {
                 BLINK_CUDA(cudaEventRecord(e0, st));
@@ -492,8 +499,6 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
                 }
             }
             p.tune_ms = best;
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
         } else {
             StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
             BLINK_TRY(launch_fft_persistent(p, p.tune, prec, static_cast<float2*>(vis), p.B, first, ta, tb - ta, H,
