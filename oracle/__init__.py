@@ -59,7 +59,7 @@ def _load():
             lib.oracle_uvw.restype = None
             lib.oracle_uvw.argtypes = [P, C.c_int, C.c_double, P]
             lib.oracle_default_cell.restype = C.c_double
-            lib.oracle_default_cell.argtypes = [P, C.c_int, P, C.c_double, C.c_int]
+            lib.oracle_default_cell.argtypes = [P, C.c_int, P, C.c_double, C.c_int, C.c_int]
             lib.oracle_cells.restype = None
             lib.oracle_cells.argtypes = [P, C.c_int64, C.c_double, C.c_int, P, P, P]
             lib.oracle_grid.restype = C.c_double
@@ -72,8 +72,21 @@ def _load():
             lib.oracle_image.argtypes = [P, C.c_int, C.c_double, P]
             lib.oracle_pipeline.restype = C.c_int
             lib.oracle_pipeline.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
-                                            C.c_int, C.c_double, C.c_int, C.c_int, P, C.c_int, P, C.c_int64,
-                                            C.c_int, P, P, P, P]
+                                            C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, P, C.c_int, P,
+                                            C.c_int64, C.c_int, P, P, P, P]
+            lib.oracle_i0.restype = C.c_double
+            lib.oracle_i0.argtypes = [C.c_double]
+            lib.oracle_kb_beta.restype = C.c_double
+            lib.oracle_kb_beta.argtypes = [C.c_int]
+            lib.oracle_kb.restype = C.c_double
+            lib.oracle_kb.argtypes = [C.c_double, C.c_int, C.c_double]
+            lib.oracle_kb_ft.restype = C.c_double
+            lib.oracle_kb_ft.argtypes = [C.c_double, C.c_int, C.c_double]
+            lib.oracle_grid_kb.restype = C.c_double
+            lib.oracle_grid_kb.argtypes = [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_double, C.c_int,
+                                           C.c_int, P]
+            lib.oracle_kb_crop_correct.restype = None
+            lib.oracle_kb_crop_correct.argtypes = [P, C.c_int, C.c_int, P]
             lib.oracle_apply_jones.restype = None
             lib.oracle_apply_jones.argtypes = [P, C.c_int, P, P]
             lib.oracle_dedisperse.restype = C.c_int
@@ -177,10 +190,10 @@ def uvw(enu: np.ndarray, nu: float) -> np.ndarray:
     return out
 
 
-def default_cell(enu: np.ndarray, nu_max: float, n_pix: int, flags=None) -> float:
+def default_cell(enu: np.ndarray, nu_max: float, n_pix: int, flags=None, support: int = 0) -> float:
     enu = np.ascontiguousarray(enu, dtype=np.float64)
     fl = _flags(flags, enu.shape[0])
-    return float(_load().oracle_default_cell(_p(enu), enu.shape[0], _p(fl), float(nu_max), n_pix))
+    return float(_load().oracle_default_cell(_p(enu), enu.shape[0], _p(fl), float(nu_max), n_pix, support))
 
 
 def cells(uvw_: np.ndarray, du: float, n_pix: int):
@@ -205,6 +218,51 @@ def grid(S_img: np.ndarray, n_tiles: int, K: int, iu, iv, keep, n_pix: int, pol:
     W = _load().oracle_grid(_p(S_img), n_tiles, _p(fl), K, pol, int(bool(autos)), _p(iu), _p(iv), _p(keep),
                             n_pix, _p(G))
     return G[..., 0] + 1j * G[..., 1], float(W)
+
+
+def i0(x: float) -> float:
+    """Modified Bessel function I0 by the oracle's power series."""
+    return float(_load().oracle_i0(float(x)))
+
+
+def kb_beta(support: int) -> float:
+    return float(_load().oracle_kb_beta(support))
+
+
+def kb(t: float, support: int) -> float:
+    """The Kaiser-Bessel gridding kernel C(t) of ``support`` cells (unit integral)."""
+    return float(_load().oracle_kb(float(t), support, kb_beta(support)))
+
+
+def kb_ft(nu: float, support: int) -> float:
+    """Its Fourier transform c(nu), nu in cycles per cell (c(0) = 1)."""
+    return float(_load().oracle_kb_ft(float(nu), support, kb_beta(support)))
+
+
+def grid_kb(V: np.ndarray, n_tiles: int, K: int, uvw_: np.ndarray, du: float, support: int, n_grid: int,
+            pol: int = POL_I, autos: bool = True, flags=None):
+    """Convolutional gridding of raw (integer or calibrated) sums ``V`` [B][4] (complex or [B][4][2]) onto
+    a grid of side ``n_grid``: full complex128 grid [n_grid][n_grid] and W."""
+    V = np.asarray(V)
+    if np.iscomplexobj(V):
+        V = np.stack([V.real, V.imag], axis=-1)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    G = np.zeros((n_grid, n_grid, 2), dtype=np.float64)
+    fl = _flags(flags, n_tiles)
+    uvw_ = np.ascontiguousarray(uvw_, dtype=np.float64)
+    W = _load().oracle_grid_kb(_p(V), n_tiles, _p(fl), K, pol, int(bool(autos)), _p(uvw_), float(du), support,
+                               n_grid, _p(G))
+    return G[..., 0] + 1j * G[..., 1], float(W)
+
+
+def kb_crop_correct(full: np.ndarray, support: int) -> np.ndarray:
+    """The central N x N of the shifted 2N x 2N image, divided by the kernel's transform along both axes
+    (grid correction)."""
+    full = np.ascontiguousarray(full, dtype=np.float64)
+    n = full.shape[0] // 2
+    out = np.zeros((n, n), dtype=np.float64)
+    _load().oracle_kb_crop_correct(_p(full), n, support, _p(out))
+    return out
 
 
 def ifft2(G: np.ndarray) -> np.ndarray:
@@ -236,8 +294,12 @@ def image(a: np.ndarray, W: float):
 
 def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int, c: int, n_pix: int,
              ids=None, flags=None, fine0: int = 0, n_fine: int | None = None, cell_lambda: float = 0.0,
-             pol: int = POL_I, autos: bool = True, n_threads: int = 1, want_grids: bool = False, gains=None):
+             pol: int = POL_I, autos: bool = True, n_threads: int = 1, want_grids: bool = False, gains=None,
+             support: int = 0):
     """Dirty images for the listed image ids (id = tau * F + f) of one set.
+
+    ``support`` >= 2: grid with the Kaiser-Bessel kernel of that many cells on a grid of side 2N (``grids``
+    are then [n][2N][2N]) and keep the corrected central N x N of each image.
 
     ``gains``: complex [F][n_tiles][2] per output channel of the set, tile and polarisation, or complex
     [F][n_tiles][2][2] full Jones matrices, or None.
@@ -260,7 +322,8 @@ def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int,
     imgs = np.zeros((n, n_pix, n_pix), dtype=np.float64)
     W = np.zeros(n, dtype=np.float64)
     mx = np.zeros(n, dtype=np.float64)
-    grids = np.zeros((n, n_pix, n_pix, 2), dtype=np.float64) if want_grids else None
+    ng = 2 * n_pix if support >= 2 else n_pix
+    grids = np.zeros((n, ng, ng, 2), dtype=np.float64) if want_grids else None
     g, full = None, 0
     if gains is not None:
         gains = np.asarray(gains)
@@ -268,7 +331,8 @@ def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int,
         assert gains.shape == ((F, nt, 2, 2) if full else (F, nt, 2))
         g = np.ascontiguousarray(np.stack([np.real(gains), np.imag(gains)], axis=-1), dtype=np.float64)
     rc = _load().oracle_pipeline(volt.ctypes.data + fine0 * nt * 2, nf_total, nt, n_fine, c, ns, _p(enu), _p(ff),
-                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), _p(g), full, _p(ids),
+                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), support, _p(g), full,
+                                 _p(ids),
                                  n, n_threads, _p(grids), _p(imgs), _p(W), _p(mx))
     if rc:
         raise ValueError("oracle_pipeline: bad arguments")

@@ -17,6 +17,10 @@
  *   fft2        Eq. 4 / Sec. 5.2.4: unnormalised inverse 2D transform, own radix-2 FFT; direct DFT
  *               for small sides.
  *   image       Sec. 5.2.4: real part / sum of weights, shifted so the phase centre is the middle pixel.
+ *   grid_kb     Sec. 5.2.4 and 8 (gridding with a convolution kernel, in progress in the paper): each
+ *               visibility spread over W x W cells of a grid twice the image side by a separable
+ *               Kaiser-Bessel kernel; the image is the central half of the transform, divided by the
+ *               kernel's Fourier transform (grid correction).
  *   dedisperse  Sec. 2 and 7 (the FRB search that follows imaging): incoherent dedispersion of the image cube,
  *               out[t] = (1/F) sum_f img[t + d_f][f] with per-channel delays d_f in integrations.
  *
@@ -169,9 +173,13 @@ void oracle_uvw(const double* enu, int n_tiles, double nu, double* uvw)
 }
 
 /* Default uv cell (wavelengths): the longest unflagged projected baseline at the highest frequency lands
- * in the outermost usable cell, du = u_max / (N/2 - 1); u_max = max |(b_E, b_N)| * (nu_max / c).
+ * in the outermost usable cell, du = u_max / (N/2 - 1); u_max = max |(b_E, b_N)| * (nu_max / c).  With a
+ * convolution kernel of W >= 2 cells the grid side is 2N and the support must stay inside it too:
+ * du = u_max / (N - 1 - W/2), which keeps the image's pixel scale within a fraction of a percent of the
+ * nearest-cell one.
  * Degenerate arrays (no unflagged baseline of non-zero length) get du = 1. */
-double oracle_default_cell(const double* enu, int n_tiles, const uint8_t* flags, double nu_max, int n_pix)
+double oracle_default_cell(const double* enu, int n_tiles, const uint8_t* flags, double nu_max, int n_pix,
+                           int support)
 {
     double dmax = 0.0;
     for (int i = 0; i < n_tiles; i++)
@@ -184,6 +192,7 @@ double oracle_default_cell(const double* enu, int n_tiles, const uint8_t* flags,
         }
     double umax = dmax * (nu_max / ORC_C_LIGHT);
     if (!(umax > 0.0)) return 1.0;
+    if (support >= 2) return umax / ((double)(n_pix - 1) - 0.5 * (double)support);
     return umax / (double)(n_pix / 2 - 1);
 }
 
@@ -290,6 +299,144 @@ double oracle_grid_v(const double* V, int n_tiles, const uint8_t* flags, int K, 
     return W;
 }
 
+/*
+ * Gridding with a convolution kernel (Sec. 5.2.4; Sec. 8 lists kernels as work in progress).  The kernel is
+ * not specified by the paper; this is a separable Kaiser-Bessel kernel of W cells,
+ *     C(t) = I0(beta sqrt(1 - (2t / W)^2)) / Z  for |t| < W/2, else 0,
+ * normalised to unit integral (Z = W sinh(beta) / beta), on a grid oversampled by alpha = 2 (grid side
+ * twice the image side), with beta = pi sqrt((W / alpha)^2 (alpha - 1/2)^2 - 0.8), the value Beatty,
+ * Nishimura and Pauly (IEEE TMI 2005) give for that oversampling.
+ */
+
+/* I0(x), the modified Bessel function of the first kind of order 0, from its power series
+ * sum_k ((x/2)^k / k!)^2 (all terms positive, summed until they stop changing the sum). */
+double oracle_i0(double x)
+{
+    double q = 0.25 * x * x, term = 1.0, sum = 1.0;
+    for (int k = 1; k < 1000; k++) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term <= 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+double oracle_kb_beta(int support)
+{
+    return 3.14159265358979323846 * sqrt(0.5625 * (double)support * (double)support - 0.8);
+}
+
+double oracle_kb(double t, int support, double beta)
+{
+    double h = 0.5 * (double)support;
+    if (!(fabs(t) < h)) return 0.0;
+    double r = t / h;
+    return oracle_i0(beta * sqrt(1.0 - r * r)) * beta / ((double)support * sinh(beta));
+}
+
+/* The kernel's Fourier transform c(nu) = integral C(t) exp(-2 pi i nu t) dt (nu in cycles per cell).  With
+ * a = pi W nu, the integral of I0(beta sqrt(1 - x^2)) cos(a x) over [-1, 1] is 2 sinh(r) / r for
+ * r = sqrt(beta^2 - a^2) (2 sin(r) / r with r = sqrt(a^2 - beta^2) beyond a = beta), so
+ * c(nu) = (sinh(r) / r) / (sinh(beta) / beta), c(0) = 1. */
+double oracle_kb_ft(double nu, int support, double beta)
+{
+    double a = 3.14159265358979323846 * (double)support * nu;
+    double d = beta * beta - a * a, s;
+    if (d > 0.0) {
+        double r = sqrt(d);
+        s = sinh(r) / r;
+    } else if (d < 0.0) {
+        double r = sqrt(-d);
+        s = sin(r) / r;
+    } else {
+        s = 1.0;
+    }
+    return s * beta / sinh(beta);
+}
+
+/* Spread value (re, im) at continuous cell position (gu, gv) over the cells (cu, cv) with |cu - gu| < W/2
+ * and |cv - gv| < W/2 with weights C(cu - gu) C(cv - gv); with `mirror` also (re, -im) at (-cu, -cv).
+ * Cell indices are taken modulo N. */
+static void orc_spread(double* G, int n, double gu, double gv, double re, double im, int mirror, int support,
+                       double beta)
+{
+    double h = 0.5 * (double)support;
+    for (int cv = (int)floor(gv - h); cv <= (int)ceil(gv + h); cv++) {
+        if (!(fabs((double)cv - gv) < h)) continue;
+        double wv = oracle_kb((double)cv - gv, support, beta);
+        for (int cu = (int)floor(gu - h); cu <= (int)ceil(gu + h); cu++) {
+            if (!(fabs((double)cu - gu) < h)) continue;
+            double w = oracle_kb((double)cu - gu, support, beta) * wv;
+            int u = ((cu % n) + n) % n, v = ((cv % n) + n) % n;
+            G[((int64_t)v * n + u) * 2 + 0] += w * re;
+            G[((int64_t)v * n + u) * 2 + 1] += w * im;
+            if (mirror) {
+                int um = ((-cu % n) + n) % n, vm = ((-cv % n) + n) % n;
+                G[((int64_t)vm * n + um) * 2 + 0] += w * re;
+                G[((int64_t)vm * n + um) * 2 + 1] -= w * im;
+            }
+        }
+    }
+}
+
+/*
+ * Convolutional gridding of one image onto a grid of side n_grid.  V: raw sums complex double [B][4][2]
+ * (integer sums, or calibrated ones), K the samples per visibility; the visibility of (i, j) is that of
+ * oracle_grid.  A cross visibility at g = (u / du, v / du) is kept iff its whole support lies within
+ * |c| <= n_grid/2 - 1 on both axes, i.e. |gu|, |gv| <= n_grid/2 - W/2; it and its mirror are spread with
+ * weight 2 in W.  Autocorrelations sit at g = 0 (no mirror, weight 1).  G: complex double
+ * [n_grid][n_grid], zeroed here.  Returns W.
+ */
+double oracle_grid_kb(const double* V, int n_tiles, const uint8_t* flags, int K, int pol, int autos,
+                      const double* uvw, double du, int support, int n_grid, double* G)
+{
+    int n = n_grid;
+    double beta = oracle_kb_beta(support), lim = 0.5 * (double)n_grid - 0.5 * (double)support;
+    memset(G, 0, (size_t)n * n * 2 * sizeof(double));
+    double W = 0.0;
+    for (int i = 0; i < n_tiles; i++) {
+        for (int j = 0; j <= i; j++) {
+            if (flags && (flags[i] || flags[j])) continue;
+            int64_t b = (int64_t)i * (i + 1) / 2 + j;
+            const double* s = V + b * 8;
+            double re, im;
+            if (pol == ORC_POL_I) {
+                re = (s[0] + s[6]) / (2.0 * (double)K);
+                im = (s[1] + s[7]) / (2.0 * (double)K);
+            } else {
+                re = s[0] / (double)K;
+                im = s[1] / (double)K;
+            }
+            if (i == j) {
+                if (!autos) continue;
+                orc_spread(G, n, 0.0, 0.0, re, im, 0, support, beta);
+                W += 1.0;
+                continue;
+            }
+            double gu = uvw[b * 3 + 0] / du, gv = uvw[b * 3 + 1] / du;
+            if (!(fabs(gu) <= lim && fabs(gv) <= lim)) continue;
+            orc_spread(G, n, gu, gv, re, im, 1, support, beta);
+            W += 2.0;
+        }
+    }
+    return W;
+}
+
+/* The N x N image from the shifted image `full` of the 2N grid: its central half (full pixel (x + N/2,
+ * y + N/2)), divided by c((x - N/2) / 2N) c((y - N/2) / 2N) to undo the kernel's taper (grid correction;
+ * |nu| <= 1/4 cycle per cell). */
+void oracle_kb_crop_correct(const double* full, int n, int support, double* img)
+{
+    double beta = oracle_kb_beta(support);
+    for (int y = 0; y < n; y++) {
+        double cy = oracle_kb_ft((double)(y - n / 2) / (double)(2 * n), support, beta);
+        for (int x = 0; x < n; x++) {
+            double cx = oracle_kb_ft((double)(x - n / 2) / (double)(2 * n), support, beta);
+            img[(int64_t)y * n + x] = full[(int64_t)(y + n / 2) * 2 * n + (x + n / 2)] / (cx * cy);
+        }
+    }
+}
+
 /* In-place unnormalised inverse DFT of n (a power of two) complex values spaced `stride` complex elements
  * apart: X[k] <- sum_m X[m] exp(+2 pi i k m / n).  Iterative radix-2 Cooley-Tukey: bit-reversal
  * permutation, then log2(n) butterfly stages; twiddles from libm cos/sin. */
@@ -376,6 +523,9 @@ double oracle_image(const double* a, int n, double W, double* img)
  * The whole path for a list of images of one set (one flag vector, one image side): for each image id
  * (= tau * F + f) correlate, compute uvw and cells at the output channel's frequency, grid, transform and
  * form the image.  cell_lambda <= 0 selects the default cell over the set's highest output frequency.
+ * support >= 2 (at most 16) grids with the Kaiser-Bessel kernel of that many cells on a grid of side 2N
+ * (oracle_grid_kb; `grids` then holds [n_ids][2N][2N][2]) and keeps the corrected central N x N image
+ * (oracle_kb_crop_correct); 0 or 1 grids to the nearest cell.
  * gains (or NULL): complex double [F][n_tiles][2 pol][2], applied to the sums before gridding; with
  * full_jones, complex double [F][n_tiles][2][2][2] full Jones matrices instead.
  * Optional outputs (NULL to skip): grids [n_ids][N][N][2], images [n_ids][N][N], W [n_ids],
@@ -384,17 +534,20 @@ double oracle_image(const double* a, int n, double W, double* img)
  */
 int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n_fine, int c, int ns,
                     const double* enu, const double* fine_freq, const uint8_t* flags,
-                    int n_pix, double cell_lambda, int pol, int autos, const double* gains, int full_jones,
+                    int n_pix, double cell_lambda, int pol, int autos, int support, const double* gains,
+                    int full_jones,
                     const int64_t* ids, int64_t n_ids, int n_threads,
                     double* grids, double* imgs, double* W_out, double* maxim_out)
 {
     if (n_pix <= 2 || (n_pix & (n_pix - 1)) || c <= 0 || ns <= 0 || n_fine % c) return -1;
+    if (support >= 2 && (support > 16 || (double)(n_pix - 1) - 0.5 * (double)support <= 0.0)) return -1;
+    int ng = support >= 2 ? 2 * n_pix : n_pix;      /* grid side */
     int F = n_fine / c;
     double* fout = (double*)malloc(sizeof(double) * F);
     oracle_output_freqs(fine_freq, n_fine, c, fout);
     double numax = fout[0];
     for (int f = 1; f < F; f++) if (fout[f] > numax) numax = fout[f];
-    double du = cell_lambda > 0.0 ? cell_lambda : oracle_default_cell(enu, n_tiles, flags, numax, n_pix);
+    double du = cell_lambda > 0.0 ? cell_lambda : oracle_default_cell(enu, n_tiles, flags, numax, n_pix, support);
     int64_t B = oracle_n_baselines(n_tiles);
     int K = ns * c;
     int bad = 0;
@@ -406,13 +559,23 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
         int32_t* iu = (int32_t*)malloc(sizeof(int32_t) * B);
         int32_t* iv = (int32_t*)malloc(sizeof(int32_t) * B);
         uint8_t* keep = (uint8_t*)malloc(B);
-        double* G = (double*)malloc(sizeof(double) * 2 * n_pix * n_pix);
-        double* im = (double*)malloc(sizeof(double) * n_pix * n_pix);
+        double* G = (double*)malloc(sizeof(double) * 2 * ng * ng);
+        double* im = (double*)malloc(sizeof(double) * ng * ng);
         oracle_correlate_one(volt, fine_stride, n_tiles, ns, c, tau, f, flags, S);
         oracle_uvw(enu, n_tiles, fout[f], uvw);
         oracle_cells(uvw, B, du, n_pix, iu, iv, keep);
         double W;
-        if (gains) {
+        if (support >= 2) {
+            double* V = (double*)malloc(sizeof(double) * B * 8);
+            if (gains && full_jones)
+                oracle_apply_jones(S, n_tiles, gains + (int64_t)f * n_tiles * 8, V);
+            else if (gains)
+                oracle_apply_gains(S, n_tiles, gains + (int64_t)f * n_tiles * 4, V);
+            else
+                for (int64_t e = 0; e < B * 8; e++) V[e] = (double)S[e];
+            W = oracle_grid_kb(V, n_tiles, flags, K, pol, autos, uvw, du, support, ng, G);
+            free(V);
+        } else if (gains) {
             double* V = (double*)malloc(sizeof(double) * B * 8);
             if (full_jones)
                 oracle_apply_jones(S, n_tiles, gains + (int64_t)f * n_tiles * 8, V);
@@ -423,10 +586,13 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
         } else {
             W = oracle_grid(S, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
         }
-        if (grids) memcpy(grids + q * 2 * n_pix * n_pix, G, sizeof(double) * 2 * n_pix * n_pix);
-        if (oracle_ifft2(G, n_pix)) bad = 1;
-        double mx = oracle_image(G, n_pix, W > 0.0 ? W : 1.0, im);
-        if (imgs) memcpy(imgs + q * n_pix * n_pix, im, sizeof(double) * n_pix * n_pix);
+        if (grids) memcpy(grids + q * 2 * ng * ng, G, sizeof(double) * 2 * ng * ng);
+        if (oracle_ifft2(G, ng)) bad = 1;
+        double mx = oracle_image(G, ng, W > 0.0 ? W : 1.0, im);
+        if (imgs && support >= 2)
+            oracle_kb_crop_correct(im, n_pix, support, imgs + q * n_pix * n_pix);
+        else if (imgs)
+            memcpy(imgs + q * n_pix * n_pix, im, sizeof(double) * n_pix * n_pix);
         if (W_out) W_out[q] = W;
         if (maxim_out) maxim_out[q] = mx;
         free(S); free(uvw); free(iu); free(iv); free(keep); free(G); free(im);
