@@ -102,6 +102,15 @@ typedef struct {
     int32_t pol;                /* BLINK_POL_I: (XX + YY) / 2; BLINK_POL_XX: XX only */
     int32_t include_autos;      /* non-zero: autocorrelations gridded at (0, 0) with weight 1 */
     int32_t precision;          /* BLINK_PREC_FP32, or BLINK_PREC_BF16 (bf16 grid/intermediate storage) */
+    int32_t support;            /* gridding kernel (Sec. 5.2.4): 0 or 1 = nearest cell; W in [2, 16] = separable
+                                   Kaiser-Bessel kernel of W cells, beta = pi sqrt((W/2)^2 (3/2)^2 - 0.8),
+                                   on a grid of side 2 n_pix (n_pix <= 1024): every visibility is spread
+                                   over the cells within W/2 of its exact (u, v) / du and kept only if that
+                                   support lies inside the grid; the image is the central n_pix x n_pix of
+                                   the transform divided by the kernel's Fourier transform along both axes.
+                                   The default cell is then u_max / (n_pix - 1 - W/2).  Batched pipeline
+                                   forms only (blink_pipeline BATCHED, blink_pipeline_sets,
+                                   blink_pipeline_host); the stage calls return BLINK_ERR_UNSUPPORTED. */
 } blink_imaging;
 
 /*

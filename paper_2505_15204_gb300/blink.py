@@ -64,7 +64,7 @@ class blink_obs(C.Structure):
 
 class blink_imaging(C.Structure):
     _fields_ = [("n_pix", C.c_int32), ("cell_lambda", C.c_double), ("pol", C.c_int32),
-                ("include_autos", C.c_int32), ("precision", C.c_int32)]
+                ("include_autos", C.c_int32), ("precision", C.c_int32), ("support", C.c_int32)]
 
 
 class blink_set(C.Structure):
@@ -178,9 +178,11 @@ class Imaging:
     pol: int = BLINK_POL_I
     include_autos: int = 1
     precision: int = BLINK_PREC_FP32
+    support: int = 0                     # 0: nearest cell; W >= 2: Kaiser-Bessel kernel of W cells
 
     def c(self):
-        return blink_imaging(self.n_pix, self.cell_lambda, self.pol, self.include_autos, self.precision)
+        return blink_imaging(self.n_pix, self.cell_lambda, self.pol, self.include_autos, self.precision,
+                             self.support)
 
 
 def _ref(x):

@@ -84,6 +84,18 @@ blink_status check_imaging(const blink_imaging* im) {
     if (im->precision != BLINK_PREC_FP32 && im->precision != BLINK_PREC_BF16)
         return set_error(BLINK_ERR_INVALID_ARG, "imaging.precision must be BLINK_PREC_FP32 or BLINK_PREC_BF16");
     if (!std::isfinite(im->cell_lambda)) return set_error(BLINK_ERR_INVALID_ARG, "imaging.cell_lambda is not finite");
+    if (im->support < 0 || im->support > 16)
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.support must be 0 or 1 (nearest cell) or a kernel width in [2, 16]");
+    if (im->support >= 2 && n > 1024)
+        return set_error(BLINK_ERR_UNSUPPORTED, "with a convolution kernel imaging.n_pix is at most 1024 (grid side 2 n_pix)");
+    return BLINK_OK;
+}
+
+// The entry points that grid to the nearest cell only (stage calls and the plain per-image form).
+blink_status nearest_only(const blink_imaging* im, const char* what) {
+    if (im && im->support >= 2)
+        return set_error(BLINK_ERR_UNSUPPORTED, std::string(what) + ": gridding with a convolution kernel runs in the "
+                                                "batched pipeline forms only");
     return BLINK_OK;
 }
 
@@ -116,6 +128,8 @@ void free_plan(Plan* p) {
     cudaFree(p->d_W);
     cudaFree(p->d_Wk);
     cudaFree(p->d_tw);
+    cudaFree(p->d_wt);
+    cudaFree(p->d_corr);
     delete p;
 }
 
@@ -131,8 +145,9 @@ std::vector<double> output_freqs(const blink_obs* o) {
     return out;
 }
 
-// Default uv cell: u_max / (N/2 - 1), u_max = longest unflagged projected baseline * nu_max / c.
-double default_cell(const blink_array* a, double nu_max, int n_pix) {
+// Default uv cell: u_max / (N/2 - 1), u_max = longest unflagged projected baseline * nu_max / c, for a grid of
+// side N; with a kernel of W cells the support must stay inside the grid too: u_max / (N/2 - 1 - W/2).
+double default_cell(const blink_array* a, double nu_max, int n_pix, int support) {
     double dmax = 0.0;
     for (int i = 0; i < a->n_tiles; i++)
         for (int j = 0; j < i; j++) {
@@ -144,36 +159,97 @@ double default_cell(const blink_array* a, double nu_max, int n_pix) {
         }
     const double umax = dmax * (nu_max / kSpeedOfLight);
     if (!(umax > 0.0)) return 1.0;
+    if (support >= 2) return umax / ((double)(n_pix / 2 - 1) - 0.5 * (double)support);
     return umax / (double)(n_pix / 2 - 1);
 }
 
 // Cell-sorted gather list of the u >= 0 half plane for every output channel: one entry per visibility (and
-// per mirror) that lands in the half plane, ordered by (u, v, baseline), with the offsets of every column
-// u so that a column, or a block of consecutive columns, is one contiguous range.
-blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std::vector<short2>& bl,
-                          const blink_array* a) {
-    const int N = p->N, half = N / 2;
-    const int64_t B = p->B;
-    const int64_t nkeys = (int64_t)half * N;                 // key = u * N + v
-    std::vector<int> count(nkeys + 1);
-    std::vector<int> ent_off((size_t)p->F * (half + 1));
+// per mirror) contribution that lands in the half plane, ordered by (u, v, baseline), with the offsets of
+// every column u so that a column, or a block of consecutive columns, is one contiguous range.  A channel's
+// contributions are collected as (key = u * N + v, (b << 1) | conj[, weight]) and appended by `add_channel`.
+struct GatherBuilder {
+    int N, half;
+    int64_t nkeys;
+    std::vector<int> count, ent_off;
     std::vector<uint2> ent;
+    std::vector<float> wt;
     std::vector<uint32_t> ekey, eval, sorted, skey;
-    ent.reserve((size_t)p->F * (B + B / 16));
-    p->W.assign(p->F, 0.f);
-    int64_t dropped = 0;
-    auto key_of = [&](int u, int v) -> uint32_t { return (uint32_t)((int64_t)u * N + v); };
-    for (int f = 0; f < p->F; f++) {
+    std::vector<float> ewt, swt;
+    GatherBuilder(int n, int F) : N(n), half(n / 2), nkeys((int64_t)(n / 2) * n), count(nkeys + 1),
+                                  ent_off((size_t)F * (n / 2 + 1)) {}
+    uint32_t key(int u, int v) const { return (uint32_t)((int64_t)u * N + v); }
+    void clear() {
         ekey.clear();
         eval.clear();
+        ewt.clear();
+    }
+    // stable counting sort by key: the entries of a cell stay in the order they were added
+    blink_status add_channel(int f, bool weighted) {
+        std::fill(count.begin(), count.end(), 0);
+        for (uint32_t k : ekey) count[k + 1]++;
+        for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
+        sorted.assign(ekey.size(), 0);
+        skey.assign(ekey.size(), 0);
+        if (weighted) swt.assign(ekey.size(), 0.f);
+        {
+            std::vector<int> cur(count.begin(), count.end() - 1);
+            for (size_t e = 0; e < ekey.size(); e++) {
+                const int at = cur[ekey[e]]++;
+                sorted[at] = eval[e];
+                skey[at] = ekey[e];
+                if (weighted) swt[at] = ewt[e];
+            }
+        }
+        const int64_t base = (int64_t)ent.size();
+        for (int u = 0; u <= half; u++)
+            ent_off[(size_t)f * (half + 1) + u] = (int)(base + count[std::min<int64_t>((int64_t)u * N, nkeys)]);
+        for (size_t e = 0; e < sorted.size(); e++) {
+            const uint32_t u = skey[e] / N, v = skey[e] % N;
+            ent.push_back(make_uint2(u | (v << 11) | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
+        }
+        if (weighted) wt.insert(wt.end(), swt.begin(), swt.end());
+        if ((int64_t)ent.size() > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
+        return BLINK_OK;
+    }
+    blink_status upload(Plan* p, bool weighted) {
+        p->n_contrib = (int64_t)ent.size();
+        p->n_cells = p->n_contrib;
+        BLINK_TRY(dmalloc(&p->d_ent_off, ent_off.size()));
+        BLINK_TRY(dmalloc(&p->d_ent, ent.size()));
+        BLINK_CUDA(cudaMemcpy(p->d_ent_off, ent_off.data(), ent_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (!ent.empty())
+            BLINK_CUDA(cudaMemcpy(p->d_ent, ent.data(), ent.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+        if (weighted) {
+            BLINK_TRY(dmalloc(&p->d_wt, wt.size()));
+            if (!wt.empty())
+                BLINK_CUDA(cudaMemcpy(p->d_wt, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+        return BLINK_OK;
+    }
+};
+
+// Nearest-cell gather list: every kept visibility in its cell, its mirror in the mirrored cell.
+blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std::vector<short2>& bl,
+                          const blink_array* a) {
+    const int N = p->N;
+    const int64_t B = p->B;
+    GatherBuilder g(N, p->F);
+    g.ent.reserve((size_t)p->F * (B + B / 16));
+    p->W.assign(p->F, 0.f);
+    int64_t dropped = 0;
+    for (int f = 0; f < p->F; f++) {
+        g.clear();
         int64_t w = 0;
+        auto add = [&](int u, int v, int64_t b, uint32_t conj) {
+            g.ekey.push_back(g.key(u, v));
+            g.eval.push_back((uint32_t)(b << 1) | conj);
+        };
         for (int64_t b = 0; b < B; b++) {
             const uint32_t c = cells[(size_t)f * B + b];
             const int i = bl[b].x, j = bl[b].y;
             if (i == j) {
                 if (c == CELL_NONE || !p->autos) continue;
-                ekey.push_back(key_of(0, 0));
-                eval.push_back((uint32_t)(b << 1));
+                add(0, 0, b, 0);
                 w += 1;
                 continue;
             }
@@ -184,51 +260,119 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
             const int iu = (int16_t)(c & 0xFFFF), iv = (int16_t)(c >> 16);
             const int vpos = ((iv % N) + N) % N, vneg = ((-iv % N) + N) % N;
             if (iu > 0) {
-                ekey.push_back(key_of(iu, vpos));
-                eval.push_back((uint32_t)(b << 1));
+                add(iu, vpos, b, 0);
             } else if (iu < 0) {
-                ekey.push_back(key_of(-iu, vneg));
-                eval.push_back((uint32_t)((b << 1) | 1));
+                add(-iu, vneg, b, 1);
             } else {
-                ekey.push_back(key_of(0, vpos));
-                eval.push_back((uint32_t)(b << 1));
-                ekey.push_back(key_of(0, vneg));
-                eval.push_back((uint32_t)((b << 1) | 1));
+                add(0, vpos, b, 0);
+                add(0, vneg, b, 1);
             }
             w += 2;
         }
         p->W[f] = (float)w;
-        // stable counting sort by key: the entries of a cell stay in baseline order
-        std::fill(count.begin(), count.end(), 0);
-        for (uint32_t k : ekey) count[k + 1]++;
-        for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
-        sorted.assign(ekey.size(), 0);
-        skey.assign(ekey.size(), 0);
-        {
-            std::vector<int> cur(count.begin(), count.end() - 1);
-            for (size_t e = 0; e < ekey.size(); e++) {
-                const int at = cur[ekey[e]]++;
-                sorted[at] = eval[e];
-                skey[at] = ekey[e];
-            }
-        }
-        const int64_t base = (int64_t)ent.size();
-        for (int u = 0; u <= half; u++)
-            ent_off[(size_t)f * (half + 1) + u] = (int)(base + count[std::min<int64_t>((int64_t)u * N, nkeys)]);
-        for (size_t e = 0; e < sorted.size(); e++) {
-            const uint32_t u = skey[e] / N, v = skey[e] % N;
-            ent.push_back(make_uint2(u | (v << 11) | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
-        }
-        if ((int64_t)ent.size() > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
+        BLINK_TRY(g.add_channel(f, false));
     }
-    p->n_contrib = (int64_t)ent.size();
-    p->n_cells = p->n_contrib;
     p->n_dropped = dropped;
-    BLINK_TRY(dmalloc(&p->d_ent_off, ent_off.size()));
-    BLINK_TRY(dmalloc(&p->d_ent, ent.size()));
-    BLINK_CUDA(cudaMemcpy(p->d_ent_off, ent_off.data(), ent_off.size() * sizeof(int), cudaMemcpyHostToDevice));
-    if (!ent.empty()) BLINK_CUDA(cudaMemcpy(p->d_ent, ent.data(), ent.size() * sizeof(uint2), cudaMemcpyHostToDevice));
-    return BLINK_OK;
+    return g.upload(p, false);
+}
+
+// ---- gridding with a convolution kernel ----------------------------------------------------------
+// Separable Kaiser-Bessel kernel of W cells on a grid twice the image side (oversampling 2):
+// C(t) = I0(beta sqrt(1 - (2t/W)^2)) beta / (W sinh beta) for |t| < W/2 (unit integral), with
+// beta = pi sqrt((W/2)^2 (3/2)^2 - 0.8) (Beatty, Nishimura and Pauly, IEEE TMI 2005, for oversampling 2).
+constexpr double kPi = 3.14159265358979323846;
+
+double kb_beta(int W) { return kPi * std::sqrt(0.5625 * W * W - 0.8); }
+
+double kb_weight(double t, int W, double beta) {
+    const double h = 0.5 * W;
+    if (!(std::fabs(t) < h)) return 0.0;
+    const double r = t / h;
+    return std::cyl_bessel_i(0.0, beta * std::sqrt(1.0 - r * r)) * beta / (W * std::sinh(beta));
+}
+
+// Its Fourier transform at nu cycles per cell (1 at nu = 0): with a = pi W nu and r = sqrt(|beta^2 - a^2|),
+// (sinh r / r) / (sinh beta / beta) below a = beta and (sin r / r) / (sinh beta / beta) above.
+double kb_transform(double nu, int W, double beta) {
+    const double a = kPi * W * nu, d = beta * beta - a * a;
+    const double r = std::sqrt(std::fabs(d));
+    const double s = r == 0.0 ? 1.0 : (d > 0.0 ? std::sinh(r) / r : std::sin(r) / r);
+    return s * beta / std::sinh(beta);
+}
+
+// Kernel gather list: a cross visibility at g = (u, v) / du is kept iff its support lies inside the grid
+// (|gu|, |gv| <= N/2 - W/2); each support cell c (|c - g| < W/2 on both axes) gets weight C(cu - gu) C(cv - gv):
+// the visibility's contribution at c lands in the half plane when cu > 0, its mirror's (conjugate, at -c)
+// when cu < 0, both when cu = 0.  Autocorrelations sit at g = 0 without mirror; their cells with cu >= 0
+// stand for the whole (real, symmetric) spread.  uvw: host [F][B][3] from the geometry kernel.
+blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std::vector<short2>& bl,
+                             const blink_array* a) {
+    const int N = p->N, W = p->support;
+    const int64_t B = p->B;
+    const double beta = kb_beta(W), h = 0.5 * W, lim = 0.5 * N - h;
+    GatherBuilder g(N, p->F);
+    p->W.assign(p->F, 0.f);
+    int64_t dropped = 0;
+    std::vector<int> cu_list, cv_list;
+    std::vector<double> wu_list, wv_list;
+    auto support_cells = [&](double gx, std::vector<int>& cs, std::vector<double>& ws) {
+        cs.clear();
+        ws.clear();
+        for (int c = (int)std::floor(gx - h); c <= (int)std::ceil(gx + h); c++)
+            if (std::fabs((double)c - gx) < h) {
+                cs.push_back(c);
+                ws.push_back(kb_weight((double)c - gx, W, beta));
+            }
+    };
+    for (int f = 0; f < p->F; f++) {
+        g.clear();
+        int64_t w = 0;
+        auto add = [&](int u, int v, int64_t b, uint32_t conj, double wt) {
+            g.ekey.push_back(g.key(u, ((v % N) + N) % N));
+            g.eval.push_back((uint32_t)(b << 1) | conj);
+            g.ewt.push_back((float)wt);
+        };
+        for (int64_t b = 0; b < B; b++) {
+            const int i = bl[b].x, j = bl[b].y;
+            if (a->flags && (a->flags[i] || a->flags[j])) continue;
+            if (i == j) {
+                if (!p->autos) continue;
+                support_cells(0.0, cu_list, wu_list);
+                for (size_t q = 0; q < cu_list.size(); q++)
+                    for (size_t r = 0; r < cu_list.size(); r++)
+                        if (cu_list[r] >= 0) add(cu_list[r], cu_list[q], b, 0, wu_list[r] * wu_list[q]);
+                w += 1;
+                continue;
+            }
+            const double gu = uvw[((size_t)f * B + b) * 3 + 0] / p->du, gv = uvw[((size_t)f * B + b) * 3 + 1] / p->du;
+            if (!(std::fabs(gu) <= lim && std::fabs(gv) <= lim)) {
+                dropped++;
+                continue;
+            }
+            support_cells(gu, cu_list, wu_list);
+            support_cells(gv, cv_list, wv_list);
+            for (size_t q = 0; q < cv_list.size(); q++)
+                for (size_t r = 0; r < cu_list.size(); r++) {
+                    const int cu = cu_list[r], cv = cv_list[q];
+                    const double wgt = wu_list[r] * wv_list[q];
+                    if (cu >= 0) add(cu, cv, b, 0, wgt);
+                    if (cu <= 0) add(-cu, -cv, b, 1, wgt);
+                }
+            w += 2;
+        }
+        p->W[f] = (float)w;
+        BLINK_TRY(g.add_channel(f, true));
+    }
+    p->n_dropped = dropped;
+    return g.upload(p, true);
+}
+
+// Grid correction of an image of side Ni from a grid of side 2 Ni: 1 / c((x - Ni/2) / (2 Ni)) per pixel index.
+std::vector<float> kb_correction(int Ni, int W) {
+    const double beta = kb_beta(W);
+    std::vector<float> c(Ni);
+    for (int x = 0; x < Ni; x++) c[x] = (float)(1.0 / kb_transform((double)(x - Ni / 2) / (2.0 * Ni), W, beta));
+    return c;
 }
 
 }  // namespace
@@ -333,6 +477,7 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         h.val(im->cell_lambda);
         h.val(im->pol);
         h.val(im->include_autos != 0);
+        h.val(im->support >= 2 ? im->support : 0);
         h.val(need_gather);
     } else {
         h.val(o->n_fine / o->chan_avg);
@@ -376,7 +521,9 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
     if (e == cudaSuccess) e = cudaMemcpy(p->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(plan)"));
     if (im) {
-        p->N = im->n_pix;
+        p->support = im->support >= 2 ? im->support : 0;
+        p->Ni = im->n_pix;
+        p->N = p->support ? 2 * im->n_pix : im->n_pix;     // with a kernel the grid is oversampled by 2
         p->pol = im->pol;
         p->autos = im->include_autos ? 1 : 0;
         p->cw = col_block_width(p->N);
@@ -384,7 +531,7 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         p->out_freq = output_freqs(o);
         double numax = p->out_freq[0];
         for (double f : p->out_freq) numax = std::max(numax, f);
-        p->du = im->cell_lambda > 0.0 ? im->cell_lambda : default_cell(a, numax, p->N);
+        p->du = im->cell_lambda > 0.0 ? im->cell_lambda : default_cell(a, numax, p->N, p->support);
         if ((s = dmalloc(&p->d_enu, 3 * a->n_tiles)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_freq, p->F)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_cells, (size_t)p->F * p->B)) != BLINK_OK) return fail(s);
@@ -395,15 +542,32 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         if (e == cudaSuccess) e = cudaMemcpy(p->d_freq, p->out_freq.data(), sizeof(double) * p->F, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(plan)"));
         if ((s = make_twiddles(p->d_tw, p->N, st)) != BLINK_OK) return fail(s);
+        // with a kernel the gather list is built from the exact (u, v), kept on the device only meanwhile
+        const bool kb = p->support && need_gather;
+        if (kb && (s = dmalloc(&p->d_uvw, (size_t)p->F * p->B * 3)) != BLINK_OK) return fail(s);
         launch_cells(*p, st);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail(cuda_error(e, "geometry kernel"));
+        if (kb) {
+            std::vector<double> uvw((size_t)p->F * p->B * 3);
+            e = cudaMemcpy(uvw.data(), p->d_uvw, uvw.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            cudaFree(p->d_uvw);
+            p->d_uvw = nullptr;
+            if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(uvw)"));
+            if ((s = build_gather_kb(p, uvw, bl, a)) != BLINK_OK) return fail(s);
+            const std::vector<float> corr = kb_correction(p->Ni, p->support);
+            if ((s = dmalloc(&p->d_corr, corr.size())) != BLINK_OK) return fail(s);
+            e = cudaMemcpy(p->d_corr, corr.data(), corr.size() * sizeof(float), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(correction)"));
+        }
         if (need_gather) {
-            std::vector<uint32_t> cells((size_t)p->F * p->B);
-            e = cudaMemcpy(cells.data(), p->d_cells, cells.size() * 4, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(cells)"));
-            if ((s = build_gather(p, cells, bl, a)) != BLINK_OK) return fail(s);
+            if (!kb) {
+                std::vector<uint32_t> cells((size_t)p->F * p->B);
+                e = cudaMemcpy(cells.data(), p->d_cells, cells.size() * 4, cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(cells)"));
+                if ((s = build_gather(p, cells, bl, a)) != BLINK_OK) return fail(s);
+            }
             // the imaging path grids raw correlation sums: scale by 1 / (W * 2K) (Stokes I) or 1 / (W * K)
             const double div = (p->pol == BLINK_POL_I ? 2.0 : 1.0) * o->samples_per_int * o->chan_avg;
             std::vector<float> wk(p->F);
@@ -658,6 +822,7 @@ blink_status blink_cells(blink_context* ctx, const blink_array* array, const bli
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, true));
     BLINK_TRY(check_imaging(imaging));
+    BLINK_TRY(nearest_only(imaging, "blink_cells"));
     if (!d_cells) return set_error(BLINK_ERR_INVALID_ARG, "d_cells is NULL");
     BLINK_TRY(make_current(ctx));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -704,6 +869,7 @@ blink_status blink_grid(blink_context* ctx, const blink_array* array, const blin
     BLINK_TRY(check_array(array));
     BLINK_TRY(check_obs(obs, true));
     BLINK_TRY(check_imaging(imaging));
+    BLINK_TRY(nearest_only(imaging, "blink_grid"));
     if (!d_vis || !d_grid) return set_error(BLINK_ERR_INVALID_ARG, "d_vis or d_grid is NULL");
     if (first_image < 0 || n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "negative image range");
     if (((uintptr_t)d_vis & 7) || ((uintptr_t)d_grid & 7))
@@ -727,6 +893,7 @@ blink_status blink_grid(blink_context* ctx, const blink_array* array, const blin
 blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const float* d_grid, int32_t n_images,
                          const float* d_weight, float* d_img, void* stream) {
     BLINK_TRY(check_imaging(imaging));
+    BLINK_TRY(nearest_only(imaging, "blink_image"));
     if (!d_grid || !d_weight || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_grid, d_weight or d_img is NULL");
     if (n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "n_images < 0");
     if (((uintptr_t)d_grid & 7) || ((uintptr_t)d_img & 7))
@@ -764,6 +931,7 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
         return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
     if (mode != BLINK_MODE_BATCHED && mode != BLINK_MODE_PLAIN)
         return set_error(BLINK_ERR_INVALID_ARG, "mode must be BLINK_MODE_BATCHED or BLINK_MODE_PLAIN");
+    if (mode == BLINK_MODE_PLAIN) BLINK_TRY(nearest_only(imaging, "blink_pipeline (plain form)"));
     if (!d_volt || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_volt or d_img is NULL");
     if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_img & 7))
         return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_img 8-byte aligned");
@@ -857,7 +1025,7 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
         if (T > 0)
             BLINK_TRY(run_batched(ctx, *p, &o, st.imaging.precision, arith, d_volt + (int64_t)st.fine0 * a.n_tiles * 2,
                                   ss, 0, T, d_img + at, strm, true, g));
-        at += (size_t)T * p->F * p->N * p->N;
+        at += (size_t)T * p->F * p->Ni * p->Ni;
     }
     return BLINK_OK;
 }
@@ -907,7 +1075,7 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
     BLINK_TRY(upload_gains(ctx, array, p->F, st, &g));
     // output the device can write: the imaging kernel writes the images straight into h_img, so the transfer
     // over the host link overlaps the computation instead of following it
-    float* direct = images_per_pass == 0 ? device_view(h_img, (size_t)n_img * p->N * p->N * sizeof(float)) : nullptr;
+    float* direct = images_per_pass == 0 ? device_view(h_img, (size_t)n_img * p->Ni * p->Ni * sizeof(float)) : nullptr;
     if (direct) {
         void* dv = nullptr;
         BLINK_TRY(workspace(ctx, 2, vbytes, &dv));
@@ -917,7 +1085,7 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
     }
     // passes of whole integrations (F images each), at least one integration per pass
     const int t_per = images_per_pass > 0 ? std::max(1, std::min(T, images_per_pass / p->F)) : T;
-    const int N = p->N;
+    const int N = p->Ni;                                // image side
     void* dv = nullptr;
     void* di = nullptr;
     BLINK_TRY(workspace(ctx, 2, vbytes, &dv));

@@ -50,6 +50,8 @@ struct Plan {
     mutable bool tuned = false;
     mutable float tune_ms = 0.f;           // time of the chosen shape on the tuning call
     int n_tiles = 0, n_fine = 0, chan_avg = 1, F = 0, N = 0, pol = 0, autos = 1;
+    int support = 0;                       // convolution kernel width in cells (0: nearest cell)
+    int Ni = 0;                            // image side: N, or N / 2 with a kernel (grid side N = 2 Ni)
     int64_t B = 0;
     int cw = 16, n_cb = 0;                 // column-block width and count of the u >= 0 half plane
     double du = 0.0;
@@ -64,6 +66,8 @@ struct Plan {
     uint32_t* d_cells = nullptr;           // [F][B]
     int* d_ent_off = nullptr;              // [F][N/2 + 1]: first gather entry of each column u
     uint2* d_ent = nullptr;                // [n_contrib] {u | v << 11 | conj << 31, b}, sorted by (u, v, b)
+    float* d_wt = nullptr;                 // [n_contrib] kernel weight of each entry (convolution only)
+    float* d_corr = nullptr;               // [Ni] grid correction 1 / c(nu) per image pixel index (convolution only)
     float* d_W = nullptr;                  // [F] W, the sum of weights
     float* d_Wk = nullptr;                 // [F] W times the divisor of the correlator's raw sums (2K or K)
     float2* d_tw = nullptr;                // twiddle set of side N (tws_total(N) entries)
@@ -471,10 +475,11 @@ __device__ __forceinline__ int ent_v(uint32_t x) { return (int)((x >> 11) & 0xFF
 __device__ __forceinline__ uint32_t ent_cell(uint32_t x) { return x & 0x7FFFFFFFu; }
 
 // Gather entry i of a column whose entries end at `end`: its cell key and visibility (conjugated for an
-// entry of the mirrored half plane); key 0xFFFFFFFF and zero past the end.
+// entry of the mirrored half plane), times the entry's weight wt[i] when `wt` is given (a convolution
+// kernel's weight); key 0xFFFFFFFF and zero past the end.
 template <typename Val>
-__device__ __forceinline__ void gather_entry(const uint2* __restrict__ ent, int i, int end, Val val, uint32_t& key,
-                                             float2& x) {
+__device__ __forceinline__ void gather_entry(const uint2* __restrict__ ent, const float* __restrict__ wt, int i,
+                                             int end, Val val, uint32_t& key, float2& x) {
     key = 0xFFFFFFFFu;
     x = make_float2(0.f, 0.f);
     if (i < end) {
@@ -482,6 +487,10 @@ __device__ __forceinline__ void gather_entry(const uint2* __restrict__ ent, int 
         key = ent_cell(e.x);
         x = val(e.y);
         if (e.x >> 31) x.y = -x.y;
+        if (wt) {
+            const float w = wt[i];
+            x = make_float2(x.x * w, x.y * w);
+        }
     }
 }
 
@@ -492,16 +501,17 @@ __device__ __forceinline__ void gather_entry(const uint2* __restrict__ ent, int 
 // contributions (the autocorrelations at (0, 0)) therefore costs a few chunks, not a serial chain, and
 // the order of additions is fixed, so results are reproducible.  `val(b)` is baseline b's visibility;
 // with `shift` every cell is multiplied by (-1)^(u+v) (the image shift by N/2).
-// (key, x) is lane's entry of the first chunk (gather_entry(ent, beg + lane, ...)), loaded by the caller so
+// (key, x) is lane's entry of the first chunk (gather_entry(ent, wt, beg + lane, ...)), loaded by the caller so
 // that its latency overlaps the caller's own work; each later chunk is loaded while the previous is summed.
 template <typename T, typename Val, typename Idx>
-__device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
-                                                   Val val, Idx idx, bool shift, uint32_t key, float2 x) {
+__device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent, const float* __restrict__ wt, int beg,
+                                                   int end, int lane, T* s, Val val, Idx idx, bool shift, uint32_t key,
+                                                   float2 x) {
     for (int base = beg; base < end; base += 32) {
         const int i = base + lane;
         uint32_t nkey;
         float2 nx;
-        gather_entry(ent, i + 32, end, val, nkey, nx);
+        gather_entry(ent, wt, i + 32, end, val, nkey, nx);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t k2 = __shfl_up_sync(0xFFFFFFFFu, key, d);
@@ -528,15 +538,15 @@ __device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent
 // stored rather than added, and bit v / 32 of occ[v % 32] records that cell v holds data (occ zeroed by the
 // caller).  Only the first run of a chunk can continue a cell of the previous chunk, which it then adds to.
 template <typename T, typename Val, typename Idx>
-__device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__ ent, int beg, int end, int lane,
-                                                       T* s, Val val, Idx idx, uint32_t key, float2 x,
-                                                       uint32_t* occ) {
+__device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__ ent, const float* __restrict__ wt,
+                                                       int beg, int end, int lane, T* s, Val val, Idx idx,
+                                                       uint32_t key, float2 x, uint32_t* occ) {
     uint32_t prev = 0xFFFFFFFFu;                    // the last cell of the previous chunk
     for (int base = beg; base < end; base += 32) {
         const int i = base + lane;
         uint32_t nkey;
         float2 nx;
-        gather_entry(ent, i + 32, end, val, nkey, nx);
+        gather_entry(ent, wt, i + 32, end, val, nkey, nx);
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t k2 = __shfl_up_sync(0xFFFFFFFFu, key, d);
@@ -565,12 +575,12 @@ __device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__
 
 // The same, loading the first chunk itself.
 template <typename T, typename Val, typename Idx>
-__device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
-                                                   Val val, Idx idx, bool shift) {
+__device__ __forceinline__ void warp_gather_column(const uint2* __restrict__ ent, const float* __restrict__ wt, int beg,
+                                                   int end, int lane, T* s, Val val, Idx idx, bool shift) {
     uint32_t key;
     float2 x;
-    gather_entry(ent, beg + lane, end, val, key, x);
-    warp_gather_column(ent, beg, end, lane, s, val, idx, shift, key, x);
+    gather_entry(ent, wt, beg + lane, end, val, key, x);
+    warp_gather_column(ent, wt, beg, end, lane, s, val, idx, shift, key, x);
 }
 
 }  // namespace blink

@@ -43,6 +43,8 @@ struct FftParams {
     int n_cb, n_rb;          // column tasks and row tasks per image
     const int* ent_off;      // [F][N/2 + 1]
     const uint2* ent;        // gather entries
+    const float* wt;         // per-entry kernel weights (convolutional gridding), else NULL
+    const float* corr;       // [N / 2] grid correction per image pixel index (convolutional gridding), else NULL
     const float2* tw;        // twiddle set of side N
     void* H;                 // ring of column-pass results, [ring][N][ldh]
     int ldh, ring, lag;
@@ -180,7 +182,10 @@ __device__ __forceinline__ void warp_fft512(T* s, const float2* tw32, int lane, 
 }
 
 // The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
-template <int N, typename T>
+// With WT (gridding with a convolution kernel) every gather entry carries a weight, the grid side N is twice
+// the image side, and the row tasks transform only the central N/2 rows and keep their central N/2 pixels,
+// multiplied by the grid correction.
+template <int N, typename T, bool WT>
 __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
                             uint32_t* s_occ, int* s_flag) {
     constexpr int CW = kCW, LD = tile_ld<N>();
@@ -205,15 +210,16 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     auto idx = [&](int, int v) { return warp * LD + padx(v); };
     const int* off = P.ent_off + f * (N / 2 + 1);
     const int beg = off[u], end = off[u + 1];
+    const float* wt = WT ? P.wt : nullptr;
     uint32_t key;
     float2 x;
-    gather_entry(P.ent, beg + lane, end, val, key, x);    // in flight while the column is prepared
+    gather_entry(P.ent, wt, beg + lane, end, val, key, x);    // in flight while the column is prepared
     if constexpr (N >= 256 && N <= 1024) {
         // no zeroing: the gridding marks the cells it writes, and the first pass reads only those
         uint32_t* occ = s_occ + warp * 32;
         occ[lane] = 0u;
         __syncwarp();
-        warp_gather_column_occ(P.ent, beg, end, lane, s, val, idx, key, x, occ);
+        warp_gather_column_occ(P.ent, wt, beg, end, lane, s, val, idx, key, x, occ);
         __syncwarp();
         if constexpr (N == 512)
             warp_fft512(col, s_twc, lane, occ[lane]);
@@ -222,7 +228,7 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     } else {
         for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
         __syncwarp();
-        warp_gather_column(P.ent, beg, end, lane, s, val, idx, true, key, x);
+        warp_gather_column(P.ent, wt, beg, end, lane, s, val, idx, true, key, x);
         __syncwarp();
         NoOut none;
         warp_fft<N, false, T, NoOut>(col, s_twc, lane, none);
@@ -237,10 +243,13 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     return P.col_done + k;
 }
 
-template <int N, typename T>
+template <int N, typename T, bool WT>
 __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre, const float2* s_twr,
                          unsigned char* work, int* s_flag) {
     constexpr int M = N / 2, LS = tile_ld<M>();
+    constexpr int NI = WT ? N / 2 : N;                  // image side
+    constexpr int Y0 = WT ? N / 4 : 0;                  // grid row of image row 0
+    constexpr int X0 = WT ? N / 8 : 0;                  // first output pair m kept (grid pixels 2m, 2m + 1)
     const int tid = threadIdx.x, r = tid >> 5, lane = tid & 31;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
@@ -249,7 +258,7 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     const float inv = 1.0f / (w > 0.f ? w : 1.f);
 #pragma unroll 1
     for (int b = 0; b < kRowBatches; b++) {
-        const int y0 = (rb * kRowBatches + b) * kRB;       // the batch's rows: y0 + h * kW + r (warp r)
+        const int y0 = Y0 + (rb * kRowBatches + b) * kRB;  // the batch's rows: y0 + h * kW + r (warp r)
 #pragma unroll
         for (int h = 0; h < kRPW; h++) {
             const int y = y0 + h * kW + r;
@@ -266,20 +275,32 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
             }
         }
         __syncwarp();
+        // image row (y - Y0) of grid row y; with a kernel each row and pixel is scaled by its grid correction
+        auto row_scale = [&](int y) { return WT ? inv * __ldg(P.corr + (y - Y0)) : inv; };
+        auto put = [&](float2* out, float sy, int m, float2 v) {    // streaming: the images are not read back
+            if constexpr (WT) {
+                if (m >= X0 && m < X0 + NI / 2) {
+                    const float2 c = __ldg(reinterpret_cast<const float2*>(P.corr) + (m - X0));
+                    __stcs(out + (m - X0), make_float2(v.x * sy * c.x, v.y * sy * c.y));
+                }
+            } else {
+                __stcs(out + m, make_float2(v.x * sy, v.y * sy));
+            }
+        };
         if constexpr (M == 256 && kRPW == 2) {
-            // both rows at once: rows h * kW + r of the buffer, image rows y0 + h * kW + r
-            float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y0 + r) * N);
-            auto store = [&](int h, int m, float2 v) {      // streaming: the images are not read back
-                __stcs(out + h * kW * (N / 2) + m, make_float2(v.x * inv, v.y * inv));
-            };
+            // both rows at once: rows h * kW + r of the buffer, grid rows y0 + h * kW + r
+            float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * NI + y0 - Y0 + r) * NI);
+            const float s0 = row_scale(y0 + r), s1 = row_scale(y0 + kW + r);
+            auto store = [&](int h, int m, float2 v) { put(out + h * kW * (NI / 2), h ? s1 : s0, m, v); };
             warp_fft256x2(reinterpret_cast<float2*>(work) + r * LS, kW * LS, s_twr, lane, store);
         } else {
 #pragma unroll 1
             for (int h = 0; h < kRPW; h++) {
                 const int y = y0 + h * kW + r;
                 float2* dst = reinterpret_cast<float2*>(work) + (h * kW + r) * LS;
-                float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y) * N);
-                auto store = [&](int, int m, float2 v) { __stcs(out + m, make_float2(v.x * inv, v.y * inv)); };
+                float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * NI + y - Y0) * NI);
+                const float sy = row_scale(y);
+                auto store = [&](int, int m, float2 v) { put(out, sy, m, v); };
                 warp_fft<M, true, float2, decltype(store)>(dst, s_twr, lane, store);
             }
         }
@@ -297,7 +318,7 @@ template <int N, typename T> constexpr size_t fft_smem() {
 }
 
 // 32 warps per SM for sides up to 512 (measured faster than 24, despite a few register spills).
-template <int N, typename T>
+template <int N, typename T, bool WT>
 __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persistent(const FftParams P) {
     constexpr int M = N / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -342,10 +363,10 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
         const int sg = t / seg, r = t - sg * seg;
         int* done = nullptr;
         if (r < P.n_cb) {
-            if (sg < P.n_img) done = column_task<N, T>(P, sg, r, s_twc, work, s_occ, &s_flag);
+            if (sg < P.n_img) done = column_task<N, T, WT>(P, sg, r, s_twc, work, s_occ, &s_flag);
         } else {
             const int k = sg - P.lag;
-            if (k >= 0 && k < P.n_img) done = row_task<N, T>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
+            if (k >= 0 && k < P.n_img) done = row_task<N, T, WT>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
         }
         // every thread's reads and writes of the task are done; thread 0 takes the next ticket and releases the
         // task (the fence orders the whole CTA's accesses before the counter), its latencies overlapping.  (Taking
@@ -364,9 +385,9 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
     }
 }
 
-template <int N, typename T>
+template <int N, typename T, bool WT>
 blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
-    auto kern = k_fft_persistent<N, T>;
+    auto kern = k_fft_persistent<N, T, WT>;
     const size_t smem = fft_smem<N, T>();
     static int per_sm = 0;                         // attributes and occupancy once per instantiation
     if (!per_sm) {
@@ -377,7 +398,7 @@ blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
     }
     if (per_sm < 1) return set_error(BLINK_ERR_UNSUPPORTED, "persistent FFT kernel does not fit on an SM");
     P.n_cb = N / 2 / kCW;
-    P.n_rb = N / (kRB * kRowBatches);
+    P.n_rb = (WT ? N / 2 : N) / (kRB * kRowBatches);
     const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, per_sm) : per_sm;
     kern<<<n_sm * per, kPT, smem, st>>>(P);
     BLINK_CUDA(cudaGetLastError());
@@ -427,14 +448,24 @@ blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec,
     P.row_done = d_counters + 2 + P.n_img;
     P.status = d_status;
     BLINK_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int) * (2 + 2 * (size_t)P.n_img), st));
-    const bool bf = prec == BLINK_PREC_BF16;
+    const bool bf = prec == BLINK_PREC_BF16, wt = p.d_wt != nullptr;
+    P.wt = p.d_wt;
+    P.corr = p.d_corr;
+    if (wt && (!p.d_corr || p.N < 128))
+        return set_error(BLINK_ERR_UNSUPPORTED, "convolutional gridding needs a grid side of at least 128");
+    const int c = tune.ctas_per_sm;
     switch (p.N) {
-        case 64: return bf ? launch_n<64, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<64, float2>(P, n_sm, tune.ctas_per_sm, st);
-        case 128: return bf ? launch_n<128, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<128, float2>(P, n_sm, tune.ctas_per_sm, st);
-        case 256: return bf ? launch_n<256, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<256, float2>(P, n_sm, tune.ctas_per_sm, st);
-        case 512: return bf ? launch_n<512, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<512, float2>(P, n_sm, tune.ctas_per_sm, st);
-        case 1024: return bf ? launch_n<1024, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<1024, float2>(P, n_sm, tune.ctas_per_sm, st);
-        case 2048: return bf ? launch_n<2048, __nv_bfloat162>(P, n_sm, tune.ctas_per_sm, st) : launch_n<2048, float2>(P, n_sm, tune.ctas_per_sm, st);
+        case 64: return bf ? launch_n<64, __nv_bfloat162, false>(P, n_sm, c, st) : launch_n<64, float2, false>(P, n_sm, c, st);
+#define BLINK_FFT_CASE(NN)                                                                                  \
+        case NN:                                                                                            \
+            if (wt) return bf ? launch_n<NN, __nv_bfloat162, true>(P, n_sm, c, st) : launch_n<NN, float2, true>(P, n_sm, c, st); \
+            return bf ? launch_n<NN, __nv_bfloat162, false>(P, n_sm, c, st) : launch_n<NN, float2, false>(P, n_sm, c, st);
+        BLINK_FFT_CASE(128)
+        BLINK_FFT_CASE(256)
+        BLINK_FFT_CASE(512)
+        BLINK_FFT_CASE(1024)
+        BLINK_FFT_CASE(2048)
+#undef BLINK_FFT_CASE
     }
     return set_error(BLINK_ERR_UNSUPPORTED, "image side must be a power of two in [64, 2048]");
 }

@@ -45,7 +45,7 @@ k_grid_gather(const float* __restrict__ vis4, int64_t B, int F, int first_image,
         auto idx = [&](int u, int v) { return v * cw + (u - u0); };
         const int* off = ent_off + f * (half + 1);
         for (int u = u0 + (tid >> 5); u < min(u0 + cw, half); u += kGridThreads / 32)   // one warp per column
-            warp_gather_column(ent, off[u], off[u + 1], tid & 31, sg, val, idx, false);
+            warp_gather_column(ent, nullptr, off[u], off[u + 1], tid & 31, sg, val, idx, false);
     }
     __syncthreads();
     const int ncols = min(cw, half + 1 - u0);

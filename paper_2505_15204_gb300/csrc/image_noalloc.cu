@@ -61,6 +61,9 @@ extern "C" blink_status blink_image_noalloc(const blink_imaging* imaging, const 
         return set_error(BLINK_ERR_UNSUPPORTED, "imaging.n_pix must be a power of two in [64, 2048]");
     if (prec != BLINK_PREC_FP32 && prec != BLINK_PREC_BF16)
         return set_error(BLINK_ERR_INVALID_ARG, "imaging.precision must be BLINK_PREC_FP32 or BLINK_PREC_BF16");
+    if (imaging->support >= 2)
+        return set_error(BLINK_ERR_UNSUPPORTED, "blink_image_noalloc: gridding with a convolution kernel runs in the "
+                                                "batched pipeline forms only");
     if (!d_grid || !d_weight || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_grid, d_weight or d_img is NULL");
     if (n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "n_images < 0");
     if (((uintptr_t)d_grid & 7) || ((uintptr_t)d_img & 7))

@@ -71,7 +71,7 @@ int main(void) {
     OFF(blink_obs, n_fine); OFF(blink_obs, fine_stride); OFF(blink_obs, fine_freq_hz); OFF(blink_obs, chan_avg);
     OFF(blink_obs, samples_per_int); OFF(blink_obs, n_samples);
     OFF(blink_imaging, n_pix); OFF(blink_imaging, cell_lambda); OFF(blink_imaging, pol);
-    OFF(blink_imaging, include_autos); OFF(blink_imaging, precision);
+    OFF(blink_imaging, include_autos); OFF(blink_imaging, precision); OFF(blink_imaging, support);
     OFF(blink_set, fine0); OFF(blink_set, n_fine); OFF(blink_set, flags); OFF(blink_set, imaging);
     printf("baselines %lld\n", (long long)blink_n_baselines(144));
     /* an argument error is returned before any device work: no context */

@@ -83,3 +83,17 @@ def test_oracle_images_of_picked_sets_use_each_sets_calibration(bench):
                               ids=np.array([i]), flags=st.flags, fine0=st.fine0, n_fine=st.n_fine,
                               gains=gains[st.fine0:st.fine0 + st.n_fine].astype(np.complex128))["images"][0]
         assert np.array_equal(img, ref)
+
+
+def test_oracle_images_of_picked_sets_use_the_kernel(bench):
+    import oracle
+    w = bs.WORKLOADS["tiny"]
+    inp = bs.build_workload("tiny")
+    sets = bench.image_sets(inp, w, 10)
+    st = sets[0][0]
+    inp = dict(inp, sets=[type(st)(fine0=st.fine0, n_fine=st.n_fine, n_pix=64, flags=st.flags)])
+    sets = bench.image_sets(inp, w, 10)
+    got = bench.oracle_sets_images(oracle, inp, w, sets, [(0, 0)], 1, None, 4)[0]
+    ref = oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], 10, 1, 64, support=4)["images"][0]
+    assert np.array_equal(got, ref)
+    assert not np.array_equal(got, oracle.pipeline(inp["volt"], inp["enu"], inp["freqs"], 10, 1, 64)["images"][0])

@@ -626,3 +626,73 @@ def test_diagonal_jones_images_equal_gains_images(B, ctx):
     B.blink_sync(ctx)
     for q in range(16):
         assert rel_rms(b[q].cpu().numpy(), a[q].cpu().numpy()) <= 1e-6
+
+
+# ---------------------------------------------------------------------------------------------------
+# gridding with a Kaiser-Bessel convolution kernel (grid of side 2N, central N x N corrected image)
+# ---------------------------------------------------------------------------------------------------
+
+KB_CASES = [
+    # name, n_samples, fine, chan_avg, n_pix, pol, autos, flags, support
+    ("tiny", None, None, 1, 256, 0, 1, False, 6),          # grid 512: two-row radix-16 row pass
+    ("precision", None, None, 1, 512, 0, 1, False, 4),     # grid 1024: generic row pass
+    ("coarse", 20, 8, 4, 128, 0, 1, False, 8),             # grid 256: several images per channel
+    ("uneven", 20, 3, 1, 64, 1, 0, True, 2),               # grid 128: zeroed columns, XX, no autos, flags
+    ("tiny", None, None, 1, 1024, 0, 1, False, 6),         # grid 2048
+]
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp32", "fp8"])
+@pytest.mark.parametrize("case", KB_CASES, ids=[f"{c[0]}-{c[4]}-W{c[8]}" for c in KB_CASES])
+def test_kb_pipeline_matches_oracle(B, ctx, case, arith):
+    name, ns_total, fine, c, n_pix, pol, autos, flags, W = case
+    w, volt, freqs, fl = _case(name, ns_total, fine, flags)
+    T = volt.shape[0] // 10
+    F = len(freqs) // c
+    img = torch.full((T * F, n_pix, n_pix), float("nan"), dtype=torch.float32, device="cuda")
+    wts = torch.empty(T * F, dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"], fl), B.Obs(freqs, c, 10, volt.shape[0]),
+                     B.Imaging(n_pix, pol=pol, include_autos=autos, support=W), arith, 0, dev(volt), img, wts)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, c, n_pix, flags=fl, pol=pol, autos=bool(autos), n_threads=8,
+                          support=W)
+    got = img.cpu().numpy()
+    for q in range(T * F):
+        err = rel_rms(got[q], ref["images"][q])
+        assert err <= IMG_RTOL, (q, err)
+        assert wts[q].item() == ref["W"][q]
+
+
+def test_kb_pipeline_with_gains_and_sets(B, ctx):
+    # calibrated Stokes I with a kernel, in a sets call next to a nearest-cell set (packed outputs of two
+    # image sides)
+    w, volt, freqs, fl = _case("coarse", 20, 8, flags=True)
+    g = _gains(8, 128, 8)
+    sets = [B.Set(0, 4, B.Imaging(256, support=4), flags=fl), B.Set(4, 4, B.Imaging(128))]
+    total = 2 * 4 * 256 * 256 + 2 * 4 * 128 * 128
+    img = torch.full((total,), float("nan"), dtype=torch.float32, device="cuda")
+    B.blink_pipeline_sets(ctx, B.Array(w["enu"], None, g), B.Obs(freqs, 1, 10, 20), sets, 1, dev(volt), img, total)
+    B.blink_sync(ctx)
+    got = img.cpu().numpy()
+    ref0 = oracle.pipeline(volt, w["enu"], freqs, 10, 1, 256, flags=fl, fine0=0, n_fine=4, support=4,
+                           gains=g[0:4].astype(np.complex128), n_threads=8)["images"]
+    ref1 = oracle.pipeline(volt, w["enu"], freqs, 10, 1, 128, fine0=4, n_fine=4,
+                           gains=g[4:8].astype(np.complex128), n_threads=8)["images"]
+    part0 = got[:8 * 256 * 256].reshape(8, 256, 256)
+    part1 = got[8 * 256 * 256:].reshape(8, 128, 128)
+    for q in range(8):
+        assert rel_rms(part0[q], ref0[q]) <= IMG_RTOL, q
+        assert rel_rms(part1[q], ref1[q]) <= IMG_RTOL, q
+
+
+@pytest.mark.parametrize("per_pass", [0, 3])
+def test_kb_pipeline_host_equals_device_path(B, ctx, per_pass):
+    w, volt, freqs, _ = _case("coarse", 20, 8)
+    arr, obs, im = B.Array(w["enu"]), B.Obs(freqs, 2, 10, 20), B.Imaging(256, support=6)
+    d = torch.empty((8, 256, 256), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, arr, obs, im, 1, 0, dev(volt), d)
+    h_volt = torch.from_numpy(volt).pin_memory()
+    h_img = torch.full((8, 256, 256), float("nan"), dtype=torch.float32).pin_memory()
+    B.blink_pipeline_host(ctx, arr, obs, im, 1, h_volt, h_img, images_per_pass=per_pass)
+    B.blink_sync(ctx)
+    assert np.array_equal(h_img.numpy(), d.cpu().numpy())

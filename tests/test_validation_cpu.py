@@ -153,3 +153,26 @@ def test_pipeline_host_arguments():
     _expect(B.BLINK_ERR_INVALID_ARG, "images_per_pass < 0", fn, None, a, o, i, 0, h_volt, h_img, -1)
     _expect(B.BLINK_ERR_INVALID_ARG, "h_volt or h_img is NULL", fn, None, a, o, i, 0, None, h_img)
     _expect(*NO_CTX, fn, None, a, o, i, 0, h_volt, h_img, 0)
+
+
+def test_convolution_kernel_options():
+    a, o = B.Array(_enu()), _obs()
+    _expect(B.BLINK_ERR_INVALID_ARG, "imaging.support", B.blink_pipeline, None, a, o, B.Imaging(64, support=17), 0, 0,
+            PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "imaging.support", B.blink_pipeline, None, a, o, B.Imaging(64, support=-1), 0, 0,
+            PTR, PTR)
+    _expect(B.BLINK_ERR_UNSUPPORTED, "at most 1024", B.blink_pipeline, None, a, o, B.Imaging(2048, support=4), 0, 0,
+            PTR, PTR)
+    k = B.Imaging(64, support=6)
+    _expect(*NO_CTX, B.blink_pipeline, None, a, o, k, 0, B.BLINK_MODE_BATCHED, PTR, PTR)
+    _expect(*NO_CTX, B.blink_pipeline, None, a, o, B.Imaging(64, support=1), 0, B.BLINK_MODE_PLAIN, PTR, PTR)
+    # the kernel runs in the batched forms only
+    only = "batched pipeline forms only"
+    _expect(B.BLINK_ERR_UNSUPPORTED, only, B.blink_pipeline, None, a, o, k, 0, B.BLINK_MODE_PLAIN, PTR, PTR)
+    _expect(B.BLINK_ERR_UNSUPPORTED, only, B.blink_grid, None, a, o, k, PTR, 0, 1, PTR)
+    _expect(B.BLINK_ERR_UNSUPPORTED, only, B.blink_image, None, k, PTR, 1, PTR, PTR)
+    _expect(B.BLINK_ERR_UNSUPPORTED, only, B.blink_cells, None, a, o, k, PTR)
+    _expect(B.BLINK_ERR_UNSUPPORTED, only, B.blink_image_noalloc, k, PTR, 1, PTR, PTR)
+    _expect(*NO_CTX, B.blink_pipeline_sets, None, a, o, [B.Set(0, 2, k), B.Set(2, 2, B.Imaging(64))], 0, PTR, PTR,
+            2 * 2 * 64 * 64)
+    _expect(*NO_CTX, B.blink_pipeline_host, None, a, o, k, 0, np.zeros(4, np.uint8), np.zeros(4, np.float32), 0)
