@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "blink_internal.cuh"
@@ -166,38 +167,33 @@ double default_cell(const blink_array* a, double nu_max, int n_pix, int support)
 // Cell-sorted gather list of the u >= 0 half plane for every output channel: one entry per visibility (and
 // per mirror) contribution that lands in the half plane, ordered by (u, v, baseline), with the offsets of
 // every column u so that a column, or a block of consecutive columns, is one contiguous range.  A channel's
-// contributions are collected as (key = u * N + v, (b << 1) | conj[, weight]) and appended by `add_channel`.
+// contributions are collected as (key = u * N + v, (b << 1) | conj) and appended by `add_channel`.
 struct GatherBuilder {
     int N, half;
     int64_t nkeys;
     std::vector<int> count, ent_off;
     std::vector<uint2> ent;
-    std::vector<float> wt;
     std::vector<uint32_t> ekey, eval, sorted, skey;
-    std::vector<float> ewt, swt;
     GatherBuilder(int n, int F) : N(n), half(n / 2), nkeys((int64_t)(n / 2) * n), count(nkeys + 1),
                                   ent_off((size_t)F * (n / 2 + 1)) {}
     uint32_t key(int u, int v) const { return (uint32_t)((int64_t)u * N + v); }
     void clear() {
         ekey.clear();
         eval.clear();
-        ewt.clear();
     }
     // stable counting sort by key: the entries of a cell stay in the order they were added
-    blink_status add_channel(int f, bool weighted) {
+    blink_status add_channel(int f) {
         std::fill(count.begin(), count.end(), 0);
         for (uint32_t k : ekey) count[k + 1]++;
         for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
         sorted.assign(ekey.size(), 0);
         skey.assign(ekey.size(), 0);
-        if (weighted) swt.assign(ekey.size(), 0.f);
         {
             std::vector<int> cur(count.begin(), count.end() - 1);
             for (size_t e = 0; e < ekey.size(); e++) {
                 const int at = cur[ekey[e]]++;
                 sorted[at] = eval[e];
                 skey[at] = ekey[e];
-                if (weighted) swt[at] = ewt[e];
             }
         }
         const int64_t base = (int64_t)ent.size();
@@ -207,11 +203,10 @@ struct GatherBuilder {
             const uint32_t u = skey[e] / N, v = skey[e] % N;
             ent.push_back(make_uint2(u | (v << 11) | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
         }
-        if (weighted) wt.insert(wt.end(), swt.begin(), swt.end());
         if ((int64_t)ent.size() > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
         return BLINK_OK;
     }
-    blink_status upload(Plan* p, bool weighted) {
+    blink_status upload(Plan* p) {
         p->n_contrib = (int64_t)ent.size();
         p->n_cells = p->n_contrib;
         BLINK_TRY(dmalloc(&p->d_ent_off, ent_off.size()));
@@ -219,11 +214,6 @@ struct GatherBuilder {
         BLINK_CUDA(cudaMemcpy(p->d_ent_off, ent_off.data(), ent_off.size() * sizeof(int), cudaMemcpyHostToDevice));
         if (!ent.empty())
             BLINK_CUDA(cudaMemcpy(p->d_ent, ent.data(), ent.size() * sizeof(uint2), cudaMemcpyHostToDevice));
-        if (weighted) {
-            BLINK_TRY(dmalloc(&p->d_wt, wt.size()));
-            if (!wt.empty())
-                BLINK_CUDA(cudaMemcpy(p->d_wt, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice));
-        }
         return BLINK_OK;
     }
 };
@@ -270,10 +260,10 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
             w += 2;
         }
         p->W[f] = (float)w;
-        BLINK_TRY(g.add_channel(f, false));
+        BLINK_TRY(g.add_channel(f));
     }
     p->n_dropped = dropped;
-    return g.upload(p, false);
+    return g.upload(p);
 }
 
 // ---- gridding with a convolution kernel ----------------------------------------------------------
@@ -305,43 +295,42 @@ double kb_transform(double nu, int W, double beta) {
 // the visibility's contribution at c lands in the half plane when cu > 0, its mirror's (conjugate, at -c)
 // when cu < 0, both when cu = 0.  Autocorrelations sit at g = 0 without mirror; their cells with cu >= 0
 // stand for the whole (real, symmetric) spread.  uvw: host [F][B][3] from the geometry kernel.
+// Channels are independent: a first pass counts each channel's entries, a second sorts every channel into
+// its own range of the list; both run on host threads, channel by channel, with the same result as in turn.
 blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std::vector<short2>& bl,
                              const blink_array* a) {
-    const int N = p->N, W = p->support;
-    const int64_t B = p->B;
+    const int N = p->N, W = p->support, half = N / 2, F = p->F;
+    const int64_t B = p->B, nkeys = (int64_t)half * N;
     const double beta = kb_beta(W), h = 0.5 * W, lim = 0.5 * N - h;
-    GatherBuilder g(N, p->F);
-    p->W.assign(p->F, 0.f);
-    int64_t dropped = 0;
-    std::vector<int> cu_list, cv_list;
-    std::vector<double> wu_list, wv_list;
-    auto support_cells = [&](double gx, std::vector<int>& cs, std::vector<double>& ws) {
-        cs.clear();
-        ws.clear();
-        for (int c = (int)std::floor(gx - h); c <= (int)std::ceil(gx + h); c++)
-            if (std::fabs((double)c - gx) < h) {
-                cs.push_back(c);
-                ws.push_back(kb_weight((double)c - gx, W, beta));
+    // the cells within W/2 of x (at most W + 1) and, when `ws` is given, their weights
+    auto support_cells = [&](double x, int* cs, double* ws) {
+        int n = 0;
+        for (int c = (int)std::floor(x - h); c <= (int)std::ceil(x + h); c++)
+            if (std::fabs((double)c - x) < h) {
+                if (ws) ws[n] = kb_weight((double)c - x, W, beta);
+                cs[n++] = c;
             }
+        return n;
     };
-    for (int f = 0; f < p->F; f++) {
-        g.clear();
-        int64_t w = 0;
-        auto add = [&](int u, int v, int64_t b, uint32_t conj, double wt) {
-            g.ekey.push_back(g.key(u, ((v % N) + N) % N));
-            g.eval.push_back((uint32_t)(b << 1) | conj);
-            g.ewt.push_back((float)wt);
-        };
+    auto key = [&](int u, int v) { return (uint32_t)((int64_t)u * N + ((v % N) + N) % N); };
+    // every half-plane contribution of channel f in baseline order: emit(key, (b << 1) | conj, weight)
+    auto channel = [&](int f, bool weights, auto&& emit, int64_t& wsum, int64_t& dropped) {
+        int cu[20], cv[20];
+        double wu[20], wv[20];
+        double* pu = weights ? wu : nullptr;
+        double* pv = weights ? wv : nullptr;
+        wsum = 0;
+        dropped = 0;
         for (int64_t b = 0; b < B; b++) {
             const int i = bl[b].x, j = bl[b].y;
             if (a->flags && (a->flags[i] || a->flags[j])) continue;
             if (i == j) {
                 if (!p->autos) continue;
-                support_cells(0.0, cu_list, wu_list);
-                for (size_t q = 0; q < cu_list.size(); q++)
-                    for (size_t r = 0; r < cu_list.size(); r++)
-                        if (cu_list[r] >= 0) add(cu_list[r], cu_list[q], b, 0, wu_list[r] * wu_list[q]);
-                w += 1;
+                const int n = support_cells(0.0, cu, pu);
+                for (int q = 0; q < n; q++)
+                    for (int r = 0; r < n; r++)
+                        if (cu[r] >= 0) emit(key(cu[r], cu[q]), (uint32_t)(b << 1), weights ? (float)(wu[r] * wu[q]) : 0.f);
+                wsum += 1;
                 continue;
             }
             const double gu = uvw[((size_t)f * B + b) * 3 + 0] / p->du, gv = uvw[((size_t)f * B + b) * 3 + 1] / p->du;
@@ -349,22 +338,81 @@ blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std:
                 dropped++;
                 continue;
             }
-            support_cells(gu, cu_list, wu_list);
-            support_cells(gv, cv_list, wv_list);
-            for (size_t q = 0; q < cv_list.size(); q++)
-                for (size_t r = 0; r < cu_list.size(); r++) {
-                    const int cu = cu_list[r], cv = cv_list[q];
-                    const double wgt = wu_list[r] * wv_list[q];
-                    if (cu >= 0) add(cu, cv, b, 0, wgt);
-                    if (cu <= 0) add(-cu, -cv, b, 1, wgt);
+            const int nu = support_cells(gu, cu, pu), nv = support_cells(gv, cv, pv);
+            for (int q = 0; q < nv; q++)
+                for (int r = 0; r < nu; r++) {
+                    const float wgt = weights ? (float)(wu[r] * wv[q]) : 0.f;
+                    if (cu[r] >= 0) emit(key(cu[r], cv[q]), (uint32_t)(b << 1), wgt);
+                    if (cu[r] <= 0) emit(key(-cu[r], -cv[q]), (uint32_t)(b << 1) | 1u, wgt);
                 }
-            w += 2;
+            wsum += 2;
         }
-        p->W[f] = (float)w;
-        BLINK_TRY(g.add_channel(f, true));
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int n_thr = (int)std::min<unsigned>(std::min<unsigned>(hw, 16u), (unsigned)F);
+    auto parallel = [&](auto&& body) {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < n_thr; t++)
+            pool.emplace_back([&, t] {
+                for (int f = t; f < F; f += n_thr) body(f);
+            });
+        for (std::thread& th : pool) th.join();
+    };
+    std::vector<int64_t> n_ent(F), wsum(F), drop(F);
+    parallel([&](int f) {
+        int64_t c = 0;
+        channel(f, false, [&](uint32_t, uint32_t, float) { c++; }, wsum[f], drop[f]);
+        n_ent[f] = c;
+    });
+    std::vector<int64_t> base(F + 1, 0);
+    for (int f = 0; f < F; f++) base[f + 1] = base[f] + n_ent[f];
+    if (base[F] > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
+    std::vector<uint2> ent((size_t)base[F]);
+    std::vector<float> wt((size_t)base[F]);
+    std::vector<int> ent_off((size_t)F * (half + 1));
+    parallel([&](int f) {
+        std::vector<uint32_t> ekey, eval;
+        std::vector<float> ewt;
+        ekey.reserve(n_ent[f]);
+        eval.reserve(n_ent[f]);
+        ewt.reserve(n_ent[f]);
+        int64_t w_, d_;
+        channel(f, true, [&](uint32_t k, uint32_t v, float x) {
+            ekey.push_back(k);
+            eval.push_back(v);
+            ewt.push_back(x);
+        }, w_, d_);
+        // stable counting sort by key into the channel's range: a cell's entries stay in baseline order
+        std::vector<int> count(nkeys + 1, 0);
+        for (uint32_t k : ekey) count[k + 1]++;
+        for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
+        for (int u = 0; u <= half; u++)
+            ent_off[(size_t)f * (half + 1) + u] = (int)(base[f] + count[std::min<int64_t>((int64_t)u * N, nkeys)]);
+        for (size_t e = 0; e < ekey.size(); e++) {
+            const int64_t at = base[f] + count[ekey[e]]++;
+            const uint32_t u = ekey[e] / N, v = ekey[e] % N;
+            ent[at] = make_uint2(u | (v << 11) | ((eval[e] & 1u) << 31), eval[e] >> 1);
+            wt[at] = ewt[e];
+        }
+    });
+    p->W.assign(F, 0.f);
+    int64_t dropped = 0;
+    for (int f = 0; f < F; f++) {
+        p->W[f] = (float)wsum[f];
+        dropped += drop[f];
     }
     p->n_dropped = dropped;
-    return g.upload(p, true);
+    p->n_contrib = base[F];
+    p->n_cells = p->n_contrib;
+    BLINK_TRY(dmalloc(&p->d_ent_off, ent_off.size()));
+    BLINK_TRY(dmalloc(&p->d_ent, ent.size()));
+    BLINK_TRY(dmalloc(&p->d_wt, wt.size()));
+    BLINK_CUDA(cudaMemcpy(p->d_ent_off, ent_off.data(), ent_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!ent.empty()) {
+        BLINK_CUDA(cudaMemcpy(p->d_ent, ent.data(), ent.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+        BLINK_CUDA(cudaMemcpy(p->d_wt, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return BLINK_OK;
 }
 
 // Grid correction of an image of side Ni from a grid of side 2 Ni: 1 / c((x - Ni/2) / (2 Ni)) per pixel index.
