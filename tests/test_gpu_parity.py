@@ -696,3 +696,24 @@ def test_kb_pipeline_host_equals_device_path(B, ctx, per_pass):
     B.blink_pipeline_host(ctx, arr, obs, im, 1, h_volt, h_img, images_per_pass=per_pass)
     B.blink_sync(ctx)
     assert np.array_equal(h_img.numpy(), d.cpu().numpy())
+
+
+def test_kb_pipeline_is_bitwise_reproducible_and_bf16_error_is_reported(B, ctx):
+    # fixed summation order with a kernel too; BF16 storage of the 2N grid and ring is reported, not gated
+    w, volt, freqs, _ = _case("coarse", 20, 8)
+    arr, obs = B.Array(w["enu"]), B.Obs(freqs, 1, 10, 20)
+    outs = []
+    for _ in range(2):
+        img = torch.empty((16, 256, 256), dtype=torch.float32, device="cuda")
+        B.blink_pipeline(ctx, arr, obs, B.Imaging(256, support=6), 1, 0, dev(volt), img)
+        B.blink_sync(ctx)
+        outs.append(img.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    img = torch.empty((16, 256, 256), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, arr, obs, B.Imaging(256, support=6, precision=1), 1, 0, dev(volt), img)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, 256, ids=np.array([0, 15]), support=6, n_threads=8)["images"]
+    got = img.cpu().numpy()
+    errs = [rel_rms(got[q], ref[k]) for k, q in enumerate((0, 15))]
+    print("bf16 storage with a kernel: rel RMS", errs)
+    assert max(errs) < 2e-2
