@@ -717,3 +717,30 @@ def test_kb_pipeline_is_bitwise_reproducible_and_bf16_error_is_reported(B, ctx):
     errs = [rel_rms(got[q], ref[k]) for k, q in enumerate((0, 15))]
     print("bf16 storage with a kernel: rel RMS", errs)
     assert max(errs) < 5e-2             # a sanity bound (BF16 storage is ~5e-3 at 512^2; the correction enlarges the edges')
+
+
+def test_dedispersion_recovers_the_injected_dispersion_measure(B, ctx):
+    # a dispersed 1 ms burst (DM 500) imaged by the path and dedispersed by blink_dedisperse at trial DMs: the
+    # phase-centre peak is largest at DM 500, and the DM-500 cube equals the oracle's within the image gate
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location("pins", os.path.join(os.path.dirname(__file__), "test_oracle_pins.py"))
+    pins = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(pins)
+    enu, freqs, volt = pins._dispersed_burst_case()
+    T, F, n = 400, 8, 64
+    img = torch.empty((T * F, n, n), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(enu), B.Obs(freqs, 1, 10, 4000), B.Imaging(n), 1, 0, dev(volt), img)
+    peaks, out500 = {}, None
+    for dm in range(0, 1001, 100):
+        d = pins._delays(freqs, dm)
+        out = torch.empty((T - int(d.max()), n, n), dtype=torch.float32, device="cuda")
+        B.blink_dedisperse(ctx, img, T, F, n, d, out)
+        B.blink_sync(ctx)
+        peaks[dm] = float(out[:, n // 2, n // 2].max())
+        if dm == 500:
+            out500 = out.cpu().numpy()
+    assert max(peaks, key=peaks.get) == 500, peaks
+    ref_img = oracle.pipeline(volt, enu, freqs, 10, 1, n, n_threads=8)["images"].reshape(T, F, n, n)
+    ref = oracle.dedisperse(ref_img, pins._delays(freqs, 500))
+    assert rel_rms(out500, ref) <= IMG_RTOL

@@ -709,3 +709,37 @@ def test_kb_pipeline_matches_stepwise_functions():
     full, _ = oracle.image(oracle.ifft2(G), Wsum)
     assert np.array_equal(out["images"][0], oracle.kb_crop_correct(full, W))
     assert out["W"][0] == 128 * 128
+
+
+def _dispersed_burst_case(dm=500.0):
+    # 16 tiles, 8 channels 20 kHz apart below 155 MHz, 400 integrations of 1 ms (K = 10): a 1 ms burst at the
+    # phase centre arriving 5.3 ms into the data at the top channel and later below it by the cold-plasma law
+    # 4.148808e3 s MHz^2 DM (nu^-2 - nu_top^-2) (Sec. 2, 7: the FRB search the images feed)
+    enu = bs.tile_positions(16, 1500.0, 31)
+    freqs = 155e6 - 20e3 * np.arange(8)
+    sky = bs.Sky(lmn=np.zeros((0, 3)), power=np.zeros(0), burst_lmn=np.array([0.0, 0.0, 1.0]), burst_power=4.0,
+                 burst_dm=dm, burst_t0_s=5.3e-3, burst_width_s=1e-3, burst_f_top_hz=freqs[0])
+    volt = bs.voltages(enu, freqs, 4000, sky, seed=33)
+    return enu, freqs, volt
+
+
+def _delays(freqs, dm, t_int=1e-3):
+    nu = freqs / 1e6
+    return np.rint(4.148808e3 * dm * (nu ** -2 - nu.max() ** -2) / t_int).astype(np.int32)
+
+
+def test_dedispersion_recovers_the_injected_dispersion_measure():
+    # the oracle's images of a dispersed burst, dedispersed at trial DMs 0..1000: the phase-centre peak is
+    # largest at the injected DM 500, where it holds most of the burst's power and stands far above the noise
+    enu, freqs, volt = _dispersed_burst_case()
+    out = oracle.pipeline(volt, enu, freqs, 10, 1, 64, n_threads=4)
+    cube = out["images"].reshape(400, 8, 64, 64)
+    peaks = {}
+    for dm in range(0, 1001, 100):
+        series = oracle.dedisperse(cube[:, :, 32, 32], _delays(freqs, dm))
+        peaks[dm] = series.max()
+    best = max(peaks, key=peaks.get)
+    assert best == 500, peaks
+    noise = bs.image_noise(2.0, 16, 10) / math.sqrt(8)
+    assert peaks[500] > 2.0 and peaks[500] > 20 * noise
+    assert peaks[500] > 2 * max(v for k, v in peaks.items() if abs(k - 500) >= 200)
