@@ -59,7 +59,13 @@ def _load():
             lib.oracle_uvw.restype = None
             lib.oracle_uvw.argtypes = [P, C.c_int, C.c_double, P]
             lib.oracle_default_cell.restype = C.c_double
-            lib.oracle_default_cell.argtypes = [P, C.c_int, P, C.c_double, C.c_int, C.c_int]
+            lib.oracle_default_cell.argtypes = [P, C.c_int, P, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double]
+            lib.oracle_phase_basis.restype = C.c_int
+            lib.oracle_phase_basis.argtypes = [C.c_double, C.c_double, P, P, P]
+            lib.oracle_uvw_phased.restype = C.c_int
+            lib.oracle_uvw_phased.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P]
+            lib.oracle_apply_phase.restype = None
+            lib.oracle_apply_phase.argtypes = [P, P, C.c_int64]
             lib.oracle_cells.restype = None
             lib.oracle_cells.argtypes = [P, C.c_int64, C.c_double, C.c_int, P, P, P]
             lib.oracle_grid.restype = C.c_double
@@ -72,8 +78,8 @@ def _load():
             lib.oracle_image.argtypes = [P, C.c_int, C.c_double, P]
             lib.oracle_pipeline.restype = C.c_int
             lib.oracle_pipeline.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P,
-                                            C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, P, C.c_int, P,
-                                            C.c_int64, C.c_int, P, P, P, P]
+                                            C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double,
+                                            C.c_double, P, C.c_int, P, C.c_int64, C.c_int, P, P, P, P]
             lib.oracle_i0.restype = C.c_double
             lib.oracle_i0.argtypes = [C.c_double]
             lib.oracle_kb_beta.restype = C.c_double
@@ -190,10 +196,38 @@ def uvw(enu: np.ndarray, nu: float) -> np.ndarray:
     return out
 
 
-def default_cell(enu: np.ndarray, nu_max: float, n_pix: int, flags=None, support: int = 0) -> float:
+def default_cell(enu: np.ndarray, nu_max: float, n_pix: int, flags=None, support: int = 0,
+                 phase_centre=(0.0, 0.0)) -> float:
     enu = np.ascontiguousarray(enu, dtype=np.float64)
     fl = _flags(flags, enu.shape[0])
-    return float(_load().oracle_default_cell(_p(enu), enu.shape[0], _p(fl), float(nu_max), n_pix, support))
+    l0, m0 = phase_centre
+    return float(_load().oracle_default_cell(_p(enu), enu.shape[0], _p(fl), float(nu_max), n_pix, support,
+                                             float(l0), float(m0)))
+
+
+def phase_basis(l0: float, m0: float):
+    """(e_l, e_m, s0) of the pointing (l0, m0): the image plane's axes and the pointing, in (E, N, Up)."""
+    el, em, s0 = np.zeros(3), np.zeros(3), np.zeros(3)
+    if _load().oracle_phase_basis(float(l0), float(m0), _p(el), _p(em), _p(s0)):
+        raise ValueError("pointing outside the unit disc")
+    return el, em, s0
+
+
+def uvw_phased(enu: np.ndarray, nu: float, l0: float, m0: float) -> np.ndarray:
+    enu = np.ascontiguousarray(enu, dtype=np.float64)
+    out = np.zeros((n_baselines(enu.shape[0]), 3), dtype=np.float64)
+    if _load().oracle_uvw_phased(_p(enu), enu.shape[0], float(nu), float(l0), float(m0), _p(out)):
+        raise ValueError("pointing outside the unit disc")
+    return out
+
+
+def apply_phase(V: np.ndarray, uvw_: np.ndarray) -> np.ndarray:
+    """V exp(+2 pi i w) per baseline (complex [B][4] in and out)."""
+    V = np.asarray(V)
+    a = np.ascontiguousarray(np.stack([V.real, V.imag], axis=-1), dtype=np.float64)
+    uvw_ = np.ascontiguousarray(uvw_, dtype=np.float64)
+    _load().oracle_apply_phase(_p(a), _p(uvw_), a.shape[0])
+    return a[..., 0] + 1j * a[..., 1]
 
 
 def cells(uvw_: np.ndarray, du: float, n_pix: int):
@@ -295,11 +329,12 @@ def image(a: np.ndarray, W: float):
 def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int, c: int, n_pix: int,
              ids=None, flags=None, fine0: int = 0, n_fine: int | None = None, cell_lambda: float = 0.0,
              pol: int = POL_I, autos: bool = True, n_threads: int = 1, want_grids: bool = False, gains=None,
-             support: int = 0):
+             support: int = 0, phase_centre=(0.0, 0.0)):
     """Dirty images for the listed image ids (id = tau * F + f) of one set.
 
     ``support`` >= 2: grid with the Kaiser-Bessel kernel of that many cells on a grid of side 2N (``grids``
-    are then [n][2N][2N]) and keep the corrected central N x N of each image.
+    are then [n][2N][2N]) and keep the corrected central N x N of each image.  ``phase_centre`` = (l0, m0):
+    phase-centre the visibilities on that pointing (direction cosines in the local E, N, Up frame).
 
     ``gains``: complex [F][n_tiles][2] per output channel of the set, tile and polarisation, or complex
     [F][n_tiles][2][2] full Jones matrices, or None.
@@ -331,8 +366,8 @@ def pipeline(volt: np.ndarray, enu: np.ndarray, fine_freqs: np.ndarray, ns: int,
         assert gains.shape == ((F, nt, 2, 2) if full else (F, nt, 2))
         g = np.ascontiguousarray(np.stack([np.real(gains), np.imag(gains)], axis=-1), dtype=np.float64)
     rc = _load().oracle_pipeline(volt.ctypes.data + fine0 * nt * 2, nf_total, nt, n_fine, c, ns, _p(enu), _p(ff),
-                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), support, _p(g), full,
-                                 _p(ids),
+                                 _p(fl), n_pix, float(cell_lambda), pol, int(bool(autos)), support,
+                                 float(phase_centre[0]), float(phase_centre[1]), _p(g), full, _p(ids),
                                  n, n_threads, _p(grids), _p(imgs), _p(W), _p(mx))
     if rc:
         raise ValueError("oracle_pipeline: bad arguments")

@@ -11,6 +11,8 @@
  *               integration and the c fine channels of an output channel; lower triangle i >= j.
  *   uvw         Sec. 5.2.3-5.2.4: (u, v, w) = (r_i - r_j) * nu / c for every baseline and channel.
  *   cells       Sec. 5.2.4 (gridding "based on the (u, v) coordinates", nearest cell, no kernel).
+ *   phase       Sec. 5.2.3 (geometric corrections: the phase centre set to a pointing direction, with the
+ *               (u, v, w) of that direction): V' = V exp(+2 pi i w), (u, v) in the tangent plane at it.
  *   gains       Sec. 5.2.3 (calibration and cable-length corrections): per-tile, per-polarisation complex
  *               gains g, V_ij^pq = g_i^p S_ij^pq conj(g_j^q) (a diagonal Jones matrix per tile).
  *   grid        Sec. 5.2.4: natural weighting, every visibility and its Hermitian mirror weight 1.
@@ -172,21 +174,94 @@ void oracle_uvw(const double* enu, int n_tiles, double nu, double* uvw)
         }
 }
 
+/*
+ * Phase centre (Sec. 5.2.3: geometric corrections set the phase centre to a pointing direction, and the
+ * imager computes (u, v, w) for it).  The pointing s0 = (l0, m0, n0) is given by direction cosines in the
+ * local (E, N, Up) frame, n0 = sqrt(1 - l0^2 - m0^2).  The image plane's axes (e_l, e_m) are E and N carried
+ * to s0 by the rotation about Up x s0 that takes Up to s0 (Rodrigues' formula; the identity at zenith):
+ * with r = sqrt(l0^2 + m0^2) and k = (-m0, l0, 0) / r,
+ *     e_l = (n0 + kx^2 (1 - n0),  kx ky (1 - n0),      -ky r)
+ *     e_m = (kx ky (1 - n0),      n0 + ky^2 (1 - n0),   kx r).
+ * Returns -1 unless l0^2 + m0^2 < 1.
+ */
+int oracle_phase_basis(double l0, double m0, double* el, double* em, double* s0)
+{
+    double r2 = l0 * l0 + m0 * m0;
+    if (!(r2 < 1.0)) return -1;
+    double n0 = sqrt(1.0 - r2);
+    s0[0] = l0;
+    s0[1] = m0;
+    s0[2] = n0;
+    if (r2 == 0.0) {
+        el[0] = 1.0; el[1] = 0.0; el[2] = 0.0;
+        em[0] = 0.0; em[1] = 1.0; em[2] = 0.0;
+        return 0;
+    }
+    double r = sqrt(r2), kx = -m0 / r, ky = l0 / r, c1 = 1.0 - n0;
+    el[0] = n0 + kx * kx * c1;
+    el[1] = kx * ky * c1;
+    el[2] = -ky * r;
+    em[0] = kx * ky * c1;
+    em[1] = n0 + ky * ky * c1;
+    em[2] = kx * r;
+    return 0;
+}
+
+/* (u, v, w) of every baseline for the pointing (l0, m0): u = b.e_l nu/c, v = b.e_m nu/c, w = b.s0 nu/c,
+ * b = r_i - r_j.  At zenith this is oracle_uvw exactly.  Returns -1 for an invalid pointing. */
+int oracle_uvw_phased(const double* enu, int n_tiles, double nu, double l0, double m0, double* uvw)
+{
+    double el[3], em[3], s0[3];
+    if (oracle_phase_basis(l0, m0, el, em, s0)) return -1;
+    double inv_lambda = nu / ORC_C_LIGHT;
+    for (int i = 0; i < n_tiles; i++)
+        for (int j = 0; j <= i; j++) {
+            int64_t b = (int64_t)i * (i + 1) / 2 + j;
+            double d[3];
+            for (int k = 0; k < 3; k++) d[k] = enu[i * 3 + k] - enu[j * 3 + k];
+            uvw[b * 3 + 0] = (d[0] * el[0] + d[1] * el[1] + d[2] * el[2]) * inv_lambda;
+            uvw[b * 3 + 1] = (d[0] * em[0] + d[1] * em[1] + d[2] * em[2]) * inv_lambda;
+            uvw[b * 3 + 2] = (d[0] * s0[0] + d[1] * s0[1] + d[2] * s0[2]) * inv_lambda;
+        }
+    return 0;
+}
+
+/* V <- V exp(+2 pi i w) for every baseline and polarisation product (V complex double [B][4][2]); the
+ * phase is taken from w's fractional part (w - round(w) is exact), so large w lose no precision. */
+void oracle_apply_phase(double* V, const double* uvw, int64_t n_baselines)
+{
+    for (int64_t b = 0; b < n_baselines; b++) {
+        double w = uvw[b * 3 + 2], fr = w - nearbyint(w);
+        double c = cos(ORC_TWO_PI * fr), sn = sin(ORC_TWO_PI * fr);
+        for (int p = 0; p < 4; p++) {
+            double* z = V + (b * 4 + p) * 2;
+            double re = z[0] * c - z[1] * sn, im = z[0] * sn + z[1] * c;
+            z[0] = re;
+            z[1] = im;
+        }
+    }
+}
+
 /* Default uv cell (wavelengths): the longest unflagged projected baseline at the highest frequency lands
  * in the outermost usable cell, du = u_max / (N/2 - 1); u_max = max |(b_E, b_N)| * (nu_max / c).  With a
  * convolution kernel of W >= 2 cells the grid side is 2N and the support must stay inside it too:
  * du = u_max / (N - 1 - W/2), which keeps the image's pixel scale within a fraction of a percent of the
- * nearest-cell one.
- * Degenerate arrays (no unflagged baseline of non-zero length) get du = 1. */
+ * nearest-cell one.  The projection is onto the image plane of the pointing (l0, m0) (oracle_phase_basis):
+ * (b_E, b_N) at zenith, (b.e_l, b.e_m) elsewhere.
+ * Degenerate arrays (no unflagged baseline of non-zero length) and invalid pointings get du = 1. */
 double oracle_default_cell(const double* enu, int n_tiles, const uint8_t* flags, double nu_max, int n_pix,
-                           int support)
+                           int support, double l0, double m0)
 {
+    double el[3], em[3], s0[3];
+    if (oracle_phase_basis(l0, m0, el, em, s0)) return 1.0;
     double dmax = 0.0;
     for (int i = 0; i < n_tiles; i++)
         for (int j = 0; j < i; j++) {
             if (flags && (flags[i] || flags[j])) continue;
-            double be = enu[i * 3 + 0] - enu[j * 3 + 0];
-            double bn = enu[i * 3 + 1] - enu[j * 3 + 1];
+            double b[3];
+            for (int k = 0; k < 3; k++) b[k] = enu[i * 3 + k] - enu[j * 3 + k];
+            double be = b[0] * el[0] + b[1] * el[1] + b[2] * el[2];
+            double bn = b[0] * em[0] + b[1] * em[1] + b[2] * em[2];
             double d = sqrt(be * be + bn * bn);
             if (d > dmax) dmax = d;
         }
@@ -525,7 +600,8 @@ double oracle_image(const double* a, int n, double W, double* img)
  * form the image.  cell_lambda <= 0 selects the default cell over the set's highest output frequency.
  * support >= 2 (at most 16) grids with the Kaiser-Bessel kernel of that many cells on a grid of side 2N
  * (oracle_grid_kb; `grids` then holds [n_ids][2N][2N][2]) and keeps the corrected central N x N image
- * (oracle_kb_crop_correct); 0 or 1 grids to the nearest cell.
+ * (oracle_kb_crop_correct); 0 or 1 grids to the nearest cell.  (phase_l, phase_m) != (0, 0) phase-centres
+ * the sums on that pointing (oracle_uvw_phased, oracle_apply_phase) before gridding.
  * gains (or NULL): complex double [F][n_tiles][2 pol][2], applied to the sums before gridding; with
  * full_jones, complex double [F][n_tiles][2][2][2] full Jones matrices instead.
  * Optional outputs (NULL to skip): grids [n_ids][N][N][2], images [n_ids][N][N], W [n_ids],
@@ -534,12 +610,14 @@ double oracle_image(const double* a, int n, double W, double* img)
  */
 int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n_fine, int c, int ns,
                     const double* enu, const double* fine_freq, const uint8_t* flags,
-                    int n_pix, double cell_lambda, int pol, int autos, int support, const double* gains,
-                    int full_jones,
+                    int n_pix, double cell_lambda, int pol, int autos, int support, double phase_l,
+                    double phase_m, const double* gains, int full_jones,
                     const int64_t* ids, int64_t n_ids, int n_threads,
                     double* grids, double* imgs, double* W_out, double* maxim_out)
 {
     if (n_pix <= 2 || (n_pix & (n_pix - 1)) || c <= 0 || ns <= 0 || n_fine % c) return -1;
+    if (!(phase_l * phase_l + phase_m * phase_m < 1.0)) return -1;
+    int phased = phase_l != 0.0 || phase_m != 0.0;
     if (support >= 2 && (support > 16 || (double)(n_pix - 1) - 0.5 * (double)support <= 0.0)) return -1;
     int ng = support >= 2 ? 2 * n_pix : n_pix;      /* grid side */
     int F = n_fine / c;
@@ -547,7 +625,8 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
     oracle_output_freqs(fine_freq, n_fine, c, fout);
     double numax = fout[0];
     for (int f = 1; f < F; f++) if (fout[f] > numax) numax = fout[f];
-    double du = cell_lambda > 0.0 ? cell_lambda : oracle_default_cell(enu, n_tiles, flags, numax, n_pix, support);
+    double du = cell_lambda > 0.0 ? cell_lambda
+                                  : oracle_default_cell(enu, n_tiles, flags, numax, n_pix, support, phase_l, phase_m);
     int64_t B = oracle_n_baselines(n_tiles);
     int K = ns * c;
     int bad = 0;
@@ -562,30 +641,31 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
         double* G = (double*)malloc(sizeof(double) * 2 * ng * ng);
         double* im = (double*)malloc(sizeof(double) * ng * ng);
         oracle_correlate_one(volt, fine_stride, n_tiles, ns, c, tau, f, flags, S);
-        oracle_uvw(enu, n_tiles, fout[f], uvw);
+        if (phased)
+            oracle_uvw_phased(enu, n_tiles, fout[f], phase_l, phase_m, uvw);
+        else
+            oracle_uvw(enu, n_tiles, fout[f], uvw);
         oracle_cells(uvw, B, du, n_pix, iu, iv, keep);
         double W;
-        if (support >= 2) {
-            double* V = (double*)malloc(sizeof(double) * B * 8);
+        /* the sums as complex doubles when anything changes them: calibration, then the phase rotation */
+        double* V = NULL;
+        if (gains || phased || support >= 2) {
+            V = (double*)malloc(sizeof(double) * B * 8);
             if (gains && full_jones)
                 oracle_apply_jones(S, n_tiles, gains + (int64_t)f * n_tiles * 8, V);
             else if (gains)
                 oracle_apply_gains(S, n_tiles, gains + (int64_t)f * n_tiles * 4, V);
             else
                 for (int64_t e = 0; e < B * 8; e++) V[e] = (double)S[e];
-            W = oracle_grid_kb(V, n_tiles, flags, K, pol, autos, uvw, du, support, ng, G);
-            free(V);
-        } else if (gains) {
-            double* V = (double*)malloc(sizeof(double) * B * 8);
-            if (full_jones)
-                oracle_apply_jones(S, n_tiles, gains + (int64_t)f * n_tiles * 8, V);
-            else
-                oracle_apply_gains(S, n_tiles, gains + (int64_t)f * n_tiles * 4, V);
-            W = oracle_grid_v(V, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
-            free(V);
-        } else {
-            W = oracle_grid(S, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
+            if (phased) oracle_apply_phase(V, uvw, B);
         }
+        if (support >= 2)
+            W = oracle_grid_kb(V, n_tiles, flags, K, pol, autos, uvw, du, support, ng, G);
+        else if (V)
+            W = oracle_grid_v(V, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
+        else
+            W = oracle_grid(S, n_tiles, flags, K, pol, autos, iu, iv, keep, n_pix, G);
+        free(V);
         if (grids) memcpy(grids + q * 2 * ng * ng, G, sizeof(double) * 2 * ng * ng);
         if (oracle_ifft2(G, ng)) bad = 1;
         double mx = oracle_image(G, ng, W > 0.0 ? W : 1.0, im);

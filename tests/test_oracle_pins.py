@@ -743,3 +743,96 @@ def test_dedispersion_recovers_the_injected_dispersion_measure():
     noise = bs.image_noise(2.0, 16, 10) / math.sqrt(8)
     assert peaks[500] > 2.0 and peaks[500] > 20 * noise
     assert peaks[500] > 2 * max(v for k, v in peaks.items() if abs(k - 500) >= 200)
+
+
+# ----------------------------------------------------------------------------------------------
+# phase centre on a pointing direction (Sec. 5.2.3, geometric corrections)
+# ----------------------------------------------------------------------------------------------
+
+POINTINGS = [(0.0, 0.0), (0.2, -0.1), (-0.35, 0.25), (0.0, 0.6), (-0.7, 0.0), (1e-9, -2e-9)]
+
+
+@pytest.mark.parametrize("l0,m0", POINTINGS)
+def test_phase_basis_is_the_minimal_rotation_of_east_and_north(l0, m0):
+    # against scipy's rotation (an independent library): the rotation about Up x s0 by the angle between Up and
+    # s0 carries (E, N, Up) to (e_l, e_m, s0); the basis is orthonormal and right-handed
+    Rotation = pytest.importorskip("scipy.spatial.transform").Rotation
+    el, em, s0 = oracle.phase_basis(l0, m0)
+    n0 = math.sqrt(1 - l0 * l0 - m0 * m0)
+    assert np.allclose(s0, [l0, m0, n0], atol=0, rtol=0)
+    axis = np.cross([0.0, 0.0, 1.0], s0)
+    if np.linalg.norm(axis) > 0:
+        rot = Rotation.from_rotvec(axis / np.linalg.norm(axis) * math.atan2(math.hypot(l0, m0), n0))
+        E, N, U = rot.apply(np.eye(3))
+        assert np.allclose(el, E, atol=1e-12) and np.allclose(em, N, atol=1e-12) and np.allclose(s0, U, atol=1e-12)
+    B3 = np.array([el, em, s0])
+    assert np.allclose(B3 @ B3.T, np.eye(3), atol=1e-14)
+    assert np.allclose(np.cross(el, em), s0, atol=1e-14)
+    with pytest.raises(ValueError):
+        oracle.phase_basis(0.8, 0.6)
+
+
+def test_phased_uvw_at_zenith_is_the_plain_uvw_and_keeps_lengths():
+    enu = bs.tile_positions(20, 1500.0, 41)
+    enu[:, 2] = np.linspace(-3.0, 3.0, 20)      # some height differences
+    assert np.array_equal(oracle.uvw_phased(enu, 150e6, 0.0, 0.0), oracle.uvw(enu, 150e6))
+    a = oracle.uvw_phased(enu, 150e6, 0.3, -0.2)
+    b = oracle.uvw(enu, 150e6)
+    assert np.allclose(np.linalg.norm(a, axis=1), np.linalg.norm(b, axis=1), rtol=1e-13, atol=1e-12)
+    _, _, s0 = oracle.phase_basis(0.3, -0.2)
+    assert np.allclose(a[:, 2], b @ s0, rtol=1e-13, atol=1e-12)     # w = b.s0 nu / c
+
+
+def test_apply_phase_rotates_by_w_turns():
+    rng = np.random.default_rng(3)
+    V = rng.normal(size=(6, 4)) + 1j * rng.normal(size=(6, 4))
+    uvw = np.zeros((6, 3))
+    uvw[:, 2] = [0.0, 0.25, -0.5, 1500.125, -2750.75, 0.1]
+    got = oracle.apply_phase(V, uvw)
+    want = V * np.exp(2j * np.pi * np.array([0.0, 0.25, -0.5, 0.125, 0.25, 0.1]))[:, None]
+    assert np.allclose(got, want, rtol=0, atol=1e-14)
+
+
+def _source_voltages(enu, nu, lmn, power=20.0, n=40):
+    sky = bs.Sky(lmn=np.array([lmn]), power=np.array([power]))
+    return bs.voltages(enu, np.array([nu]), n, sky, seed=43, sigma=0.0)
+
+
+def test_phase_centred_source_lands_in_the_centre_pixel():
+    # a noiseless source at the pointing: every phase-centred visibility is its (quantised) power, so the image
+    # peaks exactly at the centre pixel with the power the autocorrelations measure (the realised signal power
+    # plus the 4-bit rounding's 1/6 per sample); without phase centring it peaks at its offset (l0, m0)
+    enu = bs.tile_positions(48, 1500.0, 44)
+    nu, n = 154.88e6, 128
+    l0, m0 = 0.02, -0.015
+    v = _source_voltages(enu, nu, [l0, m0, math.sqrt(1 - l0 * l0 - m0 * m0)])
+    out = oracle.pipeline(v, enu, np.array([nu]), 40, 1, n, phase_centre=(l0, m0))
+    img = out["images"][0]
+    y, x = np.unravel_index(np.argmax(img), img.shape)
+    assert (y, x) == (n // 2, n // 2)
+    S = oracle.correlate(v, 40, 1)[0, 0]
+    autos = np.array([(S[_bidx(i, i), 0, 0] + S[_bidx(i, i), 3, 0]) / 80.0 for i in range(48)])
+    assert abs(img[n // 2, n // 2] - autos.mean()) < 0.03 * autos.mean()
+    du = oracle.default_cell(enu, nu, n)
+    zen = oracle.pipeline(v, enu, np.array([nu]), 40, 1, n)["images"][0]
+    y, x = np.unravel_index(np.argmax(zen), zen.shape)
+    assert abs(x - (n / 2 + l0 * n * du)) <= 1 and abs(y - (n / 2 + m0 * n * du)) <= 1
+
+
+def test_offset_source_peaks_at_its_tangent_plane_coordinates():
+    # pointing (l0, m0) far from zenith, source a little off it: the peak sits at (s.e_l, s.e_m) in the image
+    # plane of the pointing, i.e. pixel (N/2 + (s.e_l) N du, N/2 + (s.e_m) N du)
+    enu = bs.tile_positions(48, 1500.0, 45)
+    nu, n = 154.88e6, 128
+    l0, m0 = 0.3, 0.2
+    el, em, s0 = oracle.phase_basis(l0, m0)
+    du = oracle.default_cell(enu, nu, n, phase_centre=(l0, m0))
+    fov = 1.0 / du
+    off = np.array([0.21 * fov, -0.13 * fov])
+    s = s0 + off[0] * el + off[1] * em
+    s /= np.linalg.norm(s)
+    v = _source_voltages(enu, nu, s)
+    img = oracle.pipeline(v, enu, np.array([nu]), 40, 1, n, phase_centre=(l0, m0))["images"][0]
+    y, x = np.unravel_index(np.argmax(img), img.shape)
+    assert abs(x - (n / 2 + (s @ el) * n * du)) <= 1
+    assert abs(y - (n / 2 + (s @ em) * n * du)) <= 1
