@@ -64,6 +64,8 @@ def parse():
                     help="apply seeded full 2x2 Jones matrices (30 %% leakage) in the correlation")
     ap.add_argument("--support", type=int, default=0,
                     help="gridding kernel width in cells: Kaiser-Bessel on a grid of twice the image side; 0 = nearest cell")
+    ap.add_argument("--pointing", type=float, nargs=2, default=(0.0, 0.0), metavar=("L", "M"),
+                    help="phase centre: direction cosines in the local East, North, Up frame (default zenith)")
     ap.add_argument("--gains", action="store_true",
                     help="apply seeded per-channel, per-tile, per-polarisation calibration gains in the correlation")
     return ap.parse_args()
@@ -204,7 +206,7 @@ def bench_jones(n_out_chan: int, n_tiles: int) -> np.ndarray:
     return (np.eye(2) + 0.3 * z).astype(np.complex64)
 
 
-def oracle_sets_images(oracle, inp, w, sets, picks, threads, gains=None, support=0):
+def oracle_sets_images(oracle, inp, w, sets, picks, threads, gains=None, support=0, pointing=(0.0, 0.0)):
     """The oracle's images for the picked (set index, local image id) pairs, in order."""
     out = []
     for q, (st, _, _, side) in enumerate(sets):
@@ -214,6 +216,8 @@ def oracle_sets_images(oracle, inp, w, sets, picks, threads, gains=None, support
         kw = {} if len(sets) == 1 else {"flags": st.flags, "fine0": st.fine0, "n_fine": st.n_fine}
         if support:
             kw["support"] = support
+        if tuple(pointing) != (0.0, 0.0):
+            kw["phase_centre"] = tuple(pointing)
         if gains is not None:
             f0 = st.fine0 // w.chan_avg
             kw["gains"] = gains[f0:f0 + st.n_fine // w.chan_avg].astype(np.complex128)
@@ -259,7 +263,7 @@ def run_reference(args, world, rank):
         t = time.perf_counter()
         cal = (bench_jones(w.n_out_chan, w.n_tiles) if args.jones else
                bench_gains(w.n_out_chan, w.n_tiles) if args.gains else None)
-        oracle_sets_images(oracle, inp, w, sets, sel, cores, cal, args.support)
+        oracle_sets_images(oracle, inp, w, sets, sel, cores, cal, args.support, args.pointing)
         dt = time.perf_counter() - t
         if s_ >= args.warmup:
             times.append((len(sel), dt))
@@ -271,7 +275,8 @@ def run_reference(args, world, rank):
         "warmup": args.warmup, "ms_per_step": 1e3 * tt / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
         "config": {"workload": workload_label(args.workload, w), "images_per_step": n_per,
-                   "sample": "evenly spaced image ids of the chunk", "support": args.support},
+                   "sample": "evenly spaced image ids of the chunk", "support": args.support,
+                   "pointing": list(args.pointing)},
         "cpu_baseline": {"value": v, "unit": "images/s", "cores": cores, "kind": "oracle",
                          "sample": f"{n_per} images per step, ids evenly spaced over the {n_total}-image chunk"},
         "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -321,8 +326,10 @@ def run_ours(args, world, rank, local):
     jones = bench_jones(w.n_out_chan, n_tiles) if args.jones else None
     arr = B.Array(inp["enu"], None, gains, jones)
     obs = B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns)
-    im = B.Imaging(n_pix, precision=prec, support=args.support)
-    bsets = [B.Set(fine0=st.fine0, n_fine=st.n_fine, imaging=B.Imaging(side, precision=prec, support=args.support),
+    pc = tuple(args.pointing)
+    im = B.Imaging(n_pix, precision=prec, support=args.support, phase_centre=pc)
+    bsets = [B.Set(fine0=st.fine0, n_fine=st.n_fine,
+                   imaging=B.Imaging(side, precision=prec, support=args.support, phase_centre=pc),
                    flags=st.flags) for st, _, _, side in sets]
     stream = torch.cuda.current_stream()
     volt = torch.from_numpy(inp["volt"]).cuda()
@@ -422,7 +429,7 @@ def run_ours(args, world, rank, local):
         picks = pick_images(sets, n_s)
         t = time.perf_counter()
         refs = oracle_sets_images(oracle, inp, w, sets, picks, cores, jones if jones is not None else gains,
-                                  args.support)
+                                  args.support, args.pointing)
         dt = time.perf_counter() - t
         flat = img.reshape(-1)
         got = []
@@ -532,7 +539,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": workload_label(args.workload, w),
                    "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
                    "mode": args.mode, "precision": args.precision, "gains": bool(args.gains),
-                   "jones": bool(args.jones), "support": args.support,
+                   "jones": bool(args.jones), "support": args.support, "pointing": list(args.pointing),
                    "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
                           "each step timed alone after a 516 MB buffer overwrite") if small else
                          (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e9:.3g} GB per step exceed L2; "

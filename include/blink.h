@@ -111,6 +111,15 @@ typedef struct {
                                    The default cell is then u_max / (n_pix - 1 - W/2).  Batched pipeline
                                    forms only (blink_pipeline BATCHED, blink_pipeline_sets,
                                    blink_pipeline_host); the stage calls return BLINK_ERR_UNSUPPORTED. */
+    double phase_l, phase_m;    /* phase centre (Sec. 5.2.3, geometric corrections): the pointing's direction
+                                   cosines (l0, m0) in the local East, North, Up frame, l0^2 + m0^2 < 1;
+                                   (0, 0) = zenith.  (u, v, w) are taken in the pointing's basis (East and
+                                   North carried to it by the rotation about Up x s0 that takes Up to it),
+                                   every visibility is multiplied by exp(+2 pi i w) before gridding, so a
+                                   source at the pointing images at pixel (N/2, N/2); the default cell uses
+                                   the baselines projected on that basis.  A new pointing builds a new plan.
+                                   blink_grid returns BLINK_ERR_UNSUPPORTED off zenith (its visibilities are
+                                   the caller's); blink_image ignores the pointing. */
 } blink_imaging;
 
 /*

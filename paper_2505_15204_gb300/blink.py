@@ -64,7 +64,8 @@ class blink_obs(C.Structure):
 
 class blink_imaging(C.Structure):
     _fields_ = [("n_pix", C.c_int32), ("cell_lambda", C.c_double), ("pol", C.c_int32),
-                ("include_autos", C.c_int32), ("precision", C.c_int32), ("support", C.c_int32)]
+                ("include_autos", C.c_int32), ("precision", C.c_int32), ("support", C.c_int32),
+                ("phase_l", C.c_double), ("phase_m", C.c_double)]
 
 
 class blink_set(C.Structure):
@@ -179,10 +180,12 @@ class Imaging:
     include_autos: int = 1
     precision: int = BLINK_PREC_FP32
     support: int = 0                     # 0: nearest cell; W >= 2: Kaiser-Bessel kernel of W cells
+    phase_centre: tuple = (0.0, 0.0)     # pointing (l0, m0) in the local East, North, Up frame; (0, 0) = zenith
 
     def c(self):
+        l0, m0 = self.phase_centre
         return blink_imaging(self.n_pix, self.cell_lambda, self.pol, self.include_autos, self.precision,
-                             self.support)
+                             self.support, float(l0), float(m0))
 
 
 def _ref(x):

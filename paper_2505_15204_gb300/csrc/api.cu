@@ -89,6 +89,40 @@ blink_status check_imaging(const blink_imaging* im) {
         return set_error(BLINK_ERR_INVALID_ARG, "imaging.support must be 0 or 1 (nearest cell) or a kernel width in [2, 16]");
     if (im->support >= 2 && n > 1024)
         return set_error(BLINK_ERR_UNSUPPORTED, "with a convolution kernel imaging.n_pix is at most 1024 (grid side 2 n_pix)");
+    if (!std::isfinite(im->phase_l) || !std::isfinite(im->phase_m) ||
+        !(im->phase_l * im->phase_l + im->phase_m * im->phase_m < 1.0))
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.phase_l, phase_m must be direction cosines with l^2 + m^2 < 1");
+    return BLINK_OK;
+}
+
+bool off_zenith(const blink_imaging* im) { return im && (im->phase_l != 0.0 || im->phase_m != 0.0); }
+
+// The pointing's basis (Sec. 5.2.3): e_l, e_m = East and North carried to s0 = (l0, m0, n0) by the rotation
+// about Up x s0 that takes Up to s0 (Rodrigues' formula); e[0..2] = e_l, e[3..5] = e_m, e[6..8] = s0.
+void pointing_basis(double l0, double m0, double* e) {
+    const double r2 = l0 * l0 + m0 * m0, n0 = std::sqrt(1.0 - r2);
+    e[6] = l0;
+    e[7] = m0;
+    e[8] = n0;
+    if (r2 == 0.0) {
+        const double id[6] = {1, 0, 0, 0, 1, 0};
+        for (int k = 0; k < 6; k++) e[k] = id[k];
+        return;
+    }
+    const double r = std::sqrt(r2), kx = -m0 / r, ky = l0 / r, c1 = 1.0 - n0;
+    e[0] = n0 + kx * kx * c1;
+    e[1] = kx * ky * c1;
+    e[2] = -ky * r;
+    e[3] = kx * ky * c1;
+    e[4] = n0 + ky * ky * c1;
+    e[5] = kx * r;
+}
+
+// blink_grid grids the caller's visibilities as they are: no phase centre.
+blink_status zenith_only(const blink_imaging* im, const char* what) {
+    if (off_zenith(im))
+        return set_error(BLINK_ERR_UNSUPPORTED, std::string(what) + ": an off-zenith phase centre runs in the "
+                                                "pipeline forms only");
     return BLINK_OK;
 }
 
@@ -131,6 +165,7 @@ void free_plan(Plan* p) {
     cudaFree(p->d_tw);
     cudaFree(p->d_wt);
     cudaFree(p->d_corr);
+    cudaFree(p->d_phase);
     delete p;
 }
 
@@ -148,13 +183,19 @@ std::vector<double> output_freqs(const blink_obs* o) {
 
 // Default uv cell: u_max / (N/2 - 1), u_max = longest unflagged projected baseline * nu_max / c, for a grid of
 // side N; with a kernel of W cells the support must stay inside the grid too: u_max / (N/2 - 1 - W/2).
-double default_cell(const blink_array* a, double nu_max, int n_pix, int support) {
+// Off zenith the baselines are projected on the pointing's (e_l, e_m) (`basis`, NULL at zenith).
+double default_cell(const blink_array* a, double nu_max, int n_pix, int support, const double* basis) {
     double dmax = 0.0;
     for (int i = 0; i < a->n_tiles; i++)
         for (int j = 0; j < i; j++) {
             if (a->flags && (a->flags[i] || a->flags[j])) continue;
-            const double be = a->enu_m[i * 3 + 0] - a->enu_m[j * 3 + 0];
-            const double bn = a->enu_m[i * 3 + 1] - a->enu_m[j * 3 + 1];
+            double be = a->enu_m[i * 3 + 0] - a->enu_m[j * 3 + 0];
+            double bn = a->enu_m[i * 3 + 1] - a->enu_m[j * 3 + 1];
+            if (basis) {
+                const double bu = a->enu_m[i * 3 + 2] - a->enu_m[j * 3 + 2], bx = be, by = bn;
+                be = bx * basis[0] + by * basis[1] + bu * basis[2];
+                bn = bx * basis[3] + by * basis[4] + bu * basis[5];
+            }
             const double d = std::sqrt(be * be + bn * bn);
             if (d > dmax) dmax = d;
         }
@@ -526,6 +567,8 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         h.val(im->pol);
         h.val(im->include_autos != 0);
         h.val(im->support >= 2 ? im->support : 0);
+        h.val(im->phase_l);
+        h.val(im->phase_m);
         h.val(need_gather);
     } else {
         h.val(o->n_fine / o->chan_avg);
@@ -579,7 +622,10 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         p->out_freq = output_freqs(o);
         double numax = p->out_freq[0];
         for (double f : p->out_freq) numax = std::max(numax, f);
-        p->du = im->cell_lambda > 0.0 ? im->cell_lambda : default_cell(a, numax, p->N, p->support);
+        p->phased = off_zenith(im);
+        if (p->phased) pointing_basis(im->phase_l, im->phase_m, p->basis);
+        p->du = im->cell_lambda > 0.0 ? im->cell_lambda
+                                      : default_cell(a, numax, p->N, p->support, p->phased ? p->basis : nullptr);
         if ((s = dmalloc(&p->d_enu, 3 * a->n_tiles)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_freq, p->F)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_cells, (size_t)p->F * p->B)) != BLINK_OK) return fail(s);
@@ -593,6 +639,7 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         // with a kernel the gather list is built from the exact (u, v), kept on the device only meanwhile
         const bool kb = p->support && need_gather;
         if (kb && (s = dmalloc(&p->d_uvw, (size_t)p->F * p->B * 3)) != BLINK_OK) return fail(s);
+        if (p->phased && need_gather && (s = dmalloc(&p->d_phase, (size_t)p->F * p->B)) != BLINK_OK) return fail(s);
         launch_cells(*p, st);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -674,6 +721,7 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
             else
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
                                            ctx->d_status, st, gains));
+            BLINK_TRY(launch_phase_vis(static_cast<float2*>(vis), p.B, p, first, n_items, st));
         }
         if (!p.tuned && !may_tune) {
             // output over the host link: timings would measure the link, so run the default shape untuned
@@ -879,6 +927,7 @@ blink_status blink_cells(blink_context* ctx, const blink_array* array, const bli
     Plan q = *p;                   // same geometry inputs, caller's output buffers
     q.d_cells = reinterpret_cast<uint32_t*>(d_cells);
     q.d_uvw = d_uvw;
+    q.d_phase = nullptr;
     launch_cells(q, st);
     BLINK_CUDA(cudaGetLastError());
     if (h_du) *h_du = p->du;
@@ -918,6 +967,7 @@ blink_status blink_grid(blink_context* ctx, const blink_array* array, const blin
     BLINK_TRY(check_obs(obs, true));
     BLINK_TRY(check_imaging(imaging));
     BLINK_TRY(nearest_only(imaging, "blink_grid"));
+    BLINK_TRY(zenith_only(imaging, "blink_grid"));
     if (!d_vis || !d_grid) return set_error(BLINK_ERR_INVALID_ARG, "d_vis or d_grid is NULL");
     if (first_image < 0 || n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "negative image range");
     if (((uintptr_t)d_vis & 7) || ((uintptr_t)d_grid & 7))
@@ -1011,6 +1061,7 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
             else
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B,
                                            ctx->d_status, st, g));
+            BLINK_TRY(launch_phase_vis(static_cast<float2*>(vis), p->B, *p, id, 1, st));
             BLINK_CUDA(cudaMemsetAsync(grid, 0, (size_t)N * (N / 2 + 1) * sizeof(float2), st));
             BLINK_TRY(launch_grid_atomic(*p, static_cast<float2*>(vis), id, static_cast<float2*>(grid), st));
             BLINK_TRY(launch_colpass_grid(N, imaging->precision, p->d_tw, static_cast<float2*>(grid), 1, H, ldh, st));

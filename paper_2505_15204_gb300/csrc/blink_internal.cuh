@@ -51,6 +51,8 @@ struct Plan {
     mutable float tune_ms = 0.f;           // time of the chosen shape on the tuning call
     int n_tiles = 0, n_fine = 0, chan_avg = 1, F = 0, N = 0, pol = 0, autos = 1;
     int support = 0;                       // convolution kernel width in cells (0: nearest cell)
+    bool phased = false;                   // off-zenith phase centre
+    double basis[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};   // e_l, e_m, s0 of the pointing in (E, N, Up)
     int Ni = 0;                            // image side: N, or N / 2 with a kernel (grid side N = 2 Ni)
     int64_t B = 0;
     int cw = 16, n_cb = 0;                 // column-block width and count of the u >= 0 half plane
@@ -72,6 +74,7 @@ struct Plan {
     float* d_Wk = nullptr;                 // [F] W times the divisor of the correlator's raw sums (2K or K)
     float2* d_tw = nullptr;                // twiddle set of side N (tws_total(N) entries)
     double* d_uvw = nullptr;               // [F][B][3] (kept for blink_cells)
+    float2* d_phase = nullptr;             // [F][B] exp(+2 pi i w) of an off-zenith phase centre, else NULL
 };
 
 struct Workspace {
@@ -114,6 +117,8 @@ struct StageTimer {
 
 // ---- kernel launchers (defined next to their kernels) --------------------------------------------
 void launch_cells(const Plan& p, cudaStream_t st);
+// vis[i][b] *= phase[(first + i) % F][b] for the n_items items of a correlation workspace of row stride ld.
+blink_status launch_phase_vis(float2* vis, int64_t ld, const Plan& p, int first, int n_items, cudaStream_t st);
 // Calibration of a correlation launch: complex float [channels][n_tiles][2 pol] gains, or (full) complex
 // [channels][n_tiles][2][2] Jones matrices J[p][r], on the device; item channel f uses row f0 + f.
 // d == NULL: none.

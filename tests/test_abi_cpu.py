@@ -51,8 +51,8 @@ def test_struct_layout_matches_header(lib_path):
     from paper_2505_15204_gb300 import blink as B
     assert ctypes.sizeof(B.blink_array) == 40
     assert ctypes.sizeof(B.blink_obs) == 32
-    assert ctypes.sizeof(B.blink_imaging) == 32
-    assert ctypes.sizeof(B.blink_set) == 48
+    assert ctypes.sizeof(B.blink_imaging) == 48
+    assert ctypes.sizeof(B.blink_set) == 64
 
 
 C_CHECK = r"""
@@ -72,6 +72,7 @@ int main(void) {
     OFF(blink_obs, samples_per_int); OFF(blink_obs, n_samples);
     OFF(blink_imaging, n_pix); OFF(blink_imaging, cell_lambda); OFF(blink_imaging, pol);
     OFF(blink_imaging, include_autos); OFF(blink_imaging, precision); OFF(blink_imaging, support);
+    OFF(blink_imaging, phase_l); OFF(blink_imaging, phase_m);
     OFF(blink_set, fine0); OFF(blink_set, n_fine); OFF(blink_set, flags); OFF(blink_set, imaging);
     printf("baselines %lld\n", (long long)blink_n_baselines(144));
     /* an argument error is returned before any device work: no context */

@@ -101,24 +101,29 @@ def test_correlate_sub_band_with_fine_stride(B, ctx):
 # geometry
 # ---------------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name,n_pix,fine,c,flags", [("tiny", 256, None, 1, False), ("precision", 512, None, 1, False),
-                                                     ("coarse", 512, 128, 4, False), ("uneven", 1024, 8, 1, True)])
-def test_cells_and_uvw_bit_exact(B, ctx, name, n_pix, fine, c, flags):
+@pytest.mark.parametrize("name,n_pix,fine,c,flags,pc", [("tiny", 256, None, 1, False, (0.0, 0.0)),
+                                                        ("precision", 512, None, 1, False, (0.0, 0.0)),
+                                                        ("coarse", 512, 128, 4, False, (0.0, 0.0)),
+                                                        ("uneven", 1024, 8, 1, True, (0.0, 0.0)),
+                                                        ("precision", 512, None, 1, False, (0.31, -0.22)),
+                                                        ("uneven", 256, 8, 1, True, (-0.05, 0.4))])
+def test_cells_and_uvw_bit_exact(B, ctx, name, n_pix, fine, c, flags, pc):
+    # off zenith: (u, v, w) on the pointing's basis and the default cell over the projected baselines
     w, volt, freqs, fl = _case(name, 10, fine, flags)
     arr = B.Array(w["enu"], fl)
     F = len(freqs) // c
     nb = B.blink_n_baselines(w["enu"].shape[0])
     cells = torch.empty((F, nb), dtype=torch.int32, device="cuda")
     uvw = torch.empty((F, nb, 3), dtype=torch.float64, device="cuda")
-    du = B.blink_cells(ctx, arr, B.Obs(freqs, c, 10, 10), B.Imaging(n_pix), cells, uvw)
+    du = B.blink_cells(ctx, arr, B.Obs(freqs, c, 10, 10), B.Imaging(n_pix, phase_centre=pc), cells, uvw)
     B.blink_sync(ctx)
     fout = oracle.output_freqs(freqs, c)
-    du_ref = oracle.default_cell(w["enu"], fout.max(), n_pix, flags=fl)
+    du_ref = oracle.default_cell(w["enu"], fout.max(), n_pix, flags=fl, phase_centre=pc)
     assert du == du_ref
     got_c = cells.cpu().numpy().view(np.uint32)
     got_uvw = uvw.cpu().numpy()
     for f in range(F):
-        uv = oracle.uvw(w["enu"], fout[f])
+        uv = oracle.uvw_phased(w["enu"], fout[f], *pc)
         assert np.array_equal(got_uvw[f], uv)
         iu, iv, keep = oracle.cells(uv, du_ref, n_pix)
         if fl is not None:
@@ -744,3 +749,50 @@ def test_dedispersion_recovers_the_injected_dispersion_measure(B, ctx):
     ref_img = oracle.pipeline(volt, enu, freqs, 10, 1, n, n_threads=8)["images"].reshape(T, F, n, n)
     ref = oracle.dedisperse(ref_img, pins._delays(freqs, 500))
     assert rel_rms(out500, ref) <= IMG_RTOL
+
+
+# ---------------------------------------------------------------------------------------------------
+# phase centre on an off-zenith pointing (geometric corrections)
+# ---------------------------------------------------------------------------------------------------
+
+PC_CASES = [
+    # name, n_samples, fine, chan_avg, n_pix, support, pointing, mode
+    ("coarse", 20, 8, 4, 256, 0, (0.31, -0.22), 0),
+    ("precision", None, None, 1, 512, 0, (-0.05, 0.4), 0),
+    ("uneven", 20, 3, 1, 128, 0, (0.2, 0.1), 1),
+    ("coarse", 20, 8, 2, 128, 6, (0.31, -0.22), 0),
+]
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp32", "fp8"])
+@pytest.mark.parametrize("case", PC_CASES, ids=[f"{c[0]}-{c[4]}-W{c[5]}-{'plain' if c[7] else 'batched'}" for c in PC_CASES])
+def test_phase_centred_pipeline_matches_oracle(B, ctx, case, arith):
+    name, ns_total, fine, c, n_pix, W, pc, mode = case
+    w, volt, freqs, fl = _case(name, ns_total, fine, name == "uneven")
+    T = volt.shape[0] // 10
+    F = len(freqs) // c
+    img = torch.full((T * F, n_pix, n_pix), float("nan"), dtype=torch.float32, device="cuda")
+    wts = torch.empty(T * F, dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"], fl), B.Obs(freqs, c, 10, volt.shape[0]),
+                     B.Imaging(n_pix, support=W, phase_centre=pc), arith, mode, dev(volt), img, wts)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, c, n_pix, flags=fl, n_threads=8, support=W, phase_centre=pc)
+    got = img.cpu().numpy()
+    for q in range(T * F):
+        err = rel_rms(got[q], ref["images"][q])
+        assert err <= IMG_RTOL, (q, err)
+        assert wts[q].item() == ref["W"][q]
+
+
+def test_source_at_the_pointing_images_at_the_centre_pixel(B, ctx):
+    enu = bs.tile_positions(48, 1500.0, 44)
+    nu, n = 154.88e6, 128
+    l0, m0 = 0.02, -0.015
+    sky = bs.Sky(lmn=np.array([[l0, m0, np.sqrt(1 - l0 * l0 - m0 * m0)]]), power=np.array([20.0]))
+    v = bs.voltages(enu, np.array([nu]), 40, sky, seed=43, sigma=0.0)
+    img = torch.empty((1, n, n), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(enu), B.Obs(np.array([nu]), 1, 40, 40), B.Imaging(n, phase_centre=(l0, m0)), 1,
+                     0, dev(v), img)
+    B.blink_sync(ctx)
+    got = img[0].cpu().numpy()
+    assert np.unravel_index(np.argmax(got), got.shape) == (n // 2, n // 2)

@@ -176,3 +176,16 @@ def test_convolution_kernel_options():
     _expect(*NO_CTX, B.blink_pipeline_sets, None, a, o, [B.Set(0, 2, k), B.Set(2, 2, B.Imaging(64))], 0, PTR, PTR,
             2 * 2 * 64 * 64)
     _expect(*NO_CTX, B.blink_pipeline_host, None, a, o, k, 0, np.zeros(4, np.uint8), np.zeros(4, np.float32), 0)
+
+
+def test_phase_centre_options():
+    a, o = B.Array(_enu()), _obs()
+    for pc in ((0.8, 0.6), (1.0, 0.0), (float("nan"), 0.0), (0.0, float("inf"))):
+        _expect(B.BLINK_ERR_INVALID_ARG, "direction cosines", B.blink_pipeline, None, a, o,
+                B.Imaging(64, phase_centre=pc), 0, 0, PTR, PTR)
+    k = B.Imaging(64, phase_centre=(0.3, -0.2))
+    for mode in (B.BLINK_MODE_BATCHED, B.BLINK_MODE_PLAIN):
+        _expect(*NO_CTX, B.blink_pipeline, None, a, o, k, 0, mode, PTR, PTR)
+    _expect(*NO_CTX, B.blink_cells, None, a, o, k, PTR)
+    _expect(*NO_CTX, B.blink_image, None, k, PTR, 0, PTR, PTR)          # the image stage ignores the pointing
+    _expect(B.BLINK_ERR_UNSUPPORTED, "pipeline forms only", B.blink_grid, None, a, o, k, PTR, 0, 1, PTR)
