@@ -796,3 +796,31 @@ def test_source_at_the_pointing_images_at_the_centre_pixel(B, ctx):
     B.blink_sync(ctx)
     got = img[0].cpu().numpy()
     assert np.unravel_index(np.argmax(got), got.shape) == (n // 2, n // 2)
+
+
+@pytest.mark.parametrize("n_tiles,ns,c,const", [(16, 200, 4, False), (8, 10000, 4, False), (8, 10000, 4, True)])
+def test_long_integrations_exact_on_the_cuda_core_form(B, ctx, n_tiles, ns, c, const):
+    # K = 800 and 40,000 (20 ms and 1 s of 10 kHz channels averaged by 4): the CUDA-core form stays bit-exact
+    # (|S| <= 128 K < 2^24, reached by constant -8 - 8i voltages); the tensor-core form, which stages all of K
+    # in shared memory, reports UNSUPPORTED
+    enu = bs.tile_positions(n_tiles, 1500.0, 51)
+    freqs = 155e6 + 10e3 * np.arange(c)
+    if const:
+        v = bs.constant_voltages(ns, c, n_tiles, -8, -8)
+    else:
+        sky = bs.Sky(lmn=np.array([[0.1, 0.05, np.sqrt(1 - 0.0125)]]), power=np.array([4.0]))
+        v = bs.voltages(enu, freqs, ns, sky, seed=52)
+    S = oracle.correlate(v, ns, c)
+    want = oracle.visibilities(S, ns * c)
+    if const:
+        assert np.all(S[..., 0, 0] == ns * c * 128)
+    out = torch.empty(S.shape, dtype=torch.float32, device="cuda")
+    arr, obs = B.Array(enu), B.Obs(freqs, c, ns, ns)
+    B.blink_correlate(ctx, arr, obs, 0, dev(v), out)
+    B.blink_sync(ctx)
+    got = out.cpu().numpy()
+    assert np.array_equal(got[..., 0], want.real.astype(np.float32))
+    assert np.array_equal(got[..., 1], want.imag.astype(np.float32))
+    with pytest.raises(B.BlinkError) as e:
+        B.blink_correlate(ctx, arr, obs, 1, dev(v), out)
+    assert e.value.status == B.BLINK_ERR_UNSUPPORTED
