@@ -836,3 +836,17 @@ def test_offset_source_peaks_at_its_tangent_plane_coordinates():
     y, x = np.unravel_index(np.argmax(img), img.shape)
     assert abs(x - (n / 2 + (s @ el) * n * du)) <= 1
     assert abs(y - (n / 2 + (s @ em) * n * du)) <= 1
+
+
+def test_phase_centre_and_kernel_together_keep_the_source_at_the_centre():
+    # the kernel spreads the phase-centred visibilities at their exact (u, v) on the pointing's basis: a source
+    # at the pointing still peaks at the centre pixel, with the autocorrelations' measured power
+    enu = bs.tile_positions(48, 1500.0, 44)
+    nu, n = 154.88e6, 128
+    l0, m0 = 0.02, -0.015
+    v = _source_voltages(enu, nu, [l0, m0, math.sqrt(1 - l0 * l0 - m0 * m0)])
+    img = oracle.pipeline(v, enu, np.array([nu]), 40, 1, n, phase_centre=(l0, m0), support=6)["images"][0]
+    assert np.unravel_index(np.argmax(img), img.shape) == (n // 2, n // 2)
+    S = oracle.correlate(v, 40, 1)[0, 0]
+    autos = np.array([(S[_bidx(i, i), 0, 0] + S[_bidx(i, i), 3, 0]) / 80.0 for i in range(48)])
+    assert abs(img[n // 2, n // 2] - autos.mean()) < 0.03 * autos.mean()
