@@ -850,3 +850,13 @@ def test_phase_centre_and_kernel_together_keep_the_source_at_the_centre():
     S = oracle.correlate(v, 40, 1)[0, 0]
     autos = np.array([(S[_bidx(i, i), 0, 0] + S[_bidx(i, i), 3, 0]) / 80.0 for i in range(48)])
     assert abs(img[n // 2, n // 2] - autos.mean()) < 0.03 * autos.mean()
+
+
+def test_mean_of_short_integrations_is_the_long_integration_image():
+    # gridding and the transform are linear with fixed cells and weights: the mean of four 1 ms images of a
+    # channel equals the image of the 4 ms integration (time averaging needs no kernel of its own)
+    w = bs.build_workload("coarse", n_samples=40)
+    volt, freqs = w["volt"][:, :2], w["freqs"][:2]
+    short = oracle.pipeline(volt, w["enu"], freqs, 10, 1, 64)["images"].reshape(4, 2, 64, 64)
+    long_ = oracle.pipeline(volt, w["enu"], freqs, 40, 1, 64)["images"]
+    assert np.allclose(short.mean(axis=0), long_, rtol=0, atol=1e-12 * np.abs(long_).max())
