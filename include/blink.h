@@ -152,7 +152,9 @@ int64_t blink_n_baselines(int32_t n_tiles);
  * Baseline geometry (Sec. 5.2.3, geometric correction "implemented in the imaging library", and the
  * (u, v, w) computation of Sec. 5.2.4), in FP64 on the GPU: for every output channel f (centre = mean of
  * its chan_avg fine-channel centres) and baseline b, (u, v, w) = (r_i - r_j) * (nu_f / c) and the
- * nearest uv cell (iu, iv) = floor((u, v) / du + 1/2).
+ * nearest uv cell (iu, iv) = floor((u, v) / du + 1/2).  Off zenith (imaging.phase_l, phase_m) the
+ * components are taken on the pointing's basis: u = (r_i - r_j).e_l nu_f / c, v = (...).e_m nu_f / c,
+ * w = (...).s0 nu_f / c.  A gridding kernel (imaging.support >= 2) is rejected (BLINK_ERR_UNSUPPORTED).
  *   d_cells  int32 [F][B]: (iu & 0xFFFF) | (iv << 16) for a gridded baseline, or 0x80008000 when the
  *            baseline is flagged or falls outside |iu|, |iv| < N/2.
  *   d_uvw    double [F][B][3] or NULL.
