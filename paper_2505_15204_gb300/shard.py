@@ -9,10 +9,14 @@ from __future__ import annotations
 
 
 def chunks_for_rank(n_chunks: int, rank: int, world: int, first: int = 0) -> list:
-    """Chunk indices imaged by `rank`: first + rank, first + rank + world, ... (mod n_chunks)."""
-    if world < 1 or not 0 <= rank < world:
-        raise ValueError("bad rank / world")
-    return [(first + c) % n_chunks for c in range(rank, n_chunks, world)]
+    """Chunk indices imaged by `rank`: first + rank, first + rank + world, ... (mod n_chunks).
+
+    With more ranks than chunks, a rank left without a chunk images chunk (first + rank) mod n_chunks as a
+    replica, so that every rank does one chunk's work (weak scaling)."""
+    if world < 1 or not 0 <= rank < world or n_chunks < 1:
+        raise ValueError("bad rank / world / chunk count")
+    mine = [(first + c) % n_chunks for c in range(rank, n_chunks, world)]
+    return mine or [(first + rank) % n_chunks]
 
 
 def max_over_ranks(value: float, dist=None, device=None) -> float:
