@@ -54,7 +54,7 @@ def test_partition_covers_every_chunk_once():
         chunks_for_rank(4, 2, 2)
     # more ranks than chunks: every rank still images one chunk (replicas of the single-chunk workloads)
     assert [chunks_for_rank(1, r, 4) for r in range(4)] == [[0], [0], [0], [0]]
-    assert [chunks_for_rank(3, r, 4, first=1) for r in range(4)] == [[1], [2], [0], [2]]
+    assert [chunks_for_rank(3, r, 4, first=1) for r in range(4)] == [[1], [2], [0], [1]]
     assert job_rate(100, 4, 2.0) == 200.0
 
 
