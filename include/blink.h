@@ -19,6 +19,9 @@
  *   error message.
  * - A context is used by one host thread at a time, and its calls share its device workspace: calls on
  *   different streams must be ordered between those streams (an event), or use separate contexts.
+ * - One device per process: kernel attributes (shared-memory limits, occupancy) are set once per process
+ *   for the first device that launches them, so contexts on several GPUs need one process each (the
+ *   library's multi-GPU model: one process per GPU, sharding by chunk).
  * - The library allocates device memory only inside the context: per-configuration plans (cell maps,
  *   gather lists) on first use, and workspace that grows to the largest request seen.  A repeated call
  *   with the same configuration allocates nothing.
