@@ -4,7 +4,8 @@ blink_image_noalloc serves callers that cannot allocate device memory during ima
 pipeline that reserved its memory up front, or an application whose memory belongs to another
 allocator).  It uses a static scratch array shared by all calls, so this test calls it twice in a row with
 different grids and checks each result against blink_image within the imaging-stage tolerance.  The file
-is named to be collected last.
+is named to be collected after the core parity suite (its graph captures run before the static scratch
+exists).
 """
 import numpy as np
 import pytest
