@@ -285,8 +285,12 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
  *   BLINK_PREC_FP32 storage and up to 2048 with BLINK_PREC_BF16; a larger side returns
  *   BLINK_ERR_UNSUPPORTED before anything is launched.  Every call rewrites the parts of the scratch it
  *   reads, so nothing needs clearing between calls.
- *   Set-up: the first call on a device looks up the scratch's device address (cudaGetSymbolAddress)
- *   with that device current; make that first call before any stream capture.
+ *   Set-up: the first call on a device - n_images == 0 included, which does nothing else - looks up the
+ *   scratch's device address (cudaGetSymbolAddress) with that device current.  The 16 MiB are committed
+ *   when the library's module for this entry point loads on the device; under CUDA's lazy module
+ *   loading (the default) that is this first lookup, which can therefore fail for lack of device memory.
+ *   Make that first call (a zero-image call is a warm-up) before reserving the rest of the device's
+ *   memory and before any stream capture.
  *   All calls share the one scratch array: calls whose work overlaps on the GPU (different streams,
  *   or different host threads) race and corrupt each other's images.  Order them on one stream.
  */
@@ -312,6 +316,18 @@ enum {
  */
 blink_status blink_set_profiling(blink_context* ctx, int32_t enable);
 blink_status blink_read_profile(blink_context* ctx, void* stream, double* ms, int64_t* launches, int32_t reset);
+
+/*
+ * Bounded device-side waits of the batched imaging kernel (a library service; the paper has no
+ * counterpart).  The kernel's tasks wait for one another through per-image counters; each wait gives up
+ * after `budget_cycles` SM clock cycles (default about one second; budget_cycles <= 0 restores it),
+ * records BLINK_ERR_TIMEOUT in the context's status word and stops the launch, which then returns; the
+ * next blink_sync() reports BLINK_ERR_TIMEOUT.  With `unreachable` non-zero the row tasks wait for one
+ * more column task than an image has, so each of those waits runs out on purpose: this is how a test
+ * exercises the failure path without a GPU fault or hang.  The images of a launch that ran out are
+ * invalid.  The setting holds for later calls of the context until changed.
+ */
+blink_status blink_set_wait_budget(blink_context* ctx, int64_t budget_cycles, int32_t unreachable);
 
 #ifdef __cplusplus
 }

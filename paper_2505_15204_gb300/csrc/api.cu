@@ -25,6 +25,35 @@ blink_status cuda_error(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? BLINK_ERR_OOM : BLINK_ERR_CUDA;
 }
 
+// Argument checks shared by the entry points (also used by blink_image_noalloc).
+blink_status check_imaging(const blink_imaging* im) {
+    if (!im) return set_error(BLINK_ERR_INVALID_ARG, "imaging descriptor is NULL");
+    const int n = im->n_pix;
+    if (n < 64 || n > 2048 || (n & (n - 1)))
+        return set_error(BLINK_ERR_UNSUPPORTED, "imaging.n_pix must be a power of two in [64, 2048]");
+    if (im->pol != BLINK_POL_I && im->pol != BLINK_POL_XX)
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.pol must be BLINK_POL_I or BLINK_POL_XX");
+    if (im->precision != BLINK_PREC_FP32 && im->precision != BLINK_PREC_BF16)
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.precision must be BLINK_PREC_FP32 or BLINK_PREC_BF16");
+    if (!std::isfinite(im->cell_lambda)) return set_error(BLINK_ERR_INVALID_ARG, "imaging.cell_lambda is not finite");
+    if (im->support < 0 || im->support > 16)
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.support must be 0 or 1 (nearest cell) or a kernel width in [2, 16]");
+    if (im->support >= 2 && n > 1024)
+        return set_error(BLINK_ERR_UNSUPPORTED, "with a convolution kernel imaging.n_pix is at most 1024 (grid side 2 n_pix)");
+    if (!std::isfinite(im->phase_l) || !std::isfinite(im->phase_m) ||
+        !(im->phase_l * im->phase_l + im->phase_m * im->phase_m < 1.0))
+        return set_error(BLINK_ERR_INVALID_ARG, "imaging.phase_l, phase_m must be direction cosines with l^2 + m^2 < 1");
+    return BLINK_OK;
+}
+
+// The entry points that grid to the nearest cell only (stage calls and the plain per-image form).
+blink_status nearest_only(const blink_imaging* im, const char* what) {
+    if (im && im->support >= 2)
+        return set_error(BLINK_ERR_UNSUPPORTED, std::string(what) + ": gridding with a convolution kernel runs in the "
+                                                "batched pipeline forms only");
+    return BLINK_OK;
+}
+
 namespace {
 
 constexpr double kSpeedOfLight = 299792458.0;
@@ -75,26 +104,6 @@ blink_status check_obs(const blink_obs* o, bool need_freq) {
     return BLINK_OK;
 }
 
-blink_status check_imaging(const blink_imaging* im) {
-    if (!im) return set_error(BLINK_ERR_INVALID_ARG, "imaging descriptor is NULL");
-    const int n = im->n_pix;
-    if (n < 64 || n > 2048 || (n & (n - 1)))
-        return set_error(BLINK_ERR_UNSUPPORTED, "imaging.n_pix must be a power of two in [64, 2048]");
-    if (im->pol != BLINK_POL_I && im->pol != BLINK_POL_XX)
-        return set_error(BLINK_ERR_INVALID_ARG, "imaging.pol must be BLINK_POL_I or BLINK_POL_XX");
-    if (im->precision != BLINK_PREC_FP32 && im->precision != BLINK_PREC_BF16)
-        return set_error(BLINK_ERR_INVALID_ARG, "imaging.precision must be BLINK_PREC_FP32 or BLINK_PREC_BF16");
-    if (!std::isfinite(im->cell_lambda)) return set_error(BLINK_ERR_INVALID_ARG, "imaging.cell_lambda is not finite");
-    if (im->support < 0 || im->support > 16)
-        return set_error(BLINK_ERR_INVALID_ARG, "imaging.support must be 0 or 1 (nearest cell) or a kernel width in [2, 16]");
-    if (im->support >= 2 && n > 1024)
-        return set_error(BLINK_ERR_UNSUPPORTED, "with a convolution kernel imaging.n_pix is at most 1024 (grid side 2 n_pix)");
-    if (!std::isfinite(im->phase_l) || !std::isfinite(im->phase_m) ||
-        !(im->phase_l * im->phase_l + im->phase_m * im->phase_m < 1.0))
-        return set_error(BLINK_ERR_INVALID_ARG, "imaging.phase_l, phase_m must be direction cosines with l^2 + m^2 < 1");
-    return BLINK_OK;
-}
-
 bool off_zenith(const blink_imaging* im) { return im && (im->phase_l != 0.0 || im->phase_m != 0.0); }
 
 // The pointing's basis (Sec. 5.2.3): e_l, e_m = East and North carried to s0 = (l0, m0, n0) by the rotation
@@ -123,14 +132,6 @@ blink_status zenith_only(const blink_imaging* im, const char* what) {
     if (off_zenith(im))
         return set_error(BLINK_ERR_UNSUPPORTED, std::string(what) + ": an off-zenith phase centre runs in the "
                                                 "pipeline forms only");
-    return BLINK_OK;
-}
-
-// The entry points that grid to the nearest cell only (stage calls and the plain per-image form).
-blink_status nearest_only(const blink_imaging* im, const char* what) {
-    if (im && im->support >= 2)
-        return set_error(BLINK_ERR_UNSUPPORTED, std::string(what) + ": gridding with a convolution kernel runs in the "
-                                                "batched pipeline forms only");
     return BLINK_OK;
 }
 
@@ -166,6 +167,8 @@ void free_plan(Plan* p) {
     cudaFree(p->d_wt);
     cudaFree(p->d_corr);
     cudaFree(p->d_phase);
+    cudaFree(p->d_gsrc);
+    cudaFree(p->d_gphase);
     delete p;
 }
 
@@ -215,6 +218,9 @@ struct GatherBuilder {
     std::vector<int> count, ent_off;
     std::vector<uint2> ent;
     std::vector<uint32_t> ekey, eval, sorted, skey;
+    std::vector<std::vector<uint16_t>> gsrc;   // per channel: the baseline of each entry (nearest-cell lists only)
+    bool src16 = false;
+    int max_per_channel = 0;
     GatherBuilder(int n, int F) : N(n), half(n / 2), nkeys((int64_t)(n / 2) * n), count(nkeys + 1),
                                   ent_off((size_t)F * (n / 2 + 1)) {}
     uint32_t key(int u, int v) const { return (uint32_t)((int64_t)u * N + v); }
@@ -244,6 +250,12 @@ struct GatherBuilder {
             const uint32_t u = skey[e] / N, v = skey[e] % N;
             ent.push_back(make_uint2(u | (v << 11) | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
         }
+        max_per_channel = std::max(max_per_channel, (int)sorted.size());
+        if (src16) {
+            std::vector<uint16_t>& g = gsrc[f];
+            g.resize(sorted.size());
+            for (size_t e = 0; e < sorted.size(); e++) g[e] = (uint16_t)(sorted[e] >> 1);
+        }
         if ((int64_t)ent.size() > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
         return BLINK_OK;
     }
@@ -255,6 +267,14 @@ struct GatherBuilder {
         BLINK_CUDA(cudaMemcpy(p->d_ent_off, ent_off.data(), ent_off.size() * sizeof(int), cudaMemcpyHostToDevice));
         if (!ent.empty())
             BLINK_CUDA(cudaMemcpy(p->d_ent, ent.data(), ent.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+        if (src16) {
+            p->e_stride = std::max(8, (max_per_channel + 7) / 8 * 8);
+            std::vector<uint16_t> all((size_t)gsrc.size() * p->e_stride, 0);
+            for (size_t f = 0; f < gsrc.size(); f++)
+                std::copy(gsrc[f].begin(), gsrc[f].end(), all.begin() + f * p->e_stride);
+            BLINK_TRY(dmalloc(&p->d_gsrc, all.size()));
+            BLINK_CUDA(cudaMemcpy(p->d_gsrc, all.data(), all.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        }
         return BLINK_OK;
     }
 };
@@ -266,6 +286,8 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
     const int64_t B = p->B;
     GatherBuilder g(N, p->F);
     g.ent.reserve((size_t)p->F * (B + B / 16));
+    g.src16 = B <= 0x10000;
+    if (g.src16) g.gsrc.resize(p->F);
     p->W.assign(p->F, 0.f);
     int64_t dropped = 0;
     for (int f = 0; f < p->F; f++) {
@@ -636,6 +658,7 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         if (e == cudaSuccess) e = cudaMemcpy(p->d_freq, p->out_freq.data(), sizeof(double) * p->F, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(plan)"));
         if ((s = make_twiddles(p->d_tw, p->N, st)) != BLINK_OK) return fail(s);
+        if ((s = fft_constants(p->N)) != BLINK_OK) return fail(s);
         // with a kernel the gather list is built from the exact (u, v), kept on the device only meanwhile
         const bool kb = p->support && need_gather;
         if (kb && (s = dmalloc(&p->d_uvw, (size_t)p->F * p->B * 3)) != BLINK_OK) return fail(s);
@@ -662,6 +685,10 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
                 e = cudaMemcpy(cells.data(), p->d_cells, cells.size() * 4, cudaMemcpyDeviceToHost);
                 if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(cells)"));
                 if ((s = build_gather(p, cells, bl, a)) != BLINK_OK) return fail(s);
+                if (p->d_phase && p->d_gsrc) {
+                    if ((s = dmalloc(&p->d_gphase, (size_t)p->F * p->e_stride)) != BLINK_OK) return fail(s);
+                    if ((s = launch_gather_phase(*p, st)) != BLINK_OK) return fail(s);
+                }
             }
             // the imaging path grids raw correlation sums: scale by 1 / (W * 2K) (Stokes I) or 1 / (W * K)
             const double div = (p->pol == BLINK_POL_I ? 2.0 : 1.0) * o->samples_per_int * o->chan_avg;
@@ -701,14 +728,21 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
     const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
     const int T = tau1 - tau0;
     if (T <= 0) return BLINK_OK;
-    const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)p.B * 8 * F))));
+    const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
+    // the side-512 kernel reads the sums in gather order, which the FP8 correlator writes directly
+    const bool gathered = fft_takes_gathered(p) && arith == BLINK_CORR_FP8 &&
+                          corr_fp8_gathers(p, o->samples_per_int, kind, gains);
+    const int64_t vstride = gathered ? p.e_stride : p.B;          // float2 per item
+    const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)vstride * 8 * F))));
+    ImgOut io;
+    io.phase = p.d_phase;
+    io.gather = gathered;
     void* vis = nullptr;
     void* H = nullptr;
     void* cnt = nullptr;
-    BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));
+    BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * vstride * sizeof(float2), &vis));
     BLINK_TRY(workspace(ctx, 1, (size_t)fft_ring_images_max() * N * (N / 2) * el, &H));
     BLINK_TRY(workspace(ctx, 4, sizeof(int) * (2 + 2 * (size_t)t_chunk * F), &cnt));
-    const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
     const int out_first = tau0 * F;
     for (int ta = tau0; ta < tau1; ta += t_chunk) {
         const int tb = std::min(tau1, ta + t_chunk);
@@ -717,18 +751,17 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
             StageTimer t(ctx, BLINK_STAGE_CORRELATE, st);
             if (arith == BLINK_CORR_FP8)
                 BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
-                                          ctx->d_status, ctx->n_sm, st, gains));
+                                          ctx->d_status, ctx->n_sm, st, gains, io));
             else
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
-                                           ctx->d_status, st, gains));
-            BLINK_TRY(launch_phase_vis(static_cast<float2*>(vis), p.B, p, first, n_items, st));
+                                           ctx->d_status, st, gains, io));
         }
         if (!p.tuned && !may_tune) {
             // output over the host link: timings would measure the link, so run the default shape untuned
             StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
-            BLINK_TRY(launch_fft_persistent(p, fft_tune_candidates()[0], prec, static_cast<float2*>(vis), p.B, first,
+            BLINK_TRY(launch_fft_persistent(p, fft_tune_candidates(p)[0], prec, static_cast<float2*>(vis), vstride, first,
                                             ta, tb - ta, H, static_cast<int*>(cnt), d_img, out_first, ctx->d_status,
-                                            ctx->n_sm, st));
+                                            ctx->n_sm, st, ctx->fft_wait, gathered));
         } else if (!p.tuned) {
             // autotune the FFT launch shape on this first batch: time each candidate (every run writes the
             // same images), keep the fastest for every later call of the plan
@@ -743,11 +776,11 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
             BLINK_CUDA(cudaEventCreate(&ev.e[1]));
             cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
             float best = 0.f;
-            for (const FftTune& c : fft_tune_candidates()) {
+            for (const FftTune& c : fft_tune_candidates(p)) {
                 BLINK_CUDA(cudaEventRecord(e0, st));
-                BLINK_TRY(launch_fft_persistent(p, c, prec, static_cast<float2*>(vis), p.B, first, ta, tb - ta, H,
+                BLINK_TRY(launch_fft_persistent(p, c, prec, static_cast<float2*>(vis), vstride, first, ta, tb - ta, H,
                                                 static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm,
-                                                st));
+                                                st, ctx->fft_wait, gathered));
                 BLINK_CUDA(cudaEventRecord(e1, st));
                 BLINK_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -761,8 +794,9 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
             p.tune_ms = best;
         } else {
             StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
-            BLINK_TRY(launch_fft_persistent(p, p.tune, prec, static_cast<float2*>(vis), p.B, first, ta, tb - ta, H,
-                                            static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm, st));
+            BLINK_TRY(launch_fft_persistent(p, p.tune, prec, static_cast<float2*>(vis), vstride, first, ta, tb - ta, H,
+                                            static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm, st,
+                                            ctx->fft_wait, gathered));
         }
     }
     return BLINK_OK;
@@ -877,6 +911,13 @@ blink_status blink_sync(blink_context* ctx, void* stream) {
         if (status & DEV_ERR_TIMEOUT) return set_error(BLINK_ERR_TIMEOUT, "a bounded device-side wait ran out");
         return set_error(BLINK_ERR_DEVICE, "a device-side index guard failed");
     }
+    return BLINK_OK;
+}
+
+blink_status blink_set_wait_budget(blink_context* ctx, int64_t budget_cycles, int32_t unreachable) {
+    if (!ctx) return set_error(BLINK_ERR_INVALID_ARG, "context is NULL");
+    ctx->fft_wait.budget = budget_cycles > 0 ? (long long)budget_cycles : FftWait{}.budget;
+    ctx->fft_wait.extra = unreachable ? 1 : 0;
     return BLINK_OK;
 }
 
@@ -1054,14 +1095,15 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
         BLINK_TRY(workspace(ctx, 1, (size_t)N * ldh * el, &H));
         BLINK_TRY(workspace(ctx, 2, (size_t)N * (N / 2 + 1) * sizeof(float2), &grid));
         const int kind = p->pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
+        ImgOut io;
+        io.phase = p->d_phase;
         for (int id = 0; id < n_img; id++) {
             if (arith == BLINK_CORR_FP8)
                 BLINK_TRY(launch_corr_fp8(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B, ctx->d_status,
-                                          ctx->n_sm, st, g));
+                                          ctx->n_sm, st, g, io));
             else
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B,
-                                           ctx->d_status, st, g));
-            BLINK_TRY(launch_phase_vis(static_cast<float2*>(vis), p->B, *p, id, 1, st));
+                                           ctx->d_status, st, g, io));
             BLINK_CUDA(cudaMemsetAsync(grid, 0, (size_t)N * (N / 2 + 1) * sizeof(float2), st));
             BLINK_TRY(launch_grid_atomic(*p, static_cast<float2*>(vis), id, static_cast<float2*>(grid), st));
             BLINK_TRY(launch_colpass_grid(N, imaging->precision, p->d_tw, static_cast<float2*>(grid), 1, H, ldh, st));

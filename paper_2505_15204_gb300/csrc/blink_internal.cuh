@@ -75,11 +75,25 @@ struct Plan {
     float2* d_tw = nullptr;                // twiddle set of side N (tws_total(N) entries)
     double* d_uvw = nullptr;               // [F][B][3] (kept for blink_cells)
     float2* d_phase = nullptr;             // [F][B] exp(+2 pi i w) of an off-zenith phase centre, else NULL
+    // gather order of the nearest-cell list: entry p of channel f (its local position in the channel's range)
+    // takes baseline gsrc[f][p] (a baseline in the column u = 0 feeds two entries, itself and its mirror);
+    // NULL when a baseline index does not fit 16 bits.  gphase[f][p]: the phase-centre factor in that order.
+    uint16_t* d_gsrc = nullptr;            // [F][e_stride]
+    float2* d_gphase = nullptr;            // [F][e_stride] off zenith, else NULL
+    int e_stride = 0;                      // floats per plane of one gather-ordered item (>= entries per channel)
 };
 
 struct Workspace {
     void* ptr = nullptr;
     size_t bytes = 0;
+};
+
+// Bounded dependency waits of the persistent FFT kernel: the clock-cycle budget of each wait (about a
+// second by default), and an amount added to the row tasks' dependency target (0; a test sets 1 so that
+// those waits cannot be met and run out).
+struct FftWait {
+    long long budget = 2000000000ll;
+    int extra = 0;
 };
 
 }  // namespace blink
@@ -91,6 +105,7 @@ struct blink_context {
     std::vector<blink::Plan*> plans;       // most recent last
     blink::Workspace ws[8];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays
     float2* tw[16] = {};                   // twiddle tables by log2(side)
+    blink::FftWait fft_wait;               // dependency-wait budget of the persistent FFT kernel
     // per-stage profiling (blink_set_profiling): recorded (stage, start, stop) event pairs and a free pool
     bool profiling = false;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -100,6 +115,8 @@ struct blink_context {
 
 namespace blink {
 
+blink_status check_imaging(const blink_imaging* im);
+blink_status nearest_only(const blink_imaging* im, const char* what);
 blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs* o, const blink_imaging* im,
                       bool need_gather, cudaStream_t st, Plan** out);
 blink_status workspace(blink_context* ctx, int slot, size_t bytes, void** out);
@@ -117,8 +134,6 @@ struct StageTimer {
 
 // ---- kernel launchers (defined next to their kernels) --------------------------------------------
 void launch_cells(const Plan& p, cudaStream_t st);
-// vis[i][b] *= phase[(first + i) % F][b] for the n_items items of a correlation workspace of row stride ld.
-blink_status launch_phase_vis(float2* vis, int64_t ld, const Plan& p, int first, int n_items, cudaStream_t st);
 // Calibration of a correlation launch: complex float [channels][n_tiles][2 pol] gains, or (full) complex
 // [channels][n_tiles][2][2] Jones matrices J[p][r], on the device; item channel f uses row f0 + f.
 // d == NULL: none.
@@ -127,12 +142,26 @@ struct GainRef {
     int f0 = 0;
     bool full = false;
 };
+// Where the imaging kinds go: each item's sums, times the phase-centre factor of their baseline and channel
+// when `phase` is given, in baseline order (float2 [item][out_item_stride]); or, with `gather` (the FP8
+// tensor-core form only, see corr_fp8_gathers), in the gather order of the plan's nearest-cell list, as planes
+// [item][re: e_stride | im: e_stride] (floats), the factor taken from the plan's gather-ordered table.
+struct ImgOut {
+    const float2* phase = nullptr;         // [F][B] or NULL
+    bool gather = false;
+};
+
 blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sample_stride_bytes, const Plan& p,
                               int ns, int first_item, int n_items, void* out, int64_t out_item_stride,
-                              int* d_status, cudaStream_t st, GainRef gains = {});
+                              int* d_status, cudaStream_t st, GainRef gains = {}, ImgOut io = {});
 blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample_stride_bytes, const Plan& p,
                              int ns, int first_item, int n_items, void* out, int64_t out_item_stride,
-                             int* d_status, int n_sm, cudaStream_t st, GainRef gains = {});
+                             int* d_status, int n_sm, cudaStream_t st, GainRef gains = {}, ImgOut io = {});
+// Whether the FP8 form can write this plan's imaging kind in gather order (no calibration, a gather source
+// table, and the item's copy fitting in shared memory beside the operands).
+bool corr_fp8_gathers(const Plan& p, int ns, int out_kind, GainRef gains);
+// The phase-centre factors of an off-zenith plan in gather order (Plan::d_gphase from d_phase and d_gsrc).
+blink_status launch_gather_phase(const Plan& p, cudaStream_t st);
 blink_status launch_dedisperse(const float* d_img, int n_out, int F, int n_pix, const int* d_delay, float* d_out,
                                cudaStream_t st);
 blink_status launch_grid_gather(const Plan& p, const float* d_vis4, int first_image, int n_images, float* d_grid,
@@ -149,11 +178,18 @@ struct WaveMap {
 // Gridding + both FFT passes of images [tau0, tau0 + n_tau) x all channels in one persistent launch;
 // d_H holds fft_ring_images_max() column-pass results, d_counters 2 + 2 * F * n_tau ints.
 int fft_ring_images_max();
+// d_vis holds the correlation sums of images [vis_first, ...): float2 [image][vis_stride] in baseline order, or,
+// when `gathered`, gather-ordered planes of p.e_stride floats each (vis_stride = p.e_stride float2 per image).
 blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec, const float2* d_vis,
                                    int64_t vis_stride, int vis_first, int tau0, int n_tau, void* d_H, int* d_counters,
-                                   float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st);
-// Candidate launch shapes the autotuner times.
-std::vector<FftTune> fft_tune_candidates();
+                                   float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st,
+                                   const FftWait& wait, bool gathered = false);
+// Whether the persistent kernel can read gather-ordered sums for this plan (side 512, nearest cell).
+bool fft_takes_gathered(const Plan& p);
+// Candidate launch shapes the autotuner times for a plan.
+std::vector<FftTune> fft_tune_candidates(const Plan& p);
+// Constant-memory twiddles of the persistent kernel for side N on the current device (once per plan).
+blink_status fft_constants(int N);
 blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const float2* d_grid, int n_images,
                                  void* d_H, int ldh, cudaStream_t st);
 blink_status launch_rowpass(int N, int prec, const float2* d_tw, const void* d_H, int ldh, int has_nyq,
@@ -164,13 +200,22 @@ blink_status launch_rowpass(int N, int prec, const float2* d_tw, const void* d_H
 // integer sums S_XX + S_YY and S_XX (as floats) that the imaging path grids, divided later with 1/W
 enum { CORR_OUT_VIS4 = 0, CORR_OUT_STOKES_I = 1, CORR_OUT_XX = 2 };
 
+
 constexpr int COL_CW = 8;                  // u columns per column-pass CTA (one warp per column)
 
 // ------------------------------------------------------------------------------------------------
 // device helpers
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sums and differences as one packed two-lane FP32 instruction (add.rn.f32x2 / sub.rn.f32x2 of
+// Blackwell): each lane is the same round-to-nearest FP32 addition as the scalar form, so results are
+// unchanged while the butterflies issue half as many instructions.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&r);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -575,6 +620,70 @@ __device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__
         __syncwarp();
         key = nkey;
         x = nx;
+    }
+}
+
+// The same over the entries [beg, end) of several consecutive columns (the keys carry u, so runs never span
+// two columns), with the entries and their visibilities loaded NB chunks of 32 at a time.  val(i, b) is the
+// value of entry i, whose baseline is b: with sums in baseline order it depends on the entry's load (two
+// dependent round trips per NB chunks), with gather-ordered sums only on i (one).  occ(u, v) is the
+// occupancy word of cell (u, v) (bit v / 32 of the word of v % 32 in its column).
+template <int NB, typename T, typename Val, typename Idx, typename Occ>
+__device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
+                                                        Val val, Idx idx, Occ occ) {
+    uint32_t prev = 0xFFFFFFFFu;                    // the last cell of the previous chunk
+    for (int base = beg; base < end; base += 32 * NB) {
+        uint32_t key[NB], bl[NB];
+        float2 x[NB];
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            const int i = base + 32 * q + lane;
+            key[q] = 0xFFFFFFFFu;
+            bl[q] = 0u;
+            if (i < end) {
+                const uint2 e = ent[i];
+                key[q] = e.x;
+                bl[q] = e.y;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            x[q] = make_float2(0.f, 0.f);
+            if (key[q] != 0xFFFFFFFFu) {
+                x[q] = val(base + 32 * q + lane, bl[q]);
+                if (key[q] >> 31) x[q].y = -x[q].y;
+                key[q] = ent_cell(key[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            const int cb = base + 32 * q;
+            if (cb >= end) break;
+            const int i = cb + lane;
+            uint32_t k = key[q];
+            float2 y = x[q];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t k2 = __shfl_up_sync(0xFFFFFFFFu, k, d);
+                const float yr = __shfl_up_sync(0xFFFFFFFFu, y.x, d), yi = __shfl_up_sync(0xFFFFFFFFu, y.y, d);
+                if (lane >= d && k2 == k) {
+                    y.x += yr;
+                    y.y += yi;
+                }
+            }
+            const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, k, 1);
+            const uint32_t klast = __shfl_sync(0xFFFFFFFFu, k, min(31, end - 1 - cb));
+            if (i < end && (lane == 31 || i + 1 >= end || knext != k)) {
+                const int u = ent_u(k), v = ent_v(k);
+                if ((u + v) & 1) y = make_float2(-y.x, -y.y);
+                T* p = s + idx(u, v);
+                if (k == prev) y = cadd(ld_c(p), y);
+                st_c(p, y);
+                atomicOr(occ(u, v), 1u << (v >> 5));
+            }
+            prev = klast;
+            __syncwarp();
+        }
     }
 }
 

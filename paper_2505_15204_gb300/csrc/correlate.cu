@@ -28,7 +28,8 @@ template <int OUT, bool FULL>
 __global__ void __launch_bounds__(kThreads)
 k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles, int ns, int c, int F,
             int first_item, const short2* __restrict__ bl, int64_t B, const uint8_t* __restrict__ flags,
-            void* __restrict__ out, int64_t out_item_stride, int kc, const float2* __restrict__ gains, int gain_f0) {
+            void* __restrict__ out, int64_t out_item_stride, int kc, const float2* __restrict__ gains, int gain_f0,
+            ImgOut io) {
     extern __shared__ float4 xs[];                    // [kc][n_tiles]
     const int item = first_item + blockIdx.y;
     const int tau = item / F, f = item - (item / F) * F;
@@ -138,12 +139,17 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
             o[0] = make_float4(r[0], r[1], r[2], r[3]);
             o[1] = make_float4(r[4], r[5], r[6], r[7]);
         } else {
-            // imaging kinds: the exact integer sums; the 1/K (or 1/2K) is applied together with 1/W
-            float2* o = static_cast<float2*>(out) + (int64_t)blockIdx.y * out_item_stride + b;
-            if (OUT == CORR_OUT_STOKES_I)
-                *o = make_float2(acc[m][0] + acc[m][6], acc[m][1] + acc[m][7]);
-            else
-                *o = make_float2(acc[m][0], acc[m][1]);
+            // imaging kinds: the exact integer sums (the 1/K or 1/2K is applied together with 1/W), times the
+            // phase-centre factor when given
+            float re = OUT == CORR_OUT_STOKES_I ? acc[m][0] + acc[m][6] : acc[m][0];
+            float im = OUT == CORR_OUT_STOKES_I ? acc[m][1] + acc[m][7] : acc[m][1];
+            if (io.phase) {
+                const float2 ph = io.phase[(int64_t)f * B + b];
+                const float r = re * ph.x - im * ph.y, i = re * ph.y + im * ph.x;
+                re = r;
+                im = i;
+            }
+            static_cast<float2*>(out)[(int64_t)blockIdx.y * out_item_stride + b] = make_float2(re, im);
         }
     }
 }
@@ -152,14 +158,16 @@ k_corr_fp32(const uint8_t* __restrict__ volt, int64_t sample_stride, int n_tiles
 
 template <int OUT, bool FULL>
 void corr_fp32(dim3 grid, size_t smem, cudaStream_t st, const uint8_t* d_volt, int64_t sample_stride, const Plan& p,
-               int ns, int first, void* o, int64_t out_item_stride, int kc, GainRef gains) {
+               int ns, int first, void* o, int64_t out_item_stride, int kc, GainRef gains, ImgOut io) {
     k_corr_fp32<OUT, FULL><<<grid, kThreads, smem, st>>>(d_volt, sample_stride, p.n_tiles, ns, p.chan_avg, p.F, first,
-                                                         p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0);
+                                                         p.d_bl, p.B, p.d_flags, o, out_item_stride, kc, gains.d, gains.f0,
+                                                         OUT == CORR_OUT_VIS4 ? ImgOut{} : io);
 }
 
 blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
                               int first_item, int n_items, void* out, int64_t out_item_stride, int*,
-                              cudaStream_t st, GainRef gains) {
+                              cudaStream_t st, GainRef gains, ImgOut io) {
+    if (io.gather) return set_error(BLINK_ERR_UNSUPPORTED, "the CUDA-core correlator writes baseline order only");
     const int kc = std::max(1, std::min(ns * p.chan_avg, kStageFloat4 / p.n_tiles));
     const size_t smem = (size_t)kc * p.n_tiles * sizeof(float4);
     const unsigned gx = (unsigned)((p.B + kThreads * kBpt - 1) / (kThreads * kBpt));
@@ -172,21 +180,21 @@ blink_status launch_corr_fp32(int out_kind, const uint8_t* d_volt, int64_t sampl
         switch (out_kind) {
             case CORR_OUT_VIS4:
                 if (full) corr_fp32<CORR_OUT_VIS4, true>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
-                                                         out_item_stride, kc, gains);
+                                                         out_item_stride, kc, gains, io);
                 else corr_fp32<CORR_OUT_VIS4, false>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
-                                                     out_item_stride, kc, gains);
+                                                     out_item_stride, kc, gains, io);
                 break;
             case CORR_OUT_STOKES_I:
                 if (full) corr_fp32<CORR_OUT_STOKES_I, true>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0,
-                                                             o, out_item_stride, kc, gains);
+                                                             o, out_item_stride, kc, gains, io);
                 else corr_fp32<CORR_OUT_STOKES_I, false>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0,
-                                                         o, out_item_stride, kc, gains);
+                                                         o, out_item_stride, kc, gains, io);
                 break;
             default:
                 if (full) corr_fp32<CORR_OUT_XX, true>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
-                                                       out_item_stride, kc, gains);
+                                                       out_item_stride, kc, gains, io);
                 else corr_fp32<CORR_OUT_XX, false>(grid, smem, st, d_volt, sample_stride, p, ns, first_item + i0, o,
-                                                   out_item_stride, kc, gains);
+                                                   out_item_stride, kc, gains, io);
         }
     }
     BLINK_CUDA(cudaGetLastError());

@@ -60,7 +60,31 @@ struct TcParams {
     void* out;
     int64_t out_item_stride;
     int* status;
+    int64_t B;
+    ImgOut io;               // imaging kinds in baseline order: phase-centre factor
+    // imaging kinds in gather order: the item's sums go from TMEM to a baseline-ordered copy in shared memory
+    // (planes re | im of B floats at off_item), then leave in gather order (p -> baseline gsrc[f][p])
+    uint32_t off_item;       // 0: baseline order
+    const uint16_t* gsrc;
+    const float2* gphase;
+    const int* ent_off;      // [F][ent_ld]: entry range of each channel (last column's end = its count)
+    int ent_ld, e_stride;
 };
+
+// One imaging-kind sum of item `local` (channel f) and baseline b in baseline order, times the phase-centre
+// factor when given.  The factor is fetched first (img_fetch), so that a thread's fetches for several
+// baselines are in flight together.
+__device__ __forceinline__ float2 img_fetch(const TcParams& P, int f, int64_t b) {
+    return P.io.phase ? __ldg(P.io.phase + (int64_t)f * P.B + b) : make_float2(1.f, 0.f);
+}
+__device__ __forceinline__ void put_img(const TcParams& P, int local, int64_t b, float2 ph, float re, float im) {
+    if (P.io.phase) {
+        const float r = re * ph.x - im * ph.y, i = re * ph.y + im * ph.x;
+        re = r;
+        im = i;
+    }
+    static_cast<float2*>(P.out)[(int64_t)local * P.out_item_stride + b] = make_float2(re, im);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -176,6 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
     float2* s_g = reinterpret_cast<float2*>(smem + P.off_gain);
     uint32_t* lut = reinterpret_cast<uint32_t*>(smem + P.off_lut);   // raw byte -> e4m3 (re, im, im, -re)
     uint8_t* sflags = smem + P.off_flags;
+    float* s_item = P.off_item ? reinterpret_cast<float*>(smem + P.off_item) : nullptr;
     const uint32_t bar_tma0 = smem_u32(smem + P.off_bar), bar_tma1 = bar_tma0 + 8, bar_mma = bar_tma0 + 16;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + P.off_tmem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -323,6 +348,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             }
             tc_fence_after();
             const int local = it - P.first_item;
+            if (!GAINS && s_item) {
+                // gather order: every block pair of the round from TMEM straight into the item's copy (warp w reads
+                // TMEM lanes 32 (w % 4) + lane = unit row, re for lanes below 64, im above; columns 16 (w / 4) ..)
+                for (int q = q0; q < q1; q++) {
+                    int mb, jb;
+                    pair_of(q, mb, jb);
+                    const int row = (warp & 3) * 32 + lane, c0 = (warp >> 2) * 16;
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((q - q0) * 64) + c0, v);
+                    const int ui = mb * 64 + (row & 63);
+                    if (ui < P.n_tiles) {
+                        float* dst = s_item + (row >> 6) * P.B + (int64_t)ui * (ui + 1) / 2;
+#pragma unroll
+                        for (int cc = 0; cc < 16; cc++) {
+                            const int uj = jb * 64 + c0 + cc;
+                            if (uj <= ui) dst[uj] = __uint_as_float(v[cc]);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncthreads();
+                continue;
+            }
             const int stage_buf = GAINS ? P.stage_buf : 2 * kPlane;
             // stage block pair q into buffer sb: warp w reads TMEM lanes 32 (w % 4) + lane, columns 16 (w / 4) ..
             auto stage = [&](int q, int sb) {
@@ -383,8 +431,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                             for (int pq = 0; pq < 4; pq++)
                                 o[pq] = make_float2(__fdiv_rn(V[pq].x, div), __fdiv_rn(V[pq].y, div));
                         } else {
-                            float2* o = static_cast<float2*>(P.out) + (int64_t)local * P.out_item_stride + b;
-                            *o = P.mode == CORR_OUT_STOKES_I ? make_float2(V[0].x + V[3].x, V[0].y + V[3].y) : V[0];
+                            const float2 o = P.mode == CORR_OUT_STOKES_I ? make_float2(V[0].x + V[3].x, V[0].y + V[3].y) : V[0];
+                            put_img(P, local, b, img_fetch(P, it % P.F, b), o.x, o.y);
                         }
                     }
                     return;
@@ -415,15 +463,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                     // baselines of a row.
                     constexpr int kRowStep = kThreads / 64;
                     const int jl = tid & 63, uj = jb * 64 + jl;
-                    float2* out = static_cast<float2*>(P.out) + (int64_t)local * P.out_item_stride + uj;
+                    const int fch = it % P.F;
                     const float* pre = sre + jl;
                     const float* pim = sim + jl;
                     if (!GAINS) {
-#pragma unroll 4
-                        for (int il = tid >> 6; il < 64; il += kRowStep) {
-                            const int ui = mb * 64 + il;
+                        // the rows il = tid / 64 + kRowStep r: their baselines' data fetched together, then stored
+                        constexpr int kR = 64 / kRowStep;
+                        float2 ax[kR];
+#pragma unroll
+                        for (int r = 0; r < kR; r++) {
+                            const int il = (tid >> 6) + kRowStep * r, ui = mb * 64 + il;
+                            ax[r] = (ui < P.n_tiles && uj <= ui) ? img_fetch(P, fch, (int64_t)ui * (ui + 1) / 2 + uj)
+                                                                 : make_float2(1.f, 0.f);
+                        }
+#pragma unroll
+                        for (int r = 0; r < kR; r++) {
+                            const int il = (tid >> 6) + kRowStep * r, ui = mb * 64 + il;
                             if (ui >= P.n_tiles || uj > ui) continue;
-                            out[(int64_t)ui * (ui + 1) / 2] = make_float2(pre[il * kStageLd], pim[il * kStageLd]);
+                            put_img(P, local, (int64_t)ui * (ui + 1) / 2 + uj, ax[r], pre[il * kStageLd],
+                                    pim[il * kStageLd]);
                         }
                     } else {
                         // calibrated: g_i^X S_XX conj(g_j^X) (+ g_i^Y S_YY conj(g_j^Y) for Stokes I, split)
@@ -445,7 +503,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                                 vr += tr * hy.x + ti * hy.y;
                                 vi += ti * hy.x - tr * hy.y;
                             }
-                            out[(int64_t)ui * (ui + 1) / 2] = make_float2(vr, vi);
+                            const int64_t b = (int64_t)ui * (ui + 1) / 2 + uj;
+                            put_img(P, local, b, img_fetch(P, fch, b), vr, vi);
                         }
                     }
                 }
@@ -470,6 +529,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             __syncthreads();
         }
         if (abort) break;
+        if (!GAINS && s_item) {
+            // the item in gather order: entry p of channel f takes baseline gsrc[f][p] (times the factor
+            // gphase[f][p] off zenith), four entries per thread in flight, coalesced stores of both planes
+            const int f = it % P.F;
+            const int* eo = P.ent_off + (int64_t)f * P.ent_ld;
+            const int n_f = eo[P.ent_ld - 1] - eo[0];
+            const uint16_t* src = P.gsrc + (int64_t)f * P.e_stride;
+            const float2* gph = P.gphase ? P.gphase + (int64_t)f * P.e_stride : nullptr;
+            float* o = static_cast<float*>(P.out) + (int64_t)(it - P.first_item) * 2 * P.e_stride;
+            for (int p0 = tid; p0 < n_f; p0 += 4 * kThreads) {
+                uint32_t bb[4];
+                float2 w[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int pp = p0 + k * kThreads;
+                    bb[k] = pp < n_f ? __ldg(src + pp) : 0u;
+                    w[k] = (gph && pp < n_f) ? __ldg(gph + pp) : make_float2(1.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int pp = p0 + k * kThreads;
+                    if (pp >= n_f) break;
+                    float re = s_item[bb[k]], im = s_item[P.B + bb[k]];
+                    if (gph) {
+                        const float r = re * w[k].x - im * w[k].y, i = re * w[k].y + im * w[k].x;
+                        re = r;
+                        im = i;
+                    }
+                    o[pp] = re;
+                    o[P.e_stride + pp] = im;
+                }
+            }
+        }
     }
     if (abort) {
         if (tid == 0) {
@@ -502,9 +594,25 @@ uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+// Shared memory of the gather-order form: operands, two raw blocks and the item's copy (2 B floats) must fit.
+bool corr_fp8_gathers(const Plan& p, int ns, int out_kind, GainRef gains) {
+    if (gains.d || out_kind == CORR_OUT_VIS4 || !p.d_gsrc || p.N / 2 + 1 <= 0) return false;
+    const int nt = p.n_tiles, c = p.chan_avg, K = ns * c;
+    if (nt % 8 || ns > 256 || c > 256) return false;
+    const int units = nt, n_blk = (units + kUnitsPerBlk - 1) / kUnitsPerBlk, Kq = (K + 3) / 4 * 4;
+    const int Kr = out_kind == CORR_OUT_STOKES_I ? 4 * Kq : 2 * Kq, Kp = (Kr + 31) / 32 * 32;
+    const uint32_t raw = (uint32_t)(ns * c * nt * 2);
+    uint32_t off = align_up((uint32_t)n_blk * 128u * Kp, 1024);
+    off = align_up(off + raw, 128);
+    off = align_up(off + raw, 128);
+    off = align_up(off + (uint32_t)(8 * p.B), 16);
+    off += 256 * 4 + align_up((uint32_t)nt, 16) + 32 + 8;
+    return off <= 227 * 1024;
+}
+
 blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
                              int first_item, int n_items, void* out, int64_t out_item_stride, int* d_status, int n_sm,
-                             cudaStream_t st, GainRef gains) {
+                             cudaStream_t st, GainRef gains, ImgOut io) {
     if (n_items <= 0) return BLINK_OK;
     const int nt = p.n_tiles, c = p.chan_avg, K = ns * c;
     if (nt % 8 || ns > 256 || c > 256 || ((uintptr_t)d_volt & 15) || (sample_stride % 16))
@@ -545,8 +653,21 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     P.off_im = off + kPlane * 4;
     const uint32_t gain_bytes = gains.d ? (uint32_t)nt * (gains.full ? 32 : 16) : 0;
     const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32 + (gains.d ? gain_bytes + 16 : 0);
-    P.two_stage = off + 2 * P.stage_buf * 4 + tail <= 227 * 1024;
-    off = align_up(off + (P.two_stage ? 2 : 1) * P.stage_buf * 4, 16);
+    if (io.gather) {
+        // gather order: the item's baseline-ordered copy takes the staging buffers' place
+        if (!corr_fp8_gathers(p, ns, out_kind, gains))
+            return set_error(BLINK_ERR_UNSUPPORTED, "FP8 correlation: gather order not available for this plan");
+        P.off_item = off;
+        off = align_up(off + (uint32_t)(8 * p.B), 16);
+        P.gsrc = p.d_gsrc;
+        P.gphase = p.d_gphase;
+        P.ent_off = p.d_ent_off;
+        P.ent_ld = p.N / 2 + 1;
+        P.e_stride = p.e_stride;
+    } else {
+        P.two_stage = off + 2 * P.stage_buf * 4 + tail <= 227 * 1024;
+        off = align_up(off + (P.two_stage ? 2 : 1) * P.stage_buf * 4, 16);
+    }
     P.off_gain = off;                              // [n_tiles][2] (or [n_tiles][4] Jones) float2 when given
     if (gains.d) off = align_up(off + gain_bytes, 16);
     P.off_lut = off;
@@ -564,6 +685,8 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     P.out = out;
     P.out_item_stride = out_item_stride;
     P.status = d_status;
+    P.B = p.B;
+    if (out_kind != CORR_OUT_VIS4 && !io.gather) P.io = io;
 
     auto encode = encode_fn();
     if (!encode) return set_error(BLINK_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");

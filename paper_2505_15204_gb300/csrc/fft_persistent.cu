@@ -6,9 +6,18 @@
 //       sides in radix-8 passes), then write the block to the image's slot of a small ring of intermediates
 //       (kept in L2);
 //   row task (image k, row block rb): once all column tasks of image k are done, transform 32 rows
-//       along u (complex to real, in two batches of two rows per warp; 256-point rows in two radix-16
-//       passes over both rows at once), scale by 1 / (W * 2K) and write the image rows with streaming
-//       stores (they are not read back, so they should not displace the ring from L2).
+//       along u (complex to real) and scale by 1 / (W * 2K), writing the image rows with streaming stores
+//       (they are not read back, so they should not displace the ring from L2).
+// Side 512 (nearest cell) keeps the ring column-major, [u][v] with v contiguous: each column warp stores its
+// transformed column straight from registers as whole 128-byte lines, and a row task reads 32 consecutive
+// rows v of one column u per warp instruction, so that lane l holds row y0 + l.  Its first radix-16 pass
+// (the 256-point row transform is 16 x 16) then runs in registers with the rows across the lanes: warp w
+// takes the butterflies j and 16 - j (0 and 8 for warp 0), whose points u = j + 16 r and 256 - u are exactly
+// the pairs the complex-to-real pre-twiddle combines, and every twiddle it needs is the same for the whole
+// warp (read from constant memory).  One exchange through shared memory hands the 16 x 16 intermediate of
+// each row to the second pass, two rows per warp, whose outputs are consecutive pixels of one row.  Other
+// sides (and gridding with a kernel) keep the row-major ring: a column task transposes its block through
+// shared memory into ring rows, and a row task transforms whole rows in shared memory.
 // CTAs take task tickets in order from a global counter.  The ticket stream is cut into segments of
 // (column tasks of image s) + (row tasks of image s - lag), so an image's row tasks come `lag` segments
 // after its column tasks.  Dependencies are per-image counters: a row task waits for the image's column
@@ -17,6 +26,7 @@
 // end; they are nevertheless bounded, and on expiry the launch records BLINK_ERR_TIMEOUT and every CTA
 // stops taking tickets.
 #include <algorithm>
+#include <cmath>
 
 #include "blink_internal.cuh"
 
@@ -31,7 +41,11 @@ constexpr int kRPW = 2;                          // rows per warp in a row batch
 constexpr int kRB = kW * kRPW;                   // rows per row batch
 constexpr int kRowBatches = 2;                   // row batches per row task
 constexpr int kVisAhead = 8;                     // images ahead whose visibilities a column task prefetches
-constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
+constexpr int kRowLd = 257;                      // side 512: float2 pitch of a row's 16 x 16 intermediate (odd:
+                                                 //   lanes = rows write it without bank conflicts)
+
+// exp(2 pi i m / 512) for m in [0, 512): the twiddles of the side-512 row tasks, indexed by warp-uniform m
+__constant__ float2 c_circ512[512];
 
 struct FftParams {
     const float2* vis;       // correlation sums of the chunk's images, [item][B]
@@ -55,6 +69,10 @@ struct FftParams {
     int* col_done;           //   [n_img] column tasks finished per image
     int* row_done;           //   [n_img] row tasks finished per image
     int* status;
+    int gathered;            // vis holds gather-ordered planes of e_stride floats (re, then im) per image
+    int e_stride;
+    long long wait_budget;   // clock cycles a dependency wait may take before the launch gives up
+    int extra_wait;          // added to the row tasks' dependency target (0; 1 makes those waits run out)
 };
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -89,7 +107,7 @@ __device__ bool wait_count(const FftParams& P, const int* cnt, int target, int* 
         int ok = 1;
         const long long t0 = clock64();
         while (cnt && ld_acquire(cnt) < target) {
-            if (clock64() - t0 > kWaitBudget || ld_relaxed(P.tickets + 1)) {
+            if (clock64() - t0 > P.wait_budget || ld_relaxed(P.tickets + 1)) {
                 ok = 0;
                 break;
             }
@@ -103,6 +121,30 @@ __device__ bool wait_count(const FftParams& P, const int* cnt, int target, int* 
     }
     __syncthreads();
     return *s_flag != 0;
+}
+
+// The same for one warp: lane 0 waits (bounded) until *cnt reaches `target`, starting from `seen`, a value of
+// *cnt it acquired earlier (no wait when that already reaches the target, or when cnt is NULL); the
+// warp barrier orders the other lanes' later accesses after lane 0's acquire.
+__device__ bool warp_wait(const FftParams& P, const int* cnt, int target, int seen) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0 && cnt && seen < target) {
+        const long long t0 = clock64();
+        while (ld_acquire(cnt) < target) {
+            if (clock64() - t0 > P.wait_budget || ld_relaxed(P.tickets + 1)) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (!ok) {
+            atomicOr(P.status, DEV_ERR_TIMEOUT);
+            atomicExch(P.tickets + 1, 1);
+        }
+    }
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    __syncwarp();
+    return ok != 0;
 }
 
 __host__ __device__ constexpr int even(int x) { return (x + 1) / 2 * 2; }
@@ -181,6 +223,191 @@ __device__ __forceinline__ void warp_fft512(T* s, const float2* tw32, int lane, 
     __syncwarp();
 }
 
+// Unnormalised inverse DFT of 32 points in registers, v[q] <- sum_r v[r] exp(+2 pi i r q / 32): the 16-point
+// transforms of the even and the odd points, combined with exp(2 pi i q / 32).
+__device__ __forceinline__ void idft32(float2 (&v)[32]) {
+    float2 e[16], o[16];
+#pragma unroll
+    for (int r = 0; r < 16; r++) {
+        e[r] = v[2 * r];
+        o[r] = v[2 * r + 1];
+    }
+    idft<16>(e);
+    idft<16>(o);
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+        const float2 t = cmul(o[q], w32(q));
+        v[q] = cadd(e[q], t);
+        v[q + 16] = csub(e[q], t);
+    }
+}
+
+// First pass of the 512-point column transform by one warp on a column of 512 unpadded slots (point v at
+// slot v; lane = j, points n = j + 32 r): the radix-16 DFT over r, with Y[j][k1] stored at the swizzled slot
+// 16 j + (k1 ^ (j & 15)), so that both these stores and the second pass's reads of Y[j][.] for 16
+// consecutive k1 touch 16 distinct 8-byte bank pairs.  The pass reads only the points `occ` marks (point
+// lane + 32 r: bit r) and treats the others as zero.
+template <typename T>
+__device__ __forceinline__ void col512_pass1(T* s, int lane, uint32_t occ) {
+    float2 v[16];
+#pragma unroll
+    for (int r = 0; r < 16; r++) v[r] = ((occ >> r) & 1u) ? ld_c(s + lane + 32 * r) : make_float2(0.f, 0.f);
+    idft<16>(v);
+    __syncwarp();
+    const int sw = lane & 15;
+#pragma unroll
+    for (int r = 0; r < 16; r++) st_c(s + 16 * lane + (r ^ sw), v[r]);
+}
+
+// Complex-to-real pre-twiddle of one pair of row points (Eq. 4 on the Hermitian half plane): from G[q] = zk
+// and G[M - q] = zm, with wq = exp(2 pi i q / N), the inputs of the M-point complex transform are
+//   Z[q] = A + i C,  Z[M - q] = conj(A) + i conj(C),  A = zk + conj(zm),  C = (zk - conj(zm)) wq,
+// written back over zk and zm.
+__device__ __forceinline__ void pretw(float2& zk, float2& zm, float2 wq) {
+    const float2 A = make_float2(zk.x + zm.x, zk.y - zm.y);
+    const float2 C = cmul(make_float2(zk.x - zm.x, zk.y + zm.y), wq);
+    zk = make_float2(A.x - C.y, A.y + C.x);
+    zm = make_float2(A.x + C.y, C.x - A.y);
+}
+
+// Column task of side 512 with the column-major ring: 16 columns u0 + c, two per warp.  Each warp grids its
+// two columns (as in column_task), runs the first pass of both, then the second pass with one radix-32
+// butterfly per lane (lane = b + 16 c: column c of the warp's pair, butterfly b): with n = j + 32 r and
+// k = b + 16 k2,
+//   X[b + 16 k2] = sum_j exp(2 pi i j k2 / 32) exp(2 pi i j b / 512) Y[j][b],
+// and stores the column from registers, each half-warp writing 16 consecutive points (128 bytes) per
+// instruction, once the ring slot's previous image has been read.
+template <typename T>
+__device__ int* column_task512(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
+                               uint32_t* s_occ) {
+    constexpr int N = 512, M = N / 2, LD = N;             // unpadded columns (swizzled first pass)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
+    const int slot = k % P.ring;
+    // the ring slot's previous occupant, acquired now so that the load overlaps the gridding and transforms
+    const int* prev = k >= P.ring ? P.row_done + (k - P.ring) : nullptr;
+    int seen = 0;
+    if (lane == 0 && prev) seen = ld_acquire(prev);
+    if (kVisAhead > 0 && tid == 0 && cb == 0 && k + kVisAhead < P.n_img && P.vis_prefetch) {
+        const int k2 = k + kVisAhead, f2 = k2 / P.n_tau, id2 = (P.tau0 + k2 % P.n_tau) * P.F + f2;
+        prefetch_l2(P.vis + (int64_t)(id2 - P.vis_first) * P.vis_stride, P.vis_prefetch);
+    }
+    T* s = reinterpret_cast<T*>(work);
+    const float2* V = P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
+    const int* off = P.ent_off + f * (M + 1);
+    const int base = off[0];                          // the channel's first entry (gather order's position 0)
+    const float* Vre = reinterpret_cast<const float*>(V) - base;
+    auto val = [&](int i, uint32_t b) {
+        return P.gathered ? make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i)) : __ldcs(V + b);
+    };
+    const int u0 = cb * 2 * kCW + 2 * warp;           // the warp's columns u0, u0 + 1
+    {
+        // both columns in one pass over their (contiguous) entries
+        uint32_t* occ = s_occ + 2 * warp * 32;
+        occ[lane] = 0u;
+        occ[32 + lane] = 0u;
+        __syncwarp();
+        auto idx = [&](int u, int v) { return (2 * warp + (u - u0)) * LD + v; };
+        auto occw = [&](int u, int v) { return occ + (u - u0) * 32 + (v & 31); };
+        warp_gather_occ_batched<4>(P.ent, off[u0], off[u0 + 2], lane, s, val, idx, occw);
+        __syncwarp();
+        col512_pass1(s + 2 * warp * LD, lane, occ[lane]);
+        col512_pass1(s + (2 * warp + 1) * LD, lane, occ[32 + lane]);
+    }
+    __syncwarp();
+    const int b = lane & 15, c = lane >> 4;
+    const T* y = s + (2 * warp + c) * LD;             // Y[j][b] at 16 j + (b ^ (j & 15))
+    float2 v[32];
+#pragma unroll
+    for (int j = 0; j < 32; j++) v[j] = ld_c(y + 16 * j + (b ^ (j & 15)));
+#pragma unroll
+    for (int j = 1; j < 32; j++) v[j] = cmul(v[j], s_twc[16 * j + b]);
+    idft32(v);
+    if (warp_wait(P, prev, P.n_rb, seen)) {
+        T* dst = static_cast<T*>(P.H) + (int64_t)slot * M * N + (int64_t)(u0 + c) * N + b;
+#pragma unroll
+        for (int k2 = 0; k2 < 32; k2++) st_c(dst + 16 * k2, v[k2]);
+    }
+    return P.col_done + k;
+}
+
+// Row task of side 512 (32 rows y0 + l, l = lane) with the column-major ring: the first radix-16 pass of the
+// 256-point row transform in registers (lanes = rows), one exchange through shared memory, the second pass
+// with two rows per warp.  With the point index n = j + 16 r of the row (u = n) and m = k1 + 16 k2 of the
+// output pixel pair (2m, 2m + 1):
+//   Y[j][k1] = exp(2 pi i j k1 / 256) sum_r Z[j + 16 r] exp(2 pi i r k1 / 16),
+//   X[k1 + 16 k2] = sum_j Y[j][k1] exp(2 pi i j k2 / 16).
+// The ring slot's row count is released as soon as every warp has read its rows.
+template <typename T>
+__device__ int* row_task512(const FftParams& P, int k, int rb, unsigned char* work) {
+    constexpr int N = 512, M = N / 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
+    const int slot = k % P.ring;
+    const int y0 = rb * 32;
+    float2* S = reinterpret_cast<float2*>(work);
+    const bool ok = warp_wait(P, P.col_done + k, P.n_cb + P.extra_wait, 0);
+    if (ok) {
+        const int jA = warp == 0 ? 0 : warp, jB = warp == 0 ? 8 : 16 - warp;
+        const T* col = static_cast<const T*>(P.H) + (int64_t)slot * M * N + y0 + lane;
+        float2 a[16], b[16];
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+            a[r] = ldcg_c(col + (int64_t)(jA + 16 * r) * N);
+            b[r] = ldcg_c(col + (int64_t)(jB + 16 * r) * N);
+        }
+        if (warp == 0) {
+            // butterfly 0: u = 16 r pairs with 16 (16 - r); u = 0 with the (empty) Nyquist column, u = 128 with
+            // itself.  Butterfly 8: u = 8 + 16 r pairs with 8 + 16 (15 - r).
+            float2 z = make_float2(0.f, 0.f);
+            pretw(a[0], z, c_circ512[0]);
+#pragma unroll
+            for (int r = 1; r < 8; r++) pretw(a[r], a[16 - r], c_circ512[16 * r]);
+            z = a[8];
+            pretw(a[8], z, c_circ512[128]);
+#pragma unroll
+            for (int r = 0; r < 8; r++) pretw(b[r], b[15 - r], c_circ512[8 + 16 * r]);
+        } else {
+            // u = j + 16 s pairs with 256 - u = (16 - j) + 16 (15 - s); the pair's smaller index gives wq
+#pragma unroll
+            for (int s = 0; s < 8; s++) {
+                pretw(a[s], b[15 - s], c_circ512[jA + 16 * s]);
+                pretw(b[s], a[15 - s], c_circ512[jB + 16 * s]);
+            }
+        }
+        auto pass1 = [&](float2(&v)[16], int j) {
+            idft<16>(v);
+            float2* dst = S + lane * kRowLd + 16 * j;
+            dst[0] = v[0];
+#pragma unroll
+            for (int k1 = 1; k1 < 16; k1++) dst[k1] = cmul(v[k1], c_circ512[(2 * j * k1) & 511]);
+        };
+        pass1(a, jA);
+        pass1(b, jB);
+    }
+    if (__syncthreads_or(!ok)) return nullptr;
+    if (tid == 0) {                                     // every warp's ring reads are done
+        __threadfence();
+        atomicAdd(P.row_done + k, 1);
+    }
+    const float w = P.wk[f];
+    const float inv = 1.0f / (w > 0.f ? w : 1.f);
+    const int h = lane >> 4, k1 = lane & 15;
+#pragma unroll 1
+    for (int it = 0; it < 2; it++) {
+        const int rr = warp + 8 * (2 * it + h);
+        const float2* src = S + rr * kRowLd + k1;
+        float2 v[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = src[16 * j];
+        idft<16>(v);
+        float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y0 + rr) * N) + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; k2++) __stcs(out + 16 * k2, make_float2(v[k2].x * inv, v[k2].y * inv));
+    }
+    return nullptr;
+}
+
 // The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
 // With WT (gridding with a convolution kernel) every gather entry carries a weight, the grid side N is twice
 // the image side, and the row tasks transform only the central N/2 rows and keep their central N/2 pixels,
@@ -253,7 +480,7 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     const int tid = threadIdx.x, r = tid >> 5, lane = tid & 31;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
-    if (!wait_count(P, P.col_done + k, P.n_cb, s_flag)) return nullptr;
+    if (!wait_count(P, P.col_done + k, P.n_cb + P.extra_wait, s_flag)) return nullptr;
     const float w = P.wk[f];
     const float inv = 1.0f / (w > 0.f ? w : 1.f);
 #pragma unroll 1
@@ -309,25 +536,37 @@ __device__ int* row_task(const FftParams& P, int k, int rb, const float2* s_pre,
     return P.row_done + k;
 }
 
-template <int N, typename T> constexpr size_t fft_smem() {
+// Side 512 with nearest-cell gridding keeps the column-major ring and the register row pass.
+template <int N, bool WT> constexpr bool ring_cm() { return N == 512 && !WT; }
+
+template <int N, typename T, bool WT> constexpr size_t fft_smem() {
     constexpr int M = N / 2;
-    constexpr size_t tw = (size_t)(even(tw_size(N)) + even(M / 2 + 1) + even(tw_size(M))) * sizeof(float2);
     constexpr size_t col = (size_t)kCW * tile_ld<N>() * sizeof(T);
-    constexpr size_t row = (size_t)kRB * tile_ld<M>() * sizeof(float2);
-    return tw + (col > row ? col : row);
+    if constexpr (ring_cm<N, WT>()) {
+        constexpr size_t col2 = (size_t)2 * kCW * N * sizeof(T);   // two unpadded columns per warp
+        constexpr size_t row = (size_t)32 * kRowLd * sizeof(float2);
+        return (size_t)32 * 16 * sizeof(float2) + (col2 > row ? col2 : row);
+    } else {
+        constexpr size_t tw = (size_t)(even(tw_size(N)) + even(M / 2 + 1) + even(tw_size(M))) * sizeof(float2);
+        constexpr size_t row = (size_t)kRB * tile_ld<M>() * sizeof(float2);
+        return tw + (col > row ? col : row);
+    }
 }
 
-// 32 warps per SM for sides up to 512 (measured faster than 24, despite a few register spills).
-template <int N, typename T, bool WT>
-__global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persistent(const FftParams P) {
+// MINB resident CTAs per SM: 4 (32 warps) for sides up to 512 in the row-major form (measured faster than 24
+// warps, despite a few register spills), 2 or 3 for the side-512 column-major form (its register row pass
+// holds two butterflies' 32 points per lane; the autotuner picks), 1 above 512.
+template <int N, typename T, bool WT, int MINB>
+__global__ void __launch_bounds__(kPT, MINB) k_fft_persistent(const FftParams P) {
     constexpr int M = N / 2;
+    constexpr bool CM = ring_cm<N, WT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* s_twc = reinterpret_cast<float2*>(smem_raw);
-    float2* s_pre = s_twc + even(tw_size(N));
-    float2* s_twr = s_pre + even(M / 2 + 1);
-    unsigned char* work = reinterpret_cast<unsigned char*>(s_twr + even(tw_size(M)));
-    __shared__ int s_ticket, s_flag;
-    __shared__ uint32_t s_occ[kW * 32];            // per warp: occupancy of its column, one word per lane
+    float2* s_pre = s_twc + (CM ? 32 * 16 : even(tw_size(N)));
+    float2* s_twr = s_pre + (CM ? 0 : even(M / 2 + 1));
+    unsigned char* work = reinterpret_cast<unsigned char*>(s_twr + (CM ? 0 : even(tw_size(M))));
+    __shared__ int s_ticket[2], s_flag;
+    __shared__ uint32_t s_occ[2 * kW * 32];        // per column of a task: its occupancy, one word per lane
     const int tid = threadIdx.x;
     if constexpr (N == 512) {
         // exp(2 pi i k r / 512) = the pre-twiddle table's entry m = k r, or minus that of m - 256
@@ -340,55 +579,65 @@ __global__ void __launch_bounds__(kPT, (N <= 512 ? 32 / kW : 1)) k_fft_persisten
     } else {
         for (int e = tid; e < tw_size(N); e += kPT) s_twc[e] = P.tw[tws_col(N) + e];
     }
-    for (int e = tid; e <= M / 2; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
-    if constexpr (M == 256 && kRPW == 2) {
-        // exp(2 pi i j r / 256) = exp(2 pi i m / N) with m = 2 j r: the pre-twiddle table's entry m, or minus
-        // that of m - N / 2 (entries 0 .. N / 2 are stored)
-        static_assert(15 * 16 <= tw_size(M), "radix-16 table must fit the row table's room");
-        for (int e = tid; e < 15 * 16; e += kPT) {
-            const int m = 2 * (e & 15) * (e / 16 + 1);
-            const float2 w = P.tw[tws_pre(N) + (m <= N / 2 ? m : m - N / 2)];
-            s_twr[e] = m <= N / 2 ? w : make_float2(-w.x, -w.y);
+    if constexpr (!CM) {
+        for (int e = tid; e <= M / 2; e += kPT) s_pre[e] = P.tw[tws_pre(N) + e];
+        if constexpr (M == 256 && kRPW == 2) {
+            // exp(2 pi i j r / 256) = exp(2 pi i m / N) with m = 2 j r: the pre-twiddle table's entry m, or minus
+            // that of m - N / 2 (entries 0 .. N / 2 are stored)
+            static_assert(15 * 16 <= tw_size(M), "radix-16 table must fit the row table's room");
+            for (int e = tid; e < 15 * 16; e += kPT) {
+                const int m = 2 * (e & 15) * (e / 16 + 1);
+                const float2 w = P.tw[tws_pre(N) + (m <= N / 2 ? m : m - N / 2)];
+                s_twr[e] = m <= N / 2 ? w : make_float2(-w.x, -w.y);
+            }
+        } else {
+            for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
         }
-    } else {
-        for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
     }
     const int seg = P.n_cb + P.n_rb;
     const int total = (P.n_img + P.lag) * seg;
-    if (tid == 0) s_ticket = atomicAdd(P.tickets, 1);
+    // Thread 0 asks for the next ticket when a task starts, so the atomic's round trip overlaps the task, and
+    // publishes it in the other half of a two-entry slot (warps still reading this task's entry are not
+    // disturbed).  One barrier ends each task; thread 0 releases the finished task's counter after it (the
+    // fence orders the whole CTA's accesses of the task before the counter) while the other warps go on.
+    if (tid == 0) s_ticket[0] = atomicAdd(P.tickets, 1);
     __syncthreads();
-    for (;;) {
-        const int t = s_ticket;
+    for (int it = 0;; it ^= 1) {
+        const int t = s_ticket[it];
         if (t >= total) break;
+        int nt = 0;
+        if (tid == 0) nt = atomicAdd(P.tickets, 1);
         const int sg = t / seg, r = t - sg * seg;
         int* done = nullptr;
         if (r < P.n_cb) {
-            if (sg < P.n_img) done = column_task<N, T, WT>(P, sg, r, s_twc, work, s_occ, &s_flag);
+            if (sg < P.n_img) {
+                if constexpr (CM)
+                    done = column_task512<T>(P, sg, r, s_twc, work, s_occ);
+                else
+                    done = column_task<N, T, WT>(P, sg, r, s_twc, work, s_occ, &s_flag);
+            }
         } else {
             const int k = sg - P.lag;
-            if (k >= 0 && k < P.n_img) done = row_task<N, T, WT>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
-        }
-        // every thread's reads and writes of the task are done; thread 0 takes the next ticket and releases the
-        // task (the fence orders the whole CTA's accesses before the counter), its latencies overlapping.  (Taking
-        // the ticket earlier, during the task, measured slower.)
-        __syncthreads();
-        if (tid == 0) {
-            const int nt = atomicAdd(P.tickets, 1);
-            const int ab = ld_relaxed(P.tickets + 1);
-            if (done) {
-                __threadfence();
-                atomicAdd(done, 1);
+            if (k >= 0 && k < P.n_img) {
+                if constexpr (CM)
+                    done = row_task512<T>(P, k, r - P.n_cb, work);
+                else
+                    done = row_task<N, T, WT>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
             }
-            s_ticket = ab ? total : nt;
         }
+        if (tid == 0) s_ticket[it ^ 1] = ld_relaxed(P.tickets + 1) ? total : nt;
         __syncthreads();
+        if (tid == 0 && done) {
+            __threadfence();
+            atomicAdd(done, 1);
+        }
     }
 }
 
-template <int N, typename T, bool WT>
+template <int N, typename T, bool WT, int MINB>
 blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
-    auto kern = k_fft_persistent<N, T, WT>;
-    const size_t smem = fft_smem<N, T>();
+    auto kern = k_fft_persistent<N, T, WT, MINB>;
+    const size_t smem = fft_smem<N, T, WT>();
     static int per_sm = 0;                         // attributes and occupancy once per instantiation
     if (!per_sm) {
         if (smem > 48 * 1024)
@@ -397,12 +646,24 @@ blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
         BLINK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPT, smem));
     }
     if (per_sm < 1) return set_error(BLINK_ERR_UNSUPPORTED, "persistent FFT kernel does not fit on an SM");
-    P.n_cb = N / 2 / kCW;
+    P.n_cb = N / 2 / (ring_cm<N, WT>() ? 2 * kCW : kCW);
     P.n_rb = (WT ? N / 2 : N) / (kRB * kRowBatches);
     const int per = ctas_per_sm > 0 ? std::min(ctas_per_sm, per_sm) : per_sm;
     kern<<<n_sm * per, kPT, smem, st>>>(P);
     BLINK_CUDA(cudaGetLastError());
     return BLINK_OK;
+}
+
+// Instantiation by resident CTAs per SM: the side-512 column-major form at 3 when asked, else 2; the others
+// at their fixed bound.
+template <int N, typename T, bool WT>
+blink_status launch_sized(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
+    if constexpr (ring_cm<N, WT>()) {
+        if (ctas_per_sm == 3) return launch_n<N, T, WT, 3>(P, n_sm, 3, st);
+        return launch_n<N, T, WT, 2>(P, n_sm, 2, st);
+    } else {
+        return launch_n<N, T, WT, (N <= 512 ? 32 / kW : 1)>(P, n_sm, ctas_per_sm, st);
+    }
 }
 
 }  // namespace
@@ -411,20 +672,52 @@ blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
 // tasks trail by enough images that they rarely wait, and the ring is a little larger than the lag so that
 // reusing a slot rarely waits either, while staying small enough to live in L2.  The autotuner picks among
 // these shapes per plan.
-std::vector<FftTune> fft_tune_candidates() {
+std::vector<FftTune> fft_tune_candidates(const Plan& p) {
+    if (p.N == 512 && !p.d_wt)
+        return {{48, 32, 2}, {64, 32, 2}, {32, 24, 3}, {48, 32, 3}, {48, 24, 3}, {64, 32, 3}, {64, 48, 3}};
     return {{24, 16, 0}, {16, 8, 0}, {32, 24, 0}, {48, 32, 0}, {64, 48, 0}, {40, 32, 0}, {32, 24, 3}};
 }
 int fft_ring_images_max() { return 64; }
 
+bool fft_takes_gathered(const Plan& p) { return p.N == 512 && !p.d_wt && p.d_gsrc && p.e_stride > 0; }
+
+// exp(2 pi i m / 512) for m in [0, 512) into constant memory of the current device: the first octant's
+// angles in FP64, the others by the exact symmetries of the circle, so that quarter turns are exact.
+blink_status fft_constants(int N) {
+    if (N != 512) return BLINK_OK;
+    float2 t[512];
+    for (int m = 0; m < 512; m++) {
+        const int q = m / 128, k = m % 128;
+        double c = 1.0, s = 0.0;
+        if (k) {
+            const double a = 2.0 * 3.14159265358979323846 * k / 512.0;
+            c = std::cos(a);
+            s = std::sin(a);
+        }
+        const double x = q == 0 ? c : q == 1 ? -s : q == 2 ? -c : s;
+        const double y = q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
+        t[m] = make_float2((float)x, (float)y);
+    }
+    BLINK_CUDA(cudaMemcpyToSymbol(c_circ512, t, sizeof(t)));
+    return BLINK_OK;
+}
+
 blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec, const float2* d_vis,
                                    int64_t vis_stride, int vis_first, int tau0, int n_tau, void* d_H, int* d_counters,
-                                   float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st) {
+                                   float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st,
+                                   const FftWait& wait, bool gathered) {
+    if (gathered && !fft_takes_gathered(p))
+        return set_error(BLINK_ERR_UNSUPPORTED, "gather-ordered sums need the side-512 nearest-cell plan");
     FftParams P{};
+    P.gathered = gathered ? 1 : 0;
+    P.e_stride = p.e_stride;
+    P.wait_budget = wait.budget > 0 ? wait.budget : 1;
+    P.extra_wait = wait.extra;
     P.vis = d_vis;
     P.vis_stride = vis_stride;
     P.vis_first = vis_first;
     {
-        const uint64_t bytes = (uint64_t)p.B * sizeof(float2);
+        const uint64_t bytes = gathered ? (uint64_t)p.e_stride * sizeof(float2) : (uint64_t)p.B * sizeof(float2);
         const bool ok = bytes % 16 == 0 && (vis_stride * sizeof(float2)) % 16 == 0 &&
                         reinterpret_cast<uintptr_t>(d_vis) % 16 == 0 && bytes < (1ull << 31);
         P.vis_prefetch = ok ? (uint32_t)bytes : 0u;
@@ -455,11 +748,11 @@ blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec,
         return set_error(BLINK_ERR_UNSUPPORTED, "convolutional gridding needs a grid side of at least 128");
     const int c = tune.ctas_per_sm;
     switch (p.N) {
-        case 64: return bf ? launch_n<64, __nv_bfloat162, false>(P, n_sm, c, st) : launch_n<64, float2, false>(P, n_sm, c, st);
+        case 64: return bf ? launch_sized<64, __nv_bfloat162, false>(P, n_sm, c, st) : launch_sized<64, float2, false>(P, n_sm, c, st);
 #define BLINK_FFT_CASE(NN)                                                                                  \
         case NN:                                                                                            \
-            if (wt) return bf ? launch_n<NN, __nv_bfloat162, true>(P, n_sm, c, st) : launch_n<NN, float2, true>(P, n_sm, c, st); \
-            return bf ? launch_n<NN, __nv_bfloat162, false>(P, n_sm, c, st) : launch_n<NN, float2, false>(P, n_sm, c, st);
+            if (wt) return bf ? launch_sized<NN, __nv_bfloat162, true>(P, n_sm, c, st) : launch_sized<NN, float2, true>(P, n_sm, c, st); \
+            return bf ? launch_sized<NN, __nv_bfloat162, false>(P, n_sm, c, st) : launch_sized<NN, float2, false>(P, n_sm, c, st);
         BLINK_FFT_CASE(128)
         BLINK_FFT_CASE(256)
         BLINK_FFT_CASE(512)

@@ -64,16 +64,13 @@ __global__ void k_cells(const double* __restrict__ enu, const short2* __restrict
     cells[idx] = c;
 }
 
-__global__ void k_phase_vis(float2* __restrict__ vis, int64_t ld, int64_t B, int F, int first, int n_items,
-                            const float2* __restrict__ phase) {
+// gphase[f][p] = phase[f][gsrc[f][p]]: the phase-centre factors in the gather order of the plan's list
+__global__ void k_gather_phase(const float2* __restrict__ phase, const uint16_t* __restrict__ gsrc, int64_t B,
+                               int e_stride, int F, float2* __restrict__ gphase) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n_items * B) return;
-    const int it = (int)(idx / B);
-    const int64_t b = idx - (int64_t)it * B;
-    const float2 ph = phase[(int64_t)((first + it) % F) * B + b];
-    float2* z = vis + (int64_t)it * ld + b;
-    const float2 x = *z;
-    *z = make_float2(x.x * ph.x - x.y * ph.y, x.x * ph.y + x.y * ph.x);
+    if (idx >= (int64_t)F * e_stride) return;
+    const int64_t f = idx / e_stride;
+    gphase[idx] = phase[f * B + gsrc[idx]];
 }
 
 }  // namespace
@@ -88,11 +85,10 @@ void launch_cells(const Plan& p, cudaStream_t st) {
                                               p.phased ? 1 : 0, bs, p.d_cells, p.d_uvw, p.d_phase);
 }
 
-blink_status launch_phase_vis(float2* vis, int64_t ld, const Plan& p, int first, int n_items, cudaStream_t st) {
-    if (!p.d_phase || n_items <= 0) return BLINK_OK;
-    const int64_t n = (int64_t)n_items * p.B;
-    const int thr = 256;
-    k_phase_vis<<<(unsigned)((n + thr - 1) / thr), thr, 0, st>>>(vis, ld, p.B, p.F, first, n_items, p.d_phase);
+blink_status launch_gather_phase(const Plan& p, cudaStream_t st) {
+    if (!p.d_phase || !p.d_gsrc || !p.d_gphase) return BLINK_OK;
+    const int64_t n = (int64_t)p.F * p.e_stride;
+    k_gather_phase<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p.d_phase, p.d_gsrc, p.B, p.e_stride, p.F, p.d_gphase);
     BLINK_CUDA(cudaGetLastError());
     return BLINK_OK;
 }

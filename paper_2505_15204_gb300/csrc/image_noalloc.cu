@@ -55,15 +55,9 @@ using namespace blink;
 
 extern "C" blink_status blink_image_noalloc(const blink_imaging* imaging, const float* d_grid, int32_t n_images,
                                             const float* d_weight, float* d_img, void* stream) {
-    if (!imaging) return set_error(BLINK_ERR_INVALID_ARG, "imaging descriptor is NULL");
+    BLINK_TRY(check_imaging(imaging));
+    BLINK_TRY(nearest_only(imaging, "blink_image_noalloc"));
     const int N = imaging->n_pix, prec = imaging->precision;
-    if (N < 64 || N > 2048 || (N & (N - 1)))
-        return set_error(BLINK_ERR_UNSUPPORTED, "imaging.n_pix must be a power of two in [64, 2048]");
-    if (prec != BLINK_PREC_FP32 && prec != BLINK_PREC_BF16)
-        return set_error(BLINK_ERR_INVALID_ARG, "imaging.precision must be BLINK_PREC_FP32 or BLINK_PREC_BF16");
-    if (imaging->support >= 2)
-        return set_error(BLINK_ERR_UNSUPPORTED, "blink_image_noalloc: gridding with a convolution kernel runs in the "
-                                                "batched pipeline forms only");
     if (!d_grid || !d_weight || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_grid, d_weight or d_img is NULL");
     if (n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "n_images < 0");
     if (((uintptr_t)d_grid & 7) || ((uintptr_t)d_img & 7))
@@ -75,9 +69,11 @@ extern "C" blink_status blink_image_noalloc(const blink_imaging* imaging, const 
         return set_error(BLINK_ERR_UNSUPPORTED,
                          "blink_image_noalloc: one image's column-pass result exceeds the 16 MiB static scratch "
                          "(largest side: 1024 with FP32 storage, 2048 with BF16 storage)");
-    if (n_images == 0) return BLINK_OK;
+    // the set-up runs on every call, a zero-image call included, so that such a call can serve as the
+    // warm-up that commits the scratch before memory is reserved or a capture begins
     void* scratch = nullptr;
     BLINK_TRY(scratch_for_current_device(&scratch));
+    if (n_images == 0) return BLINK_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float2* tw = static_cast<float2*>(scratch);
     void* H = static_cast<unsigned char*>(scratch) + kTwiddleBytes;

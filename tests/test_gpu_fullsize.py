@@ -10,6 +10,7 @@ import pytest
 
 import blinksynth as bs
 import oracle
+from imgcheck import assert_image_close
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +63,6 @@ def test_fullband_chunk_images_on_sampled_ids(chunk):
                               n_threads=8)
         got = img[torch.from_numpy(ids).cuda()].cpu().numpy()
         for k, q in enumerate(ids):
-            err = np.linalg.norm(got[k] - ref["images"][k]) / np.linalg.norm(ref["images"][k])
-            assert err <= 1e-4, (q, err)
+            assert_image_close(got[k], ref["images"][k], q)
     finally:
         B.blink_destroy(ctx)

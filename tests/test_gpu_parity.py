@@ -2,7 +2,7 @@
 
 Correlation and cell maps must match bit for bit; grids and images within the FP32 tolerances below
 (images: relative RMS <= 1e-4 against the FP64 oracle, the precision gate of the method's mixed-precision
-form).  Sizes span several tiles and waves and include ragged ends.
+form, and max |diff| <= 1e-5 max |ref| pointwise; tests/imgcheck.py).  Sizes span several tiles and waves and include ragged ends.
 """
 import numpy as np
 import pytest
@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-IMG_RTOL = 1e-4          # relative RMS, FP32 imaging against the FP64 oracle
+from imgcheck import IMG_MAXTOL, IMG_RTOL, assert_image_close, image_errors  # noqa: F401  (shared gates)
+
 GRID_RTOL = 2e-6         # max |diff| / max |G|, FP32 gridding sums of FP32 visibilities
 
 
@@ -176,8 +177,7 @@ def test_image_stage_on_oracle_grid(B, ctx):
         wt = torch.tensor([ref["W"][0]], dtype=torch.float32, device="cuda")
         B.blink_image(ctx, B.Imaging(n_pix), dev(g), 1, wt, img)
         B.blink_sync(ctx)
-        err = rel_rms(img[0].cpu().numpy(), ref["images"][0])
-        assert err <= 1e-5, (n_pix, err)
+        assert_image_close(img[0].cpu().numpy(), ref["images"][0], n_pix, rms_tol=1e-5)
 
 
 def test_image_stage_nyquist_column(B, ctx):
@@ -227,8 +227,7 @@ def test_pipeline_matches_oracle(B, ctx, case, mode, arith):
     ref = oracle.pipeline(volt, w["enu"], freqs, 10, c, n_pix, flags=fl, pol=pol, autos=bool(autos), n_threads=8)
     got = img.cpu().numpy()
     for q in range(T * F):
-        err = rel_rms(got[q], ref["images"][q])
-        assert err <= IMG_RTOL, (q, err)
+        assert_image_close(got[q], ref["images"][q], q)
         assert wts[q].item() == ref["W"][q]
 
 
@@ -243,7 +242,7 @@ def test_pipeline_many_waves_sampled(B, ctx):
     ids = np.array([0, 63, 64, 127, 255, 300, 511])
     ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n_pix, ids=ids, n_threads=8)
     for k, q in enumerate(ids):
-        assert rel_rms(img[q].cpu().numpy(), ref["images"][k]) <= IMG_RTOL, q
+        assert_image_close(img[q].cpu().numpy(), ref["images"][k], q)
 
 
 def test_pipeline_is_bitwise_reproducible(B, ctx):
@@ -403,7 +402,7 @@ def test_pipeline_sets_uneven_flags_and_sizes(B, ctx):
         ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, n, flags=st.flags, fine0=st.fine0, n_fine=8, n_threads=8)
         part = got[at:at + 8 * n * n].reshape(8, n, n)
         for q in range(8):
-            assert rel_rms(part[q], ref["images"][q]) <= IMG_RTOL, (st.fine0, q)
+            assert_image_close(part[q], ref["images"][q], (st.fine0, q))
         at += 8 * n * n
     with pytest.raises(B.BlinkError):
         B.blink_pipeline_sets(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 10), sets, 1, dev(volt), img, total - 1)
@@ -498,7 +497,7 @@ def test_pipeline_with_gains_matches_oracle(B, ctx, arith, mode, pol):
                           n_threads=8)["images"]
     got = img.cpu().numpy()
     for q in range(2 * F):
-        assert rel_rms(got[q], ref[q]) <= IMG_RTOL, (q, rel_rms(got[q], ref[q]))
+        assert_image_close(got[q], ref[q], (q, rel_rms(got[q], ref[q])))
 
 
 @pytest.mark.parametrize("arith", [0, 1])
@@ -531,7 +530,7 @@ def test_pipeline_sets_with_gains(B, ctx):
                               gains=g[st.fine0:st.fine0 + 8].astype(np.complex128))
         part = got[at:at + 8 * n * n].reshape(8, n, n)
         for q in range(8):
-            assert rel_rms(part[q], ref["images"][q]) <= IMG_RTOL, (st.fine0, q)
+            assert_image_close(part[q], ref["images"][q], (st.fine0, q))
         at += 8 * n * n
 
 
@@ -565,7 +564,7 @@ def test_dedispersed_pipeline_images_match_oracle(B, ctx):
     ref = oracle.dedisperse(ref_img, d)
     got = out.cpu().numpy()
     for t in range(T - 2):
-        assert rel_rms(got[t], ref[t]) <= IMG_RTOL
+        assert_image_close(got[t], ref[t])
 
 
 def test_dedisperse_rejects_bad_delays(B, ctx):
@@ -613,7 +612,7 @@ def test_pipeline_with_jones_matches_oracle(B, ctx, arith, pol):
                           n_threads=8)["images"]
     got = img.cpu().numpy()
     for q in range(2 * F):
-        assert rel_rms(got[q], ref[q]) <= IMG_RTOL, (q, rel_rms(got[q], ref[q]))
+        assert_image_close(got[q], ref[q], (q, rel_rms(got[q], ref[q])))
 
 
 def test_diagonal_jones_images_equal_gains_images(B, ctx):
@@ -630,7 +629,7 @@ def test_diagonal_jones_images_equal_gains_images(B, ctx):
     B.blink_pipeline(ctx, B.Array(w["enu"], None, None, J), obs, im, 1, 0, dev(volt), b)
     B.blink_sync(ctx)
     for q in range(16):
-        assert rel_rms(b[q].cpu().numpy(), a[q].cpu().numpy()) <= 1e-6
+        assert_image_close(b[q].cpu().numpy(), a[q].cpu().numpy(), q, rms_tol=1e-6)
 
 
 # ---------------------------------------------------------------------------------------------------
@@ -663,8 +662,7 @@ def test_kb_pipeline_matches_oracle(B, ctx, case, arith):
                           support=W)
     got = img.cpu().numpy()
     for q in range(T * F):
-        err = rel_rms(got[q], ref["images"][q])
-        assert err <= IMG_RTOL, (q, err)
+        assert_image_close(got[q], ref["images"][q], q)
         assert wts[q].item() == ref["W"][q]
 
 
@@ -686,8 +684,8 @@ def test_kb_pipeline_with_gains_and_sets(B, ctx):
     part0 = got[:8 * 256 * 256].reshape(8, 256, 256)
     part1 = got[8 * 256 * 256:].reshape(8, 128, 128)
     for q in range(8):
-        assert rel_rms(part0[q], ref0[q]) <= IMG_RTOL, q
-        assert rel_rms(part1[q], ref1[q]) <= IMG_RTOL, q
+        assert_image_close(part0[q], ref0[q], q)
+        assert_image_close(part1[q], ref1[q], q)
 
 
 @pytest.mark.parametrize("per_pass", [0, 3])

@@ -130,7 +130,18 @@ def test_image_noalloc_limits_without_context():
     _expect(B.BLINK_ERR_UNSUPPORTED, "16 MiB static scratch", fn, B.Imaging(2048), PTR, 1, PTR, PTR)
     _expect(B.BLINK_ERR_INVALID_ARG, "imaging.precision", fn, B.Imaging(64, precision=5), PTR, 1, PTR, PTR)
     _expect(B.BLINK_ERR_INVALID_ARG, "8-byte aligned", fn, B.Imaging(64), PTR, 1, PTR, PTR + 4)
-    fn(B.Imaging(64), PTR, 0, PTR, PTR)          # no images: nothing to do, no device touched
+    # the checks of blink_image: support, polarisation, phase centre, cell
+    _expect(B.BLINK_ERR_INVALID_ARG, "imaging.support", fn, B.Imaging(64, support=-1), PTR, 1, PTR, PTR)
+    _expect(B.BLINK_ERR_UNSUPPORTED, "convolution kernel", fn, B.Imaging(64, support=4), PTR, 1, PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "imaging.pol", fn, B.Imaging(64, pol=7), PTR, 1, PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "direction cosines", fn, B.Imaging(64, phase_centre=(0.9, 0.9)), PTR, 1, PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "cell_lambda", fn, B.Imaging(64, cell_lambda=float("inf")), PTR, 1, PTR, PTR)
+    # no images: only the set-up (the scratch's address on the current device) runs, a warm-up; without a GPU
+    # that set-up reports the CUDA error
+    try:
+        fn(B.Imaging(64), PTR, 0, PTR, PTR)
+    except B.BlinkError as e:
+        assert e.status == B.BLINK_ERR_CUDA, str(e)
 
 
 def test_dedisperse_validates_delays_before_any_device_work():

@@ -12,6 +12,7 @@ import blinksynth as bs
 import oracle
 
 from test_gpu_parity import IMG_RTOL, B, _case, _gains, check_cells_and_uvw, ctx, dev, rel_rms  # noqa: F401
+from imgcheck import assert_image_close
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +79,7 @@ def test_dedispersion_recovers_the_injected_dispersion_measure(B, ctx):
     assert max(peaks, key=peaks.get) == 500, peaks
     ref_img = oracle.pipeline(volt, enu, freqs, 10, 1, n, n_threads=8)["images"].reshape(T, F, n, n)
     ref = oracle.dedisperse(ref_img, pins._delays(freqs, 500))
-    assert rel_rms(out500, ref) <= IMG_RTOL
+    assert_image_close(out500, ref)
 
 
 # ---------------------------------------------------------------------------------------------------
@@ -134,8 +135,7 @@ def test_phase_centred_pipeline_matches_oracle(B, ctx, case, arith):
     ref = oracle.pipeline(volt, w["enu"], freqs, 10, c, n_pix, flags=fl, n_threads=8, support=W, phase_centre=pc)
     got = img.cpu().numpy()
     for q in range(T * F):
-        err = rel_rms(got[q], ref["images"][q])
-        assert err <= IMG_RTOL, (q, err)
+        assert_image_close(got[q], ref["images"][q], q)
         assert wts[q].item() == ref["W"][q]
 
 
@@ -157,3 +157,47 @@ def test_source_at_the_pointing_images_at_the_centre_pixel(B, ctx):
                                                         ("uneven", 256, 8, 1, True, (-0.05, 0.4))])
 def test_cells_and_uvw_bit_exact_off_zenith(B, ctx, name, n_pix, fine, c, flags, pc):
     check_cells_and_uvw(B, ctx, name, n_pix, fine, c, flags, pc)
+
+
+# ---------------------------------------------------------------------------------------------------
+# bounded device-side waits
+# ---------------------------------------------------------------------------------------------------
+
+def test_bounded_wait_runs_out_and_reports_timeout(B):
+    # The batched imaging kernel's row tasks are made to wait for one more column task than an image has
+    # (a count nothing reaches); each such wait gives up after its budget (2e6 cycles, about a millisecond),
+    # the launch stops and returns, and blink_sync reports BLINK_ERR_TIMEOUT.  Nothing faults or hangs; the
+    # same context then images correctly again once the setting is restored, and so does a fresh one.
+    w, volt, freqs, _ = _case("coarse", n_samples=20, fine=16)
+    n = 2 * 16
+    arr, obs, im = B.Array(w["enu"]), B.Obs(freqs, 1, 10, 20), B.Imaging(512)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, 1, 512, ids=np.array([0, n - 1]), n_threads=8)["images"]
+    c = B.blink_create(0)
+    try:
+        img = torch.empty((n, 512, 512), dtype=torch.float32, device="cuda")
+        d_volt = dev(volt)
+        B.blink_pipeline(c, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, d_volt, img)   # plan + tuning
+        B.blink_sync(c)
+        B.blink_set_wait_budget(c, 2_000_000, unreachable=True)
+        B.blink_pipeline(c, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, d_volt, img)
+        with pytest.raises(B.BlinkError) as e:
+            B.blink_sync(c)
+        assert e.value.status == B.BLINK_ERR_TIMEOUT
+        B.blink_sync(c)                                   # the status word was cleared by the report
+        B.blink_set_wait_budget(c, 0, unreachable=False)
+        img.fill_(float("nan"))
+        B.blink_pipeline(c, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, d_volt, img)
+        B.blink_sync(c)
+        got = img.cpu().numpy()
+        for k, q in enumerate((0, n - 1)):
+            assert_image_close(got[q], ref[k], q)
+    finally:
+        B.blink_destroy(c)
+    c2 = B.blink_create(0)
+    try:
+        img = torch.full((n, 512, 512), float("nan"), dtype=torch.float32, device="cuda")
+        B.blink_pipeline(c2, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, dev(volt), img)
+        B.blink_sync(c2)
+        assert_image_close(img[n - 1].cpu().numpy(), ref[1], "fresh context")
+    finally:
+        B.blink_destroy(c2)
