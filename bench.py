@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--arith", choices=["fp8", "fp32"], default="fp8")
     ap.add_argument("--mode", choices=["batched", "plain"], default="batched")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32", help="grid / FFT storage")
-    ap.add_argument("--cufft", action="store_true", help="also time cuFFT's batched c2r on the same grid shape")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparison forms (plain FP32, batched FP32, cuFFT, four-product correlation)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--samples", type=int, default=0, help="voltage samples per step (default: the 50 ms chunk)")
@@ -181,6 +182,20 @@ def workload_label(name: str, w) -> str:
     return f"{name}: {w.description}"
 
 
+def bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes):
+    """The workload description both arms print (the reference arm times a sample of the same workload)."""
+    L2_BYTES = 129 * 2 ** 20
+    small = in_bytes + out_bytes < 2 * L2_BYTES
+    return {"workload": workload_label(args.workload, w),
+            "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
+            "mode": args.mode, "precision": args.precision, "gains": bool(args.gains),
+            "jones": bool(args.jones), "support": args.support, "pointing": list(args.pointing),
+            "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
+                   "each step timed alone after a 516 MB buffer overwrite") if small else
+                  (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e9:.3g} GB per step exceed L2; "
+                   "no flush")}
+
+
 def image_sets(inp, w, ns):
     """(set, first image, images, side) of every channel set of the workload, images packed per set."""
     T = ns // w.samples_per_int
@@ -253,6 +268,8 @@ def run_reference(args, world, rank):
     inp = bs.build_workload(args.workload, chunk=chunk, workers=min(16, os.cpu_count() or 1), n_samples=ns)
     sets = image_sets(inp, w, ns)
     n_total = sum(c for _, _, c, _ in sets)
+    img_floats = sum(c * side * side for _, _, c, side in sets)
+    config = bench_config(args, w, ns, chunk, n_total, int(inp["volt"].size), img_floats * 4)
     n_per = max(2, cores)
     picks = pick_images(sets, n_per * (args.steps + args.warmup))
     times = []
@@ -274,9 +291,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "images/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tt / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64/f64", "data": "synthetic",
-        "config": {"workload": workload_label(args.workload, w), "images_per_step": n_per,
-                   "sample": "evenly spaced image ids of the chunk", "support": args.support,
-                   "pointing": list(args.pointing)},
+        "config": config,
         "cpu_baseline": {"value": v, "unit": "images/s", "cores": cores, "kind": "oracle",
                          "sample": f"{n_per} images per step, ids evenly spaced over the {n_total}-image chunk"},
         "e2e": {"value": v, "unit": "images/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -473,25 +488,50 @@ def run_ours(args, world, rank, local):
                   "bytes_per_launch": byts, "kernel": "k_dedisperse"}
         del dd
 
-    # cuFFT's batched complex-to-real transform of grids of the same shape (a timing reference only)
-    cufft = None
-    if args.cufft and rank == 0 and not multi:
+    # the forms the headline is compared with, on the same chunk (rank 0, single set, the default form only):
+    # plain FP32 per-image path, batched FP32-correlation path, cuFFT's batched c2r transform of grids of the
+    # same shape (the FFT stage alone), and the ABI correlation entry point's four-product visibilities
+    comparison = None
+    if rank == 0 and not multi and not args.no_compare and args.mode == "batched" and args.arith == "fp8":
+        def timed(fn, reps, warm=1):
+            for _ in range(warm):
+                fn()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+        ms_b32 = timed(lambda: B.blink_pipeline(ctx, arr, obs, im, B.BLINK_CORR_FP32, B.BLINK_MODE_BATCHED, volt, img,
+                                                None, stream), 3)
+        ns_p = min(ns, 2 * w.samples_per_int)                     # the per-image form on two integrations
+        n_p = (ns_p // w.samples_per_int) * w.n_out_chan
+        obs_p = B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns_p)
+        ms_p32 = timed(lambda: B.blink_pipeline(ctx, arr, obs_p, im, B.BLINK_CORR_FP32, B.BLINK_MODE_PLAIN, volt,
+                                                img, None, stream), 2)
+        B.blink_sync(ctx, stream)
         nb = 768
         g = torch.randn((nb, n_pix, n_pix // 2 + 1), dtype=torch.complex64, device="cuda")
-        o = torch.empty((nb, n_pix, n_pix), dtype=torch.float32, device="cuda")
-        for _ in range(3):
-            o = torch.fft.irfft2(g, s=(n_pix, n_pix))
-        torch.cuda.synchronize()
-        e0.record(stream)
-        reps = 10
-        for _ in range(reps):
-            o = torch.fft.irfft2(g, s=(n_pix, n_pix))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_f = e0.elapsed_time(e1) / reps
-        cufft = {"images_per_s": nb / (ms_f / 1e3), "batch": nb,
-                 "note": "torch.fft.irfft2 (cuFFT) on random half-plane grids: the FFT stage alone, no gridding"}
-        del g, o
+        ms_cf = timed(lambda: torch.fft.irfft2(g, s=(n_pix, n_pix)), 10, warm=3)
+        del g
+        Bn = n_tiles * (n_tiles + 1) // 2
+        vis4 = torch.empty(n_img * Bn * 8, dtype=torch.float32, device="cuda")
+        ms_v4 = timed(lambda: B.blink_correlate(ctx, arr, obs, B.BLINK_CORR_FP8, volt, vis4, stream), 3)
+        del vis4
+        B.blink_sync(ctx, stream)
+        plain = n_p / (ms_p32 / 1e3)
+        comparison = {
+            "plain_fp32_per_image": {"images_per_s": plain, "images_per_step": n_p,
+                                     "note": "correlate (CUDA cores) -> atomic grid -> column and row FFT, per image"},
+            "batched_fp32": {"images_per_s": n_img / (ms_b32 / 1e3), "ms_per_step": ms_b32},
+            "batched_mixed": {"images_per_s": value, "ms_per_step": ms_step},
+            "cufft_irfft2": {"images_per_s": nb / (ms_cf / 1e3), "batch": nb,
+                             "note": "torch.fft.irfft2 (cuFFT) of random half-plane grids: the FFT stage alone"},
+            "correlate_vis4": {"vis_per_s": n_img * Bn * 4 / (ms_v4 / 1e3), "ms_per_step": ms_v4,
+                               "note": "blink_correlate, FP8 tensor cores: XX, XY, YX, YY of every baseline, V = S / K"},
+            "multiple_vs_plain_fp32": value / plain,
+        }
 
     # end to end through the host-buffer entry point (pinned voltages in, pinned images out)
     e2e = None
@@ -536,19 +576,15 @@ def run_ours(args, world, rank, local):
         "dtype": ("e4m3->f32 correlation" if arith == B.BLINK_CORR_FP8 else "f32 correlation")
                  + (", bf16-stored f32 grid/FFT" if args.precision == "bf16" else ", f32 grid/FFT"),
         "data": "synthetic",
-        "config": {"workload": workload_label(args.workload, w),
-                   "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
-                   "mode": args.mode, "precision": args.precision, "gains": bool(args.gains),
-                   "jones": bool(args.jones), "support": args.support, "pointing": list(args.pointing),
-                   "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
-                          "each step timed alone after a 516 MB buffer overwrite") if small else
-                         (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e9:.3g} GB per step exceed L2; "
-                          "no flush"),
-                   "generate_s": round(t_gen, 2), "plan_s": round(t_plan, 3)},
+        "config": bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes),
+        "setup_s": {"generate": round(t_gen, 2), "plan": round(t_plan, 3)},
         "roofline": roof, "stages": stages, "clocks": clocks, "gpu_launches": launches,
-        "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "cufft_reference": cufft, "dedisperse": dedisp,
-        "vis_per_s": value * (n_tiles * (n_tiles + 1) // 2) * 2,
-        "vis_note": "visibilities formed per second: XX and YY products of every baseline incl. autos per image",
+        "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "comparison": comparison, "dedisperse": dedisp,
+        "baselines_per_s": value * (n_tiles * (n_tiles + 1) // 2),
+        "xx_yy_products_per_s": value * (n_tiles * (n_tiles + 1) // 2) * 2,
+        "rates_note": ("per image the imaging path correlates every baseline incl. autos (baselines_per_s) and forms "
+                       "its XX and YY products (xx_yy_products_per_s); the four-product visibilities of the "
+                       "correlation entry point are comparison.correlate_vis4"),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -42,7 +42,8 @@ constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second
 struct TcParams {
     int mode;                // CORR_OUT_*
     int n_tiles, ns, c, F, K;
-    int Kq;                  // K rounded up to a multiple of 4 (one 32-bit word of e4m3 values)
+    int ns_c, n_chunks;      // K streams through the operand tiles in chunks of ns_c samples (ns_c * c values)
+    int Kq;                  // a chunk's K rounded up to a multiple of 4 (one 32-bit word of e4m3 values)
     int units, n_blk, Kr, Kp;
     int n_pairs, n_rounds;
     int split;               // Stokes I with gains: XX and YY from separate MMA chains (per-polarisation K halves)
@@ -153,19 +154,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -254,21 +242,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
     const float div = (float)(P.mode == CORR_OUT_STOKES_I ? 2 * P.K : P.K);
     const int per_k = 2 * P.n_tiles;
 
-    auto issue = [&](int item, int b) {
+    // chunk j of an item: samples [j ns_c, j ns_c + ns_c) of its integration (the last chunk's excess is masked)
+    auto issue = [&](int item, int j, int b) {
         const int tau = item / P.F, f = item - (item / P.F) * P.F;
         mbar_expect_tx(bar_tma[b], (uint32_t)P.raw_bytes);
-        tma_load_3d(raw_s[b], &tmap, bar_tma[b], 0, f * P.c, tau * P.ns);
+        tma_load_3d(raw_s[b], &tmap, bar_tma[b], 0, f * P.c, tau * P.ns + j * P.ns_c);
+    };
+    // Steps: one per item when K fits one chunk (its TMEM rounds share the operands); else one per (item,
+    // round, chunk), each round re-streaming K and accumulating its block pairs in TMEM across the chunks.
+    auto advance = [&](int& i, int& r, int& j) {
+        if (++j < P.n_chunks) return;
+        j = 0;
+        if (P.n_chunks > 1 && ++r < P.n_rounds) return;
+        r = 0;
+        i += gridDim.x;
     };
 
-    int it = P.first_item + blockIdx.x;
-    if (tid == 0 && it < total) issue(it, 0);
-    pending[0] = it < total;
-    for (int buf = 0; it < total; it += gridDim.x, buf ^= 1) {
-        const int nxt = it + gridDim.x;
-        if (nxt < total) {
-            if (tid == 0) issue(nxt, buf ^ 1);
+    int ci = P.first_item + blockIdx.x, cr = 0, cj = 0;
+    if (tid == 0 && ci < total) issue(ci, 0, 0);
+    pending[0] = ci < total;
+    for (int buf = 0; ci < total; buf ^= 1) {
+        const int it = ci;
+        int ni = ci, nr = cr, nj = cj;
+        advance(ni, nr, nj);
+        if (ni < total) {
+            if (tid == 0) issue(ni, nj, buf ^ 1);
             pending[buf ^ 1] = true;
         }
+        const bool first_chunk = cj == 0, last_chunk = cj == P.n_chunks - 1;
+        const int Kv = min(P.ns_c, P.ns - cj * P.ns_c) * P.c;     // values of this chunk inside the item
         const bool ok = mbar_wait(bar_tma[buf], tma_par[buf]);
         tma_par[buf] ^= 1;
         pending[buf] = !ok;
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             abort = true;
             break;
         }
-        if (GAINS) {
+        if (GAINS && cr == 0 && first_chunk) {
             // this item's gains, read by the epilogue (after the barrier that ends the unpack)
             const int f = it - (it / P.F) * P.F;
             const int per = FULL ? 4 : 2;                        // float2 per tile: J[p][r], or g[p]
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                 const bool live = !sflags[a];
                 uint32_t w[4];
 #pragma unroll
-                for (int i = 0; i < 4; i++) w[i] = (live && k0 + i < P.K) ? lut[raw[(k0 + i) * per_k + r]] : 0u;
+                for (int i = 0; i < 4; i++) w[i] = (live && k0 + i < Kv) ? lut[raw[(k0 + i) * per_k + r]] : 0u;
                 const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], 0x0040), __byte_perm(w[2], w[3], 0x0040), 0x5410);
                 const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], 0x0051), __byte_perm(w[2], w[3], 0x0051), 0x5410);
                 const uint32_t nre = __byte_perm(__byte_perm(w[0], w[1], 0x0073), __byte_perm(w[2], w[3], 0x0073), 0x5410);
@@ -321,8 +323,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        // ---- MMA rounds of up to 8 block pairs, each followed by its epilogue ---------------------------
-        for (int r = 0; r < P.n_rounds && !abort; r++) {
+        // ---- MMA rounds of up to 8 block pairs, each followed (after the item's last chunk) by its epilogue -
+        const int r_lo = P.n_chunks > 1 ? cr : 0, r_hi = P.n_chunks > 1 ? cr + 1 : P.n_rounds;
+        for (int r = r_lo; r < r_hi && !abort; r++) {
             const int ppr = GAINS ? P.pairs_per_round : kTmemCols / 64;
             const int q0 = r * ppr, q1 = min(P.n_pairs, q0 + ppr);
             if (tid == 0) {
@@ -336,7 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                     // one chain over all of K, or (split) the X half into columns 0-63 and the Y half into 64-127
                     for (int s = 0; s < nk; s++)
                         mma_e4m3(GAINS && s >= nh ? d + 64 : d, smem_desc(a0 + s * 256, 128, sbo),
-                                 smem_desc(b0 + s * 256, 128, sbo), idesc, GAINS ? s % nh > 0 : s > 0);
+                                 smem_desc(b0 + s * 256, 128, sbo), idesc,
+                                 !first_chunk || (GAINS ? s % nh > 0 : s > 0));
                 }
                 mma_commit(bar_mma);
             }
@@ -347,6 +351,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                 break;
             }
             tc_fence_after();
+            if (!last_chunk) {                     // the accumulators go on with the next chunk
+                tc_fence_before();
+                __syncthreads();
+                continue;
+            }
             const int local = it - P.first_item;
             if (!GAINS && s_item) {
                 // gather order: every block pair of the round from TMEM straight into the item's copy (warp w reads
@@ -529,7 +538,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
             __syncthreads();
         }
         if (abort) break;
-        if (!GAINS && s_item) {
+        ci = ni;
+        cr = nr;
+        cj = nj;
+        if (!GAINS && s_item && last_chunk && (P.n_chunks == 1 || r_lo == P.n_rounds - 1)) {
             // the item in gather order: entry p of channel f takes baseline gsrc[f][p] (times the factor
             // gphase[f][p] off zenith), four entries per thread in flight, coalesced stores of both planes
             const int f = it % P.F;
@@ -592,58 +604,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
-}  // namespace
-
-// Shared memory of the gather-order form: operands, two raw blocks and the item's copy (2 B floats) must fit.
-bool corr_fp8_gathers(const Plan& p, int ns, int out_kind, GainRef gains) {
-    if (gains.d || out_kind == CORR_OUT_VIS4 || !p.d_gsrc || p.N / 2 + 1 <= 0) return false;
-    const int nt = p.n_tiles, c = p.chan_avg, K = ns * c;
-    if (nt % 8 || ns > 256 || c > 256) return false;
-    const int units = nt, n_blk = (units + kUnitsPerBlk - 1) / kUnitsPerBlk, Kq = (K + 3) / 4 * 4;
-    const int Kr = out_kind == CORR_OUT_STOKES_I ? 4 * Kq : 2 * Kq, Kp = (Kr + 31) / 32 * 32;
-    const uint32_t raw = (uint32_t)(ns * c * nt * 2);
-    uint32_t off = align_up((uint32_t)n_blk * 128u * Kp, 1024);
-    off = align_up(off + raw, 128);
-    off = align_up(off + raw, 128);
-    off = align_up(off + (uint32_t)(8 * p.B), 16);
-    off += 256 * 4 + align_up((uint32_t)nt, 16) + 32 + 8;
-    return off <= 227 * 1024;
-}
-
-blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
-                             int first_item, int n_items, void* out, int64_t out_item_stride, int* d_status, int n_sm,
-                             cudaStream_t st, GainRef gains, ImgOut io) {
-    if (n_items <= 0) return BLINK_OK;
-    const int nt = p.n_tiles, c = p.chan_avg, K = ns * c;
-    if (nt % 8 || ns > 256 || c > 256 || ((uintptr_t)d_volt & 15) || (sample_stride % 16))
-        return set_error(BLINK_ERR_UNSUPPORTED,
-                         "FP8 tensor-core correlation needs n_tiles % 8 == 0, samples_per_int <= 256, chan_avg <= 256 "
-                         "and a 16-byte aligned voltage block");
-    TcParams P{};
-    P.mode = out_kind;
-    P.n_tiles = nt;
-    P.ns = ns;
-    P.c = c;
-    P.F = p.F;
-    P.K = K;
-    const bool four = out_kind == CORR_OUT_VIS4 || (gains.d && gains.full);   // all four products
-    P.units = four ? 2 * nt : nt;
-    P.n_blk = (P.units + kUnitsPerBlk - 1) / kUnitsPerBlk;
-    P.Kq = (K + 3) / 4 * 4;
-    P.gains = gains.d;
-    P.gain_f0 = gains.f0;
-    P.split = gains.d && !gains.full && out_kind == CORR_OUT_STOKES_I;
+// Shared-memory layout of a launch whose chunks hold ns_c samples: operand tiles for the chunk's K, two raw
+// chunks (TMA, double buffered), the epilogue's staging buffers or the item's baseline-ordered copy (gather
+// order), gains, LUT, flags, barriers.  Fills the chunk-dependent fields of P; returns the bytes needed.
+size_t tc_layout(TcParams& P, int ns_c, bool gather, GainRef gains, int64_t B) {
+    const int nt = P.n_tiles;
+    const int Kc = ns_c * P.c;
+    P.ns_c = ns_c;
+    P.n_chunks = (P.ns + ns_c - 1) / ns_c;
+    P.Kq = (Kc + 3) / 4 * 4;
     P.Kpol = (2 * P.Kq + 31) / 32 * 32;
-    P.Kr = (out_kind == CORR_OUT_STOKES_I && !four) ? 4 * P.Kq : 2 * P.Kq;
+    const bool four = P.units == 2 * nt;
+    P.Kr = (P.mode == CORR_OUT_STOKES_I && !four) ? 4 * P.Kq : 2 * P.Kq;
     P.Kp = P.split ? 2 * P.Kpol : (P.Kr + 31) / 32 * 32;
-    P.n_pairs = P.n_blk * (P.n_blk + 1) / 2;
-    P.pair_cols = P.split ? 128 : 64;
-    P.pairs_per_round = kTmemCols / P.pair_cols;
-    P.n_rounds = (P.n_pairs + P.pairs_per_round - 1) / P.pairs_per_round;
-    P.stage_buf = (P.split ? 4 : 2) * kPlane;
-    P.first_item = first_item;
-    P.n_items = n_items;
-    P.raw_bytes = ns * c * nt * 2;
+    P.raw_bytes = ns_c * P.c * nt * 2;
     uint32_t off = align_up((uint32_t)P.n_blk * 128u * P.Kp, 1024);
     P.off_raw0 = off;
     off = align_up(off + P.raw_bytes, 128);
@@ -653,17 +627,12 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     P.off_im = off + kPlane * 4;
     const uint32_t gain_bytes = gains.d ? (uint32_t)nt * (gains.full ? 32 : 16) : 0;
     const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32 + (gains.d ? gain_bytes + 16 : 0);
-    if (io.gather) {
+    P.off_item = 0;
+    if (gather) {
         // gather order: the item's baseline-ordered copy takes the staging buffers' place
-        if (!corr_fp8_gathers(p, ns, out_kind, gains))
-            return set_error(BLINK_ERR_UNSUPPORTED, "FP8 correlation: gather order not available for this plan");
         P.off_item = off;
-        off = align_up(off + (uint32_t)(8 * p.B), 16);
-        P.gsrc = p.d_gsrc;
-        P.gphase = p.d_gphase;
-        P.ent_off = p.d_ent_off;
-        P.ent_ld = p.N / 2 + 1;
-        P.e_stride = p.e_stride;
+        off = align_up(off + (uint32_t)(8 * B), 16);
+        P.two_stage = 0;
     } else {
         P.two_stage = off + 2 * P.stage_buf * 4 + tail <= 227 * 1024;
         off = align_up(off + (P.two_stage ? 2 : 1) * P.stage_buf * 4, 16);
@@ -678,9 +647,84 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     off += 24;
     P.off_tmem = off;
     off += 8;
-    const size_t smem = std::max<size_t>(off, 120 * 1024);   // one CTA per SM: it owns all 512 TMEM columns
-    if (smem > 227 * 1024 || (uint32_t)P.Kp * 8 >= (1u << 18))
-        return set_error(BLINK_ERR_UNSUPPORTED, "FP8 tensor-core correlation: operands of this K do not fit shared memory");
+    if ((uint32_t)P.Kp * 8 >= (1u << 18)) return (size_t)1 << 30;
+    return std::max<size_t>(off, 120 * 1024);      // one CTA per SM: it owns all 512 TMEM columns
+}
+
+// The launch parameters that do not depend on the chunking; false when the form cannot run this request.
+bool tc_setup(TcParams& P, int out_kind, const Plan& p, int ns, GainRef gains) {
+    const int nt = p.n_tiles, c = p.chan_avg;
+    if (nt % 8 || c > 256 || ns < 1) return false;
+    P.mode = out_kind;
+    P.n_tiles = nt;
+    P.ns = ns;
+    P.c = c;
+    P.F = p.F;
+    P.K = ns * c;
+    const bool four = out_kind == CORR_OUT_VIS4 || (gains.d && gains.full);   // all four products
+    P.units = four ? 2 * nt : nt;
+    P.n_blk = (P.units + kUnitsPerBlk - 1) / kUnitsPerBlk;
+    P.gains = gains.d;
+    P.gain_f0 = gains.f0;
+    P.split = gains.d && !gains.full && out_kind == CORR_OUT_STOKES_I;
+    P.n_pairs = P.n_blk * (P.n_blk + 1) / 2;
+    P.pair_cols = P.split ? 128 : 64;
+    P.pairs_per_round = kTmemCols / P.pair_cols;
+    P.n_rounds = (P.n_pairs + P.pairs_per_round - 1) / P.pairs_per_round;
+    P.stage_buf = (P.split ? 4 : 2) * kPlane;
+    // exactness: the FP32 accumulator holds integers below 2^24; |S| <= 128 K per product, and Stokes I without
+    // split chains sums XX and YY in one accumulator
+    const int64_t bound = (out_kind == CORR_OUT_STOKES_I && !P.split && !four) ? 256 : 128;
+    return bound * P.K < ((int64_t)1 << 24);
+}
+
+// The largest chunk (samples, at most 256: the TMA box) whose layout fits; 0 if none does.
+int tc_chunk(TcParams& P, bool gather, GainRef gains, int64_t B) {
+    for (int ns_c = std::min(P.ns, 256);; ns_c = (ns_c + 1) / 2) {
+        if (tc_layout(P, ns_c, gather, gains, B) <= 227 * 1024) return ns_c;
+        if (ns_c == 1) return 0;
+    }
+}
+
+}  // namespace
+
+// Whether the gather-order form runs for this plan: no calibration, a gather source table, and a chunking
+// whose operands fit beside the item's copy (2 B floats) in shared memory.
+bool corr_fp8_gathers(const Plan& p, int ns, int out_kind, GainRef gains) {
+    if (gains.d || out_kind == CORR_OUT_VIS4 || !p.d_gsrc) return false;
+    TcParams P{};
+    if (!tc_setup(P, out_kind, p, ns, gains)) return false;
+    return tc_chunk(P, true, gains, p.B) > 0;
+}
+
+blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample_stride, const Plan& p, int ns,
+                             int first_item, int n_items, void* out, int64_t out_item_stride, int* d_status, int n_sm,
+                             cudaStream_t st, GainRef gains, ImgOut io) {
+    if (n_items <= 0) return BLINK_OK;
+    const int nt = p.n_tiles, c = p.chan_avg;
+    if (nt % 8 || c > 256 || ((uintptr_t)d_volt & 15) || (sample_stride % 16))
+        return set_error(BLINK_ERR_UNSUPPORTED,
+                         "FP8 tensor-core correlation needs n_tiles % 8 == 0, chan_avg <= 256 and a 16-byte aligned "
+                         "voltage block");
+    TcParams P{};
+    if (!tc_setup(P, out_kind, p, ns, gains))
+        return set_error(BLINK_ERR_UNSUPPORTED, "FP8 tensor-core correlation: K too large for exact FP32 accumulation "
+                                                "(128 K, or 256 K for Stokes I, must stay below 2^24)");
+    if (io.gather && !corr_fp8_gathers(p, ns, out_kind, gains))
+        return set_error(BLINK_ERR_UNSUPPORTED, "FP8 correlation: gather order not available for this plan");
+    const int ns_c = tc_chunk(P, io.gather, gains, p.B);
+    if (!ns_c)
+        return set_error(BLINK_ERR_UNSUPPORTED, "FP8 tensor-core correlation: operands do not fit shared memory");
+    const size_t smem = tc_layout(P, ns_c, io.gather, gains, p.B);
+    if (io.gather) {
+        P.gsrc = p.d_gsrc;
+        P.gphase = p.d_gphase;
+        P.ent_off = p.d_ent_off;
+        P.ent_ld = p.N / 2 + 1;
+        P.e_stride = p.e_stride;
+    }
+    P.first_item = first_item;
+    P.n_items = n_items;
     P.flags = p.d_flags;
     P.out = out;
     P.out_item_stride = out_item_stride;
@@ -694,7 +738,7 @@ blink_status launch_corr_fp8(int out_kind, const uint8_t* d_volt, int64_t sample
     CUtensorMap map;
     const cuuint64_t dims[3] = {(cuuint64_t)(nt / 2), (cuuint64_t)p.n_fine, (cuuint64_t)(last_tau + 1) * ns};
     const cuuint64_t strides[2] = {(cuuint64_t)nt * 2, (cuuint64_t)sample_stride};
-    const cuuint32_t box[3] = {(cuuint32_t)(nt / 2), (cuuint32_t)c, (cuuint32_t)ns};
+    const cuuint32_t box[3] = {(cuuint32_t)(nt / 2), (cuuint32_t)c, (cuuint32_t)ns_c};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint8_t*>(d_volt), dims, strides, box,
                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -1,5 +1,5 @@
 """Parity of the next-row extensions of the path with the CPU oracle (GPU): the phase centre on an
-off-zenith pointing, long integrations on the CUDA-core correlator, dedispersion recovering an injected
+off-zenith pointing, long integrations on both correlators, dedispersion recovering an injected
 dispersion measure, and the reproducibility and BF16 storage of gridding with a kernel.
 
 The file sorts after the core parity suite so that a failure here, under ``-x``, leaves the core results
@@ -24,10 +24,10 @@ torch = pytest.importorskip("torch")
 # ---------------------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("n_tiles,ns,c,const", [(16, 200, 4, False), (8, 10000, 4, False), (8, 10000, 4, True)])
-def test_long_integrations_exact_on_the_cuda_core_form(B, ctx, n_tiles, ns, c, const):
-    # K = 800 and 40,000 (20 ms and 1 s of 10 kHz channels averaged by 4): the CUDA-core form stays bit-exact
-    # (|S| <= 128 K < 2^24, reached by constant -8 - 8i voltages); the tensor-core form, which stages all of K
-    # in shared memory, reports UNSUPPORTED
+def test_long_integrations_exact_on_both_correlators(B, ctx, n_tiles, ns, c, const):
+    # K = 800 and 40,000 (20 ms and 1 s of 10 kHz channels averaged by 4): both forms stay bit-exact, the
+    # tensor-core one streaming K through its operand tiles in chunks that accumulate in TMEM (|S| <= 128 K
+    # < 2^24, reached by constant -8 - 8i voltages)
     enu = bs.tile_positions(n_tiles, 1500.0, 51)
     freqs = 155e6 + 10e3 * np.arange(c)
     if const:
@@ -39,16 +39,33 @@ def test_long_integrations_exact_on_the_cuda_core_form(B, ctx, n_tiles, ns, c, c
     want = oracle.visibilities(S, ns * c)
     if const:
         assert np.all(S[..., 0, 0] == ns * c * 128)
-    out = torch.empty(S.shape, dtype=torch.float32, device="cuda")
     arr, obs = B.Array(enu), B.Obs(freqs, c, ns, ns)
-    B.blink_correlate(ctx, arr, obs, 0, dev(v), out)
+    for arith in (B.BLINK_CORR_FP32, B.BLINK_CORR_FP8):
+        out = torch.full(S.shape, float("nan"), dtype=torch.float32, device="cuda")
+        B.blink_correlate(ctx, arr, obs, arith, dev(v), out)
+        B.blink_sync(ctx)
+        got = out.cpu().numpy()
+        assert np.array_equal(got[..., 0], want.real.astype(np.float32)), arith
+        assert np.array_equal(got[..., 1], want.imag.astype(np.float32)), arith
+
+
+@pytest.mark.parametrize("ns,c", [(200, 4), (2000, 4)])
+def test_long_integration_images_on_the_tensor_core_form(B, ctx, ns, c):
+    # Stokes-I images of 144 tiles at K = 800 and 8,000 through the batched FP8 path (gather-ordered sums,
+    # K streamed in chunks), against the FP64 oracle
+    w, volt, freqs, _ = _case("precision")
+    enu = w["enu"]
+    freqs = 155e6 + 10e3 * np.arange(2 * c)
+    sky = bs.Sky(lmn=np.array([[0.05, -0.08, np.sqrt(1 - 0.0089)]]), power=np.array([2.0]))
+    v = bs.voltages(enu, freqs, ns, sky, seed=61)
+    ref = oracle.pipeline(v, enu, freqs, ns, c, 512, n_threads=8)["images"]
+    img = torch.empty((2, 512, 512), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(enu), B.Obs(freqs, c, ns, ns), B.Imaging(512), B.BLINK_CORR_FP8,
+                     B.BLINK_MODE_BATCHED, dev(v), img)
     B.blink_sync(ctx)
-    got = out.cpu().numpy()
-    assert np.array_equal(got[..., 0], want.real.astype(np.float32))
-    assert np.array_equal(got[..., 1], want.imag.astype(np.float32))
-    with pytest.raises(B.BlinkError) as e:
-        B.blink_correlate(ctx, arr, obs, 1, dev(v), out)
-    assert e.value.status == B.BLINK_ERR_UNSUPPORTED
+    got = img.cpu().numpy()
+    for q in range(2):
+        assert_image_close(got[q], ref[q], q)
 
 
 # ---------------------------------------------------------------------------------------------------
