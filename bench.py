@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--arith", choices=["fp8", "fp32"], default="fp8")
     ap.add_argument("--mode", choices=["batched", "plain"], default="batched")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32", help="grid / FFT storage")
+    ap.add_argument("--fused", action="store_true",
+                    help="correlate inside the imaging launch (one persistent launch per step)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the comparison forms (plain FP32, batched FP32, cuFFT, four-product correlation)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -145,12 +147,14 @@ def stage_bytes(stage: int, n_tiles: int, n_pix: int, K: int) -> float:
         return K * 2 * n_tiles + 8 * B
     if stage == 1:                                    # visibilities in, images out (intermediate on chip / L2)
         return 8 * B + 4 * n_pix * n_pix
+    if stage == 3:                                    # fused: the image's voltage share in, the image out
+        return K * 2 * n_tiles + 4 * n_pix * n_pix
     return 8 * half + 4 * n_pix * n_pix               # half plane in, image out
 
 
-STAGE_NAMES = ["correlate", "grid + 2D FFT", "row c2r FFT"]
-STAGE_KERNELS = ["k_corr_tc", "k_fft_persistent", "k_rowpass"]
-STAGE_SOURCES = ["correlate_tc.cu", "fft_persistent.cu", "grid_fft.cu"]
+STAGE_NAMES = ["correlate", "grid + 2D FFT", "row c2r FFT", "correlate + grid + 2D FFT (fused)"]
+STAGE_KERNELS = ["k_corr_tc", "k_fft_persistent", "k_rowpass", "k_fft_persistent"]
+STAGE_SOURCES = ["correlate_tc.cu", "fft_persistent.cu", "grid_fft.cu", "fft_persistent.cu"]
 
 
 def source_hash(name: str) -> str:
@@ -188,7 +192,7 @@ def bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes):
     small = in_bytes + out_bytes < 2 * L2_BYTES
     return {"workload": workload_label(args.workload, w),
             "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
-            "mode": args.mode, "precision": args.precision, "gains": bool(args.gains),
+            "mode": args.mode, "precision": args.precision, "gains": bool(args.gains), "fused": bool(args.fused),
             "jones": bool(args.jones), "support": args.support, "pointing": list(args.pointing),
             "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
                    "each step timed alone after a 516 MB buffer overwrite") if small else
@@ -336,6 +340,8 @@ def run_ours(args, world, rank, local):
     if multi and mode != B.BLINK_MODE_BATCHED:
         raise SystemExit("several channel sets run only in the batched mode")
     ctx = B.blink_create(local)
+    if args.fused:
+        B.blink_set_fused(ctx, True)
     prec = B.BLINK_PREC_BF16 if args.precision == "bf16" else B.BLINK_PREC_FP32
     gains = bench_gains(w.n_out_chan, n_tiles) if args.gains else None
     jones = bench_jones(w.n_out_chan, n_tiles) if args.jones else None
@@ -505,6 +511,10 @@ def run_ours(args, world, rank, local):
             return e0.elapsed_time(e1) / reps
         ms_b32 = timed(lambda: B.blink_pipeline(ctx, arr, obs, im, B.BLINK_CORR_FP32, B.BLINK_MODE_BATCHED, volt, img,
                                                 None, stream), 3)
+        B.blink_set_fused(ctx, not args.fused)                    # the other of the two batched mixed forms
+        ms_alt = timed(lambda: B.blink_pipeline(ctx, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, volt, img,
+                                                None, stream), 3)
+        B.blink_set_fused(ctx, args.fused)
         ns_p = min(ns, 2 * w.samples_per_int)                     # the per-image form on two integrations
         n_p = (ns_p // w.samples_per_int) * w.n_out_chan
         obs_p = B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns_p)
@@ -525,7 +535,10 @@ def run_ours(args, world, rank, local):
             "plain_fp32_per_image": {"images_per_s": plain, "images_per_step": n_p,
                                      "note": "correlate (CUDA cores) -> atomic grid -> column and row FFT, per image"},
             "batched_fp32": {"images_per_s": n_img / (ms_b32 / 1e3), "ms_per_step": ms_b32},
-            "batched_mixed": {"images_per_s": value, "ms_per_step": ms_step},
+            "batched_mixed": {"images_per_s": value, "ms_per_step": ms_step,
+                              "form": "fused single launch" if args.fused else "correlate launch + imaging launch"},
+            ("batched_mixed_two_launches" if args.fused else "batched_mixed_fused"): {
+                "images_per_s": n_img / (ms_alt / 1e3), "ms_per_step": ms_alt},
             "cufft_irfft2": {"images_per_s": nb / (ms_cf / 1e3), "batch": nb,
                              "note": "torch.fft.irfft2 (cuFFT) of random half-plane grids: the FFT stage alone"},
             "correlate_vis4": {"vis_per_s": n_img * Bn * 4 / (ms_v4 / 1e3), "ms_per_step": ms_v4,

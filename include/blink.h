@@ -304,7 +304,8 @@ enum {
     BLINK_STAGE_CORRELATE = 0,   /* correlation kernels */
     BLINK_STAGE_GRID_FFT = 1,    /* gridding + the 2D inverse FFT (the batched form's persistent kernel) */
     BLINK_STAGE_ROW_FFT = 2,     /* a separate row (complex-to-real) FFT pass, where one runs */
-    BLINK_N_STAGES = 3
+    BLINK_STAGE_FUSED = 3,       /* correlation + gridding + 2D inverse FFT in one persistent launch */
+    BLINK_N_STAGES = 4
 };
 
 /*
@@ -328,6 +329,17 @@ blink_status blink_read_profile(blink_context* ctx, void* stream, double* ms, in
  * invalid.  The setting holds for later calls of the context until changed.
  */
 blink_status blink_set_wait_budget(blink_context* ctx, int64_t budget_cycles, int32_t unreachable);
+
+/*
+ * The fused form of the batched imaging path (BLINK_MODE_BATCHED; a library design choice, the paper runs its
+ * stages as separate kernels, Sec. 5.2): for 512^2 nearest-cell images with FP8 correlation, no calibration
+ * and the zenith phase centre, one persistent launch per call correlates each image's integration on the
+ * tensor cores and grids and transforms it, the correlation sums staying in an L2-resident ring.  Off by
+ * default: on GB300 the separate correlation launch (its sums assembled in gather order in shared memory and
+ * written out whole) is faster than correlation tasks that scatter those sums into the ring from registers.
+ * Both forms give the same images, bit for bit.  Applies to later calls of the context.
+ */
+blink_status blink_set_fused(blink_context* ctx, int32_t enable);
 
 #ifdef __cplusplus
 }

@@ -39,12 +39,13 @@ ENTRY_POINTS = (
     "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
     "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets", "blink_dedisperse",
-    "blink_set_wait_budget",
+    "blink_set_wait_budget", "blink_set_fused",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
 BLINK_STAGE_ROW_FFT = 2
-BLINK_N_STAGES = 3
+BLINK_STAGE_FUSED = 3
+BLINK_N_STAGES = 4
 
 
 class BlinkError(RuntimeError):
@@ -97,6 +98,7 @@ def _load():
         "blink_pipeline_sets": (S, [P, P, P, P, I32, I32, P, P, C.c_size_t, P]),
         "blink_dedisperse": (S, [P, P, I32, I32, I32, P, P, P]),
         "blink_set_wait_budget": (S, [P, I64, I32]),
+        "blink_set_fused": (S, [P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -288,6 +290,11 @@ def blink_set_wait_budget(ctx, budget_cycles: int = 0, unreachable: bool = False
     """Budget (SM clock cycles, 0 = default) of the imaging kernel's dependency waits; `unreachable` makes
     the row tasks' waits run out (a test of the failure path)."""
     _check(_lib.blink_set_wait_budget(ctx, int(budget_cycles), int(bool(unreachable))), "blink_set_wait_budget")
+
+
+def blink_set_fused(ctx, enable: bool = True) -> None:
+    """Correlation inside the side-512 imaging launch, or as its own launch (the default)."""
+    _check(_lib.blink_set_fused(ctx, int(bool(enable))), "blink_set_fused")
 
 
 def blink_image_noalloc(imaging: Imaging, d_grid, n_images: int, d_weight, d_img, stream=None) -> None:

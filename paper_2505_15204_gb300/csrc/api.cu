@@ -168,6 +168,7 @@ void free_plan(Plan* p) {
     cudaFree(p->d_corr);
     cudaFree(p->d_phase);
     cudaFree(p->d_gsrc);
+    cudaFree(p->d_gpos);
     cudaFree(p->d_gphase);
     delete p;
 }
@@ -219,7 +220,9 @@ struct GatherBuilder {
     std::vector<uint2> ent;
     std::vector<uint32_t> ekey, eval, sorted, skey;
     std::vector<std::vector<uint16_t>> gsrc;   // per channel: the baseline of each entry (nearest-cell lists only)
-    bool src16 = false;
+    std::vector<uint32_t> gpos;                // [F][B]: the entries of each baseline (positions below 0xFFFF)
+    int64_t B = 0;
+    bool src16 = false, pos16 = false;
     int max_per_channel = 0;
     GatherBuilder(int n, int F) : N(n), half(n / 2), nkeys((int64_t)(n / 2) * n), count(nkeys + 1),
                                   ent_off((size_t)F * (n / 2 + 1)) {}
@@ -255,6 +258,15 @@ struct GatherBuilder {
             std::vector<uint16_t>& g = gsrc[f];
             g.resize(sorted.size());
             for (size_t e = 0; e < sorted.size(); e++) g[e] = (uint16_t)(sorted[e] >> 1);
+            if (sorted.size() < 0xFFFFu) {
+                uint32_t* gp = gpos.data() + (size_t)f * B;
+                for (size_t e = 0; e < sorted.size(); e++) {
+                    uint32_t& w = gp[sorted[e] >> 1];
+                    w = (w & 0xFFFFu) == 0xFFFFu ? ((w & 0xFFFF0000u) | (uint32_t)e) : ((w & 0xFFFFu) | ((uint32_t)e << 16));
+                }
+            } else {
+                pos16 = false;
+            }
         }
         if ((int64_t)ent.size() > INT32_MAX / 2) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
         return BLINK_OK;
@@ -274,6 +286,10 @@ struct GatherBuilder {
                 std::copy(gsrc[f].begin(), gsrc[f].end(), all.begin() + f * p->e_stride);
             BLINK_TRY(dmalloc(&p->d_gsrc, all.size()));
             BLINK_CUDA(cudaMemcpy(p->d_gsrc, all.data(), all.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+            if (pos16) {
+                BLINK_TRY(dmalloc(&p->d_gpos, gpos.size()));
+                BLINK_CUDA(cudaMemcpy(p->d_gpos, gpos.data(), gpos.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+            }
         }
         return BLINK_OK;
     }
@@ -287,7 +303,12 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
     GatherBuilder g(N, p->F);
     g.ent.reserve((size_t)p->F * (B + B / 16));
     g.src16 = B <= 0x10000;
-    if (g.src16) g.gsrc.resize(p->F);
+    if (g.src16) {
+        g.gsrc.resize(p->F);
+        g.B = B;
+        g.pos16 = true;
+        g.gpos.assign((size_t)p->F * B, 0xFFFFFFFFu);
+    }
     p->W.assign(p->F, 0.f);
     int64_t dropped = 0;
     for (int f = 0; f < p->F; f++) {
@@ -733,21 +754,34 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
     const bool gathered = fft_takes_gathered(p) && arith == BLINK_CORR_FP8 &&
                           corr_fp8_gathers(p, o->samples_per_int, kind, gains);
     const int64_t vstride = gathered ? p.e_stride : p.B;          // float2 per item
-    const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)vstride * 8 * F))));
+    // fused: one launch correlates (tensor cores) and images every item, the sums never leaving L2
+    const bool fused = gathered && ctx->fused && !gains.d && !p.d_phase &&
+                       fft_fused_ok(p, o->samples_per_int, kind, d_volt, sstride);
+    const int t_chunk = fused ? T : (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes /
+                                                                                              ((size_t)vstride * 8 * F))));
     ImgOut io;
     io.phase = p.d_phase;
     io.gather = gathered;
     void* vis = nullptr;
     void* H = nullptr;
     void* cnt = nullptr;
-    BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * vstride * sizeof(float2), &vis));
+    BLINK_TRY(workspace(ctx, 0, fused ? fused_ring_floats(p) * sizeof(float) : (size_t)t_chunk * F * vstride * sizeof(float2),
+                        &vis));
     BLINK_TRY(workspace(ctx, 1, (size_t)fft_ring_images_max() * N * (N / 2) * el, &H));
-    BLINK_TRY(workspace(ctx, 4, sizeof(int) * (2 + 2 * (size_t)t_chunk * F), &cnt));
+    BLINK_TRY(workspace(ctx, 4, sizeof(int) * (2 + 3 * (size_t)t_chunk * F), &cnt));
+    FusedIn fz;
+    fz.d_volt = d_volt;
+    fz.sample_stride = sstride;
+    fz.ns = o->samples_per_int;
+    fz.kind = kind;
+    fz.d_vring = static_cast<float*>(vis);
+    const FusedIn* fzp = fused ? &fz : nullptr;
+    const int stage = fused ? BLINK_STAGE_FUSED : BLINK_STAGE_GRID_FFT;
     const int out_first = tau0 * F;
     for (int ta = tau0; ta < tau1; ta += t_chunk) {
         const int tb = std::min(tau1, ta + t_chunk);
         const int first = ta * F, n_items = (tb - ta) * F;
-        {
+        if (!fused) {
             StageTimer t(ctx, BLINK_STAGE_CORRELATE, st);
             if (arith == BLINK_CORR_FP8)
                 BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
@@ -758,10 +792,10 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
         }
         if (!p.tuned && !may_tune) {
             // output over the host link: timings would measure the link, so run the default shape untuned
-            StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
+            StageTimer t(ctx, stage, st);
             BLINK_TRY(launch_fft_persistent(p, fft_tune_candidates(p)[0], prec, static_cast<float2*>(vis), vstride, first,
                                             ta, tb - ta, H, static_cast<int*>(cnt), d_img, out_first, ctx->d_status,
-                                            ctx->n_sm, st, ctx->fft_wait, gathered));
+                                            ctx->n_sm, st, ctx->fft_wait, gathered, fzp));
         } else if (!p.tuned) {
             // autotune the FFT launch shape on this first batch: time each candidate (every run writes the
             // same images), keep the fastest for every later call of the plan
@@ -780,7 +814,7 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
                 BLINK_CUDA(cudaEventRecord(e0, st));
                 BLINK_TRY(launch_fft_persistent(p, c, prec, static_cast<float2*>(vis), vstride, first, ta, tb - ta, H,
                                                 static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm,
-                                                st, ctx->fft_wait, gathered));
+                                                st, ctx->fft_wait, gathered, fzp));
                 BLINK_CUDA(cudaEventRecord(e1, st));
                 BLINK_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -793,10 +827,10 @@ blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, 
             }
             p.tune_ms = best;
         } else {
-            StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
+            StageTimer t(ctx, stage, st);
             BLINK_TRY(launch_fft_persistent(p, p.tune, prec, static_cast<float2*>(vis), vstride, first, ta, tb - ta, H,
                                             static_cast<int*>(cnt), d_img, out_first, ctx->d_status, ctx->n_sm, st,
-                                            ctx->fft_wait, gathered));
+                                            ctx->fft_wait, gathered, fzp));
         }
     }
     return BLINK_OK;
@@ -918,6 +952,12 @@ blink_status blink_set_wait_budget(blink_context* ctx, int64_t budget_cycles, in
     if (!ctx) return set_error(BLINK_ERR_INVALID_ARG, "context is NULL");
     ctx->fft_wait.budget = budget_cycles > 0 ? (long long)budget_cycles : FftWait{}.budget;
     ctx->fft_wait.extra = unreachable ? 1 : 0;
+    return BLINK_OK;
+}
+
+blink_status blink_set_fused(blink_context* ctx, int32_t enable) {
+    if (!ctx) return set_error(BLINK_ERR_INVALID_ARG, "context is NULL");
+    ctx->fused = enable != 0;
     return BLINK_OK;
 }
 

@@ -80,6 +80,8 @@ struct Plan {
     // NULL when a baseline index does not fit 16 bits.  gphase[f][p]: the phase-centre factor in that order.
     uint16_t* d_gsrc = nullptr;            // [F][e_stride]
     float2* d_gphase = nullptr;            // [F][e_stride] off zenith, else NULL
+    uint32_t* d_gpos = nullptr;            // [F][B] the inverse: entry positions p1 | p2 << 16 of baseline b
+                                           //   (0xFFFF: none; the second only in the column u = 0)
     int e_stride = 0;                      // floats per plane of one gather-ordered item (>= entries per channel)
 };
 
@@ -106,6 +108,7 @@ struct blink_context {
     blink::Workspace ws[8];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays
     float2* tw[16] = {};                   // twiddle tables by log2(side)
     blink::FftWait fft_wait;               // dependency-wait budget of the persistent FFT kernel
+    bool fused = false;                    // correlation inside the side-512 imaging launch (blink_set_fused)
     // per-stage profiling (blink_set_profiling): recorded (stage, start, stop) event pairs and a free pool
     bool profiling = false;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -178,12 +181,26 @@ struct WaveMap {
 // Gridding + both FFT passes of images [tau0, tau0 + n_tau) x all channels in one persistent launch;
 // d_H holds fft_ring_images_max() column-pass results, d_counters 2 + 2 * F * n_tau ints.
 int fft_ring_images_max();
+// The fused form of the side-512 launch: correlation tasks inside the persistent kernel (FP8 tensor cores,
+// Stokes I or XX, no calibration) writing each image's sums into an L2-resident ring of gather-ordered slots.
+struct FusedIn {
+    const uint8_t* d_volt = nullptr;       // the call's voltage block
+    int64_t sample_stride = 0;             // bytes between samples
+    int ns = 0;                            // samples per integration
+    int kind = 0;                          // CORR_OUT_STOKES_I or CORR_OUT_XX
+    float* d_vring = nullptr;              // fused_ring_floats(p) floats
+};
+// Whether this plan and request can run fused, and the floats its vis ring needs.
+bool fft_fused_ok(const Plan& p, int ns, int kind, const uint8_t* d_volt, int64_t sample_stride);
+size_t fused_ring_floats(const Plan& p);
 // d_vis holds the correlation sums of images [vis_first, ...): float2 [image][vis_stride] in baseline order, or,
 // when `gathered`, gather-ordered planes of p.e_stride floats each (vis_stride = p.e_stride float2 per image).
+// With `fused` (and gathered) the launch correlates the images itself and d_vis is unused; d_counters then
+// holds 2 + 3 * F * n_tau ints.
 blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec, const float2* d_vis,
                                    int64_t vis_stride, int vis_first, int tau0, int n_tau, void* d_H, int* d_counters,
                                    float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st,
-                                   const FftWait& wait, bool gathered = false);
+                                   const FftWait& wait, bool gathered = false, const FusedIn* fused = nullptr);
 // Whether the persistent kernel can read gather-ordered sums for this plan (side 512, nearest cell).
 bool fft_takes_gathered(const Plan& p);
 // Candidate launch shapes the autotuner times for a plan.

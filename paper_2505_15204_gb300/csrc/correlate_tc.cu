@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "blink_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace blink {
 
@@ -87,92 +88,12 @@ __device__ __forceinline__ void put_img(const TcParams& P, int local, int64_t b,
     static_cast<float2*>(P.out)[(int64_t)local * P.out_item_stride + b] = make_float2(re, im);
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of parity `parity` to complete; false if the budget ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitBudget) return false;
-    return true;
-}
-
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
                                             int c2) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, no swizzle.  lbo = byte distance of core matrices adjacent
-// along K, sbo = byte distance of 8-row groups; bits 46-47 hold the descriptor version 1.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
-}
-
-// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major, dense.
-__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// byte offset of (row, kbyte) inside a 128-row operand tile of Kp bytes per row
-__device__ __forceinline__ int op_off(int row, int kb, int Kp) {
-    return (row >> 3) * (Kp * 8) + (kb >> 4) * 128 + (row & 7) * 16 + (kb & 15);
-}
-
-__device__ __forceinline__ void pair_of(int q, int& mb, int& jb) {
-    mb = 0;
-    while ((mb + 1) * (mb + 2) / 2 <= q) mb++;
-    jb = q - mb * (mb + 1) / 2;
 }
 
 // CAL: 0 uncalibrated; 1 diagonal gains applied in the epilogue (Stokes I through split X / Y chains); 2 full
@@ -271,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         }
         const bool first_chunk = cj == 0, last_chunk = cj == P.n_chunks - 1;
         const int Kv = min(P.ns_c, P.ns - cj * P.ns_c) * P.c;     // values of this chunk inside the item
-        const bool ok = mbar_wait(bar_tma[buf], tma_par[buf]);
+        const bool ok = mbar_wait(bar_tma[buf], tma_par[buf], kWaitBudget);
         tma_par[buf] ^= 1;
         pending[buf] = !ok;
         if (__syncthreads_or(!ok)) {
@@ -344,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                 }
                 mma_commit(bar_mma);
             }
-            const bool okm = mbar_wait(bar_mma, mma_par);
+            const bool okm = mbar_wait(bar_mma, mma_par, kWaitBudget);
             mma_par ^= 1;
             if (__syncthreads_or(!okm)) {
                 abort = true;
@@ -579,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         if (tid == 0) {
             atomicOr(P.status, DEV_ERR_TIMEOUT);
             for (int b = 0; b < 2; b++)
-                if (pending[b]) mbar_wait(bar_tma[b], tma_par[b]);
+                if (pending[b]) mbar_wait(bar_tma[b], tma_par[b], kWaitBudget);
         }
     }
     tc_fence_before();

@@ -26,9 +26,11 @@
 // end; they are nevertheless bounded, and on expiry the launch records BLINK_ERR_TIMEOUT and every CTA
 // stops taking tickets.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 #include "blink_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace blink {
 
@@ -73,7 +75,24 @@ struct FftParams {
     int e_stride;
     long long wait_budget;   // clock cycles a dependency wait may take before the launch gives up
     int extra_wait;          // added to the row tasks' dependency target (0; 1 makes those waits run out)
+    // fused form (side 512, gather order): a correlation task per image computes its sums into a small ring
+    // of gather-ordered slots that stays in L2, instead of an earlier correlator launch writing them to memory
+    int fused;
+    const uint8_t* volt;     // the call's voltage block (sample 0, first channel of the call)
+    int64_t sample_stride;   // bytes between consecutive samples
+    int ns, cavg, n_tiles;   // samples per integration, fine channels averaged, tiles
+    int ns_c, n_chunks;      // K streams through the operand tiles in chunks of ns_c samples
+    int Kq, Kp, n_blk;       // a chunk's K (multiple of 4), operand row bytes, blocks of 64 tiles
+    int stokes;              // Stokes I (X and Y halves of K side by side), else XX
+    const uint32_t* gpos;    // [F][B]: entry positions p1 | p2 << 16 of each baseline in its channel's list
+    int64_t B;
+    const uint8_t* flags;    // [n_tiles]
+    float* vring;            // [ring_v][2][e_stride]: the gather-ordered sums of the images in flight
+    int ring_v, lead;        // its slots; segments by which an image's correlation precedes its column tasks
+    int* corr_done;          // [n_img]
 };
+
+constexpr int kCorrCols = 128;                   // TMEM columns per CTA in the fused form: two block pairs
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
@@ -91,6 +110,12 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 // multiples of 16.
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16) from global to shared memory, completing on mbarrier `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
 __device__ __forceinline__ float2 ldcg_c(const float2* p) { return __ldcg(p); }
@@ -277,7 +302,7 @@ __device__ __forceinline__ void pretw(float2& zk, float2& zm, float2 wq) {
 //   X[b + 16 k2] = sum_j exp(2 pi i j k2 / 32) exp(2 pi i j b / 512) Y[j][b],
 // and stores the column from registers, each half-warp writing 16 consecutive points (128 bytes) per
 // instruction, once the ring slot's previous image has been read.
-template <typename T>
+template <typename T, bool FUSED>
 __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
                                uint32_t* s_occ) {
     constexpr int N = 512, M = N / 2, LD = N;             // unpadded columns (swizzled first pass)
@@ -293,7 +318,10 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
         prefetch_l2(P.vis + (int64_t)(id2 - P.vis_first) * P.vis_stride, P.vis_prefetch);
     }
     T* s = reinterpret_cast<T*>(work);
-    const float2* V = P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
+    // fused form: the image's sums are in its vis-ring slot once its correlation task is done
+    if (FUSED && !warp_wait(P, P.corr_done + k, 1, 0)) return P.col_done + k;
+    const float2* V = FUSED ? reinterpret_cast<const float2*>(P.vring + (int64_t)(k % P.ring_v) * 2 * P.e_stride)
+                            : P.vis + (int64_t)(id - P.vis_first) * P.vis_stride;
     const int* off = P.ent_off + f * (M + 1);
     const int base = off[0];                          // the channel's first entry (gather order's position 0)
     const float* Vre = reinterpret_cast<const float*>(V) - base;
@@ -406,6 +434,115 @@ __device__ int* row_task512(const FftParams& P, int k, int rb, unsigned char* wo
         for (int k2 = 0; k2 < 16; k2++) __stcs(out + 16 * k2, make_float2(v[k2].x * inv, v[k2].y * inv));
     }
     return nullptr;
+}
+
+// Correlation task of image k in the fused form (Eq. 2, Sec. 5.2.2): the Stokes-I (or XX) integer sums of its
+// item (integration tau, output channel f) on the tensor cores, as in the standalone FP8 correlator - K in
+// chunks of ns_c samples bulk-copied to shared memory, unpacked to e4m3 operand tiles (the realified complex
+// product), MMAs accumulating in TMEM - with the CTA's 128 TMEM columns holding two 64 x 64 block pairs per
+// round.  Each round's sums go from TMEM to the image's vis-ring slot at the gather positions of their
+// baselines (two for a baseline of the column u = 0).  Returns false if a wait ran out (the launch aborts).
+__device__ bool corr_task512(const FftParams& P, int k, unsigned char* work, const uint32_t* lut, const uint8_t* sflags,
+                             uint32_t tmem, uint32_t bar_raw, uint32_t bar_mma, uint32_t& par_raw, uint32_t& par_mma,
+                             int* s_flag) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau;
+    const int nt = P.n_tiles;
+    // the vis-ring slot's previous image must have been gridded by all its column tasks
+    const int* prev = k >= P.ring_v ? P.col_done + (k - P.ring_v) : nullptr;
+    if (!wait_count(P, prev, P.n_cb, s_flag)) return false;
+    if (smem_u32(work) & 15) return false;             // operands and bulk copies need 16-byte alignment
+    const uint32_t tile_bytes = 128u * P.Kp;
+    uint8_t* ops = work;
+    uint8_t* raw = work + P.n_blk * tile_bytes;
+    // the work area last held another task's data: zero the operand tiles, so that the K padding of every row
+    // and the rows past the last tile, which the unpack never writes, contribute nothing
+    for (uint32_t e = tid; e < (uint32_t)P.n_blk * tile_bytes / 16; e += kPT)
+        reinterpret_cast<uint4*>(ops)[e] = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t row_bytes = (uint32_t)P.cavg * nt * 2;   // one sample's c channels of all tiles
+    const int n_pairs = P.n_blk * (P.n_blk + 1) / 2;
+    const uint32_t idesc = idesc_e4m3(128, 64), ops_s = smem_u32(ops), sbo = (uint32_t)P.Kp * 8;
+    float* vout = P.vring + (int64_t)(k % P.ring_v) * 2 * P.e_stride;
+    const uint32_t* gp = P.gpos + (int64_t)f * P.B;
+    // the item's raw samples, all of them, once: one bulk copy per sample of its c channels
+    if (tid == 0) {
+        mbar_expect_tx(bar_raw, (uint32_t)P.ns * row_bytes);
+        const uint8_t* src = P.volt + (int64_t)tau * P.ns * P.sample_stride + (int64_t)f * row_bytes;
+        for (int q = 0; q < P.ns; q++)
+            bulk_load(smem_u32(raw) + q * row_bytes, src + (int64_t)q * P.sample_stride, row_bytes, bar_raw);
+    }
+    {
+        bool ok = mbar_wait(bar_raw, par_raw, P.wait_budget);
+        if (!ok) ok = mbar_wait(bar_raw, par_raw, P.wait_budget);          // let copies in flight land
+        par_raw ^= 1;
+        if (__syncthreads_or(!ok)) return false;
+    }
+    for (int q0 = 0; q0 < n_pairs; q0 += 2) {
+        const int q1 = min(n_pairs, q0 + 2);
+        for (int j = 0; j < P.n_chunks; j++) {
+            const int s0 = j * P.ns_c, sn = min(P.ns_c, P.ns - s0);
+            const uint8_t* rj = raw + (size_t)s0 * row_bytes;
+            if (P.stokes)
+                unpack_e4m3<true, false>(rj, lut, sflags, ops, tile_bytes, nt, P.Kq, P.Kp, sn * P.cavg, tid, kPT);
+            else
+                unpack_e4m3<false, false>(rj, lut, sflags, ops, tile_bytes, nt, P.Kq, P.Kp, sn * P.cavg, tid, kPT);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                for (int q = q0; q < q1; q++) {
+                    int mb, jb;
+                    pair_of(q, mb, jb);
+                    const uint32_t d = tmem + (uint32_t)((q - q0) * 64);
+                    const uint32_t a0 = ops_s + mb * tile_bytes, b0 = ops_s + jb * tile_bytes;
+                    for (int ks = 0; ks < P.Kp / 32; ks++)
+                        mma_e4m3(d, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo), idesc,
+                                 j > 0 || ks > 0);
+                }
+                mma_commit(bar_mma);
+            }
+            bool okm = mbar_wait(bar_mma, par_mma, P.wait_budget);
+            if (!okm) okm = mbar_wait(bar_mma, par_mma, P.wait_budget);    // the MMAs still read shared memory
+            par_mma ^= 1;
+            if (__syncthreads_or(!okm)) return false;
+            tc_fence_after();
+        }
+        // warps 0-3 read block pair q0, warps 4-7 pair q0 + 1: TMEM lane 32 (w % 4) + lane = unit row (re for
+        // rows below 64, im above), 64 columns = units of the pair's column block
+        const int q = q0 + (warp >> 2);
+        if (q < q1) {
+            int mb, jb;
+            pair_of(q, mb, jb);
+            const int row = (warp & 3) * 32 + lane;
+            const int ui = mb * 64 + (row & 63);
+            float* plane = vout + (row >> 6) * P.e_stride;
+            const int64_t brow = (int64_t)ui * (ui + 1) / 2;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 64; c0 += 32) {
+                // the positions of 32 baselines in flight together, then their sums from TMEM
+                uint32_t w[32];
+#pragma unroll
+                for (int cc = 0; cc < 32; cc++) {
+                    const int uj = jb * 64 + c0 + cc;
+                    w[cc] = (ui < nt && uj <= ui) ? __ldg(gp + brow + uj) : 0xFFFFFFFFu;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((q - q0) * 64 + c0 + 16 * h), v);
+#pragma unroll
+                    for (int cc = 0; cc < 16; cc++) {
+                        const uint32_t p1 = w[16 * h + cc] & 0xFFFFu, p2 = w[16 * h + cc] >> 16;
+                        if (p1 != 0xFFFFu) plane[p1] = __uint_as_float(v[cc]);
+                        if (p2 != 0xFFFFu) plane[p2] = __uint_as_float(v[cc]);
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    return true;
 }
 
 // The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
@@ -556,10 +693,12 @@ template <int N, typename T, bool WT> constexpr size_t fft_smem() {
 // MINB resident CTAs per SM: 4 (32 warps) for sides up to 512 in the row-major form (measured faster than 24
 // warps, despite a few register spills), 2 or 3 for the side-512 column-major form (its register row pass
 // holds two butterflies' 32 points per lane; the autotuner picks), 1 above 512.
-template <int N, typename T, bool WT, int MINB>
+// FUSED (side 512 only): the instance with correlation tasks; the others carry none of their code or shared data.
+template <int N, typename T, bool WT, int MINB, bool FUSED = false>
 __global__ void __launch_bounds__(kPT, MINB) k_fft_persistent(const FftParams P) {
     constexpr int M = N / 2;
     constexpr bool CM = ring_cm<N, WT>();
+    static_assert(!FUSED || CM, "correlation tasks run in the side-512 column-major form only");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* s_twc = reinterpret_cast<float2*>(smem_raw);
     float2* s_pre = s_twc + (CM ? 32 * 16 : even(tw_size(N)));
@@ -594,8 +733,39 @@ __global__ void __launch_bounds__(kPT, MINB) k_fft_persistent(const FftParams P)
             for (int e = tid; e < tw_size(M); e += kPT) s_twr[e] = P.tw[tws_row(N) + e];
         }
     }
-    const int seg = P.n_cb + P.n_rb;
-    const int total = (P.n_img + P.lag) * seg;
+    // fused form: the CTA's TMEM columns, MMA and copy barriers, the byte -> e4m3 LUT and the flags
+    __shared__ uint32_t s_lut[FUSED ? 256 : 1];
+    __shared__ uint8_t s_tflags[FUSED ? 512 : 1];
+    __shared__ __align__(8) uint64_t s_bars[2];
+    __shared__ uint32_t s_tmem;
+    uint32_t tmem = 0, par_raw = 0, par_mma = 0;
+    const uint32_t bar_raw = (uint32_t)__cvta_generic_to_shared(&s_bars[0]), bar_mma = bar_raw + 8;
+    if constexpr (FUSED) {
+        {
+            if ((tid >> 5) == 0) {
+                asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                             ::"r"((uint32_t)__cvta_generic_to_shared(&s_tmem)), "r"(kCorrCols) : "memory");
+                asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+            }
+            if (tid == 0) {
+                mbar_init(bar_raw, 1);
+                mbar_init(bar_mma, 1);
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+            fill_e4m3_lut(s_lut, tid, kPT);
+            for (int a = tid; a < P.n_tiles; a += kPT) s_tflags[a] = P.flags[a] ? 1 : 0;
+            if (smem_u32(work) & 15) atomicOr(P.status, DEV_ERR_INDEX);   // (the correlation tasks then refuse)
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            tmem = s_tmem;
+        }
+    }
+    // the ticket stream: segments of (correlation of image s, fused form only) + (column tasks of image
+    // s - lead) + (row tasks of image s - lead - lag)
+    constexpr int fz = FUSED ? 1 : 0;
+    const int seg = fz + P.n_cb + P.n_rb;
+    const int total = (P.n_img + P.lag + (fz ? P.lead : 0)) * seg;
     // Thread 0 asks for the next ticket when a task starts, so the atomic's round trip overlaps the task, and
     // publishes it in the other half of a two-entry slot (warps still reading this task's entry are not
     // disturbed).  One barrier ends each task; thread 0 releases the finished task's counter after it (the
@@ -607,22 +777,36 @@ __global__ void __launch_bounds__(kPT, MINB) k_fft_persistent(const FftParams P)
         if (t >= total) break;
         int nt = 0;
         if (tid == 0) nt = atomicAdd(P.tickets, 1);
-        const int sg = t / seg, r = t - sg * seg;
+        const int sg = t / seg, r0 = t - sg * seg;
         int* done = nullptr;
-        if (r < P.n_cb) {
-            if (sg < P.n_img) {
-                if constexpr (CM)
-                    done = column_task512<T>(P, sg, r, s_twc, work, s_occ);
-                else
-                    done = column_task<N, T, WT>(P, sg, r, s_twc, work, s_occ, &s_flag);
+        if (fz && r0 == 0) {
+            if constexpr (FUSED) {
+                if (sg < P.n_img) {
+                    if (corr_task512(P, sg, work, s_lut, s_tflags, tmem, bar_raw, bar_mma, par_raw, par_mma, &s_flag))
+                        done = P.corr_done + sg;
+                    else if (tid == 0) {
+                        atomicOr(P.status, DEV_ERR_TIMEOUT);
+                        atomicExch(P.tickets + 1, 1);
+                    }
+                }
             }
         } else {
-            const int k = sg - P.lag;
-            if (k >= 0 && k < P.n_img) {
-                if constexpr (CM)
-                    done = row_task512<T>(P, k, r - P.n_cb, work);
-                else
-                    done = row_task<N, T, WT>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
+            const int r = r0 - fz, kc = sg - (fz ? P.lead : 0);
+            if (r < P.n_cb) {
+                if (kc >= 0 && kc < P.n_img) {
+                    if constexpr (CM)
+                        done = column_task512<T, FUSED>(P, kc, r, s_twc, work, s_occ);
+                    else
+                        done = column_task<N, T, WT>(P, kc, r, s_twc, work, s_occ, &s_flag);
+                }
+            } else {
+                const int k = kc - P.lag;
+                if (k >= 0 && k < P.n_img) {
+                    if constexpr (CM)
+                        done = row_task512<T>(P, k, r - P.n_cb, work);
+                    else
+                        done = row_task<N, T, WT>(P, k, r - P.n_cb, s_pre, s_twr, work, &s_flag);
+                }
             }
         }
         if (tid == 0) s_ticket[it ^ 1] = ld_relaxed(P.tickets + 1) ? total : nt;
@@ -632,11 +816,19 @@ __global__ void __launch_bounds__(kPT, MINB) k_fft_persistent(const FftParams P)
             atomicAdd(done, 1);
         }
     }
+    if constexpr (FUSED) {
+        {
+            tc_fence_before();
+            __syncthreads();
+            if ((tid >> 5) == 0)
+                asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCorrCols) : "memory");
+        }
+    }
 }
 
-template <int N, typename T, bool WT, int MINB>
+template <int N, typename T, bool WT, int MINB, bool FUSED = false>
 blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
-    auto kern = k_fft_persistent<N, T, WT, MINB>;
+    auto kern = k_fft_persistent<N, T, WT, MINB, FUSED>;
     const size_t smem = fft_smem<N, T, WT>();
     static int per_sm = 0;                         // attributes and occupancy once per instantiation
     if (!per_sm) {
@@ -659,6 +851,13 @@ blink_status launch_n(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
 template <int N, typename T, bool WT>
 blink_status launch_sized(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t st) {
     if constexpr (ring_cm<N, WT>()) {
+        if (P.fused) {
+            if constexpr (std::is_same<T, float2>::value) {
+                if (ctas_per_sm == 3) return launch_n<N, T, WT, 3, true>(P, n_sm, 3, st);
+                return launch_n<N, T, WT, 2, true>(P, n_sm, 2, st);
+            }
+            return set_error(BLINK_ERR_UNSUPPORTED, "the fused imaging launch stores its ring in FP32");
+        }
         if (ctas_per_sm == 3) return launch_n<N, T, WT, 3>(P, n_sm, 3, st);
         return launch_n<N, T, WT, 2>(P, n_sm, 2, st);
     } else {
@@ -680,6 +879,52 @@ std::vector<FftTune> fft_tune_candidates(const Plan& p) {
 int fft_ring_images_max() { return 64; }
 
 bool fft_takes_gathered(const Plan& p) { return p.N == 512 && !p.d_wt && p.d_gsrc && p.e_stride > 0; }
+
+namespace {
+constexpr int kRingV = 128, kLead = 96;          // vis-ring slots and the correlation lead (images)
+
+// K chunking of the fused correlation: the largest number of samples whose operand tiles fit the kernel's work
+// area beside the item's whole raw block, then balanced over the chunks; 0 if none fits.
+struct FusedChunk {
+    int ns_c = 0, n_chunks = 0, Kq = 0, Kp = 0, n_blk = 0;
+};
+FusedChunk fused_chunk(const Plan& p, int ns, int kind) {
+    FusedChunk c;
+    const int nt = p.n_tiles, cavg = p.chan_avg;
+    c.n_blk = (nt + 63) / 64;
+    const size_t room = (size_t)32 * kRowLd * sizeof(float2);         // the work area of the side-512 kernel
+    auto bytes = [&](int ns_c, int& Kq, int& Kp) {
+        Kq = (ns_c * cavg + 3) / 4 * 4;
+        const int Kr = kind == CORR_OUT_STOKES_I ? 4 * Kq : 2 * Kq;
+        Kp = (Kr + 31) / 32 * 32;
+        return (size_t)c.n_blk * 128 * Kp + (size_t)ns * cavg * nt * 2;
+    };
+    int best = 0;
+    for (int ns_c = std::min(ns, 256); ns_c >= 1; ns_c--) {
+        int Kq, Kp;
+        if (bytes(ns_c, Kq, Kp) <= room) {
+            best = ns_c;
+            break;
+        }
+    }
+    if (!best) return c;
+    c.n_chunks = (ns + best - 1) / best;
+    c.ns_c = (ns + c.n_chunks - 1) / c.n_chunks;
+    bytes(c.ns_c, c.Kq, c.Kp);
+    return c;
+}
+}  // namespace
+
+bool fft_fused_ok(const Plan& p, int ns, int kind, const uint8_t* d_volt, int64_t sample_stride) {
+    if (!fft_takes_gathered(p) || !p.d_gpos || p.n_tiles % 8 || p.n_tiles > 512) return false;
+    if (kind != CORR_OUT_STOKES_I && kind != CORR_OUT_XX) return false;
+    if (((uintptr_t)d_volt & 15) || (sample_stride % 16) || ((int64_t)p.chan_avg * p.n_tiles * 2) % 16) return false;
+    const int64_t K = (int64_t)ns * p.chan_avg;
+    if ((kind == CORR_OUT_STOKES_I ? 256 : 128) * K >= ((int64_t)1 << 24)) return false;   // exact FP32 sums
+    return fused_chunk(p, ns, kind).ns_c > 0;
+}
+
+size_t fused_ring_floats(const Plan& p) { return (size_t)kRingV * 2 * p.e_stride; }
 
 // exp(2 pi i m / 512) for m in [0, 512) into constant memory of the current device: the first octant's
 // angles in FP64, the others by the exact symmetries of the circle, so that quarter turns are exact.
@@ -705,10 +950,33 @@ blink_status fft_constants(int N) {
 blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec, const float2* d_vis,
                                    int64_t vis_stride, int vis_first, int tau0, int n_tau, void* d_H, int* d_counters,
                                    float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st,
-                                   const FftWait& wait, bool gathered) {
+                                   const FftWait& wait, bool gathered, const FusedIn* fused) {
     if (gathered && !fft_takes_gathered(p))
         return set_error(BLINK_ERR_UNSUPPORTED, "gather-ordered sums need the side-512 nearest-cell plan");
     FftParams P{};
+    if (fused) {
+        if (!gathered || !fft_fused_ok(p, fused->ns, fused->kind, fused->d_volt, fused->sample_stride) || !fused->d_vring)
+            return set_error(BLINK_ERR_UNSUPPORTED, "the fused imaging launch does not support this request");
+        const FusedChunk c = fused_chunk(p, fused->ns, fused->kind);
+        P.fused = 1;
+        P.volt = fused->d_volt;
+        P.sample_stride = fused->sample_stride;
+        P.ns = fused->ns;
+        P.cavg = p.chan_avg;
+        P.n_tiles = p.n_tiles;
+        P.ns_c = c.ns_c;
+        P.n_chunks = c.n_chunks;
+        P.Kq = c.Kq;
+        P.Kp = c.Kp;
+        P.n_blk = c.n_blk;
+        P.stokes = fused->kind == CORR_OUT_STOKES_I ? 1 : 0;
+        P.gpos = p.d_gpos;
+        P.B = p.B;
+        P.flags = p.d_flags;
+        P.vring = fused->d_vring;
+        P.ring_v = kRingV;
+        P.lead = kLead;
+    }
     P.gathered = gathered ? 1 : 0;
     P.e_stride = p.e_stride;
     P.wait_budget = wait.budget > 0 ? wait.budget : 1;
@@ -739,8 +1007,10 @@ blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec,
     P.tickets = d_counters;
     P.col_done = d_counters + 2;
     P.row_done = d_counters + 2 + P.n_img;
+    P.corr_done = fused ? d_counters + 2 + 2 * (int64_t)P.n_img : nullptr;
     P.status = d_status;
-    BLINK_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int) * (2 + 2 * (size_t)P.n_img), st));
+    if (fused) P.vis_prefetch = 0;
+    BLINK_CUDA(cudaMemsetAsync(d_counters, 0, sizeof(int) * (2 + (fused ? 3 : 2) * (size_t)P.n_img), st));
     const bool bf = prec == BLINK_PREC_BF16, wt = p.d_wt != nullptr;
     P.wt = p.d_wt;
     P.corr = p.d_corr;

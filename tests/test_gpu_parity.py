@@ -699,3 +699,49 @@ def test_kb_pipeline_host_equals_device_path(B, ctx, per_pass):
     B.blink_pipeline_host(ctx, arr, obs, im, 1, h_volt, h_img, images_per_pass=per_pass)
     B.blink_sync(ctx)
     assert np.array_equal(h_img.numpy(), d.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------------------------------
+# the fused launch (correlation inside the persistent imaging kernel)
+# ---------------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_tiles,c,flags,pol", [(144, 1, False, 0), (144, 4, True, 0), (128, 2, False, 1),
+                                                 (136, 1, True, 1)])
+def test_fused_launch_equals_two_launches_and_the_oracle(B, ctx, n_tiles, c, flags, pol):
+    # one persistent launch per call correlates each image's integration on the tensor cores (sums kept in an
+    # L2 ring in gather order) and grids and transforms it: the same images, bit for bit, as the correlator
+    # launch followed by the imaging launch, and within the image gates of the FP64 oracle
+    enu = bs.tile_positions(n_tiles, 3000.0, 71)
+    freqs = 155e6 + 10e3 * np.arange(8 * c)
+    sky = bs.Sky(lmn=np.array([[0.05, -0.08, np.sqrt(1 - 0.0089)], [-0.2, 0.1, np.sqrt(1 - 0.05)]]),
+                 power=np.array([2.0, 1.5]))
+    ns = 30
+    v = bs.voltages(enu, freqs, ns, sky, seed=72)
+    fl = bs.tile_flags(n_tiles, 0.15, 73, 1) if flags else None
+    arr, obs = B.Array(enu, fl), B.Obs(freqs, c, 10, ns)
+    im = B.Imaging(512, pol=pol)
+    n = 3 * 8
+    fused = torch.full((n, 512, 512), float("nan"), dtype=torch.float32, device="cuda")
+    split = torch.full_like(fused, float("nan"))
+    d = dev(v)
+    B.blink_set_fused(ctx, True)
+    try:
+        B.blink_pipeline(ctx, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, d, fused)    # plan and tuning
+        B.blink_read_profile(ctx, reset=True)
+        B.blink_set_profiling(ctx, True)
+        B.blink_pipeline(ctx, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, d, fused)
+        B.blink_sync(ctx)
+        B.blink_set_profiling(ctx, False)
+        ms, launches = B.blink_read_profile(ctx, reset=True)
+        assert launches[B.BLINK_STAGE_FUSED] == 1 and launches[B.BLINK_STAGE_CORRELATE] == 0, launches
+    finally:
+        B.blink_set_fused(ctx, False)
+    B.blink_pipeline(ctx, arr, obs, im, B.BLINK_CORR_FP8, B.BLINK_MODE_BATCHED, d, split)
+    B.blink_sync(ctx)
+    assert torch.equal(fused, split)
+    ids = np.array([0, 5, n - 1])
+    kw = {"flags": fl} if flags else {}
+    ref = oracle.pipeline(v, enu, freqs, 10, c, 512, ids=ids, pol=pol, n_threads=8, **kw)["images"]
+    got = fused[torch.from_numpy(ids).cuda()].cpu().numpy()
+    for k, q in enumerate(ids):
+        assert_image_close(got[k], ref[k], (n_tiles, c, q))
