@@ -162,8 +162,9 @@ def source_hash(name: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def traffic_for(kernel: str, source: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if its source is unchanged."""
+def traffic_for(kernel: str, source: str, shape=None):
+    """DRAM bytes per launch of `kernel` (at the tuned launch shape, where traffic depends on it) from the
+    committed ncu summary, if its source is unchanged."""
     p = os.path.join(PROFILES, "traffic.json")
     if not os.path.exists(p):
         return None
@@ -172,6 +173,9 @@ def traffic_for(kernel: str, source: str):
     e = d.get(kernel)
     if not e or e.get("source_sha256_16") != source_hash(source):
         return None
+    by_shape = e.get("dram_bytes_per_launch_fullsize_by_shape")
+    if by_shape is not None:
+        return by_shape.get(",".join(str(x) for x in shape)) if shape else None
     return e.get("dram_bytes_per_launch_fullsize")
 
 
@@ -432,10 +436,12 @@ def run_ours(args, world, rank, local):
         kern = STAGE_KERNELS[dom] if (dom or arith == B.BLINK_CORR_FP8) else "k_corr_fp32"
         src = STAGE_SOURCES[dom] if (dom or arith == B.BLINK_CORR_FP8) else "correlate.cu"
         # the committed DRAM counters are those of the nearest-cell kernel: none for the kernel form
-        traffic = traffic_for(kern, src) if not (args.support and dom == 1) else None
+        shape = B.blink_tuned_shape(ctx)
+        traffic = traffic_for(kern, src, shape) if not args.support else None
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": traffic, "kernel": kern, "stage": STAGE_NAMES[dom],
-                "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3, "peak_kind": f"{peak_kind} hbm_gbs"}
+                "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3, "peak_kind": f"{peak_kind} hbm_gbs",
+                "tuned_shape": {"ring": shape[0], "lag": shape[1], "ctas_per_sm": shape[2]}}
     stages = {STAGE_NAMES[s]: {"ms_per_step": stage_ms[s] / args.steps, "launches_per_step": stage_n[s] / args.steps,
                                "GBps": (set_bytes(s) * args.steps / (stage_ms[s] / 1e3) / 1e9)
                                if stage_ms[s] else None}

@@ -341,6 +341,14 @@ blink_status blink_set_wait_budget(blink_context* ctx, int64_t budget_cycles, in
  */
 blink_status blink_set_fused(blink_context* ctx, int32_t enable);
 
+/*
+ * The launch shape the batched imaging kernel's autotuner kept for the context's most recent plan (a
+ * diagnostic for measurements; no counterpart in the paper): out[0] column-result ring slots, out[1] the lag
+ * of an image's row tasks behind its column tasks (images), out[2] resident CTAs per SM (0: as many as fit);
+ * all zero before the plan's first batched call.  out: host int32[3].
+ */
+blink_status blink_tuned_shape(blink_context* ctx, int32_t* out);
+
 #ifdef __cplusplus
 }
 #endif

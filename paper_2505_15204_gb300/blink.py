@@ -39,7 +39,7 @@ ENTRY_POINTS = (
     "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
     "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets", "blink_dedisperse",
-    "blink_set_wait_budget", "blink_set_fused",
+    "blink_set_wait_budget", "blink_set_fused", "blink_tuned_shape",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
@@ -99,6 +99,7 @@ def _load():
         "blink_dedisperse": (S, [P, P, I32, I32, I32, P, P, P]),
         "blink_set_wait_budget": (S, [P, I64, I32]),
         "blink_set_fused": (S, [P, I32]),
+        "blink_tuned_shape": (S, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -295,6 +296,13 @@ def blink_set_wait_budget(ctx, budget_cycles: int = 0, unreachable: bool = False
 def blink_set_fused(ctx, enable: bool = True) -> None:
     """Correlation inside the side-512 imaging launch, or as its own launch (the default)."""
     _check(_lib.blink_set_fused(ctx, int(bool(enable))), "blink_set_fused")
+
+
+def blink_tuned_shape(ctx):
+    """(ring slots, lag, CTAs per SM) the autotuner kept for the most recent plan; zeros before tuning."""
+    out = (C.c_int32 * 3)()
+    _check(_lib.blink_tuned_shape(ctx, out), "blink_tuned_shape")
+    return tuple(out)
 
 
 def blink_image_noalloc(imaging: Imaging, d_grid, n_images: int, d_weight, d_img, stream=None) -> None:

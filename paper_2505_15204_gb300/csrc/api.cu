@@ -961,6 +961,18 @@ blink_status blink_set_fused(blink_context* ctx, int32_t enable) {
     return BLINK_OK;
 }
 
+blink_status blink_tuned_shape(blink_context* ctx, int32_t* out) {
+    if (!ctx || !out) return set_error(BLINK_ERR_INVALID_ARG, "context or out is NULL");
+    out[0] = out[1] = out[2] = 0;
+    if (!ctx->plans.empty() && ctx->plans.back()->tuned) {
+        const FftTune& t = ctx->plans.back()->tune;
+        out[0] = t.ring;
+        out[1] = t.lag;
+        out[2] = t.ctas_per_sm;
+    }
+    return BLINK_OK;
+}
+
 blink_status blink_set_profiling(blink_context* ctx, int32_t enable) {
     if (!ctx) return set_error(BLINK_ERR_INVALID_ARG, "context is NULL");
     ctx->profiling = enable != 0;

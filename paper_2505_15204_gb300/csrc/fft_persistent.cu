@@ -860,6 +860,9 @@ blink_status launch_sized(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t s
         }
         if (ctas_per_sm == 3) return launch_n<N, T, WT, 3>(P, n_sm, 3, st);
         return launch_n<N, T, WT, 2>(P, n_sm, 2, st);
+    } else if constexpr (N == 1024) {
+        if (ctas_per_sm == 2) return launch_n<N, T, WT, 2>(P, n_sm, 2, st);
+        return launch_n<N, T, WT, 1>(P, n_sm, ctas_per_sm, st);
     } else {
         return launch_n<N, T, WT, (N <= 512 ? 32 / kW : 1)>(P, n_sm, ctas_per_sm, st);
     }
@@ -874,6 +877,9 @@ blink_status launch_sized(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t s
 std::vector<FftTune> fft_tune_candidates(const Plan& p) {
     if (p.N == 512 && !p.d_wt)
         return {{48, 32, 2}, {64, 32, 2}, {32, 24, 3}, {48, 32, 3}, {48, 24, 3}, {64, 32, 3}, {64, 48, 3}};
+    // a ring slot holds N x N/2 complex values: 4 MiB at side 1024, 16 MiB at 2048, so fewer slots stay in L2
+    if (p.N >= 2048) return {{4, 2, 0}, {6, 4, 0}, {8, 4, 0}};
+    if (p.N == 1024) return {{8, 4, 0}, {12, 8, 0}, {16, 8, 0}, {8, 4, 2}, {12, 8, 2}, {16, 12, 2}, {24, 16, 0}};
     return {{24, 16, 0}, {16, 8, 0}, {32, 24, 0}, {48, 32, 0}, {64, 48, 0}, {40, 32, 0}, {32, 24, 3}};
 }
 int fft_ring_images_max() { return 64; }
