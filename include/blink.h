@@ -273,6 +273,22 @@ blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, c
                                  float* h_img, int32_t images_per_pass, void* stream);
 
 /*
+ * blink_pipeline (batched form) for a phase centre that moves during the call, as when the array tracks a
+ * source (Sec. 5.2.3: the geometric corrections set the phase centre; here one per integration): integration
+ * tau is imaged with its phase centre at the direction cosines (h_lm[2 tau], h_lm[2 tau + 1]) of the local East,
+ * North, Up frame, each with l^2 + m^2 < 1 (imaging->phase_l and phase_m are ignored).  h_lm: host double
+ * [T][2], T = obs->n_samples / obs->samples_per_int, read during the call.  Consecutive integrations with the
+ * same pointing share one plan and one launch; each distinct pointing builds a plan (cells, phase table,
+ * gather order) that the context caches like blink_pipeline's.  The uv cell is imaging->cell_lambda, or, when that is 0, the
+ * default cell of the first integration's pointing for every integration, so that all images share one pixel
+ * scale.  Images, layout and errors otherwise as blink_pipeline (BLINK_ERR_INVALID_ARG for a NULL h_lm or a
+ * pointing outside the unit circle).
+ */
+blink_status blink_pipeline_tracking(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                     const blink_imaging* imaging, const double* h_lm, int32_t arith,
+                                     const uint8_t* d_volt, float* d_img, void* stream);
+
+/*
  * blink_image without any device allocation (the paper has no counterpart; this is a library service).
  * Callers that cannot allocate device memory while they image - a real-time instrument pipeline that
  * reserves all device memory when an observation starts, or an application whose device memory belongs

@@ -39,7 +39,7 @@ ENTRY_POINTS = (
     "blink_create", "blink_destroy", "blink_last_error", "blink_status_name", "blink_sync", "blink_n_baselines",
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
     "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets", "blink_dedisperse",
-    "blink_set_wait_budget", "blink_set_fused", "blink_tuned_shape",
+    "blink_set_wait_budget", "blink_set_fused", "blink_tuned_shape", "blink_pipeline_tracking",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
@@ -100,6 +100,7 @@ def _load():
         "blink_set_wait_budget": (S, [P, I64, I32]),
         "blink_set_fused": (S, [P, I32]),
         "blink_tuned_shape": (S, [P, P]),
+        "blink_pipeline_tracking": (S, [P, P, P, P, P, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +265,17 @@ def blink_pipeline_host(ctx, array: Array, obs: Obs, imaging: Imaging, arith: in
     a, o, i = array.c(), obs.c(), imaging.c()
     _check(_lib.blink_pipeline_host(ctx, C.byref(a), C.byref(o), C.byref(i), arith, _ptr(h_volt), _ptr(h_img),
                                     images_per_pass, _stream(stream)), "blink_pipeline_host")
+
+
+def blink_pipeline_tracking(ctx, array: Array, obs: Obs, imaging: Imaging, lm, arith: int, d_volt, d_img,
+                            stream=None) -> None:
+    """Batched pipeline with one phase centre per integration: lm = (l, m) per integration, [T][2]."""
+    a, o, i = array.c(), obs.c(), imaging.c()
+    t = np.ascontiguousarray(lm, dtype=np.float64)
+    if t.ndim != 2 or t.shape[1] != 2:
+        raise ValueError("lm must be [T][2]")
+    _check(_lib.blink_pipeline_tracking(ctx, C.byref(a), C.byref(o), C.byref(i), t.ctypes.data, arith, _ptr(d_volt),
+                                        _ptr(d_img), _stream(stream)), "blink_pipeline_tracking")
 
 
 def blink_dedisperse(ctx, d_img, n_int: int, n_chan: int, n_pix: int, delays, d_out, stream=None) -> None:

@@ -1170,6 +1170,50 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
     return BLINK_OK;
 }
 
+blink_status blink_pipeline_tracking(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                     const blink_imaging* imaging, const double* h_lm, int32_t arith,
+                                     const uint8_t* d_volt, float* d_img, void* stream) {
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, true));
+    BLINK_TRY(check_imaging(imaging));
+    if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
+        return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
+    if (!h_lm || !d_volt || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "h_lm, d_volt or d_img is NULL");
+    if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_img & 7))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_img 8-byte aligned");
+    const int T = obs->n_samples / obs->samples_per_int;
+    for (int t = 0; t < T; t++) {
+        const double l = h_lm[2 * t], m = h_lm[2 * t + 1];
+        if (!std::isfinite(l) || !std::isfinite(m) || !(l * l + m * m < 1.0))
+            return set_error(BLINK_ERR_INVALID_ARG, "h_lm: every pointing must be direction cosines with l^2 + m^2 < 1");
+    }
+    BLINK_TRY(make_current(ctx));
+    if (T == 0) return BLINK_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t ss = sample_stride_bytes(obs, array->n_tiles);
+    blink_imaging im = *imaging;
+    GainRef g;
+    bool have_g = false;
+    for (int ta = 0; ta < T;) {
+        int tb = ta + 1;
+        while (tb < T && h_lm[2 * tb] == h_lm[2 * ta] && h_lm[2 * tb + 1] == h_lm[2 * ta + 1]) tb++;
+        im.phase_l = h_lm[2 * ta];
+        im.phase_m = h_lm[2 * ta + 1];
+        Plan* p = nullptr;
+        BLINK_TRY(get_plan(ctx, array, obs, &im, true, st, &p));
+        if (im.cell_lambda <= 0.0) im.cell_lambda = p->du;      // one pixel scale for the whole call
+        if (!have_g) {
+            BLINK_TRY(upload_gains(ctx, array, p->F, st, &g));
+            have_g = true;
+        }
+        // run_batched writes image tau0 * F at its output pointer
+        BLINK_TRY(run_batched(ctx, *p, obs, im.precision, arith, d_volt, ss, ta, tb,
+                              d_img + (int64_t)ta * p->F * p->Ni * p->Ni, st, true, g));
+        ta = tb;
+    }
+    return BLINK_OK;
+}
+
 blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                                  const blink_set* sets, int32_t n_sets, int32_t arith, const uint8_t* d_volt,
                                  float* d_img, size_t img_capacity, void* stream) {

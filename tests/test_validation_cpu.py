@@ -200,3 +200,14 @@ def test_phase_centre_options():
     _expect(*NO_CTX, B.blink_cells, None, a, o, k, PTR)
     _expect(*NO_CTX, B.blink_image, None, k, PTR, 0, PTR, PTR)          # the image stage ignores the pointing
     _expect(B.BLINK_ERR_UNSUPPORTED, "pipeline forms only", B.blink_grid, None, a, o, k, PTR, 0, 1, PTR)
+
+
+def test_tracking_pointings():
+    a, o, k = B.Array(_enu()), _obs(), B.Imaging(64)          # two integrations
+    for lm in ([(0.1, 0.0), (0.8, 0.7)], [(float("nan"), 0.0), (0.0, 0.0)], [(0.0, 0.0), (1.0, 0.0)]):
+        _expect(B.BLINK_ERR_INVALID_ARG, "h_lm", B.blink_pipeline_tracking, None, a, o, k, np.array(lm), 1, PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "arith", B.blink_pipeline_tracking, None, a, o, k, np.zeros((2, 2)), 5, PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "NULL", B.blink_pipeline_tracking, None, a, o, k, np.zeros((2, 2)), 1, 0, PTR)
+    _expect(*NO_CTX, B.blink_pipeline_tracking, None, a, o, k, np.array([(0.1, 0.2), (0.3, -0.1)]), 1, PTR, PTR)
+    with pytest.raises(ValueError):
+        B.blink_pipeline_tracking(None, a, o, k, np.zeros(4), 1, PTR, PTR)

@@ -170,6 +170,48 @@ def test_source_at_the_pointing_images_at_the_centre_pixel(B, ctx):
     assert np.unravel_index(np.argmax(got), got.shape) == (n // 2, n // 2)
 
 
+TRACK_CASES = [
+    # name, n_samples, fine, chan_avg, n_pix, support, one pointing per integration
+    ("coarse", 40, 8, 2, 256, 0, [(0.1, 0.05), (0.1, 0.05), (0.12, 0.04), (-0.2, 0.3)]),
+    ("uneven", 30, 3, 1, 128, 0, [(0.0, 0.0), (0.3, -0.1), (0.0, 0.0)]),
+    ("coarse", 20, 8, 2, 128, 6, [(0.31, -0.22), (0.29, -0.2)]),
+]
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp32", "fp8"])
+@pytest.mark.parametrize("case", TRACK_CASES, ids=[f"{c[0]}-{c[4]}-W{c[5]}" for c in TRACK_CASES])
+def test_tracking_pipeline_matches_the_oracle_one_pointing_at_a_time(B, ctx, case, arith):
+    # each integration against the oracle imaged on that integration's pointing, with the pixel scale fixed
+    # by the first pointing (the entry point's default cell)
+    name, ns_total, fine, c, n_pix, W, lm = case
+    w, volt, freqs, fl = _case(name, ns_total, fine, name == "uneven")
+    T, F = volt.shape[0] // 10, len(freqs) // c
+    assert len(lm) == T
+    img = torch.full((T * F, n_pix, n_pix), float("nan"), dtype=torch.float32, device="cuda")
+    B.blink_pipeline_tracking(ctx, B.Array(w["enu"], fl), B.Obs(freqs, c, 10, volt.shape[0]),
+                              B.Imaging(n_pix, support=W), np.array(lm), arith, dev(volt), img)
+    B.blink_sync(ctx)
+    nu_max = float(np.max(oracle.output_freqs(freqs, c)))
+    du = oracle.default_cell(w["enu"], nu_max, n_pix, fl, W, lm[0])
+    got = img.cpu().numpy()
+    for t in range(T):
+        ids = np.arange(t * F, (t + 1) * F)
+        ref = oracle.pipeline(volt, w["enu"], freqs, 10, c, n_pix, ids=ids, flags=fl, n_threads=8, support=W,
+                              phase_centre=lm[t], cell_lambda=du)
+        for f in range(F):
+            assert_image_close(got[t * F + f], ref["images"][f], (t, f))
+
+
+def test_tracking_pipeline_rejects_a_pointing_off_the_sky(B, ctx):
+    w, volt, freqs, fl = _case("coarse", 20, 8, False)
+    img = torch.empty((8, 128, 128), dtype=torch.float32, device="cuda")
+    for lm in ([(0.1, 0.0), (0.8, 0.7)], [(0.1, 0.0), (float("nan"), 0.0)]):
+        with pytest.raises(B.BlinkError) as e:
+            B.blink_pipeline_tracking(ctx, B.Array(w["enu"]), B.Obs(freqs, 2, 10, 20), B.Imaging(128),
+                                      np.array(lm), 1, dev(volt), img)
+        assert e.value.status == B.BLINK_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("name,n_pix,fine,c,flags,pc", [("precision", 512, None, 1, False, (0.31, -0.22)),
                                                         ("uneven", 256, 8, 1, True, (-0.05, 0.4))])
 def test_cells_and_uvw_bit_exact_off_zenith(B, ctx, name, n_pix, fine, c, flags, pc):
