@@ -100,14 +100,17 @@ typedef struct {
 
 /* Imaging parameters (Sec. 5.2.4 and the -n option). */
 typedef struct {
-    int32_t n_pix;              /* N: image and grid side, a power of two in [64, 2048] */
+    int32_t n_pix;              /* N: image and grid side, even, in [64, 8192], with no prime factor above 5
+                                   (e.g. 256, 512, 1200, 8192).  Powers of two up to 2048 run the
+                                   side-specialised kernels; the other sides run mixed-radix (2, 3, 4, 5)
+                                   column and row passes, two launches per wave of images. */
     double cell_lambda;         /* uv cell du in wavelengths; <= 0 selects u_max / (N/2 - 1) */
     int32_t pol;                /* BLINK_POL_I: (XX + YY) / 2; BLINK_POL_XX: XX only */
     int32_t include_autos;      /* non-zero: autocorrelations gridded at (0, 0) with weight 1 */
     int32_t precision;          /* BLINK_PREC_FP32, or BLINK_PREC_BF16 (bf16 grid/intermediate storage) */
     int32_t support;            /* gridding kernel (Sec. 5.2.4): 0 or 1 = nearest cell; W in [2, 16] = separable
                                    Kaiser-Bessel kernel of W cells, beta = pi sqrt((W/2)^2 (3/2)^2 - 0.8),
-                                   on a grid of side 2 n_pix (n_pix <= 1024): every visibility is spread
+                                   on a grid of side 2 n_pix (n_pix <= 4096): every visibility is spread
                                    over the cells within W/2 of its exact (u, v) / du and kept only if that
                                    support lies inside the grid; the image is the central n_pix x n_pix of
                                    the transform divided by the kernel's Fourier transform along both axes.
@@ -248,7 +251,7 @@ blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, c
  *   h_delays  host int32 [n_chan], >= 0, in integrations, e.g. round(4.148808e3 s MHz^2 * DM *
  *             (nu_f^-2 - nu_top^-2) / t_int) for a dispersion measure DM in pc cm^-3 and nu in MHz.
  *   d_out     float [n_int - max(delays)][N][N].
- * N is a power of two in [64, 2048]; max(delays) < n_int, else BLINK_ERR_INVALID_ARG before any launch.
+ * N is even, in [64, 8192]; max(delays) < n_int, else BLINK_ERR_INVALID_ARG before any launch.
  */
 blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_int, int32_t n_chan, int32_t n_pix,
                               const int32_t* h_delays, float* d_out, void* stream);
@@ -298,7 +301,9 @@ blink_status blink_pipeline_tracking(blink_context* ctx, const blink_array* arra
  *   Scratch: a fixed 16 MiB array in the library's static device memory (held by every GPU that loads
  *   the library until the process exits) holds the twiddle table and the column-pass result of as many
  *   images as fit; larger batches are processed in passes.  One image must fit: sides up to 1024 with
- *   BLINK_PREC_FP32 storage and up to 2048 with BLINK_PREC_BF16; a larger side returns
+ *   BLINK_PREC_FP32 storage and up to 2048 with BLINK_PREC_BF16 (powers of two; for the mixed-radix
+ *   sides N rows of N/2 + 1 pairs rounded up to a multiple of 4, e.g. 1200 with FP32 storage, 2400 with
+ *   BF16); a larger side returns
  *   BLINK_ERR_UNSUPPORTED before anything is launched.  Every call rewrites the parts of the scratch it
  *   reads, so nothing needs clearing between calls.
  *   Set-up: the first call on a device - n_images == 0 included, which does nothing else - looks up the

@@ -66,6 +66,8 @@ def _load():
             lib.oracle_uvw_phased.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_double, P]
             lib.oracle_apply_phase.restype = None
             lib.oracle_apply_phase.argtypes = [P, P, C.c_int64]
+            lib.oracle_image_pixels.restype = None
+            lib.oracle_image_pixels.argtypes = [P, C.c_int, C.c_double, P, C.c_int64, P]
             lib.oracle_cells.restype = None
             lib.oracle_cells.argtypes = [P, C.c_int64, C.c_double, C.c_int, P, P, P]
             lib.oracle_grid.restype = C.c_double
@@ -300,11 +302,12 @@ def kb_crop_correct(full: np.ndarray, support: int) -> np.ndarray:
 
 
 def ifft2(G: np.ndarray) -> np.ndarray:
-    """Unnormalised inverse 2D transform by the oracle's own radix-2 FFT (power-of-two sides)."""
+    """Unnormalised inverse 2D transform by the oracle's own FFT: radix 2 on power-of-two sides, the
+    mixed-radix recursion on any other side."""
     n = G.shape[0]
     a = np.ascontiguousarray(np.stack([G.real, G.imag], axis=-1), dtype=np.float64)
     if _load().oracle_ifft2(_p(a), n):
-        raise ValueError("side must be a power of two")
+        raise ValueError("side must be >= 1")
     return a[..., 0] + 1j * a[..., 1]
 
 
@@ -315,6 +318,17 @@ def idft2(G: np.ndarray) -> np.ndarray:
     a = np.zeros_like(g)
     _load().oracle_idft2(_p(g), n, _p(a))
     return a[..., 0] + 1j * a[..., 1]
+
+
+def image_pixels(G: np.ndarray, W: float, yx) -> np.ndarray:
+    """Pixels (y, x) of the dirty image of the full complex grid G, each summed directly over G's nonzero
+    cells (for sampled checks of images too large for a whole transform)."""
+    n = G.shape[0]
+    g = np.ascontiguousarray(np.stack([G.real, G.imag], axis=-1), dtype=np.float64)
+    p = np.ascontiguousarray(yx, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros(len(p), dtype=np.float64)
+    _load().oracle_image_pixels(_p(g), n, float(W), _p(p), len(p), _p(out))
+    return out
 
 
 def image(a: np.ndarray, W: float):

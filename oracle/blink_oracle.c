@@ -16,8 +16,8 @@
  *   gains       Sec. 5.2.3 (calibration and cable-length corrections): per-tile, per-polarisation complex
  *               gains g, V_ij^pq = g_i^p S_ij^pq conj(g_j^q) (a diagonal Jones matrix per tile).
  *   grid        Sec. 5.2.4: natural weighting, every visibility and its Hermitian mirror weight 1.
- *   fft2        Eq. 4 / Sec. 5.2.4: unnormalised inverse 2D transform, own radix-2 FFT; direct DFT
- *               for small sides.
+ *   fft2        Eq. 4 / Sec. 5.2.4: unnormalised inverse 2D transform, own radix-2 FFT for powers of
+ *               two and a mixed-radix Cooley-Tukey recursion for other sides; direct DFT for small sides.
  *   image       Sec. 5.2.4: real part / sum of weights, shifted so the phase centre is the middle pixel.
  *   grid_kb     Sec. 5.2.4 and 8 (gridding with a convolution kernel, in progress in the paper): each
  *               visibility spread over W x W cells of a grid twice the image side by a separable
@@ -546,13 +546,83 @@ static void orc_ifft_1d(double* x, int n, int64_t stride)
     }
 }
 
+/* The same transform for any length n >= 1 (sides that are not powers of two): recursive Cooley-Tukey
+ * decimation in time on the smallest prime factor p of n.  With q = n / p, the q-point transforms
+ * X_r[k] = sum_j x[j p + r] w_q^(j k) of the p interleaved subsequences give
+ * X[k] = sum_{r < p} w_n^(r k) X_r[k mod q]; a prime length is summed directly.  root[e] = w_N^e for the
+ * top-level length N, and w_n^e = root[e * (N / n)] with the exponent reduced modulo n in integers.
+ * x: n complex values `stride` complex elements apart; out: n contiguous complex values. */
+static void orc_idft_any(const double* x, int64_t stride, int n, const double* root, int N, double* out)
+{
+    int p = n;
+    for (int d = 2; d * d <= n; d++)
+        if (n % d == 0) { p = d; break; }
+    int64_t step = N / n;                 /* w_n^e = w_N^(e step) */
+    if (p == n) {
+        for (int k = 0; k < n; k++) {
+            double sr = 0.0, si = 0.0;
+            for (int m = 0; m < n; m++) {
+                int64_t e = ((int64_t)k * m) % n;
+                double c = root[2 * e * step], s = root[2 * e * step + 1];
+                double xr = x[(int64_t)m * stride * 2], xi = x[(int64_t)m * stride * 2 + 1];
+                sr += xr * c - xi * s;
+                si += xr * s + xi * c;
+            }
+            out[2 * k] = sr;
+            out[2 * k + 1] = si;
+        }
+        return;
+    }
+    int q = n / p;
+    double* sub = (double*)malloc(sizeof(double) * 2 * (size_t)n);      /* [p][q] sub-transforms */
+    for (int r = 0; r < p; r++)
+        orc_idft_any(x + (int64_t)r * stride * 2, stride * p, q, root, N, sub + (int64_t)r * q * 2);
+    for (int k = 0; k < n; k++) {
+        double sr = 0.0, si = 0.0;
+        for (int r = 0; r < p; r++) {
+            int64_t e = ((int64_t)r * k) % n;
+            double c = root[2 * e * step], s = root[2 * e * step + 1];
+            double yr = sub[((int64_t)r * q + k % q) * 2], yi = sub[((int64_t)r * q + k % q) * 2 + 1];
+            sr += yr * c - yi * s;
+            si += yr * s + yi * c;
+        }
+        out[2 * k] = sr;
+        out[2 * k + 1] = si;
+    }
+    free(sub);
+}
+
 /* Unnormalised inverse 2D transform in place (Eq. 4): a[y][x] = sum_{v,u} G[v][u] exp(+2 pi i (u x + v y) / n).
- * Rows (u -> x) first, then columns (v -> y).  n must be a power of two; returns 0, or -1 otherwise. */
+ * Rows (u -> x) first, then columns (v -> y): the radix-2 transform above for a power of two, the
+ * mixed-radix recursion for any other n.  Returns 0, or -1 for n < 1. */
 int oracle_ifft2(double* a, int n)
 {
-    if (n <= 0 || (n & (n - 1))) return -1;
-    for (int r = 0; r < n; r++) orc_ifft_1d(a + (int64_t)r * n * 2, n, 1);
-    for (int col = 0; col < n; col++) orc_ifft_1d(a + (int64_t)col * 2, n, n);
+    if (n <= 0) return -1;
+    if ((n & (n - 1)) == 0) {
+        for (int r = 0; r < n; r++) orc_ifft_1d(a + (int64_t)r * n * 2, n, 1);
+        for (int col = 0; col < n; col++) orc_ifft_1d(a + (int64_t)col * 2, n, n);
+        return 0;
+    }
+    double* root = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    double* line = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    for (int e = 0; e < n; e++) {
+        double ang = ORC_TWO_PI * (double)e / (double)n;
+        root[2 * e] = cos(ang);
+        root[2 * e + 1] = sin(ang);
+    }
+    for (int r = 0; r < n; r++) {
+        orc_idft_any(a + (int64_t)r * n * 2, 1, n, root, n, line);
+        memcpy(a + (int64_t)r * n * 2, line, sizeof(double) * 2 * (size_t)n);
+    }
+    for (int col = 0; col < n; col++) {
+        orc_idft_any(a + (int64_t)col * 2, n, n, root, n, line);
+        for (int y = 0; y < n; y++) {
+            a[((int64_t)y * n + col) * 2] = line[2 * y];
+            a[((int64_t)y * n + col) * 2 + 1] = line[2 * y + 1];
+        }
+    }
+    free(root);
+    free(line);
     return 0;
 }
 
@@ -575,6 +645,41 @@ void oracle_idft2(const double* G, int n, double* a)
             a[((int64_t)y * n + x) * 2] = sr;
             a[((int64_t)y * n + x) * 2 + 1] = si;
         }
+}
+
+/* Selected pixels of the dirty image of a grid, summed directly (Eq. 4 and the shift of oracle_image):
+ * out[i] = Re a[(y_i + n/2) mod n][(x_i + n/2) mod n] / W with a[Y][X] = sum G[v][u] exp(+2 pi i (u X + v Y) / n),
+ * the sum taken over the grid's nonzero cells only (a gridded image has few), the phase index reduced
+ * modulo n in integers.  G: complex double [n][n]; yx: int32 [n_px][2] (y, x). */
+void oracle_image_pixels(const double* G, int n, double W, const int32_t* yx, int64_t n_px, double* out)
+{
+    int64_t nz = 0;
+    for (int64_t c = 0; c < (int64_t)n * n; c++)
+        if (G[2 * c] != 0.0 || G[2 * c + 1] != 0.0) nz++;
+    int32_t* cu = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nz > 0 ? nz : 1));
+    int32_t* cv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nz > 0 ? nz : 1));
+    int64_t k = 0;
+    for (int v = 0; v < n; v++)
+        for (int u = 0; u < n; u++)
+            if (G[((int64_t)v * n + u) * 2] != 0.0 || G[((int64_t)v * n + u) * 2 + 1] != 0.0) {
+                cu[k] = u;
+                cv[k] = v;
+                k++;
+            }
+    int h = n / 2;
+    for (int64_t i = 0; i < n_px; i++) {
+        int64_t X = (yx[2 * i + 1] + h) % n, Y = (yx[2 * i] + h) % n;
+        double sr = 0.0;
+        for (int64_t c = 0; c < nz; c++) {
+            int64_t e = ((int64_t)cu[c] * X + (int64_t)cv[c] * Y) % n;
+            double ang = ORC_TWO_PI * (double)e / (double)n;
+            const double* g = G + ((int64_t)cv[c] * n + cu[c]) * 2;
+            sr += g[0] * cos(ang) - g[1] * sin(ang);
+        }
+        out[i] = sr / W;
+    }
+    free(cu);
+    free(cv);
 }
 
 /* Dirty image (Sec. 5.2.4): img[y][x] = Re a[(y + N/2) mod N][(x + N/2) mod N] / W, which puts the phase
@@ -615,7 +720,7 @@ int oracle_pipeline(const uint8_t* volt, int64_t fine_stride, int n_tiles, int n
                     const int64_t* ids, int64_t n_ids, int n_threads,
                     double* grids, double* imgs, double* W_out, double* maxim_out)
 {
-    if (n_pix <= 2 || (n_pix & (n_pix - 1)) || c <= 0 || ns <= 0 || n_fine % c) return -1;
+    if (n_pix <= 2 || (n_pix & 1) || c <= 0 || ns <= 0 || n_fine % c) return -1;
     if (!(phase_l * phase_l + phase_m * phase_m < 1.0)) return -1;
     int phased = phase_l != 0.0 || phase_m != 0.0;
     if (support >= 2 && (support > 16 || (double)(n_pix - 1) - 0.5 * (double)support <= 0.0)) return -1;

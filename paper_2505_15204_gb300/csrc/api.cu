@@ -29,8 +29,8 @@ blink_status cuda_error(cudaError_t e, const char* what) {
 blink_status check_imaging(const blink_imaging* im) {
     if (!im) return set_error(BLINK_ERR_INVALID_ARG, "imaging descriptor is NULL");
     const int n = im->n_pix;
-    if (n < 64 || n > 2048 || (n & (n - 1)))
-        return set_error(BLINK_ERR_UNSUPPORTED, "imaging.n_pix must be a power of two in [64, 2048]");
+    if (n < 64 || n > 8192 || !mixed_side_ok(n))
+        return set_error(BLINK_ERR_UNSUPPORTED, "imaging.n_pix must be even, in [64, 8192], with no prime factor above 5");
     if (im->pol != BLINK_POL_I && im->pol != BLINK_POL_XX)
         return set_error(BLINK_ERR_INVALID_ARG, "imaging.pol must be BLINK_POL_I or BLINK_POL_XX");
     if (im->precision != BLINK_PREC_FP32 && im->precision != BLINK_PREC_BF16)
@@ -38,8 +38,8 @@ blink_status check_imaging(const blink_imaging* im) {
     if (!std::isfinite(im->cell_lambda)) return set_error(BLINK_ERR_INVALID_ARG, "imaging.cell_lambda is not finite");
     if (im->support < 0 || im->support > 16)
         return set_error(BLINK_ERR_INVALID_ARG, "imaging.support must be 0 or 1 (nearest cell) or a kernel width in [2, 16]");
-    if (im->support >= 2 && n > 1024)
-        return set_error(BLINK_ERR_UNSUPPORTED, "with a convolution kernel imaging.n_pix is at most 1024 (grid side 2 n_pix)");
+    if (im->support >= 2 && n > 4096)
+        return set_error(BLINK_ERR_UNSUPPORTED, "with a convolution kernel imaging.n_pix is at most 4096 (grid side 2 n_pix)");
     if (!std::isfinite(im->phase_l) || !std::isfinite(im->phase_m) ||
         !(im->phase_l * im->phase_l + im->phase_m * im->phase_m < 1.0))
         return set_error(BLINK_ERR_INVALID_ARG, "imaging.phase_l, phase_m must be direction cosines with l^2 + m^2 < 1");
@@ -224,34 +224,47 @@ struct GatherBuilder {
     int64_t B = 0;
     bool src16 = false, pos16 = false;
     int max_per_channel = 0;
-    GatherBuilder(int n, int F) : N(n), half(n / 2), nkeys((int64_t)(n / 2) * n), count(nkeys + 1),
-                                  ent_off((size_t)F * (n / 2 + 1)) {}
+    GatherBuilder(int n, int F) : N(n), half(n / 2), nkeys((int64_t)(n / 2) * n), ent_off((size_t)F * (n / 2 + 1)) {}
     uint32_t key(int u, int v) const { return (uint32_t)((int64_t)u * N + v); }
     void clear() {
         ekey.clear();
         eval.clear();
     }
-    // stable counting sort by key: the entries of a cell stay in the order they were added
+    // stable sort by key: the entries of a cell stay in the order they were added (a counting sort while
+    // the keys are few next to the entries, a comparison sort on large grids)
     blink_status add_channel(int f) {
-        std::fill(count.begin(), count.end(), 0);
-        for (uint32_t k : ekey) count[k + 1]++;
-        for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
+        if (count.empty() && nkeys <= (int64_t)16 * (int64_t)ekey.size() + 4096) count.assign(nkeys + 1, 0);
         sorted.assign(ekey.size(), 0);
         skey.assign(ekey.size(), 0);
-        {
+        const int64_t base = (int64_t)ent.size();
+        if (nkeys <= (int64_t)16 * (int64_t)ekey.size() + 4096) {
+            std::fill(count.begin(), count.end(), 0);
+            for (uint32_t k : ekey) count[k + 1]++;
+            for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
             std::vector<int> cur(count.begin(), count.end() - 1);
             for (size_t e = 0; e < ekey.size(); e++) {
                 const int at = cur[ekey[e]]++;
                 sorted[at] = eval[e];
                 skey[at] = ekey[e];
             }
+            for (int u = 0; u <= half; u++)
+                ent_off[(size_t)f * (half + 1) + u] = (int)(base + count[std::min<int64_t>((int64_t)u * N, nkeys)]);
+        } else {
+            std::vector<uint32_t> ord(ekey.size());
+            for (size_t e = 0; e < ord.size(); e++) ord[e] = (uint32_t)e;
+            std::stable_sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) { return ekey[a] < ekey[b]; });
+            for (size_t e = 0; e < ord.size(); e++) {
+                sorted[e] = eval[ord[e]];
+                skey[e] = ekey[ord[e]];
+            }
+            for (int u = 0; u <= half; u++)
+                ent_off[(size_t)f * (half + 1) + u] =
+                    (int)(base + (std::lower_bound(skey.begin(), skey.end(), (uint32_t)std::min<int64_t>((int64_t)u * N, nkeys)) -
+                                  skey.begin()));
         }
-        const int64_t base = (int64_t)ent.size();
-        for (int u = 0; u <= half; u++)
-            ent_off[(size_t)f * (half + 1) + u] = (int)(base + count[std::min<int64_t>((int64_t)u * N, nkeys)]);
         for (size_t e = 0; e < sorted.size(); e++) {
             const uint32_t u = skey[e] / N, v = skey[e] % N;
-            ent.push_back(make_uint2(u | (v << 11) | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
+            ent.push_back(make_uint2(u | (v << 13) | ((sorted[e] & 1u) << 31), sorted[e] >> 1));
         }
         max_per_channel = std::max(max_per_channel, (int)sorted.size());
         if (src16) {
@@ -466,17 +479,28 @@ blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std:
             eval.push_back(v);
             ewt.push_back(x);
         }, w_, d_);
-        // stable counting sort by key into the channel's range: a cell's entries stay in baseline order
-        std::vector<int> count(nkeys + 1, 0);
-        for (uint32_t k : ekey) count[k + 1]++;
-        for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
-        for (int u = 0; u <= half; u++)
-            ent_off[(size_t)f * (half + 1) + u] = (int)(base[f] + count[std::min<int64_t>((int64_t)u * N, nkeys)]);
-        for (size_t e = 0; e < ekey.size(); e++) {
-            const int64_t at = base[f] + count[ekey[e]]++;
-            const uint32_t u = ekey[e] / N, v = ekey[e] % N;
-            ent[at] = make_uint2(u | (v << 11) | ((eval[e] & 1u) << 31), eval[e] >> 1);
-            wt[at] = ewt[e];
+        // stable sort by key into the channel's range: a cell's entries stay in baseline order (a counting
+        // sort while the keys are few next to the entries, a comparison sort on large grids)
+        std::vector<uint32_t> ord(ekey.size());
+        if (nkeys <= (int64_t)16 * (int64_t)ekey.size() + 4096) {
+            std::vector<int> count(nkeys + 1, 0);
+            for (uint32_t k : ekey) count[k + 1]++;
+            for (int64_t k = 0; k < nkeys; k++) count[k + 1] += count[k];
+            for (size_t q = 0; q < ekey.size(); q++) ord[count[ekey[q]]++] = (uint32_t)q;
+        } else {
+            for (size_t q = 0; q < ord.size(); q++) ord[q] = (uint32_t)q;
+            std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) { return ekey[x] < ekey[y]; });
+        }
+        int64_t e = 0;
+        for (int u = 0; u <= half; u++) {
+            const uint32_t lim = (uint32_t)std::min<int64_t>((int64_t)u * N, nkeys);
+            while (e < (int64_t)ord.size() && ekey[ord[e]] < lim) e++;
+            ent_off[(size_t)f * (half + 1) + u] = (int)(base[f] + e);
+        }
+        for (size_t q = 0; q < ord.size(); q++) {
+            const uint32_t k = ekey[ord[q]], u = k / N, v = k % N;
+            ent[base[f] + q] = make_uint2(u | (v << 13) | ((eval[ord[q]] & 1u) << 31), eval[ord[q]] >> 1);
+            wt[base[f] + q] = ewt[ord[q]];
         }
     });
     p->W.assign(F, 0.f);
@@ -546,6 +570,24 @@ blink_status upload_gains(blink_context* ctx, const blink_array* a, int F, cudaS
 
 // The twiddle set of side N (see tws_total), made on the device on first use and kept in the context.
 blink_status twiddles(blink_context* ctx, int N, float2** out) {
+    if (!fast_side(N)) {
+        for (auto& t : ctx->tw_any)
+            if (t.first == N) {
+                *out = t.second;
+                return BLINK_OK;
+            }
+        float2* d = nullptr;
+        BLINK_CUDA(cudaMalloc(&d, sizeof(float2) * N));
+        blink_status s = make_unit_roots(d, N, 0);
+        cudaError_t e = cudaDeviceSynchronize();
+        if (s != BLINK_OK || e != cudaSuccess) {
+            cudaFree(d);
+            return s != BLINK_OK ? s : cuda_error(e, "twiddle kernel");
+        }
+        ctx->tw_any.emplace_back(N, d);
+        *out = d;
+        return BLINK_OK;
+    }
     int lg = 0;
     while ((1 << lg) < N) lg++;
     if (lg >= 16 || (1 << lg) != N) return set_error(BLINK_ERR_UNSUPPORTED, "twiddle table side");
@@ -674,12 +716,14 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
         if ((s = dmalloc(&p->d_cells, (size_t)p->F * p->B)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_W, p->F)) != BLINK_OK) return fail(s);
         if ((s = dmalloc(&p->d_Wk, p->F)) != BLINK_OK) return fail(s);
-        if ((s = dmalloc(&p->d_tw, tws_total(p->N))) != BLINK_OK) return fail(s);
+        const bool fast = fast_side(p->N);
+        if ((s = dmalloc(&p->d_tw, fast ? tws_total(p->N) : p->N)) != BLINK_OK) return fail(s);
         e = cudaMemcpy(p->d_enu, a->enu_m, sizeof(double) * 3 * a->n_tiles, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->d_freq, p->out_freq.data(), sizeof(double) * p->F, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(cuda_error(e, "cudaMemcpy(plan)"));
-        if ((s = make_twiddles(p->d_tw, p->N, st)) != BLINK_OK) return fail(s);
-        if ((s = fft_constants(p->N)) != BLINK_OK) return fail(s);
+        if ((s = fast ? make_twiddles(p->d_tw, p->N, st) : make_unit_roots(p->d_tw, p->N, st)) != BLINK_OK)
+            return fail(s);
+        if (fast && (s = fft_constants(p->N)) != BLINK_OK) return fail(s);
         // with a kernel the gather list is built from the exact (u, v), kept on the device only meanwhile
         const bool kb = p->support && need_gather;
         if (kb && (s = dmalloc(&p->d_uvw, (size_t)p->F * p->B * 3)) != BLINK_OK) return fail(s);
@@ -742,9 +786,68 @@ int64_t sample_stride_bytes(const blink_obs* o, int n_tiles) {
 // one persistent launch that grids and transforms all of their images (fft_persistent.cu).
 constexpr size_t kVisCapBytes = (size_t)4 << 30;
 
+// Batched path on a side outside the side-specialised kernels: one correlator launch per chunk of
+// integrations, then per wave of images (their column results sized to stay in L2) the mixed-radix column
+// pass, gathering each image's cells from the sums, and the row pass (fft_mixed.cu).
+blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
+                       const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st,
+                       GainRef gains) {
+    const int F = p.F, T = tau1 - tau0;
+    if (T <= 0) return BLINK_OK;
+    const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
+    const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)p.B * 8 * F))));
+    const bool crop = p.support != 0;
+    const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
+    const size_t per_img = (size_t)(crop ? p.N / 2 : p.N) * mixed_h_row(p.N) * el;
+    const int wave = (int)std::max<size_t>(1, std::min<size_t>(65535, ((size_t)48 << 20) / per_img));
+    void* vis = nullptr;
+    void* H = nullptr;
+    BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));
+    BLINK_TRY(workspace(ctx, 1, (size_t)std::min(wave, t_chunk * F) * per_img, &H));
+    ImgOut io;
+    io.phase = p.d_phase;
+    MixedIn in;
+    in.N = p.N;
+    in.tw = p.d_tw;
+    in.vstride = p.B;
+    in.F = F;
+    in.ent_off = p.d_ent_off;
+    in.ent = p.d_ent;
+    in.wt = p.d_wt;
+    in.corr = crop ? p.d_corr : nullptr;
+    const int out_first = tau0 * F;
+    for (int ta = tau0; ta < tau1; ta += t_chunk) {
+        const int tb = std::min(tau1, ta + t_chunk);
+        const int first = ta * F, n_items = (tb - ta) * F;
+        {
+            StageTimer t(ctx, BLINK_STAGE_CORRELATE, st);
+            if (arith == BLINK_CORR_FP8)
+                BLINK_TRY(launch_corr_fp8(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
+                                          ctx->d_status, ctx->n_sm, st, gains, io));
+            else
+                BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
+                                           ctx->d_status, st, gains, io));
+        }
+        for (int w0 = 0; w0 < n_items; w0 += wave) {
+            const int nw = std::min(wave, n_items - w0);
+            in.vis = static_cast<const float2*>(vis) + (int64_t)w0 * p.B;
+            in.first = first + w0;
+            const WaveMap wm{1, 0, first + w0, nw};
+            {
+                StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
+                BLINK_TRY(launch_mixed(in, 0, prec, nw, H, nullptr, 1, wm, out_first, nullptr, st));
+            }
+            StageTimer t(ctx, BLINK_STAGE_ROW_FFT, st);
+            BLINK_TRY(launch_mixed(in, 1, prec, nw, H, p.d_Wk, F, wm, out_first, d_img, st));
+        }
+    }
+    return BLINK_OK;
+}
+
 blink_status run_batched(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
                          const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st,
                          bool may_tune = true, GainRef gains = {}) {
+    if (!fast_side(p.N)) return run_mixed(ctx, p, o, prec, arith, d_volt, sstride, tau0, tau1, d_img, st, gains);
     const int N = p.N, F = p.F;
     const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
     const int T = tau1 - tau0;
@@ -925,6 +1028,7 @@ void blink_destroy(blink_context* ctx) {
     for (Plan* p : ctx->plans) free_plan(p);
     for (auto& w : ctx->ws) cudaFree(w.ptr);
     for (float2* t : ctx->tw) cudaFree(t);
+    for (auto& t : ctx->tw_any) cudaFree(t.second);
     for (auto& r : ctx->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -1093,6 +1197,22 @@ blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const
     if (n_images == 0) return BLINK_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int N = imaging->n_pix, prec = imaging->precision;
+    if (!fast_side(N)) {
+        MixedIn in;
+        in.N = N;
+        BLINK_TRY(twiddles(ctx, N, const_cast<float2**>(&in.tw)));
+        const size_t per_img = (size_t)N * mixed_h_row(N) * (prec == BLINK_PREC_BF16 ? 4 : 8);
+        const int wave = (int)std::max<size_t>(1, std::min<size_t>({(size_t)n_images, (size_t)65535, ((size_t)48 << 20) / per_img}));
+        void* H = nullptr;
+        BLINK_TRY(workspace(ctx, 1, (size_t)wave * per_img, &H));
+        for (int w0 = 0; w0 < n_images; w0 += wave) {
+            const int nw = std::min(wave, n_images - w0);
+            in.grid = reinterpret_cast<const float2*>(d_grid) + (int64_t)w0 * N * (N / 2 + 1);
+            BLINK_TRY(launch_mixed(in, 0, prec, nw, H, nullptr, 1, WaveMap{1, 0, w0, nw}, 0, nullptr, st));
+            BLINK_TRY(launch_mixed(in, 1, prec, nw, H, d_weight, n_images, WaveMap{1, 0, w0, nw}, 0, d_img, st));
+        }
+        return BLINK_OK;
+    }
     const int cw = col_block_width(N);
     const int ldh = N / 2 + cw;                 // room for the Nyquist column u = N/2
     float2* tw = nullptr;
@@ -1139,6 +1259,34 @@ blink_status blink_pipeline(blink_context* ctx, const blink_array* array, const 
     BLINK_TRY(upload_gains(ctx, array, p->F, st, &g));
     if (mode == BLINK_MODE_BATCHED) {
         BLINK_TRY(run_batched(ctx, *p, obs, imaging->precision, arith, d_volt, ss, 0, T, d_img, st, true, g));
+    } else if (!fast_side(N)) {
+        // the plain form on a mixed-radix side: per image, atomic gridding into a stored grid, then the
+        // column and row passes of that grid
+        const size_t el = imaging->precision == BLINK_PREC_BF16 ? 4 : 8;
+        void *vis = nullptr, *H = nullptr, *grid = nullptr;
+        BLINK_TRY(workspace(ctx, 0, (size_t)p->B * sizeof(float2), &vis));
+        BLINK_TRY(workspace(ctx, 1, (size_t)N * mixed_h_row(N) * el, &H));
+        BLINK_TRY(workspace(ctx, 2, (size_t)N * (N / 2 + 1) * sizeof(float2), &grid));
+        const int kind = p->pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
+        ImgOut io;
+        io.phase = p->d_phase;
+        MixedIn in;
+        in.N = N;
+        in.tw = p->d_tw;
+        in.grid = static_cast<const float2*>(grid);
+        for (int id = 0; id < n_img; id++) {
+            if (arith == BLINK_CORR_FP8)
+                BLINK_TRY(launch_corr_fp8(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B, ctx->d_status,
+                                          ctx->n_sm, st, g, io));
+            else
+                BLINK_TRY(launch_corr_fp32(kind, d_volt, ss, *p, obs->samples_per_int, id, 1, vis, p->B,
+                                           ctx->d_status, st, g, io));
+            BLINK_CUDA(cudaMemsetAsync(grid, 0, (size_t)N * (N / 2 + 1) * sizeof(float2), st));
+            BLINK_TRY(launch_grid_atomic(*p, static_cast<float2*>(vis), id, static_cast<float2*>(grid), st));
+            const WaveMap wm{p->F, id % p->F, id / p->F, 1};
+            BLINK_TRY(launch_mixed(in, 0, imaging->precision, 1, H, nullptr, 1, wm, 0, nullptr, st));
+            BLINK_TRY(launch_mixed(in, 1, imaging->precision, 1, H, p->d_Wk, p->F, wm, 0, d_img, st));
+        }
     } else {
         const int cw = p->cw, ldh = N / 2 + cw;
         const size_t el = imaging->precision == BLINK_PREC_BF16 ? 4 : 8;
@@ -1271,8 +1419,8 @@ blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_
                               const int32_t* h_delays, float* d_out, void* stream) {
     if (!d_img || !d_out || !h_delays) return set_error(BLINK_ERR_INVALID_ARG, "d_img, d_out or h_delays is NULL");
     if (n_int < 1 || n_chan < 1) return set_error(BLINK_ERR_INVALID_ARG, "n_int and n_chan must be >= 1");
-    if (n_pix < 64 || n_pix > 2048 || (n_pix & (n_pix - 1)))
-        return set_error(BLINK_ERR_INVALID_ARG, "n_pix must be a power of two in [64, 2048]");
+    if (n_pix < 64 || n_pix > 8192 || (n_pix & 1))
+        return set_error(BLINK_ERR_INVALID_ARG, "n_pix must be even, in [64, 8192]");
     if (((uintptr_t)d_img & 15) || ((uintptr_t)d_out & 15))
         return set_error(BLINK_ERR_INVALID_ARG, "d_img and d_out must be 16-byte aligned");
     int dmax = 0;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/blink.h"
@@ -67,7 +68,7 @@ struct Plan {
     double* d_freq = nullptr;              // [F]
     uint32_t* d_cells = nullptr;           // [F][B]
     int* d_ent_off = nullptr;              // [F][N/2 + 1]: first gather entry of each column u
-    uint2* d_ent = nullptr;                // [n_contrib] {u | v << 11 | conj << 31, b}, sorted by (u, v, b)
+    uint2* d_ent = nullptr;                // [n_contrib] {u | v << 13 | conj << 31, b}, sorted by (u, v, b)
     float* d_wt = nullptr;                 // [n_contrib] kernel weight of each entry (convolution only)
     float* d_corr = nullptr;               // [Ni] grid correction 1 / c(nu) per image pixel index (convolution only)
     float* d_W = nullptr;                  // [F] W, the sum of weights
@@ -107,6 +108,7 @@ struct blink_context {
     std::vector<blink::Plan*> plans;       // most recent last
     blink::Workspace ws[8];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays
     float2* tw[16] = {};                   // twiddle tables by log2(side)
+    std::vector<std::pair<int, float2*>> tw_any;   // unit-root tables of the other sides (fft_mixed.cu)
     blink::FftWait fft_wait;               // dependency-wait budget of the persistent FFT kernel
     bool fused = false;                    // correlation inside the side-512 imaging launch (blink_set_fused)
     // per-stage profiling (blink_set_profiling): recorded (stage, start, stop) event pairs and a free pool
@@ -207,6 +209,33 @@ bool fft_takes_gathered(const Plan& p);
 std::vector<FftTune> fft_tune_candidates(const Plan& p);
 // Constant-memory twiddles of the persistent kernel for side N on the current device (once per plan).
 blink_status fft_constants(int N);
+
+// ---- sides outside the side-specialised kernels (fft_mixed.cu) -------------------------------------
+// Power-of-two sides in [64, 2048] run the side-specialised kernels; every other even side whose only
+// prime factors are 2, 3 and 5, up to 8192, runs the mixed-radix column and row passes.
+inline bool fast_side(int N) { return N >= 64 && N <= 2048 && (N & (N - 1)) == 0; }
+bool mixed_side_ok(int N);
+// exp(+2 pi i k / N) for k < N (the mixed-radix passes' twiddle table)
+blink_status make_unit_roots(float2* d_out, int N, cudaStream_t st);
+// complex elements per row of the mixed column-pass result H
+size_t mixed_h_row(int N);
+struct MixedIn {
+    int N = 0;                             // grid side
+    const float2* tw = nullptr;            // make_unit_roots(N)
+    const float2* grid = nullptr;          // stored half-plane grids [n][N][N/2 + 1] (the Nyquist column included) ...
+    const float2* vis = nullptr;           // ... or per-image sums in baseline order, image i at vis + i * vstride,
+    int64_t vstride = 0;                   //     gathered through the plan's lists of channel (first + i) % F
+    int first = 0, F = 1;
+    const int* ent_off = nullptr;
+    const uint2* ent = nullptr;
+    const float* wt = nullptr;             // kernel weights per entry, or NULL
+    const float* corr = nullptr;           // kernel grid correction [N/2]: keep the central N/2 x N/2, or NULL
+};
+// pass 0: column pass of n_images grids into d_H (n_images * rows * mixed_h_row(N) elements of the
+// storage type, rows = N, or N/2 with a correction); pass 1: row pass of d_H into images, image i written
+// at d_img + (wm.id(i) - out_first) * side^2 and divided by d_w[wm.id(i) % w_mod].
+blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, void* d_H, const float* d_w, int w_mod,
+                          WaveMap wm, int out_first, float* d_img, cudaStream_t st);
 blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const float2* d_grid, int n_images,
                                  void* d_H, int ldh, cudaStream_t st);
 blink_status launch_rowpass(int N, int prec, const float2* d_tw, const void* d_H, int ldh, int has_nyq,
@@ -263,6 +292,35 @@ template <> __device__ __forceinline__ void idft<4>(float2* v) {
     v[1] = cadd(a1, a3);
     v[2] = csub(a0, a2);
     v[3] = csub(a1, a3);
+}
+
+template <> __device__ __forceinline__ void idft<3>(float2* v) {
+    // w = exp(2 pi i / 3) = -1/2 + i sqrt(3)/2: v1 w^q + v2 w^2q = -(v1 + v2)/2 +- i sqrt(3)/2 (v1 - v2)
+    const float h = 0.86602540378443864676f;
+    const float2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    const float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    const float2 r = make_float2(-h * d.y, h * d.x);                      // i sqrt(3)/2 (v1 - v2)
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+}
+
+template <> __device__ __forceinline__ void idft<5>(float2* v) {
+    // w = exp(2 pi i / 5); with a1 = v1 + v4, b1 = v1 - v4, a2 = v2 + v3, b2 = v2 - v3:
+    // X1, X4 = v0 + c1 a1 + c2 a2 +- i (s1 b1 + s2 b2);  X2, X3 = v0 + c2 a1 + c1 a2 +- i (s2 b1 - s1 b2)
+    // where c1 = cos(2 pi/5) = (sqrt 5 - 1)/4, c2 = cos(4 pi/5) = -(sqrt 5 + 1)/4, s1 = sin(2 pi/5), s2 = sin(4 pi/5)
+    const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+    const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+    const float2 a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]), a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+    const float2 p1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+    const float2 p2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+    const float2 q1 = cmul_i(make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y));
+    const float2 q2 = cmul_i(make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y));
+    v[0] = cadd(v[0], cadd(a1, a2));
+    v[1] = cadd(p1, q1);
+    v[4] = csub(p1, q1);
+    v[2] = cadd(p2, q2);
+    v[3] = csub(p2, q2);
 }
 
 template <> __device__ __forceinline__ void idft<8>(float2* v) {
@@ -536,9 +594,9 @@ __device__ __forceinline__ void dev_fail(int* status, int code) {
 // keep the row-wise store phase free of bank conflicts.
 template <int N> __host__ __device__ constexpr int col_ld() { return N + N / 16 + 2; }
 
-// Gather entries: x = u | v << 11 | conj << 31 (cell (u, v) of the half plane), y = baseline.
-__device__ __forceinline__ int ent_u(uint32_t x) { return (int)(x & 0x7FFu); }
-__device__ __forceinline__ int ent_v(uint32_t x) { return (int)((x >> 11) & 0xFFFFFu); }
+// Gather entries: x = u | v << 13 | conj << 31 (cell (u, v) of the half plane, u <= 4096), y = baseline.
+__device__ __forceinline__ int ent_u(uint32_t x) { return (int)(x & 0x1FFFu); }
+__device__ __forceinline__ int ent_v(uint32_t x) { return (int)((x >> 13) & 0x3FFFFu); }
 __device__ __forceinline__ uint32_t ent_cell(uint32_t x) { return x & 0x7FFFFFFFu; }
 
 // Gather entry i of a column whose entries end at `end`: its cell key and visibility (conjugated for an

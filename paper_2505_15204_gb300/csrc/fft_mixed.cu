@@ -1,0 +1,351 @@
+// Imaging (gridding + Eq. 4's inverse 2D transform; Sec. 5.2.4) for image sides the side-specialised
+// kernels do not cover: any even side N = 2^a 3^b 5^c up to 8192 (1200, 2400, 4096, 8192, ...).
+//
+// Two launches per wave of images, the column results kept in L2 between them when the wave fits:
+//   column pass  one CTA per `cw` consecutive u columns of the half plane: the columns' cells are gathered
+//                (or read from a stored grid), multiplied by (-1)^(u+v) (the shift by N/2), transformed
+//                along v by an N-point mixed-radix FFT in shared memory and written to H[y][u];
+//   row pass     one CTA per `rb` image rows: the complex-to-real transform along u, formed from an
+//                N/2-point complex FFT of the paired half spectrum, scaled by 1/W (and, with a convolution
+//                kernel, cropped to the central half and grid-corrected).
+// The FFT is a Stockham autosort iteration over the factors of the length (radices 4, 2, 3, 5) between two
+// shared-memory buffers per transform: a thread reads a butterfly's inputs, transforms them in registers
+// and writes the outputs to the other buffer in the next stage's order, so only one butterfly is live in
+// registers at a time and blocks of many threads stay resident.
+#include <algorithm>
+
+#include "blink_internal.cuh"
+
+namespace blink {
+
+namespace {
+
+constexpr int kMaxThreads = 1024;
+
+__host__ __device__ __forceinline__ int pd(int i) { return i + (i >> 5); }     // one pad slot per 32 points
+
+// One Stockham stage of radix R of an n-point transform after stages whose radices multiply to L, from
+// buffer `in` to buffer `out`.  Point addresses: before the stage, Y(j, k1) (j < n/L, k1 < L) sits at
+// j L + k1 and holds the L-point transform of the points j + (n/L) t; butterfly b = j' L + k1 (j' < n/(LR))
+// reads Y(j' + m p, k1) for p < R (at b + p n/R, m = n/(LR)), multiplies input p by w_n^(p k1 m), transforms
+// over p and writes output q to Y'(j', k1 + L q) at j' L R + k1 + L q.  tw[k * tws] = exp(+2 pi i k / n).
+template <int R>
+__device__ __forceinline__ void stage(const float2* in, float2* out, int n, int L, const float2* __restrict__ tw,
+                                      int tws, int t, int nt) {
+    const int nb = n / R, m = nb / L;
+    for (int b = t; b < nb; b += nt) {
+        const int j = b / L, k1 = b - j * L;
+        float2 v[R];
+#pragma unroll
+        for (int p = 0; p < R; p++) v[p] = in[pd(b + p * nb)];
+        if (L > 1) {
+            const float2 w = __ldg(tw + (int64_t)k1 * m * tws);
+            float2 wp = w;
+#pragma unroll
+            for (int p = 1; p < R; p++) {
+                v[p] = cmul(v[p], wp);
+                if (p + 1 < R) wp = cmul(wp, w);
+            }
+        }
+        idft<R>(v);
+        const int d = j * L * R + k1;
+#pragma unroll
+        for (int q = 0; q < R; q++) out[pd(d + q * L)] = v[q];
+    }
+    __syncthreads();
+}
+
+// The whole n-point transform of a[pd(0 .. n-1)] by the threads t < nt of each transform, alternating
+// between the buffers a and b; radices packed 4 bits per stage, first stage lowest.  Every thread of the
+// block runs the same stages.  Returns the buffer that holds the result.
+__device__ __forceinline__ float2* fft_any(float2* a, float2* b, int n, uint64_t rad, int n_rad,
+                                           const float2* __restrict__ tw, int tws, int t, int nt) {
+    int L = 1;
+    for (int k = 0; k < n_rad; k++) {
+        const int R = (int)((rad >> (4 * k)) & 15u);
+        switch (R) {
+            case 4: stage<4>(a, b, n, L, tw, tws, t, nt); break;
+            case 2: stage<2>(a, b, n, L, tw, tws, t, nt); break;
+            case 3: stage<3>(a, b, n, L, tw, tws, t, nt); break;
+            default: stage<5>(a, b, n, L, tw, tws, t, nt); break;
+        }
+        float2* x = a;
+        a = b;
+        b = x;
+        L *= R;
+    }
+    return a;
+}
+
+// exp(+2 pi i k / n) for k < n: FP64 sincospi, rounded to FP32
+__global__ void k_unit_roots(float2* out, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)n, &sn, &cs);
+    out[k] = make_float2((float)cs, (float)sn);
+}
+
+struct MixedCol {
+    int N, half, cw_log, nt, ld;           // grid side, N/2, log2(columns per CTA), threads per column, column stride
+    uint64_t rad;
+    int n_rad;
+    const float2* tw;                      // exp(+2 pi i k / N), k < N
+    // input: a stored half-plane grid [img][N][N/2 + 1] ...
+    const float2* grid;
+    // ... or the gather lists: image i's sums at vis + i * vstride (baseline order), channel (first + i) % F
+    const float2* vis;
+    int64_t vstride;
+    int first, F;
+    const int* ent_off;
+    const uint2* ent;
+    const float* wt;                       // per-entry kernel weights, or NULL (nearest cell)
+    // output: rows [y0, y0 + ny) of the column transforms (all rows, or the central half with a kernel)
+    void* H;
+    int ldh, y0, ny;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_mixed_col(const MixedCol P) {
+    extern __shared__ float2 s[];          // [cw][ld] transform inputs, then [cw][ld] the second buffers
+    const int img = blockIdx.y, tid = threadIdx.x, nthr = blockDim.x;
+    const int cw = 1 << P.cw_log, u0 = blockIdx.x * cw;
+    const int ncol = min(cw, P.half + 1 - u0);
+    if (P.grid) {
+        const float2* G = P.grid + (int64_t)img * P.N * (P.half + 1);
+        for (int e = tid; e < P.N * cw; e += nthr) {
+            const int v = e >> P.cw_log, c = e & (cw - 1), u = u0 + c;
+            float2 x = make_float2(0.f, 0.f);
+            if (c < ncol) {
+                x = G[(int64_t)v * (P.half + 1) + u];
+                if ((u + v) & 1) x = make_float2(-x.x, -x.y);
+            }
+            s[c * P.ld + pd(v)] = x;
+        }
+    } else {
+        for (int e = tid; e < cw * P.ld; e += nthr) s[e] = make_float2(0.f, 0.f);
+        __syncthreads();
+        const float2* V = P.vis + (int64_t)img * P.vstride;
+        const int* off = P.ent_off + (int64_t)((P.first + img) % P.F) * (P.half + 1);
+        const int lane = tid & 31;
+        auto val = [&](uint32_t b) { return V[b]; };
+        auto idx = [&](int u, int v) { return (u - u0) * P.ld + pd(v); };
+        for (int c = tid >> 5; c < ncol; c += nthr >> 5) {
+            const int u = u0 + c;
+            if (u >= P.half) continue;     // no cell reaches the Nyquist column
+            const int beg = off[u], end = off[u + 1];
+            uint32_t key;
+            float2 x;
+            gather_entry(P.ent, P.wt, beg + lane, end, val, key, x);
+            warp_gather_column(P.ent, P.wt, beg, end, lane, s, val, idx, true, key, x);
+        }
+    }
+    __syncthreads();
+    const int c = tid / P.nt, t = tid - c * P.nt;
+    const float2* res = fft_any(s + c * P.ld, s + (cw + c) * P.ld, P.N, P.rad, P.n_rad, P.tw, 1, t, P.nt);
+    const int off = (int)(res - (s + c * P.ld));      // the result buffer's offset, the same for every column
+    T* H = static_cast<T*>(P.H) + (int64_t)img * P.ny * P.ldh + u0;
+    for (int e = tid; e < P.ny * cw; e += nthr) {
+        const int r = e >> P.cw_log, cc = e & (cw - 1);
+        if (cc < ncol) st_c(H + (int64_t)r * P.ldh + cc, s[off + cc * P.ld + pd(P.y0 + r)]);
+    }
+}
+
+struct MixedRow {
+    int N, M, nt, rb, ld;                  // grid side, N/2, threads per row, rows per CTA, row stride
+    uint64_t rad;
+    int n_rad;
+    const float2* tw;                      // exp(+2 pi i k / N), k < N
+    const void* H;
+    int ldh, ny, has_nyq;                  // H rows per image; has_nyq: column u = N/2 holds data
+    const float* wts;
+    int w_mod;
+    WaveMap wm;
+    int out_first;
+    int x0, nout;                          // output columns [x0, x0 + nout) of each row; image side nout
+    const float* corr;                     // grid correction per output pixel index, or NULL
+    float* img;
+};
+
+// With M = N/2 and the half spectrum Z[0..M] of a row, x[n] = sum_k Z[k] exp(+2 pi i k n / N) for the real
+// sequence x is x[2m] = Re y[m], x[2m+1] = Im y[m] with y the M-point inverse transform of
+// Y[k] = (Z[k] + conj Z[M-k]) + i (Z[k] - conj Z[M-k]) exp(+2 pi i k / N)  (any M, odd included).
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_mixed_row(const MixedRow P) {
+    extern __shared__ float2 s[];          // [rb][ld] transform inputs, then [rb][ld] the second buffers
+    const int img = blockIdx.y, tid = threadIdx.x;
+    const int r = tid / P.nt, t = tid - r * P.nt, y = blockIdx.x * P.rb + r;
+    const int M = P.M;
+    float2* dst = s + r * P.ld;
+    const T* row = static_cast<const T*>(P.H) + ((int64_t)img * P.ny + y) * P.ldh;
+    for (int k = t; k <= M / 2; k += P.nt) {
+        const float2 zk = ld_c(row + k);
+        const float2 zm = (k == 0) ? (P.has_nyq ? ld_c(row + M) : make_float2(0.f, 0.f)) : ld_c(row + (M - k));
+        dst[pd(k)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), __ldg(P.tw + k))));
+        if (k > 0 && k < M - k)
+            dst[pd(M - k)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), __ldg(P.tw + (M - k)))));
+    }
+    __syncthreads();
+    const float2* res = fft_any(dst, s + (P.rb + r) * P.ld, M, P.rad, P.n_rad, P.tw, 2, t, P.nt);
+    const int id = P.wm.id(img);
+    const float w = P.wts[id % P.w_mod];
+    float scale = 1.0f / (w > 0.f ? w : 1.f);
+    if (P.corr) scale *= P.corr[y];
+    float* out = P.img + ((int64_t)(id - P.out_first) * P.ny + y) * P.nout;
+    for (int x = t; x < P.nout; x += P.nt) {
+        const int X = P.x0 + x;
+        const float2 z = res[pd(X >> 1)];
+        const float a = (X & 1) ? z.y : z.x;
+        out[x] = P.corr ? a * scale * P.corr[x] : a * scale;
+    }
+}
+
+// radices of n in stage order (4s, then 2, then 3s and 5s), packed 4 bits each; false if n has another factor
+bool factor(int n, uint64_t* rad, int* n_rad) {
+    int k = 0;
+    uint64_t r = 0;
+    auto push = [&](int x) {
+        r |= (uint64_t)x << (4 * k);
+        k++;
+    };
+    while (n % 4 == 0 && k < 15) { push(4); n /= 4; }
+    while (n % 2 == 0 && k < 15) { push(2); n /= 2; }
+    while (n % 3 == 0 && k < 15) { push(3); n /= 3; }
+    while (n % 5 == 0 && k < 15) { push(5); n /= 5; }
+    *rad = r;
+    *n_rad = k;
+    return n == 1;
+}
+
+int stride_for(int n) { return (pd(n - 1) + 1 + 15) / 16 * 16 + 1; }     // odd: columns spread over banks
+
+template <typename K>
+blink_status allow_smem(K kernel, size_t bytes) {
+    static size_t done = 0;
+    if (bytes > done) {
+        BLINK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        done = bytes;
+    }
+    return BLINK_OK;
+}
+
+struct Shape {
+    uint64_t rad_c = 0, rad_r = 0;
+    int nrad_c = 0, nrad_r = 0, nt_c = 0, nt_r = 0, cw_log = 0, rb = 1, ld_c = 0, ld_r = 0;   // threads per transform, ...
+    size_t smem_c = 0, smem_r = 0;
+};
+
+bool shape_for(int N, Shape* sh) {
+    if (N < 4 || (N & 1) || N > 8192) return false;
+    if (!factor(N, &sh->rad_c, &sh->nrad_c) || !factor(N / 2, &sh->rad_r, &sh->nrad_r)) return false;
+    sh->ld_c = stride_for(N);
+    sh->ld_r = stride_for(N / 2);
+    const size_t col = 2 * (size_t)sh->ld_c * sizeof(float2), row = 2 * (size_t)sh->ld_r * sizeof(float2);
+    // columns per CTA: up to 8 within 100 KiB of shared memory (two CTAs per SM), at least one
+    int cw_log = 3;
+    while (cw_log > 0 && (col << cw_log) > (size_t)100 * 1024) cw_log--;
+    sh->cw_log = cw_log;
+    sh->smem_c = col << cw_log;
+    sh->nt_c = std::max(32, std::min(kMaxThreads, ((N >= 4096 ? 1024 : 512) >> cw_log) / 32 * 32));
+    // rows per CTA: up to 8 within 100 KiB, dividing N/2 (so both N rows and, with a kernel, N/2 rows)
+    int rb = 8;
+    while (rb > 1 && ((N / 2) % rb || rb * row > (size_t)100 * 1024)) rb /= 2;
+    sh->rb = rb;
+    sh->smem_r = row * rb;
+    sh->nt_r = std::max(32, std::min(kMaxThreads, ((N >= 8192 ? 1024 : 512) / rb) / 32 * 32));
+    return sh->smem_c <= (size_t)227 * 1024 && sh->smem_r <= (size_t)227 * 1024;
+}
+
+}  // namespace
+
+bool mixed_side_ok(int N) {
+    Shape sh;
+    return shape_for(N, &sh);
+}
+
+blink_status make_unit_roots(float2* d_out, int N, cudaStream_t st) {
+    k_unit_roots<<<(N + 255) / 256, 256, 0, st>>>(d_out, N);
+    BLINK_CUDA(cudaGetLastError());
+    return BLINK_OK;
+}
+
+size_t mixed_h_row(int N) { return ((size_t)N / 2 + 1 + 3) / 4 * 4; }
+
+blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, void* d_H, const float* d_w, int w_mod,
+                          WaveMap wm, int out_first, float* d_img, cudaStream_t st) {
+    Shape sh;
+    const int N = in.N;
+    if (!shape_for(N, &sh)) return set_error(BLINK_ERR_UNSUPPORTED, "image side has a prime factor other than 2, 3, 5");
+    if (n_images <= 0) return BLINK_OK;
+    if (n_images > 65535) return set_error(BLINK_ERR_UNSUPPORTED, "wave of more than 65535 images");
+    const bool crop = in.corr != nullptr;
+    const int ny = crop ? N / 2 : N, y0 = crop ? N / 4 : 0;
+    const bool bf16 = prec == BLINK_PREC_BF16;
+    if (pass == 0) {
+        MixedCol C{};
+        C.N = N;
+        C.half = N / 2;
+        C.cw_log = sh.cw_log;
+        C.nt = sh.nt_c;
+        C.ld = sh.ld_c;
+        C.rad = sh.rad_c;
+        C.n_rad = sh.nrad_c;
+        C.tw = in.tw;
+        C.grid = in.grid;
+        C.vis = in.vis;
+        C.vstride = in.vstride;
+        C.first = in.first;
+        C.F = in.F;
+        C.ent_off = in.ent_off;
+        C.ent = in.ent;
+        C.wt = in.wt;
+        C.H = d_H;
+        C.ldh = (int)mixed_h_row(N);
+        C.y0 = y0;
+        C.ny = ny;
+        const int cw = 1 << sh.cw_log;
+        const dim3 g((N / 2 + 1 + cw - 1) / cw, n_images);
+        if (bf16) {
+            BLINK_TRY(allow_smem(k_mixed_col<__nv_bfloat162>, sh.smem_c));
+            k_mixed_col<__nv_bfloat162><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
+        } else {
+            BLINK_TRY(allow_smem(k_mixed_col<float2>, sh.smem_c));
+            k_mixed_col<float2><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
+        }
+    } else {
+        MixedRow R{};
+        R.N = N;
+        R.M = N / 2;
+        R.nt = sh.nt_r;
+        R.rb = sh.rb;
+        R.ld = sh.ld_r;
+        R.rad = sh.rad_r;
+        R.n_rad = sh.nrad_r;
+        R.tw = in.tw;
+        R.H = d_H;
+        R.ldh = (int)mixed_h_row(N);
+        R.ny = ny;
+        R.has_nyq = in.grid != nullptr;
+        R.wts = d_w;
+        R.w_mod = w_mod;
+        R.wm = wm;
+        R.out_first = out_first;
+        R.x0 = y0;
+        R.nout = ny;
+        R.corr = in.corr;
+        R.img = d_img;
+        if (ny % sh.rb) return set_error(BLINK_ERR_UNSUPPORTED, "row blocking of the mixed-radix row pass");
+        const dim3 g(ny / sh.rb, n_images);
+        if (bf16) {
+            BLINK_TRY(allow_smem(k_mixed_row<__nv_bfloat162>, sh.smem_r));
+            k_mixed_row<__nv_bfloat162><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
+        } else {
+            BLINK_TRY(allow_smem(k_mixed_row<float2>, sh.smem_r));
+            k_mixed_row<float2><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
+        }
+    }
+    BLINK_CUDA(cudaGetLastError());
+    return BLINK_OK;
+}
+
+}  // namespace blink

@@ -221,7 +221,12 @@ blink_status rowpass_n(const float2* tw, const void* H, int ldh, int has_nyq, co
 
 }  // namespace
 
-int col_block_width(int) { return COL_CW; }
+// u columns per gather-gridding CTA: COL_CW, fewer on sides whose column tile would not fit shared memory
+int col_block_width(int N) {
+    int cw = COL_CW;
+    while (cw > 1 && (size_t)N * cw * sizeof(float2) > (size_t)160 * 1024) cw /= 2;
+    return cw;
+}
 
 namespace {
 __device__ float2 unit_root(int k, int n) {     // exp(+2 pi i k / n), FP64 sincospi rounded to FP32

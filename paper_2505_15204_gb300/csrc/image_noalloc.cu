@@ -22,7 +22,8 @@ namespace {
 // result of as many images as fit.  It lives in the module's static device memory, so every GPU that
 // loads the library holds these 16 MiB until the process exits.
 constexpr size_t kScratchBytes = (size_t)16 << 20;
-constexpr size_t kTwiddleBytes = (size_t)tws_total(2048) * sizeof(float2);   // room for the largest side
+// room for the largest table: the side-2048 twiddle set or the 8192 unit roots of the mixed-radix passes
+constexpr size_t kTwiddleBytes = ((size_t)(tws_total(2048) > 8192 ? tws_total(2048) : 8192) * sizeof(float2) + 255) / 256 * 256;
 __device__ __align__(256) unsigned char g_image_scratch[kScratchBytes];
 
 // Device address of g_image_scratch per device.  In host code the array's name stands for a host-side
@@ -62,13 +63,15 @@ extern "C" blink_status blink_image_noalloc(const blink_imaging* imaging, const 
     if (n_images < 0) return set_error(BLINK_ERR_INVALID_ARG, "n_images < 0");
     if (((uintptr_t)d_grid & 7) || ((uintptr_t)d_img & 7))
         return set_error(BLINK_ERR_INVALID_ARG, "d_grid and d_img must be 8-byte aligned");
+    const bool fast = fast_side(N);
     const int ldh = N / 2 + col_block_width(N);
-    const size_t per_img = (size_t)N * ldh * (prec == BLINK_PREC_BF16 ? 4 : 8);
+    const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
+    const size_t per_img = fast ? (size_t)N * ldh * el : (size_t)N * mixed_h_row(N) * el;
     const size_t room = kScratchBytes - kTwiddleBytes;
     if (per_img > room)
         return set_error(BLINK_ERR_UNSUPPORTED,
                          "blink_image_noalloc: one image's column-pass result exceeds the 16 MiB static scratch "
-                         "(largest side: 1024 with FP32 storage, 2048 with BF16 storage)");
+                         "(largest power-of-two side: 1024 with FP32 storage, 2048 with BF16 storage)");
     // the set-up runs on every call, a zero-image call included, so that such a call can serve as the
     // warm-up that commits the scratch before memory is reserved or a capture begins
     void* scratch = nullptr;
@@ -78,6 +81,19 @@ extern "C" blink_status blink_image_noalloc(const blink_imaging* imaging, const 
     float2* tw = static_cast<float2*>(scratch);
     void* H = static_cast<unsigned char*>(scratch) + kTwiddleBytes;
     const int wave = (int)std::min<size_t>((size_t)n_images, room / per_img);
+    if (!fast) {
+        BLINK_TRY(make_unit_roots(tw, N, st));
+        MixedIn in;
+        in.N = N;
+        in.tw = tw;
+        for (int w0 = 0; w0 < n_images; w0 += wave) {
+            const int nw = std::min(wave, n_images - w0);
+            in.grid = reinterpret_cast<const float2*>(d_grid) + (int64_t)w0 * N * (N / 2 + 1);
+            BLINK_TRY(launch_mixed(in, 0, prec, nw, H, nullptr, 1, WaveMap{1, 0, w0, nw}, 0, nullptr, st));
+            BLINK_TRY(launch_mixed(in, 1, prec, nw, H, d_weight, n_images, WaveMap{1, 0, w0, nw}, 0, d_img, st));
+        }
+        return BLINK_OK;
+    }
     BLINK_TRY(make_twiddles(tw, N, st));
     for (int w0 = 0; w0 < n_images; w0 += wave) {
         const int nw = std::min(wave, n_images - w0);

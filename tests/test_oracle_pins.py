@@ -259,8 +259,9 @@ def test_grid_flags_change_weight_sum():
 # transform and image (Eq. 4; Sec. 5.2.4)
 # ----------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n", [4, 8, 16])
+@pytest.mark.parametrize("n", [4, 8, 16, 6, 10, 12, 15, 30, 49, 60])
 def test_fft_matches_direct_dft(n):
+    # powers of two take the radix-2 path, the other sides the mixed-radix recursion (factors 2, 3, 5, and 7 x 7)
     rng = np.random.default_rng(n)
     G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
     a = oracle.ifft2(G)
@@ -268,25 +269,25 @@ def test_fft_matches_direct_dft(n):
     assert np.abs(a - d).max() <= 1e-12 * np.abs(d).max()
 
 
-def test_fft_matches_numpy_library():
+@pytest.mark.parametrize("n", [128, 150, 1200])
+def test_fft_matches_numpy_library(n):
     rng = np.random.default_rng(3)
-    n = 128
     G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
     a = oracle.ifft2(G)
     ref = np.fft.ifft2(G) * n * n
     assert np.abs(a - ref).max() <= 1e-11 * np.abs(ref).max()
 
 
-def test_fft_parseval():
+@pytest.mark.parametrize("n", [64, 90])
+def test_fft_parseval(n):
     rng = np.random.default_rng(4)
-    n = 64
     G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
     a = oracle.ifft2(G)
     assert math.isclose((np.abs(a) ** 2).sum(), n * n * (np.abs(G) ** 2).sum(), rel_tol=1e-12)
 
 
-def test_fft_delta_and_single_cell_closed_forms():
-    n = 32
+@pytest.mark.parametrize("n", [32, 120])
+def test_fft_delta_and_single_cell_closed_forms(n):
     G = np.zeros((n, n), complex)
     G[0, 0] = 2.5 - 1j
     assert np.allclose(oracle.ifft2(G), 2.5 - 1j, rtol=0, atol=1e-13)
@@ -300,9 +301,25 @@ def test_fft_delta_and_single_cell_closed_forms():
     assert np.abs(oracle.ifft2(G) - want).max() < 1e-12
 
 
-def test_fft_rejects_non_power_of_two():
+def test_fft_rejects_an_empty_side():
     with pytest.raises(ValueError):
-        oracle.ifft2(np.zeros((12, 12), complex))
+        oracle.ifft2(np.zeros((0, 0), complex))
+
+
+@pytest.mark.parametrize("n", [64, 60])
+def test_image_pixels_equal_the_whole_image(n):
+    # the direct per-pixel sum over a sparse grid's cells against the transform and shift of the whole grid
+    rng = np.random.default_rng(n)
+    G = np.zeros((n, n), complex)
+    for _ in range(40):
+        u, v = rng.integers(0, n, 2)
+        z = complex(rng.standard_normal(), rng.standard_normal())
+        G[v, u] += z
+        G[-v % n, -u % n] += np.conj(z)
+    img, _ = oracle.image(oracle.ifft2(G), 3.0)
+    yx = np.array([(y, x) for y in range(n) for x in range(n)], dtype=np.int32)
+    got = oracle.image_pixels(G, 3.0, yx).reshape(n, n)
+    assert np.abs(got - img).max() <= 1e-12 * np.abs(img).max()
 
 
 def test_image_shift_puts_phase_centre_in_middle_pixel():
@@ -331,6 +348,18 @@ def test_point_source_at_phase_centre_gives_flux_in_centre_pixel():
     img = out["images"][0]
     assert math.isclose(img[32, 32], 5.0, rel_tol=1e-12)
     assert img.max() == img[32, 32]
+    assert out["max_im"][0] < 1e-12
+
+
+@pytest.mark.parametrize("n", [96, 1200])
+def test_point_source_at_phase_centre_on_a_mixed_radix_side(n):
+    # the same closed form on sides that are not powers of two (the paper's 1200 x 1200 images)
+    w = bs.build_workload("tiny")
+    v = bs.constant_voltages(10, 1, 128, 2, 1)
+    out = oracle.pipeline(v, w["enu"], w["freqs"], 10, 1, n)
+    img = out["images"][0]
+    assert math.isclose(img[n // 2, n // 2], 5.0, rel_tol=1e-12)
+    assert img.max() == img[n // 2, n // 2]
     assert out["max_im"][0] < 1e-12
 
 

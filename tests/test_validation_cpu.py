@@ -67,9 +67,12 @@ def test_correlate_buffers_and_arith():
 
 
 @pytest.mark.parametrize("imaging,status,text", [
-    (B.Imaging(100), B.BLINK_ERR_UNSUPPORTED, "power of two in [64, 2048]"),
-    (B.Imaging(32), B.BLINK_ERR_UNSUPPORTED, "power of two in [64, 2048]"),
-    (B.Imaging(4096), B.BLINK_ERR_UNSUPPORTED, "power of two in [64, 2048]"),
+    (B.Imaging(98), B.BLINK_ERR_UNSUPPORTED, "no prime factor above 5"),         # 2 x 7^2
+    (B.Imaging(1202), B.BLINK_ERR_UNSUPPORTED, "no prime factor above 5"),       # 2 x 601
+    (B.Imaging(75), B.BLINK_ERR_UNSUPPORTED, "even, in [64, 8192]"),
+    (B.Imaging(32), B.BLINK_ERR_UNSUPPORTED, "even, in [64, 8192]"),
+    (B.Imaging(16384), B.BLINK_ERR_UNSUPPORTED, "even, in [64, 8192]"),
+    (B.Imaging(8640), B.BLINK_ERR_UNSUPPORTED, "even, in [64, 8192]"),
     (B.Imaging(64, pol=5), B.BLINK_ERR_INVALID_ARG, "imaging.pol"),
     (B.Imaging(64, precision=9), B.BLINK_ERR_INVALID_ARG, "imaging.precision"),
     (B.Imaging(64, cell_lambda=float("inf")), B.BLINK_ERR_INVALID_ARG, "cell_lambda is not finite"),
@@ -99,7 +102,7 @@ def test_pipeline_sets_validate_every_set_and_the_capacity():
     _expect(B.BLINK_ERR_INVALID_ARG, "no sets", fn, None, a, o, [], 0, PTR, PTR, cap)
     for s in (B.Set(3, 2, im), B.Set(0, 1, im), B.Set(-2, 2, im), B.Set(0, 0, im)):
         _expect(B.BLINK_ERR_INVALID_ARG, "set channel range", fn, None, a, o, [s], 0, PTR, PTR, cap)
-    _expect(B.BLINK_ERR_UNSUPPORTED, "power of two", fn, None, a, o, [B.Set(0, 2, B.Imaging(96))], 0, PTR, PTR, cap)
+    _expect(B.BLINK_ERR_UNSUPPORTED, "no prime factor", fn, None, a, o, [B.Set(0, 2, B.Imaging(98))], 0, PTR, PTR, cap)
     sets = [B.Set(0, 2, B.Imaging(64)), B.Set(2, 2, B.Imaging(128))]
     need = 2 * 1 * 64 * 64 + 2 * 1 * 128 * 128  # packed per set: T * F_set * N_set^2
     _expect(B.BLINK_ERR_INVALID_ARG, "img_capacity", fn, None, a, o, sets, 0, PTR, PTR, need - 1)
@@ -149,7 +152,8 @@ def test_dedisperse_validates_delays_before_any_device_work():
     _expect(B.BLINK_ERR_INVALID_ARG, "delays must be >= 0", fn, None, PTR, 4, 3, 64, [0, -1, 0], PTR)
     _expect(B.BLINK_ERR_INVALID_ARG, "max(delays) must be < n_int", fn, None, PTR, 4, 3, 64, [0, 4, 0], PTR)
     _expect(B.BLINK_ERR_INVALID_ARG, "n_int and n_chan must be >= 1", fn, None, PTR, 0, 3, 64, [0, 0, 0], PTR)
-    _expect(B.BLINK_ERR_INVALID_ARG, "power of two", fn, None, PTR, 4, 3, 100, [0, 0, 0], PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "even, in [64, 8192]", fn, None, PTR, 4, 3, 101, [0, 0, 0], PTR)
+    _expect(*NO_CTX, fn, None, PTR, 4, 3, 1200, [0, 0, 0], PTR)
     _expect(B.BLINK_ERR_INVALID_ARG, "16-byte aligned", fn, None, PTR + 8, 4, 3, 64, [0, 0, 0], PTR)
     _expect(*NO_CTX, fn, None, PTR, 4, 3, 64, [0, 3, 1], PTR)
     with pytest.raises(ValueError):
@@ -172,8 +176,9 @@ def test_convolution_kernel_options():
             PTR, PTR)
     _expect(B.BLINK_ERR_INVALID_ARG, "imaging.support", B.blink_pipeline, None, a, o, B.Imaging(64, support=-1), 0, 0,
             PTR, PTR)
-    _expect(B.BLINK_ERR_UNSUPPORTED, "at most 1024", B.blink_pipeline, None, a, o, B.Imaging(2048, support=4), 0, 0,
+    _expect(B.BLINK_ERR_UNSUPPORTED, "at most 4096", B.blink_pipeline, None, a, o, B.Imaging(8192, support=4), 0, 0,
             PTR, PTR)
+    _expect(*NO_CTX, B.blink_pipeline, None, a, o, B.Imaging(1200, support=6), 0, B.BLINK_MODE_BATCHED, PTR, PTR)
     k = B.Imaging(64, support=6)
     _expect(*NO_CTX, B.blink_pipeline, None, a, o, k, 0, B.BLINK_MODE_BATCHED, PTR, PTR)
     _expect(*NO_CTX, B.blink_pipeline, None, a, o, B.Imaging(64, support=1), 0, B.BLINK_MODE_PLAIN, PTR, PTR)
@@ -211,3 +216,20 @@ def test_tracking_pointings():
     _expect(*NO_CTX, B.blink_pipeline_tracking, None, a, o, k, np.array([(0.1, 0.2), (0.3, -0.1)]), 1, PTR, PTR)
     with pytest.raises(ValueError):
         B.blink_pipeline_tracking(None, a, o, k, np.zeros(4), 1, PTR, PTR)
+
+
+@pytest.mark.parametrize("n", [96, 150, 1200, 2400, 4096, 8192])
+def test_mixed_radix_sides_reach_the_context_check(n):
+    a, o, k = B.Array(_enu()), _obs(), B.Imaging(n)
+    for mode in (B.BLINK_MODE_BATCHED, B.BLINK_MODE_PLAIN):
+        _expect(*NO_CTX, B.blink_pipeline, None, a, o, k, 0, mode, PTR, PTR)
+    _expect(*NO_CTX, B.blink_image, None, k, PTR, 1, PTR, PTR)
+    _expect(*NO_CTX, B.blink_grid, None, a, o, k, PTR, 0, 1, PTR)
+    _expect(*NO_CTX, B.blink_cells, None, a, o, k, PTR)
+
+
+def test_image_noalloc_scratch_limit_on_mixed_radix_sides():
+    fn = B.blink_image_noalloc
+    # 2400 x 1204 FP32 pairs exceed the 16 MiB scratch; BF16 pairs fit.  Both are rejected or accepted before
+    # any device work: the accepted call stops at the scratch look-up, which fails without a device.
+    _expect(B.BLINK_ERR_UNSUPPORTED, "16 MiB static scratch", fn, B.Imaging(2400), PTR, 1, PTR, PTR)
