@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--samples", type=int, default=0, help="voltage samples per step (default: the 50 ms chunk)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "coarse", "precision", "uneven", "fullband"])
+    ap.add_argument("--n-pix", type=int, default=0,
+                    help="image side for every channel set instead of the workload's (e.g. 1200, 8192)")
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (default: every host core)")
     ap.add_argument("--dedisperse", action="store_true",
                     help="also time blink_dedisperse on the step's images (a DM sweeping half the chunk)")
@@ -139,12 +141,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def fast_side(n: int) -> bool:
+    """Sides the side-specialised kernels cover (the others run the two mixed-radix passes)."""
+    return 64 <= n <= 2048 and n & (n - 1) == 0
+
+
 def stage_bytes(stage: int, n_tiles: int, n_pix: int, K: int) -> float:
     """Algorithmic bytes per image of each pipeline stage (what the step must move, not what it moves)."""
     B = n_tiles * (n_tiles + 1) // 2
     half = n_pix * (n_pix // 2)                       # complex entries of the u >= 0 half plane (no Nyquist)
     if stage == 0:                                    # voltages in, Stokes-I visibilities out
         return K * 2 * n_tiles + 8 * B
+    if not fast_side(n_pix):                          # mixed-radix passes: the column results cannot stay on
+        h = n_pix * (n_pix // 2 + 1)                  # chip, so each pass moves them once (to L2 or DRAM)
+        return 8 * B + 8 * h if stage == 1 else 8 * h + 4 * n_pix * n_pix
     if stage == 1:                                    # visibilities in, images out (intermediate on chip / L2)
         return 8 * B + 4 * n_pix * n_pix
     if stage == 3:                                    # fused: the image's voltage share in, the image out
@@ -155,6 +165,10 @@ def stage_bytes(stage: int, n_tiles: int, n_pix: int, K: int) -> float:
 STAGE_NAMES = ["correlate", "grid + 2D FFT", "row c2r FFT", "correlate + grid + 2D FFT (fused)"]
 STAGE_KERNELS = ["k_corr_tc", "k_fft_persistent", "k_rowpass", "k_fft_persistent"]
 STAGE_SOURCES = ["correlate_tc.cu", "fft_persistent.cu", "grid_fft.cu", "fft_persistent.cu"]
+# on mixed-radix sides: the gather-gridding column pass and the complex-to-real row pass
+MIXED_NAMES = ["correlate", "grid + column FFT (mixed radix)", "row c2r FFT (mixed radix)", None]
+MIXED_KERNELS = ["k_corr_tc", "k_mixed_col", "k_mixed_row", None]
+MIXED_SOURCES = ["correlate_tc.cu", "fft_mixed.cu", "fft_mixed.cu", None]
 
 
 def source_hash(name: str) -> str:
@@ -183,18 +197,19 @@ def traffic_for(kernel: str, source: str, shape=None):
 # the reference arm: the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------------------------------
 
-def workload_label(name: str, w) -> str:
+def workload_label(name: str, w, n_pix=0) -> str:
     if name == "fullband":
+        side = n_pix or 512
         return ("fullband: 50 ms chunk, 144 tiles x 2 pol, 768 x 40 kHz (10 kHz averaged by 4), "
-                "50 x 1 ms (K = 40), 512^2 Stokes-I images")
-    return f"{name}: {w.description}"
+                f"50 x 1 ms (K = 40), {side}^2 Stokes-I images")
+    return f"{name}: {w.description}" + (f"; imaged at {n_pix}^2" if n_pix else "")
 
 
 def bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes):
     """The workload description both arms print (the reference arm times a sample of the same workload)."""
     L2_BYTES = 129 * 2 ** 20
     small = in_bytes + out_bytes < 2 * L2_BYTES
-    return {"workload": workload_label(args.workload, w),
+    return {"workload": workload_label(args.workload, w, args.n_pix), "n_pix": args.n_pix or None,
             "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
             "mode": args.mode, "precision": args.precision, "gains": bool(args.gains), "fused": bool(args.fused),
             "jones": bool(args.jones), "support": args.support, "pointing": list(args.pointing),
@@ -204,13 +219,14 @@ def bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes):
                    "no flush")}
 
 
-def image_sets(inp, w, ns):
-    """(set, first image, images, side) of every channel set of the workload, images packed per set."""
+def image_sets(inp, w, ns, n_pix=0):
+    """(set, first image, images, side) of every channel set of the workload, images packed per set;
+    n_pix > 0 images every set at that side instead of the workload's."""
     T = ns // w.samples_per_int
     out, first = [], 0
     for st in inp["sets"]:
         n = T * (st.n_fine // w.chan_avg)
-        out.append((st, first, n, st.n_pix))
+        out.append((st, first, n, n_pix or st.n_pix))
         first += n
     return out
 
@@ -274,7 +290,7 @@ def run_reference(args, world, rank):
     ns = args.samples or w.samples_per_chunk
     chunk = min(4, w.n_chunks - 1)
     inp = bs.build_workload(args.workload, chunk=chunk, workers=min(16, os.cpu_count() or 1), n_samples=ns)
-    sets = image_sets(inp, w, ns)
+    sets = image_sets(inp, w, ns, args.n_pix)
     n_total = sum(c for _, _, c, _ in sets)
     img_floats = sum(c * side * side for _, _, c, side in sets)
     config = bench_config(args, w, ns, chunk, n_total, int(inp["volt"].size), img_floats * 4)
@@ -334,7 +350,7 @@ def run_ours(args, world, rank, local):
     from paper_2505_15204_gb300 import blink as B
 
     n_tiles, K = w.n_tiles, w.k
-    sets = image_sets(inp, w, ns)
+    sets = image_sets(inp, w, ns, args.n_pix)
     multi = len(sets) > 1
     n_pix = sets[0][3]
     n_img = sum(c for _, _, c, _ in sets)
@@ -433,13 +449,16 @@ def run_ours(args, world, rank, local):
         per_launch = bytes_total / stage_n[dom]
         avg_s = stage_ms[dom] / 1e3 / stage_n[dom]
         ach = per_launch / avg_s / 1e9
-        kern = STAGE_KERNELS[dom] if (dom or arith == B.BLINK_CORR_FP8) else "k_corr_fp32"
-        src = STAGE_SOURCES[dom] if (dom or arith == B.BLINK_CORR_FP8) else "correlate.cu"
+        mixed = not fast_side(sets[0][3] * (2 if args.support else 1))
+        names, kerns, srcs = (MIXED_NAMES, MIXED_KERNELS, MIXED_SOURCES) if mixed else (STAGE_NAMES, STAGE_KERNELS,
+                                                                                          STAGE_SOURCES)
+        kern = kerns[dom] if (dom or arith == B.BLINK_CORR_FP8) else "k_corr_fp32"
+        src = srcs[dom] if (dom or arith == B.BLINK_CORR_FP8) else "correlate.cu"
         # the committed DRAM counters are those of the nearest-cell kernel: none for the kernel form
         shape = B.blink_tuned_shape(ctx)
         traffic = traffic_for(kern, src, shape) if not args.support else None
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": traffic, "kernel": kern, "stage": STAGE_NAMES[dom],
+                "traffic": traffic, "kernel": kern, "stage": names[dom],
                 "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3, "peak_kind": f"{peak_kind} hbm_gbs",
                 "tuned_shape": {"ring": shape[0], "lag": shape[1], "ctas_per_sm": shape[2]}}
     stages = {STAGE_NAMES[s]: {"ms_per_step": stage_ms[s] / args.steps, "launches_per_step": stage_n[s] / args.steps,

@@ -1,5 +1,6 @@
 // C ABI entry points, argument validation, plans and workspace.
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -569,6 +570,23 @@ blink_status upload_gains(blink_context* ctx, const blink_array* a, int F, cudaS
 }
 
 // The twiddle set of side N (see tws_total), made on the device on first use and kept in the context.
+blink_status kernel_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, size_t>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& d : done)
+        if (d.first == fn) {
+            if (d.second >= bytes) return BLINK_OK;
+            BLINK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+            d.second = bytes;
+            return BLINK_OK;
+        }
+    if (bytes > 48 * 1024) BLINK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    done.emplace_back(fn, bytes);
+    return BLINK_OK;
+}
+
 blink_status twiddles(blink_context* ctx, int N, float2** out) {
     if (!fast_side(N)) {
         for (auto& t : ctx->tw_any)

@@ -126,6 +126,10 @@ blink_status get_plan(blink_context* ctx, const blink_array* a, const blink_obs*
                       bool need_gather, cudaStream_t st, Plan** out);
 blink_status workspace(blink_context* ctx, int slot, size_t bytes, void** out);
 blink_status twiddles(blink_context* ctx, int N, float2** out);
+// Raise kernel `fn`'s dynamic shared-memory limit to `bytes` and prefer the largest carve-out, the first
+// time a launch needs more than before; remembered per kernel (instances of one template share a type, so
+// a cache keyed by type would mix them up).
+blink_status kernel_smem(const void* fn, size_t bytes);
 
 // Brackets one stage launch with profiling events when profiling is on.
 struct StageTimer {

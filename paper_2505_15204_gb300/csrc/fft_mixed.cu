@@ -219,16 +219,6 @@ bool factor(int n, uint64_t* rad, int* n_rad) {
 
 int stride_for(int n) { return (pd(n - 1) + 1 + 15) / 16 * 16 + 1; }     // odd: columns spread over banks
 
-template <typename K>
-blink_status allow_smem(K kernel, size_t bytes) {
-    static size_t done = 0;
-    if (bytes > done) {
-        BLINK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        done = bytes;
-    }
-    return BLINK_OK;
-}
-
 struct Shape {
     uint64_t rad_c = 0, rad_r = 0;
     int nrad_c = 0, nrad_r = 0, nt_c = 0, nt_r = 0, cw_log = 0, rb = 1, ld_c = 0, ld_r = 0;   // threads per transform, ...
@@ -306,10 +296,10 @@ blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, v
         const int cw = 1 << sh.cw_log;
         const dim3 g((N / 2 + 1 + cw - 1) / cw, n_images);
         if (bf16) {
-            BLINK_TRY(allow_smem(k_mixed_col<__nv_bfloat162>, sh.smem_c));
+            BLINK_TRY(kernel_smem((const void*)k_mixed_col<__nv_bfloat162>, sh.smem_c));
             k_mixed_col<__nv_bfloat162><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
         } else {
-            BLINK_TRY(allow_smem(k_mixed_col<float2>, sh.smem_c));
+            BLINK_TRY(kernel_smem((const void*)k_mixed_col<float2>, sh.smem_c));
             k_mixed_col<float2><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
         }
     } else {
@@ -337,10 +327,10 @@ blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, v
         if (ny % sh.rb) return set_error(BLINK_ERR_UNSUPPORTED, "row blocking of the mixed-radix row pass");
         const dim3 g(ny / sh.rb, n_images);
         if (bf16) {
-            BLINK_TRY(allow_smem(k_mixed_row<__nv_bfloat162>, sh.smem_r));
+            BLINK_TRY(kernel_smem((const void*)k_mixed_row<__nv_bfloat162>, sh.smem_r));
             k_mixed_row<__nv_bfloat162><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
         } else {
-            BLINK_TRY(allow_smem(k_mixed_row<float2>, sh.smem_r));
+            BLINK_TRY(kernel_smem((const void*)k_mixed_row<float2>, sh.smem_r));
             k_mixed_row<float2><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
         }
     }

@@ -166,14 +166,9 @@ k_rowpass(const T* __restrict__ H, int ldh, int has_nyq, const float* __restrict
     fft_run<M, 1, 1, 32, 1, 0, false, true, true, float2, decltype(store), true>(dst, stw, lane, store);
 }
 
-// Raise a kernel's dynamic shared-memory limit and prefer the largest carve-out, once per kernel.
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
-    static size_t done = (size_t)-1;
-    if (done != (size_t)-1 && done >= bytes) return;
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    done = bytes;
+    kernel_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 constexpr int col_threads(int) { return 32 * COL_CW; }

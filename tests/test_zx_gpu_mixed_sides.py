@@ -38,6 +38,18 @@ def test_image_stage_on_mixed_sides(B, ctx, n):
     assert_image_close(img[0].cpu().numpy(), ref["images"][0], n, rms_tol=1e-5)
 
 
+def test_image_stage_sides_in_descending_order(B, ctx):
+    # the shared-memory limit is raised per kernel instance: a larger side first must not leave a smaller
+    # side's instance (same signature) without its own limit
+    for n in (2048, 1024, 2400, 1200):
+        g, ref = _grids(n)
+        img = torch.full((1, n, n), float("nan"), dtype=torch.float32, device="cuda")
+        wt = torch.tensor([ref["W"][0]], dtype=torch.float32, device="cuda")
+        B.blink_image(ctx, B.Imaging(n), dev(g), 1, wt, img)
+        B.blink_sync(ctx)
+        assert_image_close(img[0].cpu().numpy(), ref["images"][0], n, rms_tol=1e-5)
+
+
 def test_image_stage_nyquist_column_on_a_mixed_side(B, ctx):
     n = 120
     G = np.zeros((n, n), complex)
