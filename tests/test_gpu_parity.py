@@ -339,7 +339,7 @@ def test_invalid_arguments_are_rejected_before_launch(B, ctx, bad):
     img = torch.zeros((1, 256, 256), device="cuda")
     d = dev(volt)
     if bad == "n_pix":
-        im = B.Imaging(300)
+        im = B.Imaging(302)                 # 2 x 151: a prime factor above 5
     elif bad == "chan_avg":
         obs = B.Obs(freqs, 2, 10, 10)
     elif bad == "n_samples":
