@@ -8,7 +8,7 @@
 //   row pass     one CTA per `rb` image rows: the complex-to-real transform along u, formed from an
 //                N/2-point complex FFT of the paired half spectrum, scaled by 1/W (and, with a convolution
 //                kernel, cropped to the central half and grid-corrected).
-// The FFT is a Stockham autosort iteration over the factors of the length (radices 4, 2, 3, 5) between two
+// The FFT is a Stockham autosort iteration over the factors of the length (radices 16, 8, 4, 2, 3, 5) between two
 // shared-memory buffers per transform: a thread reads a butterfly's inputs, transforms them in registers
 // and writes the outputs to the other buffer in the next stage's order, so only one butterfly is live in
 // registers at a time and blocks of many threads stay resident.
@@ -24,46 +24,81 @@ constexpr int kMaxThreads = 1024;
 
 __host__ __device__ __forceinline__ int pd(int i) { return i + (i >> 5); }     // one pad slot per 32 points
 
+// v[p] *= w^p for 0 < p < R, with w^1, w^2, w^4, w^8 read from the table (tw[p e], each p e < n) and the
+// other powers formed as products of at most three of them, so every factor carries the rounding of a few
+// multiplications; only a handful of powers is live at a time.
+template <int R>
+__device__ __forceinline__ void twiddle(float2* v, const float2* __restrict__ tw, int e) {
+    const float2 w1 = __ldg(tw + e);
+    v[1] = cmul(v[1], w1);
+    if (R <= 2) return;
+    const float2 w2 = __ldg(tw + 2 * e);
+    v[2] = cmul(v[2], w2);
+    if (R <= 3) return;
+    const float2 w3 = cmul(w1, w2);
+    v[3] = cmul(v[3], w3);
+    if (R <= 4) return;
+    const float2 w4 = __ldg(tw + 4 * e);
+    v[4] = cmul(v[4], w4);
+    if (R <= 5) return;
+    v[5] = cmul(v[5], cmul(w4, w1));
+    v[6] = cmul(v[6], cmul(w4, w2));
+    v[7] = cmul(v[7], cmul(w4, w3));
+    if (R <= 8) return;
+    const float2 w8 = __ldg(tw + 8 * e), w12 = cmul(w8, w4);
+    v[8] = cmul(v[8], w8);
+    v[9] = cmul(v[9], cmul(w8, w1));
+    v[10] = cmul(v[10], cmul(w8, w2));
+    v[11] = cmul(v[11], cmul(w8, w3));
+    v[12] = cmul(v[12], w12);
+    v[13] = cmul(v[13], cmul(w12, w1));
+    v[14] = cmul(v[14], cmul(w12, w2));
+    v[15] = cmul(v[15], cmul(w12, w3));
+}
+
 // One Stockham stage of radix R of an n-point transform after stages whose radices multiply to L, from
 // buffer `in` to buffer `out`.  Point addresses: before the stage, Y(j, k1) (j < n/L, k1 < L) sits at
 // j L + k1 and holds the L-point transform of the points j + (n/L) t; butterfly b = j' L + k1 (j' < n/(LR))
 // reads Y(j' + m p, k1) for p < R (at b + p n/R, m = n/(LR)), multiplies input p by w_n^(p k1 m), transforms
 // over p and writes output q to Y'(j', k1 + L q) at j' L R + k1 + L q.  tw[k * tws] = exp(+2 pi i k / n).
+// A thread takes butterflies t, t + nt, ...: (j', k1) advance by (nt / L, nt % L) with a carry, so the
+// stage divides once per thread, not once per butterfly.
 template <int R>
 __device__ __forceinline__ void stage(const float2* in, float2* out, int n, int L, const float2* __restrict__ tw,
                                       int tws, int t, int nt) {
     const int nb = n / R, m = nb / L;
+    const int dj = nt / L, dk = nt - dj * L;
+    int j = t / L, k1 = t - j * L;
     for (int b = t; b < nb; b += nt) {
-        const int j = b / L, k1 = b - j * L;
         float2 v[R];
 #pragma unroll
         for (int p = 0; p < R; p++) v[p] = in[pd(b + p * nb)];
-        if (L > 1) {
-            const float2 w = __ldg(tw + (int64_t)k1 * m * tws);
-            float2 wp = w;
-#pragma unroll
-            for (int p = 1; p < R; p++) {
-                v[p] = cmul(v[p], wp);
-                if (p + 1 < R) wp = cmul(wp, w);
-            }
-        }
+        if (L > 1) twiddle<R>(v, tw, k1 * m * tws);
         idft<R>(v);
         const int d = j * L * R + k1;
 #pragma unroll
         for (int q = 0; q < R; q++) out[pd(d + q * L)] = v[q];
+        j += dj;
+        k1 += dk;
+        if (k1 >= L) {
+            k1 -= L;
+            j++;
+        }
     }
     __syncthreads();
 }
 
 // The whole n-point transform of a[pd(0 .. n-1)] by the threads t < nt of each transform, alternating
-// between the buffers a and b; radices packed 4 bits per stage, first stage lowest.  Every thread of the
+// between the buffers a and b; radices packed 5 bits per stage, first stage lowest.  Every thread of the
 // block runs the same stages.  Returns the buffer that holds the result.
 __device__ __forceinline__ float2* fft_any(float2* a, float2* b, int n, uint64_t rad, int n_rad,
                                            const float2* __restrict__ tw, int tws, int t, int nt) {
     int L = 1;
     for (int k = 0; k < n_rad; k++) {
-        const int R = (int)((rad >> (4 * k)) & 15u);
+        const int R = (int)((rad >> (5 * k)) & 31u);
         switch (R) {
+            case 16: stage<16>(a, b, n, L, tw, tws, t, nt); break;
+            case 8: stage<8>(a, b, n, L, tw, tws, t, nt); break;
             case 4: stage<4>(a, b, n, L, tw, tws, t, nt); break;
             case 2: stage<2>(a, b, n, L, tw, tws, t, nt); break;
             case 3: stage<3>(a, b, n, L, tw, tws, t, nt); break;
@@ -106,7 +141,7 @@ struct MixedCol {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_mixed_col(const MixedCol P) {
+__global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_col(const MixedCol P) {
     extern __shared__ float2 s[];          // [cw][ld] transform inputs, then [cw][ld] the second buffers
     const int img = blockIdx.y, tid = threadIdx.x, nthr = blockDim.x;
     const int cw = 1 << P.cw_log, u0 = blockIdx.x * cw;
@@ -171,7 +206,7 @@ struct MixedRow {
 // sequence x is x[2m] = Re y[m], x[2m+1] = Im y[m] with y the M-point inverse transform of
 // Y[k] = (Z[k] + conj Z[M-k]) + i (Z[k] - conj Z[M-k]) exp(+2 pi i k / N)  (any M, odd included).
 template <typename T>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_mixed_row(const MixedRow P) {
+__global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_row(const MixedRow P) {
     extern __shared__ float2 s[];          // [rb][ld] transform inputs, then [rb][ld] the second buffers
     const int img = blockIdx.y, tid = threadIdx.x;
     const int r = tid / P.nt, t = tid - r * P.nt, y = blockIdx.x * P.rb + r;
@@ -192,6 +227,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_mixed_row(const MixedRow P) 
     float scale = 1.0f / (w > 0.f ? w : 1.f);
     if (P.corr) scale *= P.corr[y];
     float* out = P.img + ((int64_t)(id - P.out_first) * P.ny + y) * P.nout;
+    if (!P.corr && (P.nout & 3) == 0 && (reinterpret_cast<uintptr_t>(P.img) & 15) == 0) {
+        // whole rows (x0 = 0) on a 16-byte aligned output: four pixels, two results y[m], per 16-byte store
+        float4* o4 = reinterpret_cast<float4*>(out);
+        for (int q = t; q < P.nout / 4; q += P.nt) {
+            const float2 a = res[pd(2 * q)], b = res[pd(2 * q + 1)];
+            o4[q] = make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
+        }
+        return;
+    }
     for (int x = t; x < P.nout; x += P.nt) {
         const int X = P.x0 + x;
         const float2 z = res[pd(X >> 1)];
@@ -200,18 +244,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_mixed_row(const MixedRow P) 
     }
 }
 
-// radices of n in stage order (4s, then 2, then 3s and 5s), packed 4 bits each; false if n has another factor
+// radices of n in stage order (16s, then one 8, 4 or 2, then 3s and 5s), packed 5 bits each; false if n has
+// another prime factor
 bool factor(int n, uint64_t* rad, int* n_rad) {
     int k = 0;
     uint64_t r = 0;
     auto push = [&](int x) {
-        r |= (uint64_t)x << (4 * k);
+        r |= (uint64_t)x << (5 * k);
         k++;
     };
-    while (n % 4 == 0 && k < 15) { push(4); n /= 4; }
-    while (n % 2 == 0 && k < 15) { push(2); n /= 2; }
-    while (n % 3 == 0 && k < 15) { push(3); n /= 3; }
-    while (n % 5 == 0 && k < 15) { push(5); n /= 5; }
+    while (n % 16 == 0 && k < 12) { push(16); n /= 16; }
+    for (int x : {8, 4, 2})
+        if (n % x == 0 && k < 12) { push(x); n /= x; }
+    while (n % 3 == 0 && k < 12) { push(3); n /= 3; }
+    while (n % 5 == 0 && k < 12) { push(5); n /= 5; }
     *rad = r;
     *n_rad = k;
     return n == 1;
@@ -231,18 +277,26 @@ bool shape_for(int N, Shape* sh) {
     sh->ld_c = stride_for(N);
     sh->ld_r = stride_for(N / 2);
     const size_t col = 2 * (size_t)sh->ld_c * sizeof(float2), row = 2 * (size_t)sh->ld_r * sizeof(float2);
-    // columns per CTA: up to 8 within 100 KiB of shared memory (two CTAs per SM), at least one
-    int cw_log = 3;
-    while (cw_log > 0 && (col << cw_log) > (size_t)100 * 1024) cw_log--;
+    // The passes are bound by instruction issue, not by occupancy: measured sweeps over threads per
+    // transform and transforms per CTA (sides 1200 and 8192) favoured few threads per transform (about one
+    // per 16 points for columns, one per 16 of the half-length row transform's, at least 64) and CTAs of
+    // about 128 threads.
+    auto pow2_floor = [](int x) {
+        int p = 1;
+        while (2 * p <= x) p *= 2;
+        return p;
+    };
+    sh->nt_c = std::max(64, std::min(kMaxThreads / 2, pow2_floor(N / 16)));
+    int cw_log = 0;
+    while (cw_log < 3 && (sh->nt_c << (cw_log + 1)) <= 128 && (col << (cw_log + 1)) <= (size_t)100 * 1024) cw_log++;
     sh->cw_log = cw_log;
     sh->smem_c = col << cw_log;
-    sh->nt_c = std::max(32, std::min(kMaxThreads, ((N >= 4096 ? 1024 : 512) >> cw_log) / 32 * 32));
-    // rows per CTA: up to 8 within 100 KiB, dividing N/2 (so both N rows and, with a kernel, N/2 rows)
-    int rb = 8;
-    while (rb > 1 && ((N / 2) % rb || rb * row > (size_t)100 * 1024)) rb /= 2;
+    sh->nt_r = std::max(64, std::min(kMaxThreads / 2, pow2_floor(N / 32)));     // side 8192: 256 beat 512
+    int rb = 1;
+    while (2 * rb <= 8 && 2 * rb * sh->nt_r <= 128 && (N / 2) % (2 * rb) == 0 && 2 * rb * row <= (size_t)100 * 1024)
+        rb *= 2;
     sh->rb = rb;
     sh->smem_r = row * rb;
-    sh->nt_r = std::max(32, std::min(kMaxThreads, ((N >= 8192 ? 1024 : 512) / rb) / 32 * 32));
     return sh->smem_c <= (size_t)227 * 1024 && sh->smem_r <= (size_t)227 * 1024;
 }
 
