@@ -292,6 +292,25 @@ blink_status blink_pipeline_tracking(blink_context* ctx, const blink_array* arra
                                      const uint8_t* d_volt, float* d_img, void* stream);
 
 /*
+ * Averaged dirty images (the paper's long-exposure and band-averaged products: Sec. 6.1 averages the 1 s
+ * images of every fine channel over the whole time range and band into one image, Sec. 6.2 the 20 ms
+ * images of each time bin over the band): output (tau', f') is the mean of the blink_pipeline images of integrations
+ * [tau' t_avg, (tau' + 1) t_avg) and output channels [f' f_avg, (f' + 1) f_avg), written to d_img as float
+ * [T / t_avg][F / f_avg][N][N].  t_avg = T, f_avg = F gives one long-exposure image; t_avg = 1, f_avg = F the
+ * band average of each integration.
+ * The averages are formed before the transform, not after it: the mean over integrations is the image of
+ * the summed correlations (one pointing per call, so the cells do not change within it; the integration
+ * becomes t_avg samples_per_int long and its limits apply), and the mean over channels is one transform of
+ * the sum of the channels' grids, each divided by its own W.  So an output costs one 2D transform however
+ * many images it averages.  Every side the imaging descriptor allows, with or without a gridding kernel, runs
+ * the mixed-radix passes here.  Equal to the mean of the individual images up to FP32 rounding.
+ *   t_avg, f_avg  >= 1, dividing T and F; else BLINK_ERR_INVALID_ARG before any launch.
+ */
+blink_status blink_pipeline_averaged(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                     const blink_imaging* imaging, int32_t arith, int32_t t_avg, int32_t f_avg,
+                                     const uint8_t* d_volt, float* d_img, void* stream);
+
+/*
  * blink_image without any device allocation (the paper has no counterpart; this is a library service).
  * Callers that cannot allocate device memory while they image - a real-time instrument pipeline that
  * reserves all device memory when an observation starts, or an application whose device memory belongs

@@ -40,6 +40,7 @@ ENTRY_POINTS = (
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
     "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets", "blink_dedisperse",
     "blink_set_wait_budget", "blink_set_fused", "blink_tuned_shape", "blink_pipeline_tracking",
+    "blink_pipeline_averaged",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
@@ -101,6 +102,7 @@ def _load():
         "blink_set_fused": (S, [P, I32]),
         "blink_tuned_shape": (S, [P, P]),
         "blink_pipeline_tracking": (S, [P, P, P, P, P, I32, P, P, P]),
+        "blink_pipeline_averaged": (S, [P, P, P, P, I32, I32, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -276,6 +278,14 @@ def blink_pipeline_tracking(ctx, array: Array, obs: Obs, imaging: Imaging, lm, a
         raise ValueError("lm must be [T][2]")
     _check(_lib.blink_pipeline_tracking(ctx, C.byref(a), C.byref(o), C.byref(i), t.ctypes.data, arith, _ptr(d_volt),
                                         _ptr(d_img), _stream(stream)), "blink_pipeline_tracking")
+
+
+def blink_pipeline_averaged(ctx, array: Array, obs: Obs, imaging: Imaging, arith: int, t_avg: int, f_avg: int,
+                            d_volt, d_img, stream=None) -> None:
+    """Mean images over t_avg integrations and f_avg output channels: d_img [T/t_avg][F/f_avg][N][N]."""
+    a, o, i = array.c(), obs.c(), imaging.c()
+    _check(_lib.blink_pipeline_averaged(ctx, C.byref(a), C.byref(o), C.byref(i), arith, int(t_avg), int(f_avg),
+                                        _ptr(d_volt), _ptr(d_img), _stream(stream)), "blink_pipeline_averaged")
 
 
 def blink_dedisperse(ctx, d_img, n_int: int, n_chan: int, n_pix: int, delays, d_out, stream=None) -> None:

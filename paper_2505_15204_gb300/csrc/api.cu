@@ -804,13 +804,16 @@ int64_t sample_stride_bytes(const blink_obs* o, int n_tiles) {
 // one persistent launch that grids and transforms all of their images (fft_persistent.cu).
 constexpr size_t kVisCapBytes = (size_t)4 << 30;
 
-// Batched path on a side outside the side-specialised kernels: one correlator launch per chunk of
-// integrations, then per wave of images (their column results sized to stay in L2) the mixed-radix column
-// pass, gathering each image's cells from the sums, and the row pass (fft_mixed.cu).
+// Batched path on a side outside the side-specialised kernels, and every averaged call: one correlator
+// launch per chunk of integrations, then per wave of output images (their column results sized to stay in
+// L2) the mixed-radix column pass, gathering each output's cells from the sums of its fa channels, and the
+// row pass (fft_mixed.cu).  fa = 1: one image per (integration, channel), divided by W in the row pass;
+// fa > 1: the mean of fa consecutive channels' normalised images, each channel's sums divided by its own
+// W in the gather.  Outputs [tau0 F/fa, tau1 F/fa) are written from d_img on.
 blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
                        const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st,
-                       GainRef gains) {
-    const int F = p.F, T = tau1 - tau0;
+                       GainRef gains, int fa = 1) {
+    const int F = p.F, T = tau1 - tau0, Fo = F / fa;
     if (T <= 0) return BLINK_OK;
     const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
     const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)p.B * 8 * F))));
@@ -821,22 +824,26 @@ blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, in
     void* vis = nullptr;
     void* H = nullptr;
     BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));
-    BLINK_TRY(workspace(ctx, 1, (size_t)std::min(wave, t_chunk * F) * per_img, &H));
+    BLINK_TRY(workspace(ctx, 1, (size_t)std::min(wave, t_chunk * Fo) * per_img, &H));
     ImgOut io;
     io.phase = p.d_phase;
     MixedIn in;
     in.N = p.N;
     in.tw = p.d_tw;
+    in.vis = static_cast<const float2*>(vis);
     in.vstride = p.B;
     in.F = F;
+    in.fa = fa;
+    in.wk = fa > 1 ? p.d_Wk : nullptr;
     in.ent_off = p.d_ent_off;
     in.ent = p.d_ent;
     in.wt = p.d_wt;
     in.corr = crop ? p.d_corr : nullptr;
-    const int out_first = tau0 * F;
+    const float* row_w = fa > 1 ? nullptr : p.d_Wk;
+    const int out_first = tau0 * Fo;
     for (int ta = tau0; ta < tau1; ta += t_chunk) {
         const int tb = std::min(tau1, ta + t_chunk);
-        const int first = ta * F, n_items = (tb - ta) * F;
+        const int first = ta * F, n_items = (tb - ta) * F, n_out = (tb - ta) * Fo;
         {
             StageTimer t(ctx, BLINK_STAGE_CORRELATE, st);
             if (arith == BLINK_CORR_FP8)
@@ -846,17 +853,17 @@ blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, in
                 BLINK_TRY(launch_corr_fp32(kind, d_volt, sstride, p, o->samples_per_int, first, n_items, vis, p.B,
                                            ctx->d_status, st, gains, io));
         }
-        for (int w0 = 0; w0 < n_items; w0 += wave) {
-            const int nw = std::min(wave, n_items - w0);
-            in.vis = static_cast<const float2*>(vis) + (int64_t)w0 * p.B;
-            in.first = first + w0;
-            const WaveMap wm{1, 0, first + w0, nw};
+        in.first = first;
+        for (int w0 = 0; w0 < n_out; w0 += wave) {
+            const int nw = std::min(wave, n_out - w0);
+            in.o_first = w0;
+            const WaveMap wm{1, 0, ta * Fo + w0, nw};
             {
                 StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
                 BLINK_TRY(launch_mixed(in, 0, prec, nw, H, nullptr, 1, wm, out_first, nullptr, st));
             }
             StageTimer t(ctx, BLINK_STAGE_ROW_FFT, st);
-            BLINK_TRY(launch_mixed(in, 1, prec, nw, H, p.d_Wk, F, wm, out_first, d_img, st));
+            BLINK_TRY(launch_mixed(in, 1, prec, nw, H, row_w, F, wm, out_first, d_img, st));
         }
     }
     return BLINK_OK;
@@ -1378,6 +1385,38 @@ blink_status blink_pipeline_tracking(blink_context* ctx, const blink_array* arra
         ta = tb;
     }
     return BLINK_OK;
+}
+
+blink_status blink_pipeline_averaged(blink_context* ctx, const blink_array* array, const blink_obs* obs,
+                                     const blink_imaging* imaging, int32_t arith, int32_t t_avg, int32_t f_avg,
+                                     const uint8_t* d_volt, float* d_img, void* stream) {
+    BLINK_TRY(check_array(array));
+    BLINK_TRY(check_obs(obs, true));
+    BLINK_TRY(check_imaging(imaging));
+    if (arith != BLINK_CORR_FP32 && arith != BLINK_CORR_FP8)
+        return set_error(BLINK_ERR_INVALID_ARG, "arith must be BLINK_CORR_FP32 or BLINK_CORR_FP8");
+    const int T = obs->n_samples / obs->samples_per_int, F = obs->n_fine / obs->chan_avg;
+    if (t_avg < 1 || f_avg < 1 || (T > 0 && T % t_avg) || F % f_avg)
+        return set_error(BLINK_ERR_INVALID_ARG, "t_avg and f_avg must be >= 1 and divide the integrations and the "
+                                                "output channels of the call");
+    if ((int64_t)obs->samples_per_int * t_avg > INT32_MAX)
+        return set_error(BLINK_ERR_INVALID_ARG, "t_avg * samples_per_int overflows");
+    if (!d_volt || !d_img) return set_error(BLINK_ERR_INVALID_ARG, "d_volt or d_img is NULL");
+    if (((uintptr_t)d_volt & 1) || ((uintptr_t)d_img & 7))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_volt must be 2-byte and d_img 8-byte aligned");
+    BLINK_TRY(make_current(ctx));
+    if (T == 0) return BLINK_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the mean over t_avg integrations is the image of their summed correlations (one pointing, so the
+    // cells do not change within the call): correlate over integrations t_avg times longer
+    blink_obs ob = *obs;
+    ob.samples_per_int = obs->samples_per_int * t_avg;
+    Plan* p = nullptr;
+    BLINK_TRY(get_plan(ctx, array, &ob, imaging, true, st, &p));
+    GainRef g;
+    BLINK_TRY(upload_gains(ctx, array, p->F, st, &g));
+    return run_mixed(ctx, *p, &ob, imaging->precision, arith, d_volt, sample_stride_bytes(obs, array->n_tiles), 0,
+                     T / t_avg, d_img, st, g, f_avg);
 }
 
 blink_status blink_pipeline_sets(blink_context* ctx, const blink_array* array, const blink_obs* obs,

@@ -227,9 +227,11 @@ struct MixedIn {
     int N = 0;                             // grid side
     const float2* tw = nullptr;            // make_unit_roots(N)
     const float2* grid = nullptr;          // stored half-plane grids [n][N][N/2 + 1] (the Nyquist column included) ...
-    const float2* vis = nullptr;           // ... or per-image sums in baseline order, image i at vis + i * vstride,
-    int64_t vstride = 0;                   //     gathered through the plan's lists of channel (first + i) % F
-    int first = 0, F = 1;
+    const float2* vis = nullptr;           // ... or per-item sums in baseline order, item i at vis + i * vstride,
+    int64_t vstride = 0;                   //     gathered through the plan's lists of channel (first + i) % F;
+    int first = 0, F = 1;                  //     output o (o_first + launch index) sums the fa items
+    int o_first = 0, fa = 1;               //     (o / (F/fa)) F + (o % (F/fa)) fa + m, scaled by
+    const float* wk = nullptr;             //     1 / (max(wk[f], 1) fa) when wk is given
     const int* ent_off = nullptr;
     const uint2* ent = nullptr;
     const float* wt = nullptr;             // kernel weights per entry, or NULL
@@ -237,7 +239,7 @@ struct MixedIn {
 };
 // pass 0: column pass of n_images grids into d_H (n_images * rows * mixed_h_row(N) elements of the
 // storage type, rows = N, or N/2 with a correction); pass 1: row pass of d_H into images, image i written
-// at d_img + (wm.id(i) - out_first) * side^2 and divided by d_w[wm.id(i) % w_mod].
+// at d_img + (wm.id(i) - out_first) * side^2 and divided by d_w[wm.id(i) % w_mod] (d_w NULL: by 1).
 blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, void* d_H, const float* d_w, int w_mod,
                           WaveMap wm, int out_first, float* d_img, cudaStream_t st);
 blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const float2* d_grid, int n_images,

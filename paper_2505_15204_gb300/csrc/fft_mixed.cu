@@ -128,10 +128,13 @@ struct MixedCol {
     const float2* tw;                      // exp(+2 pi i k / N), k < N
     // input: a stored half-plane grid [img][N][N/2 + 1] ...
     const float2* grid;
-    // ... or the gather lists: image i's sums at vis + i * vstride (baseline order), channel (first + i) % F
+    // ... or the gather lists: item i's sums at vis + i * vstride (baseline order), channel (first + i) % F.
+    // Output o (o_first + blockIdx.y) sums the fa items (o / Fo) F + (o % Fo) fa + m, m < fa, each scaled by
+    // 1 / (max(wk[channel], 1) fa) when wk is given (an average of normalised images), else by 1.
     const float2* vis;
     int64_t vstride;
-    int first, F;
+    int first, F, o_first, fa, Fo;
+    const float* wk;
     const int* ent_off;
     const uint2* ent;
     const float* wt;                       // per-entry kernel weights, or NULL (nearest cell)
@@ -160,19 +163,28 @@ __global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_col(const MixedCol
     } else {
         for (int e = tid; e < cw * P.ld; e += nthr) s[e] = make_float2(0.f, 0.f);
         __syncthreads();
-        const float2* V = P.vis + (int64_t)img * P.vstride;
-        const int* off = P.ent_off + (int64_t)((P.first + img) % P.F) * (P.half + 1);
+        const int o = P.o_first + img;
+        const int it0 = (o / P.Fo) * P.F + (o % P.Fo) * P.fa;
         const int lane = tid & 31;
-        auto val = [&](uint32_t b) { return V[b]; };
         auto idx = [&](int u, int v) { return (u - u0) * P.ld + pd(v); };
-        for (int c = tid >> 5; c < ncol; c += nthr >> 5) {
-            const int u = u0 + c;
-            if (u >= P.half) continue;     // no cell reaches the Nyquist column
-            const int beg = off[u], end = off[u + 1];
-            uint32_t key;
-            float2 x;
-            gather_entry(P.ent, P.wt, beg + lane, end, val, key, x);
-            warp_gather_column(P.ent, P.wt, beg, end, lane, s, val, idx, true, key, x);
+        for (int m = 0; m < P.fa; m++) {           // members in a fixed order: reproducible sums
+            const int it = it0 + m, f = (P.first + it) % P.F;
+            const float2* V = P.vis + (int64_t)it * P.vstride;
+            const float sc = P.wk ? 1.0f / (fmaxf(P.wk[f], 1.0f) * (float)P.fa) : 1.0f;
+            const int* off = P.ent_off + (int64_t)f * (P.half + 1);
+            auto val = [&](uint32_t b) {
+                const float2 x = V[b];
+                return make_float2(x.x * sc, x.y * sc);
+            };
+            for (int c = tid >> 5; c < ncol; c += nthr >> 5) {
+                const int u = u0 + c;
+                if (u >= P.half) continue;     // no cell reaches the Nyquist column
+                const int beg = off[u], end = off[u + 1];
+                uint32_t key;
+                float2 x;
+                gather_entry(P.ent, P.wt, beg + lane, end, val, key, x);
+                warp_gather_column(P.ent, P.wt, beg, end, lane, s, val, idx, true, key, x);
+            }
         }
     }
     __syncthreads();
@@ -223,7 +235,7 @@ __global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_row(const MixedRow
     __syncthreads();
     const float2* res = fft_any(dst, s + (P.rb + r) * P.ld, M, P.rad, P.n_rad, P.tw, 2, t, P.nt);
     const int id = P.wm.id(img);
-    const float w = P.wts[id % P.w_mod];
+    const float w = P.wts ? P.wts[id % P.w_mod] : 1.f;
     float scale = 1.0f / (w > 0.f ? w : 1.f);
     if (P.corr) scale *= P.corr[y];
     float* out = P.img + ((int64_t)(id - P.out_first) * P.ny + y) * P.nout;
@@ -340,6 +352,10 @@ blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, v
         C.vstride = in.vstride;
         C.first = in.first;
         C.F = in.F;
+        C.o_first = in.o_first;
+        C.fa = in.fa;
+        C.Fo = in.F / in.fa;
+        C.wk = in.wk;
         C.ent_off = in.ent_off;
         C.ent = in.ent;
         C.wt = in.wt;

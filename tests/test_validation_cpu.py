@@ -233,3 +233,15 @@ def test_image_noalloc_scratch_limit_on_mixed_radix_sides():
     # 2400 x 1204 FP32 pairs exceed the 16 MiB scratch; BF16 pairs fit.  Both are rejected or accepted before
     # any device work: the accepted call stops at the scratch look-up, which fails without a device.
     _expect(B.BLINK_ERR_UNSUPPORTED, "16 MiB static scratch", fn, B.Imaging(2400), PTR, 1, PTR, PTR)
+
+
+def test_averaged_pipeline_arguments():
+    a, o, k = B.Array(_enu()), _obs(), B.Imaging(64)          # T = 2 integrations, F = 2 output channels
+    fn = B.blink_pipeline_averaged
+    for t_avg, f_avg in ((0, 1), (1, 0), (3, 1), (1, 3), (-1, 2)):
+        _expect(B.BLINK_ERR_INVALID_ARG, "t_avg and f_avg", fn, None, a, o, k, 1, t_avg, f_avg, PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "arith", fn, None, a, o, k, 7, 1, 1, PTR, PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "NULL", fn, None, a, o, k, 1, 1, 1, 0, PTR)
+    for t_avg, f_avg in ((1, 1), (2, 1), (1, 2), (2, 2)):
+        _expect(*NO_CTX, fn, None, a, o, k, 1, t_avg, f_avg, PTR, PTR)
+    _expect(*NO_CTX, fn, None, a, o, B.Imaging(1200, support=6), 0, 2, 2, PTR, PTR)

@@ -194,3 +194,84 @@ def test_dedispersion_on_a_mixed_side(B, ctx):
     B.blink_sync(ctx)
     ref = oracle.dedisperse(cube.astype(np.float64), delays)
     assert np.abs(out.cpu().numpy() - ref).max() < 1e-5
+
+
+# ---------------------------------------------------------------------------------------------------
+# averaged images: one transform per output, averaged in the uv plane
+# ---------------------------------------------------------------------------------------------------
+
+AVG_CASES = [
+    # name, n_samples, fine, chan_avg, n_pix, support, t_avg, f_avg, pointing, flags
+    ("coarse", 40, 8, 1, 256, 0, 1, 8, (0.0, 0.0), False),      # band average of every integration
+    ("coarse", 40, 8, 1, 256, 0, 4, 1, (0.0, 0.0), False),      # time average of every channel
+    ("coarse", 40, 8, 2, 1200, 0, 2, 2, (0.0, 0.0), False),     # both
+    ("uneven", 20, 6, 1, 150, 0, 2, 6, (0.0, 0.0), True),       # one long-exposure image, flagged tiles
+    ("coarse", 20, 4, 1, 300, 6, 2, 4, (0.2, -0.1), False),     # kernel gridding, off zenith
+    ("precision", None, None, 1, 512, 0, 1, 1, (0.0, 0.0), False),   # nothing averaged
+]
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp32", "fp8"])
+@pytest.mark.parametrize("case", AVG_CASES, ids=[f"{c[0]}-{c[4]}-t{c[6]}-f{c[7]}-W{c[5]}" for c in AVG_CASES])
+def test_averaged_pipeline_equals_the_mean_of_the_oracle_images(B, ctx, case, arith):
+    name, ns_total, fine, c, n_pix, W, ta, fa, pc, flags = case
+    w, volt, freqs, fl = _case(name, ns_total, fine, flags)
+    T, F = volt.shape[0] // 10, len(freqs) // c
+    out = torch.full((T // ta, F // fa, n_pix, n_pix), float("nan"), dtype=torch.float32, device="cuda")
+    B.blink_pipeline_averaged(ctx, B.Array(w["enu"], fl), B.Obs(freqs, c, 10, volt.shape[0]),
+                              B.Imaging(n_pix, support=W, phase_centre=pc), arith, ta, fa, dev(volt), out)
+    B.blink_sync(ctx)
+    ref = oracle.pipeline(volt, w["enu"], freqs, 10, c, n_pix, flags=fl, n_threads=8, support=W, phase_centre=pc)
+    imgs = ref["images"].reshape(T // ta, ta, F // fa, fa, n_pix, n_pix).mean(axis=(1, 3))
+    got = out.cpu().numpy()
+    for t in range(T // ta):
+        for f in range(F // fa):
+            assert_image_close(got[t, f], imgs[t, f], (t, f))
+
+
+def test_band_average_equals_dedispersion_with_zero_delays(B, ctx):
+    # the uv-plane band average against the image-plane one: blink_pipeline images, then blink_dedisperse
+    # with zero delays (the mean over channels), on the same data
+    w, volt, freqs, _ = _case("coarse", 30, 16)
+    T, F, n = 3, 16, 256
+    img = torch.empty((T * F, n, n), dtype=torch.float32, device="cuda")
+    B.blink_pipeline(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 30), B.Imaging(n), 1, 0, dev(volt), img)
+    band = torch.empty((T, n, n), dtype=torch.float32, device="cuda")
+    B.blink_dedisperse(ctx, img, T, F, n, np.zeros(F, np.int32), band)
+    avg = torch.empty((T, 1, n, n), dtype=torch.float32, device="cuda")
+    B.blink_pipeline_averaged(ctx, B.Array(w["enu"]), B.Obs(freqs, 1, 10, 30), B.Imaging(n), 1, 1, F, dev(volt), avg)
+    B.blink_sync(ctx)
+    a, b = avg[:, 0].cpu().numpy(), band.cpu().numpy()
+    for t in range(T):
+        assert_image_close(a[t], b[t], t, rms_tol=1e-5)
+
+
+def test_long_exposure_8192_on_sampled_pixels(B, ctx):
+    # the paper's long-exposure product at its 8192 x 8192 side: four channels and two integrations averaged
+    # into one image, checked on sampled pixels against the mean of the oracle's per-image pixels
+    n = 8192
+    w, volt, freqs, _ = _case("coarse", 20, 4)
+    enu = w["enu"]
+    out = torch.full((1, 1, n, n), float("nan"), dtype=torch.float32, device="cuda")
+    B.blink_pipeline_averaged(ctx, B.Array(enu), B.Obs(freqs, 1, 10, 20), B.Imaging(n), 1, 2, 4, dev(volt), out)
+    B.blink_sync(ctx)
+    S = oracle.correlate(volt, 10, 1)
+    nus = oracle.output_freqs(freqs, 1)
+    du = oracle.default_cell(enu, float(nus.max()), n)
+    rng = np.random.default_rng(81920)
+    pts = [(n // 2, n // 2), (0, 0), (n - 1, n - 1)] + [(n // 2, x) for x in range(0, n, 211)]
+    pts += [tuple(p) for p in rng.integers(0, n, size=(200, 2))]
+    yx = np.array(pts, dtype=np.int32)
+    want = np.zeros(len(yx))
+    for t in range(2):
+        for f in range(4):
+            iu, iv, keep = oracle.cells(oracle.uvw(enu, float(nus[f])), du, n)
+            G, Wsum = oracle.grid(S[t, f], enu.shape[0], 10, iu, iv, keep, n)
+            want += oracle.image_pixels(G, Wsum, yx) / 8.0
+            del G
+    got = out[0, 0][torch.from_numpy(yx[:, 0]).long().cuda(), torch.from_numpy(yx[:, 1]).long().cuda()].cpu().numpy()
+    scale = float(np.sqrt(np.mean(want ** 2)))
+    err = np.abs(got.astype(np.float64) - want)
+    print("8192 long exposure, sampled pixels: rel RMS", float(np.sqrt(np.mean(err ** 2))) / scale)
+    assert np.sqrt(np.mean(err ** 2)) <= 1e-4 * scale
+    assert err.max() <= 1e-3 * scale
