@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "coarse", "precision", "uneven", "fullband"])
     ap.add_argument("--n-pix", type=int, default=0,
                     help="image side for every channel set instead of the workload's (e.g. 1200, 8192)")
+    ap.add_argument("--average", type=int, nargs=2, default=None, metavar=("T_AVG", "F_AVG"),
+                    help="image means over T_AVG integrations and F_AVG channels (blink_pipeline_averaged); the "
+                         "metric then counts the images averaged")
     ap.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (default: every host core)")
     ap.add_argument("--dedisperse", action="store_true",
                     help="also time blink_dedisperse on the step's images (a DM sweeping half the chunk)")
@@ -213,6 +216,7 @@ def bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes):
             "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
             "mode": args.mode, "precision": args.precision, "gains": bool(args.gains), "fused": bool(args.fused),
             "jones": bool(args.jones), "support": args.support, "pointing": list(args.pointing),
+            "average": list(args.average) if args.average else None,
             "l2": (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e6:.3g} MB per step fit L2: "
                    "each step timed alone after a 516 MB buffer overwrite") if small else
                   (f"inputs {in_bytes / 1e6:.3g} MB and outputs {out_bytes / 1e9:.3g} GB per step exceed L2; "
@@ -355,6 +359,13 @@ def run_ours(args, world, rank, local):
     n_pix = sets[0][3]
     n_img = sum(c for _, _, c, _ in sets)
     img_floats = sum(c * side * side for _, _, c, side in sets)
+    T_int = ns // w.samples_per_int
+    avg = tuple(args.average) if args.average else None
+    if avg:
+        if multi or T_int % avg[0] or w.n_out_chan % avg[1]:
+            raise SystemExit("--average: one channel set, T_AVG and F_AVG dividing the integrations and channels")
+        n_out = (T_int // avg[0]) * (w.n_out_chan // avg[1])
+        img_floats = n_out * n_pix * n_pix
     arith = B.BLINK_CORR_FP8 if args.arith == "fp8" else B.BLINK_CORR_FP32
     mode = B.BLINK_MODE_BATCHED if args.mode == "batched" else B.BLINK_MODE_PLAIN
     if multi and mode != B.BLINK_MODE_BATCHED:
@@ -376,12 +387,16 @@ def run_ours(args, world, rank, local):
     volt = torch.from_numpy(inp["volt"]).cuda()
     if multi:
         img = torch.empty(img_floats, dtype=torch.float32, device="cuda")
+    elif avg:
+        img = torch.empty((n_out, n_pix, n_pix), dtype=torch.float32, device="cuda")
     else:
         img = torch.empty((n_img, n_pix, n_pix), dtype=torch.float32, device="cuda")
     wts = torch.empty(n_img, dtype=torch.float32, device="cuda")
 
     def step(weights=None):
-        if multi:
+        if avg:
+            B.blink_pipeline_averaged(ctx, arr, obs, im, arith, avg[0], avg[1], volt, img, stream)
+        elif multi:
             B.blink_pipeline_sets(ctx, arr, obs, bsets, arith, volt, img, img_floats, stream)
         else:
             B.blink_pipeline(ctx, arr, obs, im, arith, mode, volt, img, weights, stream)
@@ -442,6 +457,12 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = measured_peaks()
     roof = None
     def set_bytes(stage):
+        if avg:                                   # per output: fa channels' sums in, one transform
+            Bn = n_tiles * (n_tiles + 1) // 2
+            h = n_pix * (n_pix // 2 + 1)
+            if stage == 0:
+                return (n_img // avg[0]) * (K * avg[0] * 2 * n_tiles + 8 * Bn)
+            return n_out * ((avg[1] * 8 * Bn + 8 * h) if stage == 1 else (8 * h + 4 * n_pix * n_pix))
         return sum(stage_bytes(stage, n_tiles, side, K) * c for _, _, c, side in sets)
 
     if stage_n[dom]:
@@ -449,7 +470,7 @@ def run_ours(args, world, rank, local):
         per_launch = bytes_total / stage_n[dom]
         avg_s = stage_ms[dom] / 1e3 / stage_n[dom]
         ach = per_launch / avg_s / 1e9
-        mixed = not fast_side(sets[0][3] * (2 if args.support else 1))
+        mixed = bool(avg) or not fast_side(sets[0][3] * (2 if args.support else 1))
         names, kerns, srcs = (MIXED_NAMES, MIXED_KERNELS, MIXED_SOURCES) if mixed else (STAGE_NAMES, STAGE_KERNELS,
                                                                                           STAGE_SOURCES)
         kern = kerns[dom] if (dom or arith == B.BLINK_CORR_FP8) else "k_corr_fp32"
@@ -469,7 +490,7 @@ def run_ours(args, world, rank, local):
     # full-size parity on sampled images, and the oracle's own throughput on them (rank 0, one GPU)
     parity = None
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and not avg:
         import oracle
         n_s = max(4, 4 * cores)
         picks = pick_images(sets, n_s)
@@ -495,7 +516,7 @@ def run_ours(args, world, rank, local):
     # incoherent dedispersion of the step's image cube: a dispersion measure whose sweep across the band
     # fills half the chunk, delays rounded to whole integrations
     dedisp = None
-    if args.dedisperse and rank == 0 and not multi:
+    if args.dedisperse and rank == 0 and not multi and not avg:
         T_int, F = ns // w.samples_per_int, n_img // (ns // w.samples_per_int)
         t_int = w.samples_per_int * 100e-6
         nu = inp["freqs"].reshape(F, w.chan_avg).mean(axis=1) / 1e6          # MHz
@@ -523,7 +544,7 @@ def run_ours(args, world, rank, local):
     # plain FP32 per-image path, batched FP32-correlation path, cuFFT's batched c2r transform of grids of the
     # same shape (the FFT stage alone), and the ABI correlation entry point's four-product visibilities
     comparison = None
-    if rank == 0 and not multi and not args.no_compare and args.mode == "batched" and args.arith == "fp8":
+    if rank == 0 and not multi and not avg and not args.no_compare and args.mode == "batched" and args.arith == "fp8":
         def timed(fn, reps, warm=1):
             for _ in range(warm):
                 fn()
@@ -573,7 +594,7 @@ def run_ours(args, world, rank, local):
 
     # end to end through the host-buffer entry point (pinned voltages in, pinned images out)
     e2e = None
-    if not args.no_e2e and not multi:
+    if not args.no_e2e and not multi and not avg:
         ns_e = min(5 * w.samples_per_int, ns)
         n_e = (ns_e // w.samples_per_int) * w.n_out_chan
         obs_e = B.Obs(inp["freqs"], w.chan_avg, w.samples_per_int, ns_e)
