@@ -179,9 +179,10 @@ def source_hash(name: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def traffic_for(kernel: str, source: str, shape=None):
-    """DRAM bytes per launch of `kernel` (at the tuned launch shape, where traffic depends on it) from the
-    committed ncu summary, if its source is unchanged."""
+def traffic_for(kernel: str, source: str, shape=None, side=None):
+    """DRAM bytes per launch of `kernel` (at the tuned launch shape, where traffic depends on it, and at the
+    image side it was captured on, where recorded) from the committed ncu summary, if its source is
+    unchanged."""
     p = os.path.join(PROFILES, "traffic.json")
     if not os.path.exists(p):
         return None
@@ -189,6 +190,8 @@ def traffic_for(kernel: str, source: str, shape=None):
         d = json.load(f)
     e = d.get(kernel)
     if not e or e.get("source_sha256_16") != source_hash(source):
+        return None
+    if "side" in e and e["side"] != side:
         return None
     by_shape = e.get("dram_bytes_per_launch_fullsize_by_shape")
     if by_shape is not None:
@@ -475,9 +478,10 @@ def run_ours(args, world, rank, local):
                                                                                           STAGE_SOURCES)
         kern = kerns[dom] if (dom or arith == B.BLINK_CORR_FP8) else "k_corr_fp32"
         src = srcs[dom] if (dom or arith == B.BLINK_CORR_FP8) else "correlate.cu"
-        # the committed DRAM counters are those of the nearest-cell kernel: none for the kernel form
+        # the committed DRAM counters are those of the nearest-cell, two-launch, unaveraged forms
         shape = B.blink_tuned_shape(ctx)
-        traffic = traffic_for(kern, src, shape) if not args.support else None
+        traffic = (traffic_for(kern, src, shape, sets[0][3])
+                   if not (args.support or args.fused or avg or args.gains or args.jones) else None)
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": traffic, "kernel": kern, "stage": names[dom],
                 "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3, "peak_kind": f"{peak_kind} hbm_gbs",
