@@ -708,10 +708,11 @@ __device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__
 // two columns), with the entries and their visibilities loaded NB chunks of 32 at a time.  val(i, b) is the
 // value of entry i, whose baseline is b: with sums in baseline order it depends on the entry's load (two
 // dependent round trips per NB chunks), with gather-ordered sums only on i (one).  occ(u, v) is the
-// occupancy word of cell (u, v) (bit v / 32 of the word of v % 32 in its column).
+// occupancy word of cell (u, v) (bit v / 32 of the word of v % 32 in its column).  Every run's sum is
+// multiplied by `scale` before it is stored (or added to the cell's earlier part).
 template <int NB, typename T, typename Val, typename Idx, typename Occ>
 __device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
-                                                        Val val, Idx idx, Occ occ) {
+                                                        Val val, Idx idx, Occ occ, float scale) {
     uint32_t prev = 0xFFFFFFFFu;                    // the last cell of the previous chunk
     for (int base = beg; base < end; base += 32 * NB) {
         uint32_t key[NB], bl[NB];
@@ -756,7 +757,8 @@ __device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict_
             const uint32_t klast = __shfl_sync(0xFFFFFFFFu, k, min(31, end - 1 - cb));
             if (i < end && (lane == 31 || i + 1 >= end || knext != k)) {
                 const int u = ent_u(k), v = ent_v(k);
-                if ((u + v) & 1) y = make_float2(-y.x, -y.y);
+                const float sc = ((u + v) & 1) ? -scale : scale;
+                y = __fmul2_rn(y, make_float2(sc, sc));
                 T* p = s + idx(u, v);
                 if (k == prev) y = cadd(ld_c(p), y);
                 st_c(p, y);

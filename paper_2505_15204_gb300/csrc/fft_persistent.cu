@@ -6,8 +6,9 @@
 //       sides in radix-8 passes), then write the block to the image's slot of a small ring of intermediates
 //       (kept in L2);
 //   row task (image k, row block rb): once all column tasks of image k are done, transform 32 rows
-//       along u (complex to real) and scale by 1 / (W * 2K), writing the image rows with streaming stores
-//       (they are not read back, so they should not displace the ring from L2).
+//       along u (complex to real) and scale by 1 / (W * 2K) (side 512 with nearest-cell gridding scales the
+//       gridded cells instead), writing the image rows with streaming stores (they are not read back, so
+//       they should not displace the ring from L2).
 // Side 512 (nearest cell) keeps the ring column-major, [u][v] with v contiguous: each column warp stores its
 // transformed column straight from registers as whole 128-byte lines, and a row task reads 32 consecutive
 // rows v of one column u per warp instruction, so that lane l holds row y0 + l.  Its first radix-16 pass
@@ -46,8 +47,12 @@ constexpr int kVisAhead = 8;                     // images ahead whose visibilit
 constexpr int kRowLd = 257;                      // side 512: float2 pitch of a row's 16 x 16 intermediate (odd:
                                                  //   lanes = rows write it without bank conflicts)
 
-// exp(2 pi i m / 512) for m in [0, 512): the twiddles of the side-512 row tasks, indexed by warp-uniform m
-__constant__ float2 c_circ512[512];
+// The twiddles of the side-512 row tasks, per warp w (which always takes the butterflies jA, jB of the first
+// pass): [0, 9) the pre-twiddles exp(2 pi i u / 512) of its A points, [9, 17) those of its B points, [17, 32)
+// and [32, 47) the first pass's exp(2 pi i 2 j k1 / 512), k1 = 1 .. 15, for j = jA and jB.  A warp reads its
+// row at a warp-uniform base with constant offsets, so no index arithmetic is spent on them.
+constexpr int kRowTw = 48;
+__constant__ float2 c_rowtw512[kW * kRowTw];
 
 struct FftParams {
     const float2* vis;       // correlation sums of the chunk's images, [item][B]
@@ -329,6 +334,10 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
         return P.gathered ? make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i)) : __ldcs(V + b);
     };
     const int u0 = cb * 2 * kCW + 2 * warp;           // the warp's columns u0, u0 + 1
+    // 1 / (W * 2K) (or 1 / (W * K)) is applied to each gridded cell: the transforms are linear, so the image
+    // comes out scaled, and a cell costs one product where an image pixel would
+    const float wk = __ldg(P.wk + f);
+    const float inv = 1.0f / (wk > 0.f ? wk : 1.f);
     {
         // both columns in one pass over their (contiguous) entries
         uint32_t* occ = s_occ + 2 * warp * 32;
@@ -337,7 +346,7 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
         __syncwarp();
         auto idx = [&](int u, int v) { return (2 * warp + (u - u0)) * LD + v; };
         auto occw = [&](int u, int v) { return occ + (u - u0) * 32 + (v & 31); };
-        warp_gather_occ_batched<4>(P.ent, off[u0], off[u0 + 2], lane, s, val, idx, occw);
+        warp_gather_occ_batched<4>(P.ent, off[u0], off[u0 + 2], lane, s, val, idx, occw, inv);
         __syncwarp();
         col512_pass1(s + 2 * warp * LD, lane, occ[lane]);
         col512_pass1(s + (2 * warp + 1) * LD, lane, occ[32 + lane]);
@@ -377,6 +386,8 @@ __device__ int* row_task512(const FftParams& P, int k, int rb, unsigned char* wo
     const bool ok = warp_wait(P, P.col_done + k, P.n_cb + P.extra_wait, 0);
     if (ok) {
         const int jA = warp == 0 ? 0 : warp, jB = warp == 0 ? 8 : 16 - warp;
+        const int tb = warp * kRowTw;               // the warp's twiddle row
+        auto tw = [&](int q) { return c_rowtw512[tb + q]; };
         const T* col = static_cast<const T*>(P.H) + (int64_t)slot * M * N + y0 + lane;
         float2 a[16], b[16];
 #pragma unroll
@@ -388,38 +399,36 @@ __device__ int* row_task512(const FftParams& P, int k, int rb, unsigned char* wo
             // butterfly 0: u = 16 r pairs with 16 (16 - r); u = 0 with the (empty) Nyquist column, u = 128 with
             // itself.  Butterfly 8: u = 8 + 16 r pairs with 8 + 16 (15 - r).
             float2 z = make_float2(0.f, 0.f);
-            pretw(a[0], z, c_circ512[0]);
+            pretw(a[0], z, tw(0));
 #pragma unroll
-            for (int r = 1; r < 8; r++) pretw(a[r], a[16 - r], c_circ512[16 * r]);
+            for (int r = 1; r < 8; r++) pretw(a[r], a[16 - r], tw(r));
             z = a[8];
-            pretw(a[8], z, c_circ512[128]);
+            pretw(a[8], z, tw(8));
 #pragma unroll
-            for (int r = 0; r < 8; r++) pretw(b[r], b[15 - r], c_circ512[8 + 16 * r]);
+            for (int r = 0; r < 8; r++) pretw(b[r], b[15 - r], tw(9 + r));
         } else {
             // u = j + 16 s pairs with 256 - u = (16 - j) + 16 (15 - s); the pair's smaller index gives wq
 #pragma unroll
             for (int s = 0; s < 8; s++) {
-                pretw(a[s], b[15 - s], c_circ512[jA + 16 * s]);
-                pretw(b[s], a[15 - s], c_circ512[jB + 16 * s]);
+                pretw(a[s], b[15 - s], tw(s));
+                pretw(b[s], a[15 - s], tw(9 + s));
             }
         }
-        auto pass1 = [&](float2(&v)[16], int j) {
+        auto pass1 = [&](float2(&v)[16], int j, int t0) {
             idft<16>(v);
             float2* dst = S + lane * kRowLd + 16 * j;
             dst[0] = v[0];
 #pragma unroll
-            for (int k1 = 1; k1 < 16; k1++) dst[k1] = cmul(v[k1], c_circ512[(2 * j * k1) & 511]);
+            for (int k1 = 1; k1 < 16; k1++) dst[k1] = cmul(v[k1], tw(t0 + k1 - 1));
         };
-        pass1(a, jA);
-        pass1(b, jB);
+        pass1(a, jA, 17);
+        pass1(b, jB, 32);
     }
     if (__syncthreads_or(!ok)) return nullptr;
     if (tid == 0) {                                     // every warp's ring reads are done
         __threadfence();
         atomicAdd(P.row_done + k, 1);
     }
-    const float w = P.wk[f];
-    const float inv = 1.0f / (w > 0.f ? w : 1.f);
     const int h = lane >> 4, k1 = lane & 15;
 #pragma unroll 1
     for (int it = 0; it < 2; it++) {
@@ -429,9 +438,10 @@ __device__ int* row_task512(const FftParams& P, int k, int rb, unsigned char* wo
 #pragma unroll
         for (int j = 0; j < 16; j++) v[j] = src[16 * j];
         idft<16>(v);
+        // the column tasks gridded the cells already scaled by 1 / (W * 2K)
         float2* out = reinterpret_cast<float2*>(P.img_out + ((int64_t)(id - P.out_first) * N + y0 + rr) * N) + k1;
 #pragma unroll
-        for (int k2 = 0; k2 < 16; k2++) __stcs(out + 16 * k2, make_float2(v[k2].x * inv, v[k2].y * inv));
+        for (int k2 = 0; k2 < 16; k2++) __stcs(out + 16 * k2, v[k2]);
     }
     return nullptr;
 }
@@ -932,11 +942,12 @@ bool fft_fused_ok(const Plan& p, int ns, int kind, const uint8_t* d_volt, int64_
 
 size_t fused_ring_floats(const Plan& p) { return (size_t)kRingV * 2 * p.e_stride; }
 
-// exp(2 pi i m / 512) for m in [0, 512) into constant memory of the current device: the first octant's
-// angles in FP64, the others by the exact symmetries of the circle, so that quarter turns are exact.
+// The side-512 row tasks' twiddle rows into constant memory of the current device, from exp(2 pi i m / 512),
+// m in [0, 512): the first octant's angles in FP64, the others by the exact symmetries of the circle, so that
+// quarter turns are exact.
 blink_status fft_constants(int N) {
     if (N != 512) return BLINK_OK;
-    float2 t[512];
+    float2 t[512], rt[kW * kRowTw] = {};
     for (int m = 0; m < 512; m++) {
         const int q = m / 128, k = m % 128;
         double c = 1.0, s = 0.0;
@@ -949,7 +960,17 @@ blink_status fft_constants(int N) {
         const double y = q == 0 ? s : q == 1 ? c : q == 2 ? -s : -c;
         t[m] = make_float2((float)x, (float)y);
     }
-    BLINK_CUDA(cudaMemcpyToSymbol(c_circ512, t, sizeof(t)));
+    for (int w = 0; w < kW; w++) {
+        const int jA = w == 0 ? 0 : w, jB = w == 0 ? 8 : 16 - w;
+        float2* r = rt + w * kRowTw;
+        for (int q = 0; q < 9; q++) r[q] = w == 0 ? t[16 * q] : (q < 8 ? t[jA + 16 * q] : make_float2(0.f, 0.f));
+        for (int q = 0; q < 8; q++) r[9 + q] = t[jB + 16 * q];
+        for (int k1 = 1; k1 < 16; k1++) {
+            r[17 + k1 - 1] = t[(2 * jA * k1) & 511];
+            r[32 + k1 - 1] = t[(2 * jB * k1) & 511];
+        }
+    }
+    BLINK_CUDA(cudaMemcpyToSymbol(c_rowtw512, rt, sizeof(rt)));
     return BLINK_OK;
 }
 
