@@ -257,6 +257,29 @@ blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_
                               const int32_t* h_delays, float* d_out, void* stream);
 
 /*
+ * Incoherent dedispersion of a stream of image cubes (Sec. 2 and 7, Table 1: the dispersive sweep of a burst
+ * across the band lasts up to tens of seconds, far longer than one cube): the cubes of consecutive calls are
+ * the integrations [t0, t0 + n_int) of one stream, in blink_pipeline's image order, t0 = 0 in the first call
+ * and each later call's t0 the previous t0 + n_int.  With img the concatenation of all cubes and
+ * D = max(delays), the output integration t is (1/n_chan) sum_f img[t + delays[f]][f], as blink_dedisperse
+ * computes it on one cube; it is complete once integration t + D has been passed, and the call that passes
+ * it writes it.  Each call writes the outputs t in [max(0, t0 - D), t0 + n_int - D), in order, to d_out and
+ * their count to *h_n_out: n_int for every call whose t0 >= D, fewer (possibly 0) before.
+ *   d_carry   device float [D][N][N], caller-owned, kept between the calls of one stream (NULL allowed when
+ *             D = 0): the partial channel sums of the outputs still waiting for later cubes, D images
+ *             whatever n_chan; what it holds before a call with t0 = 0 is ignored.  A stream's calls must be
+ *             ordered on one stream and pass the same delays; two streams need two carry buffers.
+ *   d_img     float [n_int][n_chan][N][N]; d_out float [n_int][N][N] (room for the largest count).
+ *   h_delays  host int32 [n_chan], >= 0, in integrations (see blink_dedisperse).
+ * Sums are FP32, in channel order within a cube and cube by cube; the result equals blink_dedisperse on the
+ * concatenated cube up to that rounding.  n_int, n_chan >= 1, t0 >= 0, N even in [64, 8192], d_img, d_out
+ * and d_carry 16-byte aligned, else BLINK_ERR_INVALID_ARG before any launch (*h_n_out = 0).
+ */
+blink_status blink_dedisperse_stream(blink_context* ctx, float* d_carry, int64_t t0, const float* d_img, int32_t n_int,
+                                     int32_t n_chan, int32_t n_pix, const int32_t* h_delays, float* d_out,
+                                     int32_t* h_n_out, void* stream);
+
+/*
  * blink_pipeline on host buffers: copies h_volt to device workspace, runs the batched path and delivers
  * the images to h_img, all ordered on `stream`.
  *   images_per_pass == 0: when the device can write h_img - one page-locked allocation (cudaHostAlloc,

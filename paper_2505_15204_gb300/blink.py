@@ -40,7 +40,7 @@ ENTRY_POINTS = (
     "blink_cells", "blink_correlate", "blink_grid", "blink_image", "blink_pipeline", "blink_pipeline_host",
     "blink_set_profiling", "blink_read_profile", "blink_image_noalloc", "blink_pipeline_sets", "blink_dedisperse",
     "blink_set_wait_budget", "blink_set_fused", "blink_tuned_shape", "blink_pipeline_tracking",
-    "blink_pipeline_averaged",
+    "blink_pipeline_averaged", "blink_dedisperse_stream",
 )
 BLINK_STAGE_CORRELATE = 0
 BLINK_STAGE_GRID_FFT = 1
@@ -103,6 +103,7 @@ def _load():
         "blink_tuned_shape": (S, [P, P]),
         "blink_pipeline_tracking": (S, [P, P, P, P, P, I32, P, P, P]),
         "blink_pipeline_averaged": (S, [P, P, P, P, I32, I32, I32, P, P, P]),
+        "blink_dedisperse_stream": (S, [P, P, I64, P, I32, I32, I32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -295,6 +296,19 @@ def blink_dedisperse(ctx, d_img, n_int: int, n_chan: int, n_pix: int, delays, d_
         raise ValueError("delays must have one entry per channel")
     _check(_lib.blink_dedisperse(ctx, _ptr(d_img), n_int, n_chan, n_pix, d.ctypes.data, _ptr(d_out), _stream(stream)),
            "blink_dedisperse")
+
+
+def blink_dedisperse_stream(ctx, d_carry, t0: int, d_img, n_int: int, n_chan: int, n_pix: int, delays, d_out,
+                            stream=None) -> int:
+    """One cube [n_int][n_chan][N][N] of a stream starting at integration t0; writes the outputs it completes
+    to d_out and returns their count (the carry d_carry [max(delays)][N][N] links consecutive calls)."""
+    d = np.ascontiguousarray(delays, dtype=np.int32)
+    if d.shape != (n_chan,):
+        raise ValueError("delays must have one entry per channel")
+    n_out = C.c_int32(0)
+    _check(_lib.blink_dedisperse_stream(ctx, _ptr(d_carry), int(t0), _ptr(d_img), n_int, n_chan, n_pix, d.ctypes.data,
+                                        _ptr(d_out), C.byref(n_out), _stream(stream)), "blink_dedisperse_stream")
+    return int(n_out.value)
 
 
 def blink_set_profiling(ctx, enable: bool) -> None:

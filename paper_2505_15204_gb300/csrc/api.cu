@@ -1494,6 +1494,36 @@ blink_status blink_dedisperse(blink_context* ctx, const float* d_img, int32_t n_
     return launch_dedisperse(d_img, n_int - dmax, n_chan, n_pix, static_cast<const int*>(d), d_out, st);
 }
 
+blink_status blink_dedisperse_stream(blink_context* ctx, float* d_carry, int64_t t0, const float* d_img, int32_t n_int,
+                                     int32_t n_chan, int32_t n_pix, const int32_t* h_delays, float* d_out,
+                                     int32_t* h_n_out, void* stream) {
+    if (!d_img || !d_out || !h_delays || !h_n_out)
+        return set_error(BLINK_ERR_INVALID_ARG, "d_img, d_out, h_delays or h_n_out is NULL");
+    *h_n_out = 0;
+    if (n_int < 1 || n_chan < 1) return set_error(BLINK_ERR_INVALID_ARG, "n_int and n_chan must be >= 1");
+    if (t0 < 0) return set_error(BLINK_ERR_INVALID_ARG, "t0 must be >= 0");
+    if (n_pix < 64 || n_pix > 8192 || (n_pix & 1))
+        return set_error(BLINK_ERR_INVALID_ARG, "n_pix must be even, in [64, 8192]");
+    int dmax = 0;
+    for (int f = 0; f < n_chan; f++) {
+        if (h_delays[f] < 0) return set_error(BLINK_ERR_INVALID_ARG, "delays must be >= 0");
+        dmax = std::max(dmax, (int)h_delays[f]);
+    }
+    if (dmax > 0 && !d_carry) return set_error(BLINK_ERR_INVALID_ARG, "d_carry is NULL while max(delays) > 0");
+    if (((uintptr_t)d_img & 15) || ((uintptr_t)d_out & 15) || ((uintptr_t)d_carry & 15))
+        return set_error(BLINK_ERR_INVALID_ARG, "d_img, d_out and d_carry must be 16-byte aligned");
+    BLINK_TRY(make_current(ctx));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* d = nullptr;
+    BLINK_TRY(workspace(ctx, 7, sizeof(int32_t) * (size_t)n_chan, &d));
+    BLINK_CUDA(cudaMemcpyAsync(d, h_delays, sizeof(int32_t) * (size_t)n_chan, cudaMemcpyHostToDevice, st));
+    int n_out = 0;
+    BLINK_TRY(launch_dedisperse_stream(d_img, t0, n_int, n_chan, n_pix, static_cast<const int*>(d), dmax, d_carry, d_out,
+                                       &n_out, st));
+    *h_n_out = n_out;
+    return BLINK_OK;
+}
+
 blink_status blink_pipeline_host(blink_context* ctx, const blink_array* array, const blink_obs* obs,
                                  const blink_imaging* imaging, int32_t arith, const uint8_t* h_volt, float* h_img,
                                  int32_t images_per_pass, void* stream) {

@@ -173,6 +173,8 @@ bool corr_fp8_gathers(const Plan& p, int ns, int out_kind, GainRef gains);
 blink_status launch_gather_phase(const Plan& p, cudaStream_t st);
 blink_status launch_dedisperse(const float* d_img, int n_out, int F, int n_pix, const int* d_delay, float* d_out,
                                cudaStream_t st);
+blink_status launch_dedisperse_stream(const float* d_img, int64_t t0, int n, int F, int n_pix, const int* d_delay,
+                                      int D, float* d_carry, float* d_out, int* n_out, cudaStream_t st);
 blink_status launch_grid_gather(const Plan& p, const float* d_vis4, int first_image, int n_images, float* d_grid,
                                 int* d_status, cudaStream_t st);
 blink_status launch_grid_atomic(const Plan& p, const float2* d_visI, int image, float2* d_grid_full,

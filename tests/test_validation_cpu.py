@@ -160,6 +160,22 @@ def test_dedisperse_validates_delays_before_any_device_work():
         fn(None, PTR, 4, 3, 64, [0, 1], PTR)     # one delay per channel, checked by the binding
 
 
+def test_dedisperse_stream_validates_before_any_device_work():
+    fn = B.blink_dedisperse_stream
+    _expect(B.BLINK_ERR_INVALID_ARG, "delays must be >= 0", fn, None, PTR, 0, PTR, 4, 3, 64, [0, -1, 0], PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "n_int and n_chan must be >= 1", fn, None, PTR, 0, PTR, 0, 3, 64, [0, 0, 0], PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "t0 must be >= 0", fn, None, PTR, -1, PTR, 4, 3, 64, [0, 0, 0], PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "even, in [64, 8192]", fn, None, PTR, 0, PTR, 4, 3, 66 * 129, [0, 0, 0], PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "d_carry is NULL", fn, None, None, 0, PTR, 4, 3, 64, [0, 2, 0], PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "16-byte aligned", fn, None, PTR + 4, 0, PTR, 4, 3, 64, [0, 2, 0], PTR)
+    _expect(B.BLINK_ERR_INVALID_ARG, "h_n_out is NULL", fn, None, PTR, 0, None, 4, 3, 64, [0, 2, 0], PTR)
+    # a delay longer than the cube is allowed here (the carry spans cubes); no carry is needed for zero delays
+    _expect(*NO_CTX, fn, None, PTR, 0, PTR, 4, 3, 64, [0, 9, 1], PTR)
+    _expect(*NO_CTX, fn, None, None, 5, PTR, 4, 3, 1200, [0, 0, 0], PTR)
+    with pytest.raises(ValueError):
+        fn(None, PTR, 0, PTR, 4, 3, 64, [0, 1], PTR)     # one delay per channel, checked by the binding
+
+
 def test_pipeline_host_arguments():
     a, o, i = B.Array(_enu()), _obs(), B.Imaging(64)
     h_volt = np.zeros(16, np.uint8)
