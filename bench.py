@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--samples", type=int, default=0, help="voltage samples per step (default: the 50 ms chunk)")
+    ap.add_argument("--int-samples", type=int, default=0,
+                    help="samples per integration (default: the workload's; e.g. 200 gives the paper's 20 ms "
+                         "integrations, K = 800 on the full-band workload)")
     ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "coarse", "precision", "uneven", "fullband"])
     ap.add_argument("--n-pix", type=int, default=0,
                     help="image side for every channel set instead of the workload's (e.g. 1200, 8192)")
@@ -144,6 +147,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_bf16():
+    """Dense BF16 GEMM TFLOP/s measured on this machine's GPUs (burst), else the fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            v = json.load(f).get("bf16_tflops")
+        if v:
+            return float(v), "measured"
+    return 1900.0, "fallback"
+
+
 def fast_side(n: int) -> bool:
     """Sides the side-specialised kernels cover (the others run the two mixed-radix passes)."""
     return 64 <= n <= 2048 and n & (n - 1) == 0
@@ -203,11 +217,28 @@ def traffic_for(kernel: str, source: str, shape=None, side=None):
 # the reference arm: the CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------------------------------
 
+def workload_of(args):
+    """The workload, with the integration length of --int-samples, and the samples of one step (a whole number
+    of integrations)."""
+    import dataclasses
+    import blinksynth as bs
+    w = bs.WORKLOADS[args.workload]
+    if args.int_samples:
+        if args.int_samples < 1:
+            raise SystemExit("--int-samples must be >= 1")
+        w = dataclasses.replace(w, samples_per_int=args.int_samples)
+    ns = args.samples or (w.samples_per_chunk // w.samples_per_int) * w.samples_per_int
+    if ns < w.samples_per_int or ns % w.samples_per_int:
+        raise SystemExit("the samples of a step must be a positive multiple of the samples per integration")
+    return w, ns
+
+
 def workload_label(name: str, w, n_pix=0) -> str:
     if name == "fullband":
         side = n_pix or 512
+        T = w.samples_per_chunk // w.samples_per_int
         return ("fullband: 50 ms chunk, 144 tiles x 2 pol, 768 x 40 kHz (10 kHz averaged by 4), "
-                f"50 x 1 ms (K = 40), {side}^2 Stokes-I images")
+                f"{T} x {w.samples_per_int * 0.1:g} ms (K = {w.k}), {side}^2 Stokes-I images")
     return f"{name}: {w.description}" + (f"; imaged at {n_pix}^2" if n_pix else "")
 
 
@@ -216,7 +247,8 @@ def bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes):
     L2_BYTES = 129 * 2 ** 20
     small = in_bytes + out_bytes < 2 * L2_BYTES
     return {"workload": workload_label(args.workload, w, args.n_pix), "n_pix": args.n_pix or None,
-            "images_per_step": n_img, "samples_per_step": ns, "chunk": chunk, "arith": args.arith,
+            "images_per_step": n_img, "samples_per_step": ns, "samples_per_int": w.samples_per_int, "K": w.k,
+            "chunk": chunk, "arith": args.arith,
             "mode": args.mode, "precision": args.precision, "gains": bool(args.gains), "fused": bool(args.fused),
             "jones": bool(args.jones), "support": args.support, "pointing": list(args.pointing),
             "average": list(args.average) if args.average else None,
@@ -292,9 +324,8 @@ def run_reference(args, world, rank):
         return 0
     import blinksynth as bs
     import oracle
-    w = bs.WORKLOADS[args.workload]
+    w, ns = workload_of(args)
     cores = args.cpu_threads or os.cpu_count() or 1
-    ns = args.samples or w.samples_per_chunk
     chunk = min(4, w.n_chunks - 1)
     inp = bs.build_workload(args.workload, chunk=chunk, workers=min(16, os.cpu_count() or 1), n_samples=ns)
     sets = image_sets(inp, w, ns, args.n_pix)
@@ -337,9 +368,8 @@ def run_reference(args, world, rank):
 
 def run_ours(args, world, rank, local):
     import blinksynth as bs
-    w = bs.WORKLOADS[args.workload]
+    w, ns = workload_of(args)
     cores = args.cpu_threads or os.cpu_count() or 1
-    ns = args.samples or w.samples_per_chunk
     from paper_2505_15204_gb300.shard import chunks_for_rank, job_rate, max_over_ranks
     chunk = chunks_for_rank(w.n_chunks, rank, world, first=min(4, w.n_chunks - 1))[0]
     t_gen = time.perf_counter()
@@ -486,6 +516,24 @@ def run_ours(args, world, rank, local):
                 "traffic": traffic, "kernel": kern, "stage": names[dom],
                 "bytes_per_launch": per_launch, "avg_launch_ms": avg_s * 1e3, "peak_kind": f"{peak_kind} hbm_gbs",
                 "tuned_shape": {"ring": shape[0], "lag": shape[1], "ctas_per_sm": shape[2]}}
+    # the correlation against both of its bounds: the FP8 tensor peak (the measured BF16 GEMM peak times the
+    # nominal FP8 / BF16 ratio of 2) on the method's flops, 8 per complex product and polarisation, XX and YY
+    # for Stokes I (16 B K per image, 8 B K for XX), and the HBM copy peak on its bytes
+    corr_roof = None
+    if stage_n[0] and arith == B.BLINK_CORR_FP8 and not avg:
+        Bn = n_tiles * (n_tiles + 1) // 2
+        flops = (16 if im.pol == B.BLINK_POL_I else 8) * Bn * K * n_img * args.steps
+        t_s = stage_ms[0] / 1e3
+        bf16, kind16 = measured_bf16()
+        tf_peak = 2.0 * bf16
+        tf = flops / t_s / 1e12
+        gbs = set_bytes(0) * args.steps / t_s / 1e9
+        t_tensor, t_hbm = flops / (tf_peak * 1e12), set_bytes(0) / (peak * 1e9)
+        corr_roof = {"bound": "tensor" if t_tensor >= t_hbm else "hbm", "kernel": "k_corr_tc", "K": K,
+                     "tensor": {"achieved": tf, "peak": tf_peak, "unit": "TFLOP/s", "frac": tf / tf_peak,
+                                "peak_kind": f"{kind16} bf16_tflops x 2 (nominal fp8 / bf16 ratio)"},
+                     "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak},
+                     "flops_per_image": flops / (n_img * args.steps), "bytes_per_image": set_bytes(0) / n_img}
     stages = {STAGE_NAMES[s]: {"ms_per_step": stage_ms[s] / args.steps, "launches_per_step": stage_n[s] / args.steps,
                                "GBps": (set_bytes(s) * args.steps / (stage_ms[s] / 1e3) / 1e9)
                                if stage_ms[s] else None}
@@ -641,7 +689,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": bench_config(args, w, ns, chunk, n_img, in_bytes, out_bytes),
         "setup_s": {"generate": round(t_gen, 2), "plan": round(t_plan, 3)},
-        "roofline": roof, "stages": stages, "clocks": clocks, "gpu_launches": launches,
+        "roofline": roof, "corr_roofline": corr_roof, "stages": stages, "clocks": clocks, "gpu_launches": launches,
         "cpu_baseline": cpu, "parity": parity, "e2e": e2e, "comparison": comparison, "dedisperse": dedisp,
         "baselines_per_s": value * (n_tiles * (n_tiles + 1) // 2),
         "xx_yy_products_per_s": value * (n_tiles * (n_tiles + 1) // 2) * 2,
