@@ -66,7 +66,9 @@ struct TcParams {
     ImgOut io;               // imaging kinds in baseline order: phase-centre factor
     // imaging kinds in gather order: the item's sums go from TMEM to a baseline-ordered copy in shared memory
     // (planes re | im of B floats at off_item), then leave in gather order (p -> baseline gsrc[f][p])
-    uint32_t off_item;       // 0: baseline order
+    int gathered;            // 0: baseline order
+    int overlay;             // the item's copy shares the operand tiles' space (set by tc_chunk)
+    uint32_t off_item;       // (0 when the copy shares the operand tiles' space)
     const uint16_t* gsrc;
     const float2* gphase;
     const int* ent_off;      // [F][ent_ld]: entry range of each channel (last column's end = its count)
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
     float2* s_g = reinterpret_cast<float2*>(smem + P.off_gain);
     uint32_t* lut = reinterpret_cast<uint32_t*>(smem + P.off_lut);   // raw byte -> e4m3 (re, im, im, -re)
     uint8_t* sflags = smem + P.off_flags;
-    float* s_item = P.off_item ? reinterpret_cast<float*>(smem + P.off_item) : nullptr;
+    float* s_item = P.gathered ? reinterpret_cast<float*>(smem + P.off_item) : nullptr;
     const uint32_t bar_tma0 = smem_u32(smem + P.off_bar), bar_tma1 = bar_tma0 + 8, bar_mma = bar_tma0 + 16;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + P.off_tmem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -494,6 +496,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                     o[P.e_stride + pp] = im;
                 }
             }
+            if (P.overlay) {
+                // the copy lay over the operand tiles: zero them again for the next item (the unpack writes only
+                // the live rows and K positions)
+                __syncthreads();
+                uint4* z = reinterpret_cast<uint4*>(smem);
+                const int n16 = (int)((2 * P.B * sizeof(float) + 15) / 16);
+                for (int e = tid; e < n16; e += kThreads) z[e] = make_uint4(0, 0, 0, 0);
+            }
         }
     }
     if (abort) {
@@ -539,7 +549,14 @@ size_t tc_layout(TcParams& P, int ns_c, bool gather, GainRef gains, int64_t B) {
     P.Kr = (P.mode == CORR_OUT_STOKES_I && !four) ? 4 * P.Kq : 2 * P.Kq;
     P.Kp = P.split ? 2 * P.Kpol : (P.Kr + 31) / 32 * 32;
     P.raw_bytes = ns_c * P.c * nt * 2;
-    uint32_t off = align_up((uint32_t)P.n_blk * 128u * P.Kp, 1024);
+    // P.overlay (gather order, one round of block pairs, chosen by tc_chunk when K does not fit otherwise): the
+    // item's baseline-ordered copy is written only after the item's last MMAs have completed and read before
+    // the next item's unpack, so it can share the operand tiles' space (longer chunks: fewer barriers per item);
+    // the kernel zeroes that space again after reading the copy, since the unpack never writes the tiles'
+    // padding
+    const bool overlay = gather && P.n_rounds == 1 && P.overlay;
+    const uint32_t ops_bytes = (uint32_t)P.n_blk * 128u * P.Kp;
+    uint32_t off = align_up(overlay ? std::max(ops_bytes, (uint32_t)(8 * B)) : ops_bytes, 1024);
     P.off_raw0 = off;
     off = align_up(off + P.raw_bytes, 128);
     P.off_raw1 = off;
@@ -549,7 +566,11 @@ size_t tc_layout(TcParams& P, int ns_c, bool gather, GainRef gains, int64_t B) {
     const uint32_t gain_bytes = gains.d ? (uint32_t)nt * (gains.full ? 32 : 16) : 0;
     const uint32_t tail = 256 * 4 + align_up((uint32_t)nt, 16) + 32 + (gains.d ? gain_bytes + 16 : 0);
     P.off_item = 0;
-    if (gather) {
+    P.gathered = gather ? 1 : 0;
+    if (overlay) {
+        P.off_item = 0;
+        P.two_stage = 0;
+    } else if (gather) {
         // gather order: the item's baseline-ordered copy takes the staging buffers' place
         P.off_item = off;
         off = align_up(off + (uint32_t)(8 * B), 16);
@@ -599,12 +620,19 @@ bool tc_setup(TcParams& P, int out_kind, const Plan& p, int ns, GainRef gains) {
     return bound * P.K < ((int64_t)1 << 24);
 }
 
-// The largest chunk (samples, at most 256: the TMA box) whose layout fits; 0 if none does.
+// The chunk (samples, at most 256: the TMA box) of the fewest chunks whose layout fits; 0 if none does.
 int tc_chunk(TcParams& P, bool gather, GainRef gains, int64_t B) {
-    for (int ns_c = std::min(P.ns, 256);; ns_c = (ns_c + 1) / 2) {
-        if (tc_layout(P, ns_c, gather, gains, B) <= 227 * 1024) return ns_c;
-        if (ns_c == 1) return 0;
+    P.overlay = 0;
+    if (tc_layout(P, std::min(P.ns, 256), gather, gains, B) <= 227 * 1024) return std::min(P.ns, 256);
+    P.overlay = gather && P.n_rounds == 1 ? 1 : 0;
+    // the longest chunk that fits, then the same number of chunks balanced (equal lengths but the last)
+    for (int ns_c = std::min(P.ns, 256); ns_c >= 1; ns_c--) {
+        if (tc_layout(P, ns_c, gather, gains, B) <= 227 * 1024) {
+            const int n = (P.ns + ns_c - 1) / ns_c;
+            return (P.ns + n - 1) / n;
+        }
     }
+    return 0;
 }
 
 }  // namespace
