@@ -263,18 +263,30 @@ constexpr int COL_CW = 8;                  // u columns per column-pass CTA (one
 // Complex sums and differences as one packed two-lane FP32 instruction (add.rn.f32x2 / sub.rn.f32x2 of
 // Blackwell): each lane is the same round-to-nearest FP32 addition as the scalar form, so results are
 // unchanged while the butterflies issue half as many instructions.
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+// (Host versions of these and of the register DFTs below exist so that transform plans can be checked on a
+// CPU; they compute the same sums with scalar operations.)
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
     unsigned long long r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*reinterpret_cast<unsigned long long*>(&a)),
         "l"(*reinterpret_cast<unsigned long long*>(&b)));
     return *reinterpret_cast<float2*>(&r);
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
 }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }     // a * i
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cmul_i(float2 a) { return make_float2(-a.y, a.x); }     // a * i
+__host__ __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
 // storage of complex values in shared or global memory: FP32 pairs or BF16 pairs
 __device__ __forceinline__ float2 ld_c(const float2* p) { return *p; }
@@ -283,17 +295,17 @@ __device__ __forceinline__ void st_c(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void st_c(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
 
 // Unnormalised inverse DFT of R points in registers: v[q] <- sum_r v[r] exp(+2 pi i r q / R).
-template <int R> __device__ __forceinline__ void idft(float2* v);
+template <int R> __host__ __device__ __forceinline__ void idft(float2* v);
 
-template <> __device__ __forceinline__ void idft<1>(float2*) {}
+template <> __host__ __device__ __forceinline__ void idft<1>(float2*) {}
 
-template <> __device__ __forceinline__ void idft<2>(float2* v) {
+template <> __host__ __device__ __forceinline__ void idft<2>(float2* v) {
     float2 a = cadd(v[0], v[1]), b = csub(v[0], v[1]);
     v[0] = a;
     v[1] = b;
 }
 
-template <> __device__ __forceinline__ void idft<4>(float2* v) {
+template <> __host__ __device__ __forceinline__ void idft<4>(float2* v) {
     float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
     float2 a2 = cadd(v[1], v[3]), a3 = cmul_i(csub(v[1], v[3]));
     v[0] = cadd(a0, a2);
@@ -302,7 +314,7 @@ template <> __device__ __forceinline__ void idft<4>(float2* v) {
     v[3] = csub(a1, a3);
 }
 
-template <> __device__ __forceinline__ void idft<3>(float2* v) {
+template <> __host__ __device__ __forceinline__ void idft<3>(float2* v) {
     // w = exp(2 pi i / 3) = -1/2 + i sqrt(3)/2: v1 w^q + v2 w^2q = -(v1 + v2)/2 +- i sqrt(3)/2 (v1 - v2)
     const float h = 0.86602540378443864676f;
     const float2 t = cadd(v[1], v[2]), d = csub(v[1], v[2]);
@@ -313,7 +325,7 @@ template <> __device__ __forceinline__ void idft<3>(float2* v) {
     v[2] = csub(m, r);
 }
 
-template <> __device__ __forceinline__ void idft<5>(float2* v) {
+template <> __host__ __device__ __forceinline__ void idft<5>(float2* v) {
     // w = exp(2 pi i / 5); with a1 = v1 + v4, b1 = v1 - v4, a2 = v2 + v3, b2 = v2 - v3:
     // X1, X4 = v0 + c1 a1 + c2 a2 +- i (s1 b1 + s2 b2);  X2, X3 = v0 + c2 a1 + c1 a2 +- i (s2 b1 - s1 b2)
     // where c1 = cos(2 pi/5) = (sqrt 5 - 1)/4, c2 = cos(4 pi/5) = -(sqrt 5 + 1)/4, s1 = sin(2 pi/5), s2 = sin(4 pi/5)
@@ -331,7 +343,7 @@ template <> __device__ __forceinline__ void idft<5>(float2* v) {
     v[3] = csub(p2, q2);
 }
 
-template <> __device__ __forceinline__ void idft<8>(float2* v) {
+template <> __host__ __device__ __forceinline__ void idft<8>(float2* v) {
     // radix-2 split into the 4-point transforms of the even and odd samples
     float2 a0 = cadd(v[0], v[4]), a1 = csub(v[0], v[4]);
     float2 a2 = cadd(v[2], v[6]), a3 = cmul_i(csub(v[2], v[6]));
@@ -354,7 +366,7 @@ template <> __device__ __forceinline__ void idft<8>(float2* v) {
     v[7] = csub(e3, t3);
 }
 
-template <> __device__ __forceinline__ void idft<16>(float2* v) {
+template <> __host__ __device__ __forceinline__ void idft<16>(float2* v) {
     // 4 x 4: 4-point transforms over r1 of v[4 r1 + r2], twiddles exp(2 pi i r2 q1 / 16), then 4-point
     // transforms over r2, giving v[q1 + 4 q2]
     const float c = 0.92387953251128675613f, s = 0.38268343236508977173f, h = 0.70710678118654752440f;
@@ -385,6 +397,28 @@ template <> __device__ __forceinline__ void idft<16>(float2* v) {
         v[q1 + 4] = t[1];
         v[q1 + 8] = t[2];
         v[q1 + 12] = t[3];
+    }
+}
+
+// 15 points in the prime-factor form (15 = 3 x 5, coprime factors, so no twiddles): input x[(5 n1 + 3 n2) mod 15]
+// goes through 3-point transforms over n1 for every n2, then 5-point transforms over n2 for every k1, and the
+// output of (k1, k2) is X[(10 k1 + 6 k2) mod 15] (10 = 1 mod 3, 0 mod 5; 6 = 0 mod 3, 1 mod 5).
+template <> __host__ __device__ __forceinline__ void idft<15>(float2* v) {
+    float2 a[5][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 5; n2++) {
+#pragma unroll
+        for (int n1 = 0; n1 < 3; n1++) a[n2][n1] = v[(5 * n1 + 3 * n2) % 15];
+        idft<3>(a[n2]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; k1++) {
+        float2 b[5];
+#pragma unroll
+        for (int n2 = 0; n2 < 5; n2++) b[n2] = a[n2][k1];
+        idft<5>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < 5; k2++) v[(10 * k1 + 6 * k2) % 15] = b[k2];
     }
 }
 

@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "blink_internal.cuh"
+#include "fft_ct.cuh"
 
 namespace blink {
 
@@ -143,30 +144,44 @@ struct MixedCol {
     int ldh, y0, ny;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_col(const MixedCol P) {
+// FIX = 1200: the side-1200 form, fixed plan (fft_ct.cuh): 80 threads per column, cw columns per CTA, columns
+// unpadded in slots of kFixLd, the unit roots of 1200 copied to shared memory after the buffers.
+constexpr int kFixLd = 1280;                       // column slots: >= kCol1200Slots, even
+constexpr int kFixRowLd = 680;                     // row slots: >= kRow600Slots, even
+constexpr int kFixCols = 4;                        // columns per CTA of the side-1200 column pass
+constexpr int kFixRows = 8;                        // rows per CTA of the side-1200 row pass
+
+template <typename T, int FIX>
+__global__ void __launch_bounds__(FIX ? kFixCols * kCol1200Threads : kMaxThreads / 2, 2) k_mixed_col(const MixedCol P) {
     extern __shared__ float2 s[];          // [cw][ld] transform inputs, then [cw][ld] the second buffers
     const int img = blockIdx.y, tid = threadIdx.x, nthr = blockDim.x;
-    const int cw = 1 << P.cw_log, u0 = blockIdx.x * cw;
+    static_assert(!FIX || kFixCols == 4, "the side-1200 form takes four columns per CTA");
+    const int cw_log = FIX ? 2 : P.cw_log;
+    const int cw = 1 << cw_log, u0 = blockIdx.x * cw;
     const int ncol = min(cw, P.half + 1 - u0);
+    const int ld = FIX ? kFixLd : P.ld;
+    auto pv = [&](int v) { return FIX ? v : pd(v); };      // a point's slot in a column
+    float2* roots = s + 2 * cw * ld;
+    if constexpr (FIX != 0)
+        for (int e = tid; e < FIX; e += nthr) roots[e] = __ldg(P.tw + e);
     if (P.grid) {
         const float2* G = P.grid + (int64_t)img * P.N * (P.half + 1);
         for (int e = tid; e < P.N * cw; e += nthr) {
-            const int v = e >> P.cw_log, c = e & (cw - 1), u = u0 + c;
+            const int v = e >> cw_log, c = e & (cw - 1), u = u0 + c;
             float2 x = make_float2(0.f, 0.f);
             if (c < ncol) {
                 x = G[(int64_t)v * (P.half + 1) + u];
                 if ((u + v) & 1) x = make_float2(-x.x, -x.y);
             }
-            s[c * P.ld + pd(v)] = x;
+            s[c * ld + pv(v)] = x;
         }
     } else {
-        for (int e = tid; e < cw * P.ld; e += nthr) s[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < cw * ld; e += nthr) s[e] = make_float2(0.f, 0.f);
         __syncthreads();
         const int o = P.o_first + img;
         const int it0 = (o / P.Fo) * P.F + (o % P.Fo) * P.fa;
         const int lane = tid & 31;
-        auto idx = [&](int u, int v) { return (u - u0) * P.ld + pd(v); };
+        auto idx = [&](int u, int v) { return (u - u0) * ld + pv(v); };
         for (int m = 0; m < P.fa; m++) {           // members in a fixed order: reproducible sums
             const int it = it0 + m, f = (P.first + it) % P.F;
             const float2* V = P.vis + (int64_t)it * P.vstride;
@@ -188,13 +203,20 @@ __global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_col(const MixedCol
         }
     }
     __syncthreads();
-    const int c = tid / P.nt, t = tid - c * P.nt;
-    const float2* res = fft_any(s + c * P.ld, s + (cw + c) * P.ld, P.N, P.rad, P.n_rad, P.tw, 1, t, P.nt);
-    const int off = (int)(res - (s + c * P.ld));      // the result buffer's offset, the same for every column
+    int off;                                          // the result buffer's offset, the same for every column
+    if constexpr (FIX == 1200) {
+        const int c = tid / kCol1200Threads, t = tid - c * kCol1200Threads;
+        fft1200_cols(s + c * ld, s + (cw + c) * ld, roots, t, [] { __syncthreads(); });
+        off = cw * ld;
+    } else {
+        const int c = tid / P.nt, t = tid - c * P.nt;
+        const float2* res = fft_any(s + c * ld, s + (cw + c) * ld, P.N, P.rad, P.n_rad, P.tw, 1, t, P.nt);
+        off = (int)(res - (s + c * ld));
+    }
     T* H = static_cast<T*>(P.H) + (int64_t)img * P.ny * P.ldh + u0;
     for (int e = tid; e < P.ny * cw; e += nthr) {
-        const int r = e >> P.cw_log, cc = e & (cw - 1);
-        if (cc < ncol) st_c(H + (int64_t)r * P.ldh + cc, s[off + cc * P.ld + pd(P.y0 + r)]);
+        const int r = e >> cw_log, cc = e & (cw - 1);
+        if (cc < ncol) st_c(H + (int64_t)r * P.ldh + cc, s[off + cc * ld + pv(P.y0 + r)]);
     }
 }
 
@@ -217,23 +239,34 @@ struct MixedRow {
 // With M = N/2 and the half spectrum Z[0..M] of a row, x[n] = sum_k Z[k] exp(+2 pi i k n / N) for the real
 // sequence x is x[2m] = Re y[m], x[2m+1] = Im y[m] with y the M-point inverse transform of
 // Y[k] = (Z[k] + conj Z[M-k]) + i (Z[k] - conj Z[M-k]) exp(+2 pi i k / N)  (any M, odd included).
-template <typename T>
-__global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_row(const MixedRow P) {
+template <typename T, int FIX>
+__global__ void __launch_bounds__(FIX ? kFixRows * kRow600Threads : kMaxThreads / 2, 2) k_mixed_row(const MixedRow P) {
     extern __shared__ float2 s[];          // [rb][ld] transform inputs, then [rb][ld] the second buffers
     const int img = blockIdx.y, tid = threadIdx.x;
-    const int r = tid / P.nt, t = tid - r * P.nt, y = blockIdx.x * P.rb + r;
-    const int M = P.M;
-    float2* dst = s + r * P.ld;
+    const int nt = FIX ? kRow600Threads : P.nt, rb = FIX ? kFixRows : P.rb, ld = FIX ? kFixRowLd : P.ld;
+    const int r = tid / nt, t = tid - r * nt, y = blockIdx.x * rb + r;
+    const int M = FIX ? FIX / 2 : P.M;
+    auto pv = [&](int k) { return FIX ? k : pd(k); };
+    float2* roots = s + 2 * rb * ld;                 // FIX: exp(+2 pi i x / M), x < M
+    if constexpr (FIX != 0)
+        for (int e = tid; e < M; e += blockDim.x) roots[e] = __ldg(P.tw + 2 * e);
+    float2* dst = s + r * ld;
     const T* row = static_cast<const T*>(P.H) + ((int64_t)img * P.ny + y) * P.ldh;
-    for (int k = t; k <= M / 2; k += P.nt) {
+    for (int k = t; k <= M / 2; k += nt) {
         const float2 zk = ld_c(row + k);
         const float2 zm = (k == 0) ? (P.has_nyq ? ld_c(row + M) : make_float2(0.f, 0.f)) : ld_c(row + (M - k));
-        dst[pd(k)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), __ldg(P.tw + k))));
+        dst[pv(k)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), __ldg(P.tw + k))));
         if (k > 0 && k < M - k)
-            dst[pd(M - k)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), __ldg(P.tw + (M - k)))));
+            dst[pv(M - k)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), __ldg(P.tw + (M - k)))));
     }
     __syncthreads();
-    const float2* res = fft_any(dst, s + (P.rb + r) * P.ld, M, P.rad, P.n_rad, P.tw, 2, t, P.nt);
+    const float2* res;
+    if constexpr (FIX == 1200) {
+        fft600_rows(dst, s + (rb + r) * ld, roots, t, [] { __syncthreads(); });
+        res = s + (rb + r) * ld;
+    } else {
+        res = fft_any(dst, s + (rb + r) * ld, M, P.rad, P.n_rad, P.tw, 2, t, nt);
+    }
     const int id = P.wm.id(img);
     const float w = P.wts ? P.wts[id % P.w_mod] : 1.f;
     float scale = 1.0f / (w > 0.f ? w : 1.f);
@@ -242,15 +275,15 @@ __global__ void __launch_bounds__(kMaxThreads / 2, 2) k_mixed_row(const MixedRow
     if (!P.corr && (P.nout & 3) == 0 && (reinterpret_cast<uintptr_t>(P.img) & 15) == 0) {
         // whole rows (x0 = 0) on a 16-byte aligned output: four pixels, two results y[m], per 16-byte store
         float4* o4 = reinterpret_cast<float4*>(out);
-        for (int q = t; q < P.nout / 4; q += P.nt) {
-            const float2 a = res[pd(2 * q)], b = res[pd(2 * q + 1)];
+        for (int q = t; q < P.nout / 4; q += nt) {
+            const float2 a = res[pv(2 * q)], b = res[pv(2 * q + 1)];
             o4[q] = make_float4(a.x * scale, a.y * scale, b.x * scale, b.y * scale);
         }
         return;
     }
-    for (int x = t; x < P.nout; x += P.nt) {
+    for (int x = t; x < P.nout; x += nt) {
         const int X = P.x0 + x;
-        const float2 z = res[pd(X >> 1)];
+        const float2 z = res[pv(X >> 1)];
         const float a = (X & 1) ? z.y : z.x;
         out[x] = P.corr ? a * scale * P.corr[x] : a * scale;
     }
@@ -363,14 +396,28 @@ blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, v
         C.ldh = (int)mixed_h_row(N);
         C.y0 = y0;
         C.ny = ny;
+        if (N == 1200) {
+            // the fixed plan: four columns of 80 threads per CTA, the unit roots beside the buffers
+            const dim3 g((N / 2 + 1 + kFixCols - 1) / kFixCols, n_images);
+            const size_t smem = (size_t)(2 * kFixCols * kFixLd + 1200) * sizeof(float2);
+            if (bf16) {
+                BLINK_TRY(kernel_smem((const void*)k_mixed_col<__nv_bfloat162, 1200>, smem));
+                k_mixed_col<__nv_bfloat162, 1200><<<g, kFixCols * kCol1200Threads, smem, st>>>(C);
+            } else {
+                BLINK_TRY(kernel_smem((const void*)k_mixed_col<float2, 1200>, smem));
+                k_mixed_col<float2, 1200><<<g, kFixCols * kCol1200Threads, smem, st>>>(C);
+            }
+            BLINK_CUDA(cudaGetLastError());
+            return BLINK_OK;
+        }
         const int cw = 1 << sh.cw_log;
         const dim3 g((N / 2 + 1 + cw - 1) / cw, n_images);
         if (bf16) {
-            BLINK_TRY(kernel_smem((const void*)k_mixed_col<__nv_bfloat162>, sh.smem_c));
-            k_mixed_col<__nv_bfloat162><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
+            BLINK_TRY(kernel_smem((const void*)k_mixed_col<__nv_bfloat162, 0>, sh.smem_c));
+            k_mixed_col<__nv_bfloat162, 0><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
         } else {
-            BLINK_TRY(kernel_smem((const void*)k_mixed_col<float2>, sh.smem_c));
-            k_mixed_col<float2><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
+            BLINK_TRY(kernel_smem((const void*)k_mixed_col<float2, 0>, sh.smem_c));
+            k_mixed_col<float2, 0><<<g, sh.nt_c * cw, sh.smem_c, st>>>(C);
         }
     } else {
         MixedRow R{};
@@ -394,14 +441,28 @@ blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, v
         R.nout = ny;
         R.corr = in.corr;
         R.img = d_img;
+        if (N == 1200 && ny % kFixRows == 0) {
+            // the fixed plan: eight rows of 40 threads per CTA, the unit roots of 600 beside the buffers
+            const dim3 g(ny / kFixRows, n_images);
+            const size_t smem = (size_t)(2 * kFixRows * kFixRowLd + 600) * sizeof(float2);
+            if (bf16) {
+                BLINK_TRY(kernel_smem((const void*)k_mixed_row<__nv_bfloat162, 1200>, smem));
+                k_mixed_row<__nv_bfloat162, 1200><<<g, kFixRows * kRow600Threads, smem, st>>>(R);
+            } else {
+                BLINK_TRY(kernel_smem((const void*)k_mixed_row<float2, 1200>, smem));
+                k_mixed_row<float2, 1200><<<g, kFixRows * kRow600Threads, smem, st>>>(R);
+            }
+            BLINK_CUDA(cudaGetLastError());
+            return BLINK_OK;
+        }
         if (ny % sh.rb) return set_error(BLINK_ERR_UNSUPPORTED, "row blocking of the mixed-radix row pass");
         const dim3 g(ny / sh.rb, n_images);
         if (bf16) {
-            BLINK_TRY(kernel_smem((const void*)k_mixed_row<__nv_bfloat162>, sh.smem_r));
-            k_mixed_row<__nv_bfloat162><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
+            BLINK_TRY(kernel_smem((const void*)k_mixed_row<__nv_bfloat162, 0>, sh.smem_r));
+            k_mixed_row<__nv_bfloat162, 0><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
         } else {
-            BLINK_TRY(kernel_smem((const void*)k_mixed_row<float2>, sh.smem_r));
-            k_mixed_row<float2><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
+            BLINK_TRY(kernel_smem((const void*)k_mixed_row<float2, 0>, sh.smem_r));
+            k_mixed_row<float2, 0><<<g, sh.nt_r * sh.rb, sh.smem_r, st>>>(R);
         }
     }
     BLINK_CUDA(cudaGetLastError());
