@@ -805,8 +805,8 @@ int64_t sample_stride_bytes(const blink_obs* o, int n_tiles) {
 constexpr size_t kVisCapBytes = (size_t)4 << 30;
 
 // Batched path on a side outside the side-specialised kernels, and every averaged call: one correlator
-// launch per chunk of integrations, then per wave of output images (their column results sized to stay in
-// L2) the mixed-radix column pass, gathering each output's cells from the sums of its fa channels, and the
+// launch per chunk of integrations, then per wave of output images (their column results about the size of
+// L2: 96 MB measured a little faster than 48 MB at side 1200, with half the launches) the mixed-radix column pass, gathering each output's cells from the sums of its fa channels, and the
 // row pass (fft_mixed.cu).  fa = 1: one image per (integration, channel), divided by W in the row pass;
 // fa > 1: the mean of fa consecutive channels' normalised images, each channel's sums divided by its own
 // W in the gather.  Outputs [tau0 F/fa, tau1 F/fa) are written from d_img on.
@@ -820,7 +820,7 @@ blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, in
     const bool crop = p.support != 0;
     const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
     const size_t per_img = (size_t)(crop ? p.N / 2 : p.N) * mixed_h_row(p.N) * el;
-    const int wave = (int)std::max<size_t>(1, std::min<size_t>(65535, ((size_t)48 << 20) / per_img));
+    const int wave = (int)std::max<size_t>(1, std::min<size_t>(65535, ((size_t)96 << 20) / per_img));
     void* vis = nullptr;
     void* H = nullptr;
     BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));

@@ -252,12 +252,37 @@ __global__ void __launch_bounds__(FIX ? kFixRows * kRow600Threads : kMaxThreads 
         for (int e = tid; e < M; e += blockDim.x) roots[e] = __ldg(P.tw + 2 * e);
     float2* dst = s + r * ld;
     const T* row = static_cast<const T*>(P.H) + ((int64_t)img * P.ny + y) * P.ldh;
+    if constexpr (FIX != 0) {
+        // every load of the thread's share of the row first, then the pre-twiddles
+        constexpr int MF = FIX / 2, KN = (MF / 2 + kRow600Threads) / kRow600Threads;
+        float2 zk[KN], zm[KN], wk[KN], wm[KN];
+#pragma unroll
+        for (int i = 0; i < KN; i++) {
+            const int k = t + i * kRow600Threads;
+            if (k <= MF / 2) {
+                zk[i] = ld_c(row + k);
+                zm[i] = k == 0 ? (P.has_nyq ? ld_c(row + MF) : make_float2(0.f, 0.f)) : ld_c(row + (MF - k));
+                wk[i] = __ldg(P.tw + k);
+                wm[i] = __ldg(P.tw + (MF - k));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < KN; i++) {
+            const int k = t + i * kRow600Threads;
+            if (k <= MF / 2) {
+                dst[k] = cadd(cadd(zk[i], conjf2(zm[i])), cmul_i(cmul(csub(zk[i], conjf2(zm[i])), wk[i])));
+                if (k > 0 && k < MF - k)
+                    dst[MF - k] = cadd(cadd(zm[i], conjf2(zk[i])), cmul_i(cmul(csub(zm[i], conjf2(zk[i])), wm[i])));
+            }
+        }
+    } else {
     for (int k = t; k <= M / 2; k += nt) {
         const float2 zk = ld_c(row + k);
         const float2 zm = (k == 0) ? (P.has_nyq ? ld_c(row + M) : make_float2(0.f, 0.f)) : ld_c(row + (M - k));
         dst[pv(k)] = cadd(cadd(zk, conjf2(zm)), cmul_i(cmul(csub(zk, conjf2(zm)), __ldg(P.tw + k))));
         if (k > 0 && k < M - k)
             dst[pv(M - k)] = cadd(cadd(zm, conjf2(zk)), cmul_i(cmul(csub(zm, conjf2(zk)), __ldg(P.tw + (M - k)))));
+    }
     }
     __syncthreads();
     const float2* res;
