@@ -764,11 +764,16 @@ __device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict_
                 bl[q] = e.y;
             }
         }
+        // the values' loads are guarded by the entry index alone, so that with gather-ordered sums (val
+        // independent of the baseline) they are in flight together with the entries' loads
 #pragma unroll
         for (int q = 0; q < NB; q++) {
-            x[q] = make_float2(0.f, 0.f);
+            const int i = base + 32 * q + lane;
+            x[q] = i < end ? val(i, bl[q]) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
             if (key[q] != 0xFFFFFFFFu) {
-                x[q] = val(base + 32 * q + lane, bl[q]);
                 if (key[q] >> 31) x[q].y = -x[q].y;
                 key[q] = ent_cell(key[q]);
             }
