@@ -745,10 +745,11 @@ __device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__
 // value of entry i, whose baseline is b: with sums in baseline order it depends on the entry's load (two
 // dependent round trips per NB chunks), with gather-ordered sums only on i (one).  occ(u, v) is the
 // occupancy word of cell (u, v) (bit v / 32 of the word of v % 32 in its column).  Every run's sum is
-// multiplied by `scale` before it is stored (or added to the cell's earlier part).
-template <int NB, typename T, typename Val, typename Idx, typename Occ>
+// multiplied by `scale` before it is stored (or added to the cell's earlier part).  hook() runs once, while the
+// first batch's loads are in flight.
+template <int NB, typename T, typename Val, typename Idx, typename Occ, typename Hook>
 __device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
-                                                        Val val, Idx idx, Occ occ, float scale) {
+                                                        Val val, Idx idx, Occ occ, float scale, Hook hook) {
     uint32_t prev = 0xFFFFFFFFu;                    // the last cell of the previous chunk
     for (int base = beg; base < end; base += 32 * NB) {
         uint32_t key[NB], bl[NB];
@@ -771,6 +772,7 @@ __device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict_
             const int i = base + 32 * q + lane;
             x[q] = i < end ? val(i, bl[q]) : make_float2(0.f, 0.f);
         }
+        if (base == beg) hook();                    // the first batch's loads are in flight
 #pragma unroll
         for (int q = 0; q < NB; q++) {
             if (key[q] != 0xFFFFFFFFu) {

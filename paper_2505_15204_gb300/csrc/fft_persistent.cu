@@ -314,10 +314,10 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
-    // the ring slot's previous occupant, acquired now so that the load overlaps the gridding and transforms
+    // the ring slot's previous occupant, acquired while the gather's first loads are in flight (an acquire
+    // holds the warp's later loads until it completes, so it must not precede them)
     const int* prev = k >= P.ring ? P.row_done + (k - P.ring) : nullptr;
     int seen = 0;
-    if (lane == 0 && prev) seen = ld_acquire(prev);
     if (kVisAhead > 0 && tid == 0 && cb == 0 && k + kVisAhead < P.n_img && P.vis_prefetch) {
         const int k2 = k + kVisAhead, f2 = k2 / P.n_tau, id2 = (P.tau0 + k2 % P.n_tau) * P.F + f2;
         prefetch_l2(P.vis + (int64_t)(id2 - P.vis_first) * P.vis_stride, P.vis_prefetch);
@@ -346,7 +346,9 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
         __syncwarp();
         auto idx = [&](int u, int v) { return (2 * warp + (u - u0)) * LD + v; };
         auto occw = [&](int u, int v) { return occ + (u - u0) * 32 + (v & 31); };
-        warp_gather_occ_batched<4>(P.ent, off[u0], off[u0 + 2], lane, s, val, idx, occw, inv);
+        warp_gather_occ_batched<4>(P.ent, off[u0], off[u0 + 2], lane, s, val, idx, occw, inv, [&]() {
+            if (lane == 0 && prev) seen = ld_acquire(prev);
+        });
         __syncwarp();
         col512_pass1(s + 2 * warp * LD, lane, occ[lane]);
         col512_pass1(s + (2 * warp + 1) * LD, lane, occ[32 + lane]);
@@ -780,13 +782,17 @@ __global__ void __launch_bounds__(kPT, MINB) k_fft_persistent(const FftParams P)
     // publishes it in the other half of a two-entry slot (warps still reading this task's entry are not
     // disturbed).  One barrier ends each task; thread 0 releases the finished task's counter after it (the
     // fence orders the whole CTA's accesses of the task before the counter) while the other warps go on.
+    // The abort flag is read with the ticket request, so that its round trip too overlaps the task.
     if (tid == 0) s_ticket[0] = atomicAdd(P.tickets, 1);
     __syncthreads();
     for (int it = 0;; it ^= 1) {
         const int t = s_ticket[it];
         if (t >= total) break;
-        int nt = 0;
-        if (tid == 0) nt = atomicAdd(P.tickets, 1);
+        int nt = 0, ab = 0;
+        if (tid == 0) {
+            nt = atomicAdd(P.tickets, 1);
+            ab = ld_relaxed(P.tickets + 1);
+        }
         const int sg = t / seg, r0 = t - sg * seg;
         int* done = nullptr;
         if (fz && r0 == 0) {
@@ -819,7 +825,7 @@ __global__ void __launch_bounds__(kPT, MINB) k_fft_persistent(const FftParams P)
                 }
             }
         }
-        if (tid == 0) s_ticket[it ^ 1] = ld_relaxed(P.tickets + 1) ? total : nt;
+        if (tid == 0) s_ticket[it ^ 1] = ab ? total : nt;
         __syncthreads();
         if (tid == 0 && done) {
             __threadfence();
