@@ -34,6 +34,7 @@ namespace blink {
 namespace {
 
 constexpr int kThreads = 512;                   // 16 warps: four per TMEM lane quarter
+constexpr int kGatherIlp = 16;                  // gather-order pass: entries per thread in flight
 constexpr int kUnitsPerBlk = 64;
 constexpr int kTmemCols = 512;
 constexpr int kStageLd = 65;                     // padded row of the epilogue staging tiles (floats)
@@ -466,24 +467,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         cj = nj;
         if (!GAINS && s_item && last_chunk && (P.n_chunks == 1 || r_lo == P.n_rounds - 1)) {
             // the item in gather order: entry p of channel f takes baseline gsrc[f][p] (times the factor
-            // gphase[f][p] off zenith), four entries per thread in flight, coalesced stores of both planes
+            // gphase[f][p] off zenith), kGatherIlp entries per thread in flight (a 144-tile item's 10,440
+            // entries in two round trips), coalesced stores of both planes
             const int f = it % P.F;
             const int* eo = P.ent_off + (int64_t)f * P.ent_ld;
             const int n_f = eo[P.ent_ld - 1] - eo[0];
             const uint16_t* src = P.gsrc + (int64_t)f * P.e_stride;
             const float2* gph = P.gphase ? P.gphase + (int64_t)f * P.e_stride : nullptr;
             float* o = static_cast<float*>(P.out) + (int64_t)(it - P.first_item) * 2 * P.e_stride;
-            for (int p0 = tid; p0 < n_f; p0 += 4 * kThreads) {
-                uint32_t bb[4];
-                float2 w[4];
+            for (int p0 = tid; p0 < n_f; p0 += kGatherIlp * kThreads) {
+                uint32_t bb[kGatherIlp];
+                float2 w[kGatherIlp];
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < kGatherIlp; k++) {
                     const int pp = p0 + k * kThreads;
                     bb[k] = pp < n_f ? __ldg(src + pp) : 0u;
                     w[k] = (gph && pp < n_f) ? __ldg(gph + pp) : make_float2(1.f, 0.f);
                 }
 #pragma unroll
-                for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < kGatherIlp; k++) {
                     const int pp = p0 + k * kThreads;
                     if (pp >= n_f) break;
                     float re = s_item[bb[k]], im = s_item[P.B + bb[k]];
