@@ -214,36 +214,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         // P_re, P_im (= Q_im) and Q_-re of four consecutive K positions of one unit row.
         const uint8_t* raw = smem + (buf ? P.off_raw1 : P.off_raw0);
         const int n_groups = P.Kq >> 2;
-        for (int g = 0; g < n_groups; g++) {
+        // (group, row) tasks over all threads: a short K has fewer rows (2 n_tiles) than the CTA has threads
+        for (int e = tid; e < n_groups * per_k; e += kThreads) {
+            const int g = e / per_k, r = e - g * per_k;
             const int k0 = 4 * g;
-            for (int r = tid; r < per_k; r += kThreads) {
-                const int a = r >> 1, p = r & 1;
-                int unit, kp, kh;
-                if (GAINS && P.mode == CORR_OUT_STOKES_I && P.split) {
-                    unit = a; kp = p * P.Kpol + k0; kh = P.Kq;          // [re, im] of X, then of Y
-                } else if (P.mode == CORR_OUT_STOKES_I && !FULL) {
-                    unit = a; kp = p * P.Kq + k0; kh = 2 * P.Kq;        // re X, re Y, im X, im Y
-                } else if (P.mode == CORR_OUT_VIS4 || FULL) {
-                    unit = 2 * a + p; kp = k0; kh = P.Kq;
-                } else {
-                    if (p) continue;
-                    unit = a; kp = k0; kh = P.Kq;
-                }
-                // a flagged tile's operand rows are zero, so every product involving it is exactly zero
-                const bool live = !sflags[a];
-                uint32_t w[4];
-#pragma unroll
-                for (int i = 0; i < 4; i++) w[i] = (live && k0 + i < Kv) ? lut[raw[(k0 + i) * per_k + r]] : 0u;
-                const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], 0x0040), __byte_perm(w[2], w[3], 0x0040), 0x5410);
-                const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], 0x0051), __byte_perm(w[2], w[3], 0x0051), 0x5410);
-                const uint32_t nre = __byte_perm(__byte_perm(w[0], w[1], 0x0073), __byte_perm(w[2], w[3], 0x0073), 0x5410);
-                uint8_t* tile = ops + (unit >> 6) * tile_bytes;
-                const int row = unit & 63;
-                *reinterpret_cast<uint32_t*>(tile + op_off(row, kp, P.Kp)) = re;
-                *reinterpret_cast<uint32_t*>(tile + op_off(row, kp + kh, P.Kp)) = im;
-                *reinterpret_cast<uint32_t*>(tile + op_off(row + 64, kp, P.Kp)) = im;
-                *reinterpret_cast<uint32_t*>(tile + op_off(row + 64, kp + kh, P.Kp)) = nre;
+            const int a = r >> 1, p = r & 1;
+            int unit, kp, kh;
+            if (GAINS && P.mode == CORR_OUT_STOKES_I && P.split) {
+                unit = a; kp = p * P.Kpol + k0; kh = P.Kq;          // [re, im] of X, then of Y
+            } else if (P.mode == CORR_OUT_STOKES_I && !FULL) {
+                unit = a; kp = p * P.Kq + k0; kh = 2 * P.Kq;        // re X, re Y, im X, im Y
+            } else if (P.mode == CORR_OUT_VIS4 || FULL) {
+                unit = 2 * a + p; kp = k0; kh = P.Kq;
+            } else {
+                if (p) continue;
+                unit = a; kp = k0; kh = P.Kq;
             }
+            // a flagged tile's operand rows are zero, so every product involving it is exactly zero
+            const bool live = !sflags[a];
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) w[i] = (live && k0 + i < Kv) ? lut[raw[(k0 + i) * per_k + r]] : 0u;
+            const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], 0x0040), __byte_perm(w[2], w[3], 0x0040), 0x5410);
+            const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], 0x0051), __byte_perm(w[2], w[3], 0x0051), 0x5410);
+            const uint32_t nre = __byte_perm(__byte_perm(w[0], w[1], 0x0073), __byte_perm(w[2], w[3], 0x0073), 0x5410);
+            uint8_t* tile = ops + (unit >> 6) * tile_bytes;
+            const int row = unit & 63;
+            *reinterpret_cast<uint32_t*>(tile + op_off(row, kp, P.Kp)) = re;
+            *reinterpret_cast<uint32_t*>(tile + op_off(row, kp + kh, P.Kp)) = im;
+            *reinterpret_cast<uint32_t*>(tile + op_off(row + 64, kp, P.Kp)) = im;
+            *reinterpret_cast<uint32_t*>(tile + op_off(row + 64, kp + kh, P.Kp)) = nre;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
