@@ -272,11 +272,12 @@ __device__ __forceinline__ void idft32(float2 (&v)[32]) {
     }
 }
 
-// First pass of the 512-point column transform by one warp on a column of 512 unpadded slots (point v at
-// slot v; lane = j, points n = j + 32 r): the radix-16 DFT over r, with Y[j][k1] stored at the swizzled slot
-// 16 j + (k1 ^ (j & 15)), so that both these stores and the second pass's reads of Y[j][.] for 16
-// consecutive k1 touch 16 distinct 8-byte bank pairs.  The pass reads only the points `occ` marks (point
-// lane + 32 r: bit r) and treats the others as zero.
+// First pass of the 512-point column transform by one warp on a column of kCol512Ld slots whose first 512 hold
+// point v at slot v (lane = j, points n = j + 32 r): the radix-16 DFT over r, with Y[j][k1] stored at slot
+// 17 j + k1, so that both these stores (lanes j, fixed k1) and the second pass's reads of Y[.][b] (lanes b,
+// fixed j) touch 16 distinct 8-byte bank pairs per half-warp, at a base plus constant offsets.  The pass
+// reads only the points `occ` marks (point lane + 32 r: bit r) and treats the others as zero.
+constexpr int kCol512Ld = 32 * 17;
 template <typename T>
 __device__ __forceinline__ void col512_pass1(T* s, int lane, uint32_t occ) {
     float2 v[16];
@@ -284,9 +285,8 @@ __device__ __forceinline__ void col512_pass1(T* s, int lane, uint32_t occ) {
     for (int r = 0; r < 16; r++) v[r] = ((occ >> r) & 1u) ? ld_c(s + lane + 32 * r) : make_float2(0.f, 0.f);
     idft<16>(v);
     __syncwarp();
-    const int sw = lane & 15;
 #pragma unroll
-    for (int r = 0; r < 16; r++) st_c(s + 16 * lane + (r ^ sw), v[r]);
+    for (int r = 0; r < 16; r++) st_c(s + 17 * lane + r, v[r]);
 }
 
 // Complex-to-real pre-twiddle of one pair of row points (Eq. 4 on the Hermitian half plane): from G[q] = zk
@@ -310,7 +310,7 @@ __device__ __forceinline__ void pretw(float2& zk, float2& zm, float2 wq) {
 template <typename T, bool FUSED>
 __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* s_twc, unsigned char* work,
                                uint32_t* s_occ) {
-    constexpr int N = 512, M = N / 2, LD = N;             // unpadded columns (swizzled first pass)
+    constexpr int N = 512, M = N / 2, LD = kCol512Ld;     // columns: 512 points, then Y[j][k1] at 17 j + k1
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int f = k / P.n_tau, tau = P.tau0 + k % P.n_tau, id = tau * P.F + f;
     const int slot = k % P.ring;
@@ -355,10 +355,10 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
     }
     __syncwarp();
     const int b = lane & 15, c = lane >> 4;
-    const T* y = s + (2 * warp + c) * LD;             // Y[j][b] at 16 j + (b ^ (j & 15))
+    const T* y = s + (2 * warp + c) * LD + b;         // Y[j][b] at 17 j + b
     float2 v[32];
 #pragma unroll
-    for (int j = 0; j < 32; j++) v[j] = ld_c(y + 16 * j + (b ^ (j & 15)));
+    for (int j = 0; j < 32; j++) v[j] = ld_c(y + 17 * j);
 #pragma unroll
     for (int j = 1; j < 32; j++) v[j] = cmul(v[j], s_twc[16 * j + b]);
     idft32(v);
@@ -692,7 +692,7 @@ template <int N, typename T, bool WT> constexpr size_t fft_smem() {
     constexpr int M = N / 2;
     constexpr size_t col = (size_t)kCW * tile_ld<N>() * sizeof(T);
     if constexpr (ring_cm<N, WT>()) {
-        constexpr size_t col2 = (size_t)2 * kCW * N * sizeof(T);   // two unpadded columns per warp
+        constexpr size_t col2 = (size_t)2 * kCW * kCol512Ld * sizeof(T);   // two columns per warp
         constexpr size_t row = (size_t)32 * kRowLd * sizeof(float2);
         return (size_t)32 * 16 * sizeof(float2) + (col2 > row ? col2 : row);
     } else {
