@@ -746,23 +746,28 @@ __device__ __forceinline__ void warp_gather_column_occ(const uint2* __restrict__
 // dependent round trips per NB chunks), with gather-ordered sums only on i (one).  occ(u, v) is the
 // occupancy word of cell (u, v) (bit v / 32 of the word of v % 32 in its column).  Every run's sum is
 // multiplied by `scale` before it is stored (or added to the cell's earlier part).  hook() runs once, while the
-// first batch's loads are in flight.
+// first batch's loads are in flight.  With `wt` every entry's value is first multiplied by its weight wt[i] (a
+// convolution kernel's), loaded with the entry.
 template <int NB, typename T, typename Val, typename Idx, typename Occ, typename Hook>
 __device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict__ ent, int beg, int end, int lane, T* s,
-                                                        Val val, Idx idx, Occ occ, float scale, Hook hook) {
+                                                        Val val, Idx idx, Occ occ, float scale, Hook hook,
+                                                        const float* __restrict__ wt = nullptr) {
     uint32_t prev = 0xFFFFFFFFu;                    // the last cell of the previous chunk
     for (int base = beg; base < end; base += 32 * NB) {
         uint32_t key[NB], bl[NB];
         float2 x[NB];
+        float w[NB];
 #pragma unroll
         for (int q = 0; q < NB; q++) {
             const int i = base + 32 * q + lane;
             key[q] = 0xFFFFFFFFu;
             bl[q] = 0u;
+            w[q] = 1.0f;
             if (i < end) {
                 const uint2 e = ent[i];
                 key[q] = e.x;
                 bl[q] = e.y;
+                if (wt) w[q] = wt[i];
             }
         }
         // the values' loads are guarded by the entry index alone, so that with gather-ordered sums (val
@@ -777,6 +782,7 @@ __device__ __forceinline__ void warp_gather_occ_batched(const uint2* __restrict_
         for (int q = 0; q < NB; q++) {
             if (key[q] != 0xFFFFFFFFu) {
                 if (key[q] >> 31) x[q].y = -x[q].y;
+                if (wt) x[q] = make_float2(x[q].x * w[q], x[q].y * w[q]);
                 key[q] = ent_cell(key[q]);
             }
         }

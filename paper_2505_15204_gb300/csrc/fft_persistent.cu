@@ -587,21 +587,23 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     const int* off = P.ent_off + f * (N / 2 + 1);
     const int beg = off[u], end = off[u + 1];
     const float* wt = WT ? P.wt : nullptr;
-    uint32_t key;
-    float2 x;
-    gather_entry(P.ent, wt, beg + lane, end, val, key, x);    // in flight while the column is prepared
     if constexpr (N >= 256 && N <= 1024) {
-        // no zeroing: the gridding marks the cells it writes, and the first pass reads only those
+        // no zeroing: the gridding marks the cells it writes, and the first pass reads only those; the entries
+        // (and weights) of four chunks are loaded together, then their sums (baseline order: after the entries)
         uint32_t* occ = s_occ + warp * 32;
         occ[lane] = 0u;
         __syncwarp();
-        warp_gather_column_occ(P.ent, wt, beg, end, lane, s, val, idx, key, x, occ);
+        warp_gather_occ_batched<4>(P.ent, beg, end, lane, s, [&](int, uint32_t b) { return val(b); }, idx,
+                                   [&](int, int v) { return occ + (v & 31); }, 1.0f, [] {}, wt);
         __syncwarp();
         if constexpr (N == 512)
             warp_fft512(col, s_twc, lane, occ[lane]);
         else
             warp_fft_masked<N, T>(col, s_twc, lane, occ[lane]);
     } else {
+        uint32_t key;
+        float2 x;
+        gather_entry(P.ent, wt, beg + lane, end, val, key, x);    // in flight while the column is zeroed
         for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
         __syncwarp();
         warp_gather_column(P.ent, wt, beg, end, lane, s, val, idx, true, key, x);
