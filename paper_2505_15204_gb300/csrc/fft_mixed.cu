@@ -151,6 +151,69 @@ constexpr int kFixRowLd = 680;                     // row slots: >= kRow600Slots
 constexpr int kFixCols = 4;                        // columns per CTA of the side-1200 column pass
 constexpr int kFixRows = 8;                        // rows per CTA of the side-1200 row pass
 
+// The gather of a column CTA's columns from its output's members (fa consecutive channels, or the image's own
+// channel): a warp owns a column and adds the members' entries in member order, the members' column ranges,
+// first chunks of entries and their sums loaded G at a time.
+template <int G, typename Idx>
+__device__ __forceinline__ void gather_members(const MixedCol& P, int u0, int ncol, int it0, float2* s, Idx idx) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int c = tid >> 5; c < ncol; c += blockDim.x >> 5) {
+        const int u = u0 + c;
+        if (u >= P.half) continue;             // no cell reaches the Nyquist column
+        for (int m0 = 0; m0 < P.fa; m0 += G) {
+            int beg[G], end[G];
+            float sc[G];
+            const float2* V[G];
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                beg[g] = end[g] = 0;
+                sc[g] = 1.0f;
+                V[g] = P.vis;
+                if (m0 + g < P.fa) {
+                    const int it = it0 + m0 + g, f = (P.first + it) % P.F;
+                    const int* off = P.ent_off + (int64_t)f * (P.half + 1);
+                    beg[g] = off[u];
+                    end[g] = off[u + 1];
+                    V[g] = P.vis + (int64_t)it * P.vstride;
+                    if (P.wk) sc[g] = 1.0f / (fmaxf(P.wk[f], 1.0f) * (float)P.fa);
+                }
+            }
+            uint2 e[G];
+#pragma unroll
+            for (int g = 0; g < G; g++)
+                if (beg[g] + lane < end[g]) e[g] = P.ent[beg[g] + lane];
+            float2 xv[G];
+#pragma unroll
+            for (int g = 0; g < G; g++)
+                if (beg[g] + lane < end[g]) xv[g] = V[g][e[g].y];
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                if (m0 + g >= P.fa) break;
+                const float2* Vg = V[g];
+                const float scg = sc[g];
+                auto val = [&](uint32_t b) {
+                    const float2 x = Vg[b];
+                    return make_float2(x.x * scg, x.y * scg);
+                };
+                // the member's first chunk as gather_entry forms it, from the values loaded above
+                uint32_t key = 0xFFFFFFFFu;
+                float2 x = make_float2(0.f, 0.f);
+                const int i = beg[g] + lane;
+                if (i < end[g]) {
+                    key = ent_cell(e[g].x);
+                    x = make_float2(xv[g].x * scg, xv[g].y * scg);
+                    if (e[g].x >> 31) x.y = -x.y;
+                    if (P.wt) {
+                        const float w = P.wt[i];
+                        x = make_float2(x.x * w, x.y * w);
+                    }
+                }
+                warp_gather_column(P.ent, P.wt, beg[g], end[g], lane, s, val, idx, true, key, x);
+            }
+        }
+    }
+}
+
 template <typename T, int FIX>
 __global__ void __launch_bounds__(FIX ? kFixCols * kCol1200Threads : kMaxThreads / 2, 2) k_mixed_col(const MixedCol P) {
     extern __shared__ float2 s[];          // [cw][ld] transform inputs, then [cw][ld] the second buffers
@@ -180,27 +243,14 @@ __global__ void __launch_bounds__(FIX ? kFixCols * kCol1200Threads : kMaxThreads
         __syncthreads();
         const int o = P.o_first + img;
         const int it0 = (o / P.Fo) * P.F + (o % P.Fo) * P.fa;
-        const int lane = tid & 31;
         auto idx = [&](int u, int v) { return (u - u0) * ld + pv(v); };
-        for (int m = 0; m < P.fa; m++) {           // members in a fixed order: reproducible sums
-            const int it = it0 + m, f = (P.first + it) % P.F;
-            const float2* V = P.vis + (int64_t)it * P.vstride;
-            const float sc = P.wk ? 1.0f / (fmaxf(P.wk[f], 1.0f) * (float)P.fa) : 1.0f;
-            const int* off = P.ent_off + (int64_t)f * (P.half + 1);
-            auto val = [&](uint32_t b) {
-                const float2 x = V[b];
-                return make_float2(x.x * sc, x.y * sc);
-            };
-            for (int c = tid >> 5; c < ncol; c += nthr >> 5) {
-                const int u = u0 + c;
-                if (u >= P.half) continue;     // no cell reaches the Nyquist column
-                const int beg = off[u], end = off[u + 1];
-                uint32_t key;
-                float2 x;
-                gather_entry(P.ent, P.wt, beg + lane, end, val, key, x);
-                warp_gather_column(P.ent, P.wt, beg, end, lane, s, val, idx, true, key, x);
-            }
-        }
+        // A warp owns a column and adds its members' entries in member order (reproducible sums); with an
+        // average the members' column ranges, first chunks of entries and their sums are loaded kMembers at a
+        // time, so an average over many channels costs a few load round trips per kMembers members.
+        if (P.fa == 1)
+            gather_members<1>(P, u0, ncol, it0, s, idx);
+        else
+            gather_members<FIX ? 8 : 4>(P, u0, ncol, it0, s, idx);
     }
     __syncthreads();
     int off;                                          // the result buffer's offset, the same for every column
