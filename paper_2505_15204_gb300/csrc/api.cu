@@ -806,10 +806,11 @@ constexpr size_t kVisCapBytes = (size_t)4 << 30;
 
 // Batched path on a side outside the side-specialised kernels, and every averaged call: one correlator
 // launch per chunk of integrations, then per wave of output images (their column results about the size of
-// L2: 96 MB measured a little faster than 48 MB at side 1200, with half the launches) the mixed-radix column pass, gathering each output's cells from the sums of its fa channels, and the
-// row pass (fft_mixed.cu).  fa = 1: one image per (integration, channel), divided by W in the row pass;
-// fa > 1: the mean of fa consecutive channels' normalised images, each channel's sums divided by its own
-// W in the gather.  Outputs [tau0 F/fa, tau1 F/fa) are written from d_img on.
+// L2: 96 MB measured a little faster than 48 MB at side 1200, with half the launches) the mixed-radix column
+// pass, gathering each output's cells from the sums of its fa channels, and the row pass (fft_mixed.cu).
+// fa = 1: one image per (integration, channel), divided by W in the row pass; fa > 1: the mean of fa
+// consecutive channels' normalised images, each channel's sums divided by its own W in the gather.
+// Outputs [tau0 F/fa, tau1 F/fa) are written from d_img on.
 blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, int prec, int arith,
                        const uint8_t* d_volt, int64_t sstride, int tau0, int tau1, float* d_img, cudaStream_t st,
                        GainRef gains, int fa = 1) {
