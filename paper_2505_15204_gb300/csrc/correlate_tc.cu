@@ -39,6 +39,7 @@ constexpr int kUnitsPerBlk = 64;
 constexpr int kTmemCols = 512;
 constexpr int kStageLd = 65;                     // padded row of the epilogue staging tiles (floats)
 constexpr int kPlane = 64 * kStageLd;            // floats of one staging plane (64 x 64 values, padded rows)
+constexpr int kHalfLd = 33;                      // padded row of the half-pair staging (calibrated, gather order)
 constexpr long long kWaitBudget = 2000000000ll;  // clock cycles (about a second)
 
 struct TcParams {
@@ -281,6 +282,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                 continue;
             }
             const int local = it - P.first_item;
+            if (GAINS && !FULL && s_item) {
+                // calibrated, gather order: each block pair in two halves of 32 columns, staged from TMEM (Re and Im
+                // of a unit row sit in TMEM lanes 64 apart, so in different warps) and combined into the item's
+                // copy as g_i S conj(g_j) (summed over X and Y for Stokes I); the gather pass below writes it out
+                float* hs = reinterpret_cast<float*>(smem + P.off_re);   // planes [XX re, XX im, YY re, YY im]
+                for (int q = q0; q < q1; q++) {
+                    int mb, jb;
+                    pair_of(q, mb, jb);
+                    for (int h = 0; h < 2; h++) {
+                        {
+                            const int row = (warp & 3) * 32 + lane, g = warp >> 2;
+                            const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                                (uint32_t)((q - q0) * P.pair_cols + 32 * h + 8 * g);
+                            float* st = hs + (row >> 6) * 64 * kHalfLd + (row & 63) * kHalfLd + 8 * g;
+                            uint32_t v[8];
+                            tmem_ld8(ta, v);
+#pragma unroll
+                            for (int cc = 0; cc < 8; cc++) st[cc] = __uint_as_float(v[cc]);
+                            if (P.split) {                     // YY: planes 2 and 3
+                                tmem_ld8(ta + 64, v);
+#pragma unroll
+                                for (int cc = 0; cc < 8; cc++) st[2 * 64 * kHalfLd + cc] = __uint_as_float(v[cc]);
+                            }
+                        }
+                        __syncthreads();
+                        for (int e = tid; e < 64 * 32; e += kThreads) {
+                            const int il = e >> 5, jl = e & 31;
+                            const int ui = mb * 64 + il, uj = jb * 64 + 32 * h + jl;
+                            if (ui >= P.n_tiles || uj > ui) continue;
+                            const float2 gx = s_g[2 * ui], hx = s_g[2 * uj];
+                            float sr = hs[il * kHalfLd + jl], si = hs[64 * kHalfLd + il * kHalfLd + jl];
+                            float tr = gx.x * sr - gx.y * si, ti = gx.x * si + gx.y * sr;
+                            float vr = tr * hx.x + ti * hx.y, vi = ti * hx.x - tr * hx.y;
+                            if (P.split) {
+                                const float2 gy = s_g[2 * ui + 1], hy = s_g[2 * uj + 1];
+                                sr = hs[2 * 64 * kHalfLd + il * kHalfLd + jl];
+                                si = hs[3 * 64 * kHalfLd + il * kHalfLd + jl];
+                                tr = gy.x * sr - gy.y * si;
+                                ti = gy.x * si + gy.y * sr;
+                                vr += tr * hy.x + ti * hy.y;
+                                vi += ti * hy.x - tr * hy.y;
+                            }
+                            const int64_t b = (int64_t)ui * (ui + 1) / 2 + uj;
+                            s_item[b] = vr;
+                            s_item[P.B + b] = vi;
+                        }
+                        __syncthreads();
+                    }
+                }
+                tc_fence_before();
+                __syncthreads();
+                continue;
+            }
             if (!GAINS && s_item) {
                 // gather order: every block pair of the round from TMEM straight into the item's copy (warp w reads
                 // TMEM lanes 32 (w % 4) + lane = unit row, re for lanes below 64, im above; columns 16 (w / 4) ..)
@@ -465,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         ci = ni;
         cr = nr;
         cj = nj;
-        if (!GAINS && s_item && last_chunk && (P.n_chunks == 1 || r_lo == P.n_rounds - 1)) {
+        if (!FULL && s_item && last_chunk && (P.n_chunks == 1 || r_lo == P.n_rounds - 1)) {
             // the item in gather order: entry p of channel f takes baseline gsrc[f][p] (times the factor
             // gphase[f][p] off zenith), kGatherIlp entries per thread in flight (a 144-tile item's 10,440
             // entries in two round trips), coalesced stores of both planes
@@ -572,6 +626,17 @@ size_t tc_layout(TcParams& P, int ns_c, bool gather, GainRef gains, int64_t B) {
     if (overlay) {
         P.off_item = 0;
         P.two_stage = 0;
+        if (gains.d) {                             // the calibrated epilogue's half-pair staging
+            P.off_re = off;
+            off = align_up(off + 4 * 64 * kHalfLd * 4, 16);
+        }
+    } else if (gather && gains.d) {
+        // calibrated: half-pair staging (four planes of 64 x kHalfLd floats at off_re), then the item's copy
+        P.off_re = off;
+        off = align_up(off + 4 * 64 * kHalfLd * 4, 16);
+        P.off_item = off;
+        off = align_up(off + (uint32_t)(8 * B), 16);
+        P.two_stage = 0;
     } else if (gather) {
         // gather order: the item's baseline-ordered copy takes the staging buffers' place
         P.off_item = off;
@@ -642,7 +707,7 @@ int tc_chunk(TcParams& P, bool gather, GainRef gains, int64_t B) {
 // Whether the gather-order form runs for this plan: no calibration, a gather source table, and a chunking
 // whose operands fit beside the item's copy (2 B floats) in shared memory.
 bool corr_fp8_gathers(const Plan& p, int ns, int out_kind, GainRef gains) {
-    if (gains.d || out_kind == CORR_OUT_VIS4 || !p.d_gsrc) return false;
+    if ((gains.d && gains.full) || out_kind == CORR_OUT_VIS4 || !p.d_gsrc) return false;
     TcParams P{};
     if (!tc_setup(P, out_kind, p, ns, gains)) return false;
     return tc_chunk(P, true, gains, p.B) > 0;
