@@ -419,7 +419,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
                                 o[pq] = make_float2(__fdiv_rn(V[pq].x, div), __fdiv_rn(V[pq].y, div));
                         } else {
                             const float2 o = P.mode == CORR_OUT_STOKES_I ? make_float2(V[0].x + V[3].x, V[0].y + V[3].y) : V[0];
-                            put_img(P, local, b, img_fetch(P, it % P.F, b), o.x, o.y);
+                            if (s_item) {                       // gather order: into the item's copy
+                                s_item[b] = o.x;
+                                s_item[P.B + b] = o.y;
+                            } else {
+                                put_img(P, local, b, img_fetch(P, it % P.F, b), o.x, o.y);
+                            }
                         }
                     }
                     return;
@@ -519,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_corr_tc(const __grid_constant__
         ci = ni;
         cr = nr;
         cj = nj;
-        if (!FULL && s_item && last_chunk && (P.n_chunks == 1 || r_lo == P.n_rounds - 1)) {
+        if (s_item && last_chunk && (P.n_chunks == 1 || r_lo == P.n_rounds - 1)) {
             // the item in gather order: entry p of channel f takes baseline gsrc[f][p] (times the factor
             // gphase[f][p] off zenith), kGatherIlp entries per thread in flight (a 144-tile item's 10,440
             // entries in two round trips), coalesced stores of both planes
@@ -626,14 +631,17 @@ size_t tc_layout(TcParams& P, int ns_c, bool gather, GainRef gains, int64_t B) {
     if (overlay) {
         P.off_item = 0;
         P.two_stage = 0;
-        if (gains.d) {                             // the calibrated epilogue's half-pair staging
+        if (gains.d) {                             // the calibrated epilogue's staging
             P.off_re = off;
-            off = align_up(off + 4 * 64 * kHalfLd * 4, 16);
+            P.off_im = off + kPlane * 4;
+            off = align_up(off + (gains.full ? P.stage_buf * 4 : 4 * 64 * kHalfLd * 4), 16);
         }
     } else if (gather && gains.d) {
-        // calibrated: half-pair staging (four planes of 64 x kHalfLd floats at off_re), then the item's copy
+        // calibrated: half-pair staging (four planes of 64 x kHalfLd floats at off_re), or with Jones matrices one
+        // whole-pair staging buffer (two planes: the four products of 32 x 32 tile pairs), then the item's copy
         P.off_re = off;
-        off = align_up(off + 4 * 64 * kHalfLd * 4, 16);
+        P.off_im = off + kPlane * 4;
+        off = align_up(off + (gains.full ? P.stage_buf * 4 : 4 * 64 * kHalfLd * 4), 16);
         P.off_item = off;
         off = align_up(off + (uint32_t)(8 * B), 16);
         P.two_stage = 0;
@@ -707,7 +715,7 @@ int tc_chunk(TcParams& P, bool gather, GainRef gains, int64_t B) {
 // Whether the gather-order form runs for this plan: no calibration, a gather source table, and a chunking
 // whose operands fit beside the item's copy (2 B floats) in shared memory.
 bool corr_fp8_gathers(const Plan& p, int ns, int out_kind, GainRef gains) {
-    if ((gains.d && gains.full) || out_kind == CORR_OUT_VIS4 || !p.d_gsrc) return false;
+    if (out_kind == CORR_OUT_VIS4 || !p.d_gsrc) return false;
     TcParams P{};
     if (!tc_setup(P, out_kind, p, ns, gains)) return false;
     return tc_chunk(P, true, gains, p.B) > 0;
