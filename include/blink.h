@@ -155,7 +155,7 @@ int64_t blink_n_baselines(int32_t n_tiles);
 /* ---- the hot path, one stage per call ---------------------------------------------------------- */
 
 /*
- * Baseline geometry (Sec. 5.2.3, geometric correction "implemented in the imaging library", and the
+ * Baseline geometry (Sec. 5.2.3, the geometric correction, which the paper performs inside its imager, and the
  * (u, v, w) computation of Sec. 5.2.4), in FP64 on the GPU: for every output channel f (centre = mean of
  * its chan_avg fine-channel centres) and baseline b, (u, v, w) = (r_i - r_j) * (nu_f / c) and the
  * nearest uv cell (iu, iv) = floor((u, v) / du + 1/2).  Off zenith (imaging.phase_l, phase_m) the
@@ -208,7 +208,7 @@ blink_status blink_image(blink_context* ctx, const blink_imaging* imaging, const
                          int32_t n_images, const float* d_weight, float* d_img, void* stream);
 
 /*
- * The whole path (Sec. 5, Fig. "BLINK FRB search pipeline", imaging half): correlation -> gridding ->
+ * The whole path (Sec. 5, the imaging half of the paper's FRB search pipeline figure): correlation -> gridding ->
  * inverse FFT -> shifted, normalised dirty images for every integration and output channel of the call,
  * d_img float [T * F][N][N] in image-id order.  Only the products the imaged polarisation needs are
  * formed (XX and YY for Stokes I), calibrated with array.gains when given.

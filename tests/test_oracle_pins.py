@@ -418,7 +418,7 @@ def test_noise_level_of_pure_noise_image():
 
 
 def test_layout_sizes_match_paper_data_volume_table():
-    # Table "Data volumes" (Sec. 7): visibilities and images per second of data for the two test cases,
+    # the data-volume table (Sec. 7): visibilities and images per second of data for the two test cases,
     # reproduced by this layout (lower triangle with autos, 4 polarisations, complex64; float32 images).
     with open(os.path.join(GOLDEN, "paper_data_volumes.json")) as f:
         gold = json.load(f)
