@@ -803,6 +803,7 @@ int64_t sample_stride_bytes(const blink_obs* o, int n_tiles) {
 // image tau0 F: one correlator launch over as many integrations as the visibility workspace holds, then
 // one persistent launch that grids and transforms all of their images (fft_persistent.cu).
 constexpr size_t kVisCapBytes = (size_t)4 << 30;
+constexpr int kAvgGridMembers = 16;              // channels per averaged output from which its grid is built first
 
 // Batched path on a side outside the side-specialised kernels, and every averaged call: one correlator
 // launch per chunk of integrations, then per wave of output images (their column results about the size of
@@ -826,6 +827,12 @@ blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, in
     void* H = nullptr;
     BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));
     BLINK_TRY(workspace(ctx, 1, (size_t)std::min(wave, t_chunk * Fo) * per_img, &H));
+    // averages over many channels: their grids first, summed by every warp of the GPU (k_avg_grid), then the
+    // column pass from those grids
+    const bool grid_first = fa >= kAvgGridMembers;
+    const size_t grid_bytes = (size_t)p.N * (p.N / 2 + 1) * sizeof(float2);
+    void* G = nullptr;
+    if (grid_first) BLINK_TRY(workspace(ctx, 8, (size_t)std::min(wave, t_chunk * Fo) * grid_bytes, &G));
     ImgOut io;
     io.phase = p.d_phase;
     MixedIn in;
@@ -861,7 +868,15 @@ blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, in
             const WaveMap wm{1, 0, ta * Fo + w0, nw};
             {
                 StageTimer t(ctx, BLINK_STAGE_GRID_FFT, st);
-                BLINK_TRY(launch_mixed(in, 0, prec, nw, H, nullptr, 1, wm, out_first, nullptr, st));
+                if (grid_first) {
+                    BLINK_CUDA(cudaMemsetAsync(G, 0, (size_t)nw * grid_bytes, st));
+                    BLINK_TRY(launch_avg_grid(in, nw, static_cast<float2*>(G), st));
+                    MixedIn ig = in;
+                    ig.grid = static_cast<const float2*>(G);
+                    BLINK_TRY(launch_mixed(ig, 0, prec, nw, H, nullptr, 1, wm, out_first, nullptr, st));
+                } else {
+                    BLINK_TRY(launch_mixed(in, 0, prec, nw, H, nullptr, 1, wm, out_first, nullptr, st));
+                }
             }
             StageTimer t(ctx, BLINK_STAGE_ROW_FFT, st);
             BLINK_TRY(launch_mixed(in, 1, prec, nw, H, row_w, F, wm, out_first, d_img, st));

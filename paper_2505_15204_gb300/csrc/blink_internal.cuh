@@ -106,7 +106,7 @@ struct blink_context {
     int n_sm = 0;
     int* d_status = nullptr;
     std::vector<blink::Plan*> plans;       // most recent last
-    blink::Workspace ws[8];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays
+    blink::Workspace ws[9];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays, 8 averaged grids
     float2* tw[16] = {};                   // twiddle tables by log2(side)
     std::vector<std::pair<int, float2*>> tw_any;   // unit-root tables of the other sides (fft_mixed.cu)
     blink::FftWait fft_wait;               // dependency-wait budget of the persistent FFT kernel
@@ -244,6 +244,9 @@ struct MixedIn {
 // at d_img + (wm.id(i) - out_first) * side^2 and divided by d_w[wm.id(i) % w_mod] (d_w NULL: by 1).
 blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, void* d_H, const float* d_w, int w_mod,
                           WaveMap wm, int out_first, float* d_img, cudaStream_t st);
+// Averaged outputs over many channels: their half-plane grids [n_out][N][N/2 + 1], unshifted, summed into d_grid
+// (zeroed by the caller) from in.vis / the plan's lists, for a column pass with in.grid = d_grid.
+blink_status launch_avg_grid(const MixedIn& in, int n_out, float2* d_grid, cudaStream_t st);
 blink_status launch_colpass_grid(int N, int prec, const float2* d_tw, const float2* d_grid, int n_images,
                                  void* d_H, int ldh, cudaStream_t st);
 blink_status launch_rowpass(int N, int prec, const float2* d_tw, const void* d_H, int ldh, int has_nyq,

@@ -153,8 +153,9 @@ constexpr int kFixRows = 8;                        // rows per CTA of the side-1
 
 // The gather of a column CTA's columns from its output's members (fa consecutive channels, or the image's own
 // channel): a warp owns a column and adds the members' entries in member order, the members' column ranges,
-// first chunks of entries and their sums loaded G at a time.
-template <int G, typename Idx>
+// first chunks of entries and their sums loaded G at a time.  SHIFT: cells multiplied by (-1)^(u+v) (the image
+// shift), else stored as they are.
+template <int G, bool SHIFT, typename Idx>
 __device__ __forceinline__ void gather_members(const MixedCol& P, int u0, int ncol, int it0, float2* s, Idx idx) {
     const int tid = threadIdx.x, lane = tid & 31;
     for (int c = tid >> 5; c < ncol; c += blockDim.x >> 5) {
@@ -208,10 +209,25 @@ __device__ __forceinline__ void gather_members(const MixedCol& P, int u0, int nc
                         x = make_float2(x.x * w, x.y * w);
                     }
                 }
-                warp_gather_column(P.ent, P.wt, beg[g], end[g], lane, s, val, idx, true, key, x);
+                warp_gather_column(P.ent, P.wt, beg[g], end[g], lane, s, val, idx, SHIFT, key, x);
             }
         }
     }
+}
+
+// The grids of averaged outputs over many channels, summed in global memory (zeroed by the caller) with one
+// warp per column of the half plane, so that every warp of the GPU gathers (inside the column pass one warp per
+// column does, while the rest of its CTA waits).  Per cell the members are added in the same order as there;
+// cells are stored unshifted, for the column pass's grid input; the Nyquist column stays zero.
+constexpr int kAvgGridWarps = 8;
+__global__ void __launch_bounds__(32 * kAvgGridWarps) k_avg_grid(const MixedCol P, float2* grid) {
+    const int img = blockIdx.y, u0 = blockIdx.x * kAvgGridWarps;
+    const int ncol = min(kAvgGridWarps, P.half + 1 - u0);
+    const int o = P.o_first + img;
+    const int it0 = (o / P.Fo) * P.F + (o % P.Fo) * P.fa;
+    float2* G = grid + (int64_t)img * P.N * (P.half + 1);
+    auto idx = [&](int u, int v) { return (int64_t)v * (P.half + 1) + u; };
+    gather_members<8, false>(P, u0, ncol, it0, G, idx);
 }
 
 template <typename T, int FIX>
@@ -248,9 +264,9 @@ __global__ void __launch_bounds__(FIX ? kFixCols * kCol1200Threads : kMaxThreads
         // average the members' column ranges, first chunks of entries and their sums are loaded kMembers at a
         // time, so an average over many channels costs a few load round trips per kMembers members.
         if (P.fa == 1)
-            gather_members<1>(P, u0, ncol, it0, s, idx);
+            gather_members<1, true>(P, u0, ncol, it0, s, idx);
         else
-            gather_members<FIX ? 8 : 4>(P, u0, ncol, it0, s, idx);
+            gather_members<FIX ? 8 : 4, true>(P, u0, ncol, it0, s, idx);
     }
     __syncthreads();
     int off;                                          // the result buffer's offset, the same for every column
@@ -425,6 +441,30 @@ bool shape_for(int N, Shape* sh) {
 bool mixed_side_ok(int N) {
     Shape sh;
     return shape_for(N, &sh);
+}
+
+blink_status launch_avg_grid(const MixedIn& in, int n_out, float2* d_grid, cudaStream_t st) {
+    if (n_out <= 0) return BLINK_OK;
+    if (n_out > 65535) return set_error(BLINK_ERR_UNSUPPORTED, "wave of more than 65535 images");
+    MixedCol C{};
+    C.N = in.N;
+    C.half = in.N / 2;
+    C.tw = in.tw;
+    C.vis = in.vis;
+    C.vstride = in.vstride;
+    C.first = in.first;
+    C.F = in.F;
+    C.o_first = in.o_first;
+    C.fa = in.fa;
+    C.Fo = in.F / in.fa;
+    C.wk = in.wk;
+    C.ent_off = in.ent_off;
+    C.ent = in.ent;
+    C.wt = in.wt;
+    const dim3 g((in.N / 2 + 1 + kAvgGridWarps - 1) / kAvgGridWarps, n_out);
+    k_avg_grid<<<g, 32 * kAvgGridWarps, 0, st>>>(C, d_grid);
+    BLINK_CUDA(cudaGetLastError());
+    return BLINK_OK;
 }
 
 blink_status make_unit_roots(float2* d_out, int N, cudaStream_t st) {
