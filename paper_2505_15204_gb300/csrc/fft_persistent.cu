@@ -593,8 +593,16 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
         uint32_t* occ = s_occ + warp * 32;
         occ[lane] = 0u;
         __syncwarp();
-        warp_gather_occ_batched<4>(P.ent, beg, end, lane, s, [&](int, uint32_t b) { return val(b); }, idx,
-                                   [&](int, int v) { return occ + (v & 31); }, 1.0f, [] {}, wt);
+        // gather-ordered sums (planes of e_stride floats from the channel's first entry; nearest cell only) or
+        // baseline order
+        const float* Vre = reinterpret_cast<const float*>(V) - off[0];
+        auto valg = [&](int i, uint32_t b) {
+            if constexpr (!WT)
+                if (P.gathered) return make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i));
+            return val(b);
+        };
+        warp_gather_occ_batched<4>(P.ent, beg, end, lane, s, valg, idx, [&](int, int v) { return occ + (v & 31); },
+                                   1.0f, [] {}, wt);
         __syncwarp();
         if constexpr (N == 512)
             warp_fft512(col, s_twc, lane, occ[lane]);
@@ -902,7 +910,10 @@ std::vector<FftTune> fft_tune_candidates(const Plan& p) {
 }
 int fft_ring_images_max() { return 64; }
 
-bool fft_takes_gathered(const Plan& p) { return p.N == 512 && !p.d_wt && p.d_gsrc && p.e_stride > 0; }
+// Sums in gather order: the nearest-cell sides whose column tasks run the batched gather (256 to 1024)
+bool fft_takes_gathered(const Plan& p) {
+    return p.N >= 256 && p.N <= 1024 && !p.d_wt && p.d_gsrc && p.e_stride > 0;
+}
 
 namespace {
 constexpr int kRingV = 128, kLead = 96;          // vis-ring slots and the correlation lead (images)
@@ -940,7 +951,7 @@ FusedChunk fused_chunk(const Plan& p, int ns, int kind) {
 }  // namespace
 
 bool fft_fused_ok(const Plan& p, int ns, int kind, const uint8_t* d_volt, int64_t sample_stride) {
-    if (!fft_takes_gathered(p) || !p.d_gpos || p.n_tiles % 8 || p.n_tiles > 512) return false;
+    if (p.N != 512 || !fft_takes_gathered(p) || !p.d_gpos || p.n_tiles % 8 || p.n_tiles > 512) return false;
     if (kind != CORR_OUT_STOKES_I && kind != CORR_OUT_XX) return false;
     if (((uintptr_t)d_volt & 15) || (sample_stride % 16) || ((int64_t)p.chan_avg * p.n_tiles * 2) % 16) return false;
     const int64_t K = (int64_t)ns * p.chan_avg;
@@ -987,7 +998,7 @@ blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec,
                                    float* d_img, int out_first, int* d_status, int n_sm, cudaStream_t st,
                                    const FftWait& wait, bool gathered, const FusedIn* fused) {
     if (gathered && !fft_takes_gathered(p))
-        return set_error(BLINK_ERR_UNSUPPORTED, "gather-ordered sums need the side-512 nearest-cell plan");
+        return set_error(BLINK_ERR_UNSUPPORTED, "gather-ordered sums need a nearest-cell plan of side 256 to 1024");
     FftParams P{};
     if (fused) {
         if (!gathered || !fft_fused_ok(p, fused->ns, fused->kind, fused->d_volt, fused->sample_stride) || !fused->d_vring)

@@ -133,6 +133,7 @@ PC_CASES = [
     ("coarse", 20, 8, 4, 256, 0, (0.31, -0.22), 0),
     ("precision", None, None, 1, 512, 0, (-0.05, 0.4), 0),
     ("uneven", 20, 3, 1, 128, 0, (0.2, 0.1), 1),
+    ("uneven", 20, 2, 1, 1024, 0, (-0.15, 0.25), 0),
     ("coarse", 20, 8, 2, 128, 6, (0.31, -0.22), 0),
 ]
 
