@@ -818,14 +818,18 @@ blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, in
     const int F = p.F, T = tau1 - tau0, Fo = F / fa;
     if (T <= 0) return BLINK_OK;
     const int kind = p.pol == BLINK_POL_I ? CORR_OUT_STOKES_I : CORR_OUT_XX;
-    const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)p.B * 8 * F))));
+    // nearest cell with FP8: the correlator writes the sums in the gather's entry order
+    const bool gathered = arith == BLINK_CORR_FP8 && !p.d_wt && p.d_gsrc && p.e_stride > 0 &&
+                          corr_fp8_gathers(p, o->samples_per_int, kind, gains);
+    const int64_t vstride = gathered ? p.e_stride : p.B;          // float2 per item
+    const int t_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(kVisCapBytes / ((size_t)vstride * 8 * F))));
     const bool crop = p.support != 0;
     const size_t el = prec == BLINK_PREC_BF16 ? 4 : 8;
     const size_t per_img = (size_t)(crop ? p.N / 2 : p.N) * mixed_h_row(p.N) * el;
     const int wave = (int)std::max<size_t>(1, std::min<size_t>(65535, ((size_t)96 << 20) / per_img));
     void* vis = nullptr;
     void* H = nullptr;
-    BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * p.B * sizeof(float2), &vis));
+    BLINK_TRY(workspace(ctx, 0, (size_t)t_chunk * F * vstride * sizeof(float2), &vis));
     BLINK_TRY(workspace(ctx, 1, (size_t)std::min(wave, t_chunk * Fo) * per_img, &H));
     // averages over many channels: their grids first, summed by every warp of the GPU (k_avg_grid), then the
     // column pass from those grids
@@ -835,11 +839,14 @@ blink_status run_mixed(blink_context* ctx, const Plan& p, const blink_obs* o, in
     if (grid_first) BLINK_TRY(workspace(ctx, 8, (size_t)std::min(wave, t_chunk * Fo) * grid_bytes, &G));
     ImgOut io;
     io.phase = p.d_phase;
+    io.gather = gathered;
     MixedIn in;
     in.N = p.N;
     in.tw = p.d_tw;
     in.vis = static_cast<const float2*>(vis);
-    in.vstride = p.B;
+    in.vstride = vstride;
+    in.gathered = gathered;
+    in.e_stride = p.e_stride;
     in.F = F;
     in.fa = fa;
     in.wk = fa > 1 ? p.d_Wk : nullptr;

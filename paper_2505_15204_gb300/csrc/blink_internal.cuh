@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -230,7 +231,9 @@ struct MixedIn {
     const float2* tw = nullptr;            // make_unit_roots(N)
     const float2* grid = nullptr;          // stored half-plane grids [n][N][N/2 + 1] (the Nyquist column included) ...
     const float2* vis = nullptr;           // ... or per-item sums in baseline order, item i at vis + i * vstride,
-    int64_t vstride = 0;                   //     gathered through the plan's lists of channel (first + i) % F;
+    int64_t vstride = 0;                   //     gathered through the plan's lists of channel (first + i) % F
+    bool gathered = false;                 //     (gathered: in that channel's entry order, planar, e_stride real
+    int e_stride = 0;                      //     parts then e_stride imaginary parts; nearest cell only);
     int first = 0, F = 1;                  //     output o (o_first + launch index) sums the fa items
     int o_first = 0, fa = 1;               //     (o / (F/fa)) F + (o % (F/fa)) fa + m, scaled by
     const float* wk = nullptr;             //     1 / (max(wk[f], 1) fa) when wk is given
@@ -646,7 +649,8 @@ __device__ __forceinline__ uint32_t ent_cell(uint32_t x) { return x & 0x7FFFFFFF
 
 // Gather entry i of a column whose entries end at `end`: its cell key and visibility (conjugated for an
 // entry of the mirrored half plane), times the entry's weight wt[i] when `wt` is given (a convolution
-// kernel's weight); key 0xFFFFFFFF and zero past the end.
+// kernel's weight); key 0xFFFFFFFF and zero past the end.  The visibility is val(b) of the entry's baseline
+// b, or val(i, b) where the caller's sums are in gather order (then its load does not wait for the entry's).
 template <typename Val>
 __device__ __forceinline__ void gather_entry(const uint2* __restrict__ ent, const float* __restrict__ wt, int i,
                                              int end, Val val, uint32_t& key, float2& x) {
@@ -655,7 +659,10 @@ __device__ __forceinline__ void gather_entry(const uint2* __restrict__ ent, cons
     if (i < end) {
         const uint2 e = ent[i];
         key = ent_cell(e.x);
-        x = val(e.y);
+        if constexpr (std::is_invocable_v<Val, int, uint32_t>)
+            x = val(i, e.y);
+        else
+            x = val(e.y);
         if (e.x >> 31) x.y = -x.y;
         if (wt) {
             const float w = wt[i];

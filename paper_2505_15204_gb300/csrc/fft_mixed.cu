@@ -129,11 +129,13 @@ struct MixedCol {
     const float2* tw;                      // exp(+2 pi i k / N), k < N
     // input: a stored half-plane grid [img][N][N/2 + 1] ...
     const float2* grid;
-    // ... or the gather lists: item i's sums at vis + i * vstride (baseline order), channel (first + i) % F.
+    // ... or the gather lists: item i's sums at vis + i * vstride, channel (first + i) % F, in baseline order
+    // or (gathered) in the channel's entry order, planar (e_stride real parts, then e_stride imaginary parts).
     // Output o (o_first + blockIdx.y) sums the fa items (o / Fo) F + (o % Fo) fa + m, m < fa, each scaled by
     // 1 / (max(wk[channel], 1) fa) when wk is given (an average of normalised images), else by 1.
     const float2* vis;
     int64_t vstride;
+    int gathered, e_stride;
     int first, F, o_first, fa, Fo;
     const float* wk;
     const int* ent_off;
@@ -154,8 +156,9 @@ constexpr int kFixRows = 8;                        // rows per CTA of the side-1
 // The gather of a column CTA's columns from its output's members (fa consecutive channels, or the image's own
 // channel): a warp owns a column and adds the members' entries in member order, the members' column ranges,
 // first chunks of entries and their sums loaded G at a time.  SHIFT: cells multiplied by (-1)^(u+v) (the image
-// shift), else stored as they are.
-template <int G, bool SHIFT, typename Idx>
+// shift), else stored as they are.  GATH: sums in gather order, loaded beside their entries (one round trip
+// fewer per G members).
+template <int G, bool SHIFT, bool GATH, typename Idx>
 __device__ __forceinline__ void gather_members(const MixedCol& P, int u0, int ncol, int it0, float2* s, Idx idx) {
     const int tid = threadIdx.x, lane = tid & 31;
     for (int c = tid >> 5; c < ncol; c += blockDim.x >> 5) {
@@ -165,35 +168,46 @@ __device__ __forceinline__ void gather_members(const MixedCol& P, int u0, int nc
             int beg[G], end[G];
             float sc[G];
             const float2* V[G];
+            const float* Vr[G];                // gathered: the member's real parts, indexed by the entry
 #pragma unroll
             for (int g = 0; g < G; g++) {
                 beg[g] = end[g] = 0;
                 sc[g] = 1.0f;
                 V[g] = P.vis;
+                Vr[g] = nullptr;
                 if (m0 + g < P.fa) {
                     const int it = it0 + m0 + g, f = (P.first + it) % P.F;
                     const int* off = P.ent_off + (int64_t)f * (P.half + 1);
                     beg[g] = off[u];
                     end[g] = off[u + 1];
                     V[g] = P.vis + (int64_t)it * P.vstride;
+                    if constexpr (GATH) Vr[g] = reinterpret_cast<const float*>(V[g]) - off[0];
                     if (P.wk) sc[g] = 1.0f / (fmaxf(P.wk[f], 1.0f) * (float)P.fa);
                 }
             }
             uint2 e[G];
-#pragma unroll
-            for (int g = 0; g < G; g++)
-                if (beg[g] + lane < end[g]) e[g] = P.ent[beg[g] + lane];
             float2 xv[G];
 #pragma unroll
-            for (int g = 0; g < G; g++)
-                if (beg[g] + lane < end[g]) xv[g] = V[g][e[g].y];
+            for (int g = 0; g < G; g++) {
+                const int i = beg[g] + lane;
+                if (i < end[g]) {
+                    e[g] = P.ent[i];
+                    if constexpr (GATH) xv[g] = make_float2(Vr[g][i], Vr[g][P.e_stride + i]);
+                }
+            }
+            if constexpr (!GATH) {
+#pragma unroll
+                for (int g = 0; g < G; g++)
+                    if (beg[g] + lane < end[g]) xv[g] = V[g][e[g].y];
+            }
 #pragma unroll
             for (int g = 0; g < G; g++) {
                 if (m0 + g >= P.fa) break;
                 const float2* Vg = V[g];
+                const float* Vrg = Vr[g];
                 const float scg = sc[g];
-                auto val = [&](uint32_t b) {
-                    const float2 x = Vg[b];
+                auto val = [&](int i, uint32_t b) {
+                    const float2 x = GATH ? make_float2(Vrg[i], Vrg[P.e_stride + i]) : Vg[b];
                     return make_float2(x.x * scg, x.y * scg);
                 };
                 // the member's first chunk as gather_entry forms it, from the values loaded above
@@ -227,7 +241,10 @@ __global__ void __launch_bounds__(32 * kAvgGridWarps) k_avg_grid(const MixedCol 
     const int it0 = (o / P.Fo) * P.F + (o % P.Fo) * P.fa;
     float2* G = grid + (int64_t)img * P.N * (P.half + 1);
     auto idx = [&](int u, int v) { return (int64_t)v * (P.half + 1) + u; };
-    gather_members<8, false>(P, u0, ncol, it0, G, idx);
+    if (P.gathered)
+        gather_members<8, false, true>(P, u0, ncol, it0, G, idx);
+    else
+        gather_members<8, false, false>(P, u0, ncol, it0, G, idx);
 }
 
 template <typename T, int FIX>
@@ -263,10 +280,13 @@ __global__ void __launch_bounds__(FIX ? kFixCols * kCol1200Threads : kMaxThreads
         // A warp owns a column and adds its members' entries in member order (reproducible sums); with an
         // average the members' column ranges, first chunks of entries and their sums are loaded kMembers at a
         // time, so an average over many channels costs a few load round trips per kMembers members.
+        constexpr int GM = FIX ? 8 : 4;
         if (P.fa == 1)
-            gather_members<1, true>(P, u0, ncol, it0, s, idx);
+            P.gathered ? gather_members<1, true, true>(P, u0, ncol, it0, s, idx)
+                       : gather_members<1, true, false>(P, u0, ncol, it0, s, idx);
         else
-            gather_members<FIX ? 8 : 4, true>(P, u0, ncol, it0, s, idx);
+            P.gathered ? gather_members<GM, true, true>(P, u0, ncol, it0, s, idx)
+                       : gather_members<GM, true, false>(P, u0, ncol, it0, s, idx);
     }
     __syncthreads();
     int off;                                          // the result buffer's offset, the same for every column
@@ -452,6 +472,8 @@ blink_status launch_avg_grid(const MixedIn& in, int n_out, float2* d_grid, cudaS
     C.tw = in.tw;
     C.vis = in.vis;
     C.vstride = in.vstride;
+    C.gathered = in.gathered;
+    C.e_stride = in.e_stride;
     C.first = in.first;
     C.F = in.F;
     C.o_first = in.o_first;
@@ -498,6 +520,8 @@ blink_status launch_mixed(const MixedIn& in, int pass, int prec, int n_images, v
         C.grid = in.grid;
         C.vis = in.vis;
         C.vstride = in.vstride;
+        C.gathered = in.gathered;
+        C.e_stride = in.e_stride;
         C.first = in.first;
         C.F = in.F;
         C.o_first = in.o_first;

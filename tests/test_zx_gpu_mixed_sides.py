@@ -208,6 +208,8 @@ AVG_CASES = [
     ("uneven", 20, 6, 1, 150, 0, 2, 6, (0.0, 0.0), True),       # one long-exposure image, flagged tiles
     ("coarse", 20, 4, 1, 300, 6, 2, 4, (0.2, -0.1), False),     # kernel gridding, off zenith
     ("precision", None, None, 1, 512, 0, 1, 1, (0.0, 0.0), False),   # nothing averaged
+    ("coarse", 20, 16, 1, 256, 0, 1, 16, (0.0, 0.0), False),    # 16 channels: the grid summed first
+    ("coarse", 20, 16, 1, 1200, 0, 2, 16, (0.15, -0.2), True),  # the same, time too, off zenith, flags
 ]
 
 
