@@ -166,6 +166,9 @@ void free_plan(Plan* p) {
     cudaFree(p->d_Wk);
     cudaFree(p->d_tw);
     cudaFree(p->d_wt);
+    cudaFree(p->d_sep_off);
+    cudaFree(p->d_sep);
+    cudaFree(p->d_sep_w);
     cudaFree(p->d_corr);
     cudaFree(p->d_phase);
     cudaFree(p->d_gsrc);
@@ -504,6 +507,112 @@ blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std:
             wt[base[f] + q] = ewt[ord[q]];
         }
     });
+    // the separable form: per channel, records in baseline order (a visibility, then its mirror), and per
+    // column the entries of the records whose support meets it, sorted by (v0, record)
+    if (W <= kSepMaxW && N >= 256 && N <= 1024 && B <= 0x7FFFFFFF) {
+        struct Sep {
+            std::vector<uint4> ent;            // sorted, channel-local record numbers in .w
+            std::vector<float> wrow;           // [records][kSepMaxW]
+            std::vector<int> off;              // [half + 1], channel-local
+        };
+        std::vector<Sep> sep(F);
+        parallel([&](int f) {
+            Sep& S = sep[f];
+            struct Col {
+                int u, v0;
+                uint32_t rec, bc;
+                float wu;
+            };
+            std::vector<Col> cols;
+            int cu[20], cv[20];
+            double wu[20], wv[20];
+            // a record of nv rows from v0 (weights ws in increasing v) meeting the columns us[0 .. nu) (weights wus)
+            auto record = [&](uint32_t bc, int v0, const double* ws, int nv, const int* us, const double* wus, int nu) {
+                const uint32_t r = (uint32_t)(S.wrow.size() / kSepMaxW);
+                for (int k = 0; k < kSepMaxW; k++)
+                    S.wrow.push_back(k < nv ? (float)((k & 1) ? -ws[k] : ws[k]) : 0.f);
+                for (int q = 0; q < nu; q++) cols.push_back({us[q], v0, r, bc, (float)wus[q]});
+            };
+            for (int64_t b = 0; b < B; b++) {
+                const int i = bl[b].x, j = bl[b].y;
+                if (a->flags && (a->flags[i] || a->flags[j])) continue;
+                int us[20], n_us = 0;
+                double wus[20];
+                if (i == j) {
+                    if (!p->autos) continue;
+                    const int n = support_cells(0.0, cu, wu);
+                    for (int r = 0; r < n; r++)
+                        if (cu[r] >= 0) {
+                            us[n_us] = cu[r];
+                            wus[n_us++] = wu[r];
+                        }
+                    record((uint32_t)b, cu[0], wu, n, us, wus, n_us);
+                    continue;
+                }
+                const double gu = uvw[((size_t)f * B + b) * 3 + 0] / p->du, gv = uvw[((size_t)f * B + b) * 3 + 1] / p->du;
+                if (!(std::fabs(gu) <= lim && std::fabs(gv) <= lim)) continue;
+                const int nu = support_cells(gu, cu, wu), nv = support_cells(gv, cv, wv);
+                for (int r = 0; r < nu; r++)
+                    if (cu[r] >= 0) {
+                        us[n_us] = cu[r];
+                        wus[n_us++] = wu[r];
+                    }
+                if (n_us) record((uint32_t)b, cv[0], wv, nv, us, wus, n_us);
+                // the mirror: rows -cv[nv - 1] .. -cv[0], columns -cu[r] for cu[r] <= 0
+                double wm[20];
+                for (int k = 0; k < nv; k++) wm[k] = wv[nv - 1 - k];
+                n_us = 0;
+                for (int r = 0; r < nu; r++)
+                    if (cu[r] <= 0) {
+                        us[n_us] = -cu[r];
+                        wus[n_us++] = wu[r];
+                    }
+                if (n_us) record((uint32_t)b | 0x80000000u, -cv[nv - 1], wm, nv, us, wus, n_us);
+            }
+            std::sort(cols.begin(), cols.end(), [](const Col& x, const Col& y) {
+                return x.u != y.u ? x.u < y.u : (x.v0 != y.v0 ? x.v0 < y.v0 : x.rec < y.rec);
+            });
+            S.off.assign(half + 1, 0);
+            size_t e = 0;
+            for (int u = 0; u <= half; u++) {
+                while (e < cols.size() && cols[e].u < u) e++;
+                S.off[u] = (int)e;
+            }
+            S.ent.resize(cols.size());
+            for (size_t q = 0; q < cols.size(); q++) {
+                uint32_t wbits;
+                std::memcpy(&wbits, &cols[q].wu, 4);
+                S.ent[q] = make_uint4(cols[q].bc, (uint32_t)cols[q].v0, wbits, cols[q].rec);
+            }
+        });
+        std::vector<int64_t> e0(F + 1, 0), r0(F + 1, 0);
+        for (int f = 0; f < F; f++) {
+            e0[f + 1] = e0[f] + (int64_t)sep[f].ent.size();
+            r0[f + 1] = r0[f] + (int64_t)sep[f].wrow.size() / kSepMaxW;
+        }
+        if (e0[F] > INT32_MAX / 2 || r0[F] * kSepMaxW > INT32_MAX) return set_error(BLINK_ERR_UNSUPPORTED, "gather list too large");
+        std::vector<int> soff((size_t)F * (half + 1) + 1);
+        std::vector<uint4> sent((size_t)e0[F]);
+        std::vector<float> swt((size_t)r0[F] * kSepMaxW);
+        for (int f = 0; f < F; f++) {
+            for (int u = 0; u <= half; u++) soff[(size_t)f * (half + 1) + u] = (int)(e0[f] + sep[f].off[u]);
+            for (size_t q = 0; q < sep[f].ent.size(); q++) {
+                uint4 x = sep[f].ent[q];
+                x.w = (uint32_t)((r0[f] + x.w) * kSepMaxW);
+                sent[(size_t)e0[f] + q] = x;
+            }
+            std::copy(sep[f].wrow.begin(), sep[f].wrow.end(), swt.begin() + r0[f] * kSepMaxW);
+        }
+        soff[(size_t)F * (half + 1)] = (int)e0[F];
+        BLINK_TRY(dmalloc(&p->d_sep_off, soff.size()));
+        BLINK_CUDA(cudaMemcpy(p->d_sep_off, soff.data(), soff.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (!sent.empty()) {
+            BLINK_TRY(dmalloc(&p->d_sep, sent.size()));
+            BLINK_TRY(dmalloc(&p->d_sep_w, swt.size()));
+            BLINK_CUDA(cudaMemcpy(p->d_sep, sent.data(), sent.size() * sizeof(uint4), cudaMemcpyHostToDevice));
+            BLINK_CUDA(cudaMemcpy(p->d_sep_w, swt.data(), swt.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
     p->W.assign(F, 0.f);
     int64_t dropped = 0;
     for (int f = 0; f < F; f++) {

@@ -36,6 +36,7 @@ blink_status cuda_error(cudaError_t e, const char* what);
 enum : int { DEV_ERR_INDEX = 1, DEV_ERR_TIMEOUT = 2 };
 
 constexpr uint32_t CELL_NONE = 0x80008000u;   // flagged or outside the grid
+constexpr int kSepMaxW = 8;                  // widest kernel with a separable gather list (row weights per record)
 
 // ------------------------------------------------------------------------------------------------
 // plan: everything that depends only on (array, channels, imaging), built once and cached
@@ -72,6 +73,13 @@ struct Plan {
     uint2* d_ent = nullptr;                // [n_contrib] {u | v << 13 | conj << 31, b}, sorted by (u, v, b)
     float* d_wt = nullptr;                 // [n_contrib] kernel weight of each entry (convolution only)
     float* d_corr = nullptr;               // [Ni] grid correction 1 / c(nu) per image pixel index (convolution only)
+    // the separable form of a kernel's list (W <= kSepMaxW, persistent sides 256 to 1024): a record is a cross
+    // visibility, its mirror (conjugate, at -g) or an autocorrelation, with its support's rows v0 .. v0 + W - 1
+    // (v0 signed, rows taken mod N) and weights C(v - gv); per channel and column u, one entry for each record
+    // whose support meets the column, sorted by (v0, record)
+    int* d_sep_off = nullptr;              // [F][N/2 + 1] + 1: first entry of each column u
+    uint4* d_sep = nullptr;                // {b | conj << 31, v0, C(u - gu) (float bits), record's weight row}
+    float* d_sep_w = nullptr;              // [records][kSepMaxW]: row weights C(v0 + k - gv) (-1)^k, 0 past W
     float* d_W = nullptr;                  // [F] W, the sum of weights
     float* d_Wk = nullptr;                 // [F] W times the divisor of the correlator's raw sums (2K or K)
     float2* d_tw = nullptr;                // twiddle set of side N (tws_total(N) entries)

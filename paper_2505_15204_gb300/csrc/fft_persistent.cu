@@ -65,6 +65,10 @@ struct FftParams {
     const int* ent_off;      // [F][N/2 + 1]
     const uint2* ent;        // gather entries
     const float* wt;         // per-entry kernel weights (convolutional gridding), else NULL
+    const int* sep_off;      // the separable form of a kernel's list (FP32 storage), else NULL: [F][N/2 + 1] + 1
+    const uint4* sep;        //   {b | conj << 31, v0, C(u - gu) bits, weight row}
+    const float* sep_w;      //   [records][kSepMaxW] row weights C(v0 + k - gv) (-1)^k
+    int sep_W;               //   kernel width (rows per record)
     const float* corr;       // [N / 2] grid correction per image pixel index (convolutional gridding), else NULL
     const float2* tw;        // twiddle set of side N
     void* H;                 // ring of column-pass results, [ring][N][ldh]
@@ -557,6 +561,67 @@ __device__ bool corr_task512(const FftParams& P, int k, unsigned char* work, con
     return true;
 }
 
+// Grid column u (zeroed by the caller) from the separable form of a kernel's list: entries [beg, end) name
+// the records whose support meets the column, sorted by (v0, record).  Entry e adds its record's sum (conjugated
+// for a mirror) times C(u - gu) C(v - gv) (-1)^(u + v) to each row v = v0 + k, k < W (mod N); the row weights
+// carry (-1)^k.  Lanes take an entry each, two chunks of 32 loaded together (their entries, then their sums
+// and weight rows).  Entries with equal v0 take turns by their rank among them, so that in each of a turn's W
+// steps the lanes write different cells, and each cell's additions come in a fixed order.
+template <int N, typename Cell>
+__device__ __forceinline__ void warp_gather_sep(const uint4* __restrict__ ent, const float* __restrict__ wrow,
+                                                const float2* __restrict__ V, int beg, int end, int W, int lane, int u,
+                                                Cell cell) {
+    constexpr int NB = 2;
+    for (int base = beg; base < end; base += 32 * NB) {
+        uint4 e[NB];
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            const int i = base + 32 * q + lane;
+            e[q] = i < end ? __ldg(ent + i) : make_uint4(0u, 0x7FFFFFFFu, 0u, 0u);
+        }
+        float2 x[NB];
+        float4 w0[NB], w1[NB];
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            x[q] = make_float2(0.f, 0.f);
+            w0[q] = w1[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (base + 32 * q + lane < end) {
+                x[q] = __ldg(V + (e[q].x & 0x7FFFFFFFu));
+                const float4* wr = reinterpret_cast<const float4*>(wrow + e[q].w);
+                w0[q] = __ldg(wr);
+                w1[q] = __ldg(wr + 1);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            if (base + 32 * q >= end) break;
+            const bool ok = base + 32 * q + lane < end;
+            const int v0 = (int)e[q].y;                     // 0x7FFFFFFF past the end: equal to no v0
+            float2 y = x[q];
+            if (e[q].x >> 31) y.y = -y.y;
+            const float wu = ((u ^ v0) & 1) ? -__uint_as_float(e[q].z) : __uint_as_float(e[q].z);
+            y = make_float2(y.x * wu, y.y * wu);
+            const float w[kSepMaxW] = {w0[q].x, w0[q].y, w0[q].z, w0[q].w, w1[q].x, w1[q].y, w1[q].z, w1[q].w};
+            const unsigned same = __match_any_sync(0xFFFFFFFFu, v0);
+            const int rank = __popc(same & ((1u << lane) - 1u));
+            const int turns = __reduce_max_sync(0xFFFFFFFFu, ok ? (unsigned)rank : 0u) + 1;
+            for (int t = 0; t < turns; t++) {
+                const bool mine = ok && rank == t;
+#pragma unroll
+                for (int k = 0; k < kSepMaxW; k++) {
+                    if (k >= W) break;
+                    if (mine) {
+                        float2* c = cell((v0 + k) & (N - 1));
+                        const float2 a = *c;
+                        *c = make_float2(fmaf(y.x, w[k], a.x), fmaf(y.y, w[k], a.y));
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+    }
+}
+
 // The tasks return the counter their completion increments (NULL after an abort); the caller releases it.
 // With WT (gridding with a convolution kernel) every gather entry carries a weight, the grid side N is twice
 // the image side, and the row tasks transform only the central N/2 rows and keep their central N/2 pixels,
@@ -588,21 +653,37 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     const int beg = off[u], end = off[u + 1];
     const float* wt = WT ? P.wt : nullptr;
     if constexpr (N >= 256 && N <= 1024) {
-        // no zeroing: the gridding marks the cells it writes, and the first pass reads only those; the entries
-        // (and weights) of four chunks are loaded together, then their sums (baseline order: after the entries)
         uint32_t* occ = s_occ + warp * 32;
-        occ[lane] = 0u;
-        __syncwarp();
-        // gather-ordered sums (planes of e_stride floats from the channel's first entry; nearest cell only) or
-        // baseline order
-        const float* Vre = reinterpret_cast<const float*>(V) - off[0];
-        auto valg = [&](int i, uint32_t b) {
-            if constexpr (!WT)
-                if (P.gathered) return make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i));
-            return val(b);
-        };
-        warp_gather_occ_batched<4>(P.ent, beg, end, lane, s, valg, idx, [&](int, int v) { return occ + (v & 31); },
-                                   1.0f, [] {}, wt);
+        bool sep = false;
+        if constexpr (WT && std::is_same_v<T, float2>) {
+            sep = P.sep != nullptr;
+            if (sep) {
+                // a kernel's separable list: the column zeroed, then each record's W rows added; all rows read
+                for (int e = lane; e < LD; e += 32) col[e] = make_float2(0.f, 0.f);
+                occ[lane] = 0xFFFFFFFFu;
+                __syncwarp();
+                const int* so = P.sep_off + f * (N / 2 + 1);
+                warp_gather_sep<N>(P.sep, P.sep_w, V, so[u], so[u + 1], P.sep_W, lane, u,
+                                   [&](int v) { return col + padx(v); });
+            }
+        }
+        if (!sep) {
+            // no zeroing: the gridding marks the cells it writes, and the first pass reads only those; the
+            // entries (and weights) of four chunks are loaded together, then their sums (baseline order: after
+            // the entries)
+            occ[lane] = 0u;
+            __syncwarp();
+            // gather-ordered sums (planes of e_stride floats from the channel's first entry; nearest cell only)
+            // or baseline order
+            const float* Vre = reinterpret_cast<const float*>(V) - off[0];
+            auto valg = [&](int i, uint32_t b) {
+                if constexpr (!WT)
+                    if (P.gathered) return make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i));
+                return val(b);
+            };
+            warp_gather_occ_batched<4>(P.ent, beg, end, lane, s, valg, idx,
+                                       [&](int, int v) { return occ + (v & 31); }, 1.0f, [] {}, wt);
+        }
         __syncwarp();
         if constexpr (N == 512)
             warp_fft512(col, s_twc, lane, occ[lane]);
@@ -1060,6 +1141,12 @@ blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec,
     const bool bf = prec == BLINK_PREC_BF16, wt = p.d_wt != nullptr;
     P.wt = p.d_wt;
     P.corr = p.d_corr;
+    if (wt && !bf && p.d_sep && p.N >= 256 && p.N <= 1024) {
+        P.sep_off = p.d_sep_off;
+        P.sep = p.d_sep;
+        P.sep_w = p.d_sep_w;
+        P.sep_W = p.support;
+    }
     if (wt && (!p.d_corr || p.N < 128))
         return set_error(BLINK_ERR_UNSUPPORTED, "convolutional gridding needs a grid side of at least 128");
     const int c = tune.ctas_per_sm;
