@@ -334,9 +334,6 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
     const int* off = P.ent_off + f * (M + 1);
     const int base = off[0];                          // the channel's first entry (gather order's position 0)
     const float* Vre = reinterpret_cast<const float*>(V) - base;
-    auto val = [&](int i, uint32_t b) {
-        return P.gathered ? make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i)) : __ldcs(V + b);
-    };
     const int u0 = cb * 2 * kCW + 2 * warp;           // the warp's columns u0, u0 + 1
     // 1 / (W * 2K) (or 1 / (W * K)) is applied to each gridded cell: the transforms are linear, so the image
     // comes out scaled, and a cell costs one product where an image pixel would
@@ -350,9 +347,16 @@ __device__ int* column_task512(const FftParams& P, int k, int cb, const float2* 
         __syncwarp();
         auto idx = [&](int u, int v) { return (2 * warp + (u - u0)) * LD + v; };
         auto occw = [&](int u, int v) { return occ + (u - u0) * 32 + (v & 31); };
-        warp_gather_occ_batched<4>(P.ent, off[u0], off[u0 + 2], lane, s, val, idx, occw, inv, [&]() {
-            if (lane == 0 && prev) seen = ld_acquire(prev);
-        });
+        auto gather = [&](auto val) {
+            warp_gather_occ_batched<4>(P.ent, off[u0], off[u0 + 2], lane, s, val, idx, occw, inv, [&]() {
+                if (lane == 0 && prev) seen = ld_acquire(prev);
+            });
+        };
+        // one instance per order of the sums, so that the choice stays outside the unrolled loads
+        if (FUSED || P.gathered)
+            gather([&](int i, uint32_t) { return make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i)); });
+        else
+            gather([&](int, uint32_t b) { return __ldcs(V + b); });
         __syncwarp();
         col512_pass1(s + 2 * warp * LD, lane, occ[lane]);
         col512_pass1(s + (2 * warp + 1) * LD, lane, occ[32 + lane]);
@@ -674,15 +678,16 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
             occ[lane] = 0u;
             __syncwarp();
             // gather-ordered sums (planes of e_stride floats from the channel's first entry; nearest cell only)
-            // or baseline order
+            // or baseline order, one instance each
             const float* Vre = reinterpret_cast<const float*>(V) - off[0];
-            auto valg = [&](int i, uint32_t b) {
-                if constexpr (!WT)
-                    if (P.gathered) return make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i));
-                return val(b);
+            auto gather = [&](auto valg) {
+                warp_gather_occ_batched<4>(P.ent, beg, end, lane, s, valg, idx,
+                                           [&](int, int v) { return occ + (v & 31); }, 1.0f, [] {}, wt);
             };
-            warp_gather_occ_batched<4>(P.ent, beg, end, lane, s, valg, idx,
-                                       [&](int, int v) { return occ + (v & 31); }, 1.0f, [] {}, wt);
+            if (!WT && P.gathered)
+                gather([&](int i, uint32_t) { return make_float2(__ldcs(Vre + i), __ldcs(Vre + P.e_stride + i)); });
+            else
+                gather([&](int, uint32_t b) { return val(b); });
         }
         __syncwarp();
         if constexpr (N == 512)
