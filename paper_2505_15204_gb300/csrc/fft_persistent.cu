@@ -707,9 +707,11 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
     }
     // all columns transformed (the wait's barrier), and the ring slot free of its previous image
     if (!wait_count(P, prev_done >= P.n_rb ? nullptr : prev, P.n_rb, s_flag)) return nullptr;
+    // with a kernel the row tasks read only the central N/2 rows, so only those are stored
+    constexpr int YS = WT ? N / 4 : 0, NY = WT ? N / 2 : N;
     T* out = static_cast<T*>(P.H) + (int64_t)slot * N * P.ldh + cb * CW;
-    for (int e = tid; e < N * CW; e += kPT) {
-        const int y = e / CW, c = e % CW;
+    for (int e = tid; e < NY * CW; e += kPT) {
+        const int y = YS + e / CW, c = e % CW;
         out[(int64_t)y * P.ldh + c] = s[c * LD + padx(y)];
     }
     return P.col_done + k;
