@@ -993,7 +993,12 @@ std::vector<FftTune> fft_tune_candidates(const Plan& p) {
         return {{48, 32, 2}, {64, 32, 2}, {32, 24, 3}, {48, 32, 3}, {48, 24, 3}, {64, 32, 3}, {64, 48, 3}};
     // a ring slot holds N x N/2 complex values: 4 MiB at side 1024, 16 MiB at 2048, so fewer slots stay in L2
     if (p.N >= 2048) return {{4, 2, 0}, {6, 4, 0}, {8, 4, 0}};
-    if (p.N == 1024) return {{8, 4, 0}, {12, 8, 0}, {16, 8, 0}, {8, 4, 2}, {12, 8, 2}, {16, 12, 2}, {24, 16, 0}};
+    // with a kernel only a slot's central rows are written, and longer rings (more images in flight for the
+    // heavier gridding) measured faster
+    if (p.N == 1024 && p.d_wt)
+        return {{12, 8, 0}, {16, 12, 2}, {24, 16, 2}, {32, 24, 2}, {48, 32, 2}, {48, 40, 2}, {64, 48, 2}};
+    if (p.N == 1024)
+        return {{8, 4, 0}, {12, 8, 0}, {16, 8, 0}, {12, 8, 2}, {16, 12, 2}, {24, 16, 0}, {32, 24, 0}, {32, 24, 2}};
     return {{24, 16, 0}, {16, 8, 0}, {32, 24, 0}, {48, 32, 0}, {64, 48, 0}, {40, 32, 0}, {32, 24, 3}};
 }
 int fft_ring_images_max() { return 64; }
