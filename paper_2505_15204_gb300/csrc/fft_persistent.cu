@@ -990,7 +990,8 @@ blink_status launch_sized(FftParams P, int n_sm, int ctas_per_sm, cudaStream_t s
 // these shapes per plan.
 std::vector<FftTune> fft_tune_candidates(const Plan& p) {
     if (p.N == 512 && !p.d_wt)
-        return {{48, 32, 2}, {64, 32, 2}, {32, 24, 3}, {48, 32, 3}, {48, 24, 3}, {64, 32, 3}, {64, 48, 3}};
+        return {{48, 32, 2}, {64, 32, 2}, {32, 24, 3}, {48, 32, 3}, {48, 24, 3}, {64, 32, 3}, {64, 48, 3},
+                {64, 40, 3}, {56, 32, 3}};
     // a ring slot holds N x N/2 complex values: 4 MiB at side 1024, 16 MiB at 2048, so fewer slots stay in L2
     if (p.N >= 2048) return {{4, 2, 0}, {6, 4, 0}, {8, 4, 0}};
     // with a kernel only a slot's central rows are written, and longer rings (more images in flight for the
