@@ -643,6 +643,8 @@ KB_CASES = [
     ("coarse", 20, 8, 4, 128, 0, 1, False, 8),             # grid 256: several images per channel
     ("uneven", 20, 3, 1, 64, 1, 0, True, 2),               # grid 128: zeroed columns, XX, no autos, flags
     ("tiny", None, None, 1, 1024, 0, 1, False, 6),         # grid 2048
+    ("uneven", 20, 3, 1, 256, 1, 0, True, 6),              # grid 512, separable list: XX, no autos, flags
+    ("precision", None, None, 1, 512, 0, 1, False, 8),     # grid 1024, separable list: eight row weights
 ]
 
 
