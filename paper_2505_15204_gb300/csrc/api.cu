@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "blink_internal.cuh"
+#include "kb_lists.h"
 
 namespace blink {
 
@@ -367,20 +368,9 @@ blink_status build_gather(Plan* p, const std::vector<uint32_t>& cells, const std
     return g.upload(p);
 }
 
-// ---- gridding with a convolution kernel ----------------------------------------------------------
-// Separable Kaiser-Bessel kernel of W cells on a grid twice the image side (oversampling 2):
-// C(t) = I0(beta sqrt(1 - (2t/W)^2)) beta / (W sinh beta) for |t| < W/2 (unit integral), with
-// beta = pi sqrt((W/2)^2 (3/2)^2 - 0.8) (Beatty, Nishimura and Pauly, IEEE TMI 2005, for oversampling 2).
+// ---- gridding with a convolution kernel (the kernel C(t) and its weights: kb_lists.h) ------------------
 constexpr double kPi = 3.14159265358979323846;
-
-double kb_beta(int W) { return kPi * std::sqrt(0.5625 * W * W - 0.8); }
-
-double kb_weight(double t, int W, double beta) {
-    const double h = 0.5 * W;
-    if (!(std::fabs(t) < h)) return 0.0;
-    const double r = t / h;
-    return std::cyl_bessel_i(0.0, beta * std::sqrt(1.0 - r * r)) * beta / (W * std::sinh(beta));
-}
+static_assert(kSepMaxW == kSepRowW, "the kernel's row weights per record and the plan's agree");
 
 // Its Fourier transform at nu cycles per cell (1 at nu = 0): with a = pi W nu and r = sqrt(|beta^2 - a^2|),
 // (sinh r / r) / (sinh beta / beta) below a = beta and (sin r / r) / (sinh beta / beta) above.
@@ -403,16 +393,8 @@ blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std:
     const int N = p->N, W = p->support, half = N / 2, F = p->F;
     const int64_t B = p->B, nkeys = (int64_t)half * N;
     const double beta = kb_beta(W), h = 0.5 * W, lim = 0.5 * N - h;
-    // the cells within W/2 of x (at most W + 1) and, when `ws` is given, their weights
-    auto support_cells = [&](double x, int* cs, double* ws) {
-        int n = 0;
-        for (int c = (int)std::floor(x - h); c <= (int)std::ceil(x + h); c++)
-            if (std::fabs((double)c - x) < h) {
-                if (ws) ws[n] = kb_weight((double)c - x, W, beta);
-                cs[n++] = c;
-            }
-        return n;
-    };
+    // the cells within W/2 of x and, when `ws` is given, their weights
+    auto support_cells = [&](double x, int* cs, double* ws) { return kb_support_cells(x, W, beta, cs, ws); };
     auto key = [&](int u, int v) { return (uint32_t)((int64_t)u * N + ((v % N) + N) % N); };
     // every half-plane contribution of channel f in baseline order: emit(key, (b << 1) | conj, weight)
     auto channel = [&](int f, bool weights, auto&& emit, int64_t& wsum, int64_t& dropped) {
@@ -517,72 +499,15 @@ blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std:
         };
         std::vector<Sep> sep(F);
         parallel([&](int f) {
-            Sep& S = sep[f];
-            struct Col {
-                int u, v0;
-                uint32_t rec, bc;
-                float wu;
-            };
-            std::vector<Col> cols;
-            int cu[20], cv[20];
-            double wu[20], wv[20];
-            // a record of nv rows from v0 (weights ws in increasing v) meeting the columns us[0 .. nu) (weights wus)
-            auto record = [&](uint32_t bc, int v0, const double* ws, int nv, const int* us, const double* wus, int nu) {
-                const uint32_t r = (uint32_t)(S.wrow.size() / kSepMaxW);
-                for (int k = 0; k < kSepMaxW; k++)
-                    S.wrow.push_back(k < nv ? (float)((k & 1) ? -ws[k] : ws[k]) : 0.f);
-                for (int q = 0; q < nu; q++) cols.push_back({us[q], v0, r, bc, (float)wus[q]});
-            };
-            for (int64_t b = 0; b < B; b++) {
-                const int i = bl[b].x, j = bl[b].y;
-                if (a->flags && (a->flags[i] || a->flags[j])) continue;
-                int us[20], n_us = 0;
-                double wus[20];
-                if (i == j) {
-                    if (!p->autos) continue;
-                    const int n = support_cells(0.0, cu, wu);
-                    for (int r = 0; r < n; r++)
-                        if (cu[r] >= 0) {
-                            us[n_us] = cu[r];
-                            wus[n_us++] = wu[r];
-                        }
-                    record((uint32_t)b, cu[0], wu, n, us, wus, n_us);
-                    continue;
-                }
-                const double gu = uvw[((size_t)f * B + b) * 3 + 0] / p->du, gv = uvw[((size_t)f * B + b) * 3 + 1] / p->du;
-                if (!(std::fabs(gu) <= lim && std::fabs(gv) <= lim)) continue;
-                const int nu = support_cells(gu, cu, wu), nv = support_cells(gv, cv, wv);
-                for (int r = 0; r < nu; r++)
-                    if (cu[r] >= 0) {
-                        us[n_us] = cu[r];
-                        wus[n_us++] = wu[r];
-                    }
-                if (n_us) record((uint32_t)b, cv[0], wv, nv, us, wus, n_us);
-                // the mirror: rows -cv[nv - 1] .. -cv[0], columns -cu[r] for cu[r] <= 0
-                double wm[20];
-                for (int k = 0; k < nv; k++) wm[k] = wv[nv - 1 - k];
-                n_us = 0;
-                for (int r = 0; r < nu; r++)
-                    if (cu[r] <= 0) {
-                        us[n_us] = -cu[r];
-                        wus[n_us++] = wu[r];
-                    }
-                if (n_us) record((uint32_t)b | 0x80000000u, -cv[nv - 1], wm, nv, us, wus, n_us);
-            }
-            std::sort(cols.begin(), cols.end(), [](const Col& x, const Col& y) {
-                return x.u != y.u ? x.u < y.u : (x.v0 != y.v0 ? x.v0 < y.v0 : x.rec < y.rec);
-            });
-            S.off.assign(half + 1, 0);
-            size_t e = 0;
-            for (int u = 0; u <= half; u++) {
-                while (e < cols.size() && cols[e].u < u) e++;
-                S.off[u] = (int)e;
-            }
-            S.ent.resize(cols.size());
-            for (size_t q = 0; q < cols.size(); q++) {
+            std::vector<SepEntry> ent;
+            kb_sep_channel(N, W, B, p->autos, p->du, uvw.data() + (size_t)f * B * 3,
+                           [&](int64_t b) { return a->flags && (a->flags[bl[b].x] || a->flags[bl[b].y]); },
+                           [&](int64_t b) { return bl[b].x == bl[b].y; }, ent, sep[f].wrow, sep[f].off);
+            sep[f].ent.resize(ent.size());
+            for (size_t q = 0; q < ent.size(); q++) {
                 uint32_t wbits;
-                std::memcpy(&wbits, &cols[q].wu, 4);
-                S.ent[q] = make_uint4(cols[q].bc, (uint32_t)cols[q].v0, wbits, cols[q].rec);
+                std::memcpy(&wbits, &ent[q].wu, 4);
+                sep[f].ent[q] = make_uint4(ent[q].bc, (uint32_t)ent[q].v0, wbits, ent[q].rec);
             }
         });
         std::vector<int64_t> e0(F + 1, 0), r0(F + 1, 0);
