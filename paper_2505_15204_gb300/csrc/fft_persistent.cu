@@ -997,7 +997,7 @@ std::vector<FftTune> fft_tune_candidates(const Plan& p) {
     // with a kernel only a slot's central rows are written, and longer rings (more images in flight for the
     // heavier gridding) measured faster
     if (p.N == 1024 && p.d_wt)
-        return {{12, 8, 0}, {16, 12, 2}, {24, 16, 2}, {32, 24, 2}, {48, 32, 2}, {48, 40, 2}, {64, 48, 2}};
+        return {{16, 12, 2}, {32, 24, 2}, {40, 32, 2}, {48, 32, 2}, {48, 40, 2}, {56, 32, 2}, {64, 32, 2}, {64, 48, 2}};
     if (p.N == 1024)
         return {{8, 4, 0}, {12, 8, 0}, {16, 8, 0}, {12, 8, 2}, {16, 12, 2}, {24, 16, 0}, {32, 24, 0}, {32, 24, 2}};
     return {{24, 16, 0}, {16, 8, 0}, {32, 24, 0}, {48, 32, 0}, {64, 48, 0}, {40, 32, 0}, {32, 24, 3}};
