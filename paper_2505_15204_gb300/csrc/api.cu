@@ -491,7 +491,7 @@ blink_status build_gather_kb(Plan* p, const std::vector<double>& uvw, const std:
     });
     // the separable form: per channel, records in baseline order (a visibility, then its mirror), and per
     // column the entries of the records whose support meets it, sorted by (v0, record)
-    if (W <= kSepMaxW && N >= 256 && N <= 1024 && B <= 0x7FFFFFFF) {
+    if (W <= kSepMaxW && fast_side(N) && B <= 0x7FFFFFFF) {
         struct Sep {
             std::vector<uint4> ent;            // sorted, channel-local record numbers in .w
             std::vector<float> wrow;           // [records][kSepMaxW]

@@ -73,7 +73,7 @@ struct Plan {
     uint2* d_ent = nullptr;                // [n_contrib] {u | v << 13 | conj << 31, b}, sorted by (u, v, b)
     float* d_wt = nullptr;                 // [n_contrib] kernel weight of each entry (convolution only)
     float* d_corr = nullptr;               // [Ni] grid correction 1 / c(nu) per image pixel index (convolution only)
-    // the separable form of a kernel's list (W <= kSepMaxW, persistent sides 256 to 1024): a record is a cross
+    // the separable form of a kernel's list (W <= kSepMaxW, the persistent kernel's sides): a record is a cross
     // visibility, its mirror (conjugate, at -g) or an autocorrelation, with its support's rows v0 .. v0 + W - 1
     // (v0 signed, rows taken mod N) and weights C(v - gv); per channel and column u, one entry for each record
     // whose support meets the column, sorted by (v0, record)

@@ -695,12 +695,26 @@ __device__ int* column_task(const FftParams& P, int k, int cb, const float2* s_t
         else
             warp_fft_masked<N, T>(col, s_twc, lane, occ[lane]);
     } else {
-        uint32_t key;
-        float2 x;
-        gather_entry(P.ent, wt, beg + lane, end, val, key, x);    // in flight while the column is zeroed
-        for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
-        __syncwarp();
-        warp_gather_column(P.ent, wt, beg, end, lane, s, val, idx, true, key, x);
+        bool sep = false;
+        if constexpr (WT && std::is_same_v<T, float2>) {
+            sep = P.sep != nullptr;
+            if (sep) {
+                // a kernel's separable list on the zeroed column
+                for (int e = lane; e < LD; e += 32) col[e] = make_float2(0.f, 0.f);
+                __syncwarp();
+                const int* so = P.sep_off + f * (N / 2 + 1);
+                warp_gather_sep<N>(P.sep, P.sep_w, V, so[u], so[u + 1], P.sep_W, lane, u,
+                                   [&](int v) { return col + padx(v); });
+            }
+        }
+        if (!sep) {
+            uint32_t key;
+            float2 x;
+            gather_entry(P.ent, wt, beg + lane, end, val, key, x);    // in flight while the column is zeroed
+            for (int e = lane; e < LD; e += 32) st_c(col + e, make_float2(0.f, 0.f));
+            __syncwarp();
+            warp_gather_column(P.ent, wt, beg, end, lane, s, val, idx, true, key, x);
+        }
         __syncwarp();
         NoOut none;
         warp_fft<N, false, T, NoOut>(col, s_twc, lane, none);
@@ -1154,7 +1168,7 @@ blink_status launch_fft_persistent(const Plan& p, const FftTune& tune, int prec,
     const bool bf = prec == BLINK_PREC_BF16, wt = p.d_wt != nullptr;
     P.wt = p.d_wt;
     P.corr = p.d_corr;
-    if (wt && !bf && p.d_sep && p.N >= 256 && p.N <= 1024) {
+    if (wt && !bf && p.d_sep) {
         P.sep_off = p.d_sep_off;
         P.sep = p.d_sep;
         P.sep_w = p.d_sep_w;

@@ -1,7 +1,7 @@
 """The separable gather list of Kaiser-Bessel gridding (kb_lists.h), built on the CPU and expanded back into
 half-plane cells, against the oracle's direct FP64 gridding (oracle_grid_kb).
 
-The persistent imaging kernel grids with this list at the sides 256 to 1024 (W <= 8): one entry per
+The persistent imaging kernel grids with this list at every side it serves (W <= 8): one entry per
 (visibility or its mirror, column of its support) with the column weight C(u - gu), the record's first row v0
 and a row of W weights C(v - gv) (-1)^k.  A small host program compiles the library's own list builder,
 expands every entry over its W rows (mod N) in FP64 and prints the half plane u in [0, N/2); the test feeds it
