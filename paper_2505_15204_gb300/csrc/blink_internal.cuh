@@ -115,7 +115,9 @@ struct blink_context {
     int n_sm = 0;
     int* d_status = nullptr;
     std::vector<blink::Plan*> plans;       // most recent last
-    blink::Workspace ws[9];                 // 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays, 8 averaged grids
+    // workspaces: 0 vis, 1 ring, 2 voltages / grid, 3 images, 4 counters, 5 plain form, 6 gains, 7 delays,
+    // 8 averaged grids
+    blink::Workspace ws[9];
     float2* tw[16] = {};                   // twiddle tables by log2(side)
     std::vector<std::pair<int, float2*>> tw_any;   // unit-root tables of the other sides (fft_mixed.cu)
     blink::FftWait fft_wait;               // dependency-wait budget of the persistent FFT kernel
